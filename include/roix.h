@@ -1,0 +1,198 @@
+/* libroix: GB300 (sm_103a) implementation of the ROIX-Comp hot path.
+ *
+ * ROIX-Comp (arXiv 2602.15917) compresses X-ray CT data by keeping only the
+ * region of interest: background subtraction and binarisation (Sec. 4.1),
+ * extraction of the object as row geometry plus a pixel section (Sec. 4.2.1-
+ * 4.2.2), error-bounded quantisation of the pixels (Sec. 4.2.3) and an
+ * error-bounded prediction + entropy coder in the role of Sz3 (Sec. 4.3), with
+ * the matching reconstruction (Sec. 4.3, decompression).
+ *
+ * Conventions for every call:
+ *  - Volumes are (nx, ny, nz) with x fastest: voxel (x, y, z) sits at index
+ *    x + nx * (y + ny * z); row r = y + ny * z holds nx voxels. 1 <= nx <= 65534.
+ *    A 2D image is nz = 1. Any of nx, ny, nz may be 0 only for an empty volume.
+ *  - Every data pointer is DEVICE memory owned by the caller (e.g. a tensor's
+ *    data pointer), unless the name ends in _host. Pointers to parameter structs
+ *    are host memory and are read before the call returns.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls only enqueue work on it and return; outputs are valid once the
+ *    stream has reached that point. Counts produced on the device are written
+ *    to *_dev outputs (device memory), never returned on the host.
+ *  - Argument errors are returned at once (ROIX_EINVAL) and nothing is
+ *    enqueued. Errors found on the device (a container that does not fit its
+ *    buffer, a corrupt container, a wait that ran out) are recorded in the
+ *    context's status word; roix_sync() returns the first one and clears it.
+ *    No call traps the GPU on any input; outputs are unspecified after an error.
+ *  - A context is used from one host thread and one stream at a time: its
+ *    workspace is shared by the calls made on it. Use one context per stream
+ *    for concurrent work. Workspace grows on demand (cudaMalloc, which
+ *    synchronises the device); roix_reserve() pre-sizes it.
+ */
+#ifndef ROIX_H_
+#define ROIX_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ROIX_OK = 0,
+  ROIX_EINVAL = 1,     /* bad argument: nothing was enqueued */
+  ROIX_ENOMEM = 2,     /* device workspace could not be allocated */
+  ROIX_ECAPACITY = 3,  /* output buffer too small; *size_dev holds the size needed */
+  ROIX_ECORRUPT = 4,   /* container inconsistent with itself or with size/dims/dtype */
+  ROIX_ETIMEOUT = 5,   /* a bounded inter-block wait ran out (results invalid) */
+  ROIX_ECUDA = 6,      /* a CUDA runtime call failed (see roix_last_error) */
+  ROIX_EBUSY = 7
+} roix_status;
+
+typedef enum { ROIX_F32 = 1, ROIX_U16 = 2 } roix_dtype;
+
+typedef struct {
+  uint64_t nx, ny, nz;
+} roix_dims;
+
+/* Region of interest (Sec. 4.1.1, 4.1.3-4.1.4, 4.2.1):
+ *   v = value (float32) or raw - dark (uint16, exact integer: M = I - B with a
+ *       constant background level B);
+ *   T = [v > threshold] (cmp 0) or [v < threshold] (cmp 1), comparison of the
+ *       exact value against the binary64 threshold; NaN is never in T;
+ *   keep = 1: T is reduced to its largest connected component (most voxels,
+ *       ties to the component holding the smallest voxel index) under 6- or
+ *       26-connectivity (4 or 8 in 2D): the paper's "largest object" step;
+ *   D = T dilated by the (2*dilate+1)^3 cube (3x3 in 2D), clipped at the
+ *       borders; D is the set of retained voxels. */
+typedef struct {
+  int32_t cmp;           /* 0: v > threshold, 1: v < threshold */
+  int32_t keep;          /* 0: all of T, 1: largest component of T */
+  int32_t connectivity;  /* 6 or 26 */
+  int32_t dilate;        /* 0 or 1 */
+  double threshold;
+  double dark;           /* uint16: integer in [0, 65535]; float32: must be 0 */
+} roix_roi;
+
+/* Error bound (Sec. 4.2.3: E_abs with |Q - D| <= E_abs on every retained voxel).
+ * mode 0: E_abs = value. mode 1: E_abs = value * (max - min) over the finite
+ * retained values (the value-range convention of Sz3, applied to the pixel
+ * section as in ROIX-Sz3). value must be finite and > 0 (uint16 mode 0: >= 0,
+ * integer part used; 0 = lossless). */
+typedef struct {
+  int32_t mode;
+  double value;
+} roix_eb;
+
+/* Entropy-coder settings and the reconstruction fill value. */
+typedef struct {
+  uint32_t radius;  /* R: deltas with |d| < R are coded as symbol d + R;
+                       2 <= R <= 2048 (default 512) */
+  uint32_t chunk;   /* C: symbols per independently decodable chunk; a power of
+                       two in [256, 16384] (default 4096) */
+  double fill;      /* value of non-retained voxels after decoding (uint16:
+                       integer in [0, 65535]) */
+} roix_params;
+
+/* Error-bound constants as computed on the device (written by roix_quantize,
+ * read by roix_encode). Layout is fixed: 40 bytes. */
+typedef struct {
+  double eb_abs;            /* E_abs */
+  double vmin, vmax;        /* finite range of the retained values */
+  float two_eb, inv2eb;     /* float32 lattice step and its reciprocal */
+  float bound;              /* acceptance bound of |x - x_hat| (< E_abs) */
+  int32_t eb_int;           /* uint16: integer half-width */
+} roix_eb_info;
+
+typedef struct roix_ctx roix_ctx;
+
+/* ----------------------------------------------------------- context */
+roix_status roix_ctx_create(int device, roix_ctx** out);
+roix_status roix_ctx_destroy(roix_ctx* ctx);
+/* Pre-sizes the workspace to at least `bytes` (call before graph capture). */
+roix_status roix_reserve(roix_ctx* ctx, size_t bytes);
+/* Workspace bytes roix_compress needs for this volume. */
+size_t roix_workspace_size(roix_dtype dtype, roix_dims dims, const roix_roi* roi,
+                           const roix_params* params, uint64_t cap);
+/* Waits for `stream`, returns the first device-side error since the last call
+ * (or ROIX_ECUDA) and clears it. */
+roix_status roix_sync(roix_ctx* ctx, void* stream);
+const char* roix_last_error(const roix_ctx* ctx);
+const char* roix_status_string(roix_status s);
+/* Words of a bit mask: rows = ny*nz rows of ceil(nx/32) uint32 words; voxel x
+ * of a row is bit (x % 32) of word (x / 32); bits at x >= nx are 0. */
+uint64_t roix_mask_words(roix_dims dims);
+/* Upper bound of a container's size in bytes for this volume (worst case:
+ * every voxel retained, every value an outlier). */
+uint64_t roix_compress_bound(roix_dtype dtype, roix_dims dims, const roix_params* params);
+
+/* ------------------------------------------------------------- stages
+ * Chained, the four stages give the bytes of roix_compress:
+ *   extract_roi -> compact -> quantize -> encode. */
+
+/* Sec. 4.1-4.2.1: retained-voxel mask D (layout of roix_mask_words) and its
+ * voxel count (*popcount_dev, uint64). */
+roix_status roix_extract_roi(roix_ctx* ctx, const void* in, roix_dtype dtype, roix_dims dims,
+                             const roix_roi* roi, uint32_t* mask_out, uint64_t* popcount_dev,
+                             void* stream);
+
+/* Sec. 4.2.2: geometry and pixel section of the voxels set in `mask`.
+ *  pixels_out: the retained values in voxel order (dtype; room for every voxel
+ *              of the volume, nx*ny*nz values);
+ *  counts_out: per row, the number of boundaries (uint16, ny*nz entries);
+ *  bounds_out: the boundaries, row after row: x positions where the mask turns
+ *              on (x_start) or off (x_end, one past the last voxel), so a row's
+ *              runs are [b0, b1), [b2, b3), ...; room for bounds_cap entries;
+ *  sizes_dev:  [0] = n retained voxels, [1] = number of boundaries (uint64).
+ *  More than bounds_cap boundaries sets ROIX_ECAPACITY. */
+roix_status roix_compact(roix_ctx* ctx, const void* in, roix_dtype dtype, roix_dims dims,
+                         const uint32_t* mask, void* pixels_out, uint16_t* counts_out,
+                         uint16_t* bounds_out, uint64_t bounds_cap, uint64_t* sizes_dev,
+                         void* stream);
+
+/* Sec. 4.2.3: error-bounded quantisation of a pixel sequence D[0..n-1] into
+ * codes Q with |Q*2E_abs - D| <= E_abs (float32: reconstruction checked in
+ * binary32; values that fail, and non-finite ones, are outliers: bit k of
+ * outlier_bits_out set, q_out[k] = 0). n = *n_dev when n_dev is not NULL (it
+ * must not exceed n_cap), else n_cap. Writes the constants to *info_dev. */
+roix_status roix_quantize(roix_ctx* ctx, const void* pixels, roix_dtype dtype, uint64_t n_cap,
+                          const uint64_t* n_dev, const roix_eb* eb, double dark,
+                          int32_t* q_out, uint32_t* outlier_bits_out,
+                          roix_eb_info* info_dev, void* stream);
+
+/* Sec. 4.3: prediction (1D Lorenzo over the pixel section), canonical Huffman
+ * coding and the container. Inputs are the outputs of the three calls above
+ * (sizes_dev of roix_compact). Writes at most `cap` bytes to `out` and the
+ * container size to *size_dev (uint64; the size needed if it exceeds cap,
+ * with ROIX_ECAPACITY). */
+roix_status roix_encode(roix_ctx* ctx, const int32_t* q, const uint32_t* outlier_bits,
+                        const void* pixels, uint64_t n_cap, const uint64_t* sizes_dev,
+                        const uint16_t* counts, const uint16_t* bounds,
+                        const roix_eb_info* info_dev, roix_dtype dtype, roix_dims dims,
+                        const roix_roi* roi, const roix_eb* eb, const roix_params* params,
+                        void* out, uint64_t cap, uint64_t* size_dev, void* stream);
+
+/* Sec. 4.3, decompression: rebuilds the volume (dtype, dims must match the
+ * container) from `size` bytes at `in`. Retained voxels get their
+ * error-bounded value, the others params.fill. */
+roix_status roix_decode(roix_ctx* ctx, const void* in, uint64_t size, void* out,
+                        roix_dtype dtype, roix_dims dims, void* stream);
+
+/* Per-stage timing: with profiling on, roix_compress records a CUDA event on
+ * its stream after each stage; roix_profile_read waits for them and writes up
+ * to `max` stage durations (ms) of the last call, returning their number. The
+ * stages are: reset, binarisation, compaction, symbols, codebook, pack,
+ * finalise. */
+roix_status roix_profile(roix_ctx* ctx, int on);
+int roix_profile_read(roix_ctx* ctx, float* ms, int max);
+
+/* The fused path: the same bytes as the four stages, in fewer passes. */
+roix_status roix_compress(roix_ctx* ctx, const void* in, roix_dtype dtype, roix_dims dims,
+                          const roix_roi* roi, const roix_eb* eb, const roix_params* params,
+                          void* out, uint64_t cap, uint64_t* size_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ROIX_H_ */

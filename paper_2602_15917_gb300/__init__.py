@@ -1,0 +1,297 @@
+"""Python binding of libroix, the GB300 (sm_103a) ROIX-Comp hot path.
+
+The binding only marshals arguments: every step runs in the CUDA kernels of
+``csrc/`` behind the C ABI of ``include/roix.h``. PyTorch supplies device
+memory and streams. There is no CPU fallback: if ``libroix.so`` has not been
+built (``__graft_entry__.build()``) or no GPU is present, the calls raise.
+
+Two layers:
+* ``lib()`` - the ctypes handle; its functions carry the C names
+  (``roix_compress``, ``roix_extract_roi``, ``roix_compact``,
+  ``roix_quantize``, ``roix_encode``, ``roix_decode`` ...) and take raw pointers.
+* ``Roix`` - the same calls on torch tensors, with the ROI / error-bound /
+  coder settings given as keyword arguments (``eb``, ``eb_mode``, ``cmp``,
+  ``threshold``, ``keep``, ``connectivity``, ``dilate``, ``dark``, ``fill``,
+  ``radius``, ``chunk``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+from . import _build
+
+F32, U16 = 1, 2
+STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory",
+          3: "output buffer too small", 4: "corrupt container", 5: "wait timed out",
+          6: "CUDA error", 7: "busy"}
+
+
+class RoixError(RuntimeError):
+    def __init__(self, status: int, msg: str = ""):
+        super().__init__(f"{STATUS.get(status, status)}{': ' + msg if msg else ''}")
+        self.status = status
+
+
+class Dims(C.Structure):
+    _fields_ = [("nx", C.c_uint64), ("ny", C.c_uint64), ("nz", C.c_uint64)]
+
+
+class Roi(C.Structure):
+    _fields_ = [("cmp", C.c_int32), ("keep", C.c_int32), ("connectivity", C.c_int32),
+                ("dilate", C.c_int32), ("threshold", C.c_double), ("dark", C.c_double)]
+
+
+class Eb(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("value", C.c_double)]
+
+
+class Params(C.Structure):
+    _fields_ = [("radius", C.c_uint32), ("chunk", C.c_uint32), ("fill", C.c_double)]
+
+
+class EbInfo(C.Structure):
+    _fields_ = [("eb_abs", C.c_double), ("vmin", C.c_double), ("vmax", C.c_double),
+                ("two_eb", C.c_float), ("inv2eb", C.c_float), ("bound", C.c_float),
+                ("eb_int", C.c_int32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """The loaded libroix (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError("libroix.so is not built: call __graft_entry__.build()")
+            L = C.CDLL(_build.LIB)
+            P, u64, i32, st = C.c_void_p, C.c_uint64, C.c_int32, C.c_int
+            D, R, E, PR = Dims, C.POINTER(Roi), C.POINTER(Eb), C.POINTER(Params)
+            sig = {
+                "roix_ctx_create": (st, [i32, C.POINTER(P)]),
+                "roix_ctx_destroy": (st, [P]),
+                "roix_reserve": (st, [P, C.c_size_t]),
+                "roix_workspace_size": (C.c_size_t, [i32, D, R, PR, u64]),
+                "roix_sync": (st, [P, P]),
+                "roix_last_error": (C.c_char_p, [P]),
+                "roix_status_string": (C.c_char_p, [st]),
+                "roix_mask_words": (u64, [D]),
+                "roix_compress_bound": (u64, [i32, D, PR]),
+                "roix_extract_roi": (st, [P, P, i32, D, R, P, P, P]),
+                "roix_compact": (st, [P, P, i32, D, P, P, P, P, u64, P, P]),
+                "roix_quantize": (st, [P, P, i32, u64, P, E, C.c_double, P, P, P, P]),
+                "roix_encode": (st, [P, P, P, P, u64, P, P, P, P, i32, D, R, E, PR, P, u64, P,
+                                     P]),
+                "roix_decode": (st, [P, P, u64, P, i32, D, P]),
+                "roix_compress": (st, [P, P, i32, D, R, E, PR, P, u64, P, P]),
+                "roix_profile": (st, [P, C.c_int]),
+                "roix_profile_read": (C.c_int, [P, C.POINTER(C.c_float), C.c_int]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def symbols():
+    """Names of the entry points the binding knows (all declared in roix.h)."""
+    return ["roix_ctx_create", "roix_ctx_destroy", "roix_reserve", "roix_workspace_size",
+            "roix_sync", "roix_last_error", "roix_status_string", "roix_mask_words",
+            "roix_compress_bound", "roix_extract_roi", "roix_compact", "roix_quantize",
+            "roix_encode", "roix_decode", "roix_compress", "roix_profile",
+            "roix_profile_read"]
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.uint16:
+        return U16
+    raise TypeError("float32 or uint16 tensors only")
+
+
+def dims_of(shape) -> Dims:
+    shape = tuple(int(s) for s in shape)
+    if len(shape) == 1:
+        return Dims(shape[0], 1, 1)
+    if len(shape) == 2:
+        return Dims(shape[1], shape[0], 1)
+    if len(shape) == 3:
+        return Dims(shape[2], shape[1], shape[0])
+    raise ValueError("1D, 2D or 3D volumes only")
+
+
+def roi_of(cmp="gt", threshold=0.1, keep="all", connectivity=26, dilate=1, dark=0.0, **_) -> Roi:
+    return Roi(0 if cmp == "gt" else 1, 0 if keep == "all" else 1, int(connectivity),
+               int(dilate), float(threshold), float(dark))
+
+
+def eb_of(eb=1e-3, eb_mode="abs", **_) -> Eb:
+    return Eb(0 if eb_mode == "abs" else 1, float(eb))
+
+
+def params_of(radius=512, chunk=4096, fill=0.0, **_) -> Params:
+    return Params(int(radius), int(chunk), float(fill))
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+class Roix:
+    """A libroix context on one GPU, with tensor-level calls."""
+
+    def __init__(self, device: int = 0):
+        self.L = lib()
+        self.device = device
+        h = C.c_void_p()
+        self._check(self.L.roix_ctx_create(int(device), C.byref(h)), ctx=False)
+        self.ctx = h
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.L.roix_ctx_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, status: int, ctx: bool = True):
+        if status != 0:
+            msg = self.L.roix_last_error(self.ctx).decode() if ctx and self.ctx else ""
+            raise RoixError(status, msg)
+
+    def sync(self, stream=None):
+        self._check(self.L.roix_sync(self.ctx, _stream(stream)))
+
+    def reserve(self, nbytes: int):
+        self._check(self.L.roix_reserve(self.ctx, int(nbytes)))
+
+    def profile(self, on: bool = True):
+        self._check(self.L.roix_profile(self.ctx, int(on)))
+
+    def profile_read(self, n: int = 16):
+        buf = (C.c_float * n)()
+        k = self.L.roix_profile_read(self.ctx, buf, n)
+        return [buf[i] for i in range(k)]
+
+    def bound(self, shape, dtype=torch.float32, **cfg) -> int:
+        code = F32 if dtype == torch.float32 else U16
+        return int(self.L.roix_compress_bound(code, dims_of(shape), C.byref(params_of(**cfg))))
+
+    def workspace_size(self, shape, dtype=torch.float32, cap=None, **cfg) -> int:
+        code = F32 if dtype == torch.float32 else U16
+        cap = self.bound(shape, dtype, **cfg) if cap is None else cap
+        return int(self.L.roix_workspace_size(code, dims_of(shape), C.byref(roi_of(**cfg)),
+                                              C.byref(params_of(**cfg)), int(cap)))
+
+    # ------------------------------------------------------------ fused path
+    def compress(self, x: torch.Tensor, out: torch.Tensor | None = None, cap: int | None = None,
+                 size: torch.Tensor | None = None, stream=None, **cfg):
+        """Enqueues the whole compression of x; returns (out, size) with size a
+        1-element uint64 device tensor holding the container's byte count."""
+        assert x.is_cuda and x.is_contiguous()
+        if out is None:
+            cap = cap if cap is not None else x.numel() * x.element_size() + 65536
+            out = torch.empty(cap, dtype=torch.uint8, device=x.device)
+        cap = out.numel() if cap is None else cap
+        if size is None:
+            size = torch.zeros(1, dtype=torch.uint64, device=x.device)
+        self._check(self.L.roix_compress(
+            self.ctx, x.data_ptr(), _dtype_code(x), dims_of(x.shape), C.byref(roi_of(**cfg)),
+            C.byref(eb_of(**cfg)), C.byref(params_of(**cfg)), out.data_ptr(), int(cap),
+            size.data_ptr(), _stream(stream)))
+        return out, size
+
+    def compress_bytes(self, x: torch.Tensor, **cfg) -> torch.Tensor:
+        """compress + sync; returns the container as a uint8 device tensor. An
+        output too small for the container is grown once to the size needed."""
+        out, size = self.compress(x, **cfg)
+        try:
+            self.sync()
+        except RoixError as e:
+            if e.status != 3:
+                raise
+            need = int(size.item())
+            out, size = self.compress(x, cap=need, out=torch.empty(need, dtype=torch.uint8,
+                                                                   device=x.device), **cfg)
+            self.sync()
+        return out[:int(size.item())]
+
+    def decode(self, buf: torch.Tensor, shape, dtype=torch.float32, size: int | None = None,
+               out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        assert buf.is_cuda and buf.dtype == torch.uint8
+        if out is None:
+            out = torch.empty(shape, dtype=dtype, device=buf.device)
+        size = buf.numel() if size is None else size
+        self._check(self.L.roix_decode(self.ctx, buf.data_ptr(), int(size), out.data_ptr(),
+                                       _dtype_code(out), dims_of(shape), _stream(stream)))
+        return out
+
+    # ---------------------------------------------------------------- stages
+    def extract_roi(self, x: torch.Tensor, stream=None, **cfg):
+        d = dims_of(x.shape)
+        words = int(self.L.roix_mask_words(d))
+        mask = torch.empty(max(words, 1), dtype=torch.int32, device=x.device)
+        pop = torch.zeros(1, dtype=torch.uint64, device=x.device)
+        self._check(self.L.roix_extract_roi(self.ctx, x.data_ptr(), _dtype_code(x), d,
+                                            C.byref(roi_of(**cfg)), mask.data_ptr(),
+                                            pop.data_ptr(), _stream(stream)))
+        return mask[:words], pop
+
+    def compact(self, x: torch.Tensor, mask: torch.Tensor, bounds_cap: int | None = None,
+                stream=None):
+        d = dims_of(x.shape)
+        rows = d.ny * d.nz
+        bounds_cap = rows * (d.nx + 1) if bounds_cap is None else bounds_cap
+        pixels = torch.empty(max(x.numel(), 1), dtype=x.dtype, device=x.device)
+        counts = torch.empty(max(rows, 1), dtype=torch.uint16, device=x.device)
+        bounds = torch.empty(max(bounds_cap, 1), dtype=torch.uint16, device=x.device)
+        sizes = torch.zeros(2, dtype=torch.uint64, device=x.device)
+        self._check(self.L.roix_compact(self.ctx, x.data_ptr(), _dtype_code(x), d,
+                                        mask.data_ptr(), pixels.data_ptr(), counts.data_ptr(),
+                                        bounds.data_ptr(), int(bounds_cap), sizes.data_ptr(),
+                                        _stream(stream)))
+        return pixels, counts[:rows], bounds, sizes
+
+    def quantize(self, pixels: torch.Tensor, n_cap: int | None = None,
+                 n_dev: torch.Tensor | None = None, stream=None, **cfg):
+        n_cap = pixels.numel() if n_cap is None else n_cap
+        dark = cfg.get("dark", 0.0)
+        q = torch.empty(max(n_cap, 1), dtype=torch.int32, device=pixels.device)
+        ob = torch.empty(max((n_cap + 31) // 32, 1), dtype=torch.int32, device=pixels.device)
+        info = torch.zeros(C.sizeof(EbInfo), dtype=torch.uint8, device=pixels.device)
+        self._check(self.L.roix_quantize(
+            self.ctx, pixels.data_ptr(), _dtype_code(pixels), int(n_cap),
+            n_dev.data_ptr() if n_dev is not None else None, C.byref(eb_of(**cfg)), float(dark),
+            q.data_ptr(), ob.data_ptr(), info.data_ptr(), _stream(stream)))
+        return q, ob, info
+
+    def encode(self, q, obits, pixels, n_cap, sizes, counts, bounds, info, shape, dtype,
+               cap: int | None = None, out: torch.Tensor | None = None, stream=None, **cfg):
+        dev = q.device
+        if out is None:
+            cap = cap if cap is not None else self.bound(shape, dtype, **cfg)
+            out = torch.empty(cap, dtype=torch.uint8, device=dev)
+        cap = out.numel() if cap is None else cap
+        size = torch.zeros(1, dtype=torch.uint64, device=dev)
+        self._check(self.L.roix_encode(
+            self.ctx, q.data_ptr(), obits.data_ptr(), pixels.data_ptr(), int(n_cap),
+            sizes.data_ptr(), counts.data_ptr(), bounds.data_ptr(), info.data_ptr(),
+            F32 if dtype == torch.float32 else U16, dims_of(shape), C.byref(roi_of(**cfg)),
+            C.byref(eb_of(**cfg)), C.byref(params_of(**cfg)), out.data_ptr(), int(cap),
+            size.data_ptr(), _stream(stream)))
+        return out, size

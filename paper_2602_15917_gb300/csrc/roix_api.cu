@@ -1,0 +1,600 @@
+// Host side of libroix: argument checks, workspace planning and the ordered
+// kernel launches behind each entry point of include/roix.h.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "roix_internal.cuh"
+
+using namespace roix;
+
+struct roix_ctx {
+  int device = 0;
+  int sms = 0;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  u32 pending = 0;  // status carried over a workspace reallocation
+  std::string err;
+  // per-stage timing (profiling mode)
+  int profile = 0;
+  cudaEvent_t ev[16] = {};
+  int nev = 0;
+  float stage_ms[16] = {};
+  int stage_count = 0;
+};
+
+namespace {
+
+// ---------------------------------------------------------- device guard
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+roix_status fail(roix_ctx* ctx, roix_status s, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return s;
+}
+
+roix_status cuda_fail(roix_ctx* ctx, cudaError_t e, const char* where) {
+  return fail(ctx, ROIX_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// --------------------------------------------------------------- arena
+struct Arena {
+  size_t off = 0;
+  size_t take(size_t bytes, size_t align = 256) {
+    off = (off + align - 1) / align * align;
+    size_t o = off;
+    off += bytes;
+    return o;
+  }
+};
+
+constexpr size_t kStateBytes = 256;
+static_assert(sizeof(State) <= kStateBytes, "state fits its slot");
+
+roix_status ensure_ws(roix_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->ws_bytes) return ROIX_OK;
+  if (ctx->ws) {
+    // keep an unread device status across the reallocation
+    cudaDeviceSynchronize();
+    u32 st = 0;
+    cudaMemcpy(&st, ctx->ws, 4, cudaMemcpyDeviceToHost);
+    if (!ctx->pending) ctx->pending = st;
+    cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+  }
+  size_t want = bytes + (bytes >> 3);  // 12.5 % headroom against regrowth
+  cudaError_t e = cudaMalloc(&ctx->ws, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    e = cudaMalloc(&ctx->ws, bytes);
+    want = bytes;
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ctx->ws = nullptr;
+    return fail(ctx, ROIX_ENOMEM, "workspace allocation of " + std::to_string(bytes) + " bytes failed");
+  }
+  ctx->ws_bytes = want;
+  cudaMemset(ctx->ws, 0, kStateBytes);
+  return ROIX_OK;
+}
+
+// ----------------------------------------------------------- parameters
+float f32_round_down(double t) {
+  float f = (float)t;
+  if ((double)f > t) f = std::nextafterf(f, -INFINITY);
+  return f;
+}
+float f32_round_up(double t) {
+  float f = (float)t;
+  if ((double)f < t) f = std::nextafterf(f, INFINITY);
+  return f;
+}
+
+bool dims_ok(roix_dims d) {
+  if (d.nx > 65534) return false;
+  if (d.ny > 0xffffffffull || d.nz > 0xffffffffull) return false;
+  const double N = (double)d.nx * (double)d.ny * (double)d.nz;
+  return N < 1.1e12;
+}
+
+roix_status make_desc(roix_ctx* ctx, roix_dtype dtype, roix_dims dims, const roix_roi* roi,
+                      const roix_eb* eb, const roix_params* prm, Desc* d) {
+  std::memset(d, 0, sizeof(*d));
+  if (dtype != ROIX_F32 && dtype != ROIX_U16) return fail(ctx, ROIX_EINVAL, "dtype must be ROIX_F32 or ROIX_U16");
+  if (!dims_ok(dims)) return fail(ctx, ROIX_EINVAL, "dims: nx <= 65534, ny, nz < 2^32, N < 1.1e12");
+  d->nx = dims.nx;
+  d->ny = dims.ny;
+  d->nz = dims.nz;
+  d->rows = dims.ny * dims.nz;
+  d->W = (dims.nx + 31) / 32;
+  d->N = dims.nx * dims.ny * dims.nz;
+  d->dtype = dtype;
+  if (roi) {
+    if (roi->cmp != 0 && roi->cmp != 1) return fail(ctx, ROIX_EINVAL, "roi.cmp must be 0 or 1");
+    if (roi->keep != 0 && roi->keep != 1) return fail(ctx, ROIX_EINVAL, "roi.keep must be 0 or 1");
+    if (roi->connectivity != 6 && roi->connectivity != 26)
+      return fail(ctx, ROIX_EINVAL, "roi.connectivity must be 6 or 26");
+    if (roi->dilate != 0 && roi->dilate != 1) return fail(ctx, ROIX_EINVAL, "roi.dilate must be 0 or 1");
+    d->cmp = roi->cmp;
+    d->keep = roi->keep;
+    d->conn = roi->connectivity;
+    d->dilate = roi->dilate;
+    d->threshold = roi->threshold;
+    d->dark_d = roi->dark;
+    if (dtype == ROIX_F32) {
+      if (roi->dark != 0.0) return fail(ctx, ROIX_EINVAL, "roi.dark must be 0 for float32 input");
+      d->thr_never = std::isnan(roi->threshold);
+      d->thr_f = roi->cmp == 0 ? f32_round_down(roi->threshold) : f32_round_up(roi->threshold);
+    } else {
+      if (!(roi->dark >= 0.0 && roi->dark <= 65535.0 && roi->dark == std::floor(roi->dark)))
+        return fail(ctx, ROIX_EINVAL, "roi.dark must be an integer in [0, 65535]");
+      d->dark = (int)roi->dark;
+      const double t = roi->threshold;
+      d->thr_never = std::isnan(t);
+      double ti = roi->cmp == 0 ? std::floor(t) : std::ceil(t);
+      if (ti < -1e6) ti = -1e6;
+      if (ti > 1e6) ti = 1e6;
+      d->thr_i = std::isnan(ti) ? 0 : (int)ti;
+    }
+  }
+  if (eb) {
+    if (eb->mode != 0 && eb->mode != 1) return fail(ctx, ROIX_EINVAL, "eb.mode must be 0 or 1");
+    const bool lossless_u16 = dtype == ROIX_U16 && eb->mode == 0 && eb->value == 0.0;
+    if (!(std::isfinite(eb->value) && (eb->value > 0.0 || lossless_u16)))
+      return fail(ctx, ROIX_EINVAL, "eb.value must be finite and > 0");
+    d->eb_mode = eb->mode;
+    d->eb_value = eb->value;
+  }
+  if (prm) {
+    if (prm->radius < 2 || prm->radius > kMaxRadius)
+      return fail(ctx, ROIX_EINVAL, "params.radius must be in [2, 2048]");
+    const u32 C = prm->chunk;
+    if (C < 256 || C > 16384 || (C & (C - 1)))
+      return fail(ctx, ROIX_EINVAL, "params.chunk must be a power of two in [256, 16384]");
+    if (dtype == ROIX_U16 &&
+        !(prm->fill >= 0.0 && prm->fill <= 65535.0 && prm->fill == std::floor(prm->fill)))
+      return fail(ctx, ROIX_EINVAL, "params.fill must be an integer in [0, 65535] for uint16");
+    d->R = prm->radius;
+    d->S = 2 * prm->radius;
+    d->C = C;
+    d->fill = prm->fill;
+  }
+  return ROIX_OK;
+}
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+u32 front_rows_per_tile(const Desc& d) {
+  const u64 target_words = 2048;
+  u64 rpt = d.W ? target_words / d.W : 1;
+  if (rpt < 1) rpt = 1;
+  if (rpt > d.rows) rpt = d.rows ? d.rows : 1;
+  return (u32)rpt;
+}
+
+// ----------------------------------------------------- compress workspace
+struct CompressPlan {
+  size_t st, zero_begin, zero_end;
+  size_t ff, qf, pf, hist;      // look-back flags, histogram
+  size_t fa, qa, pa;            // look-back data
+  size_t T, P, sym, rk, rv, lens, codes;
+  size_t total;
+  u64 ftiles, qtiles, pchunks, rec_cap;
+  u32 rpt;
+};
+
+CompressPlan plan_compress(const Desc& d, u64 n_cap, u64 cap, bool need_T, bool need_P) {
+  CompressPlan p{};
+  Arena a;
+  p.st = a.take(kStateBytes);
+  p.rpt = front_rows_per_tile(d);
+  p.ftiles = d.rows ? (d.rows + p.rpt - 1) / p.rpt : 0;
+  p.qtiles = (n_cap + kQuantTile - 1) / kQuantTile;
+  p.pchunks = d.C ? (n_cap + d.C - 1) / d.C : 0;
+  p.rec_cap = umin(n_cap, cap / 12 + 1);
+  p.zero_begin = a.take(0);
+  p.ff = a.take(4 * (p.ftiles + 1));
+  p.qf = a.take(4 * (p.qtiles + 1));
+  p.pf = a.take(4 * (p.pchunks + 1));
+  p.hist = a.take(8 * (size_t)d.S);
+  p.zero_end = a.take(0);
+  p.fa = a.take(8 * 4 * (p.ftiles + 1));
+  p.qa = a.take(8 * 2 * (p.qtiles + 1));
+  p.pa = a.take(8 * 2 * (p.pchunks + 1));
+  p.T = need_T ? a.take(4 * d.rows * d.W) : 0;
+  const size_t esz = d.dtype == ROIX_F32 ? 4 : 2;
+  p.P = need_P ? a.take(esz * n_cap + 16) : 0;
+  p.sym = a.take(2 * n_cap + 16);
+  p.rk = a.take(8 * (p.rec_cap + 1));
+  p.rv = a.take(4 * (p.rec_cap + 1));
+  p.lens = a.take(d.S + 16);
+  p.codes = a.take(4 * (size_t)d.S);
+  p.total = a.take(0);
+  return p;
+}
+
+template <int NV>
+LookBack<NV> lb_at(char* ws, size_t flags, size_t data, u64 tiles) {
+  LookBack<NV> lb;
+  lb.flags = (u32*)(ws + flags);
+  lb.agg = (u64*)(ws + data);
+  lb.inc = (u64*)(ws + data) + NV * (tiles + 1);
+  return lb;
+}
+
+// profiling marks: an event after each stage when profiling is on
+void mark(roix_ctx* ctx, cudaStream_t s) {
+  if (!ctx->profile || ctx->nev >= 16) return;
+  if (!ctx->ev[ctx->nev]) cudaEventCreate(&ctx->ev[ctx->nev]);
+  cudaEventRecord(ctx->ev[ctx->nev], s);
+  ctx->nev++;
+}
+
+}  // namespace
+
+namespace roix {
+void launch_init(const Launch& L, State* st, void* zero, size_t zero_bytes);
+}
+
+extern "C" {
+
+const char* roix_status_string(roix_status s) {
+  switch (s) {
+    case ROIX_OK: return "ok";
+    case ROIX_EINVAL: return "invalid argument";
+    case ROIX_ENOMEM: return "out of device memory";
+    case ROIX_ECAPACITY: return "output buffer too small";
+    case ROIX_ECORRUPT: return "corrupt container";
+    case ROIX_ETIMEOUT: return "inter-block wait timed out";
+    case ROIX_ECUDA: return "CUDA error";
+    case ROIX_EBUSY: return "busy";
+  }
+  return "unknown status";
+}
+
+roix_status roix_ctx_create(int device, roix_ctx** out) {
+  if (!out) return ROIX_EINVAL;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    return ROIX_ECUDA;
+  }
+  roix_ctx* c = new roix_ctx();
+  c->device = device;
+  DeviceGuard g(device);
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+  if (c->sms <= 0) c->sms = 1;
+  *out = c;
+  return ROIX_OK;
+}
+
+roix_status roix_ctx_destroy(roix_ctx* ctx) {
+  if (!ctx) return ROIX_EINVAL;
+  DeviceGuard g(ctx->device);
+  if (ctx->ws) {
+    cudaDeviceSynchronize();
+    cudaFree(ctx->ws);
+  }
+  for (auto& e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  delete ctx;
+  return ROIX_OK;
+}
+
+roix_status roix_reserve(roix_ctx* ctx, size_t bytes) {
+  if (!ctx) return ROIX_EINVAL;
+  DeviceGuard g(ctx->device);
+  return ensure_ws(ctx, bytes < kStateBytes ? kStateBytes : bytes);
+}
+
+const char* roix_last_error(const roix_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+uint64_t roix_mask_words(roix_dims d) { return d.ny * d.nz * ((d.nx + 31) / 32); }
+
+uint64_t roix_compress_bound(roix_dtype dtype, roix_dims dims, const roix_params* prm) {
+  (void)dtype;
+  const u32 R = prm ? prm->radius : 512, C = prm && prm->chunk ? prm->chunk : 4096;
+  const u64 N = dims.nx * dims.ny * dims.nz, rows = dims.ny * dims.nz;
+  const u64 nch = (N + C - 1) / C;
+  const u64 nw = (N * kLMax + 31) / 32 + nch;
+  return make_layout(2ull * R, rows, rows * (dims.nx + 1), N, nch, nw).total;
+}
+
+size_t roix_workspace_size(roix_dtype dtype, roix_dims dims, const roix_roi* roi,
+                           const roix_params* params, uint64_t cap) {
+  Desc d;
+  if (make_desc(nullptr, dtype, dims, roi, nullptr, params, &d) != ROIX_OK) return 0;
+  return plan_compress(d, d.N, cap, true, true).total;
+}
+
+roix_status roix_sync(roix_ctx* ctx, void* stream) {
+  if (!ctx) return ROIX_EINVAL;
+  DeviceGuard g(ctx->device);
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
+  u32 st = ctx->pending;
+  ctx->pending = 0;
+  if (ctx->ws) {
+    u32 dev = 0;
+    e = cudaMemcpy(&dev, ctx->ws, 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "status read");
+    if (dev) {
+      const u32 zero = 0;
+      cudaMemcpy(ctx->ws, &zero, 4, cudaMemcpyHostToDevice);
+    }
+    if (!st) st = dev;
+  }
+  if (st) {
+    ctx->err = std::string("device reported: ") + roix_status_string((roix_status)st);
+    return (roix_status)st;
+  }
+  return ROIX_OK;
+}
+
+// Profiling: when on, the fused path records an event after every stage; the
+// stage durations of the last call are read with roix_profile_read.
+roix_status roix_profile(roix_ctx* ctx, int on) {
+  if (!ctx) return ROIX_EINVAL;
+  ctx->profile = on;
+  return ROIX_OK;
+}
+
+int roix_profile_read(roix_ctx* ctx, float* ms, int max) {
+  if (!ctx || ctx->nev < 2) return 0;
+  DeviceGuard g(ctx->device);
+  int k = 0;
+  for (int i = 1; i < ctx->nev && k < max; ++i, ++k) {
+    cudaEventSynchronize(ctx->ev[i]);
+    cudaEventElapsedTime(&ms[k], ctx->ev[i - 1], ctx->ev[i]);
+  }
+  return k;
+}
+
+roix_status roix_extract_roi(roix_ctx* ctx, const void* in, roix_dtype dtype, roix_dims dims,
+                             const roix_roi* roi, uint32_t* mask_out, uint64_t* popcount_dev,
+                             void* stream) {
+  if (!ctx || !roi) return fail(ctx, ROIX_EINVAL, "null context or roi");
+  Desc d;
+  roix_status s = make_desc(ctx, dtype, dims, roi, nullptr, nullptr, &d);
+  if (s) return s;
+  if (d.keep) return fail(ctx, ROIX_EINVAL, "keep = largest component is not available yet");
+  if (d.N && (!in || !mask_out)) return fail(ctx, ROIX_EINVAL, "null buffer");
+  if (!popcount_dev) return fail(ctx, ROIX_EINVAL, "null popcount_dev");
+  DeviceGuard g(ctx->device);
+  Arena a;
+  const size_t st_off = a.take(kStateBytes);
+  const size_t T_off = a.take(4 * d.rows * d.W + 16);
+  if ((s = ensure_ws(ctx, a.take(0)))) return s;
+  cudaStream_t cs = (cudaStream_t)stream;
+  Launch L{cs, ctx->sms};
+  State* st = (State*)(ctx->ws + st_off);
+  launch_init(L, st, nullptr, 0);
+  cudaMemsetAsync(popcount_dev, 0, 8, cs);
+  u32* T = (u32*)(ctx->ws + T_off);
+  launch_threshold(L, d, in, T);
+  launch_dilate(L, d, T, mask_out, (u64*)popcount_dev);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ROIX_OK : cuda_fail(ctx, e, "extract_roi launch");
+}
+
+roix_status roix_compact(roix_ctx* ctx, const void* in, roix_dtype dtype, roix_dims dims,
+                         const uint32_t* mask, void* pixels_out, uint16_t* counts_out,
+                         uint16_t* bounds_out, uint64_t bounds_cap, uint64_t* sizes_dev,
+                         void* stream) {
+  if (!ctx) return ROIX_EINVAL;
+  Desc d;
+  roix_status s = make_desc(ctx, dtype, dims, nullptr, nullptr, nullptr, &d);
+  if (s) return s;
+  if (d.N && (!in || !mask || !pixels_out || !counts_out || (!bounds_out && bounds_cap)))
+    return fail(ctx, ROIX_EINVAL, "null buffer");
+  if (!sizes_dev) return fail(ctx, ROIX_EINVAL, "null sizes_dev");
+  if (!aligned(pixels_out, 4)) return fail(ctx, ROIX_EINVAL, "pixels_out must be 4-byte aligned");
+  DeviceGuard g(ctx->device);
+  Arena a;
+  const size_t st_off = a.take(kStateBytes);
+  const u32 rpt = front_rows_per_tile(d);
+  const u64 tiles = d.rows ? (d.rows + rpt - 1) / rpt : 0;
+  const size_t zb = a.take(0);
+  const size_t ff = a.take(4 * (tiles + 1));
+  const size_t ze = a.take(0);
+  const size_t fa = a.take(8 * 4 * (tiles + 1));
+  if ((s = ensure_ws(ctx, a.take(0)))) return s;
+  cudaStream_t cs = (cudaStream_t)stream;
+  Launch L{cs, ctx->sms};
+  State* st = (State*)(ctx->ws + st_off);
+  launch_init(L, st, ctx->ws + zb, ze - zb);
+  cudaMemsetAsync(sizes_dev, 0, 16, cs);
+  launch_front(L, d, in, mask, 0, pixels_out, counts_out, d.rows, bounds_out, bounds_cap, st,
+               lb_at<2>(ctx->ws, ff, fa, tiles), rpt, tiles, (u64*)sizes_dev);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ROIX_OK : cuda_fail(ctx, e, "compact launch");
+}
+
+roix_status roix_quantize(roix_ctx* ctx, const void* pixels, roix_dtype dtype, uint64_t n_cap,
+                          const uint64_t* n_dev, const roix_eb* eb, double dark, int32_t* q_out,
+                          uint32_t* outlier_bits_out, roix_eb_info* info_dev, void* stream) {
+  if (!ctx || !eb) return fail(ctx, ROIX_EINVAL, "null context or eb");
+  Desc d;
+  if (n_cap > (1ull << 40)) return fail(ctx, ROIX_EINVAL, "n_cap too large");
+  const roix_dims dims{1, 1, 1};
+  roix_status s = make_desc(ctx, dtype, dims, nullptr, eb, nullptr, &d);
+  if (s) return s;
+  if (dtype == ROIX_U16 && !(dark >= 0.0 && dark <= 65535.0 && dark == std::floor(dark)))
+    return fail(ctx, ROIX_EINVAL, "dark must be an integer in [0, 65535]");
+  if (dtype == ROIX_F32 && dark != 0.0) return fail(ctx, ROIX_EINVAL, "dark must be 0 for float32");
+  d.dark = (int)dark;
+  d.dark_d = dark;
+  if (n_cap && (!pixels || !q_out || !outlier_bits_out))
+    return fail(ctx, ROIX_EINVAL, "null buffer");
+  if (!info_dev) return fail(ctx, ROIX_EINVAL, "null info_dev");
+  DeviceGuard g(ctx->device);
+  Arena a;
+  const size_t st_off = a.take(kStateBytes);
+  if ((s = ensure_ws(ctx, a.take(0)))) return s;
+  cudaStream_t cs = (cudaStream_t)stream;
+  Launch L{cs, ctx->sms};
+  State* st = (State*)(ctx->ws + st_off);
+  launch_init(L, st, nullptr, 0);
+  launch_quantize_stage(L, d, pixels, n_cap, (const u64*)n_dev, q_out, outlier_bits_out,
+                        info_dev, st);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ROIX_OK : cuda_fail(ctx, e, "quantize launch");
+}
+
+roix_status roix_encode(roix_ctx* ctx, const int32_t* q, const uint32_t* outlier_bits,
+                        const void* pixels, uint64_t n_cap, const uint64_t* sizes_dev,
+                        const uint16_t* counts, const uint16_t* bounds,
+                        const roix_eb_info* info_dev, roix_dtype dtype, roix_dims dims,
+                        const roix_roi* roi, const roix_eb* eb, const roix_params* params,
+                        void* out, uint64_t cap, uint64_t* size_dev, void* stream) {
+  if (!ctx || !roi || !eb || !params) return fail(ctx, ROIX_EINVAL, "null parameter struct");
+  Desc d;
+  roix_status s = make_desc(ctx, dtype, dims, roi, eb, params, &d);
+  if (s) return s;
+  if (n_cap > d.N) return fail(ctx, ROIX_EINVAL, "n_cap exceeds the voxel count");
+  if (!sizes_dev || !info_dev || !out || !size_dev) return fail(ctx, ROIX_EINVAL, "null buffer");
+  if (n_cap && (!q || !outlier_bits || !pixels)) return fail(ctx, ROIX_EINVAL, "null buffer");
+  if (d.rows && !counts) return fail(ctx, ROIX_EINVAL, "null counts");
+  if (!aligned(out, 16)) return fail(ctx, ROIX_EINVAL, "out must be 16-byte aligned");
+  DeviceGuard g(ctx->device);
+  CompressPlan p = plan_compress(d, n_cap, cap, false, false);
+  if ((s = ensure_ws(ctx, p.total))) return s;
+  cudaStream_t cs = (cudaStream_t)stream;
+  Launch L{cs, ctx->sms};
+  char* ws = ctx->ws;
+  State* st = (State*)(ws + p.st);
+  launch_init(L, st, ws + p.zero_begin, p.zero_end - p.zero_begin);
+  launch_symbols(L, d, pixels, q, outlier_bits, n_cap, (const u64*)sizes_dev, info_dev, st,
+                 (uint16_t*)(ws + p.sym), (u64*)(ws + p.rk), (u32*)(ws + p.rv), p.rec_cap,
+                 (unsigned long long*)(ws + p.hist), lb_at<1>(ws, p.qf, p.qa, p.qtiles));
+  launch_codebook(L, d, (unsigned long long*)(ws + p.hist), (uint8_t*)(ws + p.lens),
+                  (u32*)(ws + p.codes), (uint8_t*)out, cap, st);
+  launch_pack(L, d, (uint16_t*)(ws + p.sym), (const u64*)sizes_dev, (const u64*)sizes_dev + 1,
+              (uint8_t*)(ws + p.lens), (u32*)(ws + p.codes), st, (uint8_t*)out, cap,
+              lb_at<1>(ws, p.pf, p.pa, p.pchunks), p.pchunks);
+  launch_finalize(L, d, st, (const u64*)sizes_dev, (const u64*)sizes_dev + 1, info_dev,
+                  (u64*)(ws + p.rk), (u32*)(ws + p.rv), p.rec_cap, counts, bounds,
+                  (uint8_t*)out, cap, (u64*)size_dev);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ROIX_OK : cuda_fail(ctx, e, "encode launch");
+}
+
+roix_status roix_compress(roix_ctx* ctx, const void* in, roix_dtype dtype, roix_dims dims,
+                          const roix_roi* roi, const roix_eb* eb, const roix_params* params,
+                          void* out, uint64_t cap, uint64_t* size_dev, void* stream) {
+  if (!ctx || !roi || !eb || !params) return fail(ctx, ROIX_EINVAL, "null parameter struct");
+  Desc d;
+  roix_status s = make_desc(ctx, dtype, dims, roi, eb, params, &d);
+  if (s) return s;
+  if (d.keep) return fail(ctx, ROIX_EINVAL, "keep = largest component is not available yet");
+  if ((d.N && !in) || !out || !size_dev) return fail(ctx, ROIX_EINVAL, "null buffer");
+  if (!aligned(out, 16)) return fail(ctx, ROIX_EINVAL, "out must be 16-byte aligned");
+  if (!aligned(in, dtype == ROIX_F32 ? 4 : 2)) return fail(ctx, ROIX_EINVAL, "misaligned input");
+  DeviceGuard g(ctx->device);
+  CompressPlan p = plan_compress(d, d.N, cap, true, true);
+  if ((s = ensure_ws(ctx, p.total))) return s;
+  cudaStream_t cs = (cudaStream_t)stream;
+  Launch L{cs, ctx->sms};
+  char* ws = ctx->ws;
+  State* st = (State*)(ws + p.st);
+  uint8_t* o = (uint8_t*)out;
+  const Layout lo = make_layout(d.S, d.rows, 0, 0, 0, 0);
+  const u64 counts_cap = cap > lo.off_counts ? (cap - lo.off_counts) / 2 : 0;
+  const u64 bounds_cap = cap > lo.off_bounds ? (cap - lo.off_bounds) / 2 : 0;
+  ctx->nev = 0;
+  mark(ctx, cs);
+  launch_init(L, st, ws + p.zero_begin, p.zero_end - p.zero_begin);
+  mark(ctx, cs);
+  launch_threshold(L, d, in, (u32*)(ws + p.T));
+  mark(ctx, cs);
+  launch_front(L, d, in, (u32*)(ws + p.T), d.dilate, ws + p.P, (uint16_t*)(o + lo.off_counts),
+               counts_cap, (uint16_t*)(o + lo.off_bounds), bounds_cap, st,
+               lb_at<2>(ws, p.ff, p.fa, p.ftiles), p.rpt, p.ftiles, &st->n);
+  mark(ctx, cs);
+  launch_symbols(L, d, ws + p.P, nullptr, nullptr, d.N, &st->n, nullptr, st,
+                 (uint16_t*)(ws + p.sym), (u64*)(ws + p.rk), (u32*)(ws + p.rv), p.rec_cap,
+                 (unsigned long long*)(ws + p.hist), lb_at<1>(ws, p.qf, p.qa, p.qtiles));
+  mark(ctx, cs);
+  launch_codebook(L, d, (unsigned long long*)(ws + p.hist), (uint8_t*)(ws + p.lens),
+                  (u32*)(ws + p.codes), o, cap, st);
+  mark(ctx, cs);
+  launch_pack(L, d, (uint16_t*)(ws + p.sym), &st->n, &st->nb, (uint8_t*)(ws + p.lens),
+              (u32*)(ws + p.codes), st, o, cap, lb_at<1>(ws, p.pf, p.pa, p.pchunks), p.pchunks);
+  mark(ctx, cs);
+  launch_finalize(L, d, st, &st->n, &st->nb, &st->eb, (u64*)(ws + p.rk), (u32*)(ws + p.rv),
+                  p.rec_cap, nullptr, nullptr, o, cap, (u64*)size_dev);
+  mark(ctx, cs);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ROIX_OK : cuda_fail(ctx, e, "compress launch");
+}
+
+roix_status roix_decode(roix_ctx* ctx, const void* in, uint64_t size, void* out,
+                        roix_dtype dtype, roix_dims dims, void* stream) {
+  if (!ctx) return ROIX_EINVAL;
+  Desc d;
+  roix_status s = make_desc(ctx, dtype, dims, nullptr, nullptr, nullptr, &d);
+  if (s) return s;
+  if (!in || (d.N && !out)) return fail(ctx, ROIX_EINVAL, "null buffer");
+  if (!aligned(in, 16)) return fail(ctx, ROIX_EINVAL, "in must be 16-byte aligned");
+  DeviceGuard g(ctx->device);
+  const u64 max_chunks = (d.N + 255) / 256;
+  const u64 row_tiles = (d.rows + kDecRowTile - 1) / kDecRowTile;
+  const size_t esz = dtype == ROIX_F32 ? 4 : 2;
+  Arena a;
+  const size_t st_off = a.take(kStateBytes);
+  const size_t plan = a.take(8 * kPlanWords);
+  const size_t zb = a.take(0);
+  const size_t table = a.take(dec_table_bytes());
+  const size_t fb = a.take(4 * (row_tiles + 1));
+  const size_t fv = a.take(4 * (row_tiles + 1));
+  const size_t ctr = a.take(16);
+  const size_t ze = a.take(0);
+  const size_t db = a.take(8 * 2 * (row_tiles + 1));
+  const size_t dv = a.take(8 * 2 * (row_tiles + 1));
+  const size_t sym = a.take(2 * d.N + 16);
+  const size_t agg = a.take(16 * (max_chunks + 1));
+  const size_t carry = a.take(8 * (max_chunks + 1));
+  const size_t vals = a.take(esz * d.N + 16);
+  const size_t rb = a.take(8 * (d.rows + 1));
+  const size_t rv = a.take(8 * (d.rows + 1));
+  if ((s = ensure_ws(ctx, a.take(0)))) return s;
+  cudaStream_t cs = (cudaStream_t)stream;
+  Launch L{cs, ctx->sms};
+  char* ws = ctx->ws;
+  State* st = (State*)(ws + st_off);
+  launch_init(L, st, ws + zb, ze - zb);
+  DecodeWs w;
+  w.status = &st->status;
+  w.plan = (u64*)(ws + plan);
+  w.table = ws + table;
+  w.sym = (uint16_t*)(ws + sym);
+  w.agg = (u64*)(ws + agg);
+  w.carry = (u64*)(ws + carry);
+  w.vals = ws + vals;
+  w.row_boff = (u64*)(ws + rb);
+  w.row_voff = (u64*)(ws + rv);
+  w.lb_rows_b = lb_at<1>(ws, fb, db, row_tiles);
+  w.lb_rows_v = lb_at<1>(ws, fv, dv, row_tiles);
+  w.row_ctr = (u32*)(ws + ctr);
+  launch_decode(L, d, (const uint8_t*)in, size, out, w, max_chunks);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ROIX_OK : cuda_fail(ctx, e, "decode launch");
+}
+
+}  // extern "C"

@@ -1,0 +1,323 @@
+// Internal declarations of libroix: device helpers shared by the kernel files
+// and the launch functions the host API calls. Not installed; the public
+// interface is include/roix.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "roix.h"
+
+namespace roix {
+
+typedef unsigned long long u64;
+typedef unsigned int u32;
+
+constexpr u32 kHeaderBytes = 256;   // container header
+constexpr u32 kLMax = 24;           // longest Huffman code
+constexpr u32 kMaxRadius = 2048;    // R limit: 2R symbols fit the codebook block
+constexpr u32 kMaxSym = 2 * kMaxRadius;
+constexpr u32 kVersion = 1;
+
+// Status word codes (first error wins).
+__device__ __forceinline__ void set_status(u32* status, u32 code) {
+  atomicCAS(status, 0u, code);
+}
+
+// ---------------------------------------------------------------- memory
+__device__ __forceinline__ u32 ld_acquire(const u32* p) {
+  u32 v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(u32* p, u32 v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ u64 ld_relaxed(const u64* p) {
+  u64 v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed(u64* p, u64 v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ u32 ld_relaxed32(const u32* p) {
+  u32 v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// ------------------------------------------------------------ look-back
+// Single-pass decoupled look-back scan (Merrill & Garland 2016) over tiles
+// taken in increasing order from an atomic counter: a tile publishes its
+// aggregate, walks back over predecessors until one has published an
+// inclusive prefix, then publishes its own inclusive prefix. NV 64-bit sums
+// are carried. Every wait is bounded: after kSpinLimit polls the tile gives up,
+// records ROIX_ETIMEOUT and treats the missing value as 0 (results invalid,
+// the kernel still ends).
+constexpr u32 kSpinLimit = 1u << 22;
+
+template <int NV>
+struct LookBack {
+  u32* flags;  // [tiles], zero before the launch
+  u64* agg;    // [tiles * NV]
+  u64* inc;    // [tiles * NV]
+};
+
+template <int NV>
+__device__ void lookback(LookBack<NV> lb, u64 t, const u64 (&mine)[NV], u64 (&excl)[NV],
+                         u32* status) {
+  for (int i = 0; i < NV; ++i) excl[i] = 0;
+  if (t == 0) {
+    for (int i = 0; i < NV; ++i) st_relaxed(&lb.inc[i], mine[i]);
+    st_release(&lb.flags[0], 2u);
+    return;
+  }
+  for (int i = 0; i < NV; ++i) st_relaxed(&lb.agg[t * NV + i], mine[i]);
+  st_release(&lb.flags[t], 1u);
+  u64 j = t - 1;
+  u32 spins = 0;
+  while (true) {
+    u32 f = ld_acquire(&lb.flags[j]);
+    if (f == 0) {
+      if (++spins > kSpinLimit) {
+        set_status(status, ROIX_ETIMEOUT);
+        break;
+      }
+      __nanosleep(64);
+      continue;
+    }
+    if (f == 2) {
+      for (int i = 0; i < NV; ++i) excl[i] += ld_relaxed(&lb.inc[j * NV + i]);
+      break;
+    }
+    for (int i = 0; i < NV; ++i) excl[i] += ld_relaxed(&lb.agg[j * NV + i]);
+    if (j == 0) break;  // tile 0 always publishes an inclusive prefix; guard only
+    --j;
+  }
+  for (int i = 0; i < NV; ++i) st_relaxed(&lb.inc[t * NV + i], excl[i] + mine[i]);
+  st_release(&lb.flags[t], 2u);
+}
+
+// ------------------------------------------------------------------- scans
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    T o = __shfl_up_sync(0xffffffffu, v, d);
+    if (lane >= d) v += o;
+  }
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+  return v;
+}
+
+// Block-wide exclusive scan of one value per thread; `scratch` holds 33 T.
+// Returns the exclusive prefix; *total receives the block sum.
+template <typename T>
+__device__ T block_excl_scan(T v, T* scratch, T* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = (blockDim.x + 31) >> 5;
+  T inc = warp_incl_scan(v);
+  if (lane == 31) scratch[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    T s = lane < nwarps ? scratch[lane] : T(0);
+    T si = warp_incl_scan(s);
+    if (lane < nwarps) scratch[lane] = si - s;
+    if (lane == nwarps - 1) scratch[32] = si;
+  }
+  __syncthreads();
+  T out = scratch[warp] + inc - v;
+  *total = scratch[32];
+  __syncthreads();
+  return out;
+}
+
+// ------------------------------------------------------- ordered float keys
+// Monotone map of binary32 bit patterns to uint32 (for atomicMin/Max).
+__device__ __forceinline__ u32 f32_key(float f) {
+  u32 b = __float_as_uint(f);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float key_f32(u32 k) {
+  u32 b = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+  return __uint_as_float(b);
+}
+
+// ----------------------------------------------------------------- layout
+__host__ __device__ __forceinline__ u64 align16(u64 v) { return (v + 15) & ~u64(15); }
+__host__ __device__ __forceinline__ u64 umin(u64 a, u64 b) { return a < b ? a : b; }
+__host__ __device__ __forceinline__ u64 umax(u64 a, u64 b) { return a > b ? a : b; }
+
+// Section offsets of a container (all little-endian, 16-byte aligned).
+struct Layout {
+  u64 off_lens, off_counts, off_bounds, off_outk, off_outv, off_chunks, off_payload, total;
+};
+__host__ __device__ __forceinline__ Layout make_layout(u64 S, u64 rows, u64 nb, u64 nout,
+                                                       u64 nchunks, u64 nwords) {
+  Layout L;
+  L.off_lens = kHeaderBytes;
+  L.off_counts = align16(L.off_lens + S);
+  L.off_bounds = align16(L.off_counts + 2 * rows);
+  L.off_outk = align16(L.off_bounds + 2 * nb);
+  L.off_outv = align16(L.off_outk + 8 * nout);
+  L.off_chunks = align16(L.off_outv + 4 * nout);
+  L.off_payload = align16(L.off_chunks + 8 * nchunks);
+  L.total = align16(L.off_payload + 4 * nwords);
+  return L;
+}
+
+// Device-side state of one compression (workspace head, zeroed per call).
+struct State {
+  u32 status;
+  u32 ctr_front, ctr_quant, ctr_pack;  // dynamic tile counters
+  u64 n, nb, nout, nwords;             // sizes found on the device
+  u32 vmin_key, vmax_key;              // range of retained finite values
+  u32 cap_flag, pad0;
+  u64 total;
+  roix_eb_info eb;
+};
+
+// Static description of one volume and its coder settings (kernel argument).
+struct Desc {
+  u64 nx, ny, nz, rows, W, N;  // W = mask words per row
+  int dtype;                   // ROIX_F32 / ROIX_U16
+  int cmp, keep, conn, dilate;
+  float thr_f;                 // float32: x > thr_f (cmp 0) or x < thr_f (cmp 1)
+  int thr_i;                   // uint16: v > thr_i or v < thr_i, v = raw - dark
+  int thr_never;               // NaN threshold: nothing passes
+  int dark;
+  double threshold, dark_d, fill;
+  int eb_mode;
+  double eb_value;
+  u32 R, S, C;
+};
+
+// Error-bound constants from the mode, the value and the range keys; the same
+// sequence of binary64 operations as the definition (Sec. 4.2.3, Sz3 range).
+__device__ __forceinline__ roix_eb_info make_eb(const Desc& d, u32 vmin_key, u32 vmax_key) {
+  roix_eb_info e;
+  double vmin, vmax;
+  if (d.dtype == ROIX_F32) {
+    vmin = vmin_key == 0xffffffffu ? __longlong_as_double(0x7ff0000000000000ll)
+                                   : (double)key_f32(vmin_key);
+    vmax = vmax_key == 0u ? -__longlong_as_double(0x7ff0000000000000ll)
+                          : (double)key_f32(vmax_key);
+  } else {
+    vmin = vmin_key == 0xffffffffu ? __longlong_as_double(0x7ff0000000000000ll)
+                                   : (double)(vmin_key - 1);
+    vmax = vmax_key == 0u ? -__longlong_as_double(0x7ff0000000000000ll) : (double)(vmax_key - 1);
+  }
+  e.vmin = vmin;
+  e.vmax = vmax;
+  double eb;
+  if (d.eb_mode == 0) eb = d.eb_value;
+  else eb = (vmax >= vmin) ? __dmul_rn(d.eb_value, __dsub_rn(vmax, vmin)) : 0.0;
+  e.eb_abs = eb;
+  double two_d = __dmul_rn(2.0, eb);
+  float two = __double2float_rn(two_d);
+  float inv = eb > 0.0 ? __double2float_rn(__ddiv_rn(1.0, two_d)) : 0.0f;
+  bool ok = eb > 0.0 && isfinite(eb) && isfinite(two) && two > 0.0f && isfinite(inv) &&
+            inv > 0.0f;
+  if (ok) {
+    e.two_eb = two;
+    e.inv2eb = inv;
+    e.bound = __double2float_rz(__dmul_rn(eb, 1.0 - 0x1p-23));
+  } else {
+    e.two_eb = 0.0f;
+    e.inv2eb = 0.0f;
+    e.bound = -1.0f;
+  }
+  double ebi = floor(eb);
+  if (!(ebi >= 0.0)) ebi = 0.0;
+  if (ebi > 65535.0) ebi = 65535.0;
+  e.eb_int = (int)ebi;
+  return e;
+}
+
+// Linear quantiser of one value (Sec. 4.2.3 contract): returns the code, sets
+// `out` for an outlier (code 0). Binary32 operations rounded to nearest, no
+// contraction: the decoder repeats the reconstruction bit for bit.
+__device__ __forceinline__ int quant_f32(float x, const roix_eb_info& e, bool& out) {
+  if (!isfinite(x)) {
+    out = true;
+    return 0;
+  }
+  float y = __fmul_rn(x, e.inv2eb);
+  if (!(fabsf(y) < 1073741824.0f)) {
+    out = true;
+    return 0;
+  }
+  int q = __float2int_rn(y);
+  float xh = __fmul_rn(__int2float_rn(q), e.two_eb);
+  float dd = __fsub_rn(x, xh);
+  out = !(fabsf(dd) <= e.bound);
+  return out ? 0 : q;
+}
+__device__ __forceinline__ int quant_u16(unsigned raw, int dark, int eb_int) {
+  int v = (int)raw - dark;
+  if (eb_int == 0) return v;
+  int num = v + eb_int, den = 2 * eb_int;
+  return num >= 0 ? num / den : -((-num + den - 1) / den);
+}
+
+// ------------------------------------------------------ launch functions
+struct Launch {
+  cudaStream_t stream;
+  int sms;
+};
+
+// mask kernels (k_mask.cu)
+void launch_threshold(const Launch& L, const Desc& d, const void* in, u32* T);
+void launch_dilate(const Launch& L, const Desc& d, const u32* T, u32* D, u64* popcount);
+void launch_front(const Launch& L, const Desc& d, const void* in, const u32* T, int dilate,
+                  void* P, uint16_t* counts, u64 counts_cap, uint16_t* bounds, u64 bounds_cap,
+                  State* st, LookBack<2> lb, u32 rows_per_tile, u64 tiles, u64* sizes_out);
+
+// coder kernels (k_encode.cu)
+constexpr u32 kQuantTile = 8192;  // elements per quantiser tile
+void launch_quantize_stage(const Launch& L, const Desc& d, const void* P, u64 n_cap,
+                           const u64* n_dev, int32_t* q, u32* obits, roix_eb_info* info_out,
+                           State* st);
+void launch_symbols(const Launch& L, const Desc& d, const void* P, const int32_t* q,
+                    const u32* obits, u64 n_cap, const u64* n_dev, const roix_eb_info* info_in,
+                    State* st, uint16_t* sym, u64* rk, u32* rv, u64 rec_cap,
+                    unsigned long long* hist, LookBack<1> lb);
+void launch_codebook(const Launch& L, const Desc& d, const unsigned long long* hist,
+                     uint8_t* lens_ws, u32* codes_ws, uint8_t* out, u64 cap, State* st);
+void launch_pack(const Launch& L, const Desc& d, const uint16_t* sym, const u64* n_dev,
+                 const u64* nb_dev, const uint8_t* lens_ws, const u32* codes_ws, State* st,
+                 uint8_t* out, u64 cap, LookBack<1> lb, u64 chunks_cap);
+void launch_finalize(const Launch& L, const Desc& d, State* st, const u64* n_dev,
+                     const u64* nb_dev, const roix_eb_info* info, const u64* rk, const u32* rv,
+                     u64 rec_cap, const uint16_t* counts_src, const uint16_t* bounds_src,
+                     uint8_t* out, u64 cap, u64* size_dev);
+
+// decoder kernels (k_decode.cu)
+struct DecodeWs {
+  u32* status;
+  u64* plan;          // decoded header values (kPlanWords), zeroed by the header kernel
+  void* table;        // canonical decode table (dec_table_bytes(), zeroed by the host)
+  uint16_t* sym;      // [N]
+  u64* agg;           // [max chunks * 2] chunk aggregates (reset flag, value)
+  u64* carry;         // [max chunks]
+  void* vals;         // [N] values in retained order
+  u64* row_boff;      // [rows]
+  u64* row_voff;      // [rows]
+  LookBack<1> lb_rows_b, lb_rows_v;  // flags zeroed by the host
+  u32* row_ctr;       // zeroed by the host
+};
+constexpr int kPlanWords = 32;
+constexpr u64 kDecRowTile = 1024;
+size_t dec_table_bytes();
+void launch_decode(const Launch& L, const Desc& d, const uint8_t* in, u64 size, void* out,
+                   const DecodeWs& ws, u64 max_chunks);
+
+}  // namespace roix

@@ -1,0 +1,247 @@
+"""CUDA path against the CPU oracle, through the C ABI, on seeded inputs.
+
+Integer outputs (masks, geometry, codes, symbols, container bytes) must be
+bit-identical; decoded values must be bit-identical to the oracle's decode
+(the error bound itself is pinned on the oracle side)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import phantom
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2602_15917_gb300 as roix
+    r = roix.Roix(0)
+    yield r
+    r.close()
+
+
+def _unpack_mask(words: torch.Tensor, shape) -> np.ndarray:
+    nz, ny, nx = shape
+    W = (nx + 31) // 32
+    w = words.cpu().numpy().view(np.uint32).reshape(ny * nz, W)
+    bits = np.unpackbits(w.view(np.uint8), bitorder="little").reshape(ny * nz, W * 32)
+    return bits[:, :nx].reshape(shape).astype(np.uint8)
+
+
+def _compress_both(rx, x: np.ndarray, **cfg):
+    ref = oracle.compress(x, **cfg)
+    got = rx.compress_bytes(torch.from_numpy(x).cuda(), **cfg).cpu().numpy()
+    return ref, got
+
+
+def _assert_same_container(ref, got):
+    if got.size != ref.size or not np.array_equal(got, ref):
+        h_r, h_g = oracle.header(ref), oracle.header(got) if got.size >= 256 else {}
+        diff = {k: (h_r[k], h_g.get(k)) for k in h_r if h_r[k] != h_g.get(k)}
+        first = int(np.flatnonzero(got[:min(got.size, ref.size)] != ref[:min(got.size, ref.size)])[0]) \
+            if min(got.size, ref.size) and (got[:min(got.size, ref.size)] != ref[:min(got.size, ref.size)]).any() else -1
+        raise AssertionError(f"containers differ: sizes {got.size} vs {ref.size}, "
+                             f"header diff {diff}, first differing byte {first}")
+
+
+F32_CASES = [
+    ("ellipsoids48", lambda: phantom.ellipsoids(48, seed=1).numpy(), {}),
+    ("ragged", lambda: phantom.ellipsoids(shape=(17, 23, 33), seed=2).numpy(), {}),
+    ("wide_rows", lambda: phantom.ellipsoids(shape=(5, 7, 100), seed=3).numpy(), {}),
+    ("nx32", lambda: phantom.ellipsoids(shape=(9, 11, 32), seed=4).numpy(), {}),
+    ("nx64_2d", lambda: phantom.ellipsoids(shape=(1, 64, 64), seed=5).numpy(), {}),
+    ("nx1", lambda: phantom.random_field((3, 50, 1), seed=6), dict(threshold=0.0)),
+    ("single", lambda: np.array([[[0.5]]], np.float32), {}),
+    ("no_dilate", lambda: phantom.ellipsoids(40, seed=7).numpy(), dict(dilate=0)),
+    ("below", lambda: phantom.ellipsoids(40, seed=8).numpy(), dict(cmp="lt", threshold=0.5)),
+    ("rel", lambda: phantom.porous_cylinder(40, radius=15, seed=1).numpy(),
+     dict(eb=1e-3, eb_mode="rel")),
+    ("rel_tight", lambda: phantom.porous_cylinder(40, radius=15, seed=2).numpy(),
+     dict(eb=1e-5, eb_mode="rel")),
+    ("radius2", lambda: phantom.ellipsoids(32, seed=9).numpy(), dict(radius=2)),
+    ("radius2048_chunk256", lambda: phantom.ellipsoids(32, seed=10).numpy(),
+     dict(radius=2048, chunk=256, eb=1e-5)),
+    ("chunk16384", lambda: phantom.ellipsoids(48, seed=11).numpy(), dict(chunk=16384)),
+    ("all_roi", lambda: phantom.random_field((4, 9, 70), seed=12), dict(threshold=-1e30)),
+    ("no_roi", lambda: phantom.random_field((4, 9, 70), seed=13), dict(threshold=1e30)),
+    ("noise_white", lambda: phantom.random_field((6, 20, 90), seed=14, smooth=False),
+     dict(threshold=-0.5, eb=1e-2)),
+    ("fill", lambda: phantom.ellipsoids(24, seed=15).numpy(), dict(fill=-7.25)),
+]
+
+
+@pytest.mark.parametrize("name,make,cfg", F32_CASES, ids=[c[0] for c in F32_CASES])
+def test_fused_float32_bit_exact(rx, name, make, cfg):
+    x = make()
+    base = dict(eb=1e-3, eb_mode="abs", threshold=0.1, dilate=1)
+    base.update(cfg)
+    ref, got = _compress_both(rx, x, **base)
+    _assert_same_container(ref, got)
+
+
+def test_fused_float32_special_values(rx):
+    x = phantom.random_field((5, 13, 77), seed=20)
+    flat = x.reshape(-1)
+    flat[::37] = np.nan
+    flat[5::41] = np.inf
+    flat[7::43] = -np.inf
+    flat[9::47] = 3e38
+    flat[11::53] = -1e-41  # subnormal
+    flat[13::59] = -0.0
+    for eb in (1e-3, 1e-40, 1e30):
+        ref, got = _compress_both(rx, x, eb=eb, threshold=-1.0, dilate=1)
+        _assert_same_container(ref, got)
+
+
+def test_fused_config1_workload(rx):
+    # 128^3 ellipsoid phantom, eb 1e-3 absolute, threshold 0.1, 1-voxel dilation
+    x = phantom.ellipsoids(128, seed=0).numpy()
+    ref, got = _compress_both(rx, x, eb=1e-3, threshold=0.1, dilate=1)
+    _assert_same_container(ref, got)
+    assert got.size < x.nbytes / 2
+
+
+U16_CASES = [
+    ("proj", (200, 211), dict(eb=4)),
+    ("proj_lossless", (97, 130), dict(eb=0)),
+    ("proj_dilate", (150, 150), dict(eb=4, dilate=1)),
+    ("proj_rel", (128, 160), dict(eb=1e-4, eb_mode="rel")),
+    ("proj_nx32", (40, 32), dict(eb=2)),
+]
+
+
+@pytest.mark.parametrize("name,shape,cfg", U16_CASES, ids=[c[0] for c in U16_CASES])
+def test_fused_uint16_bit_exact(rx, name, shape, cfg):
+    side = max(shape)
+    x = phantom.projection(side, 3, seed=1).numpy()[:shape[0], :shape[1]].copy()
+    base = dict(eb=4, eb_mode="abs", cmp="lt", threshold=57000, dark=100, dilate=0, fill=60100)
+    base.update(cfg)
+    ref, got = _compress_both(rx, x, **base)
+    _assert_same_container(ref, got)
+
+
+def test_staged_chain_matches_oracle_and_fused(rx):
+    x = phantom.ellipsoids(shape=(20, 30, 45), seed=30).numpy()
+    cfg = dict(eb=2e-3, eb_mode="rel", threshold=0.1, dilate=1)
+    xt = torch.from_numpy(x).cuda()
+    # extract_roi
+    mask, pop = rx.extract_roi(xt, **cfg)
+    D = oracle.mask(x, **cfg)
+    rx.sync()
+    assert np.array_equal(_unpack_mask(mask, x.shape), D)
+    assert int(pop.item()) == int(D.sum())
+    # compact
+    pixels, counts, bounds, sizes = rx.compact(xt, mask)
+    rx.sync()
+    P, c_ref, b_ref = oracle.compact(x, D)
+    n, nb = (int(v) for v in sizes.cpu().numpy())
+    assert n == P.size and nb == b_ref.size
+    assert np.array_equal(pixels[:n].cpu().numpy(), P)
+    assert np.array_equal(counts.cpu().numpy(), c_ref)
+    assert np.array_equal(bounds[:nb].cpu().numpy(), b_ref)
+    # quantize
+    q, ob, info = rx.quantize(pixels, n_cap=x.size, n_dev=sizes[:1], **cfg)
+    rx.sync()
+    e = oracle.error_bound(P, "rel", cfg["eb"])
+    q_ref, o_ref = oracle.quantize(P, e)
+    assert np.array_equal(q[:n].cpu().numpy(), q_ref)
+    obits = np.unpackbits(ob.cpu().numpy().view(np.uint8), bitorder="little")[:n]
+    assert np.array_equal(obits, o_ref)
+    inf = np.frombuffer(info.cpu().numpy().tobytes(), dtype=[("eb_abs", "<f8"), ("vmin", "<f8"),
+                        ("vmax", "<f8"), ("two", "<f4"), ("inv", "<f4"), ("bound", "<f4"),
+                        ("ebi", "<i4")])[0]
+    assert inf["eb_abs"] == e.eb_abs and inf["two"] == e.two_eb and inf["bound"] == e.bound
+    # encode
+    out, size = rx.encode(q, ob, pixels, x.size, sizes, counts, bounds, info, x.shape,
+                          torch.float32, **cfg)
+    rx.sync()
+    got = out[:int(size.item())].cpu().numpy()
+    ref = oracle.compress(x, **cfg)
+    _assert_same_container(ref, got)
+    fused = rx.compress_bytes(xt, **cfg).cpu().numpy()
+    assert np.array_equal(fused, got)
+
+
+def test_staged_uint16(rx):
+    x = phantom.projection(180, 4, seed=2).numpy()
+    cfg = dict(eb=4, cmp="lt", threshold=57000, dark=100, dilate=0, fill=60100)
+    xt = torch.from_numpy(x).cuda()
+    mask, pop = rx.extract_roi(xt, **cfg)
+    pixels, counts, bounds, sizes = rx.compact(xt, mask)
+    q, ob, info = rx.quantize(pixels, n_cap=x.size, n_dev=sizes[:1], **cfg)
+    out, size = rx.encode(q, ob, pixels, x.size, sizes, counts, bounds, info, x.shape,
+                          torch.uint16, **cfg)
+    rx.sync()
+    _assert_same_container(oracle.compress(x, **cfg), out[:int(size.item())].cpu().numpy())
+
+
+@pytest.mark.parametrize("kind", ["f32", "f32_rel", "u16", "empty", "full"])
+def test_decode_bit_exact(rx, kind):
+    if kind.startswith("f32"):
+        x = phantom.ellipsoids(shape=(21, 34, 50), seed=40).numpy()
+        cfg = dict(eb=1e-3, eb_mode="rel" if kind == "f32_rel" else "abs", threshold=0.1,
+                   dilate=1, fill=0.5)
+        dt = torch.float32
+    elif kind == "u16":
+        x = phantom.projection(160, 5, seed=3).numpy()
+        cfg = dict(eb=4, cmp="lt", threshold=57000, dark=100, dilate=0, fill=60100)
+        dt = torch.uint16
+    else:
+        x = phantom.random_field((3, 10, 40), seed=41)
+        cfg = dict(eb=1e-2, threshold=1e30 if kind == "empty" else -1e30, fill=2.0)
+        dt = torch.float32
+    ref = oracle.compress(x, **cfg)
+    y_ref = oracle.decode(ref, x.shape, x.dtype)
+    y = rx.decode(torch.from_numpy(ref).cuda(), x.shape, dt)
+    rx.sync()
+    a = y.cpu().numpy()
+    assert np.array_equal(a.view(np.uint8), y_ref.view(np.uint8))
+
+
+def test_decode_rejects_corrupt(rx):
+    import paper_2602_15917_gb300 as roix
+    x = phantom.ellipsoids(24, seed=42).numpy()
+    ref = oracle.compress(x, eb=1e-3, threshold=0.1)
+    buf = torch.from_numpy(ref).cuda()
+    for size, shape in [(100, x.shape), (ref.size - 16, x.shape), (ref.size, (24, 24, 25))]:
+        rx.decode(buf, shape, torch.float32, size=size)
+        with pytest.raises(roix.RoixError) as ei:
+            rx.sync()
+        assert ei.value.status == 4
+    bad = ref.copy()
+    bad[0] = 0
+    rx.decode(torch.from_numpy(bad).cuda(), x.shape, torch.float32)
+    with pytest.raises(roix.RoixError):
+        rx.sync()
+    # the context stays usable
+    rx.decode(buf, x.shape, torch.float32)
+    rx.sync()
+
+
+def test_capacity_error_reports_size(rx):
+    import paper_2602_15917_gb300 as roix
+    x = torch.from_numpy(phantom.ellipsoids(32, seed=43).numpy()).cuda()
+    out = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    _, size = rx.compress(x, out=out, eb=1e-4, threshold=0.1)
+    with pytest.raises(roix.RoixError) as ei:
+        rx.sync()
+    assert ei.value.status == 3
+    need = int(size.item())
+    ref = oracle.compress(x.cpu().numpy(), eb=1e-4, threshold=0.1)
+    assert need == ref.size
+
+
+def test_deterministic_and_stream_ordered(rx):
+    x = torch.from_numpy(phantom.porous_cylinder(64, radius=24, seed=5).numpy()).cuda()
+    cfg = dict(eb=1e-4, eb_mode="rel", threshold=0.1)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        a = rx.compress_bytes(x, **cfg).clone()
+        b = rx.compress_bytes(x, **cfg).clone()
+    s.synchronize()
+    assert torch.equal(a, b)
