@@ -1,0 +1,421 @@
+"""Benchmark of the ROIX-Comp hot path (quantise + ROI + encode) on GB300.
+
+One JSON line on rank 0. A step compresses one batch of the workload with
+inputs resident in HBM (``value``); ``e2e`` repeats it through host buffers
+(pinned host -> device copies of the inputs and device -> host reads of the
+containers inside the timed region). Workloads (seeded synthetic phantoms):
+
+  projections64  64 uint16 flat-field projections, sides U{512..2048}, Poisson
+                 counts I0 = 60000 through a random ellipsoid phantom, dark 100;
+                 ROI = (raw - 100) < 57000; eb = 4 counts absolute; fill 60100
+  cube1024       1024^3 float32 porous cylinder (radius 400, ~20 % of voxels,
+                 pores r 2..30, 5 % porosity, noise 0.005); relative eb 1e-4;
+                 ROI = value > 0.1 with 1-voxel dilation
+  ellipsoids128  128^3 float32, 5 ellipsoids + noise 0.01; eb 1e-3 absolute;
+                 ROI = value > 0.1 with 1-voxel dilation
+
+``--impl reference`` times the CPU oracle (the plain restatement of the
+method) on the host cores on a bounded sample of the same workload.
+Multi-GPU (torchrun): every rank compresses its own batch (replicas, weak
+scaling); there is no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GB/s in (quantize+ROI+encode) vs HBM peak, batched/served vs plain; p50/p99 latency"
+
+WORKLOADS = {
+    "projections64": dict(
+        desc="64 uint16 projections, sides U{512..2048}, I0=60000, dark 100, eb=4 abs, "
+             "ROI raw-100 < 57000, no dilation, fill 60100",
+        cfg=dict(eb=4, eb_mode="abs", cmp="lt", threshold=57000, dark=100, dilate=0,
+                 fill=60100, radius=512, chunk=4096)),
+    "cube1024": dict(
+        desc="1024^3 float32 porous cylinder r=400 (~20%), pores 2..30 (5%), noise 0.005, "
+             "relative eb 1e-4, ROI > 0.1 + 1-voxel dilation",
+        cfg=dict(eb=1e-4, eb_mode="rel", cmp="gt", threshold=0.1, dilate=1, fill=0.0,
+                 radius=512, chunk=4096)),
+    "cube512": dict(
+        desc="512^3 float32 porous cylinder r=200 (~20%), pores 2..30 (5%), noise 0.005, "
+             "relative eb 1e-4, ROI > 0.1 + 1-voxel dilation (profiling size)",
+        cfg=dict(eb=1e-4, eb_mode="rel", cmp="gt", threshold=0.1, dilate=1, fill=0.0,
+                 radius=512, chunk=4096)),
+    "ellipsoids128": dict(
+        desc="128^3 float32, 5 ellipsoids U(0.2,1.0) + noise 0.01, eb 1e-3 abs, ROI > 0.1 "
+             "+ 1-voxel dilation",
+        cfg=dict(eb=1e-3, eb_mode="abs", cmp="gt", threshold=0.1, dilate=1, fill=0.0,
+                 radius=512, chunk=4096)),
+}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def make_inputs(workload: str, device, seed: int = 0):
+    import torch
+    import phantom
+    if workload == "projections64":
+        return [phantom.projection(s, i, seed=seed, device=device)
+                for i, s in enumerate(phantom.projection_sides(64, 512, 2048, seed))]
+    if workload == "cube1024":
+        return [phantom.porous_cylinder(1024, radius=400.0, seed=seed, device=device)]
+    if workload == "cube512":
+        return [phantom.porous_cylinder(512, radius=200.0, seed=seed, device=device)]
+    if workload == "ellipsoids128":
+        return [phantom.ellipsoids(128, seed=seed, device=device)]
+    raise ValueError(workload)
+
+
+class Clocks:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [v.strip() for v in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": mx or None, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def stage_bytes(xs, outs, sizes, cfg):
+    """Algorithmic bytes per stage for one step (all items): what each kernel
+    must move at least, from the container headers (n retained voxels, nb
+    boundaries, nout records, nw payload words)."""
+    import oracle
+    names = ["reset", "threshold", "front", "symbols", "codebook", "pack", "finalize"]
+    tot = dict.fromkeys(names, 0.0)
+    S = 2 * cfg["radius"]
+    for x, o, sz in zip(xs, outs, sizes):
+        h = oracle.header(o[:256].cpu().numpy())
+        N, esz = x.numel(), x.element_size()
+        rows = N // x.shape[-1]
+        n, nb, nout, nw, nch = h["n"], h["n_bounds"], h["n_outliers"], h["payload_words"], h["n_chunks"]
+        tot["threshold"] += N * esz + N / 8
+        tot["front"] += N / 8 + 2 * n * esz + 2 * nb + 2 * rows
+        tot["symbols"] += n * esz + 2 * n + 12 * nout
+        tot["codebook"] += 8 * S + 5 * S
+        tot["pack"] += 2 * n + 4 * nw + 8 * nch
+        tot["finalize"] += 256 + 12 * nout
+    return tot
+
+
+# ---------------------------------------------------------------- ours
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    import paper_2602_15917_gb300 as roix
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    wl = WORKLOADS[args.workload]
+    cfg = wl["cfg"]
+    xs = make_inputs(args.workload, dev, seed=args.seed)
+    torch.cuda.synchronize()
+    in_bytes = sum(x.numel() * x.element_size() for x in xs)
+    esz = xs[0].element_size()
+    nstreams = min(args.streams, len(xs))
+    ctxs = [roix.Roix(local_rank) for _ in range(nstreams)]
+    streams = [torch.cuda.Stream(dev) for _ in range(nstreams)]
+    caps = [x.numel() * x.element_size() + 65536 for x in xs]
+    outs = [torch.empty(c, dtype=torch.uint8, device=dev) for c in caps]
+    sizes = torch.zeros(len(xs), dtype=torch.uint64, device=dev)
+    need = max(ctxs[0].workspace_size(x.shape, x.dtype, cap=caps[j], **cfg)
+               for j, x in enumerate(xs))
+    for c in ctxs:
+        c.reserve(need)  # no workspace growth once the graph holds its pointers
+    main = torch.cuda.current_stream(dev)
+
+    def step(inputs):
+        for s in streams:
+            s.wait_stream(main)
+        for i, x in enumerate(inputs):
+            k = i % nstreams
+            ctxs[k].compress(x, out=outs[i], cap=caps[i], size=sizes[i:i + 1],
+                             stream=streams[k], **cfg)
+        for s in streams:
+            main.wait_stream(s)
+
+    # correctness of the measured configuration: one step, sizes vs a re-run
+    step(xs)
+    for c, s in zip(ctxs, streams):
+        c.sync(s)
+    graph = None
+    if args.graph:
+        try:
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=main, capture_error_mode="thread_local"):
+                step(xs)
+            graph.replay()
+            torch.cuda.synchronize()
+        except Exception as e:  # capture refused: time the plain launches
+            print(f"# graph capture unavailable: {e}", file=sys.stderr)
+            graph = None
+    run = (lambda: graph.replay()) if graph is not None else (lambda: step(xs))
+    launches_per_step = 7 * len(xs)
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local_rank) as clk:
+        e0.record(main)
+        for _ in range(args.steps):
+            run()
+        e1.record(main)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms_total = e0.elapsed_time(e1)
+    for c, s in zip(ctxs, streams):
+        c.sync(s)
+    # max over ranks
+    t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = in_bytes * world / (ms_step / 1e3) / 1e9
+    out_bytes = int(sizes.sum().item())
+
+    # end to end: pinned host inputs -> device, compress, containers -> host
+    host_in = [x.cpu().pin_memory() for x in xs]
+    dev_in = [torch.empty_like(x) for x in xs]
+    host_out = [torch.empty(c, dtype=torch.uint8).pin_memory() for c in caps]
+    host_sizes = torch.empty(len(xs), dtype=torch.uint64).pin_memory()
+    sz_list = [int(v) for v in sizes.cpu().numpy()]
+
+    def e2e_step():
+        for h, d in zip(host_in, dev_in):
+            d.copy_(h, non_blocking=True)
+        step(dev_in)
+        host_sizes.copy_(sizes, non_blocking=True)
+        for i in range(len(xs)):
+            host_out[i][:sz_list[i]].copy_(outs[i][:sz_list[i]], non_blocking=True)
+
+    for _ in range(max(1, args.warmup // 2)):
+        e2e_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_s = float(te.item())
+    for c, s in zip(ctxs, streams):
+        c.sync(s)
+    e2e = {"value": in_bytes * world / e2e_s / 1e9, "unit": "GB/s",
+           "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": sum(sz_list) + 8 * len(xs)}
+
+    # dominant kernel: per-stage CUDA events on the launching stream, one item
+    # at a time (a profiling pass after the timed region)
+    prof = ctxs[0]
+    prof.profile(True)
+    stage_ms = np.zeros(8)
+    for _ in range(3):
+        for i, x in enumerate(xs):
+            prof.compress(x, out=outs[i], cap=caps[i], size=sizes[i:i + 1], stream=main, **cfg)
+            st = prof.profile_read(8)
+            stage_ms[:len(st)] += st
+    prof.profile(False)
+    torch.cuda.synchronize()
+    stage_ms /= 3
+    names = ["reset", "threshold", "front", "symbols", "codebook", "pack", "finalize"]
+    dom = int(np.argmax(stage_ms[:7]))
+    peak, peak_kind = load_peaks()
+    alg = stage_bytes(xs, outs, sizes.cpu().numpy(), cfg)
+    ach = alg[names[dom]] / (stage_ms[dom] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": names[dom], "achieved": round(ach, 1),
+                "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
+                "frac": round(ach / peak, 4), "traffic": None,
+                "algorithmic_bytes_per_step": round(alg[names[dom]]),
+                "stage_ms_per_step": {n: round(float(v), 4) for n, v in zip(names, stage_ms)},
+                "stage_gbs": {n: round(alg[n] / (float(v) / 1e3) / 1e9, 1)
+                              for n, v in zip(names, stage_ms) if v > 0}}
+
+    result = None
+    if rank == 0:
+        cpu = cpu_baseline(args, xs, cfg) if world == 1 and not args.no_cpu else None
+        result = {
+            "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u16" if esz == 2 else "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"], "items": len(xs),
+                       "bytes_in_per_step": in_bytes, "bytes_out_per_step": out_bytes,
+                       "compression_ratio": round(in_bytes / max(out_bytes, 1), 3),
+                       "path": "plain calls on %d streams%s" % (
+                           nstreams, " under one CUDA graph" if graph is not None else ""),
+                       "l2": "inputs larger than L2 (129 MB)" if in_bytes > 129e6
+                       else "inputs smaller than L2: not flushed",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": {k: (round(v, 2) if isinstance(v, float) else v) for k, v in e2e.items()},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk.summary(),
+        }
+    for c in ctxs:
+        c.close()
+    return result
+
+
+def cpu_baseline(args, xs, cfg, budget_s: float = None):
+    """The oracle as it stands, single-threaded on the host, on a bounded
+    sample of the workload's items (~budget_s of work)."""
+    import oracle
+    budget_s = args.cpu_budget if budget_s is None else budget_s
+    if len(xs) == 1 and xs[0].dim() == 3 and xs[0].shape[0] > 64:
+        # one large volume: a slab of whole slices from its middle
+        z = xs[0].shape[0]
+        nz = 16
+        items = [xs[0][z // 2 - nz // 2: z // 2 + nz // 2].cpu().numpy()]
+        sample = f"{nz} middle slices of the volume, repeated for ~{budget_s:.0f} s"
+    else:
+        items = [x.cpu().numpy() for x in xs]
+        sample = f"items in order until ~{budget_s:.0f} s"
+    done, t0, i = 0, time.perf_counter(), 0
+    while True:
+        x = items[i % len(items)]
+        oracle.compress(x, **cfg)
+        done += x.nbytes
+        i += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": round(done / dt / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{sample}: {i} items, {done / 1e6:.0f} MB in {dt:.1f} s"}
+
+
+# ---------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import torch
+    wl = WORKLOADS[args.workload]
+    xs = make_inputs(args.workload, "cpu", seed=args.seed)
+    per_step = max(1.0, args.cpu_budget / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_baseline(args, xs, wl["cfg"], budget_s=per_step)
+    vals = [cpu_baseline(args, xs, wl["cfg"], budget_s=per_step) for _ in range(args.steps)]
+    gbs = float(np.mean([v["value"] for v in vals]))
+    esz = xs[0].element_size()
+    in_bytes = sum(x.numel() * x.element_size() for x in xs)
+    return {
+        "metric": METRIC, "value": round(gbs, 4), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(in_bytes / (gbs * 1e9) * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u16" if esz == 2 else "f32",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": args.workload, "desc": wl["desc"], "items": len(xs)},
+        "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": vals[-1]["sample"]},
+        "e2e": {"value": round(gbs, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="projections64", choices=sorted(WORKLOADS))
+    ap.add_argument("--streams", type=int, default=8)
+    ap.add_argument("--graph", type=int, default=1)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--cpu-budget", type=float, default=10.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+    else:
+        if world > 1:
+            import torch
+            import torch.distributed as dist
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+        res = run_ours(args, rank, world, local_rank)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+    if rank == 0 and res is not None:
+        print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()
