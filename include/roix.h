@@ -178,6 +178,26 @@ roix_status roix_encode(roix_ctx* ctx, const int32_t* q, const uint32_t* outlier
 roix_status roix_decode(roix_ctx* ctx, const void* in, uint64_t size, void* out,
                         roix_dtype dtype, roix_dims dims, void* stream);
 
+/* Allocation-free variant of roix_extract_roi, for callers that cannot
+ * allocate device memory when they need a mask: code recording a CUDA graph in
+ * global capture mode (where cudaMalloc is refused), acquisition loops that
+ * must never block on the device synchronisation that cudaMalloc/cudaFree
+ * imply, and processes whose device memory all belongs to another allocator or
+ * a fixed budget. The paper has no counterpart; this is an interface choice.
+ * Same inputs, outputs and results as roix_extract_roi, without a context: it
+ * runs on the calling thread's current CUDA device. Its scratch (the mask
+ * before dilation) is a 32 MiB device array in the library itself, present on
+ * every GPU that loads the library until the process exits; volumes needing
+ * more than 2^23 mask words (ny*nz*ceil(nx/32)) return ROIX_EINVAL before
+ * anything is enqueued. The first call on a device looks up the array's
+ * device address; make that first call before any stream capture. All calls
+ * share the array: calls that overlap on the GPU (other streams or host
+ * threads on the same device) race and must be serialised by the caller.
+ * Nothing is allocated: no cudaMalloc, no cudaFree. */
+roix_status roix_extract_roi_static(const void* in, roix_dtype dtype, roix_dims dims,
+                                    const roix_roi* roi, uint32_t* mask_out,
+                                    uint64_t* popcount_dev, void* stream);
+
 /* Per-stage timing: with profiling on, roix_compress records a CUDA event on
  * its stream after each stage; roix_profile_read waits for them and writes up
  * to `max` stage durations (ms) of the last call, returning their number. The

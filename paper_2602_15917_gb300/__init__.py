@@ -92,6 +92,7 @@ def lib():
                 "roix_compress": (st, [P, P, i32, D, R, E, PR, P, u64, P, P]),
                 "roix_profile": (st, [P, C.c_int]),
                 "roix_profile_read": (C.c_int, [P, C.POINTER(C.c_float), C.c_int]),
+                "roix_extract_roi_static": (st, [P, i32, D, R, P, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -107,7 +108,7 @@ def symbols():
             "roix_sync", "roix_last_error", "roix_status_string", "roix_mask_words",
             "roix_compress_bound", "roix_extract_roi", "roix_compact", "roix_quantize",
             "roix_encode", "roix_decode", "roix_compress", "roix_profile",
-            "roix_profile_read"]
+            "roix_profile_read", "roix_extract_roi_static"]
 
 
 def _dtype_code(t: torch.Tensor) -> int:

@@ -112,8 +112,12 @@ bool dims_ok(roix_dims d) {
   return N < 1.1e12;
 }
 
-roix_status make_desc(roix_ctx* ctx, roix_dtype dtype, roix_dims dims, const roix_roi* roi,
-                      const roix_eb* eb, const roix_params* prm, Desc* d) {
+}  // namespace
+
+// Validates the settings of a call and turns them into the kernel descriptor
+// (thresholds converted once, on the host, to the comparisons the kernels do).
+roix_status roix::make_desc(roix_ctx* ctx, roix_dtype dtype, roix_dims dims, const roix_roi* roi,
+                            const roix_eb* eb, const roix_params* prm, Desc* d) {
   std::memset(d, 0, sizeof(*d));
   if (dtype != ROIX_F32 && dtype != ROIX_U16) return fail(ctx, ROIX_EINVAL, "dtype must be ROIX_F32 or ROIX_U16");
   if (!dims_ok(dims)) return fail(ctx, ROIX_EINVAL, "dims: nx <= 65534, ny, nz < 2^32, N < 1.1e12");
@@ -176,6 +180,8 @@ roix_status make_desc(roix_ctx* ctx, roix_dtype dtype, roix_dims dims, const roi
   }
   return ROIX_OK;
 }
+
+namespace {
 
 bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 

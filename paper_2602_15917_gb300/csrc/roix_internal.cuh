@@ -268,6 +268,10 @@ __device__ __forceinline__ int quant_u16(unsigned raw, int dark, int eb_int) {
   return num >= 0 ? num / den : -((-num + den - 1) / den);
 }
 
+// Host: argument checks and descriptor (roix_api.cu); ctx may be null.
+roix_status make_desc(roix_ctx* ctx, roix_dtype dtype, roix_dims dims, const roix_roi* roi,
+                      const roix_eb* eb, const roix_params* prm, Desc* d);
+
 // ------------------------------------------------------ launch functions
 struct Launch {
   cudaStream_t stream;
