@@ -74,7 +74,8 @@ __global__ void __launch_bounds__(kThreads) k_quantize_stage(Desc d, const TV* _
 
 // -------------------------------------------------------------- symbols
 // Code of value k and its outlier flag, either quantised on the fly from the
-// pixel section (fused path) or read from the staged codes.
+// pixel section (fused path) or read from the staged codes. Loads and the
+// evaluation are separate so that a batch of loads can be issued first.
 template <typename TV, bool FROM_Q>
 struct Src {
   const TV* P;
@@ -82,42 +83,87 @@ struct Src {
   const u32* obits;
   roix_eb_info e;
   int dark;
-  __device__ __forceinline__ int code(u64 k, bool& out) const {
+  struct R {
+    TV x;
+    int q;
+    u32 o;
+  };
+  __device__ __forceinline__ R load1(u64 k) const {
+    R r{TV(0), 0, 0u};
     if constexpr (FROM_Q) {
-      out = (__ldg(obits + (k >> 5)) >> (k & 31)) & 1u;
-      return out ? 0 : __ldg(q + k);
-    } else if constexpr (sizeof(TV) == 4) {
-      return quant_f32(__ldg(P + k), e, out);
+      r.q = __ldg(q + k);
+      r.o = (__ldg(obits + (k >> 5)) >> (k & 31)) & 1u;
     } else {
-      out = false;
-      return quant_u16(__ldg(P + k), dark, e.eb_int);
+      r.x = __ldg(P + k);
+    }
+    return r;
+  }
+  // k0 even and k0 + 1 < n: one vector load for the pair
+  __device__ __forceinline__ void load2(u64 k0, R& a, R& b) const {
+    a = R{TV(0), 0, 0u};
+    b = R{TV(0), 0, 0u};
+    if constexpr (FROM_Q) {
+      const int2 v = __ldg(reinterpret_cast<const int2*>(q + k0));
+      const u32 w = __ldg(obits + (k0 >> 5));
+      a.q = v.x;
+      b.q = v.y;
+      a.o = (w >> (k0 & 31)) & 1u;
+      b.o = (w >> ((k0 + 1) & 31)) & 1u;
+    } else if constexpr (sizeof(TV) == 4) {
+      const float2 v = __ldg(reinterpret_cast<const float2*>(P + k0));
+      a.x = v.x;
+      b.x = v.y;
+    } else {
+      const ushort2 v = __ldg(reinterpret_cast<const ushort2*>(P + k0));
+      a.x = v.x;
+      b.x = v.y;
     }
   }
+  __device__ __forceinline__ int eval(const R& r, bool& out) const {
+    if constexpr (FROM_Q) {
+      out = r.o != 0u;
+      return out ? 0 : r.q;
+    } else if constexpr (sizeof(TV) == 4) {
+      return quant_f32(r.x, e, out);
+    } else {
+      out = false;
+      return quant_u16(r.x, dark, e.eb_int);
+    }
+  }
+  __device__ __forceinline__ int code(u64 k, bool& out) const { return eval(load1(k), out); }
   __device__ __forceinline__ u32 raw_bits(u64 k) const {
     if constexpr (sizeof(TV) == 4) return __float_as_uint(__ldg(P + k));
     else return (u32)__ldg(P + k);
   }
 };
 
+// Symbol of a delta: d + R when -R < d < R, else 0. Codes lie in
+// [-2^30, 2^30], so the true delta lies in [-2^31, 2^31]; its two's-complement
+// wrap to 0x80000000 at the extremes still fails the unsigned range test.
 __device__ __forceinline__ u32 symbol_of(int c, int prev, bool out, u32 R) {
   if (out) return 0u;
-  const long long dd = (long long)c - (long long)prev;
-  return (dd > -(long long)R && dd < (long long)R) ? (u32)(dd + R) : 0u;
+  const u32 dd = (u32)c - (u32)prev;
+  return (dd + R - 1u < 2u * R - 1u) ? dd + R : 0u;
 }
 
-__device__ __forceinline__ u32 interleave16(u32 a, u32 b) {  // bit i of a -> 2i, of b -> 2i+1
-  u32 r = 0;
-#pragma unroll
-  for (int i = 0; i < 16; ++i) r |= (((a >> i) & 1u) << (2 * i)) | (((b >> i) & 1u) << (2 * i + 1));
-  return r;
+// bits 0..15 of v spread to the even positions 0, 2, ..., 30
+__device__ __forceinline__ u32 spread16(u32 v) {
+  v &= 0xffffu;
+  v = (v | (v << 8)) & 0x00ff00ffu;
+  v = (v | (v << 4)) & 0x0f0f0f0fu;
+  v = (v | (v << 2)) & 0x33333333u;
+  v = (v | (v << 1)) & 0x55555555u;
+  return v;
 }
 
-// Persistent blocks take tiles of kQuantTile values. A thread handles pairs
-// (k, k+1) so that symbol stores are 32-bit and coalesced; the predecessor code
-// of the pair comes from the neighbouring lane (lane 0 recomputes it). Symbol-0
-// positions (records) are marked in a shared bitmap, counted, placed by the
-// look-back and written in order. The histogram is kept in shared memory per
-// block, warp-aggregated with __match_any_sync, and flushed once at the end.
+// Persistent blocks take tiles of kQuantTile values; each warp owns a
+// contiguous span of the tile and walks it 64 values (a pair per lane) per
+// step, so loads and symbol stores are coalesced vectors and the predecessor
+// of a step's first value is the warp's own last value of the step before.
+// Loads of four steps are issued before any is used. Symbol-0 positions
+// (records) are marked in a shared bitmap, counted, placed by the look-back
+// and written in order. The histogram lives in shared memory per block and is
+// flushed once at the end.
 template <typename TV, bool FROM_Q>
 __global__ void __launch_bounds__(kThreads) k_symbols(Desc d, Src<TV, FROM_Q> src, u64 n_cap,
                                                       const u64* n_dev, State* st,
@@ -125,17 +171,22 @@ __global__ void __launch_bounds__(kThreads) k_symbols(Desc d, Src<TV, FROM_Q> sr
                                                       u64* __restrict__ rk, u32* __restrict__ rv,
                                                       u64 rec_cap, unsigned long long* hist,
                                                       LookBack<1> lb, int compute_eb) {
+  using R = typename Src<TV, FROM_Q>::R;
+  constexpr u32 kSpan = kQuantTile / (kThreads / 32);  // values per warp and tile
+  constexpr int kSteps = kSpan / 64;
+  constexpr int kBatch = 4;
   __shared__ u32 h[kMaxSym];
   __shared__ u32 bitmap[kQuantTile / 32];
   __shared__ u32 scratch[40];
   __shared__ u64 s_tile, s_base;
   static_assert(kQuantTile / 32 == kThreads, "one bitmap word per thread");
+  static_assert(kSteps % kBatch == 0, "whole batches");
   const u64 n = n_dev ? min(*n_dev, n_cap) : n_cap;
   if (compute_eb) {
     src.e = make_eb(d, st->vmin_key, st->vmax_key);
     if (blockIdx.x == 0 && threadIdx.x == 0) st->eb = src.e;
   }
-  const u32 R = d.R;
+  const u32 R_ = d.R;
   for (u32 i = threadIdx.x; i < d.S; i += blockDim.x) h[i] = 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const u64 ntiles = (n + kQuantTile - 1) / kQuantTile;
@@ -146,43 +197,56 @@ __global__ void __launch_bounds__(kThreads) k_symbols(Desc d, Src<TV, FROM_Q> sr
     const u64 t = s_tile;
     if (t >= ntiles) break;
     const u64 base = t * kQuantTile;
-    for (u32 it = 0; it < kQuantTile / (2 * kThreads); ++it) {
-      const u32 pl = it * kThreads + threadIdx.x;  // pair within tile
-      const u64 k0 = base + 2 * (u64)pl, k1 = k0 + 1;
-      bool o0 = false, o1 = false;
-      int c0 = 0, c1 = 0;
-      if (k0 < n) c0 = src.code(k0, o0);
-      if (k1 < n) c1 = src.code(k1, o1);
-      int prev = __shfl_up_sync(0xffffffffu, c1, 1);
-      if (lane == 0) {
-        prev = 0;
-        if (k0 > 0 && k0 < n) {
-          bool op;
-          prev = src.code(k0 - 1, op);
+    const u64 span = base + (u64)warp * kSpan;
+    bitmap[threadIdx.x] = 0u;
+    // code of the value just before the warp's span
+    int carry = 0;
+    if (lane == 0 && span > 0 && span < n) {
+      bool op;
+      carry = src.code(span - 1, op);
+    }
+    carry = __shfl_sync(0xffffffffu, carry, 0);
+    __syncthreads();
+    for (int b0 = 0; b0 < kSteps; b0 += kBatch) {
+      R ra[kBatch], rb[kBatch];
+#pragma unroll
+      for (int j = 0; j < kBatch; ++j) {
+        const u64 k0 = span + 64 * (u64)(b0 + j) + 2 * lane;
+        if (k0 + 1 < n) {
+          src.load2(k0, ra[j], rb[j]);
+        } else {
+          ra[j] = k0 < n ? src.load1(k0) : R{TV(0), 0, 0u};
+          rb[j] = R{TV(0), 0, 0u};
         }
       }
-      const u32 s0 = k0 < n ? symbol_of(c0, prev, o0, R) : 1u;
-      const u32 s1 = k1 < n ? symbol_of(c1, c0, o1, R) : 1u;
-      if (k1 < n) {
-        *reinterpret_cast<u32*>(sym + k0) = s0 | (s1 << 16);
-      } else if (k0 < n) {
-        sym[k0] = (uint16_t)s0;
-      }
-      const bool r0 = k0 < n && s0 == 0, r1 = k1 < n && s1 == 0;
-      const u32 b0 = __ballot_sync(0xffffffffu, r0), b1 = __ballot_sync(0xffffffffu, r1);
-      if (lane == 0) {
-        const u32 wi = (it * kThreads + warp * 32) / 16;
-        bitmap[wi] = interleave16(b0 & 0xffffu, b1 & 0xffffu);
-        bitmap[wi + 1] = interleave16(b0 >> 16, b1 >> 16);
-      }
-      // histogram, one shared atomic per distinct symbol of the warp
-      {
-        const bool v0 = k0 < n;
-        const u32 m0 = __match_any_sync(0xffffffffu, v0 ? s0 : 0xffffffffu);
-        if (v0 && (__ffs(m0) - 1) == lane) atomicAdd(&h[s0], (u32)__popc(m0));
-        const bool v1 = k1 < n;
-        const u32 m1 = __match_any_sync(0xffffffffu, v1 ? s1 : 0xffffffffu);
-        if (v1 && (__ffs(m1) - 1) == lane) atomicAdd(&h[s1], (u32)__popc(m1));
+#pragma unroll
+      for (int j = 0; j < kBatch; ++j) {
+        const int it = b0 + j;
+        const u64 k0 = span + 64 * (u64)it + 2 * lane, k1 = k0 + 1;
+        bool o0 = false, o1 = false;
+        const int c0 = k0 < n ? src.eval(ra[j], o0) : 0;
+        const int c1 = k1 < n ? src.eval(rb[j], o1) : 0;
+        int prev = __shfl_up_sync(0xffffffffu, c1, 1);
+        if (lane == 0) prev = carry;
+        carry = __shfl_sync(0xffffffffu, c1, 31);
+        const u32 s0 = k0 < n ? symbol_of(c0, prev, o0, R_) : 1u;
+        const u32 s1 = k1 < n ? symbol_of(c1, c0, o1, R_) : 1u;
+        if (k1 < n) {
+          *reinterpret_cast<u32*>(sym + k0) = s0 | (s1 << 16);
+        } else if (k0 < n) {
+          sym[k0] = (uint16_t)s0;
+        }
+        const bool r0 = k0 < n && s0 == 0, r1 = k1 < n && s1 == 0;
+        const u32 bb0 = __ballot_sync(0xffffffffu, r0), bb1 = __ballot_sync(0xffffffffu, r1);
+        if ((bb0 | bb1) && lane < 2) {  // records are rare: the bitmap starts zeroed
+          const u32 wi = warp * (kSpan / 32) + 2 * it + lane;
+          const u32 sh = lane ? 16u : 0u;
+          bitmap[wi] = spread16(bb0 >> sh) | (spread16(bb1 >> sh) << 1);
+        }
+        // histogram: deltas of noisy data rarely repeat within a warp, so plain
+        // shared-memory atomics beat warp aggregation here
+        if (k0 < n) atomicAdd(&h[s0], 1u);
+        if (k1 < n) atomicAdd(&h[s1], 1u);
       }
     }
     __syncthreads();
@@ -190,11 +254,13 @@ __global__ void __launch_bounds__(kThreads) k_symbols(Desc d, Src<TV, FROM_Q> sr
     const u32 word = bitmap[threadIdx.x];
     u32 total;
     const u32 off = block_excl_scan<u32>(__popc(word), scratch, &total);
-    if (threadIdx.x == 0) {
+    if (warp == 0) {
       u64 mine[1] = {total}, excl[1];
-      lookback<1>(lb, t, mine, excl, &st->status);
-      s_base = excl[0];
-      if (t == ntiles - 1) st->nout = excl[0] + total;
+      lookback_warp<1>(lb, t, mine, excl, &st->status);
+      if (lane == 0) {
+        s_base = excl[0];
+        if (t == ntiles - 1) st->nout = excl[0] + total;
+      }
     }
     __syncthreads();
     if (word) {
@@ -417,24 +483,57 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(Desc d, const unsigned 
 }
 
 // ------------------------------------------------------------------- pack
-// Persistent blocks take chunks of C symbols. Per chunk: code lengths summed
-// per thread (consecutive symbols), block scan, look-back for the chunk's word
-// offset, codes OR-ed into a shared word buffer MSB first, buffer copied out.
+// Persistent blocks take ranges of kPackRange chunks of C symbols, in order.
+// Pass 1 sums the code lengths of every chunk of the range (block scans; the
+// per-thread bit offsets are kept in shared memory); one look-back per range
+// gives the range's word offset. Pass 2 re-reads each chunk (from L2), shifts
+// every thread's codes through a 64-bit register, stores the words that lie
+// wholly inside its bit range and OR-s only its first and last (shared)
+// words into the shared buffer, which is copied out with coalesced stores.
+constexpr u32 kPackRange = 8;
+
+template <int EPT>
+__device__ __forceinline__ void load_syms(const uint16_t* __restrict__ sym, u64 k0, u64 n,
+                                          uint16_t (&sv)[EPT]) {
+  if constexpr (EPT % 8 == 0) {
+    if (k0 + EPT <= n) {
+#pragma unroll
+      for (int j = 0; j < EPT; j += 8) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(sym + k0 + j));
+        const u32 w4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          sv[j + 2 * q] = (uint16_t)(w4[q] & 0xffffu);
+          sv[j + 2 * q + 1] = (uint16_t)(w4[q] >> 16);
+        }
+      }
+      return;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < EPT; ++j) sv[j] = k0 + j < n ? __ldg(sym + k0 + j) : (uint16_t)0;
+}
+
 template <int EPT>  // symbols per thread = C / 256
-__global__ void __launch_bounds__(kThreads) k_pack(Desc d, const uint16_t* __restrict__ sym,
-                                                   const u64* n_dev, const u64* nb_dev,
-                                                   const uint8_t* lens_ws, const u32* codes_ws,
-                                                   State* st, uint8_t* out, u64 cap,
-                                                   LookBack<1> lb) {
+__global__ void __launch_bounds__(kThreads, 4) k_pack(Desc d, const uint16_t* __restrict__ sym,
+                                                      const u64* n_dev, const u64* nb_dev,
+                                                      const uint8_t* lens_ws,
+                                                      const u32* codes_ws, State* st,
+                                                      uint8_t* out, u64 cap, LookBack<1> lb) {
   extern __shared__ u32 wbuf[];  // C * 24 / 32 + 2 words
+  constexpr u32 kPackWordsMax = EPT * kThreads * kLMax / 32 + 2;
   __shared__ uint8_t slen[kMaxSym];
   __shared__ u32 scode[kMaxSym];
+  __shared__ u32 boffs[kPackRange][kThreads];
+  __shared__ u32 cwords[kPackRange];
   __shared__ u32 scratch[40];
   __shared__ u64 s_tile, s_base;
   const u64 n = *n_dev;
   const u32 C = d.C;
   const u64 nchunks = (n + C - 1) / C;
+  const u64 nranges = (nchunks + kPackRange - 1) / kPackRange;
   const Layout Lo = make_layout(d.S, d.rows, *nb_dev, st->nout, nchunks, 0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (u32 i = threadIdx.x; i < d.S; i += blockDim.x) {
     slen[i] = lens_ws[i];
     scode[i] = codes_ws[i];
@@ -443,69 +542,82 @@ __global__ void __launch_bounds__(kThreads) k_pack(Desc d, const uint16_t* __res
   while (true) {
     if (threadIdx.x == 0) s_tile = atomicAdd(&st->ctr_pack, 1u);
     __syncthreads();
-    const u64 t = s_tile;
-    if (t >= nchunks) break;
-    const u64 k0 = t * C + (u64)threadIdx.x * EPT;
-    uint16_t sv[EPT];
-    u32 bits = 0;
-    if constexpr (EPT % 8 == 0) {
-      if (k0 + EPT <= n) {
+    const u64 r = s_tile;
+    if (r >= nranges) break;
+    const u64 c_lo = r * kPackRange;
+    const u32 nc = (u32)umin(kPackRange, nchunks - c_lo);
+    // pass 1: bits per thread and chunk
+    for (u32 c = 0; c < nc; ++c) {
+      const u64 k0 = (c_lo + c) * C + (u64)threadIdx.x * EPT;
+      uint16_t sv[EPT];
+      load_syms<EPT>(sym, k0, n, sv);
+      u32 bits = 0;
 #pragma unroll
-        for (int j = 0; j < EPT; j += 8) {
-          const uint4 v = __ldg(reinterpret_cast<const uint4*>(sym + k0 + j));
-          const u32 w4[4] = {v.x, v.y, v.z, v.w};
+      for (int j = 0; j < EPT; ++j) bits += (k0 + j < n) ? slen[sv[j]] : 0u;
+      u32 total;
+      boffs[c][threadIdx.x] = block_excl_scan<u32>(bits, scratch, &total);
+      if (threadIdx.x == 0) cwords[c] = (total + 31) >> 5;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      u32 rw = lane < nc ? cwords[lane] : 0u;
+      rw = warp_sum(rw);
+      u64 mine[1] = {rw}, excl[1];
+      lookback_warp<1>(lb, r, mine, excl, &st->status);
+      if (lane == 0) {
+        s_base = excl[0];
+        if (r == nranges - 1) st->nwords = excl[0] + rw;
+      }
+    }
+    __syncthreads();
+    // pass 2: pack and copy out each chunk
+    u64 cbase = s_base;
+    for (u32 c = 0; c < nc; ++c) {
+      const u64 t = c_lo + c;
+      const u32 words = cwords[c];
+      if (threadIdx.x == 0) {
+        const u64 o = Lo.off_chunks + 8 * t;
+        if (o + 8 <= cap) *reinterpret_cast<u64*>(out + o) = cbase;
+      }
+      for (u32 i = threadIdx.x; i <= words && i < kPackWordsMax; i += blockDim.x) wbuf[i] = 0;
+      __syncthreads();
+      const u64 k0 = t * C + (u64)threadIdx.x * EPT;
+      uint16_t sv[EPT];
+      load_syms<EPT>(sym, k0, n, sv);
+      const u32 boff = boffs[c][threadIdx.x];
+      u64 acc = 0;
+      u32 nacc = boff & 31;  // leading bits belong to earlier threads (zeros here)
+      u32 wi = boff >> 5;
+      bool shared_first = (boff & 31) != 0;
+      u32 mybits = 0;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            sv[j + 2 * q] = (uint16_t)(w4[q] & 0xffffu);
-            sv[j + 2 * q + 1] = (uint16_t)(w4[q] >> 16);
+      for (int j = 0; j < EPT; ++j) {
+        if (k0 + j < n) {
+          const u32 l = slen[sv[j]];
+          mybits += l;
+          acc = (acc << l) | scode[sv[j]];
+          nacc += l;
+          if (nacc >= 32) {
+            const u32 wv = (u32)(acc >> (nacc - 32));
+            if (shared_first) atomicOr(&wbuf[wi], wv);
+            else wbuf[wi] = wv;
+            shared_first = false;
+            ++wi;
+            nacc -= 32;
+            acc &= (1ull << nacc) - 1ull;
           }
         }
-      } else {
-#pragma unroll
-        for (int j = 0; j < EPT; ++j) sv[j] = k0 + j < n ? __ldg(sym + k0 + j) : (uint16_t)0;
       }
-    } else {
-#pragma unroll
-      for (int j = 0; j < EPT; ++j) sv[j] = k0 + j < n ? __ldg(sym + k0 + j) : (uint16_t)0;
-    }
-#pragma unroll
-    for (int j = 0; j < EPT; ++j) bits += (k0 + j < n) ? slen[sv[j]] : 0u;
-    u32 total;
-    const u32 boff = block_excl_scan<u32>(bits, scratch, &total);
-    const u32 words = (total + 31) >> 5;
-    if (threadIdx.x == 0) {
-      u64 mine[1] = {words}, excl[1];
-      lookback<1>(lb, t, mine, excl, &st->status);
-      s_base = excl[0];
-      if (t == nchunks - 1) st->nwords = excl[0] + words;
-      const u64 o = Lo.off_chunks + 8 * t;
-      if (o + 8 <= cap) *reinterpret_cast<u64*>(out + o) = excl[0];
-    }
-    for (u32 i = threadIdx.x; i < words + 1; i += blockDim.x) wbuf[i] = 0;
-    __syncthreads();
-    u32 p = boff;
-#pragma unroll
-    for (int j = 0; j < EPT; ++j) {
-      if (k0 + j < n) {
-        const u32 l = slen[sv[j]], c = scode[sv[j]];
-        const u32 wi = p >> 5, bo = p & 31;  // code occupies bits bo..bo+l-1 from the MSB
-        if (bo + l <= 32) {
-          atomicOr(&wbuf[wi], c << (32 - bo - l));
-        } else {
-          const u32 spill = bo + l - 32;
-          atomicOr(&wbuf[wi], c >> spill);
-          atomicOr(&wbuf[wi + 1], c << (32 - spill));
-        }
-        p += l;
+      if (mybits && nacc > (shared_first ? (boff & 31) : 0u))
+        atomicOr(&wbuf[wi], (u32)(acc << (32 - nacc)));
+      __syncthreads();
+      for (u32 i = threadIdx.x; i < words; i += blockDim.x) {
+        const u64 o = Lo.off_payload + 4 * (cbase + i);
+        if (o + 4 <= cap) *reinterpret_cast<u32*>(out + o) = wbuf[i];
       }
+      cbase += words;
+      __syncthreads();
     }
-    __syncthreads();
-    const u64 base = s_base;
-    for (u32 i = threadIdx.x; i < words; i += blockDim.x) {
-      const u64 o = Lo.off_payload + 4 * (base + i);
-      if (o + 4 <= cap) *reinterpret_cast<u32*>(out + o) = wbuf[i];
-    }
-    __syncthreads();
   }
 }
 
@@ -703,6 +815,7 @@ void launch_pack(const Launch& L, const Desc& d, const uint16_t* sym, const u64*
                  uint8_t* out, u64 cap, LookBack<1> lb, u64 chunks_cap) {
   if (chunks_cap == 0) return;
   const size_t smem = ((size_t)d.C * kLMax / 32 + 2) * 4;
+  chunks_cap = (chunks_cap + kPackRange - 1) / kPackRange;  // tickets are ranges
   auto run = [&](auto kernel) {
     cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);

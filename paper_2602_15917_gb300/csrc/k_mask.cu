@@ -28,10 +28,10 @@ __device__ __forceinline__ u32 last_mask(const Desc& d, u64 w) {
 }
 
 // ----------------------------------------------------------- binarisation
-// One warp turns a row segment of up to 1024 voxels into 32 mask words: each
-// lane reads one voxel per step (one coalesced 128-byte line per warp for
-// float32), and a ballot forms the word. Eight independent loads are issued
-// before the ballots so that every warp keeps several lines in flight.
+// One warp turns a row segment of up to 1024 voxels into 32 mask words. All of
+// the segment's loads are issued before any is used (32 coalesced lines per
+// warp in flight per batch of 8), then one ballot per 32 voxels forms each
+// word. Used for rows that are not 16-byte aligned.
 template <typename TV>
 __global__ void __launch_bounds__(kThreads) k_threshold(Desc d, const TV* __restrict__ in,
                                                         u32* __restrict__ T) {
@@ -40,29 +40,88 @@ __global__ void __launch_bounds__(kThreads) k_threshold(Desc d, const TV* __rest
   const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
   const u64 spr = (d.nx + 1023) >> 10;  // segments per row
   const u64 nseg = d.rows * spr;
+  const u32 nx = (u32)d.nx;
   for (u64 s = warp; s < nseg; s += nwarps) {
-    const u64 r = s / spr, sg = s - r * spr;
-    const u64 x0 = sg << 10;
-    const u32 nw = (u32)umin(32, (d.nx - x0 + 31) >> 5);
+    const u64 r = s / spr;
+    const u32 x0 = (u32)(s - r * spr) << 10;
+    const u32 nw = min(32u, (nx - x0 + 31) >> 5);
     const TV* row = in + r * d.nx;
     u32 mine = 0;
     for (u32 i = 0; i < nw; i += 8) {
       TV v[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        const u64 x = x0 + (u64)(i + j) * 32 + lane;
-        v[j] = (i + j < nw && x < d.nx) ? __ldg(row + x) : TV(0);
+        const u32 x = x0 + (i + j) * 32 + lane;
+        v[j] = x < nx ? __ldg(row + x) : TV(0);
       }
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        const u64 x = x0 + (u64)(i + j) * 32 + lane;
+        const u32 x = x0 + (i + j) * 32 + lane;
         bool p;
         if constexpr (sizeof(TV) == 4) p = pass_f32(v[j], d);
         else p = pass_u16(v[j], d);
-        p = p && (i + j < nw) && (x < d.nx);
-        const u32 b = __ballot_sync(0xffffffffu, p);
+        const u32 b = __ballot_sync(0xffffffffu, p && x < nx);
         if (lane == (int)(i + j)) mine = b;
       }
+    }
+    if ((u32)lane < nw) T[r * d.W + (x0 >> 5) + lane] = mine;
+  }
+}
+
+// Vector form for 16-byte aligned rows (float32: nx % 4 == 0, uint16: nx % 8
+// == 0). A warp reads a 1024-voxel segment with 8 (float4) or 4 (uint4)
+// coalesced 512-byte loads per lane group, all in flight before use. Each lane
+// turns its 4 or 8 voxels into a nibble or byte; XOR-shuffles OR the 8 nibbles
+// (4 bytes) of a mask word together, and lane w picks word w.
+template <typename TV>
+__global__ void __launch_bounds__(kThreads) k_threshold_vec(Desc d, const TV* __restrict__ in,
+                                                            u32* __restrict__ T) {
+  constexpr int kPer = sizeof(TV) == 4 ? 4 : 8;  // voxels per lane and load
+  constexpr int kLoads = 1024 / (32 * kPer);      // loads per segment
+  constexpr int kLanesPerWord = 32 / kPer;        // lanes contributing to one word
+  constexpr int kWordsPerLoad = 32 / kLanesPerWord;
+  const int lane = threadIdx.x & 31;
+  const u64 warp = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
+  const u64 spr = (d.nx + 1023) >> 10;
+  const u64 nseg = d.rows * spr;
+  const u32 nx = (u32)d.nx;
+  for (u64 s = warp; s < nseg; s += nwarps) {
+    const u64 r = s / spr;
+    const u32 x0 = (u32)(s - r * spr) << 10;
+    const u32 nw = min(32u, (nx - x0 + 31) >> 5);
+    const uint4* row = reinterpret_cast<const uint4*>(in + r * d.nx);
+    uint4 v[kLoads];
+#pragma unroll
+    for (int i = 0; i < kLoads; ++i) {
+      const u32 x = x0 + (u32)i * (32 * kPer) + (u32)lane * kPer;
+      v[i] = x < nx ? __ldg(row + x / kPer) : make_uint4(0u, 0u, 0u, 0u);
+    }
+    u32 mine = 0;
+#pragma unroll
+    for (int i = 0; i < kLoads; ++i) {
+      const u32 x = x0 + (u32)i * (32 * kPer) + (u32)lane * kPer;
+      u32 bits = 0;
+      if (x < nx) {
+        if constexpr (sizeof(TV) == 4) {
+          bits = (pass_f32(__uint_as_float(v[i].x), d) ? 1u : 0u) |
+                 (pass_f32(__uint_as_float(v[i].y), d) ? 2u : 0u) |
+                 (pass_f32(__uint_as_float(v[i].z), d) ? 4u : 0u) |
+                 (pass_f32(__uint_as_float(v[i].w), d) ? 8u : 0u);
+        } else {
+          const u32 q[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            bits |= (pass_u16(q[k] & 0xffffu, d) ? 1u : 0u) << (2 * k);
+            bits |= (pass_u16(q[k] >> 16, d) ? 1u : 0u) << (2 * k + 1);
+          }
+        }
+      }
+      u32 t = bits << (kPer * (lane & (kLanesPerWord - 1)));
+#pragma unroll
+      for (int o = 1; o < kLanesPerWord; o <<= 1) t |= __shfl_xor_sync(0xffffffffu, t, o);
+      const u32 wv = __shfl_sync(0xffffffffu, t, kLanesPerWord * (lane & (kWordsPerLoad - 1)));
+      if (lane / kWordsPerLoad == i) mine = wv;
     }
     if ((u32)lane < nw) T[r * d.W + (x0 >> 5) + lane] = mine;
   }
@@ -111,17 +170,13 @@ __global__ void __launch_bounds__(kThreads) k_dilate(Desc d, const u32* __restri
 // from the decoupled look-back, then write the pixel values, the boundaries
 // and the per-row boundary counts. Lanes map to the 32 bits of a word, so
 // both the value loads and the compacted stores are coalesced.
+constexpr u32 kListCap = 512;  // boundaries of one row kept per warp for run copies
+
 struct FrontSmem {
   u32 wn[kThreads / 32], wb[kThreads / 32];  // per-warp totals, then offsets
   u64 base_n, base_nb, tile;
   u32 scratch[40];
 };
-
-__device__ __forceinline__ u32 e_word(const u32* Dw, u64 i, u64 w) {
-  const u32 dv = Dw[i];
-  const u32 prev = w > 0 ? Dw[i - 1] : 0u;
-  return dv ^ ((dv << 1) | (prev >> 31));
-}
 
 template <typename TV>
 __global__ void __launch_bounds__(kThreads) k_front(Desc d, const TV* __restrict__ in,
@@ -134,10 +189,16 @@ __global__ void __launch_bounds__(kThreads) k_front(Desc d, const TV* __restrict
   extern __shared__ u32 smem_dyn[];
   __shared__ FrontSmem sh;
   const u32 W = (u32)d.W;
-  u32* Dw = smem_dyn;                    // [rpt * W]
-  u32* band = smem_dyn + (u64)rpt * W;   // [3][rpt + 2][W] when dilating
+  const FastDiv divW(W);
+  u32* Dw = smem_dyn;                                 // [rpt * W]
+  u32* rowcnt = Dw + (u64)rpt * W;                    // [rpt]
+  u32* bflag = rowcnt + rpt;                          // [rpt + 2]
+  uint16_t* blist = (uint16_t*)(bflag + rpt + 2);     // [8][kListCap] row boundary lists
+  u32* U = (u32*)(blist + (kThreads / 32) * kListCap);  // [rpt + 2][W] when dilating
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool end_extra = (d.nx & 31) == 0;  // boundary at x = nx lives past the last word
+  const u32 below = (1u << lane) - 1u;
+  const u64 zstride = d.ny * (u64)W;
   u32 kmin = 0xffffffffu, kmax = 0u;
 
   while (true) {
@@ -149,162 +210,232 @@ __global__ void __launch_bounds__(kThreads) k_front(Desc d, const TV* __restrict
     const u32 nrows = (u32)umin(rpt, d.rows - r0);
     const u32 nw = nrows * W;
 
-    // ---- D words
+    // ---- retained words D. Dilation by the 3x3x3 cube is separable: U = OR
+    // over z of T (staged once per band row), V = OR over y of U, D = V
+    // dilated in x. Band row j is row r0 - 1 + j; its flags say which
+    // neighbours exist (bit 16 = the row itself exists).
+    u32 any = 0u;
     if (dilate) {
-      const u32 bw = (rpt + 2) * W;
-      for (u32 i = threadIdx.x; i < 3 * bw; i += blockDim.x) {
-        const u32 b = i / bw, j = i - b * bw;
-        const int64_t rr = (int64_t)r0 + ((int64_t)b - 1) * (int64_t)d.ny - 1 + j / W;
-        band[i] = (rr >= 0 && rr < (int64_t)d.rows) ? __ldg(T + (u64)rr * W + (j % W)) : 0u;
+      for (u32 j = threadIdx.x; j < rpt + 2; j += blockDim.x) {
+        const int64_t rr = (int64_t)r0 - 1 + j;
+        u32 f = 0u;
+        if (rr >= 0 && rr < (int64_t)d.rows) {
+          const u64 z = (u64)rr / d.ny, y = (u64)rr - z * d.ny;
+          f = 16u | (y > 0 ? 1u : 0u) | (y + 1 < d.ny ? 2u : 0u) | (z > 0 ? 4u : 0u) |
+              (z + 1 < d.nz ? 8u : 0u);
+        }
+        bflag[j] = f;
       }
       __syncthreads();
-      for (u32 i = threadIdx.x; i < nw; i += blockDim.x) {
-        const u32 lr = i / W, w = i - lr * W;
-        const u64 r = r0 + lr;
-        const u64 y = r % d.ny, z = r / d.ny;
-        u32 acc = 0;
-#pragma unroll
-        for (int dz = -1; dz <= 1; ++dz) {
-          if ((dz < 0 && z == 0) || (dz > 0 && z + 1 >= d.nz)) continue;
-#pragma unroll
-          for (int dy = -1; dy <= 1; ++dy) {
-            if ((dy < 0 && y == 0) || (dy > 0 && y + 1 >= d.ny)) continue;
-            const u32* row = band + (dz + 1) * (rpt + 2) * W + (lr + 1 + dy) * W;
-            const u32 c = row[w];
-            const u32 lo = w > 0 ? row[w - 1] : 0u;
-            const u32 hi = w + 1 < W ? row[w + 1] : 0u;
-            acc |= c | (c << 1) | (lo >> 31) | (c >> 1) | (hi << 31);
-          }
+      const u32 nu = (nrows + 2) * W;
+      for (u32 i = threadIdx.x; i < nu; i += blockDim.x) {
+        const u32 j = divW.div(i), w = i - j * W;
+        const u32 f = bflag[j];
+        u32 u = 0u;
+        if (f & 16u) {
+          const u32* tr = T + (u64)((int64_t)r0 - 1 + j) * W + w;
+          u = __ldg(tr);
+          if (f & 4u) u |= __ldg(tr - zstride);
+          if (f & 8u) u |= __ldg(tr + zstride);
         }
-        Dw[i] = acc & last_mask(d, w);
+        U[i] = u;
+        any |= u;
+      }
+      any = __syncthreads_or(any);
+      if (any) {
+        for (u32 i = threadIdx.x; i < nw; i += blockDim.x) {
+          const u32 lr = divW.div(i), w = i - lr * W;
+          const u32 f = bflag[lr + 1];
+          const u32* um = U + lr * W;  // row above (band row lr)
+          const u32* uc = um + W;      // the row itself
+          const u32* up = uc + W;      // row below
+          auto vword = [&](u32 ww) {
+            u32 v = uc[ww];
+            if (f & 1u) v |= um[ww];
+            if (f & 2u) v |= up[ww];
+            return v;
+          };
+          const u32 c = vword(w);
+          const u32 lo = w > 0 ? vword(w - 1) : 0u;
+          const u32 hi = w + 1 < W ? vword(w + 1) : 0u;
+          Dw[i] = (c | (c << 1) | (lo >> 31) | (c >> 1) | (hi << 31)) & last_mask(d, w);
+        }
       }
     } else {
       for (u32 i = threadIdx.x; i < nw; i += blockDim.x) {
-        const u32 w = i % W;
-        Dw[i] = __ldg(T + r0 * W + i) & last_mask(d, w);
+        const u32 lr = divW.div(i), w = i - lr * W;
+        const u32 v = __ldg(T + r0 * W + i) & last_mask(d, w);
+        Dw[i] = v;
+        any |= v;
       }
+      any = __syncthreads_or(any);
     }
     __syncthreads();
 
-    // ---- per-warp totals of retained voxels and boundaries
-    const u32 per_warp = (nw + (kThreads / 32) - 1) / (kThreads / 32);
-    const u32 wbeg = min(nw, warp * per_warp), wend = min(nw, wbeg + per_warp);
+    // ---- per-warp totals: warps own whole rows (in order), lanes walk words
+    const u32 pwr = (nrows + (kThreads / 32) - 1) / (kThreads / 32);
+    const u32 rbeg = min(nrows, warp * pwr), rend = min(nrows, rbeg + pwr);
     {
       u32 cn = 0, cb = 0;
-      for (u32 i = wbeg + lane; i < wend; i += 32) {
-        const u32 w = i % W;
-        cn += __popc(Dw[i]);
-        cb += __popc(e_word(Dw, i, w));
-        if (end_extra && w == W - 1) cb += Dw[i] >> 31;
+      if (!any)
+        for (u32 lr = rbeg + lane; lr < rend; lr += 32) rowcnt[lr] = 0;
+      for (u32 lr = any ? rbeg : rend; lr < rend; ++lr) {
+        const u32* drow = Dw + lr * W;
+        u32 rn = 0, rb = 0;
+        for (u32 w = lane; w < W; w += 32) {
+          const u32 dv = drow[w];
+          const u32 pv = w ? drow[w - 1] : 0u;
+          rn += __popc(dv);
+          rb += __popc(dv ^ ((dv << 1) | (pv >> 31))) +
+                ((end_extra && w == W - 1) ? (dv >> 31) : 0u);
+        }
+        rn = warp_sum(rn);
+        rb = warp_sum(rb);
+        if (lane == 0) rowcnt[lr] = rb;
+        cn += rn;
+        cb += rb;
       }
-      cn = warp_sum(cn);
-      cb = warp_sum(cb);
       if (lane == 0) {
         sh.wn[warp] = cn;
         sh.wb[warp] = cb;
       }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      u64 tn = 0, tb = 0;
-      for (int k = 0; k < kThreads / 32; ++k) {
-        const u32 a = sh.wn[k], b = sh.wb[k];
-        sh.wn[k] = (u32)tn;
-        sh.wb[k] = (u32)tb;
-        tn += a;
-        tb += b;
+    if (warp == 0) {
+      const u32 a = lane < kThreads / 32 ? sh.wn[lane] : 0u;
+      const u32 b = lane < kThreads / 32 ? sh.wb[lane] : 0u;
+      const u32 ia = warp_incl_scan(a), ib = warp_incl_scan(b);
+      const u64 tn = __shfl_sync(0xffffffffu, ia, kThreads / 32 - 1);
+      const u64 tb = __shfl_sync(0xffffffffu, ib, kThreads / 32 - 1);
+      if (lane < kThreads / 32) {
+        sh.wn[lane] = ia - a;
+        sh.wb[lane] = ib - b;
       }
       u64 mine[2] = {tn, tb}, excl[2];
-      lookback<2>(lb, t, mine, excl, &st->status);
-      sh.base_n = excl[0];
-      sh.base_nb = excl[1];
-      if (t == ntiles - 1) {
-        sizes_out[0] = excl[0] + tn;
-        sizes_out[1] = excl[1] + tb;
+      lookback_warp<2>(lb, t, mine, excl, &st->status);
+      if (lane == 0) {
+        sh.base_n = excl[0];
+        sh.base_nb = excl[1];
+        if (t == ntiles - 1) {
+          sizes_out[0] = excl[0] + tn;
+          sizes_out[1] = excl[1] + tb;
+        }
       }
     }
     __syncthreads();
 
-    // ---- writes: values and boundaries, word by word, lane = bit
+    // ---- per row: boundaries (x positions where D turns on / off), then the
+    // values of each run [x_start, x_end) copied with coalesced loads/stores
     {
       u64 on = sh.base_n + sh.wn[warp];
       u64 ob = sh.base_nb + sh.wb[warp];
-      const u32 below = (1u << lane) - 1u;
-      for (u32 c0 = wbeg; c0 < wend; c0 += 32) {
-        const u32 i_l = c0 + lane;
-        const bool valid = i_l < wend;
-        const u32 w_l = i_l % W;
-        const u32 dv_l = valid ? Dw[i_l] : 0u;
-        const u32 ev_l = valid ? e_word(Dw, i_l, w_l) : 0u;
-        const u32 ex_l = (valid && end_extra && w_l == W - 1) ? (dv_l >> 31) : 0u;
-        const u32 pn = __popc(dv_l), pb = __popc(ev_l) + ex_l;
-        const u32 sn = warp_incl_scan(pn) - pn, sb = warp_incl_scan(pb) - pb;
-        const u32 cnt = min(32u, wend - c0);
-        for (u32 k0 = 0; k0 < cnt; k0 += 4) {
-          TV v[4];
-          bool has[4];
-          u64 pos[4];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const u32 k = k0 + j;
-            const u32 dv = __shfl_sync(0xffffffffu, dv_l, k & 31);
-            const u32 so = __shfl_sync(0xffffffffu, sn, k & 31);
-            const u32 i = c0 + k;
-            has[j] = k < cnt && ((dv >> lane) & 1u);
-            const u32 lr = i / W, w = i - lr * W;
-            pos[j] = on + so + __popc(dv & below);
-            v[j] = has[j] ? __ldg(in + (r0 + lr) * d.nx + (u64)w * 32 + lane) : TV(0);
+      uint16_t* lst = blist + warp * kListCap;
+      for (u32 lr = any ? rbeg : rend; lr < rend; ++lr) {
+        const u32 nbr = rowcnt[lr];
+        if (nbr == 0) continue;  // no boundary: nothing retained in this row
+        const u32* drow = Dw + lr * W;
+        const TV* irow = in + (r0 + lr) * d.nx;
+        const bool fast = nbr <= kListCap;
+        u32 bo = 0;
+        for (u32 w0 = 0; w0 < W; w0 += 32) {
+          const u32 w = w0 + lane;
+          u32 ev = 0u, ex = 0u;
+          if (w < W) {
+            const u32 dv = drow[w];
+            const u32 pv = w ? drow[w - 1] : 0u;
+            ev = dv ^ ((dv << 1) | (pv >> 31));
+            ex = (end_extra && w == W - 1) ? (dv >> 31) : 0u;
           }
+          const u32 pb = __popc(ev) + ex;
+          const u32 inc = warp_incl_scan(pb);
+          u32 o = bo + inc - pb;
+          while (ev) {
+            const u32 x = w * 32 + (__ffs(ev) - 1);
+            ev &= ev - 1;
+            if (ob + o < bounds_cap) bounds[ob + o] = (uint16_t)x;
+            else set_status(&st->status, ROIX_ECAPACITY);
+            if (fast) lst[o] = (uint16_t)x;
+            ++o;
+          }
+          if (ex) {
+            if (ob + o < bounds_cap) bounds[ob + o] = (uint16_t)d.nx;
+            else set_status(&st->status, ROIX_ECAPACITY);
+            if (fast) lst[o] = (uint16_t)d.nx;
+          }
+          bo += __shfl_sync(0xffffffffu, inc, 31);
+        }
+        __syncwarp();
+        if (fast) {
+          for (u32 i = 0; i < nbr; i += 2) {
+            const u32 xs = lst[i], xe = lst[i + 1];
+            const TV* src = irow + xs;
+            TV* dst = P + on;
+            const u32 len = xe - xs;
+            for (u32 e0 = 0; e0 < len; e0 += 128) {
+              TV v[4];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            if (has[j]) {
-              P[pos[j]] = v[j];
-              if constexpr (sizeof(TV) == 4) {
-                if (isfinite(v[j])) {
-                  const u32 kk = f32_key(__fadd_rn(v[j], 0.0f));
-                  kmin = min(kmin, kk);
-                  kmax = max(kmax, kk);
+              for (int j = 0; j < 4; ++j) {
+                const u32 e = e0 + j * 32 + lane;
+                v[j] = e < len ? __ldg(src + e) : TV(0);
+              }
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                const u32 e = e0 + j * 32 + lane;
+                if (e < len) {
+                  dst[e] = v[j];
+                  if constexpr (sizeof(TV) == 4) {
+                    if (isfinite(v[j])) {
+                      const u32 kq = f32_key(__fadd_rn(v[j], 0.0f));
+                      kmin = min(kmin, kq);
+                      kmax = max(kmax, kq);
+                    }
+                  } else {
+                    kmin = min(kmin, (u32)v[j] + 1u);
+                    kmax = max(kmax, (u32)v[j] + 1u);
+                  }
                 }
-              } else {
-                kmin = min(kmin, (u32)v[j] + 1u);
-                kmax = max(kmax, (u32)v[j] + 1u);
               }
             }
+            on += len;
+          }
+        } else {
+          // many short runs: lanes take the bits of one word at a time
+          for (u32 w0 = 0; w0 < W; w0 += 32) {
+            const u32 dv_l = w0 + lane < W ? drow[w0 + lane] : 0u;
+            const u32 pn = __popc(dv_l);
+            const u32 sn = warp_incl_scan(pn) - pn;
+            u32 nz = __ballot_sync(0xffffffffu, dv_l != 0u);
+            while (nz) {
+              const int k = __ffs(nz) - 1;
+              nz &= nz - 1;
+              const u32 dv = __shfl_sync(0xffffffffu, dv_l, k);
+              const u32 so = __shfl_sync(0xffffffffu, sn, k);
+              if ((dv >> lane) & 1u) {
+                const TV v = __ldg(irow + (u64)(w0 + k) * 32 + lane);
+                P[on + so + __popc(dv & below)] = v;
+                if constexpr (sizeof(TV) == 4) {
+                  if (isfinite(v)) {
+                    const u32 kq = f32_key(__fadd_rn(v, 0.0f));
+                    kmin = min(kmin, kq);
+                    kmax = max(kmax, kq);
+                  }
+                } else {
+                  kmin = min(kmin, (u32)v + 1u);
+                  kmax = max(kmax, (u32)v + 1u);
+                }
+              }
+            }
+            on += __shfl_sync(0xffffffffu, sn + pn, 31);
           }
         }
-        // boundaries
-        for (u32 k = 0; k < cnt; ++k) {
-          const u32 ev = __shfl_sync(0xffffffffu, ev_l, k);
-          const u32 ex = __shfl_sync(0xffffffffu, ex_l, k);
-          const u32 so = __shfl_sync(0xffffffffu, sb, k);
-          if (!(ev | ex)) continue;
-          const u32 i = c0 + k;
-          const u32 w = i % W;
-          if ((ev >> lane) & 1u) {
-            const u64 p = ob + so + __popc(ev & below);
-            if (p < bounds_cap) bounds[p] = (uint16_t)(w * 32 + lane);
-            else atomicExch(&st->cap_flag, 1u);
-          }
-          if (ex && lane == 0) {
-            const u64 p = ob + so + __popc(ev);
-            if (p < bounds_cap) bounds[p] = (uint16_t)d.nx;
-            else atomicExch(&st->cap_flag, 1u);
-          }
-        }
-        on += __shfl_sync(0xffffffffu, sn + pn, 31);
-        ob += __shfl_sync(0xffffffffu, sb + pb, 31);
+        ob += nbr;
+        __syncwarp();
       }
     }
     // ---- per-row boundary counts
     for (u32 lr = threadIdx.x; lr < nrows; lr += blockDim.x) {
-      u32 c = 0;
-      for (u32 w = 0; w < W; ++w) {
-        const u32 i = lr * W + w;
-        c += __popc(e_word(Dw, i, w));
-        if (end_extra && w == W - 1) c += Dw[i] >> 31;
-      }
       const u64 r = r0 + lr;
-      if (r < counts_cap) counts[r] = (uint16_t)c;
+      if (r < counts_cap) counts[r] = (uint16_t)rowcnt[lr];
     }
     __syncthreads();
   }
@@ -335,11 +466,20 @@ void launch_threshold(const Launch& L, const Desc& d, const void* in, u32* T) {
   u64 blocks = (segs + warps_per_block - 1) / warps_per_block;
   const u64 cap = (u64)L.sms * 8;  // 8 blocks of 256 threads per SM in flight
   if (blocks > cap) blocks = cap;
-  if (d.dtype == ROIX_F32)
-    k_threshold<float><<<(unsigned)blocks, kThreads, 0, L.stream>>>(d, (const float*)in, T);
-  else
-    k_threshold<unsigned short><<<(unsigned)blocks, kThreads, 0, L.stream>>>(
-        d, (const unsigned short*)in, T);
+  const bool al16 = ((uintptr_t)in & 15) == 0;
+  if (d.dtype == ROIX_F32) {
+    if (al16 && (d.nx & 3) == 0)
+      k_threshold_vec<float><<<(unsigned)blocks, kThreads, 0, L.stream>>>(d, (const float*)in, T);
+    else
+      k_threshold<float><<<(unsigned)blocks, kThreads, 0, L.stream>>>(d, (const float*)in, T);
+  } else {
+    if (al16 && (d.nx & 7) == 0)
+      k_threshold_vec<unsigned short><<<(unsigned)blocks, kThreads, 0, L.stream>>>(
+          d, (const unsigned short*)in, T);
+    else
+      k_threshold<unsigned short><<<(unsigned)blocks, kThreads, 0, L.stream>>>(
+          d, (const unsigned short*)in, T);
+  }
 }
 
 void launch_dilate(const Launch& L, const Desc& d, const u32* T, u32* D, u64* popcount) {
@@ -354,8 +494,9 @@ void launch_front(const Launch& L, const Desc& d, const void* in, const u32* T, 
                   void* P, uint16_t* counts, u64 counts_cap, uint16_t* bounds, u64 bounds_cap,
                   State* st, LookBack<2> lb, u32 rows_per_tile, u64 tiles, u64* sizes_out) {
   if (tiles == 0) return;
-  const size_t smem = (size_t)rows_per_tile * d.W * 4 +
-                      (dilate ? (size_t)3 * (rows_per_tile + 2) * d.W * 4 : 0);
+  const size_t smem = (size_t)rows_per_tile * d.W * 4 + (size_t)rows_per_tile * 8 + 8 +
+                      (size_t)(kThreads / 32) * kListCap * 2 +
+                      (dilate ? (size_t)(rows_per_tile + 2) * d.W * 4 : 0);
   const void* fn = d.dtype == ROIX_F32 ? (const void*)k_front<float>
                                        : (const void*)k_front<unsigned short>;
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

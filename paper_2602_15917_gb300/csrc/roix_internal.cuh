@@ -99,6 +99,62 @@ __device__ void lookback(LookBack<NV> lb, u64 t, const u64 (&mine)[NV], u64 (&ex
   st_release(&lb.flags[t], 2u);
 }
 
+// Warp-parallel form (Merrill & Garland's window variant): all 32 lanes of one
+// warp call it; lane j inspects predecessor t-1-j, so a window of 32 flags is
+// read per L2 round trip. Lanes up to the nearest inclusive prefix must have
+// published; their aggregates and that prefix are summed by a warp reduction.
+// Returns the exclusive prefix in every lane. Bounded like lookback().
+template <int NV>
+__device__ void lookback_warp(LookBack<NV> lb, u64 t, const u64 (&mine)[NV], u64 (&excl)[NV],
+                              u32* status) {
+  const int lane = threadIdx.x & 31;
+  for (int i = 0; i < NV; ++i) excl[i] = 0;
+  if (t == 0) {
+    if (lane == 0) {
+      for (int i = 0; i < NV; ++i) st_relaxed(&lb.inc[i], mine[i]);
+      st_release(&lb.flags[0], 2u);
+    }
+    return;
+  }
+  if (lane == 0) {
+    for (int i = 0; i < NV; ++i) st_relaxed(&lb.agg[t * NV + i], mine[i]);
+    st_release(&lb.flags[t], 1u);
+  }
+  long long base = (long long)t - 1;
+  u32 spins = 0;
+  while (true) {
+    const long long j = base - lane;
+    const u32 f = j >= 0 ? ld_acquire(&lb.flags[j]) : 2u;
+    const u32 incl = __ballot_sync(0xffffffffu, f == 2u);
+    const u32 zero = __ballot_sync(0xffffffffu, f == 0u);
+    const int first = incl ? __ffs(incl) - 1 : 32;
+    const u32 need = first == 32 ? 0xffffffffu : (0xffffffffu >> (31 - first));
+    if (zero & need) {
+      if (++spins > kSpinLimit) {
+        if (lane == 0) set_status(status, ROIX_ETIMEOUT);
+        break;
+      }
+      __nanosleep(32);
+      continue;
+    }
+    u64 v[NV];
+    for (int i = 0; i < NV; ++i) {
+      v[i] = 0;
+      if (lane < first) v[i] = ld_relaxed(&lb.agg[(u64)j * NV + i]);
+      else if (lane == first && j >= 0) v[i] = ld_relaxed(&lb.inc[(u64)j * NV + i]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+      excl[i] += v[i];
+    }
+    if (first < 32) break;
+    base -= 32;
+  }
+  if (lane == 0) {
+    for (int i = 0; i < NV; ++i) st_relaxed(&lb.inc[t * NV + i], excl[i] + mine[i]);
+    st_release(&lb.flags[t], 2u);
+  }
+}
+
 // ------------------------------------------------------------------- scans
 template <typename T>
 __device__ __forceinline__ T warp_incl_scan(T v) {
@@ -139,6 +195,24 @@ __device__ T block_excl_scan(T v, T* scratch, T* total) {
   __syncthreads();
   return out;
 }
+
+// ------------------------------------------------------------ fast division
+// Division of 32-bit numerators by an invariant divisor with a multiply-high
+// and shifts (Granlund & Montgomery 1994, round-up method).
+struct FastDiv {
+  u32 d, m, s;
+  __host__ __device__ explicit FastDiv(u32 div = 1) : d(div ? div : 1), m(0), s(0) {
+    u32 l = 0;
+    while ((1ull << l) < d) ++l;
+    s = l;
+    m = l ? (u32)(((1ull << 32) * ((1ull << l) - d)) / d + 1) : 0u;
+  }
+  __device__ __forceinline__ u32 div(u32 n) const {
+    if (s == 0) return n;
+    const u32 t = __umulhi(m, n);
+    return (t + ((n - t) >> 1)) >> (s - 1);
+  }
+};
 
 // ------------------------------------------------------- ordered float keys
 // Monotone map of binary32 bit patterns to uint32 (for atomicMin/Max).
@@ -246,10 +320,8 @@ __device__ __forceinline__ roix_eb_info make_eb(const Desc& d, u32 vmin_key, u32
 // `out` for an outlier (code 0). Binary32 operations rounded to nearest, no
 // contraction: the decoder repeats the reconstruction bit for bit.
 __device__ __forceinline__ int quant_f32(float x, const roix_eb_info& e, bool& out) {
-  if (!isfinite(x)) {
-    out = true;
-    return 0;
-  }
+  // a non-finite x gives a non-finite y (inf * positive, NaN, or inf * 0 =
+  // NaN for the degenerate bound), so the range test below also rejects it
   float y = __fmul_rn(x, e.inv2eb);
   if (!(fabsf(y) < 1073741824.0f)) {
     out = true;
