@@ -186,17 +186,24 @@ def run_ours(args, rank, world, local_rank):
                for j, x in enumerate(xs))
     for c in ctxs:
         c.reserve(need)  # no workspace growth once the graph holds its pointers
-    main = torch.cuda.current_stream(dev)
+    main = torch.cuda.Stream(dev)  # graphs must be captured off the legacy default stream
+    torch.cuda.set_stream(main)
 
-    def step(inputs):
-        for s in streams:
-            s.wait_stream(main)
-        for i, x in enumerate(inputs):
-            k = i % nstreams
-            ctxs[k].compress(x, out=outs[i], cap=caps[i], size=sizes[i:i + 1],
-                             stream=streams[k], **cfg)
-        for s in streams:
-            main.wait_stream(s)
+    if args.path == "batch":
+        def step(inputs):
+            ctxs[0].compress_batch(inputs, outs=outs, caps=caps, sizes=sizes, stream=main, **cfg)
+        launches_per_step = 7 * ((len(xs) + 63) // 64)
+    else:
+        def step(inputs):
+            for s in streams:
+                s.wait_stream(main)
+            for i, x in enumerate(inputs):
+                k = i % nstreams
+                ctxs[k].compress(x, out=outs[i], cap=caps[i], size=sizes[i:i + 1],
+                                 stream=streams[k], **cfg)
+            for s in streams:
+                main.wait_stream(s)
+        launches_per_step = 7 * len(xs)
 
     # correctness of the measured configuration: one step, sizes vs a re-run
     step(xs)
@@ -214,7 +221,6 @@ def run_ours(args, rank, world, local_rank):
             print(f"# graph capture unavailable: {e}", file=sys.stderr)
             graph = None
     run = (lambda: graph.replay()) if graph is not None else (lambda: step(xs))
-    launches_per_step = 7 * len(xs)
     for _ in range(args.warmup):
         run()
     torch.cuda.synchronize()
@@ -276,19 +282,26 @@ def run_ours(args, rank, world, local_rank):
     e2e = {"value": in_bytes * world / e2e_s / 1e9, "unit": "GB/s",
            "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": sum(sz_list) + 8 * len(xs)}
 
-    # dominant kernel: per-stage CUDA events on the launching stream, one item
-    # at a time (a profiling pass after the timed region)
+    # dominant kernel: per-stage CUDA events on the launching stream between
+    # the kernels of one step (a profiling pass after the timed region)
     prof = ctxs[0]
     prof.profile(True)
     stage_ms = np.zeros(8)
-    for _ in range(3):
-        for i, x in enumerate(xs):
-            prof.compress(x, out=outs[i], cap=caps[i], size=sizes[i:i + 1], stream=main, **cfg)
+    reps = 3
+    for _ in range(reps):
+        if args.path == "batch":
+            step(xs)
             st = prof.profile_read(8)
             stage_ms[:len(st)] += st
+        else:
+            for i, x in enumerate(xs):
+                prof.compress(x, out=outs[i], cap=caps[i], size=sizes[i:i + 1], stream=main,
+                              **cfg)
+                st = prof.profile_read(8)
+                stage_ms[:len(st)] += st
     prof.profile(False)
     torch.cuda.synchronize()
-    stage_ms /= 3
+    stage_ms /= reps
     names = ["reset", "threshold", "front", "symbols", "codebook", "pack", "finalize"]
     dom = int(np.argmax(stage_ms[:7]))
     peak, peak_kind = load_peaks()
@@ -313,8 +326,9 @@ def run_ours(args, rank, world, local_rank):
             "config": {"workload": args.workload, "desc": wl["desc"], "items": len(xs),
                        "bytes_in_per_step": in_bytes, "bytes_out_per_step": out_bytes,
                        "compression_ratio": round(in_bytes / max(out_bytes, 1), 3),
-                       "path": "plain calls on %d streams%s" % (
-                           nstreams, " under one CUDA graph" if graph is not None else ""),
+                       "path": ("roix_compress_batch: 7 launches per 64 items" if
+                                args.path == "batch" else "plain calls on %d streams" % nstreams)
+                               + (", one CUDA graph per step" if graph is not None else ""),
                        "l2": "inputs larger than L2 (129 MB)" if in_bytes > 129e6
                        else "inputs smaller than L2: not flushed",
                        "parallelism": f"replicas x{world}"},
@@ -392,6 +406,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="projections64", choices=sorted(WORKLOADS))
     ap.add_argument("--streams", type=int, default=8)
+    ap.add_argument("--path", default="batch", choices=["batch", "plain"])
     ap.add_argument("--graph", type=int, default=1)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-budget", type=float, default=10.0)

@@ -206,6 +206,26 @@ roix_status roix_extract_roi_static(const void* in, roix_dtype dtype, roix_dims 
 roix_status roix_profile(roix_ctx* ctx, int on);
 int roix_profile_read(roix_ctx* ctx, float* ms, int max);
 
+/* One volume or image of a batch (device pointers, caller-owned). */
+typedef struct {
+  const void* in;      /* input values (dtype of the batch), nx*ny*nz of them */
+  roix_dims dims;
+  void* out;           /* container buffer, 16-byte aligned */
+  uint64_t cap;        /* its size in bytes */
+  uint64_t* size_dev;  /* container size (uint64, device), as for roix_compress */
+} roix_item;
+
+/* Batched fused path (no paper counterpart; a throughput form of
+ * roix_compress): n independent items sharing dtype and settings are
+ * compressed together, 64 items per group of 7 kernel launches whose work
+ * tickets run over all items of the group; each item's container is the one
+ * roix_compress would write for it alone. Enqueued on `stream`, capturable in
+ * a CUDA graph once the workspace is reserved (roix_reserve with
+ * roix_workspace_size of the largest group). */
+roix_status roix_compress_batch(roix_ctx* ctx, uint32_t n, const roix_item* items,
+                                roix_dtype dtype, const roix_roi* roi, const roix_eb* eb,
+                                const roix_params* params, void* stream);
+
 /* The fused path: the same bytes as the four stages, in fewer passes. */
 roix_status roix_compress(roix_ctx* ctx, const void* in, roix_dtype dtype, roix_dims dims,
                           const roix_roi* roi, const roix_eb* eb, const roix_params* params,

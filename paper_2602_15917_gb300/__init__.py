@@ -53,6 +53,11 @@ class Params(C.Structure):
     _fields_ = [("radius", C.c_uint32), ("chunk", C.c_uint32), ("fill", C.c_double)]
 
 
+class Item(C.Structure):
+    _fields_ = [("in_", C.c_void_p), ("dims", Dims), ("out", C.c_void_p), ("cap", C.c_uint64),
+                ("size_dev", C.c_void_p)]
+
+
 class EbInfo(C.Structure):
     _fields_ = [("eb_abs", C.c_double), ("vmin", C.c_double), ("vmax", C.c_double),
                 ("two_eb", C.c_float), ("inv2eb", C.c_float), ("bound", C.c_float),
@@ -93,6 +98,7 @@ def lib():
                 "roix_profile": (st, [P, C.c_int]),
                 "roix_profile_read": (C.c_int, [P, C.POINTER(C.c_float), C.c_int]),
                 "roix_extract_roi_static": (st, [P, i32, D, R, P, P, P]),
+                "roix_compress_batch": (st, [P, C.c_uint32, C.POINTER(Item), i32, R, E, PR, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -108,7 +114,7 @@ def symbols():
             "roix_sync", "roix_last_error", "roix_status_string", "roix_mask_words",
             "roix_compress_bound", "roix_extract_roi", "roix_compact", "roix_quantize",
             "roix_encode", "roix_decode", "roix_compress", "roix_profile",
-            "roix_profile_read", "roix_extract_roi_static"]
+            "roix_profile_read", "roix_extract_roi_static", "roix_compress_batch"]
 
 
 def _dtype_code(t: torch.Tensor) -> int:
@@ -216,6 +222,30 @@ class Roix:
             C.byref(eb_of(**cfg)), C.byref(params_of(**cfg)), out.data_ptr(), int(cap),
             size.data_ptr(), _stream(stream)))
         return out, size
+
+    def compress_batch(self, xs, outs=None, caps=None, sizes: torch.Tensor | None = None,
+                       stream=None, **cfg):
+        """Enqueues the batched compression of the tensors xs (same dtype and
+        settings); returns (outs, sizes) with sizes a uint64 device tensor."""
+        n = len(xs)
+        if n == 0:
+            return [], torch.zeros(0, dtype=torch.uint64)
+        dev = xs[0].device
+        if outs is None:
+            caps = [x.numel() * x.element_size() + 65536 for x in xs] if caps is None else caps
+            outs = [torch.empty(c, dtype=torch.uint8, device=dev) for c in caps]
+        caps = [o.numel() for o in outs] if caps is None else caps
+        if sizes is None:
+            sizes = torch.zeros(n, dtype=torch.uint64, device=dev)
+        arr = (Item * n)()
+        for i, x in enumerate(xs):
+            assert x.is_cuda and x.is_contiguous() and x.dtype == xs[0].dtype
+            arr[i] = Item(x.data_ptr(), dims_of(x.shape), outs[i].data_ptr(), int(caps[i]),
+                          sizes.data_ptr() + 8 * i)
+        self._check(self.L.roix_compress_batch(
+            self.ctx, n, arr, _dtype_code(xs[0]), C.byref(roi_of(**cfg)), C.byref(eb_of(**cfg)),
+            C.byref(params_of(**cfg)), _stream(stream)))
+        return outs, sizes
 
     def compress_bytes(self, x: torch.Tensor, **cfg) -> torch.Tensor:
         """compress + sync; returns the container as a uint8 device tensor. An

@@ -164,13 +164,24 @@ __device__ __forceinline__ u32 spread16(u32 v) {
 // (records) are marked in a shared bitmap, counted, placed by the look-back
 // and written in order. The histogram lives in shared memory per block and is
 // flushed once at the end.
+// Tiles of every item, in order: prefix of ceil(n_i / kQuantTile) over the
+// items (n_i found by the compaction), computed by each block at start.
+__device__ __forceinline__ void tile_prefix(const Batch& B, u64* pre, u64 per, u64 group) {
+  if (threadIdx.x == 0) {
+    u64 acc = 0;
+    for (u32 i = 0; i < B.n; ++i) {
+      pre[i] = acc;
+      const Item& I = B.it[i];
+      const u64 n = umin(I.sizes[0], I.N);
+      acc += ((n + per - 1) / per + group - 1) / group;
+    }
+    pre[B.n] = acc;
+  }
+  __syncthreads();
+}
+
 template <typename TV, bool FROM_Q>
-__global__ void __launch_bounds__(kThreads) k_symbols(Desc d, Src<TV, FROM_Q> src, u64 n_cap,
-                                                      const u64* n_dev, State* st,
-                                                      uint16_t* __restrict__ sym,
-                                                      u64* __restrict__ rk, u32* __restrict__ rv,
-                                                      u64 rec_cap, unsigned long long* hist,
-                                                      LookBack<1> lb, int compute_eb) {
+__global__ void __launch_bounds__(kThreads) k_symbols(const __grid_constant__ Batch B) {
   using R = typename Src<TV, FROM_Q>::R;
   constexpr u32 kSpan = kQuantTile / (kThreads / 32);  // values per warp and tile
   constexpr int kSteps = kSpan / 64;
@@ -179,23 +190,46 @@ __global__ void __launch_bounds__(kThreads) k_symbols(Desc d, Src<TV, FROM_Q> sr
   __shared__ u32 bitmap[kQuantTile / 32];
   __shared__ u32 scratch[40];
   __shared__ u64 s_tile, s_base;
+  __shared__ u64 pre[kMaxBatch + 1];
   static_assert(kQuantTile / 32 == kThreads, "one bitmap word per thread");
   static_assert(kSteps % kBatch == 0, "whole batches");
-  const u64 n = n_dev ? min(*n_dev, n_cap) : n_cap;
-  if (compute_eb) {
-    src.e = make_eb(d, st->vmin_key, st->vmax_key);
-    if (blockIdx.x == 0 && threadIdx.x == 0) st->eb = src.e;
-  }
-  const u32 R_ = d.R;
-  for (u32 i = threadIdx.x; i < d.S; i += blockDim.x) h[i] = 0;
+  const u32 R_ = B.c.R, S = B.c.S;
+  for (u32 i = threadIdx.x; i < S; i += blockDim.x) h[i] = 0;
+  tile_prefix(B, pre, kQuantTile, 1);
+  const u64 total = pre[B.n];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const u64 ntiles = (n + kQuantTile - 1) / kQuantTile;
-  __syncthreads();
+  u32 cur = 0xffffffffu;
+  Src<TV, FROM_Q> src{};
+  u64 n = 0;
   while (true) {
-    if (threadIdx.x == 0) s_tile = atomicAdd(&st->ctr_quant, 1u);
+    if (threadIdx.x == 0) s_tile = atomicAdd(&B.ctr[1], 1u);
     __syncthreads();
-    const u64 t = s_tile;
-    if (t >= ntiles) break;
+    const u64 gt = s_tile;
+    if (gt >= total) break;
+    const u32 item = find_item(pre, B.n, gt);
+    const Item& I = B.it[item];
+    if (item != cur) {  // histogram of the previous item out, the next one's settings in
+      if (cur != 0xffffffffu) {
+        unsigned long long* hg = B.it[cur].hist;
+        for (u32 i = threadIdx.x; i < S; i += blockDim.x)
+          if (h[i]) {
+            atomicAdd(hg + i, (unsigned long long)h[i]);
+            h[i] = 0;
+          }
+      }
+      cur = item;
+      const Desc d = desc_of(B, I);
+      src.P = (const TV*)I.P;
+      src.q = I.q;
+      src.obits = I.obits;
+      src.dark = d.dark;
+      if constexpr (!FROM_Q) src.e = make_eb(d, I.st->vmin_key, I.st->vmax_key);
+      n = umin(I.sizes[0], I.N);
+      __syncthreads();
+    }
+    const u64 t = gt - pre[item];
+    const u64 ntiles = (n + kQuantTile - 1) / kQuantTile;
+    uint16_t* __restrict__ sym = I.sym;
     const u64 base = t * kQuantTile;
     const u64 span = base + (u64)warp * kSpan;
     bitmap[threadIdx.x] = 0u;
@@ -252,14 +286,14 @@ __global__ void __launch_bounds__(kThreads) k_symbols(Desc d, Src<TV, FROM_Q> sr
     __syncthreads();
     // records of this tile, in order
     const u32 word = bitmap[threadIdx.x];
-    u32 total;
-    const u32 off = block_excl_scan<u32>(__popc(word), scratch, &total);
+    u32 tot;
+    const u32 off = block_excl_scan<u32>(__popc(word), scratch, &tot);
     if (warp == 0) {
-      u64 mine[1] = {total}, excl[1];
-      lookback_warp<1>(lb, t, mine, excl, &st->status);
+      u64 mine[1] = {tot}, excl[1];
+      lookback_warp<1>(I.lbq, t, mine, excl, B.status);
       if (lane == 0) {
         s_base = excl[0];
-        if (t == ntiles - 1) st->nout = excl[0] + total;
+        if (t == ntiles - 1) I.st->nout = excl[0] + tot;
       }
     }
     __syncthreads();
@@ -272,11 +306,11 @@ __global__ void __launch_bounds__(kThreads) k_symbols(Desc d, Src<TV, FROM_Q> sr
         const u64 k = base + (u64)threadIdx.x * 32 + j;
         bool out;
         const int c = src.code(k, out);
-        if (idx < rec_cap) {
-          rk[idx] = k | (out ? (1ull << 63) : 0ull);
-          rv[idx] = out ? src.raw_bits(k) : (u32)c;
+        if (idx < I.rec_cap) {
+          I.rk[idx] = k | (out ? (1ull << 63) : 0ull);
+          I.rv[idx] = out ? src.raw_bits(k) : (u32)c;
         } else {
-          atomicExch(&st->cap_flag, 1u);
+          atomicExch(&I.st->cap_flag, 1u);
         }
         ++idx;
       }
@@ -284,8 +318,11 @@ __global__ void __launch_bounds__(kThreads) k_symbols(Desc d, Src<TV, FROM_Q> sr
     __syncthreads();
   }
   __syncthreads();
-  for (u32 i = threadIdx.x; i < d.S; i += blockDim.x)
-    if (h[i]) atomicAdd(hist + i, (unsigned long long)h[i]);
+  if (cur != 0xffffffffu) {
+    unsigned long long* hg = B.it[cur].hist;
+    for (u32 i = threadIdx.x; i < S; i += blockDim.x)
+      if (h[i]) atomicAdd(hg + i, (unsigned long long)h[i]);
+  }
 }
 
 // ------------------------------------------------------------- codebook
@@ -330,11 +367,15 @@ size_t codebook_smem(u32 S) {
          + (size_t)S;         // lengths
 }
 
-__global__ void __launch_bounds__(kCbThreads) k_codebook(Desc d, const unsigned long long* hist,
-                                                         uint8_t* lens_ws, u32* codes_ws,
-                                                         uint8_t* out, u64 cap, State* st) {
+__global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__ Batch B) {
   extern __shared__ __align__(16) unsigned char cb_smem[];
-  const u32 S = d.S;
+  const Item& I = B.it[blockIdx.x];
+  const unsigned long long* hist = I.hist;
+  uint8_t* lens_ws = I.lens;
+  u32* codes_ws = I.codes;
+  uint8_t* out = I.out;
+  const u64 cap = I.cap;
+  const u32 S = B.c.S;
   u64* key = (u64*)cb_smem;                       // [next_pow2(S)] (count << 16 | symbol)
   u64* wint = key + next_pow2(S);                 // [S] internal node weights
   int32_t* par = (int32_t*)(wint + S);            // [2S]
@@ -367,31 +408,45 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(Desc d, const unsigned 
       bl[1] = 1;
     }
   } else if (m >= 2) {
-    // two-queue construction: leaves 0..m-1 in sorted order, internal m..2m-2
+    // two-queue construction: leaves 0..m-1 in sorted order, internal m..2m-2.
+    // Both queue fronts live in registers; an empty queue reads as the
+    // sentinel ~0 (weights are below 2^48), so "leaf if wl <= wi" keeps the
+    // leaf-first tie rule. The next front is loaded right after a pop.
     if (tid == 0) {
+      constexpr u64 kNone = ~0ull;
       u32 lf = 0, in = 0, created = 0;
-      u64 wl = key[0] >> 16;
+      u64 wl = key[0] >> 16, wi = kNone;
       for (u32 t = 0; t + 1 < m; ++t) {
-        u64 w2 = 0;
-        int32_t pick[2];
-        for (int a = 0; a < 2; ++a) {
-          const bool leaf_ok = lf < m, int_ok = in < created;
-          const u64 wiv = int_ok ? wint[in] : 0ull;
-          if (leaf_ok && (!int_ok || wl <= wiv)) {
-            pick[a] = (int32_t)lf;
-            w2 += wl;
-            ++lf;
-            wl = lf < m ? (key[lf] >> 16) : 0ull;
-          } else {
-            pick[a] = (int32_t)(m + in);
-            w2 += wiv;
-            ++in;
-          }
+        int32_t pa, pb;
+        u64 wa, wb;
+        if (wl <= wi) {
+          pa = (int32_t)lf;
+          wa = wl;
+          ++lf;
+          wl = lf < m ? (key[lf] >> 16) : kNone;
+        } else {
+          pa = (int32_t)(m + in);
+          wa = wi;
+          ++in;
+          wi = in < created ? wint[in] : kNone;
         }
+        if (wl <= wi) {
+          pb = (int32_t)lf;
+          wb = wl;
+          ++lf;
+          wl = lf < m ? (key[lf] >> 16) : kNone;
+        } else {
+          pb = (int32_t)(m + in);
+          wb = wi;
+          ++in;
+          wi = in < created ? wint[in] : kNone;
+        }
+        const u64 w2 = wa + wb;
         wint[created] = w2;
-        par[pick[0]] = (int32_t)(m + created);
-        par[pick[1]] = (int32_t)(m + created);
+        par[pa] = (int32_t)(m + created);
+        par[pb] = (int32_t)(m + created);
         ++created;
+        if (in == created - 1) wi = w2;  // the queue was empty: the new node is its front
       }
       par[2 * m - 2] = -1;
     }
@@ -490,7 +545,6 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(Desc d, const unsigned 
 // every thread's codes through a 64-bit register, stores the words that lie
 // wholly inside its bit range and OR-s only its first and last (shared)
 // words into the shared buffer, which is copied out with coalesced stores.
-constexpr u32 kPackRange = 8;
 
 template <int EPT>
 __device__ __forceinline__ void load_syms(const uint16_t* __restrict__ sym, u64 k0, u64 n,
@@ -515,11 +569,7 @@ __device__ __forceinline__ void load_syms(const uint16_t* __restrict__ sym, u64 
 }
 
 template <int EPT>  // symbols per thread = C / 256
-__global__ void __launch_bounds__(kThreads, 4) k_pack(Desc d, const uint16_t* __restrict__ sym,
-                                                      const u64* n_dev, const u64* nb_dev,
-                                                      const uint8_t* lens_ws,
-                                                      const u32* codes_ws, State* st,
-                                                      uint8_t* out, u64 cap, LookBack<1> lb) {
+__global__ void __launch_bounds__(kThreads, 4) k_pack(const __grid_constant__ Batch B) {
   extern __shared__ u32 wbuf[];  // C * 24 / 32 + 2 words
   constexpr u32 kPackWordsMax = EPT * kThreads * kLMax / 32 + 2;
   __shared__ uint8_t slen[kMaxSym];
@@ -528,22 +578,40 @@ __global__ void __launch_bounds__(kThreads, 4) k_pack(Desc d, const uint16_t* __
   __shared__ u32 cwords[kPackRange];
   __shared__ u32 scratch[40];
   __shared__ u64 s_tile, s_base;
-  const u64 n = *n_dev;
-  const u32 C = d.C;
-  const u64 nchunks = (n + C - 1) / C;
-  const u64 nranges = (nchunks + kPackRange - 1) / kPackRange;
-  const Layout Lo = make_layout(d.S, d.rows, *nb_dev, st->nout, nchunks, 0);
+  __shared__ u64 pre[kMaxBatch + 1];
+  const u32 C = B.c.C, S = B.c.S;
+  tile_prefix(B, pre, C, kPackRange);
+  const u64 total = pre[B.n];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (u32 i = threadIdx.x; i < d.S; i += blockDim.x) {
-    slen[i] = lens_ws[i];
-    scode[i] = codes_ws[i];
-  }
-  __syncthreads();
+  u32 cur = 0xffffffffu;
+  u64 n = 0, nchunks = 0, nranges = 0;
+  Layout Lo{};
+  const uint16_t* __restrict__ sym = nullptr;
+  uint8_t* out = nullptr;
+  u64 cap = 0;
   while (true) {
-    if (threadIdx.x == 0) s_tile = atomicAdd(&st->ctr_pack, 1u);
+    if (threadIdx.x == 0) s_tile = atomicAdd(&B.ctr[2], 1u);
     __syncthreads();
-    const u64 r = s_tile;
-    if (r >= nranges) break;
+    const u64 gr = s_tile;
+    if (gr >= total) break;
+    const u32 item = find_item(pre, B.n, gr);
+    const Item& I = B.it[item];
+    if (item != cur) {  // the item's code table into shared memory
+      cur = item;
+      for (u32 i = threadIdx.x; i < S; i += blockDim.x) {
+        slen[i] = I.lens[i];
+        scode[i] = I.codes[i];
+      }
+      n = umin(I.sizes[0], I.N);
+      nchunks = (n + C - 1) / C;
+      nranges = (nchunks + kPackRange - 1) / kPackRange;
+      Lo = make_layout(S, I.rows, I.sizes[1], I.st->nout, nchunks, 0);
+      sym = I.sym;
+      out = I.out;
+      cap = I.cap;
+      __syncthreads();
+    }
+    const u64 r = gr - pre[item];
     const u64 c_lo = r * kPackRange;
     const u32 nc = (u32)umin(kPackRange, nchunks - c_lo);
     // pass 1: bits per thread and chunk
@@ -563,10 +631,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_pack(Desc d, const uint16_t* __
       u32 rw = lane < nc ? cwords[lane] : 0u;
       rw = warp_sum(rw);
       u64 mine[1] = {rw}, excl[1];
-      lookback_warp<1>(lb, r, mine, excl, &st->status);
+      lookback_warp<1>(I.lbp, r, mine, excl, B.status);
       if (lane == 0) {
         s_base = excl[0];
-        if (r == nranges - 1) st->nwords = excl[0] + rw;
+        if (r == nranges - 1) I.st->nwords = excl[0] + rw;
       }
     }
     __syncthreads();
@@ -627,15 +695,18 @@ __device__ __forceinline__ void put_bytes(uint8_t* h, u32 off, const void* src, 
   for (u32 i = 0; i < bytes; ++i) h[off + i] = s[i];
 }
 
-__global__ void __launch_bounds__(kThreads) k_finalize(Desc d, State* st, const u64* n_dev,
-                                                       const u64* nb_dev,
-                                                       const roix_eb_info* info,
-                                                       const u64* __restrict__ rk,
-                                                       const u32* __restrict__ rv, u64 rec_cap,
-                                                       const uint16_t* counts_src,
-                                                       const uint16_t* bounds_src, uint8_t* out,
-                                                       u64 cap, u64* size_dev) {
-  const u64 n = *n_dev, nb = *nb_dev, nout = st->nout, nwords = st->nwords;
+__global__ void __launch_bounds__(kThreads) k_finalize(const __grid_constant__ Batch B) {
+  const Item& I = B.it[blockIdx.y];
+  const Desc d = desc_of(B, I);
+  State* st = I.st;
+  uint8_t* out = I.out;
+  const u64 cap = I.cap;
+  const u64 rec_cap = I.rec_cap;
+  const u64* __restrict__ rk = I.rk;
+  const u32* __restrict__ rv = I.rv;
+  const uint16_t* counts_src = I.counts_src;
+  const uint16_t* bounds_src = I.bounds_src;
+  const u64 n = umin(I.sizes[0], I.N), nb = I.sizes[1], nout = st->nout, nwords = st->nwords;
   const u64 nchunks = (n + d.C - 1) / d.C;
   const Layout Lo = make_layout(d.S, d.rows, nb, nout, nchunks, nwords);
   const u64 gtid = (u64)blockIdx.x * blockDim.x + threadIdx.x;
@@ -643,7 +714,7 @@ __global__ void __launch_bounds__(kThreads) k_finalize(Desc d, State* st, const 
   if (gtid == 0) {
     uint8_t h[kHeaderBytes];
     for (u32 i = 0; i < kHeaderBytes; ++i) h[i] = 0;
-    const roix_eb_info e = *info;
+    const roix_eb_info e = I.info_in ? *I.info_in : make_eb(d, st->vmin_key, st->vmax_key);
     h[0] = 'R'; h[1] = 'O'; h[2] = 'I'; h[3] = 'X';
     const uint16_t ver = kVersion;
     put_bytes(h, 4, &ver, 2);
@@ -688,9 +759,9 @@ __global__ void __launch_bounds__(kThreads) k_finalize(Desc d, State* st, const 
     if (cap >= kHeaderBytes)
       for (u32 i = 0; i < kHeaderBytes; i += 4)
         *reinterpret_cast<u32*>(out + i) = *reinterpret_cast<const u32*>(h + i);
-    *size_dev = Lo.total;
+    *I.size_dev = Lo.total;
     st->total = Lo.total;
-    if (Lo.total > cap || st->cap_flag) set_status(&st->status, ROIX_ECAPACITY);
+    if (Lo.total > cap || st->cap_flag) set_status(B.status, ROIX_ECAPACITY);
   }
   // zero the alignment gaps between sections
   const u64 gaps[7][2] = {{Lo.off_lens + d.S, Lo.off_counts},
@@ -726,12 +797,12 @@ __global__ void __launch_bounds__(kThreads) k_finalize(Desc d, State* st, const 
 
 // Per-call reset: the state (all but its first word, the status that
 // persists until it is read) and a region of look-back flags and counters.
-__global__ void k_init(State* st, u64* zero, u64 words) {
+__global__ void k_init(State* st, u32 nstates, u64* zero, u64 words) {
   const u64 gtid = (u64)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gtid == 0) {
-    u32* s = reinterpret_cast<u32*>(st);
-    for (u32 i = 1; i < sizeof(State) / 4; ++i) s[i] = 0;
-    st->vmin_key = 0xffffffffu;
+  if (gtid < nstates) {
+    u32* s = reinterpret_cast<u32*>(st + gtid);
+    for (u32 i = gtid == 0 ? 1 : 0; i < sizeof(State) / 4; ++i) s[i] = 0;
+    st[gtid].vmin_key = 0xffffffffu;
   }
   for (u64 i = gtid; i < words; i += (u64)gridDim.x * blockDim.x) zero[i] = 0;
 }
@@ -745,12 +816,12 @@ int grid_for(const void* fn, int threads, size_t smem, int sms) {
 
 }  // namespace
 
-void launch_init(const Launch& L, State* st, void* zero, size_t zero_bytes) {
+void launch_init(const Launch& L, State* st, u32 nstates, void* zero, size_t zero_bytes) {
   const u64 words = zero ? zero_bytes / 8 : 0;
-  u64 blocks = (words + kThreads - 1) / kThreads;
+  u64 blocks = (umax(words, nstates) + kThreads - 1) / kThreads;
   if (blocks < 1) blocks = 1;
-  if (blocks > (u64)L.sms * 4) blocks = (u64)L.sms * 4;
-  k_init<<<(unsigned)blocks, kThreads, 0, L.stream>>>(st, (u64*)zero, words);
+  if (blocks > (u64)L.sms * 4) blocks = umax((u64)L.sms * 4, (nstates + kThreads - 1) / kThreads);
+  k_init<<<(unsigned)blocks, kThreads, 0, L.stream>>>(st, nstates, (u64*)zero, words);
 }
 
 void launch_quantize_stage(const Launch& L, const Desc& d, const void* P, u64 n_cap,
@@ -769,62 +840,41 @@ void launch_quantize_stage(const Launch& L, const Desc& d, const void* P, u64 n_
   }
 }
 
-void launch_symbols(const Launch& L, const Desc& d, const void* P, const int32_t* q,
-                    const u32* obits, u64 n_cap, const u64* n_dev, const roix_eb_info* info_in,
-                    State* st, uint16_t* sym, u64* rk, u32* rv, u64 rec_cap,
-                    unsigned long long* hist, LookBack<1> lb) {
-  const u64 tiles_cap = (n_cap + kQuantTile - 1) / kQuantTile;
+void launch_symbols(const Launch& L, const Batch& B, u64 tiles_cap) {
   if (tiles_cap == 0) return;
-  const bool from_q = q != nullptr;
-  const int compute_eb = info_in == nullptr;
-  auto run = [&](auto kernel, auto src) {
+  const bool from_q = B.it[0].q != nullptr;
+  auto run = [&](auto kernel) {
     u64 grid = (u64)grid_for((const void*)kernel, kThreads, 0, L.sms);
     if (grid > tiles_cap) grid = tiles_cap;
-    kernel<<<(unsigned)grid, kThreads, 0, L.stream>>>(d, src, n_cap, n_dev, st, sym, rk, rv,
-                                                       rec_cap, hist, lb, compute_eb);
+    kernel<<<(unsigned)grid, kThreads, 0, L.stream>>>(B);
   };
-  if (d.dtype == ROIX_F32) {
-    if (from_q) {
-      Src<float, true> s{(const float*)P, q, obits, {}, d.dark};
-      run(k_symbols<float, true>, s);
-    } else {
-      Src<float, false> s{(const float*)P, nullptr, nullptr, {}, d.dark};
-      run(k_symbols<float, false>, s);
-    }
+  if (B.c.dtype == ROIX_F32) {
+    if (from_q) run(k_symbols<float, true>);
+    else run(k_symbols<float, false>);
   } else {
-    if (from_q) {
-      Src<unsigned short, true> s{(const unsigned short*)P, q, obits, {}, d.dark};
-      run(k_symbols<unsigned short, true>, s);
-    } else {
-      Src<unsigned short, false> s{(const unsigned short*)P, nullptr, nullptr, {}, d.dark};
-      run(k_symbols<unsigned short, false>, s);
-    }
+    if (from_q) run(k_symbols<unsigned short, true>);
+    else run(k_symbols<unsigned short, false>);
   }
 }
 
-void launch_codebook(const Launch& L, const Desc& d, const unsigned long long* hist,
-                     uint8_t* lens_ws, u32* codes_ws, uint8_t* out, u64 cap, State* st) {
-  const size_t smem = codebook_smem(d.S);
+void launch_codebook(const Launch& L, const Batch& B) {
+  const size_t smem = codebook_smem(B.c.S);
   cudaFuncSetAttribute((const void*)k_codebook, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)smem);
-  k_codebook<<<1, kCbThreads, smem, L.stream>>>(d, hist, lens_ws, codes_ws, out, cap, st);
+  k_codebook<<<B.n, kCbThreads, smem, L.stream>>>(B);
 }
 
-void launch_pack(const Launch& L, const Desc& d, const uint16_t* sym, const u64* n_dev,
-                 const u64* nb_dev, const uint8_t* lens_ws, const u32* codes_ws, State* st,
-                 uint8_t* out, u64 cap, LookBack<1> lb, u64 chunks_cap) {
-  if (chunks_cap == 0) return;
-  const size_t smem = ((size_t)d.C * kLMax / 32 + 2) * 4;
-  chunks_cap = (chunks_cap + kPackRange - 1) / kPackRange;  // tickets are ranges
+void launch_pack(const Launch& L, const Batch& B, u64 ranges_cap) {
+  if (ranges_cap == 0) return;
+  const size_t smem = ((size_t)B.c.C * kLMax / 32 + 2) * 4;
   auto run = [&](auto kernel) {
     cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     u64 grid = (u64)grid_for((const void*)kernel, kThreads, smem, L.sms);
-    if (grid > chunks_cap) grid = chunks_cap;
-    kernel<<<(unsigned)grid, kThreads, smem, L.stream>>>(d, sym, n_dev, nb_dev, lens_ws,
-                                                         codes_ws, st, out, cap, lb);
+    if (grid > ranges_cap) grid = ranges_cap;
+    kernel<<<(unsigned)grid, kThreads, smem, L.stream>>>(B);
   };
-  switch (d.C / kThreads) {
+  switch (B.c.C / kThreads) {
     case 1: run(k_pack<1>); break;
     case 2: run(k_pack<2>); break;
     case 4: run(k_pack<4>); break;
@@ -836,13 +886,10 @@ void launch_pack(const Launch& L, const Desc& d, const uint16_t* sym, const u64*
   }
 }
 
-void launch_finalize(const Launch& L, const Desc& d, State* st, const u64* n_dev,
-                     const u64* nb_dev, const roix_eb_info* info, const u64* rk, const u32* rv,
-                     u64 rec_cap, const uint16_t* counts_src, const uint16_t* bounds_src,
-                     uint8_t* out, u64 cap, u64* size_dev) {
-  const unsigned blocks = (unsigned)L.sms * 2;
-  k_finalize<<<blocks, kThreads, 0, L.stream>>>(d, st, n_dev, nb_dev, info, rk, rv, rec_cap,
-                                                counts_src, bounds_src, out, cap, size_dev);
+void launch_finalize(const Launch& L, const Batch& B) {
+  const unsigned bx = B.n > 8 ? 4u : (unsigned)L.sms;
+  dim3 grid(bx, B.n);
+  k_finalize<<<grid, kThreads, 0, L.stream>>>(B);
 }
 
 }  // namespace roix

@@ -33,97 +33,99 @@ __device__ __forceinline__ u32 last_mask(const Desc& d, u64 w) {
 // warp in flight per batch of 8), then one ballot per 32 voxels forms each
 // word. Used for rows that are not 16-byte aligned.
 template <typename TV>
-__global__ void __launch_bounds__(kThreads) k_threshold(Desc d, const TV* __restrict__ in,
-                                                        u32* __restrict__ T) {
-  const int lane = threadIdx.x & 31;
-  const u64 warp = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
-  const u64 spr = (d.nx + 1023) >> 10;  // segments per row
-  const u64 nseg = d.rows * spr;
+__device__ __forceinline__ void thr_segment(const Desc& d, const TV* __restrict__ in,
+                                            u32* __restrict__ T, u64 r, u32 x0, int lane) {
   const u32 nx = (u32)d.nx;
-  for (u64 s = warp; s < nseg; s += nwarps) {
-    const u64 r = s / spr;
-    const u32 x0 = (u32)(s - r * spr) << 10;
-    const u32 nw = min(32u, (nx - x0 + 31) >> 5);
-    const TV* row = in + r * d.nx;
-    u32 mine = 0;
-    for (u32 i = 0; i < nw; i += 8) {
-      TV v[8];
+  const u32 nw = min(32u, (nx - x0 + 31) >> 5);
+  const TV* row = in + r * d.nx;
+  u32 mine = 0;
+  for (u32 i = 0; i < nw; i += 8) {
+    TV v[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const u32 x = x0 + (i + j) * 32 + lane;
-        v[j] = x < nx ? __ldg(row + x) : TV(0);
-      }
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const u32 x = x0 + (i + j) * 32 + lane;
-        bool p;
-        if constexpr (sizeof(TV) == 4) p = pass_f32(v[j], d);
-        else p = pass_u16(v[j], d);
-        const u32 b = __ballot_sync(0xffffffffu, p && x < nx);
-        if (lane == (int)(i + j)) mine = b;
-      }
+    for (int j = 0; j < 8; ++j) {
+      const u32 x = x0 + (i + j) * 32 + lane;
+      v[j] = x < nx ? __ldg(row + x) : TV(0);
     }
-    if ((u32)lane < nw) T[r * d.W + (x0 >> 5) + lane] = mine;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const u32 x = x0 + (i + j) * 32 + lane;
+      bool p;
+      if constexpr (sizeof(TV) == 4) p = pass_f32(v[j], d);
+      else p = pass_u16(v[j], d);
+      const u32 bl = __ballot_sync(0xffffffffu, p && x < nx);
+      if (lane == (int)(i + j)) mine = bl;
+    }
   }
+  if ((u32)lane < nw) T[r * d.W + (x0 >> 5) + lane] = mine;
 }
 
 // Vector form for 16-byte aligned rows (float32: nx % 4 == 0, uint16: nx % 8
 // == 0). A warp reads a 1024-voxel segment with 8 (float4) or 4 (uint4)
-// coalesced 512-byte loads per lane group, all in flight before use. Each lane
-// turns its 4 or 8 voxels into a nibble or byte; XOR-shuffles OR the 8 nibbles
-// (4 bytes) of a mask word together, and lane w picks word w.
+// coalesced 512-byte loads, all in flight before use. Each lane turns its 4
+// or 8 voxels into a nibble or byte; XOR-shuffles OR the nibbles (bytes) of a
+// mask word together, and lane w picks word w.
 template <typename TV>
-__global__ void __launch_bounds__(kThreads) k_threshold_vec(Desc d, const TV* __restrict__ in,
-                                                            u32* __restrict__ T) {
+__device__ __forceinline__ void thr_segment_vec(const Desc& d, const TV* __restrict__ in,
+                                                u32* __restrict__ T, u64 r, u32 x0, int lane) {
   constexpr int kPer = sizeof(TV) == 4 ? 4 : 8;  // voxels per lane and load
   constexpr int kLoads = 1024 / (32 * kPer);      // loads per segment
   constexpr int kLanesPerWord = 32 / kPer;        // lanes contributing to one word
   constexpr int kWordsPerLoad = 32 / kLanesPerWord;
+  const u32 nx = (u32)d.nx;
+  const u32 nw = min(32u, (nx - x0 + 31) >> 5);
+  const uint4* row = reinterpret_cast<const uint4*>(in + r * d.nx);
+  uint4 v[kLoads];
+#pragma unroll
+  for (int i = 0; i < kLoads; ++i) {
+    const u32 x = x0 + (u32)i * (32 * kPer) + (u32)lane * kPer;
+    v[i] = x < nx ? __ldg(row + x / kPer) : make_uint4(0u, 0u, 0u, 0u);
+  }
+  u32 mine = 0;
+#pragma unroll
+  for (int i = 0; i < kLoads; ++i) {
+    const u32 x = x0 + (u32)i * (32 * kPer) + (u32)lane * kPer;
+    u32 bits = 0;
+    if (x < nx) {
+      if constexpr (sizeof(TV) == 4) {
+        bits = (pass_f32(__uint_as_float(v[i].x), d) ? 1u : 0u) |
+               (pass_f32(__uint_as_float(v[i].y), d) ? 2u : 0u) |
+               (pass_f32(__uint_as_float(v[i].z), d) ? 4u : 0u) |
+               (pass_f32(__uint_as_float(v[i].w), d) ? 8u : 0u);
+      } else {
+        const u32 q[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          bits |= (pass_u16(q[k] & 0xffffu, d) ? 1u : 0u) << (2 * k);
+          bits |= (pass_u16(q[k] >> 16, d) ? 1u : 0u) << (2 * k + 1);
+        }
+      }
+    }
+    u32 t = bits << (kPer * (lane & (kLanesPerWord - 1)));
+#pragma unroll
+    for (int o = 1; o < kLanesPerWord; o <<= 1) t |= __shfl_xor_sync(0xffffffffu, t, o);
+    const u32 wv = __shfl_sync(0xffffffffu, t, kLanesPerWord * (lane & (kWordsPerLoad - 1)));
+    if (lane / kWordsPerLoad == i) mine = wv;
+  }
+  if ((u32)lane < nw) T[r * d.W + (x0 >> 5) + lane] = mine;
+}
+
+// Warps take the batch's 1024-voxel row segments in order (all items).
+template <typename TV>
+__global__ void __launch_bounds__(kThreads) k_threshold(const __grid_constant__ Batch B) {
   const int lane = threadIdx.x & 31;
   const u64 warp = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
-  const u64 spr = (d.nx + 1023) >> 10;
-  const u64 nseg = d.rows * spr;
-  const u32 nx = (u32)d.nx;
-  for (u64 s = warp; s < nseg; s += nwarps) {
-    const u64 r = s / spr;
-    const u32 x0 = (u32)(s - r * spr) << 10;
-    const u32 nw = min(32u, (nx - x0 + 31) >> 5);
-    const uint4* row = reinterpret_cast<const uint4*>(in + r * d.nx);
-    uint4 v[kLoads];
-#pragma unroll
-    for (int i = 0; i < kLoads; ++i) {
-      const u32 x = x0 + (u32)i * (32 * kPer) + (u32)lane * kPer;
-      v[i] = x < nx ? __ldg(row + x / kPer) : make_uint4(0u, 0u, 0u, 0u);
-    }
-    u32 mine = 0;
-#pragma unroll
-    for (int i = 0; i < kLoads; ++i) {
-      const u32 x = x0 + (u32)i * (32 * kPer) + (u32)lane * kPer;
-      u32 bits = 0;
-      if (x < nx) {
-        if constexpr (sizeof(TV) == 4) {
-          bits = (pass_f32(__uint_as_float(v[i].x), d) ? 1u : 0u) |
-                 (pass_f32(__uint_as_float(v[i].y), d) ? 2u : 0u) |
-                 (pass_f32(__uint_as_float(v[i].z), d) ? 4u : 0u) |
-                 (pass_f32(__uint_as_float(v[i].w), d) ? 8u : 0u);
-        } else {
-          const u32 q[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            bits |= (pass_u16(q[k] & 0xffffu, d) ? 1u : 0u) << (2 * k);
-            bits |= (pass_u16(q[k] >> 16, d) ? 1u : 0u) << (2 * k + 1);
-          }
-        }
-      }
-      u32 t = bits << (kPer * (lane & (kLanesPerWord - 1)));
-#pragma unroll
-      for (int o = 1; o < kLanesPerWord; o <<= 1) t |= __shfl_xor_sync(0xffffffffu, t, o);
-      const u32 wv = __shfl_sync(0xffffffffu, t, kLanesPerWord * (lane & (kWordsPerLoad - 1)));
-      if (lane / kWordsPerLoad == i) mine = wv;
-    }
-    if ((u32)lane < nw) T[r * d.W + (x0 >> 5) + lane] = mine;
+  const u64 total = B.seg0[B.n];
+  for (u64 s = warp; s < total; s += nwarps) {
+    const u32 i = find_item(B.seg0, B.n, s);
+    const Item& I = B.it[i];
+    const u64 local = s - B.seg0[i];
+    const u64 spr = (I.nx + 1023) >> 10;
+    const u64 r = local / spr;
+    const u32 x0 = (u32)(local - r * spr) << 10;
+    const Desc d = desc_of(B, I);
+    if (I.vec) thr_segment_vec<TV>(d, (const TV*)I.in, I.T, r, x0, lane);
+    else thr_segment<TV>(d, (const TV*)I.in, I.T, r, x0, lane);
   }
 }
 
@@ -172,6 +174,21 @@ __global__ void __launch_bounds__(kThreads) k_dilate(Desc d, const u32* __restri
 // both the value loads and the compacted stores are coalesced.
 constexpr u32 kListCap = 512;  // boundaries of one row kept per warp for run copies
 
+// Range of the retained finite values of one item: warp-reduced per-thread
+// keys, one atomic per warp; the keys restart for the next item.
+__device__ __forceinline__ void flush_range(State* st, u32& kmin, u32& kmax, int lane) {
+  for (int o = 16; o > 0; o >>= 1) {
+    kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+    kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+  }
+  if (st && lane == 0) {
+    if (kmin != 0xffffffffu) atomicMin(&st->vmin_key, kmin);
+    if (kmax != 0u) atomicMax(&st->vmax_key, kmax);
+  }
+  kmin = 0xffffffffu;
+  kmax = 0u;
+}
+
 struct FrontSmem {
   u32 wn[kThreads / 32], wb[kThreads / 32];  // per-warp totals, then offsets
   u64 base_n, base_nb, tile;
@@ -179,33 +196,49 @@ struct FrontSmem {
 };
 
 template <typename TV>
-__global__ void __launch_bounds__(kThreads) k_front(Desc d, const TV* __restrict__ in,
-                                                    const u32* __restrict__ T, int dilate,
-                                                    TV* __restrict__ P,
-                                                    uint16_t* __restrict__ counts, u64 counts_cap,
-                                                    uint16_t* __restrict__ bounds, u64 bounds_cap,
-                                                    State* st, u64* sizes_out, LookBack<2> lb,
-                                                    u32 rpt, u64 ntiles) {
+__global__ void __launch_bounds__(kThreads, 4) k_front(const __grid_constant__ Batch B) {
   extern __shared__ u32 smem_dyn[];
   __shared__ FrontSmem sh;
-  const u32 W = (u32)d.W;
-  const FastDiv divW(W);
-  u32* Dw = smem_dyn;                                 // [rpt * W]
-  u32* rowcnt = Dw + (u64)rpt * W;                    // [rpt]
-  u32* bflag = rowcnt + rpt;                          // [rpt + 2]
-  uint16_t* blist = (uint16_t*)(bflag + rpt + 2);     // [8][kListCap] row boundary lists
-  u32* U = (u32*)(blist + (kThreads / 32) * kListCap);  // [rpt + 2][W] when dilating
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const bool end_extra = (d.nx & 31) == 0;  // boundary at x = nx lives past the last word
   const u32 below = (1u << lane) - 1u;
-  const u64 zstride = d.ny * (u64)W;
+  const int dilate = B.c.dilate;
+  const u64 total_tiles = B.ftile0[B.n];
   u32 kmin = 0xffffffffu, kmax = 0u;
+  u32 cur = 0xffffffffu;  // item whose range the block accumulates
 
   while (true) {
-    if (threadIdx.x == 0) sh.tile = atomicAdd(&st->ctr_front, 1u);
+    if (threadIdx.x == 0) sh.tile = atomicAdd(&B.ctr[0], 1u);
     __syncthreads();
-    const u64 t = sh.tile;
-    if (t >= ntiles) break;
+    const u64 gt = sh.tile;
+    if (gt >= total_tiles) break;
+    const u32 item = find_item(B.ftile0, B.n, gt);
+    const Item& I = B.it[item];
+    if (item != cur) {  // flush the value range of the previous item
+      flush_range(cur == 0xffffffffu ? nullptr : B.it[cur].st, kmin, kmax, lane);
+      cur = item;
+    }
+    const Desc d = desc_of(B, I);
+    const u64 t = gt - B.ftile0[item];
+    const u64 ntiles = I.ftiles;
+    const u32 rpt = I.rpt;
+    const TV* __restrict__ in = (const TV*)I.in;
+    const u32* __restrict__ T = I.T;
+    TV* __restrict__ P = (TV*)I.P;
+    uint16_t* __restrict__ counts = I.counts;
+    const u64 counts_cap = I.counts_cap;
+    uint16_t* __restrict__ bounds = I.bounds;
+    const u64 bounds_cap = I.bounds_cap;
+    u64* sizes_out = I.sizes;
+    const LookBack<2> lb = I.lbf;
+    const u32 W = (u32)d.W;
+    const FastDiv divW(W);
+    u32* Dw = smem_dyn;                                 // [rpt * W]
+    u32* rowcnt = Dw + (u64)rpt * W;                    // [rpt]
+    u32* bflag = rowcnt + rpt;                          // [rpt + 2]
+    uint16_t* blist = (uint16_t*)(bflag + rpt + 2);     // [8][kListCap] row boundary lists
+    u32* U = (u32*)(blist + (kThreads / 32) * kListCap);  // [rpt + 2][W] when dilating
+    const bool end_extra = (d.nx & 31) == 0;  // boundary at x = nx lives past the last word
+    const u64 zstride = d.ny * (u64)W;
     const u64 r0 = t * rpt;
     const u32 nrows = (u32)umin(rpt, d.rows - r0);
     const u32 nw = nrows * W;
@@ -312,7 +345,7 @@ __global__ void __launch_bounds__(kThreads) k_front(Desc d, const TV* __restrict
         sh.wb[lane] = ib - b;
       }
       u64 mine[2] = {tn, tb}, excl[2];
-      lookback_warp<2>(lb, t, mine, excl, &st->status);
+      lookback_warp<2>(lb, t, mine, excl, B.status);
       if (lane == 0) {
         sh.base_n = excl[0];
         sh.base_nb = excl[1];
@@ -353,13 +386,13 @@ __global__ void __launch_bounds__(kThreads) k_front(Desc d, const TV* __restrict
             const u32 x = w * 32 + (__ffs(ev) - 1);
             ev &= ev - 1;
             if (ob + o < bounds_cap) bounds[ob + o] = (uint16_t)x;
-            else set_status(&st->status, ROIX_ECAPACITY);
+            else set_status(B.status, ROIX_ECAPACITY);
             if (fast) lst[o] = (uint16_t)x;
             ++o;
           }
           if (ex) {
             if (ob + o < bounds_cap) bounds[ob + o] = (uint16_t)d.nx;
-            else set_status(&st->status, ROIX_ECAPACITY);
+            else set_status(B.status, ROIX_ECAPACITY);
             if (fast) lst[o] = (uint16_t)d.nx;
           }
           bo += __shfl_sync(0xffffffffu, inc, 31);
@@ -439,15 +472,7 @@ __global__ void __launch_bounds__(kThreads) k_front(Desc d, const TV* __restrict
     }
     __syncthreads();
   }
-  // range of the retained finite values
-  for (int o = 16; o > 0; o >>= 1) {
-    kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
-    kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
-  }
-  if (lane == 0) {
-    if (kmin != 0xffffffffu) atomicMin(&st->vmin_key, kmin);
-    if (kmax != 0u) atomicMax(&st->vmax_key, kmax);
-  }
+  flush_range(cur == 0xffffffffu ? nullptr : B.it[cur].st, kmin, kmax, lane);
 }
 
 int occupancy_grid(const void* fn, int threads, size_t smem, int sms) {
@@ -459,27 +484,17 @@ int occupancy_grid(const void* fn, int threads, size_t smem, int sms) {
 
 }  // namespace
 
-void launch_threshold(const Launch& L, const Desc& d, const void* in, u32* T) {
-  const u64 segs = d.rows * ((d.nx + 1023) >> 10);
+void launch_threshold(const Launch& L, const Batch& B) {
+  const u64 segs = B.seg0[B.n];
   if (segs == 0) return;
   const u64 warps_per_block = kThreads / 32;
   u64 blocks = (segs + warps_per_block - 1) / warps_per_block;
   const u64 cap = (u64)L.sms * 8;  // 8 blocks of 256 threads per SM in flight
   if (blocks > cap) blocks = cap;
-  const bool al16 = ((uintptr_t)in & 15) == 0;
-  if (d.dtype == ROIX_F32) {
-    if (al16 && (d.nx & 3) == 0)
-      k_threshold_vec<float><<<(unsigned)blocks, kThreads, 0, L.stream>>>(d, (const float*)in, T);
-    else
-      k_threshold<float><<<(unsigned)blocks, kThreads, 0, L.stream>>>(d, (const float*)in, T);
-  } else {
-    if (al16 && (d.nx & 7) == 0)
-      k_threshold_vec<unsigned short><<<(unsigned)blocks, kThreads, 0, L.stream>>>(
-          d, (const unsigned short*)in, T);
-    else
-      k_threshold<unsigned short><<<(unsigned)blocks, kThreads, 0, L.stream>>>(
-          d, (const unsigned short*)in, T);
-  }
+  if (B.c.dtype == ROIX_F32)
+    k_threshold<float><<<(unsigned)blocks, kThreads, 0, L.stream>>>(B);
+  else
+    k_threshold<unsigned short><<<(unsigned)blocks, kThreads, 0, L.stream>>>(B);
 }
 
 void launch_dilate(const Launch& L, const Desc& d, const u32* T, u32* D, u64* popcount) {
@@ -490,26 +505,28 @@ void launch_dilate(const Launch& L, const Desc& d, const u32* T, u32* D, u64* po
   k_dilate<<<(unsigned)blocks, kThreads, 0, L.stream>>>(d, T, D, popcount);
 }
 
-void launch_front(const Launch& L, const Desc& d, const void* in, const u32* T, int dilate,
-                  void* P, uint16_t* counts, u64 counts_cap, uint16_t* bounds, u64 bounds_cap,
-                  State* st, LookBack<2> lb, u32 rows_per_tile, u64 tiles, u64* sizes_out) {
+size_t front_smem(u32 rpt, u64 W, int dilate) {
+  return (size_t)rpt * W * 4 + (size_t)rpt * 8 + 8 + (size_t)(kThreads / 32) * kListCap * 2 +
+         (dilate ? (size_t)(rpt + 2) * W * 4 : 0);
+}
+
+void launch_front(const Launch& L, const Batch& B) {
+  const u64 tiles = B.ftile0[B.n];
   if (tiles == 0) return;
-  const size_t smem = (size_t)rows_per_tile * d.W * 4 + (size_t)rows_per_tile * 8 + 8 +
-                      (size_t)(kThreads / 32) * kListCap * 2 +
-                      (dilate ? (size_t)(rows_per_tile + 2) * d.W * 4 : 0);
-  const void* fn = d.dtype == ROIX_F32 ? (const void*)k_front<float>
-                                       : (const void*)k_front<unsigned short>;
+  size_t smem = 0;
+  for (u32 i = 0; i < B.n; ++i) {
+    const size_t s = front_smem(B.it[i].rpt, B.it[i].W, B.c.dilate);
+    if (s > smem) smem = s;
+  }
+  const void* fn = B.c.dtype == ROIX_F32 ? (const void*)k_front<float>
+                                         : (const void*)k_front<unsigned short>;
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   u64 grid = (u64)occupancy_grid(fn, kThreads, smem, L.sms);
   if (grid > tiles) grid = tiles;
-  if (d.dtype == ROIX_F32)
-    k_front<float><<<(unsigned)grid, kThreads, smem, L.stream>>>(
-        d, (const float*)in, T, dilate, (float*)P, counts, counts_cap, bounds, bounds_cap, st,
-        sizes_out, lb, rows_per_tile, tiles);
+  if (B.c.dtype == ROIX_F32)
+    k_front<float><<<(unsigned)grid, kThreads, smem, L.stream>>>(B);
   else
-    k_front<unsigned short><<<(unsigned)grid, kThreads, smem, L.stream>>>(
-        d, (const unsigned short*)in, T, dilate, (unsigned short*)P, counts, counts_cap, bounds,
-        bounds_cap, st, sizes_out, lb, rows_per_tile, tiles);
+    k_front<unsigned short><<<(unsigned)grid, kThreads, smem, L.stream>>>(B);
 }
 
 }  // namespace roix

@@ -5,6 +5,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "roix_internal.cuh"
 
@@ -194,44 +195,70 @@ u32 front_rows_per_tile(const Desc& d) {
 }
 
 // ----------------------------------------------------- compress workspace
-struct CompressPlan {
-  size_t st, zero_begin, zero_end;
-  size_t ff, qf, pf, hist;      // look-back flags, histogram
-  size_t fa, qa, pa;            // look-back data
-  size_t T, P, sym, rk, rv, lens, codes;
-  size_t total;
-  u64 ftiles, qtiles, pchunks, rec_cap;
+// Layout of a batch's workspace: State[n] at offset 0 (state 0's first word is
+// the context status), then one zeroed region (look-back flags, histograms of
+// every item), then every item's data (look-back values, mask, pixel section,
+// symbols, records, code tables).
+struct ItemPlan {
+  size_t ff, qf, pf, hist;  // zeroed
+  size_t fa, qa, pa, T, P, sym, rk, rv, lens, codes;
+  u64 ftiles, qtiles, pchunks, pranges, rec_cap, n_cap;
   u32 rpt;
 };
 
-CompressPlan plan_compress(const Desc& d, u64 n_cap, u64 cap, bool need_T, bool need_P) {
-  CompressPlan p{};
+struct BatchPlan {
+  size_t zero_begin = 0, zero_end = 0, total = 0;
+  std::vector<ItemPlan> items;
+  u64 qtiles = 0, pranges = 0;
+};
+
+BatchPlan plan_batch(const Desc& c, const roix_dims* dims, const u64* n_caps, const u64* caps,
+                     u32 n, bool need_T, bool need_P) {
+  BatchPlan bp;
+  bp.items.resize(n);
   Arena a;
-  p.st = a.take(kStateBytes);
-  p.rpt = front_rows_per_tile(d);
-  p.ftiles = d.rows ? (d.rows + p.rpt - 1) / p.rpt : 0;
-  p.qtiles = (n_cap + kQuantTile - 1) / kQuantTile;
-  p.pchunks = d.C ? (n_cap + d.C - 1) / d.C : 0;
-  p.rec_cap = umin(n_cap, cap / 12 + 1);
-  p.zero_begin = a.take(0);
-  p.ff = a.take(4 * (p.ftiles + 1));
-  p.qf = a.take(4 * (p.qtiles + 1));
-  p.pf = a.take(4 * (p.pchunks + 1));
-  p.hist = a.take(8 * (size_t)d.S);
-  p.zero_end = a.take(0);
-  p.fa = a.take(8 * 4 * (p.ftiles + 1));
-  p.qa = a.take(8 * 2 * (p.qtiles + 1));
-  p.pa = a.take(8 * 2 * (p.pchunks + 1));
-  p.T = need_T ? a.take(4 * d.rows * d.W) : 0;
-  const size_t esz = d.dtype == ROIX_F32 ? 4 : 2;
-  p.P = need_P ? a.take(esz * n_cap + 16) : 0;
-  p.sym = a.take(2 * n_cap + 16);
-  p.rk = a.take(8 * (p.rec_cap + 1));
-  p.rv = a.take(4 * (p.rec_cap + 1));
-  p.lens = a.take(d.S + 16);
-  p.codes = a.take(4 * (size_t)d.S);
-  p.total = a.take(0);
-  return p;
+  a.take(sizeof(State) * (n ? n : 1));
+  bp.zero_begin = a.take(0);
+  const size_t esz = c.dtype == ROIX_F32 ? 4 : 2;
+  for (u32 i = 0; i < n; ++i) {
+    ItemPlan& p = bp.items[i];
+    Desc d = c;
+    d.nx = dims[i].nx;
+    d.ny = dims[i].ny;
+    d.nz = dims[i].nz;
+    d.rows = d.ny * d.nz;
+    d.W = (d.nx + 31) / 32;
+    p.n_cap = n_caps[i];
+    p.rpt = front_rows_per_tile(d);
+    p.ftiles = d.rows ? (d.rows + p.rpt - 1) / p.rpt : 0;
+    p.qtiles = (p.n_cap + kQuantTile - 1) / kQuantTile;
+    p.pchunks = c.C ? (p.n_cap + c.C - 1) / c.C : 0;
+    p.pranges = (p.pchunks + kPackRange - 1) / kPackRange;
+    p.rec_cap = umin(p.n_cap, caps[i] / 12 + 1);
+    p.ff = a.take(4 * (p.ftiles + 1));
+    p.qf = a.take(4 * (p.qtiles + 1));
+    p.pf = a.take(4 * (p.pranges + 1));
+    p.hist = a.take(8 * (size_t)c.S);
+    bp.qtiles += p.qtiles;
+    bp.pranges += p.pranges;
+  }
+  bp.zero_end = a.take(0);
+  for (u32 i = 0; i < n; ++i) {
+    ItemPlan& p = bp.items[i];
+    const u64 rows = dims[i].ny * dims[i].nz, W = (dims[i].nx + 31) / 32;
+    p.fa = a.take(8 * 4 * (p.ftiles + 1));
+    p.qa = a.take(8 * 2 * (p.qtiles + 1));
+    p.pa = a.take(8 * 2 * (p.pranges + 1));
+    p.T = need_T ? a.take(4 * rows * W + 16) : 0;
+    p.P = need_P ? a.take(esz * p.n_cap + 16) : 0;
+    p.sym = a.take(2 * p.n_cap + 16);
+    p.rk = a.take(8 * (p.rec_cap + 1));
+    p.rv = a.take(4 * (p.rec_cap + 1));
+    p.lens = a.take(c.S + 16);
+    p.codes = a.take(4 * (size_t)c.S);
+  }
+  bp.total = a.take(0);
+  return bp;
 }
 
 template <int NV>
@@ -241,6 +268,91 @@ LookBack<NV> lb_at(char* ws, size_t flags, size_t data, u64 tiles) {
   lb.agg = (u64*)(ws + data);
   lb.inc = (u64*)(ws + data) + NV * (tiles + 1);
   return lb;
+}
+
+bool rows_vector_aligned(const void* in, roix_dtype dt, u64 nx) {
+  if (((uintptr_t)in & 15) != 0) return false;
+  return dt == ROIX_F32 ? (nx & 3) == 0 : (nx & 7) == 0;
+}
+
+// Fills the batch structure for the plan; pointers into `ws`. Item fields for
+// outputs and inputs are set by the caller.
+void fill_batch(Batch& B, const Desc& c, const BatchPlan& bp, const roix_dims* dims, char* ws,
+                u32 n) {
+  std::memset(&B, 0, sizeof(B));
+  B.c = c;
+  B.n = n;
+  State* st = (State*)ws;
+  B.status = &st[0].status;
+  B.ctr = &st[0].ctr_front;
+  u64 seg = 0, ft = 0;
+  for (u32 i = 0; i < n; ++i) {
+    const ItemPlan& p = bp.items[i];
+    Item& I = B.it[i];
+    I.nx = dims[i].nx;
+    I.ny = dims[i].ny;
+    I.nz = dims[i].nz;
+    I.rows = I.ny * I.nz;
+    I.W = (I.nx + 31) / 32;
+    I.N = p.n_cap;
+    I.st = st + i;
+    I.T = p.T ? (u32*)(ws + p.T) : nullptr;
+    I.P = p.P ? (void*)(ws + p.P) : nullptr;
+    I.sym = (uint16_t*)(ws + p.sym);
+    I.rk = (u64*)(ws + p.rk);
+    I.rv = (u32*)(ws + p.rv);
+    I.rec_cap = p.rec_cap;
+    I.hist = (unsigned long long*)(ws + p.hist);
+    I.lens = (uint8_t*)(ws + p.lens);
+    I.codes = (u32*)(ws + p.codes);
+    I.sizes = &I.st->n;
+    I.lbf = lb_at<2>(ws, p.ff, p.fa, p.ftiles);
+    I.lbq = lb_at<1>(ws, p.qf, p.qa, p.qtiles);
+    I.lbp = lb_at<1>(ws, p.pf, p.pa, p.pranges);
+    I.rpt = p.rpt;
+    I.ftiles = p.ftiles;
+    B.seg0[i] = seg;
+    B.ftile0[i] = ft;
+    seg += I.rows * ((I.nx + 1023) / 1024);
+    ft += p.ftiles;
+  }
+  B.seg0[n] = seg;
+  B.ftile0[n] = ft;
+}
+
+}  // namespace
+
+// One-item batch for the binarisation kernel alone.
+void roix::make_threshold_batch(Batch& B, const Desc& d, const void* in, u32* T) {
+  std::memset(&B, 0, sizeof(B));
+  B.c = d;
+  B.n = 1;
+  Item& I = B.it[0];
+  I.nx = d.nx;
+  I.ny = d.ny;
+  I.nz = d.nz;
+  I.rows = d.rows;
+  I.W = d.W;
+  I.N = d.N;
+  I.in = in;
+  I.T = T;
+  I.vec = rows_vector_aligned(in, (roix_dtype)d.dtype, d.nx) ? 1u : 0u;
+  B.seg0[1] = d.rows * ((d.nx + 1023) / 1024);
+}
+
+namespace {
+
+// Output side of a fused item: geometry written straight into the container.
+void set_container(Item& I, const Desc& c, void* out, u64 cap, u64* size_dev) {
+  const Layout lo = make_layout(c.S, I.rows, 0, 0, 0, 0);
+  uint8_t* o = (uint8_t*)out;
+  I.out = o;
+  I.cap = cap;
+  I.size_dev = size_dev;
+  I.counts = (uint16_t*)(o + lo.off_counts);
+  I.counts_cap = cap > lo.off_counts ? (cap - lo.off_counts) / 2 : 0;
+  I.bounds = (uint16_t*)(o + lo.off_bounds);
+  I.bounds_cap = cap > lo.off_bounds ? (cap - lo.off_bounds) / 2 : 0;
 }
 
 // profiling marks: an event after each stage when profiling is on
@@ -253,9 +365,6 @@ void mark(roix_ctx* ctx, cudaStream_t s) {
 
 }  // namespace
 
-namespace roix {
-void launch_init(const Launch& L, State* st, void* zero, size_t zero_bytes);
-}
 
 extern "C" {
 
@@ -326,7 +435,8 @@ size_t roix_workspace_size(roix_dtype dtype, roix_dims dims, const roix_roi* roi
                            const roix_params* params, uint64_t cap) {
   Desc d;
   if (make_desc(nullptr, dtype, dims, roi, nullptr, params, &d) != ROIX_OK) return 0;
-  return plan_compress(d, d.N, cap, true, true).total;
+  const u64 ncap = d.N, cap64 = cap;
+  return plan_batch(d, &dims, &ncap, &cap64, 1, true, true).total;
 }
 
 roix_status roix_sync(roix_ctx* ctx, void* stream) {
@@ -384,16 +494,16 @@ roix_status roix_extract_roi(roix_ctx* ctx, const void* in, roix_dtype dtype, ro
   if (!popcount_dev) return fail(ctx, ROIX_EINVAL, "null popcount_dev");
   DeviceGuard g(ctx->device);
   Arena a;
-  const size_t st_off = a.take(kStateBytes);
+  a.take(sizeof(State));
   const size_t T_off = a.take(4 * d.rows * d.W + 16);
   if ((s = ensure_ws(ctx, a.take(0)))) return s;
   cudaStream_t cs = (cudaStream_t)stream;
   Launch L{cs, ctx->sms};
-  State* st = (State*)(ctx->ws + st_off);
-  launch_init(L, st, nullptr, 0);
-  cudaMemsetAsync(popcount_dev, 0, 8, cs);
   u32* T = (u32*)(ctx->ws + T_off);
-  launch_threshold(L, d, in, T);
+  cudaMemsetAsync(popcount_dev, 0, 8, cs);
+  static thread_local Batch B;  // 22 KB: kept off the stack
+  make_threshold_batch(B, d, in, T);
+  launch_threshold(L, B);
   launch_dilate(L, d, T, mask_out, (u64*)popcount_dev);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? ROIX_OK : cuda_fail(ctx, e, "extract_roi launch");
@@ -412,22 +522,27 @@ roix_status roix_compact(roix_ctx* ctx, const void* in, roix_dtype dtype, roix_d
   if (!sizes_dev) return fail(ctx, ROIX_EINVAL, "null sizes_dev");
   if (!aligned(pixels_out, 4)) return fail(ctx, ROIX_EINVAL, "pixels_out must be 4-byte aligned");
   DeviceGuard g(ctx->device);
-  Arena a;
-  const size_t st_off = a.take(kStateBytes);
-  const u32 rpt = front_rows_per_tile(d);
-  const u64 tiles = d.rows ? (d.rows + rpt - 1) / rpt : 0;
-  const size_t zb = a.take(0);
-  const size_t ff = a.take(4 * (tiles + 1));
-  const size_t ze = a.take(0);
-  const size_t fa = a.take(8 * 4 * (tiles + 1));
-  if ((s = ensure_ws(ctx, a.take(0)))) return s;
+  d.dilate = 0;  // the mask is used as given
+  d.S = 2;       // no coder settings: one histogram bin pair reserved, unused
+  const u64 ncap = d.N, cap = 0;
+  BatchPlan bp = plan_batch(d, &dims, &ncap, &cap, 1, false, false);
+  if ((s = ensure_ws(ctx, bp.total))) return s;
   cudaStream_t cs = (cudaStream_t)stream;
   Launch L{cs, ctx->sms};
-  State* st = (State*)(ctx->ws + st_off);
-  launch_init(L, st, ctx->ws + zb, ze - zb);
+  static thread_local Batch B;
+  fill_batch(B, d, bp, &dims, ctx->ws, 1);
+  Item& I = B.it[0];
+  I.in = in;
+  I.T = const_cast<uint32_t*>(mask);
+  I.P = pixels_out;
+  I.counts = counts_out;
+  I.counts_cap = d.rows;
+  I.bounds = bounds_out;
+  I.bounds_cap = bounds_cap;
+  I.sizes = (u64*)sizes_dev;
+  launch_init(L, (State*)ctx->ws, 1, ctx->ws + bp.zero_begin, bp.zero_end - bp.zero_begin);
   cudaMemsetAsync(sizes_dev, 0, 16, cs);
-  launch_front(L, d, in, mask, 0, pixels_out, counts_out, d.rows, bounds_out, bounds_cap, st,
-               lb_at<2>(ctx->ws, ff, fa, tiles), rpt, tiles, (u64*)sizes_dev);
+  launch_front(L, B);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? ROIX_OK : cuda_fail(ctx, e, "compact launch");
 }
@@ -456,7 +571,7 @@ roix_status roix_quantize(roix_ctx* ctx, const void* pixels, roix_dtype dtype, u
   cudaStream_t cs = (cudaStream_t)stream;
   Launch L{cs, ctx->sms};
   State* st = (State*)(ctx->ws + st_off);
-  launch_init(L, st, nullptr, 0);
+  launch_init(L, st, 1, nullptr, 0);
   launch_quantize_stage(L, d, pixels, n_cap, (const u64*)n_dev, q_out, outlier_bits_out,
                         info_dev, st);
   cudaError_t e = cudaGetLastError();
@@ -478,27 +593,86 @@ roix_status roix_encode(roix_ctx* ctx, const int32_t* q, const uint32_t* outlier
   if (n_cap && (!q || !outlier_bits || !pixels)) return fail(ctx, ROIX_EINVAL, "null buffer");
   if (d.rows && !counts) return fail(ctx, ROIX_EINVAL, "null counts");
   if (!aligned(out, 16)) return fail(ctx, ROIX_EINVAL, "out must be 16-byte aligned");
+  if (!aligned(q, 8)) return fail(ctx, ROIX_EINVAL, "q must be 8-byte aligned");
   DeviceGuard g(ctx->device);
-  CompressPlan p = plan_compress(d, n_cap, cap, false, false);
-  if ((s = ensure_ws(ctx, p.total))) return s;
+  const u64 ncap64 = n_cap, cap64 = cap;
+  BatchPlan bp = plan_batch(d, &dims, &ncap64, &cap64, 1, false, false);
+  if ((s = ensure_ws(ctx, bp.total))) return s;
   cudaStream_t cs = (cudaStream_t)stream;
   Launch L{cs, ctx->sms};
-  char* ws = ctx->ws;
-  State* st = (State*)(ws + p.st);
-  launch_init(L, st, ws + p.zero_begin, p.zero_end - p.zero_begin);
-  launch_symbols(L, d, pixels, q, outlier_bits, n_cap, (const u64*)sizes_dev, info_dev, st,
-                 (uint16_t*)(ws + p.sym), (u64*)(ws + p.rk), (u32*)(ws + p.rv), p.rec_cap,
-                 (unsigned long long*)(ws + p.hist), lb_at<1>(ws, p.qf, p.qa, p.qtiles));
-  launch_codebook(L, d, (unsigned long long*)(ws + p.hist), (uint8_t*)(ws + p.lens),
-                  (u32*)(ws + p.codes), (uint8_t*)out, cap, st);
-  launch_pack(L, d, (uint16_t*)(ws + p.sym), (const u64*)sizes_dev, (const u64*)sizes_dev + 1,
-              (uint8_t*)(ws + p.lens), (u32*)(ws + p.codes), st, (uint8_t*)out, cap,
-              lb_at<1>(ws, p.pf, p.pa, p.pchunks), p.pchunks);
-  launch_finalize(L, d, st, (const u64*)sizes_dev, (const u64*)sizes_dev + 1, info_dev,
-                  (u64*)(ws + p.rk), (u32*)(ws + p.rv), p.rec_cap, counts, bounds,
-                  (uint8_t*)out, cap, (u64*)size_dev);
+  static thread_local Batch B;
+  fill_batch(B, d, bp, &dims, ctx->ws, 1);
+  Item& I = B.it[0];
+  I.out = (uint8_t*)out;
+  I.cap = cap;
+  I.size_dev = (u64*)size_dev;
+  I.P = const_cast<void*>(pixels);
+  I.q = q ? q : (const int32_t*)ctx->ws;  // non-null selects the staged-code kernels
+  I.obits = outlier_bits;
+  I.info_in = info_dev;
+  I.sizes = const_cast<u64*>((const u64*)sizes_dev);
+  I.counts_src = counts;
+  I.bounds_src = bounds;
+  launch_init(L, (State*)ctx->ws, 1, ctx->ws + bp.zero_begin, bp.zero_end - bp.zero_begin);
+  launch_symbols(L, B, bp.qtiles);
+  launch_codebook(L, B);
+  launch_pack(L, B, bp.pranges);
+  launch_finalize(L, B);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? ROIX_OK : cuda_fail(ctx, e, "encode launch");
+}
+
+// The fused path for one group of at most kMaxBatch items sharing `c`.
+roix_status enqueue_group(roix_ctx* ctx, const Desc& c, const roix_item* items, u32 n,
+                          cudaStream_t cs, bool profile) {
+  std::vector<roix_dims> dims(n);
+  std::vector<u64> ncaps(n), caps(n);
+  for (u32 i = 0; i < n; ++i) {
+    dims[i] = items[i].dims;
+    ncaps[i] = items[i].dims.nx * items[i].dims.ny * items[i].dims.nz;
+    caps[i] = items[i].cap;
+  }
+  BatchPlan bp = plan_batch(c, dims.data(), ncaps.data(), caps.data(), n, true, true);
+  roix_status s = ensure_ws(ctx, bp.total);
+  if (s) return s;
+  Launch L{cs, ctx->sms};
+  static thread_local Batch B;
+  fill_batch(B, c, bp, dims.data(), ctx->ws, n);
+  for (u32 i = 0; i < n; ++i) {
+    Item& I = B.it[i];
+    I.in = items[i].in;
+    I.vec = rows_vector_aligned(items[i].in, (roix_dtype)c.dtype, I.nx) ? 1u : 0u;
+    set_container(I, c, items[i].out, items[i].cap, (u64*)items[i].size_dev);
+  }
+  if (profile) {
+    ctx->nev = 0;
+    mark(ctx, cs);
+  }
+  launch_init(L, (State*)ctx->ws, n, ctx->ws + bp.zero_begin, bp.zero_end - bp.zero_begin);
+  if (profile) mark(ctx, cs);
+  launch_threshold(L, B);
+  if (profile) mark(ctx, cs);
+  launch_front(L, B);
+  if (profile) mark(ctx, cs);
+  launch_symbols(L, B, bp.qtiles);
+  if (profile) mark(ctx, cs);
+  launch_codebook(L, B);
+  if (profile) mark(ctx, cs);
+  launch_pack(L, B, bp.pranges);
+  if (profile) mark(ctx, cs);
+  launch_finalize(L, B);
+  if (profile) mark(ctx, cs);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ROIX_OK : cuda_fail(ctx, e, "compress launch");
+}
+
+roix_status check_item(roix_ctx* ctx, const roix_item& it, roix_dtype dtype) {
+  if (!dims_ok(it.dims)) return fail(ctx, ROIX_EINVAL, "dims: nx <= 65534, ny, nz < 2^32");
+  const u64 N = it.dims.nx * it.dims.ny * it.dims.nz;
+  if ((N && !it.in) || !it.out || !it.size_dev) return fail(ctx, ROIX_EINVAL, "null buffer");
+  if (!aligned(it.out, 16)) return fail(ctx, ROIX_EINVAL, "out must be 16-byte aligned");
+  if (!aligned(it.in, dtype == ROIX_F32 ? 4 : 2)) return fail(ctx, ROIX_EINVAL, "misaligned input");
+  return ROIX_OK;
 }
 
 roix_status roix_compress(roix_ctx* ctx, const void* in, roix_dtype dtype, roix_dims dims,
@@ -509,45 +683,31 @@ roix_status roix_compress(roix_ctx* ctx, const void* in, roix_dtype dtype, roix_
   roix_status s = make_desc(ctx, dtype, dims, roi, eb, params, &d);
   if (s) return s;
   if (d.keep) return fail(ctx, ROIX_EINVAL, "keep = largest component is not available yet");
-  if ((d.N && !in) || !out || !size_dev) return fail(ctx, ROIX_EINVAL, "null buffer");
-  if (!aligned(out, 16)) return fail(ctx, ROIX_EINVAL, "out must be 16-byte aligned");
-  if (!aligned(in, dtype == ROIX_F32 ? 4 : 2)) return fail(ctx, ROIX_EINVAL, "misaligned input");
+  const roix_item it{in, dims, out, cap, size_dev};
+  if ((s = check_item(ctx, it, dtype))) return s;
   DeviceGuard g(ctx->device);
-  CompressPlan p = plan_compress(d, d.N, cap, true, true);
-  if ((s = ensure_ws(ctx, p.total))) return s;
-  cudaStream_t cs = (cudaStream_t)stream;
-  Launch L{cs, ctx->sms};
-  char* ws = ctx->ws;
-  State* st = (State*)(ws + p.st);
-  uint8_t* o = (uint8_t*)out;
-  const Layout lo = make_layout(d.S, d.rows, 0, 0, 0, 0);
-  const u64 counts_cap = cap > lo.off_counts ? (cap - lo.off_counts) / 2 : 0;
-  const u64 bounds_cap = cap > lo.off_bounds ? (cap - lo.off_bounds) / 2 : 0;
-  ctx->nev = 0;
-  mark(ctx, cs);
-  launch_init(L, st, ws + p.zero_begin, p.zero_end - p.zero_begin);
-  mark(ctx, cs);
-  launch_threshold(L, d, in, (u32*)(ws + p.T));
-  mark(ctx, cs);
-  launch_front(L, d, in, (u32*)(ws + p.T), d.dilate, ws + p.P, (uint16_t*)(o + lo.off_counts),
-               counts_cap, (uint16_t*)(o + lo.off_bounds), bounds_cap, st,
-               lb_at<2>(ws, p.ff, p.fa, p.ftiles), p.rpt, p.ftiles, &st->n);
-  mark(ctx, cs);
-  launch_symbols(L, d, ws + p.P, nullptr, nullptr, d.N, &st->n, nullptr, st,
-                 (uint16_t*)(ws + p.sym), (u64*)(ws + p.rk), (u32*)(ws + p.rv), p.rec_cap,
-                 (unsigned long long*)(ws + p.hist), lb_at<1>(ws, p.qf, p.qa, p.qtiles));
-  mark(ctx, cs);
-  launch_codebook(L, d, (unsigned long long*)(ws + p.hist), (uint8_t*)(ws + p.lens),
-                  (u32*)(ws + p.codes), o, cap, st);
-  mark(ctx, cs);
-  launch_pack(L, d, (uint16_t*)(ws + p.sym), &st->n, &st->nb, (uint8_t*)(ws + p.lens),
-              (u32*)(ws + p.codes), st, o, cap, lb_at<1>(ws, p.pf, p.pa, p.pchunks), p.pchunks);
-  mark(ctx, cs);
-  launch_finalize(L, d, st, &st->n, &st->nb, &st->eb, (u64*)(ws + p.rk), (u32*)(ws + p.rv),
-                  p.rec_cap, nullptr, nullptr, o, cap, (u64*)size_dev);
-  mark(ctx, cs);
-  cudaError_t e = cudaGetLastError();
-  return e == cudaSuccess ? ROIX_OK : cuda_fail(ctx, e, "compress launch");
+  return enqueue_group(ctx, d, &it, 1, (cudaStream_t)stream, ctx->profile != 0);
+}
+
+roix_status roix_compress_batch(roix_ctx* ctx, uint32_t n, const roix_item* items,
+                                roix_dtype dtype, const roix_roi* roi, const roix_eb* eb,
+                                const roix_params* params, void* stream) {
+  if (!ctx || !roi || !eb || !params || (n && !items))
+    return fail(ctx, ROIX_EINVAL, "null argument");
+  Desc d;
+  const roix_dims one{1, 1, 1};
+  roix_status s = make_desc(ctx, dtype, one, roi, eb, params, &d);
+  if (s) return s;
+  if (d.keep) return fail(ctx, ROIX_EINVAL, "keep = largest component is not available yet");
+  for (u32 i = 0; i < n; ++i)
+    if ((s = check_item(ctx, items[i], dtype))) return s;
+  DeviceGuard g(ctx->device);
+  for (u32 i0 = 0; i0 < n; i0 += kMaxBatch) {
+    const u32 m = n - i0 < (u32)kMaxBatch ? n - i0 : (u32)kMaxBatch;
+    if ((s = enqueue_group(ctx, d, items + i0, m, (cudaStream_t)stream, ctx->profile != 0)))
+      return s;
+  }
+  return ROIX_OK;
 }
 
 roix_status roix_decode(roix_ctx* ctx, const void* in, uint64_t size, void* out,
@@ -584,7 +744,7 @@ roix_status roix_decode(roix_ctx* ctx, const void* in, uint64_t size, void* out,
   Launch L{cs, ctx->sms};
   char* ws = ctx->ws;
   State* st = (State*)(ws + st_off);
-  launch_init(L, st, ws + zb, ze - zb);
+  launch_init(L, st, 1, ws + zb, ze - zb);
   DecodeWs w;
   w.status = &st->status;
   w.plan = (u64*)(ws + plan);

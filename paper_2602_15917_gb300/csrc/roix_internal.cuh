@@ -248,10 +248,11 @@ __host__ __device__ __forceinline__ Layout make_layout(u64 S, u64 rows, u64 nb, 
   return L;
 }
 
-// Device-side state of one compression (workspace head, zeroed per call).
+// Device-side state of one compressed item (zeroed per call, except the
+// first word of the context's first state, which is the context status).
 struct State {
-  u32 status;
-  u32 ctr_front, ctr_quant, ctr_pack;  // dynamic tile counters
+  u32 status;                          // context status word (state 0 only)
+  u32 ctr_front, ctr_quant, ctr_pack;  // dynamic tile counters (state 0: batch tickets)
   u64 n, nb, nout, nwords;             // sizes found on the device
   u32 vmin_key, vmax_key;              // range of retained finite values
   u32 cap_flag, pad0;
@@ -273,6 +274,81 @@ struct Desc {
   double eb_value;
   u32 R, S, C;
 };
+
+// ------------------------------------------------------------------ batches
+// A batch is up to kMaxBatch independent items (volumes or images) sharing
+// the ROI / error-bound / coder settings. Kernels take it as a
+// __grid_constant__ parameter and map global work tickets to (item, tile)
+// through prefix sums; every item has its own state, look-back descriptors,
+// histogram, codebook and container. A single volume is a batch of one.
+constexpr int kMaxBatch = 64;
+
+struct Item {
+  u64 nx, ny, nz, rows, W, N;          // geometry
+  const void* in;                      // input values
+  uint8_t* out;                        // container
+  u64 cap;
+  u64* size_dev;                       // container size (output)
+  State* st;
+  u32* T;                              // thresholded mask (fused path)
+  void* P;                             // pixel section
+  uint16_t* sym;
+  u64* rk;                             // records
+  u32* rv;
+  u64 rec_cap;
+  unsigned long long* hist;
+  uint8_t* lens;
+  u32* codes;
+  const int32_t* q;                    // staged codes (encode from codes), else null
+  const u32* obits;
+  const roix_eb_info* info_in;         // staged error-bound constants, else null
+  uint16_t* counts;                    // row geometry destinations
+  u64 counts_cap;
+  uint16_t* bounds;
+  u64 bounds_cap;
+  const uint16_t* counts_src;          // staged geometry to copy into the container
+  const uint16_t* bounds_src;
+  u64* sizes;                          // [n, nb]
+  LookBack<2> lbf;                     // front tiles
+  LookBack<1> lbq;                     // symbol tiles
+  LookBack<1> lbp;                     // pack ranges
+  u32 rpt;                             // rows per front tile
+  u32 vec;                             // rows are 16-byte aligned (vector loads)
+  u64 ftiles;                          // front tiles
+};
+
+struct Batch {
+  Desc c;                              // shared settings (geometry fields unused)
+  u32 n;                               // items
+  u32* status;                         // context status word
+  u32* ctr;                            // [4] tickets: front, symbols, pack, spare
+  u64 seg0[kMaxBatch + 1];             // prefix of threshold row segments
+  u64 ftile0[kMaxBatch + 1];           // prefix of front tiles
+  Item it[kMaxBatch];
+};
+
+__device__ __forceinline__ Desc desc_of(const Batch& B, const Item& I) {
+  Desc d = B.c;
+  d.nx = I.nx;
+  d.ny = I.ny;
+  d.nz = I.nz;
+  d.rows = I.rows;
+  d.W = I.W;
+  d.N = I.N;
+  return d;
+}
+
+// Largest i in [0, n) with prefix[i] <= x (prefix[0] = 0, nondecreasing).
+template <typename P>
+__device__ __forceinline__ u32 find_item(const P& prefix, u32 n, u64 x) {
+  u32 lo = 0, hi = n;  // invariant: prefix[lo] <= x < prefix[hi] (prefix[n] = total)
+  while (hi - lo > 1) {
+    const u32 mid = (lo + hi) >> 1;
+    if (prefix[mid] <= x) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
 
 // Error-bound constants from the mode, the value and the range keys; the same
 // sequence of binary64 operations as the definition (Sec. 4.2.3, Sz3 range).
@@ -344,6 +420,9 @@ __device__ __forceinline__ int quant_u16(unsigned raw, int dark, int eb_int) {
 roix_status make_desc(roix_ctx* ctx, roix_dtype dtype, roix_dims dims, const roix_roi* roi,
                       const roix_eb* eb, const roix_params* prm, Desc* d);
 
+// Host: a one-item batch for the binarisation kernel alone (roix_api.cu).
+void make_threshold_batch(Batch& B, const Desc& d, const void* in, u32* T);
+
 // ------------------------------------------------------ launch functions
 struct Launch {
   cudaStream_t stream;
@@ -351,30 +430,23 @@ struct Launch {
 };
 
 // mask kernels (k_mask.cu)
-void launch_threshold(const Launch& L, const Desc& d, const void* in, u32* T);
+void launch_threshold(const Launch& L, const Batch& B);
 void launch_dilate(const Launch& L, const Desc& d, const u32* T, u32* D, u64* popcount);
-void launch_front(const Launch& L, const Desc& d, const void* in, const u32* T, int dilate,
-                  void* P, uint16_t* counts, u64 counts_cap, uint16_t* bounds, u64 bounds_cap,
-                  State* st, LookBack<2> lb, u32 rows_per_tile, u64 tiles, u64* sizes_out);
+void launch_front(const Launch& L, const Batch& B);
+size_t front_smem(u32 rpt, u64 W, int dilate);
 
 // coder kernels (k_encode.cu)
 constexpr u32 kQuantTile = 8192;  // elements per quantiser tile
+constexpr u32 kPackRange = 8;     // chunks per pack ticket
+void launch_init(const Launch& L, State* st, u32 nstates, void* zero, size_t zero_bytes);
 void launch_quantize_stage(const Launch& L, const Desc& d, const void* P, u64 n_cap,
                            const u64* n_dev, int32_t* q, u32* obits, roix_eb_info* info_out,
                            State* st);
-void launch_symbols(const Launch& L, const Desc& d, const void* P, const int32_t* q,
-                    const u32* obits, u64 n_cap, const u64* n_dev, const roix_eb_info* info_in,
-                    State* st, uint16_t* sym, u64* rk, u32* rv, u64 rec_cap,
-                    unsigned long long* hist, LookBack<1> lb);
-void launch_codebook(const Launch& L, const Desc& d, const unsigned long long* hist,
-                     uint8_t* lens_ws, u32* codes_ws, uint8_t* out, u64 cap, State* st);
-void launch_pack(const Launch& L, const Desc& d, const uint16_t* sym, const u64* n_dev,
-                 const u64* nb_dev, const uint8_t* lens_ws, const u32* codes_ws, State* st,
-                 uint8_t* out, u64 cap, LookBack<1> lb, u64 chunks_cap);
-void launch_finalize(const Launch& L, const Desc& d, State* st, const u64* n_dev,
-                     const u64* nb_dev, const roix_eb_info* info, const u64* rk, const u32* rv,
-                     u64 rec_cap, const uint16_t* counts_src, const uint16_t* bounds_src,
-                     uint8_t* out, u64 cap, u64* size_dev);
+// tiles_cap / ranges_cap: upper bounds of the batch's symbol tiles / pack ranges
+void launch_symbols(const Launch& L, const Batch& B, u64 tiles_cap);
+void launch_codebook(const Launch& L, const Batch& B);
+void launch_pack(const Launch& L, const Batch& B, u64 ranges_cap);
+void launch_finalize(const Launch& L, const Batch& B);
 
 // decoder kernels (k_decode.cu)
 struct DecodeWs {

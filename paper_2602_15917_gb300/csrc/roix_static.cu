@@ -84,7 +84,9 @@ extern "C" roix_status roix_extract_roi_static(const void* in, roix_dtype dtype,
     return ROIX_ECUDA;
   }
   u32* T = reinterpret_cast<u32*>(scratch);
-  launch_threshold(L, d, in, T);
+  static thread_local Batch B;  // kernel argument, built on the host
+  make_threshold_batch(B, d, in, T);
+  launch_threshold(L, B);
   launch_dilate(L, d, T, mask_out, (u64*)popcount_dev);
   return cudaGetLastError() == cudaSuccess ? ROIX_OK : ROIX_ECUDA;
 }

@@ -245,3 +245,58 @@ def test_deterministic_and_stream_ordered(rx):
         b = rx.compress_bytes(x, **cfg).clone()
     s.synchronize()
     assert torch.equal(a, b)
+
+
+def test_batch_equals_single_and_oracle(rx):
+    # uneven uint16 projections, one batched call; every container must be the
+    # one compress() writes alone, and the oracle's
+    sides = [37, 64, 130, 211, 96, 1, 300, 45]
+    xs = [phantom.projection(s, i, seed=7).numpy() for i, s in enumerate(sides)]
+    cfg = dict(eb=4, cmp="lt", threshold=57000, dark=100, dilate=0, fill=60100)
+    outs, sizes = rx.compress_batch([torch.from_numpy(x).cuda() for x in xs], **cfg)
+    rx.sync()
+    for x, o, sz in zip(xs, outs, sizes.cpu().numpy()):
+        got = o[:int(sz)].cpu().numpy()
+        _assert_same_container(oracle.compress(x, **cfg), got)
+
+
+def test_batch_float32_volumes_and_empty_items(rx):
+    shapes = [(9, 17, 33), (1, 1, 1), (12, 40, 64), (3, 5, 7), (20, 20, 20)]
+    xs = [phantom.ellipsoids(shape=sh, seed=i + 50).numpy() for i, sh in enumerate(shapes)]
+    xs[3][:] = -1.0  # nothing above the threshold
+    cfg = dict(eb=1e-3, eb_mode="rel", threshold=0.1, dilate=1)
+    outs, sizes = rx.compress_batch([torch.from_numpy(x).cuda() for x in xs], **cfg)
+    rx.sync()
+    for x, o, sz in zip(xs, outs, sizes.cpu().numpy()):
+        _assert_same_container(oracle.compress(x, **cfg), o[:int(sz)].cpu().numpy())
+
+
+def test_batch_more_items_than_one_group(rx):
+    xs = [phantom.projection(40 + (i % 7) * 9, i, seed=8).numpy() for i in range(70)]
+    cfg = dict(eb=2, cmp="lt", threshold=57000, dark=100, dilate=1, fill=60100)
+    outs, sizes = rx.compress_batch([torch.from_numpy(x).cuda() for x in xs], **cfg)
+    rx.sync()
+    for i in (0, 31, 63, 64, 69):
+        _assert_same_container(oracle.compress(xs[i], **cfg),
+                               outs[i][:int(sizes[i].item())].cpu().numpy())
+
+
+def test_batch_under_cuda_graph(rx):
+    xs = [torch.from_numpy(phantom.projection(s, i, seed=9).numpy()).cuda()
+          for i, s in enumerate([100, 150, 77])]
+    cfg = dict(eb=4, cmp="lt", threshold=57000, dark=100, dilate=0, fill=60100)
+    outs, sizes = rx.compress_batch(xs, **cfg)  # sizes the workspace, warms up
+    rx.sync()
+    ref = [o[:int(s)].clone() for o, s in zip(outs, sizes.cpu().numpy())]
+    for o in outs:
+        o.zero_()
+    sizes.zero_()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
+        rx.compress_batch(xs, outs=outs, sizes=sizes, stream=s, **cfg)
+    g.replay()
+    torch.cuda.synchronize()
+    rx.sync()
+    for r, o, sz in zip(ref, outs, sizes.cpu().numpy()):
+        assert torch.equal(o[:int(sz)], r)
