@@ -202,6 +202,9 @@ u32 front_rows_per_tile(const Desc& d) {
 struct ItemPlan {
   size_t ff, qf, pf, hist;  // zeroed
   size_t fa, qa, pa, T, P, sym, rk, rv, lens, codes;
+  // largest-component scratch (keep = 1): zeroed flags and counters, then data
+  size_t cf, cvars, ca, crr, cro, cxs, cxe, cpar, csize, T2;
+  u64 ctiles;
   u64 ftiles, qtiles, pchunks, pranges, rec_cap, n_cap;
   u32 rpt;
 };
@@ -239,6 +242,12 @@ BatchPlan plan_batch(const Desc& c, const roix_dims* dims, const u64* n_caps, co
     p.qf = a.take(4 * (p.qtiles + 1));
     p.pf = a.take(4 * (p.pranges + 1));
     p.hist = a.take(8 * (size_t)c.S);
+    if (c.keep) {
+      const u64 rows = dims[i].ny * dims[i].nz;
+      p.ctiles = (rows + 2047) / 2048;
+      p.cf = a.take(4 * (p.ctiles + 1));
+      p.cvars = a.take(64);  // total, best, best_root, tickets
+    }
     bp.qtiles += p.qtiles;
     bp.pranges += p.pranges;
   }
@@ -256,6 +265,20 @@ BatchPlan plan_batch(const Desc& c, const roix_dims* dims, const u64* n_caps, co
     p.rv = a.take(4 * (p.rec_cap + 1));
     p.lens = a.take(c.S + 16);
     p.codes = a.take(4 * (size_t)c.S);
+    if (c.keep) {
+      Desc di = c;
+      di.nx = dims[i].nx;
+      di.rows = rows;
+      const u64 maxr = ccl_max_runs(di);
+      p.ca = a.take(8 * 2 * (p.ctiles + 1));
+      p.crr = a.take(4 * rows + 16);
+      p.cro = a.take(8 * rows + 16);
+      p.cxs = a.take(2 * maxr + 16);
+      p.cxe = a.take(2 * maxr + 16);
+      p.cpar = a.take(4 * maxr + 16);
+      p.csize = a.take(8 * maxr + 16);
+      p.T2 = a.take(4 * rows * W + 16);
+    }
   }
   bp.total = a.take(0);
   return bp;
@@ -341,6 +364,36 @@ void roix::make_threshold_batch(Batch& B, const Desc& d, const void* in, u32* T)
 }
 
 namespace {
+
+CclWs ccl_ws(char* ws, const ItemPlan& p, u32* status) {
+  CclWs w;
+  w.row_runs = (u32*)(ws + p.crr);
+  w.row_off = (u64*)(ws + p.cro);
+  w.xs = (uint16_t*)(ws + p.cxs);
+  w.xe = (uint16_t*)(ws + p.cxe);
+  w.par = (u32*)(ws + p.cpar);
+  w.size = (unsigned long long*)(ws + p.csize);
+  w.total = (u64*)(ws + p.cvars);
+  w.best = (unsigned long long*)(ws + p.cvars + 8);
+  w.best_root = (u32*)(ws + p.cvars + 16);
+  w.ctr = (u32*)(ws + p.cvars + 20);
+  w.lb = lb_at<1>(ws, p.cf, p.ca, p.ctiles);
+  w.status = status;
+  return w;
+}
+
+bool ccl_fits(const Desc& d) { return ccl_max_runs(d) < 0xffffffffull; }
+
+Desc item_desc(const Desc& c, const Item& I) {
+  Desc d = c;
+  d.nx = I.nx;
+  d.ny = I.ny;
+  d.nz = I.nz;
+  d.rows = I.rows;
+  d.W = I.W;
+  d.N = I.N;
+  return d;
+}
 
 // Output side of a fused item: geometry written straight into the container.
 void set_container(Item& I, const Desc& c, void* out, u64 cap, u64* size_dev) {
@@ -489,21 +542,29 @@ roix_status roix_extract_roi(roix_ctx* ctx, const void* in, roix_dtype dtype, ro
   Desc d;
   roix_status s = make_desc(ctx, dtype, dims, roi, nullptr, nullptr, &d);
   if (s) return s;
-  if (d.keep) return fail(ctx, ROIX_EINVAL, "keep = largest component is not available yet");
+  if (d.keep && !ccl_fits(d)) return fail(ctx, ROIX_EINVAL, "too many rows x runs for keep = 1");
   if (d.N && (!in || !mask_out)) return fail(ctx, ROIX_EINVAL, "null buffer");
   if (!popcount_dev) return fail(ctx, ROIX_EINVAL, "null popcount_dev");
   DeviceGuard g(ctx->device);
-  Arena a;
-  a.take(sizeof(State));
-  const size_t T_off = a.take(4 * d.rows * d.W + 16);
-  if ((s = ensure_ws(ctx, a.take(0)))) return s;
+  // the mask T lives in the item plan (with the largest-component scratch)
+  const u64 ncap = 0, cap = 0;
+  Desc dp = d;
+  dp.S = 2;
+  BatchPlan bp = plan_batch(dp, &dims, &ncap, &cap, 1, true, false);
+  if ((s = ensure_ws(ctx, bp.total))) return s;
   cudaStream_t cs = (cudaStream_t)stream;
   Launch L{cs, ctx->sms};
-  u32* T = (u32*)(ctx->ws + T_off);
+  u32* T = (u32*)(ctx->ws + bp.items[0].T);
+  launch_init(L, (State*)ctx->ws, 1, ctx->ws + bp.zero_begin, bp.zero_end - bp.zero_begin);
   cudaMemsetAsync(popcount_dev, 0, 8, cs);
   static thread_local Batch B;  // 22 KB: kept off the stack
   make_threshold_batch(B, d, in, T);
   launch_threshold(L, B);
+  if (d.keep) {
+    u32* T2 = (u32*)(ctx->ws + bp.items[0].T2);
+    launch_keep_largest(L, d, T, T2, ccl_ws(ctx->ws, bp.items[0], &((State*)ctx->ws)->status));
+    T = T2;
+  }
   launch_dilate(L, d, T, mask_out, (u64*)popcount_dev);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? ROIX_OK : cuda_fail(ctx, e, "extract_roi launch");
@@ -651,6 +712,15 @@ roix_status enqueue_group(roix_ctx* ctx, const Desc& c, const roix_item* items, 
   launch_init(L, (State*)ctx->ws, n, ctx->ws + bp.zero_begin, bp.zero_end - bp.zero_begin);
   if (profile) mark(ctx, cs);
   launch_threshold(L, B);
+  if (c.keep) {  // largest component of each item's mask, then compact from that mask
+    for (u32 i = 0; i < n; ++i) {
+      Item& I = B.it[i];
+      const Desc di = item_desc(c, I);
+      launch_keep_largest(L, di, I.T, (u32*)(ctx->ws + bp.items[i].T2),
+                          ccl_ws(ctx->ws, bp.items[i], B.status));
+      I.T = (u32*)(ctx->ws + bp.items[i].T2);
+    }
+  }
   if (profile) mark(ctx, cs);
   launch_front(L, B);
   if (profile) mark(ctx, cs);
@@ -682,7 +752,7 @@ roix_status roix_compress(roix_ctx* ctx, const void* in, roix_dtype dtype, roix_
   Desc d;
   roix_status s = make_desc(ctx, dtype, dims, roi, eb, params, &d);
   if (s) return s;
-  if (d.keep) return fail(ctx, ROIX_EINVAL, "keep = largest component is not available yet");
+  if (d.keep && !ccl_fits(d)) return fail(ctx, ROIX_EINVAL, "too many rows x runs for keep = 1");
   const roix_item it{in, dims, out, cap, size_dev};
   if ((s = check_item(ctx, it, dtype))) return s;
   DeviceGuard g(ctx->device);
@@ -698,9 +768,13 @@ roix_status roix_compress_batch(roix_ctx* ctx, uint32_t n, const roix_item* item
   const roix_dims one{1, 1, 1};
   roix_status s = make_desc(ctx, dtype, one, roi, eb, params, &d);
   if (s) return s;
-  if (d.keep) return fail(ctx, ROIX_EINVAL, "keep = largest component is not available yet");
-  for (u32 i = 0; i < n; ++i)
+  for (u32 i = 0; i < n; ++i) {
     if ((s = check_item(ctx, items[i], dtype))) return s;
+    Desc di = d;
+    di.nx = items[i].dims.nx;
+    di.rows = items[i].dims.ny * items[i].dims.nz;
+    if (d.keep && !ccl_fits(di)) return fail(ctx, ROIX_EINVAL, "too many rows x runs for keep = 1");
+  }
   DeviceGuard g(ctx->device);
   for (u32 i0 = 0; i0 < n; i0 += kMaxBatch) {
     const u32 m = n - i0 < (u32)kMaxBatch ? n - i0 : (u32)kMaxBatch;

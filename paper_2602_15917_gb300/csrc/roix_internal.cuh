@@ -448,6 +448,27 @@ void launch_codebook(const Launch& L, const Batch& B);
 void launch_pack(const Launch& L, const Batch& B, u64 ranges_cap);
 void launch_finalize(const Launch& L, const Batch& B);
 
+// largest component (k_ccl.cu)
+struct CclWs {
+  u32* row_runs;              // [rows]
+  u64* row_off;               // [rows]
+  uint16_t* xs;               // [max runs]
+  uint16_t* xe;               // [max runs]
+  u32* par;                   // [max runs]
+  unsigned long long* size;   // [max runs]
+  u64* total;                 // run count
+  unsigned long long* best;   // largest size (zeroed)
+  u32* best_root;             // ~root of that component (zeroed: none)
+  LookBack<1> lb;             // scan of the run counts (flags zeroed)
+  u32* ctr;                   // scan tickets (zeroed)
+  u32* status;
+};
+// Largest connected component of the mask T (rows x W words) into `out`
+// (same layout; every word written).
+void launch_keep_largest(const Launch& L, const Desc& d, const u32* T, u32* out,
+                         const CclWs& w);
+inline u64 ccl_max_runs(const Desc& d) { return d.rows * ((d.nx + 1) / 2); }
+
 // decoder kernels (k_decode.cu)
 struct DecodeWs {
   u32* status;

@@ -300,3 +300,52 @@ def test_batch_under_cuda_graph(rx):
     rx.sync()
     for r, o, sz in zip(ref, outs, sizes.cpu().numpy()):
         assert torch.equal(o[:int(sz)], r)
+
+
+KEEP_CASES = [
+    ((7, 9, 33), 26, 0.0), ((7, 9, 33), 6, 0.0), ((12, 20, 70), 26, 0.3),
+    ((12, 20, 70), 6, -0.3), ((1, 50, 64), 26, 0.0), ((1, 50, 64), 6, 0.2),
+    ((5, 1, 200), 26, 0.0), ((9, 31, 32), 26, 0.5),
+]
+
+
+@pytest.mark.parametrize("shape,conn,thr", KEEP_CASES,
+                         ids=[f"{s}-{c}-{t}" for s, c, t in KEEP_CASES])
+def test_keep_largest_mask(rx, shape, conn, thr):
+    x = phantom.random_field(shape, seed=sum(shape) + conn, smooth=False)
+    cfg = dict(threshold=thr, keep="largest", connectivity=conn, dilate=1)
+    mask, pop = rx.extract_roi(torch.from_numpy(x).cuda(), **cfg)
+    rx.sync()
+    D = oracle.mask(x, **cfg)
+    assert np.array_equal(_unpack_mask(mask, shape), D)
+    assert int(pop.item()) == int(D.sum())
+
+
+def test_keep_largest_tie_and_empty(rx):
+    x = np.zeros((1, 12, 12), np.float32)
+    x[0, 1:3, 1:3] = 1.0
+    x[0, 8:10, 8:10] = 1.0  # same size: the first one (smallest index) is kept
+    cfg = dict(threshold=0.5, keep="largest", dilate=0)
+    mask, _ = rx.extract_roi(torch.from_numpy(x).cuda(), **cfg)
+    rx.sync()
+    assert np.array_equal(_unpack_mask(mask, x.shape), oracle.mask(x, **cfg))
+    e = np.zeros((3, 4, 40), np.float32)
+    mask, pop = rx.extract_roi(torch.from_numpy(e).cuda(), **cfg)
+    rx.sync()
+    assert int(pop.item()) == 0
+
+
+def test_keep_largest_fused_and_batch(rx):
+    xs = [phantom.ellipsoids(shape=(20, 30, 45), seed=60).numpy(),
+          phantom.random_field((6, 25, 50), seed=61, smooth=False)]
+    cfgs = [dict(eb=1e-3, threshold=0.1, keep="largest", dilate=1),
+            dict(eb=1e-2, threshold=0.4, keep="largest", connectivity=6, dilate=1)]
+    for x, cfg in zip(xs, cfgs):
+        ref, got = _compress_both(rx, x, **cfg)
+        _assert_same_container(ref, got)
+    cfg = dict(eb=4, cmp="lt", threshold=57000, dark=100, dilate=0, fill=60100, keep="largest")
+    ps = [phantom.projection(s, i, seed=10).numpy() for i, s in enumerate([90, 120, 64])]
+    outs, sizes = rx.compress_batch([torch.from_numpy(p).cuda() for p in ps], **cfg)
+    rx.sync()
+    for p, o, sz in zip(ps, outs, sizes.cpu().numpy()):
+        _assert_same_container(oracle.compress(p, **cfg), o[:int(sz)].cpu().numpy())
