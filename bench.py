@@ -245,6 +245,18 @@ def run_ours(args, rank, world, local_rank):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_total = float(t.item())
     ms_step = ms_total / args.steps
+    # latency of one step (the batch completes as a unit): events per step
+    step_ms = []
+    for _ in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(main)
+        run()
+        b.record(main)
+        b.synchronize()
+        step_ms.append(a.elapsed_time(b))
+    latency = {"p50_ms": round(float(np.percentile(step_ms, 50)), 4),
+               "p99_ms": round(float(np.percentile(step_ms, 99)), 4),
+               "of": "one step (the whole batch) from launch to completion"}
     value = in_bytes * world / (ms_step / 1e3) / 1e9
     out_bytes = int(sizes.sum().item())
 
@@ -333,6 +345,7 @@ def run_ours(args, rank, world, local_rank):
                        else "inputs smaller than L2: not flushed",
                        "parallelism": f"replicas x{world}"},
             "e2e": {k: (round(v, 2) if isinstance(v, float) else v) for k, v in e2e.items()},
+            "latency": latency,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "gpu_launches": launches_per_step * args.steps,
@@ -370,13 +383,143 @@ def cpu_baseline(args, xs, cfg, budget_s: float = None):
             "sample": f"{sample}: {i} items, {done / 1e6:.0f} MB in {dt:.1f} s"}
 
 
+# --------------------------------------------------------------- serving
+SERVE_CLASSES = [  # (share, kind, settings)
+    (0.70, "proj2048", WORKLOADS["projections64"]["cfg"]),
+    (0.25, "vol512", WORKLOADS["cube512"]["cfg"]),
+    (0.05, "vol1024", WORKLOADS["cube1024"]["cfg"]),
+]
+
+
+def run_serve(args, rank, world, local_rank):
+    """Poisson arrivals (200/s) of mixed requests from device-resident pools
+    into the continuous-batching server; latency = done - submit."""
+    import torch
+    import phantom
+    import paper_2602_15917_gb300 as roix
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    pools = {
+        "proj2048": [phantom.projection(2048, i, seed=args.seed + 1, device=dev) for i in range(16)],
+        "vol512": [phantom.porous_cylinder(512, radius=200.0, seed=args.seed + i, device=dev)
+                   for i in range(8)],
+        "vol1024": [phantom.porous_cylinder(1024, radius=400.0, seed=args.seed + i, device=dev)
+                    for i in range(4)],
+    }
+    ring = {"proj2048": 192, "vol512": 24, "vol1024": 6}
+    outs = {k: [torch.empty(pools[k][0].numel() * pools[k][0].element_size() + 65536,
+                            dtype=torch.uint8, device=dev) for _ in range(ring[k])] for k in pools}
+    free = {k: list(range(ring[k])) for k in pools}
+    torch.cuda.synchronize()
+    srv = roix.RoixServer(local_rank, hbm_budget=args.serve_budget_gb << 30, lanes=args.serve_lanes,
+                          max_batch=64)
+    rng = np.random.default_rng(args.seed)
+    shares = np.cumsum([c[0] for c in SERVE_CLASSES])
+    inflight = {}
+    lat = {k: [] for k in pools}
+    done_bytes = 0
+    first_submit, last_done = None, 0.0
+
+    def collect(block=False):
+        nonlocal done_bytes, last_done
+        got = srv.poll(1024)
+        for c in got:
+            kind, slot, nbytes = inflight.pop(c["tag"])
+            free[kind].append(slot)
+            if c["status"] != 0:
+                raise RuntimeError(f"request {c['tag']} failed with status {c['status']}")
+            lat[kind].append(c["t_done"] - c["t_submit"])
+            done_bytes += nbytes
+            last_done = max(last_done, c["t_done"])
+        return len(got)
+
+    # ---- open loop: Poisson arrivals for serve_seconds
+    t0 = time.perf_counter()
+    t_next = 0.0
+    tag = 0
+    submitted_bytes = 0
+    with Clocks(local_rank) as clk:
+        while t_next < args.serve_seconds:
+            now = time.perf_counter() - t0
+            if now < t_next:
+                collect()
+                time.sleep(min(0.0002, t_next - now))
+                continue
+            u = rng.random()
+            ci = int(np.searchsorted(shares, u, side="right"))
+            share, kind, cfg = SERVE_CLASSES[min(ci, len(SERVE_CLASSES) - 1)]
+            while not free[kind]:
+                collect()
+            slot = free[kind].pop()
+            x = pools[kind][int(rng.integers(len(pools[kind])))]
+            rc = srv.submit(tag, x, outs[kind][slot], **cfg)
+            if rc != 0:
+                raise RuntimeError(f"submit refused: {rc}")
+            nbytes = x.numel() * x.element_size()
+            inflight[tag] = (kind, slot, nbytes)
+            submitted_bytes += nbytes
+            tag += 1
+            t_next += float(rng.exponential(1.0 / args.serve_rate))
+        srv.drain(120.0)
+        while collect():
+            pass
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    open_loop = {"requests": tag, "offered_gbs": round(submitted_bytes / args.serve_seconds / 1e9, 2),
+                 "wall_s": round(wall, 2), "batches": st["batches"], "max_queue": st["max_queue"]}
+    allv = np.concatenate([np.array(v) for v in lat.values() if v]) * 1e3
+    per = {k: {"n": len(v), "p50_ms": round(float(np.percentile(np.array(v) * 1e3, 50)), 3),
+               "p99_ms": round(float(np.percentile(np.array(v) * 1e3, 99)), 3)}
+           for k, v in lat.items() if v}
+
+    # ---- closed loop: keep every ring slot busy for a few seconds (saturation)
+    for k in lat:
+        lat[k] = []
+    done_bytes = 0
+    t1 = time.perf_counter()
+    tag0 = tag
+    while time.perf_counter() - t1 < args.serve_saturate_s:
+        u = rng.random()
+        ci = int(np.searchsorted(shares, u, side="right"))
+        share, kind, cfg = SERVE_CLASSES[min(ci, len(SERVE_CLASSES) - 1)]
+        while not free[kind]:
+            collect()
+        slot = free[kind].pop()
+        x = pools[kind][int(rng.integers(len(pools[kind])))]
+        srv.submit(tag, x, outs[kind][slot], **cfg)
+        inflight[tag] = (kind, slot, x.numel() * x.element_size())
+        tag += 1
+    srv.drain(120.0)
+    while collect():
+        pass
+    sat_s = time.perf_counter() - t1
+    saturated = done_bytes / sat_s / 1e9
+    srv.close()
+    return {
+        "metric": METRIC, "value": round(saturated, 2), "unit": "GB/s", "n_gpus": world,
+        "steps": tag, "warmup": 0, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "mixed u16/f32", "data": "synthetic",
+        "config": {"workload": "serve", "desc": "Poisson arrivals %.0f/s: 70%% 2048^2 u16 "
+                   "projections, 25%% 512^3 f32, 5%% 1024^3 f32; budget %d GB, %d lanes" %
+                   (args.serve_rate, args.serve_budget_gb, args.serve_lanes),
+                   "value_is": "saturated closed-loop GB/s of input",
+                   "parallelism": f"replicas x{world}"},
+        "latency": {"p50_ms": round(float(np.percentile(allv, 50)), 3),
+                    "p99_ms": round(float(np.percentile(allv, 99)), 3), "per_class": per},
+        "open_loop": open_loop,
+        "e2e": None, "roofline": None, "cpu_baseline": None,
+        "gpu_launches": None, "clocks": clk.summary(),
+    }
+
+
 # ---------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
     if rank != 0:
         return None
     import torch
-    wl = WORKLOADS[args.workload]
-    xs = make_inputs(args.workload, "cpu", seed=args.seed)
+    name = "projections64" if args.workload == "serve" else args.workload
+    wl = WORKLOADS[name]
+    xs = make_inputs(name, "cpu", seed=args.seed)
     per_step = max(1.0, args.cpu_budget / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
         cpu_baseline(args, xs, wl["cfg"], budget_s=per_step)
@@ -404,7 +547,12 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="projections64", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="projections64", choices=sorted(WORKLOADS) + ["serve"])
+    ap.add_argument("--serve-seconds", type=float, default=15.0)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-budget-gb", type=int, default=120)
+    ap.add_argument("--serve-lanes", type=int, default=4)
+    ap.add_argument("--serve-saturate-s", type=float, default=5.0)
     ap.add_argument("--streams", type=int, default=8)
     ap.add_argument("--path", default="batch", choices=["batch", "plain"])
     ap.add_argument("--graph", type=int, default=1)
@@ -424,7 +572,8 @@ def main():
             import torch.distributed as dist
             torch.cuda.set_device(local_rank)
             dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-        res = run_ours(args, rank, world, local_rank)
+        res = (run_serve(args, rank, world, local_rank) if args.workload == "serve"
+               else run_ours(args, rank, world, local_rank))
         if world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()

@@ -105,6 +105,7 @@ typedef struct {
 } roix_eb_info;
 
 typedef struct roix_ctx roix_ctx;
+typedef struct roix_server roix_server;
 
 /* ----------------------------------------------------------- context */
 roix_status roix_ctx_create(int device, roix_ctx** out);
@@ -225,6 +226,59 @@ typedef struct {
 roix_status roix_compress_batch(roix_ctx* ctx, uint32_t n, const roix_item* items,
                                 roix_dtype dtype, const roix_roi* roi, const roix_eb* eb,
                                 const roix_params* params, void* stream);
+
+/* --------------------------------------------------------------- serving
+ * A serving loop for compression requests that arrive over time (no paper
+ * counterpart; a deployment form of roix_compress_batch). The server holds
+ * `lanes` contexts, each with its own stream and a workspace of
+ * hbm_budget / lanes bytes reserved at creation: the device state (masks,
+ * pixel sections, symbols, records, code tables) of the requests it admits.
+ * A scheduler thread batches continuously: when a lane is free, the oldest
+ * pending request opens a batch and later pending requests with the same
+ * dtype and settings join it, in arrival order, while the batch has fewer
+ * than max_batch items and its workspace fits the lane. Batches on different
+ * lanes run concurrently. Each request's container is the one roix_compress
+ * writes for it alone. Requests reference caller-owned device buffers that
+ * must stay valid until their completion is polled. */
+typedef struct {
+  uint64_t hbm_budget;  /* bytes of workspace over all lanes */
+  uint32_t lanes;       /* batches in flight at once (>= 1) */
+  uint32_t max_batch;   /* requests per batch, 1..64 */
+} roix_server_config;
+
+typedef struct {
+  uint64_t tag;         /* returned in the completion */
+  const void* in;
+  roix_dtype dtype;
+  roix_dims dims;
+  roix_roi roi;
+  roix_eb eb;
+  roix_params params;
+  void* out;            /* container buffer, 16-byte aligned */
+  uint64_t cap;
+} roix_request;
+
+typedef struct {
+  uint64_t tag;
+  int32_t status;       /* roix_status of the request */
+  uint64_t size;        /* container size (bytes) */
+  double t_submit, t_admit, t_done;  /* seconds since the server was created */
+} roix_completion;
+
+typedef struct {
+  uint64_t submitted, completed, batches, bytes_in, max_queue, pending, lane_bytes;
+} roix_server_stats;
+
+roix_status roix_server_create(int device, const roix_server_config* cfg, roix_server** out);
+/* Thread-safe. ROIX_ENOMEM: the request alone does not fit one lane. */
+roix_status roix_server_submit(roix_server* s, const roix_request* req);
+/* Non-blocking: moves up to `max` completions to `out`, returns how many. */
+uint32_t roix_server_poll(roix_server* s, roix_completion* out, uint32_t max);
+/* Waits until every submitted request has completed (ROIX_ETIMEOUT otherwise). */
+roix_status roix_server_drain(roix_server* s, double timeout_s);
+roix_status roix_server_get_stats(roix_server* s, roix_server_stats* out);
+/* Finishes the pending requests, then releases the lanes. */
+roix_status roix_server_destroy(roix_server* s);
 
 /* The fused path: the same bytes as the four stages, in fewer passes. */
 roix_status roix_compress(roix_ctx* ctx, const void* in, roix_dtype dtype, roix_dims dims,

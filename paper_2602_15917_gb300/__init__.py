@@ -58,6 +58,27 @@ class Item(C.Structure):
                 ("size_dev", C.c_void_p)]
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [("hbm_budget", C.c_uint64), ("lanes", C.c_uint32), ("max_batch", C.c_uint32)]
+
+
+class Request(C.Structure):
+    _fields_ = [("tag", C.c_uint64), ("in_", C.c_void_p), ("dtype", C.c_int32), ("dims", Dims),
+                ("roi", Roi), ("eb", Eb), ("params", Params), ("out", C.c_void_p),
+                ("cap", C.c_uint64)]
+
+
+class Completion(C.Structure):
+    _fields_ = [("tag", C.c_uint64), ("status", C.c_int32), ("size", C.c_uint64),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("batches", C.c_uint64),
+                ("bytes_in", C.c_uint64), ("max_queue", C.c_uint64), ("pending", C.c_uint64),
+                ("lane_bytes", C.c_uint64)]
+
+
 class EbInfo(C.Structure):
     _fields_ = [("eb_abs", C.c_double), ("vmin", C.c_double), ("vmax", C.c_double),
                 ("two_eb", C.c_float), ("inv2eb", C.c_float), ("bound", C.c_float),
@@ -99,6 +120,12 @@ def lib():
                 "roix_profile_read": (C.c_int, [P, C.POINTER(C.c_float), C.c_int]),
                 "roix_extract_roi_static": (st, [P, i32, D, R, P, P, P]),
                 "roix_compress_batch": (st, [P, C.c_uint32, C.POINTER(Item), i32, R, E, PR, P]),
+                "roix_server_create": (st, [i32, C.POINTER(ServerConfig), C.POINTER(P)]),
+                "roix_server_submit": (st, [P, C.POINTER(Request)]),
+                "roix_server_poll": (C.c_uint32, [P, C.POINTER(Completion), C.c_uint32]),
+                "roix_server_drain": (st, [P, C.c_double]),
+                "roix_server_get_stats": (st, [P, C.POINTER(ServerStats)]),
+                "roix_server_destroy": (st, [P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -114,7 +141,9 @@ def symbols():
             "roix_sync", "roix_last_error", "roix_status_string", "roix_mask_words",
             "roix_compress_bound", "roix_extract_roi", "roix_compact", "roix_quantize",
             "roix_encode", "roix_decode", "roix_compress", "roix_profile",
-            "roix_profile_read", "roix_extract_roi_static", "roix_compress_batch"]
+            "roix_profile_read", "roix_extract_roi_static", "roix_compress_batch",
+            "roix_server_create", "roix_server_submit", "roix_server_poll", "roix_server_drain",
+            "roix_server_get_stats", "roix_server_destroy"]
 
 
 def _dtype_code(t: torch.Tensor) -> int:
@@ -326,3 +355,53 @@ class Roix:
             C.byref(eb_of(**cfg)), C.byref(params_of(**cfg)), out.data_ptr(), int(cap),
             size.data_ptr(), _stream(stream)))
         return out, size
+
+
+class RoixServer:
+    """Continuous-batching compression server on one GPU (roix_server_*).
+    Inputs and outputs are caller-owned device tensors that must stay alive
+    until their completion has been polled."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 8 << 30, lanes: int = 4,
+                 max_batch: int = 64):
+        self.L = lib()
+        h = C.c_void_p()
+        cfg = ServerConfig(int(hbm_budget), int(lanes), int(max_batch))
+        rc = self.L.roix_server_create(int(device), C.byref(cfg), C.byref(h))
+        if rc != 0:
+            raise RoixError(rc, "server create")
+        self.h = h
+
+    def submit(self, tag: int, x: torch.Tensor, out: torch.Tensor, cap: int | None = None,
+               **cfg) -> int:
+        """Returns the status (0 = queued)."""
+        r = Request(int(tag), x.data_ptr(), _dtype_code(x), dims_of(x.shape), roi_of(**cfg),
+                    eb_of(**cfg), params_of(**cfg), out.data_ptr(),
+                    int(out.numel() if cap is None else cap))
+        return int(self.L.roix_server_submit(self.h, C.byref(r)))
+
+    def poll(self, max_n: int = 256):
+        buf = (Completion * max_n)()
+        k = self.L.roix_server_poll(self.h, buf, max_n)
+        return [dict(tag=buf[i].tag, status=buf[i].status, size=buf[i].size,
+                     t_submit=buf[i].t_submit, t_admit=buf[i].t_admit, t_done=buf[i].t_done)
+                for i in range(k)]
+
+    def drain(self, timeout_s: float = 60.0) -> int:
+        return int(self.L.roix_server_drain(self.h, float(timeout_s)))
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        self.L.roix_server_get_stats(self.h, C.byref(st))
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.roix_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

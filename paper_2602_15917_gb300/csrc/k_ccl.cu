@@ -202,7 +202,18 @@ __global__ void __launch_bounds__(kThreads) k_run_union(Desc d, const u64* __res
   }
 }
 
-// ---- 5. flatten, sizes per root
+// ---- 5. flatten, sizes per root. The forest no longer changes, so the walk
+// to the root only reads; the single write par[i] = root is thread i's own
+// (a path-halving store here could overwrite it with a non-root ancestor).
+__device__ __forceinline__ u32 find_root_ro(const u32* par, u32 x) {
+  u32 p = __ldcg(par + x);
+  while (p != x) {
+    x = p;
+    p = __ldcg(par + x);
+  }
+  return x;
+}
+
 __global__ void __launch_bounds__(kThreads) k_run_sizes(const u64* total, u32* par,
                                                         const uint16_t* __restrict__ xs,
                                                         const uint16_t* __restrict__ xe,
@@ -210,7 +221,7 @@ __global__ void __launch_bounds__(kThreads) k_run_sizes(const u64* total, u32* p
   const u64 n = *total;
   for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (u64)gridDim.x * blockDim.x) {
-    const u32 root = find_root(par, (u32)i);
+    const u32 root = find_root_ro(par, (u32)i);
     par[i] = root;
     atomicAdd(size + root, (unsigned long long)(xe[i] - xs[i]));
   }

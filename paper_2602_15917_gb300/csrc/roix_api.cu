@@ -11,20 +11,6 @@
 
 using namespace roix;
 
-struct roix_ctx {
-  int device = 0;
-  int sms = 0;
-  char* ws = nullptr;
-  size_t ws_bytes = 0;
-  u32 pending = 0;  // status carried over a workspace reallocation
-  std::string err;
-  // per-stage timing (profiling mode)
-  int profile = 0;
-  cudaEvent_t ev[16] = {};
-  int nev = 0;
-  float stage_ms[16] = {};
-  int stage_count = 0;
-};
 
 namespace {
 
@@ -65,7 +51,9 @@ struct Arena {
 constexpr size_t kStateBytes = 256;
 static_assert(sizeof(State) <= kStateBytes, "state fits its slot");
 
-roix_status ensure_ws(roix_ctx* ctx, size_t bytes) {
+}  // namespace
+
+roix_status roix::ensure_ws(roix_ctx* ctx, size_t bytes, bool exact) {
   if (bytes <= ctx->ws_bytes) return ROIX_OK;
   if (ctx->ws) {
     // keep an unread device status across the reallocation
@@ -77,7 +65,7 @@ roix_status ensure_ws(roix_ctx* ctx, size_t bytes) {
     ctx->ws = nullptr;
     ctx->ws_bytes = 0;
   }
-  size_t want = bytes + (bytes >> 3);  // 12.5 % headroom against regrowth
+  size_t want = exact ? bytes : bytes + (bytes >> 3);  // headroom against regrowth
   cudaError_t e = cudaMalloc(&ctx->ws, want);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -93,6 +81,8 @@ roix_status ensure_ws(roix_ctx* ctx, size_t bytes) {
   cudaMemset(ctx->ws, 0, kStateBytes);
   return ROIX_OK;
 }
+
+namespace {
 
 // ----------------------------------------------------------- parameters
 float f32_round_down(double t) {
@@ -468,7 +458,7 @@ roix_status roix_ctx_destroy(roix_ctx* ctx) {
 roix_status roix_reserve(roix_ctx* ctx, size_t bytes) {
   if (!ctx) return ROIX_EINVAL;
   DeviceGuard g(ctx->device);
-  return ensure_ws(ctx, bytes < kStateBytes ? kStateBytes : bytes);
+  return ensure_ws(ctx, bytes < kStateBytes ? kStateBytes : bytes, true);
 }
 
 const char* roix_last_error(const roix_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
@@ -683,6 +673,10 @@ roix_status roix_encode(roix_ctx* ctx, const int32_t* q, const uint32_t* outlier
   return e == cudaSuccess ? ROIX_OK : cuda_fail(ctx, e, "encode launch");
 }
 
+}  // extern "C"
+
+namespace {
+
 // The fused path for one group of at most kMaxBatch items sharing `c`.
 roix_status enqueue_group(roix_ctx* ctx, const Desc& c, const roix_item* items, u32 n,
                           cudaStream_t cs, bool profile) {
@@ -736,6 +730,21 @@ roix_status enqueue_group(roix_ctx* ctx, const Desc& c, const roix_item* items, 
   return e == cudaSuccess ? ROIX_OK : cuda_fail(ctx, e, "compress launch");
 }
 
+}  // namespace
+
+size_t roix::batch_workspace(const Desc& c, const roix_item* items, u32 n) {
+  std::vector<roix_dims> dims(n);
+  std::vector<u64> ncaps(n), caps(n);
+  for (u32 i = 0; i < n; ++i) {
+    dims[i] = items[i].dims;
+    ncaps[i] = items[i].dims.nx * items[i].dims.ny * items[i].dims.nz;
+    caps[i] = items[i].cap;
+  }
+  return plan_batch(c, dims.data(), ncaps.data(), caps.data(), n, true, true).total;
+}
+
+namespace {
+
 roix_status check_item(roix_ctx* ctx, const roix_item& it, roix_dtype dtype) {
   if (!dims_ok(it.dims)) return fail(ctx, ROIX_EINVAL, "dims: nx <= 65534, ny, nz < 2^32");
   const u64 N = it.dims.nx * it.dims.ny * it.dims.nz;
@@ -744,6 +753,10 @@ roix_status check_item(roix_ctx* ctx, const roix_item& it, roix_dtype dtype) {
   if (!aligned(it.in, dtype == ROIX_F32 ? 4 : 2)) return fail(ctx, ROIX_EINVAL, "misaligned input");
   return ROIX_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 roix_status roix_compress(roix_ctx* ctx, const void* in, roix_dtype dtype, roix_dims dims,
                           const roix_roi* roi, const roix_eb* eb, const roix_params* params,

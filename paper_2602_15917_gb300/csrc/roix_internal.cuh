@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "roix.h"
 
 namespace roix {
@@ -415,6 +417,28 @@ __device__ __forceinline__ int quant_u16(unsigned raw, int dark, int eb_int) {
   int num = v + eb_int, den = 2 * eb_int;
   return num >= 0 ? num / den : -((-num + den - 1) / den);
 }
+
+}  // namespace roix
+
+// A context: device, workspace, status carry-over, profiling events.
+struct roix_ctx {
+  int device = 0;
+  int sms = 0;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  roix::u32 pending = 0;  // status carried over a workspace reallocation
+  std::string err;
+  int profile = 0;        // per-stage events in the fused path
+  cudaEvent_t ev[16] = {};
+  int nev = 0;
+};
+
+namespace roix {
+
+// Host: grows the context workspace (synchronises the device); exact = no headroom.
+roix_status ensure_ws(roix_ctx* ctx, size_t bytes, bool exact = false);
+// Host: workspace bytes of one fused group of items sharing the settings `c`.
+size_t batch_workspace(const Desc& c, const roix_item* items, u32 n);
 
 // Host: argument checks and descriptor (roix_api.cu); ctx may be null.
 roix_status make_desc(roix_ctx* ctx, roix_dtype dtype, roix_dims dims, const roix_roi* roi,

@@ -72,3 +72,15 @@ def test_ctx_create_without_gpu_fails_cleanly(libpath):
     assert roix.lib().roix_ctx_create(0, C.byref(h)) == 6  # ROIX_ECUDA
     with pytest.raises(roix.RoixError):
         roix.Roix(0)
+
+
+def test_server_create_without_gpu_fails_cleanly(libpath):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import paper_2602_15917_gb300 as roix
+    with pytest.raises(roix.RoixError):
+        roix.RoixServer(0, hbm_budget=1 << 30, lanes=2)
+    h = C.c_void_p()
+    bad = roix.ServerConfig(1 << 30, 0, 8)  # no lanes
+    assert roix.lib().roix_server_create(0, C.byref(bad), C.byref(h)) == 1

@@ -349,3 +349,17 @@ def test_keep_largest_fused_and_batch(rx):
     rx.sync()
     for p, o, sz in zip(ps, outs, sizes.cpu().numpy()):
         _assert_same_container(oracle.compress(p, **cfg), o[:int(sz)].cpu().numpy())
+
+
+def test_keep_largest_repeatable(rx):
+    # many small components near the percolation threshold: every run must
+    # land on its final root, call after call
+    x = phantom.random_field((10, 40, 90), seed=77, smooth=False)
+    cfg = dict(threshold=0.4, keep="largest", connectivity=6, dilate=0)
+    D = oracle.mask(x, **cfg)
+    xt = torch.from_numpy(x).cuda()
+    for _ in range(20):
+        mask, pop = rx.extract_roi(xt, **cfg)
+        rx.sync()
+        assert int(pop.item()) == int(D.sum())
+        assert np.array_equal(_unpack_mask(mask, x.shape), D)
