@@ -83,6 +83,7 @@ struct Src {
   const u32* obits;
   roix_eb_info e;
   int dark;
+  FastDiv fd;  // division by 2 * eb_int (uint16 path)
   struct R {
     TV x;
     int q;
@@ -127,7 +128,7 @@ struct Src {
       return quant_f32(r.x, e, out);
     } else {
       out = false;
-      return quant_u16(r.x, dark, e.eb_int);
+      return quant_u16_fd(r.x, dark, e.eb_int, fd);
     }
   }
   __device__ __forceinline__ int code(u64 k, bool& out) const { return eval(load1(k), out); }
@@ -223,7 +224,10 @@ __global__ void __launch_bounds__(kThreads) k_symbols(const __grid_constant__ Ba
       src.q = I.q;
       src.obits = I.obits;
       src.dark = d.dark;
-      if constexpr (!FROM_Q) src.e = make_eb(d, I.st->vmin_key, I.st->vmax_key);
+      if constexpr (!FROM_Q) {
+        src.e = make_eb(d, I.st->vmin_key, I.st->vmax_key);
+        src.fd = FastDiv(2u * (u32)src.e.eb_int);
+      }
       n = umin(I.sizes[0], I.N);
       __syncthreads();
     }
@@ -358,17 +362,32 @@ __host__ __device__ __forceinline__ u32 next_pow2(u32 v) {
   return p;
 }
 
+// leaves-per-depth entries: depths up to m - 1 < S while building, and the
+// lengths 0..kLMax + 1 when they are summed
+__host__ __device__ __forceinline__ u32 bl_entries(u32 S) {
+  return S + 2 > kLMax + 2 ? S + 2 : kLMax + 2;
+}
+
 size_t codebook_smem(u32 S) {
   return (size_t)next_pow2(S) * 8  // key (sorted with a power-of-two bitonic network)
          + (size_t)S * 8      // internal weights
          + (size_t)2 * S * 4  // parent / ancestor
          + (size_t)2 * S * 4  // depth
-         + (size_t)(S + 2) * 4  // leaves per depth
+         + (size_t)bl_entries(S) * 4  // leaves per depth
          + (size_t)S;         // lengths
 }
 
+#ifdef ROIX_CB_PROBE
+__device__ long long g_cb_probe[16];
+#define CB_MARK(i) \
+  if (threadIdx.x == 0 && blockIdx.x == 0) g_cb_probe[i] = clock64();
+#else
+#define CB_MARK(i)
+#endif
+
 __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__ Batch B) {
   extern __shared__ __align__(16) unsigned char cb_smem[];
+  CB_MARK(0)
   const Item& I = B.it[blockIdx.x];
   const unsigned long long* hist = I.hist;
   uint8_t* lens_ws = I.lens;
@@ -380,8 +399,8 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__
   u64* wint = key + next_pow2(S);                 // [S] internal node weights
   int32_t* par = (int32_t*)(wint + S);            // [2S]
   int32_t* dep = par + 2 * S;                     // [2S]
-  u32* bl = (u32*)(dep + 2 * S);                  // [S + 2]
-  uint8_t* len = (uint8_t*)(bl + S + 2);          // [S]
+  u32* bl = (u32*)(dep + 2 * S);                  // [bl_entries(S)]
+  uint8_t* len = (uint8_t*)(bl + bl_entries(S));  // [S]
   __shared__ u32 scratch[40];
   __shared__ u32 s_maxl, s_next[kLMax + 2], s_cum[kLMax + 2];
   const int tid = threadIdx.x;
@@ -396,12 +415,26 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__
     m += tot;
   }
   for (u32 s = tid; s < S; s += kCbThreads) len[s] = 0;
-  for (u32 i = tid; i < S + 2; i += kCbThreads) bl[i] = 0;
+  for (u32 i = tid; i < bl_entries(S); i += kCbThreads) bl[i] = 0;
   u32 M = 1;
   while (M < m) M <<= 1;
   for (u32 i = m + tid; i < M; i += kCbThreads) key[i] = ~0ull;
   __syncthreads();
-  bitonic_sort(key, M);  // ascending (count, symbol)
+  CB_MARK(1)
+  if (m <= (u32)kCbThreads) {
+    // rank of each (count, symbol) key among the m distinct keys: one key per
+    // thread, every thread reads the keys in the same order (smem broadcast)
+    u64 mine = tid < (int)m ? key[tid] : 0ull;
+    u32 rank = 0;
+    if (tid < (int)m)  // only the warps holding keys read them
+      for (u32 j = 0; j < m; ++j) rank += key[j] < mine;
+    __syncthreads();
+    if (tid < (int)m) key[rank] = mine;
+    __syncthreads();
+  } else {
+    bitonic_sort(key, M);  // ascending (count, symbol)
+  }
+  CB_MARK(2)
   if (m == 1) {
     if (tid == 0) {
       len[key[0] & 0xffffu] = 1;
@@ -416,6 +449,7 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__
       constexpr u64 kNone = ~0ull;
       u32 lf = 0, in = 0, created = 0;
       u64 wl = key[0] >> 16, wi = kNone;
+      u64 wl_next = m > 1 ? (key[1] >> 16) : kNone;  // the leaf after the front, prefetched
       for (u32 t = 0; t + 1 < m; ++t) {
         int32_t pa, pb;
         u64 wa, wb;
@@ -423,7 +457,8 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__
           pa = (int32_t)lf;
           wa = wl;
           ++lf;
-          wl = lf < m ? (key[lf] >> 16) : kNone;
+          wl = wl_next;
+          wl_next = lf + 1 < m ? (key[lf + 1] >> 16) : kNone;
         } else {
           pa = (int32_t)(m + in);
           wa = wi;
@@ -434,7 +469,8 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__
           pb = (int32_t)lf;
           wb = wl;
           ++lf;
-          wl = lf < m ? (key[lf] >> 16) : kNone;
+          wl = wl_next;
+          wl_next = lf + 1 < m ? (key[lf + 1] >> 16) : kNone;
         } else {
           pb = (int32_t)(m + in);
           wb = wi;
@@ -451,6 +487,7 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__
       par[2 * m - 2] = -1;
     }
     __syncthreads();
+    CB_MARK(3)
     // depth = distance to the root, by pointer jumping
     const u32 nodes = 2 * m - 1;
     for (u32 i = tid; i < nodes; i += kCbThreads) dep[i] = par[i] >= 0 ? 1 : 0;
@@ -472,6 +509,7 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__
       }
       __syncthreads();
     }
+    CB_MARK(4)
     if (tid == 0) s_maxl = 0;
     __syncthreads();
     for (u32 i = tid; i < m; i += kCbThreads) {
@@ -518,23 +556,45 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__
     }
   }
   __syncthreads();
-  // canonical order: sort used symbols by (length, symbol)
-  for (u32 i = tid; i < m; i += kCbThreads) {
-    const u32 s = (u32)(key[i] & 0xffffu);
-    key[i] = ((u64)len[s] << 16) | s;
+  CB_MARK(5)
+  // canonical codes: code = first code of its length + rank of the symbol
+  // among the symbols of that length. Ranks in symbol order, chunk by chunk of
+  // kCbThreads symbols: lanes of equal length found with __match_any_sync,
+  // per-warp counts per length scanned across warps, carried across chunks.
+  {
+    __shared__ u32 wcnt[32][kLMax + 1];  // per warp and length: count, then offset
+    __shared__ u32 s_carry[kLMax + 1];
+    if (tid <= (int)kLMax) s_carry[tid] = 0;
+    const int lane = tid & 31, warp = tid >> 5;
+    for (u32 c0 = 0; c0 < S; c0 += kCbThreads) {
+      for (u32 i = tid; i < 32 * (kLMax + 1); i += kCbThreads) (&wcnt[0][0])[i] = 0u;
+      __syncthreads();
+      const u32 s = c0 + tid;
+      const u32 l = s < S ? len[s] : 0u;
+      const u32 same = __match_any_sync(0xffffffffu, l);
+      const u32 below = __popc(same & ((1u << lane) - 1u));
+      if (lane == __ffs(same) - 1) wcnt[warp][l] = __popc(same);
+      __syncthreads();
+      if (tid <= (int)kLMax) {  // exclusive scan over warps, one thread per length
+        u32 acc = s_carry[tid];
+        for (int w = 0; w < 32; ++w) {
+          const u32 present = wcnt[w][tid];
+          wcnt[w][tid] = acc;
+          acc += present;
+        }
+        s_carry[tid] = acc;
+      }
+      __syncthreads();
+      if (s < S) codes_ws[s] = l ? s_next[l] + wcnt[warp][l] + below : 0u;
+      __syncthreads();
+    }
   }
-  __syncthreads();
-  bitonic_sort(key, M);
-  for (u32 s = tid; s < S; s += kCbThreads) codes_ws[s] = 0;
-  __syncthreads();
-  for (u32 i = tid; i < m; i += kCbThreads) {
-    const u32 l = (u32)(key[i] >> 16), s = (u32)(key[i] & 0xffffu);
-    codes_ws[s] = s_next[l] + (i - s_cum[l - 1]);
-  }
+  CB_MARK(6)
   for (u32 s = tid; s < S; s += kCbThreads) {
     lens_ws[s] = len[s];
     if (kHeaderBytes + s < cap) out[kHeaderBytes + s] = len[s];
   }
+  CB_MARK(7)
 }
 
 // ------------------------------------------------------------------- pack

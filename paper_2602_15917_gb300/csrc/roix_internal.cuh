@@ -203,7 +203,7 @@ __device__ T block_excl_scan(T v, T* scratch, T* total) {
 // and shifts (Granlund & Montgomery 1994, round-up method).
 struct FastDiv {
   u32 d, m, s;
-  __host__ __device__ explicit FastDiv(u32 div = 1) : d(div ? div : 1), m(0), s(0) {
+  __host__ __device__ FastDiv(u32 div = 1) : d(div ? div : 1), m(0), s(0) {
     u32 l = 0;
     while ((1ull << l) < d) ++l;
     s = l;
@@ -215,6 +215,14 @@ struct FastDiv {
     return (t + ((n - t) >> 1)) >> (s - 1);
   }
 };
+
+__device__ __forceinline__ int quant_u16_fd(unsigned raw, int dark, int eb_int,
+                                            const FastDiv& fd) {
+  const int v = (int)raw - dark;  // in [-65535, 65535]
+  if (eb_int == 0) return v;
+  const int num = v + eb_int;
+  return num >= 0 ? (int)fd.div((u32)num) : -(int)fd.div((u32)(-num + 2 * eb_int - 1));
+}
 
 // ------------------------------------------------------- ordered float keys
 // Monotone map of binary32 bit patterns to uint32 (for atomicMin/Max).
@@ -417,6 +425,9 @@ __device__ __forceinline__ int quant_u16(unsigned raw, int dark, int eb_int) {
   int num = v + eb_int, den = 2 * eb_int;
   return num >= 0 ? num / den : -((-num + den - 1) / den);
 }
+// Same value with the division by 2*eb_int done by `fd` (a FastDiv of it).
+__device__ __forceinline__ int quant_u16_fd(unsigned raw, int dark, int eb_int,
+                                            const struct FastDiv& fd);
 
 }  // namespace roix
 
