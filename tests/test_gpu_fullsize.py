@@ -1,0 +1,101 @@
+"""Parity at the benchmark's full sizes, in the launch configuration bench.py
+times (batched call, device-resident inputs).
+
+* 64 uint16 projections (512^2 .. 2048^2): every container equals the
+  oracle's, byte for byte.
+* 1024^3 float32 porous cylinder, relative bound 1e-4: too large for the
+  oracle as a whole, so (a) properties that hold at any size are checked on
+  all voxels: the decoded values lie within E_abs of the input on retained
+  voxels and equal the fill elsewhere; the retained set equals threshold +
+  3x3x3 dilation recomputed with torch.max_pool3d; and (b) sampled rows are
+  recomputed by the oracle from their 3x3 neighbourhood of input rows: mask,
+  row geometry and dequantised values must match exactly.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import phantom
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2602_15917_gb300 as roix
+    r = roix.Roix(0)
+    yield r
+    r.close()
+
+
+def test_projections64_batch_equals_oracle(rx):
+    cfg = dict(eb=4, eb_mode="abs", cmp="lt", threshold=57000, dark=100, dilate=0,
+               fill=60100, radius=512, chunk=4096)
+    xs = [phantom.projection(s, i, seed=0, device="cuda")
+          for i, s in enumerate(phantom.projection_sides(64, 512, 2048, 0))]
+    outs, sizes = rx.compress_batch(xs, **cfg)
+    rx.sync()
+    for x, o, sz in zip(xs, outs, sizes.cpu().numpy()):
+        ref = oracle.compress(x.cpu().numpy(), **cfg)
+        got = o[:int(sz)].cpu().numpy()
+        assert got.size == ref.size and np.array_equal(got, ref)
+
+
+def _row_from_container(buf: np.ndarray, hdr: dict, row: int):
+    counts = np.frombuffer(buf[hdr["off_counts"]:hdr["off_counts"] + 2 * (hdr["ny"] * hdr["nz"])],
+                           np.uint16)
+    b0 = int(counts[:row].astype(np.int64).sum())
+    return buf[hdr["off_bounds"] + 2 * b0: hdr["off_bounds"] + 2 * (b0 + int(counts[row]))].view(
+        np.uint16)
+
+
+def test_cube1024_properties_and_sampled_rows(rx):
+    n = 1024
+    cfg = dict(eb=1e-4, eb_mode="rel", cmp="gt", threshold=0.1, dilate=1, fill=0.0,
+               radius=512, chunk=4096)
+    x = phantom.porous_cylinder(n, radius=400.0, seed=0, device="cuda")
+    outs, sizes = rx.compress_batch([x], **cfg)
+    rx.sync()
+    buf_d = outs[0][:int(sizes[0].item())]
+    buf = buf_d.cpu().numpy()
+    hdr = oracle.header(buf)
+    y = rx.decode(buf_d, x.shape, torch.float32)
+    rx.sync()
+    # (a) properties on every voxel
+    T = (x > 0.1).float()[None, None]
+    D = torch.nn.functional.max_pool3d(T, 3, stride=1, padding=1)[0, 0] > 0
+    assert int(D.sum().item()) == hdr["n"]
+    eb = hdr["eb_abs"]
+    finite = torch.isfinite(x)
+    xr, yr = x[D & finite].double(), y[D & finite].double()
+    assert float((xr - yr).abs().max().item()) <= eb
+    assert bool((y[~D] == 0).all().item())
+    # the range the relative bound was taken from
+    assert hdr["vmin"] == float(x[D].min().item()) and hdr["vmax"] == float(x[D].max().item())
+    # (b) sampled rows against the oracle
+    rng = np.random.default_rng(5)
+    zs = rng.integers(280, 744, 40)  # inside the cylinder's slab, plus a few outside
+    zs[:4] = [0, 100, 900, 1023]
+    ys = rng.integers(0, n, 40)
+    xc = x.cpu()
+    yc = y.cpu()
+    for z, yy in zip(zs.tolist(), ys.tolist()):
+        z0, z1 = max(0, z - 1), min(n, z + 2)
+        y0, y1 = max(0, yy - 1), min(n, yy + 2)
+        block = xc[z0:z1, y0:y1].numpy()
+        Dm = oracle.mask(block, **cfg)[z - z0, yy - y0]
+        P, counts, bounds = oracle.compact(xc[z:z + 1, yy:yy + 1].numpy(), Dm[None, None])
+        got_b = _row_from_container(buf, hdr, z * n + yy)
+        assert np.array_equal(got_b, bounds)
+        e = oracle.Eb()
+        e.eb_abs, e.two_eb, e.inv2eb, e.bound, e.eb_int = (hdr["eb_abs"], hdr["two_eb"],
+                                                          hdr["inv2eb"], hdr["bound"], 0)
+        q, o = oracle.quantize(P, e)
+        want = np.where(o.astype(bool), P, (q.astype(np.float32) * np.float32(hdr["two_eb"])))
+        assert np.array_equal(yc[z, yy].numpy()[Dm.astype(bool)].view(np.uint32),
+                              want.astype(np.float32).view(np.uint32))
