@@ -24,7 +24,7 @@ _OUT = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-F32, U16 = 1, 2
+F32, U16, U8 = 1, 2, 3
 HEADER_BYTES = 256
 LMAX = 24
 
@@ -80,6 +80,12 @@ def lib():
             L.oracle_free.argtypes = [P]
             L.oracle_free.restype = None
             L.oracle_decode.argtypes = [P, u64, P, i32, u64, u64, u64]
+            L.oracle_normalize8.argtypes = [P, i32, u64, d, P]
+            L.oracle_normalize8.restype = d
+            L.oracle_greedy_seq.argtypes = [P, u64, d, P]
+            L.oracle_greedy_seq.restype = None
+            L.oracle_greedy_rows.argtypes = [P, P, u64, u64, u64, d, P]
+            L.oracle_greedy_rows.restype = u64
             _lib = L
     return _lib
 
@@ -103,7 +109,9 @@ def _dtype_code(x: np.ndarray) -> int:
         return F32
     if x.dtype == np.uint16:
         return U16
-    raise TypeError("float32 or uint16 input")
+    if x.dtype == np.uint8:
+        return U8
+    raise TypeError("float32, uint16 or uint8 input")
 
 
 def params(dtype: int, eb=1e-3, eb_mode="abs", cmp="gt", threshold=0.1, keep="all",
@@ -265,3 +273,31 @@ def header(buf: np.ndarray) -> dict:
                 off_counts=f(160, "<u8"), off_bounds=f(168, "<u8"), off_outk=f(176, "<u8"),
                 off_outv=f(184, "<u8"), off_chunks=f(192, "<u8"), off_payload=f(200, "<u8"),
                 total=f(208, "<u8"))
+
+
+# ------------------------------------------ the paper's 8-bit quantiser path
+def normalize8(x: np.ndarray, dark: float = 0.0):
+    """Sec. 4.1.2: 8-bit image I_n = round(v / I_max * 255); returns (I_n, I_max)."""
+    x = np.ascontiguousarray(x)
+    if x.dtype == np.uint8:
+        raise TypeError("float32 or uint16 input")
+    out = np.zeros(x.shape, np.uint8)
+    imax = lib().oracle_normalize8(_ptr(x), _dtype_code(x), x.size, float(dark), _ptr(out))
+    return out, imax
+
+
+def greedy_seq(D: np.ndarray, eabs: float) -> np.ndarray:
+    """Sec. 4.2.3 on one sequence of 8-bit pixels."""
+    D = np.ascontiguousarray(D, np.uint8)
+    Q = np.zeros(max(D.size, 1), np.uint8)
+    lib().oracle_greedy_seq(_ptr(D), D.size, float(eabs), _ptr(Q))
+    return Q[:D.size].copy()
+
+
+def greedy_rows(img: np.ndarray, mask: np.ndarray, eabs: float) -> np.ndarray:
+    """Quantised pixel section: every row's retained pixels as one sequence."""
+    img = np.ascontiguousarray(img, np.uint8)
+    mask = np.ascontiguousarray(mask, np.uint8)
+    Q = np.zeros(max(img.size, 1), np.uint8)
+    n = lib().oracle_greedy_rows(_ptr(img), _ptr(mask), *_dims(img), float(eabs), _ptr(Q))
+    return Q[:n].copy()

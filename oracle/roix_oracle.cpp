@@ -37,7 +37,7 @@
 
 namespace {
 
-enum { DT_F32 = 1, DT_U16 = 2 };
+enum { DT_F32 = 1, DT_U16 = 2, DT_U8 = 3 };  // uint8: the normalised image (Sec. 4.1.2)
 enum { ERR_OK = 0, ERR_INVAL = 1, ERR_CORRUPT = 4 };
 
 const uint32_t kLMax = 24;          // longest Huffman code
@@ -99,6 +99,8 @@ int oracle_threshold(const void* in, const OracleParams* p, uint64_t nx,
     double v;
     if (p->dtype == DT_F32) {
       v = (double)((const float*)in)[i];
+    } else if (p->dtype == DT_U8) {
+      v = (double)((int64_t)((const uint8_t*)in)[i] - (int64_t)p->dark);
     } else {
       v = (double)((int64_t)((const uint16_t*)in)[i] - (int64_t)p->dark);
     }
@@ -204,6 +206,8 @@ int64_t oracle_compact(const void* in, int32_t dtype, uint64_t nx, uint64_t ny,
       if (x < nx && cur) {
         if (dtype == DT_F32)
           ((float*)P)[n] = ((const float*)in)[r * nx + x];
+        else if (dtype == DT_U8)
+          ((uint8_t*)P)[n] = ((const uint8_t*)in)[r * nx + x];
         else
           ((uint16_t*)P)[n] = ((const uint16_t*)in)[r * nx + x];
         n++;
@@ -460,6 +464,7 @@ int oracle_compress(const void* in, const OracleParams* p, uint64_t nx,
                     uint64_t ny, uint64_t nz, uint8_t** out, uint64_t* out_size) {
   *out = nullptr;
   *out_size = 0;
+  if (p->dtype != DT_F32 && p->dtype != DT_U16) return ERR_INVAL;  // linear quantiser only
   uint64_t N = nx * ny * nz, rows = ny * nz;
   uint32_t R = p->radius, S = 2 * R, C = p->chunk;
   std::vector<uint8_t> T(N), D(N);
@@ -572,6 +577,7 @@ int oracle_decode(const uint8_t* buf, uint64_t size, void* outv, int32_t dtype,
     std::memcpy(dst, buf + off, bytes);
     return true;
   };
+  if (dtype != DT_F32 && dtype != DT_U16) return ERR_INVAL;
   if (size < kHeaderBytes || std::memcmp(buf, "ROIX", 4) != 0) return ERR_CORRUPT;
   uint16_t version; uint8_t dt;
   uint32_t hx, hy, hz, R, C, lmax;
@@ -709,6 +715,110 @@ int oracle_decode(const uint8_t* buf, uint64_t size, void* outv, int32_t dtype,
   }
   if (k != n || b != nb) return ERR_CORRUPT;
   return ERR_OK;
+}
+
+// ------------------------------------------- 8-bit normalisation (Sec. 4.1.2)
+// I_n = I / I_max * 255 on the background-subtracted values (Sec. 4.1.1):
+// v = x (float32) or raw - dark (uint16); negative and non-finite values are
+// taken as 0; I_max = the largest v of the image (0 maps every pixel to 0).
+// The paper leaves the arithmetic open. float32: the formula in its own order
+// in binary32, fl(fl(v / I_max) * 255), rounded half to even; uint16: the exact
+// rational 255 v / I_max rounded half to even (integer arithmetic). Returns
+// I_max.
+double oracle_normalize8(const void* in, int32_t dtype, uint64_t count, double dark,
+                         uint8_t* out) {
+  if (dtype == DT_F32) {
+    const float* x = (const float*)in;
+    auto value = [&](uint64_t i) -> float {
+      const float f = x[i];
+      return (std::isfinite(f) && f > 0.0f) ? f : 0.0f;
+    };
+    float imax = 0.0f;
+    for (uint64_t i = 0; i < count; ++i) imax = std::max(imax, value(i));
+    for (uint64_t i = 0; i < count; ++i) {
+      float q = 0.0f;
+      if (imax > 0.0f) {
+        volatile float ratio = value(i) / imax;  // one rounding per operation
+        volatile float scaled = ratio * 255.0f;
+        q = std::nearbyint((float)scaled);
+      }
+      out[i] = (uint8_t)std::min(255.0f, q);
+    }
+    return (double)imax;
+  }
+  const uint16_t* raw = (const uint16_t*)in;
+  const int64_t dk = (int64_t)dark;
+  auto value = [&](uint64_t i) -> int64_t {
+    const int64_t v = (int64_t)raw[i] - dk;
+    return v > 0 ? v : 0;
+  };
+  int64_t imax = 0;
+  for (uint64_t i = 0; i < count; ++i) imax = std::max(imax, value(i));
+  for (uint64_t i = 0; i < count; ++i) {
+    int64_t q = 0;
+    if (imax > 0) {
+      const int64_t num = 255 * value(i);
+      q = num / imax;
+      const int64_t r2 = 2 * (num - q * imax);
+      if (r2 > imax || (r2 == imax && (q & 1))) ++q;  // half to even
+    }
+    out[i] = (uint8_t)q;
+  }
+  return (double)imax;
+}
+
+// ------------------------------------ greedy error-bounded quantiser (Sec. 4.2.3)
+// The paper's steps on one pixel sequence D (Step 1 bounds, Step 2 init,
+// Step 3 running intersection, Step 4 final group, Step 5 clip), with Q
+// restricted to integers as it is stored in 8 bits: pixel k accepts the
+// integers [ceil(D - E), floor(D + E)]; a group's value is floor((u + l) / 2)
+// of its intersection [l, u], hence within every member's bound.
+void oracle_greedy_seq(const uint8_t* D, uint64_t m, double eabs, uint8_t* Q) {
+  const int64_t e = (int64_t)std::floor(eabs);
+  int64_t l = 0, u = 0;
+  uint64_t head = 0;
+  bool open = false;
+  for (uint64_t i = 0; i < m; ++i) {
+    const int64_t lo = (int64_t)D[i] - e, hi = (int64_t)D[i] + e;
+    if (!open) {
+      l = lo;
+      u = hi;
+      head = i;
+      open = true;
+      continue;
+    }
+    const int64_t ln = std::max(l, lo), un = std::min(u, hi);
+    if (un < ln) {  // no overlap: close the group
+      const int64_t q = floor_div(u + l, 2);
+      for (uint64_t j = head; j < i; ++j) Q[j] = (uint8_t)std::min<int64_t>(255, std::max<int64_t>(0, q));
+      l = lo;
+      u = hi;
+      head = i;
+    } else {
+      l = ln;
+      u = un;
+    }
+  }
+  if (open) {
+    const int64_t q = floor_div(u + l, 2);
+    for (uint64_t j = head; j < m; ++j) Q[j] = (uint8_t)std::min<int64_t>(255, std::max<int64_t>(0, q));
+  }
+}
+
+// Every row's retained pixels (mask D, one byte per voxel) form one sequence
+// P(i) (Sec. 4.2.2); Q holds the quantised pixel section in voxel order.
+uint64_t oracle_greedy_rows(const uint8_t* img, const uint8_t* mask, uint64_t nx, uint64_t ny,
+                            uint64_t nz, double eabs, uint8_t* Q) {
+  std::vector<uint8_t> seq(nx + 1);
+  uint64_t n = 0;
+  for (uint64_t r = 0; r < ny * nz; ++r) {
+    uint64_t m = 0;
+    for (uint64_t x = 0; x < nx; ++x)
+      if (mask[r * nx + x]) seq[m++] = img[r * nx + x];
+    oracle_greedy_seq(seq.data(), m, eabs, Q + n);
+    n += m;
+  }
+  return n;
 }
 
 }  // extern "C"

@@ -477,3 +477,124 @@ def test_decode_rejects_corruption():
         oracle.decode(buf, (2, 4, 41), np.float32)
     with pytest.raises(ValueError):
         oracle.decode(buf[:-64], x.shape, np.float32)
+
+
+# ----------------------------------- 8-bit normalisation + greedy quantiser
+def _min_groups_brute(D, e):
+    """Minimum number of constant groups with |Q - D| <= e (integers), by
+    dynamic programming over all segmentations (independent of the greedy)."""
+    m = len(D)
+    best = [0] + [10**9] * m
+    for j in range(1, m + 1):
+        for i in range(j):
+            lo = max(int(d) - e for d in D[i:j])
+            hi = min(int(d) + e for d in D[i:j])
+            if lo <= hi:
+                best[j] = min(best[j], best[i] + 1)
+    return best[m]
+
+
+def _groups(Q):
+    return 0 if len(Q) == 0 else 1 + int(np.count_nonzero(np.diff(Q.astype(np.int64))))
+
+
+def test_greedy_hand_example():
+    # D = 1 2 3 10, E = 1: [0,2] n [1,3] n [2,4] = [2,2] -> 2 2 2; then [9,11] -> 10
+    assert oracle.greedy_seq(np.array([1, 2, 3, 10], np.uint8), 1).tolist() == [2, 2, 2, 10]
+    # odd u + l rounds down: [0,2] n [1,3] = [1,2] -> floor(3/2) = 1
+    assert oracle.greedy_seq(np.array([1, 2], np.uint8), 1).tolist() == [1, 1]
+    # touching ranges still overlap: [-1,1] n [1,3] = [1,1]
+    assert oracle.greedy_seq(np.array([0, 2], np.uint8), 1).tolist() == [1, 1]
+    assert oracle.greedy_seq(np.array([0, 3], np.uint8), 1).tolist() == [0, 3]
+    # E < 1 keeps every value: groups are runs of equal pixels
+    D = np.array([5, 5, 6, 200, 200, 0], np.uint8)
+    assert np.array_equal(oracle.greedy_seq(D, 0.1), D)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_greedy_bound_and_minimal_groups(seed):
+    rng = np.random.default_rng(seed)
+    m = int(rng.integers(1, 14))
+    D = np.clip(np.cumsum(rng.integers(-6, 7, m)) + 128, 0, 255).astype(np.uint8)
+    for e in (0, 1, 2, 5, 15):
+        Q = oracle.greedy_seq(D, e + 0.5 * (seed % 2))  # fractional E uses floor(E)
+        assert (np.abs(Q.astype(int) - D.astype(int)) <= e).all()
+        # constant groups: the greedy closes a group only when it must, so it
+        # reaches the minimum number of groups (interval stabbing)
+        assert _groups(Q) <= _min_groups_brute(D, e)
+
+
+def test_greedy_clips_to_8_bits():
+    D = np.array([255, 254, 0, 1], np.uint8)
+    Q = oracle.greedy_seq(D, 15)
+    assert Q.max() <= 255 and (np.abs(Q.astype(int) - D.astype(int)) <= 15).all()
+
+
+def test_normalize8_closed_form_points():
+    x = np.array([0.0, 1.0, 2.0, 4.0, -3.0, np.nan, 0.5], np.float32)
+    img, imax = oracle.normalize8(x)
+    assert imax == 4.0
+    # 4 -> 255; 2 -> 127.5 -> 128 (half to even); 1 -> 63.75 -> 64; 0.5 -> 31.875 -> 32
+    assert img.tolist() == [0, 64, 128, 255, 0, 0, 32]
+    raw = np.array([100, 100, 355, 610], np.uint16)  # v = 0, 0, 255, 510
+    img, imax = oracle.normalize8(raw, dark=100)
+    assert imax == 510.0 and img.tolist() == [0, 0, 128, 255]
+
+
+def test_greedy_rows_resets_per_row():
+    img = np.array([[10, 11, 12, 50], [12, 13, 90, 91]], np.uint8)
+    mask = np.array([[1, 1, 1, 0], [1, 1, 1, 1]], np.uint8)
+    # row 0: [9,11] n [10,12] n [11,13] = [11,11]; row 1 starts afresh:
+    # [11,13] n [12,14] = [12,13] -> 12, then [89,91] n [90,92] = [90,91] -> 90
+    assert oracle.greedy_rows(img, mask, 1).tolist() == [11, 11, 11, 12, 12, 90, 90]
+
+
+def test_normalize8_u16_exact_rational_half_even():
+    from fractions import Fraction
+    rng = np.random.default_rng(3)
+    raw = rng.integers(0, 4000, 3000).astype(np.uint16)
+    raw[:4] = [0, 37, 2037, 3999]
+    img, imax = oracle.normalize8(raw, dark=37)
+    v = np.maximum(raw.astype(np.int64) - 37, 0)
+    assert imax == v.max()
+    want = [round(Fraction(255 * int(a), int(imax))) for a in v]  # Python rounds half to even
+    assert img.tolist() == want
+
+
+def test_normalize8_f32_error_and_order():
+    rng = np.random.default_rng(4)
+    x = rng.gamma(2.0, 1.5, 20000).astype(np.float32)
+    x[::97] = -x[::97]
+    x[5] = np.inf
+    img, imax = oracle.normalize8(x)
+    v = np.where(np.isfinite(x) & (x > 0), x, 0).astype(np.float64)
+    assert imax == v.max()
+    exact = v / imax * 255.0
+    # two binary32 roundings then rounding to an integer: within 1/2 + a few ulps
+    assert np.abs(img - exact).max() <= 0.5 + 1e-4
+    order = np.argsort(v, kind="stable")
+    assert (np.diff(img[order].astype(int)) >= 0).all()  # monotone in v
+    assert img[np.argmax(v)] == 255 and (img[v == 0] == 0).all()
+
+
+def test_normalize8_zero_image():
+    img, imax = oracle.normalize8(np.zeros(10, np.uint16), dark=0)
+    assert imax == 0 and not img.any()
+    img, imax = oracle.normalize8(np.full(10, -1.0, np.float32))
+    assert imax == 0 and not img.any()
+
+
+def test_uint8_threshold_and_compact():
+    rng = np.random.default_rng(6)
+    img = rng.integers(0, 256, (3, 7, 45)).astype(np.uint8)
+    T = oracle.threshold(img, threshold=140.5, cmp="gt", dilate=0)
+    assert np.array_equal(T, (img > 140.5).astype(np.uint8))
+    T = oracle.threshold(img, threshold=20, cmp="lt", dark=5, dilate=0)
+    assert np.array_equal(T, (img.astype(int) - 5 < 20).astype(np.uint8))
+    P, counts, bounds = oracle.compact(img, T)
+    assert np.array_equal(P, img[T.astype(bool)])
+
+
+def test_uint8_refused_by_linear_path():
+    with pytest.raises(Exception):
+        oracle.compress(np.zeros((4, 4), np.uint8))
