@@ -49,7 +49,13 @@ typedef enum {
   ROIX_EBUSY = 7
 } roix_status;
 
-typedef enum { ROIX_F32 = 1, ROIX_U16 = 2 } roix_dtype;
+/* ROIX_U8 is the 8-bit normalised image of Sec. 4.1.2 (roix_normalize8). It is
+ * accepted by the region and compaction stages (roix_extract_roi,
+ * roix_extract_roi_static, roix_compact), where it behaves like uint16 (v =
+ * raw - dark, integer comparisons), and its pixel section is quantised by
+ * roix_greedy_quantize; the linear quantiser, the coder and the container
+ * (roix_quantize, roix_encode, roix_compress*, roix_decode) refuse it. */
+typedef enum { ROIX_F32 = 1, ROIX_U16 = 2, ROIX_U8 = 3 } roix_dtype;
 
 typedef struct {
   uint64_t nx, ny, nz;
@@ -178,6 +184,50 @@ roix_status roix_encode(roix_ctx* ctx, const int32_t* q, const uint32_t* outlier
  * error-bounded value, the others params.fill. */
 roix_status roix_decode(roix_ctx* ctx, const void* in, uint64_t size, void* out,
                         roix_dtype dtype, roix_dims dims, void* stream);
+
+/* Sec. 4.1.2: 8-bit intensity normalisation I_n = I / I_max * 255 of the
+ * background-subtracted image (Sec. 4.1.1): v = x for float32 input (negative
+ * and non-finite values count as 0), v = max(raw - dark, 0) for uint16 (dark an
+ * integer in [0, 65535]). I_max is the largest v of the count = nx*ny*nz
+ * values at `in`; I_max = 0 maps every voxel to 0.
+ *  float32: I_n = rint(fl(fl(v / I_max) * 255)) in binary32, round half to
+ *           even, at most 255;
+ *  uint16:  I_n = the exact rational 255 v / I_max rounded half to even.
+ * out: count uint8 values (device). imax_dev: I_max as a double (device, may
+ * be NULL). Buffers are the caller's; `in` and `out` may not overlap. Two
+ * passes over the input (the maximum, then the scaling). */
+roix_status roix_normalize8(roix_ctx* ctx, const void* in, roix_dtype dtype, roix_dims dims,
+                            double dark, uint8_t* out, double* imax_dev, void* stream);
+
+/* Sec. 4.2.3: the greedy absolute-error-bounded quantiser over the pixel
+ * section of an 8-bit image. Every row's retained pixels (the bits of `mask`
+ * in that row, layout of roix_mask_words) form one pixel sequence P(i) of
+ * Sec. 4.2.2; `pixels` holds the sequences row after row (the pixel section
+ * roix_compact writes for a ROIX_U8 image). Each sequence is cut greedily into
+ * groups whose acceptable sets [D - E_abs, D + E_abs] share an integer; a
+ * group's value is floor((u + l) / 2) of that shared interval [l, u], so
+ * |Q - D| <= E_abs for every pixel and Q is in [0, 255]. Q is integer (it is
+ * stored in 8 bits), so only floor(E_abs) matters; eabs must be finite and
+ * >= 0 (eabs < 1 returns Q = D).
+ *  q_out: n uint8 values (device), n = popcount of the mask; n_dev (device,
+ *  uint64, may be NULL) receives n. `pixels` must hold n values; q_out may
+ *  equal pixels (in place) but may not overlap it otherwise. */
+roix_status roix_greedy_quantize(roix_ctx* ctx, const uint8_t* pixels, const uint32_t* mask,
+                                 roix_dims dims, double eabs, uint8_t* q_out,
+                                 uint64_t* n_dev, void* stream);
+
+/* roix_greedy_quantize over several images in one call (same E_abs): their
+ * rows are scanned together, so that small images fill the device. Items are
+ * independent; n_dev of each (may be NULL) receives its pixel count. */
+typedef struct {
+  const uint8_t* pixels;
+  const uint32_t* mask;
+  roix_dims dims;
+  uint8_t* q_out;
+  uint64_t* n_dev;
+} roix_greedy_item;
+roix_status roix_greedy_quantize_batch(roix_ctx* ctx, uint32_t n, const roix_greedy_item* items,
+                                       double eabs, void* stream);
 
 /* Allocation-free variant of roix_extract_roi, for callers that cannot
  * allocate device memory when they need a mask: code recording a CUDA graph in

@@ -24,7 +24,7 @@ import torch
 
 from . import _build
 
-F32, U16 = 1, 2
+F32, U16, U8 = 1, 2, 3
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory",
           3: "output buffer too small", 4: "corrupt container", 5: "wait timed out",
           6: "CUDA error", 7: "busy"}
@@ -56,6 +56,11 @@ class Params(C.Structure):
 class Item(C.Structure):
     _fields_ = [("in_", C.c_void_p), ("dims", Dims), ("out", C.c_void_p), ("cap", C.c_uint64),
                 ("size_dev", C.c_void_p)]
+
+
+class GreedyItem(C.Structure):
+    _fields_ = [("pixels", C.c_void_p), ("mask", C.c_void_p), ("dims", Dims),
+                ("q_out", C.c_void_p), ("n_dev", C.c_void_p)]
 
 
 class ServerConfig(C.Structure):
@@ -126,6 +131,10 @@ def lib():
                 "roix_server_drain": (st, [P, C.c_double]),
                 "roix_server_get_stats": (st, [P, C.POINTER(ServerStats)]),
                 "roix_server_destroy": (st, [P]),
+                "roix_normalize8": (st, [P, P, i32, D, C.c_double, P, P, P]),
+                "roix_greedy_quantize": (st, [P, P, P, D, C.c_double, P, P, P]),
+                "roix_greedy_quantize_batch": (st, [P, C.c_uint32, C.POINTER(GreedyItem),
+                                                    C.c_double, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -143,7 +152,8 @@ def symbols():
             "roix_encode", "roix_decode", "roix_compress", "roix_profile",
             "roix_profile_read", "roix_extract_roi_static", "roix_compress_batch",
             "roix_server_create", "roix_server_submit", "roix_server_poll", "roix_server_drain",
-            "roix_server_get_stats", "roix_server_destroy"]
+            "roix_server_get_stats", "roix_server_destroy", "roix_normalize8",
+            "roix_greedy_quantize", "roix_greedy_quantize_batch"]
 
 
 def _dtype_code(t: torch.Tensor) -> int:
@@ -151,7 +161,9 @@ def _dtype_code(t: torch.Tensor) -> int:
         return F32
     if t.dtype == torch.uint16:
         return U16
-    raise TypeError("float32 or uint16 tensors only")
+    if t.dtype == torch.uint8:
+        return U8
+    raise TypeError("float32, uint16 or uint8 tensors only")
 
 
 def dims_of(shape) -> Dims:
@@ -326,6 +338,42 @@ class Roix:
                                         bounds.data_ptr(), int(bounds_cap), sizes.data_ptr(),
                                         _stream(stream)))
         return pixels, counts[:rows], bounds, sizes
+
+    def normalize8(self, x: torch.Tensor, dark: float = 0.0, out: torch.Tensor | None = None,
+                   stream=None):
+        """Sec. 4.1.2: the 8-bit image (uint8, shape of x) and I_max (float64[1])."""
+        d = dims_of(x.shape)
+        out = torch.empty(x.shape, dtype=torch.uint8, device=x.device) if out is None else out
+        imax = torch.zeros(1, dtype=torch.float64, device=x.device)
+        self._check(self.L.roix_normalize8(self.ctx, x.data_ptr(), _dtype_code(x), d,
+                                           float(dark), out.data_ptr(), imax.data_ptr(),
+                                           _stream(stream)))
+        return out, imax
+
+    def greedy(self, pixels: torch.Tensor, mask: torch.Tensor, shape, eabs: float,
+               out: torch.Tensor | None = None, stream=None):
+        """Sec. 4.2.3 over every row's retained pixels; returns (Q, n[1])."""
+        d = dims_of(shape)
+        out = torch.empty_like(pixels) if out is None else out
+        n = torch.zeros(1, dtype=torch.uint64, device=pixels.device)
+        self._check(self.L.roix_greedy_quantize(self.ctx, pixels.data_ptr(), mask.data_ptr(), d,
+                                                float(eabs), out.data_ptr(), n.data_ptr(),
+                                                _stream(stream)))
+        return out, n
+
+    def greedy_batch(self, items, eabs: float, outs=None, stream=None):
+        """Sec. 4.2.3 over several images in one call: items = [(pixels, mask,
+        shape), ...]; returns ([Q, ...], n[len(items)])."""
+        dev = items[0][0].device if items else torch.device("cuda")
+        outs = [torch.empty_like(p) for p, _, _ in items] if outs is None else outs
+        n = torch.zeros(max(len(items), 1), dtype=torch.uint64, device=dev)
+        arr = (GreedyItem * max(len(items), 1))()
+        for k, ((p, m, shape), q) in enumerate(zip(items, outs)):
+            arr[k] = GreedyItem(p.data_ptr(), m.data_ptr(), dims_of(shape), q.data_ptr(),
+                                n.data_ptr() + 8 * k)
+        self._check(self.L.roix_greedy_quantize_batch(self.ctx, len(items), arr, float(eabs),
+                                                      _stream(stream)))
+        return outs, n[:len(items)]
 
     def quantize(self, pixels: torch.Tensor, n_cap: int | None = None,
                  n_dev: torch.Tensor | None = None, stream=None, **cfg):

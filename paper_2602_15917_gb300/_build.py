@@ -12,7 +12,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libroix.so")
-SOURCES = ["roix_api.cu", "k_mask.cu", "k_encode.cu", "k_decode.cu", "k_ccl.cu", "roix_server.cu", "roix_static.cu"]
+SOURCES = ["roix_api.cu", "k_mask.cu", "k_encode.cu", "k_decode.cu", "k_ccl.cu", "roix_server.cu", "roix_static.cu",
+           "k_greedy.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

@@ -60,14 +60,14 @@ __device__ __forceinline__ void thr_segment(const Desc& d, const TV* __restrict_
 }
 
 // Vector form for 16-byte aligned rows (float32: nx % 4 == 0, uint16: nx % 8
-// == 0). A warp reads a 1024-voxel segment with 8 (float4) or 4 (uint4)
-// coalesced 512-byte loads, all in flight before use. Each lane turns its 4
-// or 8 voxels into a nibble or byte; XOR-shuffles OR the nibbles (bytes) of a
-// mask word together, and lane w picks word w.
+// == 0, uint8: nx % 16 == 0). A warp reads a 1024-voxel segment with 8
+// (float4), 4 or 2 (uint4) coalesced 512-byte loads, all in flight before use.
+// Each lane turns its 4, 8 or 16 voxels into a nibble, byte or half-word;
+// XOR-shuffles OR those of a mask word together, and lane w picks word w.
 template <typename TV>
 __device__ __forceinline__ void thr_segment_vec(const Desc& d, const TV* __restrict__ in,
                                                 u32* __restrict__ T, u64 r, u32 x0, int lane) {
-  constexpr int kPer = sizeof(TV) == 4 ? 4 : 8;  // voxels per lane and load
+  constexpr int kPer = 16 / sizeof(TV);  // voxels per lane and load
   constexpr int kLoads = 1024 / (32 * kPer);      // loads per segment
   constexpr int kLanesPerWord = 32 / kPer;        // lanes contributing to one word
   constexpr int kWordsPerLoad = 32 / kLanesPerWord;
@@ -91,13 +91,20 @@ __device__ __forceinline__ void thr_segment_vec(const Desc& d, const TV* __restr
                (pass_f32(__uint_as_float(v[i].y), d) ? 2u : 0u) |
                (pass_f32(__uint_as_float(v[i].z), d) ? 4u : 0u) |
                (pass_f32(__uint_as_float(v[i].w), d) ? 8u : 0u);
-      } else {
+      } else if constexpr (sizeof(TV) == 2) {
         const u32 q[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           bits |= (pass_u16(q[k] & 0xffffu, d) ? 1u : 0u) << (2 * k);
           bits |= (pass_u16(q[k] >> 16, d) ? 1u : 0u) << (2 * k + 1);
         }
+      } else {
+        const u32 q[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+          for (int b = 0; b < 4; ++b)
+            bits |= (pass_u16((q[k] >> (8 * b)) & 0xffu, d) ? 1u : 0u) << (4 * k + b);
       }
     }
     u32 t = bits << (kPer * (lane & (kLanesPerWord - 1)));
@@ -129,36 +136,63 @@ __global__ void __launch_bounds__(kThreads) k_threshold(const __grid_constant__ 
   }
 }
 
-// Dilated word: OR over the 3x3 neighbour rows (clipped) of the word shifted
-// by -1, 0, +1 in x, carries taken from the neighbouring words.
-__device__ __forceinline__ u32 dilate_word_global(const u32* __restrict__ T, const Desc& d,
-                                                  u64 r, u64 w) {
-  const u64 y = r % d.ny, z = r / d.ny;
-  u32 acc = 0;
-  for (int dz = -1; dz <= 1; ++dz) {
-    if ((dz < 0 && z == 0) || (dz > 0 && z + 1 >= d.nz)) continue;
-    for (int dy = -1; dy <= 1; ++dy) {
-      if ((dy < 0 && y == 0) || (dy > 0 && y + 1 >= d.ny)) continue;
-      const u32* row = T + (r + (int64_t)dz * (int64_t)d.ny + dy) * d.W;
-      const u32 c = __ldg(row + w);
-      const u32 lo = w > 0 ? __ldg(row + w - 1) : 0u;
-      const u32 hi = w + 1 < d.W ? __ldg(row + w + 1) : 0u;
-      acc |= c | (c << 1) | (lo >> 31) | (c >> 1) | (hi << 31);
-    }
-  }
-  return acc & last_mask(d, w);
-}
-
+// Cube dilation of the mask on its own (the fused path dilates inside the
+// compaction). A block takes a tile of rpt consecutive rows of one z slice:
+// it stages their band, one row above and below, already OR-ed over the three
+// slices z-1, z, z+1 (coalesced, three loads per word), then forms each word
+// from the three band rows around it, the x shift taking its carries from the
+// neighbouring words. Tiles never cross a slice, so the row's y and z come
+// from the tile index alone.
 __global__ void __launch_bounds__(kThreads) k_dilate(Desc d, const u32* __restrict__ T,
-                                                     u32* __restrict__ D, u64* popcount) {
-  const u64 total = d.rows * d.W;
+                                                     u32* __restrict__ D, u64* popcount,
+                                                     u32 rpt, FastDiv fdW) {
+  extern __shared__ u32 band[];  // (rpt + 2) x W
+  const u64 W = d.W;
+  const u64 tps = (d.ny + rpt - 1) / rpt;  // tiles per slice
+  const u64 tiles = tps * d.nz;
   u64 cnt = 0;
-  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (u64)gridDim.x * blockDim.x) {
-    const u64 r = i / d.W, w = i - r * d.W;
-    const u32 v = d.dilate ? dilate_word_global(T, d, r, w) : (T[i] & last_mask(d, w));
-    D[i] = v;
-    cnt += __popc(v);
+  for (u64 t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const u64 z = t / tps;
+    const u64 y0 = (t - z * tps) * rpt;
+    const u32 nr = (u32)umin((u64)rpt, d.ny - y0);
+    const u64 y_lo = y0 ? y0 - 1 : 0, y_hi = umin(y0 + nr + 1, d.ny);  // staged rows [y_lo, y_hi)
+    const u32 nb = (u32)((y_hi - y_lo) * W);  // at most (rpt + 2) W <= 6144
+    for (u32 k = threadIdx.x; k < nb; k += blockDim.x) {
+      const u32 q = fdW.div(k);
+      const u64 yy = y_lo + q, w = k - q * (u32)W;
+      const u64 r = z * d.ny + yy;
+      u32 v = __ldg(T + r * W + w);
+      if (d.dilate) {
+        if (z > 0) v |= __ldg(T + (r - d.ny) * W + w);
+        if (z + 1 < d.nz) v |= __ldg(T + (r + d.ny) * W + w);
+      }
+      band[(yy - y0 + 1) * W + w] = v;  // band row 0 is y0 - 1
+    }
+    __syncthreads();
+    const u32 nw = nr * (u32)W;
+    for (u32 k = threadIdx.x; k < nw; k += blockDim.x) {
+      const u32 ly32 = fdW.div(k);
+      const u64 ly = ly32, w = k - ly32 * (u32)W;
+      const u64 y = y0 + ly;
+      u32 v;
+      if (d.dilate) {
+        u32 c = 0, lo = 0, hi = 0;
+        for (int dy = -1; dy <= 1; ++dy) {
+          if ((dy < 0 && y == 0) || (dy > 0 && y + 1 >= d.ny)) continue;
+          const u32* b = band + (ly + 1 + dy) * W;
+          c |= b[w];
+          if (w > 0) lo |= b[w - 1];
+          if (w + 1 < W) hi |= b[w + 1];
+        }
+        v = c | (c << 1) | (lo >> 31) | (c >> 1) | (hi << 31);
+      } else {
+        v = band[(ly + 1) * W + w];
+      }
+      v &= last_mask(d, w);
+      D[(z * d.ny + y) * W + w] = v;
+      cnt += __popc(v);
+    }
+    __syncthreads();
   }
   cnt = warp_sum(cnt);
   if ((threadIdx.x & 31) == 0 && cnt) atomicAdd((unsigned long long*)popcount, cnt);
@@ -187,6 +221,31 @@ __device__ __forceinline__ void flush_range(State* st, u32& kmin, u32& kmax, int
   }
   kmin = 0xffffffffu;
   kmax = 0u;
+}
+
+// Copy of one run of 8-bit values by a warp: byte copies up to the first
+// 16-byte boundary of the destination and after the last one; in between
+// every lane writes aligned 16-byte chunks, funnel-shifting them out of five
+// aligned source words (each holding at least one byte of the run).
+__device__ __forceinline__ void copy_run_u8(const u8* __restrict__ src, u8* __restrict__ dst,
+                                            u32 len, int lane) {
+  const u32 head = (u32)((16u - ((uintptr_t)dst & 15u)) & 15u);
+  const u32 hb = umin(head, len);
+  if ((u32)lane < hb) dst[lane] = __ldg(src + lane);
+  const u32 n16 = (len - hb) >> 4;
+  const uintptr_t sa = (uintptr_t)(src + hb);
+  const u32 sh = (u32)(sa & 3u) * 8u;
+  const u32* sw = reinterpret_cast<const u32*>(sa & ~(uintptr_t)3);
+  uint4* dw = reinterpret_cast<uint4*>(dst + hb);
+  for (u32 k = lane; k < n16; k += 32) {
+    const u32 w0 = __ldg(sw + 4 * k), w1 = __ldg(sw + 4 * k + 1), w2 = __ldg(sw + 4 * k + 2),
+              w3 = __ldg(sw + 4 * k + 3);
+    const u32 w4 = sh ? __ldg(sw + 4 * k + 4) : 0u;
+    dw[k] = make_uint4(__funnelshift_r(w0, w1, sh), __funnelshift_r(w1, w2, sh),
+                       __funnelshift_r(w2, w3, sh), __funnelshift_r(w3, w4, sh));
+  }
+  const u32 done = hb + 16 * n16;
+  if ((u32)lane < len - done) dst[done + lane] = __ldg(src + done + lane);
 }
 
 struct FrontSmem {
@@ -404,6 +463,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_front(const __grid_constant__ B
             const TV* src = irow + xs;
             TV* dst = P + on;
             const u32 len = xe - xs;
+            if constexpr (sizeof(TV) == 1) {
+              copy_run_u8(reinterpret_cast<const u8*>(src), reinterpret_cast<u8*>(dst), len, lane);
+              on += len;
+              continue;
+            }
             for (u32 e0 = 0; e0 < len; e0 += 128) {
               TV v[4];
 #pragma unroll
@@ -493,16 +557,26 @@ void launch_threshold(const Launch& L, const Batch& B) {
   if (blocks > cap) blocks = cap;
   if (B.c.dtype == ROIX_F32)
     k_threshold<float><<<(unsigned)blocks, kThreads, 0, L.stream>>>(B);
-  else
+  else if (B.c.dtype == ROIX_U16)
     k_threshold<unsigned short><<<(unsigned)blocks, kThreads, 0, L.stream>>>(B);
+  else
+    k_threshold<unsigned char><<<(unsigned)blocks, kThreads, 0, L.stream>>>(B);
 }
 
 void launch_dilate(const Launch& L, const Desc& d, const u32* T, u32* D, u64* popcount) {
   const u64 total = d.rows * d.W;
   if (total == 0) return;
-  u64 blocks = (total + kThreads - 1) / kThreads;
+  u64 rpt = 2048 / d.W;  // about 2048 words per tile
+  if (rpt < 1) rpt = 1;
+  if (rpt > d.ny) rpt = d.ny;
+  const size_t smem = (size_t)(rpt + 2) * d.W * 4;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_dilate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const u64 tiles = (d.ny + rpt - 1) / rpt * d.nz;
+  u64 blocks = tiles;
   if (blocks > (u64)L.sms * 8) blocks = (u64)L.sms * 8;
-  k_dilate<<<(unsigned)blocks, kThreads, 0, L.stream>>>(d, T, D, popcount);
+  k_dilate<<<(unsigned)blocks, kThreads, smem, L.stream>>>(d, T, D, popcount, (u32)rpt,
+                                                            FastDiv((u32)d.W));
 }
 
 size_t front_smem(u32 rpt, u64 W, int dilate) {
@@ -518,15 +592,18 @@ void launch_front(const Launch& L, const Batch& B) {
     const size_t s = front_smem(B.it[i].rpt, B.it[i].W, B.c.dilate);
     if (s > smem) smem = s;
   }
-  const void* fn = B.c.dtype == ROIX_F32 ? (const void*)k_front<float>
-                                         : (const void*)k_front<unsigned short>;
+  const void* fn = B.c.dtype == ROIX_F32   ? (const void*)k_front<float>
+                   : B.c.dtype == ROIX_U16 ? (const void*)k_front<unsigned short>
+                                           : (const void*)k_front<unsigned char>;
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   u64 grid = (u64)occupancy_grid(fn, kThreads, smem, L.sms);
   if (grid > tiles) grid = tiles;
   if (B.c.dtype == ROIX_F32)
     k_front<float><<<(unsigned)grid, kThreads, smem, L.stream>>>(B);
-  else
+  else if (B.c.dtype == ROIX_U16)
     k_front<unsigned short><<<(unsigned)grid, kThreads, smem, L.stream>>>(B);
+  else
+    k_front<unsigned char><<<(unsigned)grid, kThreads, smem, L.stream>>>(B);
 }
 
 }  // namespace roix

@@ -110,7 +110,10 @@ bool dims_ok(roix_dims d) {
 roix_status roix::make_desc(roix_ctx* ctx, roix_dtype dtype, roix_dims dims, const roix_roi* roi,
                             const roix_eb* eb, const roix_params* prm, Desc* d) {
   std::memset(d, 0, sizeof(*d));
-  if (dtype != ROIX_F32 && dtype != ROIX_U16) return fail(ctx, ROIX_EINVAL, "dtype must be ROIX_F32 or ROIX_U16");
+  if (dtype != ROIX_F32 && dtype != ROIX_U16 && dtype != ROIX_U8)
+    return fail(ctx, ROIX_EINVAL, "dtype must be ROIX_F32, ROIX_U16 or ROIX_U8");
+  if (dtype == ROIX_U8 && (eb || prm))
+    return fail(ctx, ROIX_EINVAL, "uint8 images go through roix_greedy_quantize, not the coder");
   if (!dims_ok(dims)) return fail(ctx, ROIX_EINVAL, "dims: nx <= 65534, ny, nz < 2^32, N < 1.1e12");
   d->nx = dims.nx;
   d->ny = dims.ny;
@@ -176,6 +179,8 @@ namespace {
 
 bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
+size_t dtype_bytes(int dt) { return dt == ROIX_F32 ? 4 : dt == ROIX_U16 ? 2 : 1; }
+
 u32 front_rows_per_tile(const Desc& d) {
   const u64 target_words = 2048;
   u64 rpt = d.W ? target_words / d.W : 1;
@@ -212,7 +217,7 @@ BatchPlan plan_batch(const Desc& c, const roix_dims* dims, const u64* n_caps, co
   Arena a;
   a.take(sizeof(State) * (n ? n : 1));
   bp.zero_begin = a.take(0);
-  const size_t esz = c.dtype == ROIX_F32 ? 4 : 2;
+  const size_t esz = dtype_bytes(c.dtype);
   for (u32 i = 0; i < n; ++i) {
     ItemPlan& p = bp.items[i];
     Desc d = c;
@@ -285,7 +290,7 @@ LookBack<NV> lb_at(char* ws, size_t flags, size_t data, u64 tiles) {
 
 bool rows_vector_aligned(const void* in, roix_dtype dt, u64 nx) {
   if (((uintptr_t)in & 15) != 0) return false;
-  return dt == ROIX_F32 ? (nx & 3) == 0 : (nx & 7) == 0;
+  return (nx * dtype_bytes(dt)) % 16 == 0;
 }
 
 // Fills the batch structure for the plan; pointers into `ws`. Item fields for
@@ -803,6 +808,7 @@ roix_status roix_decode(roix_ctx* ctx, const void* in, uint64_t size, void* out,
   Desc d;
   roix_status s = make_desc(ctx, dtype, dims, nullptr, nullptr, nullptr, &d);
   if (s) return s;
+  if (dtype == ROIX_U8) return fail(ctx, ROIX_EINVAL, "containers hold float32 or uint16");
   if (!in || (d.N && !out)) return fail(ctx, ROIX_EINVAL, "null buffer");
   if (!aligned(in, 16)) return fail(ctx, ROIX_EINVAL, "in must be 16-byte aligned");
   DeviceGuard g(ctx->device);
@@ -851,3 +857,114 @@ roix_status roix_decode(roix_ctx* ctx, const void* in, uint64_t size, void* out,
 }
 
 }  // extern "C"
+
+// ------------------------------------------------ 8-bit preprocessor path
+roix_status roix_normalize8(roix_ctx* ctx, const void* in, roix_dtype dtype, roix_dims dims,
+                            double dark, uint8_t* out, double* imax_dev, void* stream) {
+  if (!ctx) return ROIX_EINVAL;
+  if (dtype != ROIX_F32 && dtype != ROIX_U16)
+    return fail(ctx, ROIX_EINVAL, "normalize8 takes float32 or uint16 input");
+  Desc d;
+  roix_status s = make_desc(ctx, dtype, dims, nullptr, nullptr, nullptr, &d);
+  if (s) return s;
+  if (dtype == ROIX_U16 && !(dark >= 0.0 && dark <= 65535.0 && dark == std::floor(dark)))
+    return fail(ctx, ROIX_EINVAL, "dark must be an integer in [0, 65535]");
+  if (dtype == ROIX_F32 && dark != 0.0) return fail(ctx, ROIX_EINVAL, "dark must be 0 for float32");
+  if (d.N && (!in || !out)) return fail(ctx, ROIX_EINVAL, "null buffer");
+  if (d.N && !aligned(in, dtype_bytes(dtype))) return fail(ctx, ROIX_EINVAL, "misaligned input");
+  DeviceGuard g(ctx->device);
+  Arena a;
+  a.take(kStateBytes);
+  const size_t key = a.take(16);
+  if ((s = ensure_ws(ctx, a.take(0)))) return s;
+  cudaStream_t cs = (cudaStream_t)stream;
+  Launch L{cs, ctx->sms};
+  cudaMemsetAsync(ctx->ws + key, 0, 4, cs);
+  if (d.N == 0) {
+    if (imax_dev) cudaMemsetAsync(imax_dev, 0, 8, cs);
+  } else {
+    launch_normalize8(L, dtype, in, d.N, (int)dark, out, (u32*)(ctx->ws + key), imax_dev);
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ROIX_OK : cuda_fail(ctx, e, "normalize8 launch");
+}
+
+roix_status roix_greedy_quantize_batch(roix_ctx* ctx, uint32_t n, const roix_greedy_item* items,
+                                       double eabs, void* stream) {
+  if (!ctx) return ROIX_EINVAL;
+  if (n && !items) return fail(ctx, ROIX_EINVAL, "null items");
+  if (!(std::isfinite(eabs) && eabs >= 0.0))
+    return fail(ctx, ROIX_EINVAL, "eabs must be finite and >= 0");
+  u64 rows_all = 0, tiles_all = 0, rows_max = 0, tiles_max = 0;
+  for (u32 k = 0; k < n; ++k) {
+    Desc d;
+    roix_status s = make_desc(ctx, ROIX_U8, items[k].dims, nullptr, nullptr, nullptr, &d);
+    if (s) return s;
+    if (d.N && (!items[k].pixels || !items[k].mask || !items[k].q_out))
+      return fail(ctx, ROIX_EINVAL, "null buffer");
+    rows_all += d.rows;
+    tiles_all += (d.rows + 31) / 32;
+  }
+  DeviceGuard g(ctx->device);
+  // workspace for the largest group of up to kGreedyMaxItems items
+  for (u32 k0 = 0; k0 < n; k0 += kGreedyMaxItems) {
+    u64 r = 0, t = 0;
+    for (u32 k = k0; k < n && k < k0 + kGreedyMaxItems; ++k) {
+      const u64 rows = items[k].dims.ny * items[k].dims.nz;
+      r += rows;
+      t += (rows + 31) / 32;
+    }
+    rows_max = r > rows_max ? r : rows_max;
+    tiles_max = t > tiles_max ? t : tiles_max;
+  }
+  (void)rows_all;
+  (void)tiles_all;
+  Arena a;
+  a.take(kStateBytes);
+  const size_t lens = a.take(4 * rows_max + 16);
+  const size_t rpre = a.take(4 * rows_max + 16);
+  const size_t ctr = a.take(16 * ((n + kGreedyMaxItems - 1) / kGreedyMaxItems + 1));
+  const size_t tsum = a.take(4 * tiles_max + 16);
+  const size_t toff = a.take(8 * (tiles_max + 1));
+  roix_status s;
+  if ((s = ensure_ws(ctx, a.take(0)))) return s;
+  cudaStream_t cs = (cudaStream_t)stream;
+  Launch L{cs, ctx->sms};
+  static thread_local GreedyBatch B;
+  const double ef = std::floor(eabs);
+  for (u32 k0 = 0; k0 < n; k0 += kGreedyMaxItems) {
+    std::memset(&B, 0, sizeof(B));
+    B.n = n - k0 < kGreedyMaxItems ? n - k0 : kGreedyMaxItems;
+    B.e2 = (u32)(2.0 * (ef > 255.0 ? 255.0 : ef));
+    B.lens = (u32*)(ctx->ws + lens);
+    B.tsum = (u32*)(ctx->ws + tsum);
+    B.toff = (u64*)(ctx->ws + toff);
+    B.rpre = (u32*)(ctx->ws + rpre);
+    B.rowctr = (u64*)(ctx->ws + ctr) + 2 * (k0 / kGreedyMaxItems);
+    cudaMemsetAsync(B.rowctr, 0, 8, cs);
+    for (u32 k = 0; k < B.n; ++k) {
+      const roix_greedy_item& it = items[k0 + k];
+      GreedyItem& I = B.it[k];
+      I.P = it.pixels;
+      I.mask = it.mask;
+      I.Q = it.q_out;
+      I.n_out = (u64*)it.n_dev;
+      I.rows = it.dims.ny * it.dims.nz;
+      I.W = (it.dims.nx + 31) / 32;
+      I.inplace = it.q_out == it.pixels ? 1u : 0u;
+      if (it.dims.nx == 0) I.rows = 0;  // no voxels: no rows to scan
+      B.tile0[k + 1] = B.tile0[k] + (I.rows + 31) / 32;
+      B.row0[k + 1] = B.row0[k] + I.rows;
+    }
+    launch_greedy(L, B);
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ROIX_OK : cuda_fail(ctx, e, "greedy launch");
+}
+
+roix_status roix_greedy_quantize(roix_ctx* ctx, const uint8_t* pixels, const uint32_t* mask,
+                                 roix_dims dims, double eabs, uint8_t* q_out, uint64_t* n_dev,
+                                 void* stream) {
+  const roix_greedy_item it{pixels, mask, dims, q_out, n_dev};
+  return roix_greedy_quantize_batch(ctx, 1, &it, eabs, stream);
+}

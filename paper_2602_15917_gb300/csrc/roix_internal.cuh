@@ -14,6 +14,7 @@ namespace roix {
 
 typedef unsigned long long u64;
 typedef unsigned int u32;
+typedef unsigned char u8;
 
 constexpr u32 kHeaderBytes = 256;   // container header
 constexpr u32 kLMax = 24;           // longest Huffman code
@@ -523,5 +524,33 @@ constexpr u64 kDecRowTile = 1024;
 size_t dec_table_bytes();
 void launch_decode(const Launch& L, const Desc& d, const uint8_t* in, u64 size, void* out,
                    const DecodeWs& ws, u64 max_chunks);
+
+// ------------------------------------- 8-bit normalisation, greedy quantiser
+// imax_key: one zeroed uint32 (the largest value's bits); imax_out may be null.
+void launch_normalize8(const Launch& L, int dtype, const void* in, u64 N, int dark, u8* out,
+                       u32* imax_key, double* imax_out);
+
+constexpr u32 kGreedyMaxItems = 64;
+struct GreedyItem {
+  const u8* P;      // pixel sections of the rows, row after row
+  const u32* mask;  // rows x W words
+  u8* Q;            // quantised sections (may equal P)
+  u64* n_out;       // total pixels (may be null)
+  u64 rows, W;
+  u32 inplace;      // Q == P: pixel loads bypass the non-coherent cache
+};
+struct GreedyBatch {
+  u32 n;
+  u32 e2;                            // 2 floor(E_abs), at most 510
+  u64 tile0[kGreedyMaxItems + 1];    // prefix of 32-row tiles over the items
+  u64 row0[kGreedyMaxItems + 1];     // prefix of rows over the items
+  GreedyItem it[kGreedyMaxItems];
+  u32* lens;                         // [rows of all items]
+  u32* rpre;                         // [rows]: prefix of lengths within the row's tile
+  u64* rowctr;                       // zeroed: next row to scan
+  u32* tsum;                         // [tiles]
+  u64* toff;                         // [tiles + 1]
+};
+void launch_greedy(const Launch& L, const GreedyBatch& B);
 
 }  // namespace roix

@@ -12,6 +12,9 @@ pine cone, seashell scans) are not available; these phantoms stand in for them:
                        ellipsoid phantom, plus a constant dark offset (Sec. 4.1.1).
 * ``porous_cylinder``  reconstructed volume: a cylinder of material with spherical
                        pores on zero-valued air, optional lognormal texture, noise.
+* ``walk8``, ``runs``  8-bit rows that drift by small random steps (flat stretches
+                       and slopes, as in a normalised image) and random run masks,
+                       for the row-wise stages on their own.
 
 Structure parameters come from ``numpy.random.default_rng(seed)``; per-voxel
 noise and Poisson counts from a ``torch.Generator`` seeded with ``seed`` on the
@@ -211,3 +214,37 @@ def random_field(shape, seed: int = 0, scale: float = 1.0, smooth: bool = True,
     else:
         field = rng.standard_normal(shape) * scale
     return field.astype(dtype)
+
+
+def walk8(shape, seed: int = 0, step: int = 3, hold: float = 0.3) -> np.ndarray:
+    """uint8 image whose rows are clipped random walks from U[0, 255]: each
+    pixel repeats the previous one with probability `hold`, else moves by
+    U[-step, step]."""
+    rng = np.random.default_rng(seed)
+    shape = tuple(int(s) for s in shape)
+    rows = int(np.prod(shape[:-1])) if len(shape) > 1 else 1
+    nx = shape[-1]
+    d = rng.integers(-step, step + 1, (rows, nx))
+    d[rng.random((rows, nx)) < hold] = 0
+    d[:, 0] = rng.integers(0, 256, rows)
+    return np.clip(np.cumsum(d, axis=1), 0, 255).astype(np.uint8).reshape(shape)
+
+
+def runs(shape, seed: int = 0, density: float = 0.5, mean_run: float = 40.0) -> np.ndarray:
+    """uint8 0/1 mask whose rows alternate off/on runs of geometric lengths
+    (mean `mean_run` when on)."""
+    rng = np.random.default_rng(seed)
+    shape = tuple(int(s) for s in shape)
+    rows = int(np.prod(shape[:-1])) if len(shape) > 1 else 1
+    nx = shape[-1]
+    m = np.zeros((rows, nx), np.uint8)
+    off_mean = mean_run * (1.0 - density) / max(density, 1e-6)
+    for r in range(rows):
+        x, on = 0, bool(rng.random() < density)
+        while x < nx:
+            length = int(rng.geometric(1.0 / max(mean_run if on else off_mean, 1.0)))
+            if on:
+                m[r, x:x + length] = 1
+            x += length
+            on = not on
+    return m.reshape(shape)
