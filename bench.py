@@ -61,6 +61,21 @@ WORKLOADS = {
 }
 
 
+# The 8-bit preprocessor path of Sec. 4.1.2-4.2.3 (normalise to 8 bits, ROI on
+# the 8-bit image, compaction, greedy quantiser): a step runs the four stages
+# over the workload's items.
+PAPER8 = {
+    "paper8_cube1024": dict(
+        base="cube1024", dark=0, roi=dict(threshold=25, cmp="gt", dilate=1), eabs=2,
+        desc="1024^3 float32 porous cylinder as cube1024 -> 8 bits -> ROI I_n > 25 + "
+             "1-voxel dilation -> compaction -> greedy quantiser E_abs = 2"),
+    "paper8_projections64": dict(
+        base="projections64", dark=100, roi=dict(threshold=200, cmp="lt", dilate=0), eabs=2,
+        desc="64 uint16 projections as projections64 -> 8 bits (dark 100) -> ROI I_n < 200 "
+             "-> compaction -> greedy quantiser E_abs = 2 (one batched call)"),
+}
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -439,6 +454,220 @@ def cpu_baseline(args, xs, cfg, budget_s: float = None):
             "sample": f"{sample}: {i} items, {done / 1e6:.0f} MB in {dt:.1f} s"}
 
 
+# ------------------------------------------------- 8-bit preprocessor path
+def paper8_stage_bytes(xs, ns, nbs):
+    """Algorithmic bytes of the four stages for one step: normalise reads the
+    input twice (maximum, then scaling) and writes N bytes; the ROI reads the
+    8-bit image and writes the mask (N/8) twice (binarised, dilated); the
+    compaction reads the mask and moves n bytes in and out plus the geometry;
+    the greedy pass reads the mask and n bytes and writes n bytes."""
+    tot = {"normalize": 0.0, "roi": 0.0, "compact": 0.0, "greedy": 0.0}
+    for x, n, nb in zip(xs, ns, nbs):
+        N, esz = x.numel(), x.element_size()
+        rows = N // x.shape[-1]
+        tot["normalize"] += 2 * N * esz + N
+        tot["roi"] += N + 2 * N / 8
+        tot["compact"] += N / 8 + 2 * n + 2 * nb + 2 * rows
+        tot["greedy"] += N / 8 + 2 * n
+    return tot
+
+
+def oracle_paper8(x, pc):
+    import oracle
+    img, _ = oracle.normalize8(x, dark=pc["dark"])
+    D = oracle.mask(img, **pc["roi"])
+    return oracle.greedy_rows(img, D, pc["eabs"])
+
+
+def paper8_cpu(xs, pc, budget_s):
+    if len(xs) == 1 and xs[0].dim() == 3 and xs[0].shape[0] > 64:
+        z = xs[0].shape[0]
+        items = [xs[0][z // 2 - 8: z // 2 + 8].cpu().numpy()]
+        sample = "16 middle slices of the volume (their own I_max), repeated"
+    else:
+        items = [x.cpu().numpy() for x in xs]
+        sample = "items in order"
+    done, t0, i = 0, time.perf_counter(), 0
+    while True:
+        x = items[i % len(items)]
+        oracle_paper8(x, pc)
+        done += x.nbytes
+        i += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": round(done / dt / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{sample} for ~{budget_s:.0f} s: {i} items, {done / 1e6:.0f} MB in {dt:.1f} s"}
+
+
+def run_paper8(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    import paper_2602_15917_gb300 as roix
+
+    pc = PAPER8[args.workload]
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    xs = make_inputs(pc["base"], dev, seed=args.seed)
+    torch.cuda.synchronize()
+    in_bytes = sum(x.numel() * x.element_size() for x in xs)
+    rx = roix.Roix(local_rank)
+    main = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(main)
+    imgs = [torch.empty(x.shape, dtype=torch.uint8, device=dev) for x in xs]
+    words = [torch.empty(max(int(rx.L.roix_mask_words(roix.dims_of(x.shape))), 1),
+                         dtype=torch.int32, device=dev) for x in xs]
+    pops = torch.zeros(len(xs), dtype=torch.uint64, device=dev)
+    Ps = [torch.empty(x.numel(), dtype=torch.uint8, device=dev) for x in xs]
+    Qs = [torch.empty(x.numel(), dtype=torch.uint8, device=dev) for x in xs]
+    counts = [torch.empty(max(x.numel() // x.shape[-1], 1), dtype=torch.uint16, device=dev)
+              for x in xs]
+    bounds = [torch.empty(x.numel() + x.numel() // x.shape[-1], dtype=torch.uint16, device=dev)
+              for x in xs]
+    sizes = torch.zeros(len(xs), 2, dtype=torch.uint64, device=dev)
+    imax = torch.zeros(len(xs), dtype=torch.float64, device=dev)
+    ns = torch.zeros(len(xs), dtype=torch.uint64, device=dev)
+    L, C = rx.L, __import__("ctypes")
+    marks = []
+
+    def mark(tag):
+        if marks is not None and args._profile:
+            e = torch.cuda.Event(enable_timing=True)
+            e.record(main)
+            marks.append((tag, e))
+
+    def stages(inputs, s):
+        mark("start")
+        for k, x in enumerate(inputs):
+            rx._check(L.roix_normalize8(rx.ctx, x.data_ptr(), roix._dtype_code(x),
+                                        roix.dims_of(x.shape), float(pc["dark"]),
+                                        imgs[k].data_ptr(), imax[k:k + 1].data_ptr(), s))
+        mark("normalize")
+        for k, x in enumerate(inputs):
+            rx._check(L.roix_extract_roi(rx.ctx, imgs[k].data_ptr(), roix.U8, roix.dims_of(x.shape),
+                                         C.byref(roix.roi_of(**pc["roi"])), words[k].data_ptr(),
+                                         pops[k:k + 1].data_ptr(), s))
+        mark("roi")
+        for k, x in enumerate(inputs):
+            nrow = x.numel() // x.shape[-1]
+            rx._check(L.roix_compact(rx.ctx, imgs[k].data_ptr(), roix.U8, roix.dims_of(x.shape),
+                                     words[k].data_ptr(), Ps[k].data_ptr(), counts[k].data_ptr(),
+                                     bounds[k].data_ptr(), x.numel() + nrow,
+                                     sizes[k].data_ptr(), s))
+        mark("compact")
+        arr = (roix.GreedyItem * len(inputs))()
+        for k, x in enumerate(inputs):
+            arr[k] = roix.GreedyItem(Ps[k].data_ptr(), words[k].data_ptr(), roix.dims_of(x.shape),
+                                     Qs[k].data_ptr(), ns[k:k + 1].data_ptr())
+        rx._check(L.roix_greedy_quantize_batch(rx.ctx, len(inputs), arr, float(pc["eabs"]), s))
+        mark("greedy")
+
+    s_ptr = main.cuda_stream
+    args._profile = False
+    stages(xs, s_ptr)
+    rx.sync(main)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=main, capture_error_mode="thread_local"):
+        stages(xs, s_ptr)
+    graph.replay()
+    rx.sync(main)
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local_rank) as clk:
+        e0.record(main)
+        for _ in range(args.steps):
+            graph.replay()
+        e1.record(main)
+        torch.cuda.synchronize()
+    rx.sync(main)
+    ms_step = e0.elapsed_time(e1) / args.steps
+    value = in_bytes * world / (ms_step / 1e3) / 1e9
+    n_host = ns.cpu().numpy().astype(np.int64)
+    nb_host = sizes[:, 1].cpu().numpy().astype(np.int64)
+    # step latency
+    step_ms = []
+    for _ in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(main)
+        graph.replay()
+        b.record(main)
+        b.synchronize()
+        step_ms.append(a.elapsed_time(b))
+    # stage times: events between the stages on the launching stream
+    args._profile = True
+    acc = {}
+    for _ in range(3):
+        marks.clear()
+        stages(xs, s_ptr)
+        torch.cuda.synchronize()
+        for (t0_, a), (t1_, b) in zip(marks[:-1], marks[1:]):
+            acc[t1_] = acc.get(t1_, 0.0) + a.elapsed_time(b) / 3
+    args._profile = False
+    alg = paper8_stage_bytes(xs, n_host, nb_host)
+    dom = max(acc, key=acc.get)
+    peak, kind = load_peaks()
+    ach = alg[dom] / (acc[dom] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": peak,
+                "peak_source": kind, "unit": "GB/s", "frac": round(ach / peak, 4),
+                "traffic": None, "algorithmic_bytes_per_step": round(alg[dom]),
+                "stage_ms_per_step": {k: round(v, 4) for k, v in acc.items()},
+                "stage_gbs": {k: round(alg[k] / (v / 1e3) / 1e9, 1) for k, v in acc.items()}}
+    # end to end: pinned host inputs uploaded, the stages, Q read back, per step
+    host_in = [x.cpu().pin_memory() for x in xs]
+    host_q = [torch.empty(int(n), dtype=torch.uint8).pin_memory() for n in n_host]
+    dev_in = [torch.empty_like(x) for x in xs]
+
+    def e2e_step():
+        for h, d in zip(host_in, dev_in):
+            d.copy_(h, non_blocking=True)
+        graph2.replay()
+        for q, hq, n in zip(Qs, host_q, n_host):
+            hq.copy_(q[:int(n)], non_blocking=True)
+
+    stages(dev_in, s_ptr)
+    rx.sync(main)
+    graph2 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph2, stream=main, capture_error_mode="thread_local"):
+        stages(dev_in, s_ptr)
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    rx.sync(main)
+    result = None
+    if rank == 0:
+        cpu = paper8_cpu(xs, pc, args.cpu_budget) if world == 1 and not args.no_cpu else None
+        result = {
+            "metric": "GB/s in (8-bit preprocessor: normalise + ROI + compaction + greedy)",
+            "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "u16->u8" if xs[0].element_size() == 2 else "f32->u8", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": pc["desc"], "items": len(xs),
+                       "bytes_in_per_step": in_bytes, "pixels_out_per_step": int(n_host.sum()),
+                       "path": "stage calls, one CUDA graph per step",
+                       "l2": "inputs larger than L2 (129 MB)" if in_bytes > 129e6
+                       else "inputs smaller than L2: not flushed",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": {"value": round(in_bytes * world / e2e_s / 1e9, 2), "unit": "GB/s",
+                    "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": int(n_host.sum()),
+                    "how": "pinned host inputs uploaded, stages, Q read back; one stream"},
+            "latency": {"p50_ms": round(float(np.percentile(step_ms, 50)), 4),
+                        "p99_ms": round(float(np.percentile(step_ms, 99)), 4),
+                        "of": "one step from launch to completion"},
+            "roofline": roofline, "cpu_baseline": cpu,
+            "gpu_launches": None, "clocks": clk.summary(),
+        }
+    rx.close()
+    return result
+
+
 # --------------------------------------------------------------- serving
 SERVE_CLASSES = [  # (share, kind, settings)
     (0.70, "proj2048", WORKLOADS["projections64"]["cfg"]),
@@ -573,6 +802,28 @@ def run_reference(args, rank, world):
     if rank != 0:
         return None
     import torch
+    if args.workload in PAPER8:
+        pc = PAPER8[args.workload]
+        xs = make_inputs(pc["base"], "cpu", seed=args.seed)
+        per_step = max(1.0, args.cpu_budget / max(1, args.steps + args.warmup))
+        for _ in range(args.warmup):
+            paper8_cpu(xs, pc, per_step)
+        vals = [paper8_cpu(xs, pc, per_step) for _ in range(args.steps)]
+        gbs = float(np.mean([v["value"] for v in vals]))
+        in_bytes = sum(x.numel() * x.element_size() for x in xs)
+        return {
+            "metric": "GB/s in (8-bit preprocessor: normalise + ROI + compaction + greedy)",
+            "value": round(gbs, 4), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(in_bytes / (gbs * 1e9) * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u16->u8" if xs[0].element_size() == 2 else "f32->u8", "data": "synthetic",
+            "impl": "reference", "config": {"workload": args.workload, "desc": pc["desc"],
+                                            "items": len(xs)},
+            "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s", "cores": 1,
+                             "kind": "oracle", "sample": vals[-1]["sample"]},
+            "e2e": {"value": round(gbs, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+        }
     name = "projections64" if args.workload == "serve" else args.workload
     wl = WORKLOADS[name]
     xs = make_inputs(name, "cpu", seed=args.seed)
@@ -603,7 +854,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="projections64", choices=sorted(WORKLOADS) + ["serve"])
+    ap.add_argument("--workload", default="projections64",
+                    choices=sorted(WORKLOADS) + sorted(PAPER8) + ["serve"])
     ap.add_argument("--serve-seconds", type=float, default=15.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-budget-gb", type=int, default=120)
@@ -629,6 +881,7 @@ def main():
             torch.cuda.set_device(local_rank)
             dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
         res = (run_serve(args, rank, world, local_rank) if args.workload == "serve"
+               else run_paper8(args, rank, world, local_rank) if args.workload in PAPER8
                else run_ours(args, rank, world, local_rank))
         if world > 1:
             import torch.distributed as dist
