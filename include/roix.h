@@ -229,6 +229,44 @@ typedef struct {
 roix_status roix_greedy_quantize_batch(roix_ctx* ctx, uint32_t n, const roix_greedy_item* items,
                                        double eabs, void* stream);
 
+/* ------------------------------------------------ evaluation metrics */
+/* Sec. 5.2: quality of a predicted ROI A against a ground truth B, both bit
+ * masks in the layout of roix_mask_words. Counts TP = |A and B|, FP = |A and
+ * not B|, FN = |B and not A|, TN = the rest; the ratios are the section's
+ * equations in binary64, one IEEE operation at a time in their printed order:
+ *   DSC = 2TP / ((TP + FP) + (TP + FN)),  IoU = TP / (TP + FP + FN),
+ *   sensitivity = TP / (TP + FN),  specificity = TN / (TN + FP),
+ *   accuracy = (TP + TN) / (TP + TN + FP + FN),
+ *   f_c = ((TN + FN)(TN + FP) + (FP + TP)(FN + TP)) / (TP + TN + FN + FP),
+ *   kappa = ((TP + TN) - f_c) / ((TP + TN + FN + FP) - f_c),
+ *   AUC = 1 - (FP / (FP + TN) + FN / (FN + TP)) / 2;
+ * a zero denominator gives NaN or inf as IEEE division does. With distances =
+ * 1 also the average Hausdorff distance AHD = max(sum_ab / |A|, sum_ba / |B|),
+ * sum_ab = sum over a in A of the Euclidean distance (voxel units) to the
+ * nearest voxel of B (exact distance transform), sum_ba the reverse; NaN when
+ * A or B is empty. The sums are accumulated with binary64 atomics (order not
+ * fixed). Distances need (nx-1)^2 + (ny-1)^2 + (nz-1)^2 < 2^32 - 1 and a
+ * workspace of about 8 bytes per voxel. out_dev: one roix_roi_metrics on the
+ * device. */
+typedef struct {
+  uint64_t tp, fp, fn, tn;
+  double dsc, iou, sensitivity, specificity, accuracy, kappa, auc, ahd;
+  double sum_ab, sum_ba;
+} roix_roi_metrics;
+roix_status roix_roi_quality(roix_ctx* ctx, const uint32_t* pred_mask, const uint32_t* truth_mask,
+                             roix_dims dims, int distances, roix_roi_metrics* out_dev,
+                             void* stream);
+
+/* Sec. 5.6: structural similarity of x and y (same dtype and dims; float32,
+ * uint16 or uint8), in the form of Wang, Bovik, Sheikh and Simoncelli (2004):
+ * Gaussian weights (sigma 1.5, 11 x 11, normalised), population moments,
+ * C1 = (0.01 L)^2, C2 = (0.03 L)^2 with L = data_range, evaluated on every 2D
+ * slice (z) at every position where the window lies inside the slice, and
+ * averaged over all those positions (binary64; sums by atomics, order not
+ * fixed). Slices smaller than 11 x 11 give NaN. ssim_dev: one double. */
+roix_status roix_ssim(roix_ctx* ctx, const void* x, const void* y, roix_dtype dtype,
+                      roix_dims dims, double data_range, double* ssim_dev, void* stream);
+
 /* Allocation-free variant of roix_extract_roi, for callers that cannot
  * allocate device memory when they need a mask: code recording a CUDA graph in
  * global capture mode (where cudaMalloc is refused), acquisition loops that

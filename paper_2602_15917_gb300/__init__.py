@@ -58,6 +58,12 @@ class Item(C.Structure):
                 ("size_dev", C.c_void_p)]
 
 
+class RoiMetrics(C.Structure):
+    _fields_ = [(k, C.c_uint64) for k in ("tp", "fp", "fn", "tn")] + \
+        [(k, C.c_double) for k in ("dsc", "iou", "sensitivity", "specificity", "accuracy",
+                                   "kappa", "auc", "ahd", "sum_ab", "sum_ba")]
+
+
 class GreedyItem(C.Structure):
     _fields_ = [("pixels", C.c_void_p), ("mask", C.c_void_p), ("dims", Dims),
                 ("q_out", C.c_void_p), ("n_dev", C.c_void_p)]
@@ -135,6 +141,8 @@ def lib():
                 "roix_greedy_quantize": (st, [P, P, P, D, C.c_double, P, P, P]),
                 "roix_greedy_quantize_batch": (st, [P, C.c_uint32, C.POINTER(GreedyItem),
                                                     C.c_double, P]),
+                "roix_roi_quality": (st, [P, P, P, D, C.c_int, P, P]),
+                "roix_ssim": (st, [P, P, P, i32, D, C.c_double, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -153,7 +161,8 @@ def symbols():
             "roix_profile_read", "roix_extract_roi_static", "roix_compress_batch",
             "roix_server_create", "roix_server_submit", "roix_server_poll", "roix_server_drain",
             "roix_server_get_stats", "roix_server_destroy", "roix_normalize8",
-            "roix_greedy_quantize", "roix_greedy_quantize_batch"]
+            "roix_greedy_quantize", "roix_greedy_quantize_batch", "roix_roi_quality",
+            "roix_ssim"]
 
 
 def _dtype_code(t: torch.Tensor) -> int:
@@ -374,6 +383,26 @@ class Roix:
         self._check(self.L.roix_greedy_quantize_batch(self.ctx, len(items), arr, float(eabs),
                                                       _stream(stream)))
         return outs, n[:len(items)]
+
+    def roi_quality(self, pred: torch.Tensor, truth: torch.Tensor, shape, distances=True,
+                    stream=None) -> dict:
+        """Sec. 5.2 metrics of mask words `pred` against `truth` (synchronises)."""
+        out = torch.zeros(C.sizeof(RoiMetrics), dtype=torch.uint8, device=pred.device)
+        self._check(self.L.roix_roi_quality(self.ctx, pred.data_ptr(), truth.data_ptr(),
+                                            dims_of(shape), int(bool(distances)),
+                                            out.data_ptr(), _stream(stream)))
+        self.sync(stream)
+        raw = bytes(out.cpu().numpy())
+        m = RoiMetrics.from_buffer_copy(raw)
+        return {k: getattr(m, k) for k, _ in RoiMetrics._fields_}
+
+    def ssim(self, x: torch.Tensor, y: torch.Tensor, data_range: float, stream=None):
+        """Sec. 5.6 mean SSIM of x and y; returns a float64 device tensor [1]."""
+        out = torch.zeros(1, dtype=torch.float64, device=x.device)
+        self._check(self.L.roix_ssim(self.ctx, x.data_ptr(), y.data_ptr(), _dtype_code(x),
+                                     dims_of(x.shape), float(data_range), out.data_ptr(),
+                                     _stream(stream)))
+        return out
 
     def quantize(self, pixels: torch.Tensor, n_cap: int | None = None,
                  n_dev: torch.Tensor | None = None, stream=None, **cfg):

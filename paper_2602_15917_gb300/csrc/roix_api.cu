@@ -968,3 +968,53 @@ roix_status roix_greedy_quantize(roix_ctx* ctx, const uint8_t* pixels, const uin
   const roix_greedy_item it{pixels, mask, dims, q_out, n_dev};
   return roix_greedy_quantize_batch(ctx, 1, &it, eabs, stream);
 }
+
+// ------------------------------------------------------ evaluation metrics
+roix_status roix_roi_quality(roix_ctx* ctx, const uint32_t* pred_mask, const uint32_t* truth_mask,
+                             roix_dims dims, int distances, roix_roi_metrics* out_dev,
+                             void* stream) {
+  if (!ctx) return ROIX_EINVAL;
+  Desc d;
+  roix_status s = make_desc(ctx, ROIX_U8, dims, nullptr, nullptr, nullptr, &d);
+  if (s) return s;
+  if (distances != 0 && distances != 1) return fail(ctx, ROIX_EINVAL, "distances must be 0 or 1");
+  if (!out_dev || (d.N && (!pred_mask || !truth_mask))) return fail(ctx, ROIX_EINVAL, "null buffer");
+  if (distances) {
+    const double a = (double)(dims.nx ? dims.nx - 1 : 0), b = (double)(dims.ny ? dims.ny - 1 : 0),
+                 c = (double)(dims.nz ? dims.nz - 1 : 0);
+    if (a * a + b * b + c * c >= 4294967295.0)
+      return fail(ctx, ROIX_EINVAL, "volume too large for 32-bit squared distances");
+  }
+  DeviceGuard g(ctx->device);
+  Arena ar;
+  ar.take(kStateBytes);
+  const size_t off = ar.take(roi_quality_ws_bytes(dims.nx, dims.ny, dims.nz, distances));
+  if ((s = ensure_ws(ctx, ar.take(0)))) return s;
+  Launch L{(cudaStream_t)stream, ctx->sms};
+  launch_roi_quality(L, pred_mask, truth_mask, dims.nx, dims.ny, dims.nz, distances,
+                     ctx->ws + off, out_dev);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ROIX_OK : cuda_fail(ctx, e, "roi_quality launch");
+}
+
+roix_status roix_ssim(roix_ctx* ctx, const void* x, const void* y, roix_dtype dtype,
+                      roix_dims dims, double data_range, double* ssim_dev, void* stream) {
+  if (!ctx) return ROIX_EINVAL;
+  Desc d;
+  roix_status s = make_desc(ctx, dtype, dims, nullptr, nullptr, nullptr, &d);
+  if (s) return s;
+  if (!(std::isfinite(data_range) && data_range > 0.0))
+    return fail(ctx, ROIX_EINVAL, "data_range must be finite and > 0");
+  if (!ssim_dev || (d.N && (!x || !y))) return fail(ctx, ROIX_EINVAL, "null buffer");
+  if (d.N && (!aligned(x, dtype_bytes(dtype)) || !aligned(y, dtype_bytes(dtype))))
+    return fail(ctx, ROIX_EINVAL, "misaligned input");
+  DeviceGuard g(ctx->device);
+  Arena ar;
+  ar.take(kStateBytes);
+  const size_t off = ar.take(64);
+  if ((s = ensure_ws(ctx, ar.take(0)))) return s;
+  Launch L{(cudaStream_t)stream, ctx->sms};
+  launch_ssim(L, dtype, x, y, dims.nx, dims.ny, dims.nz, data_range, ctx->ws + off, ssim_dev);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ROIX_OK : cuda_fail(ctx, e, "ssim launch");
+}

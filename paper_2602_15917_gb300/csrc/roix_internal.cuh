@@ -553,4 +553,11 @@ struct GreedyBatch {
 };
 void launch_greedy(const Launch& L, const GreedyBatch& B);
 
+// ------------------------------------------------ evaluation metrics
+size_t roi_quality_ws_bytes(u64 nx, u64 ny, u64 nz, int distances);
+void launch_roi_quality(const Launch& L, const u32* A, const u32* B, u64 nx, u64 ny, u64 nz,
+                        int distances, char* ws, roix_roi_metrics* out);
+void launch_ssim(const Launch& L, int dtype, const void* X, const void* Y, u64 nx, u64 ny, u64 nz,
+                 double data_range, char* ws, double* out);
+
 }  // namespace roix
