@@ -668,6 +668,159 @@ def run_paper8(args, rank, world, local_rank):
     return result
 
 
+# ------------------------------------------------------ evaluation metrics
+EVAL = {
+    "eval_cube1024": dict(
+        base="cube1024",
+        desc="Sec. 5.2 metrics of the ROI (x > 0.1) against the dilated ROI as reference, with "
+             "the average Hausdorff distance, and Sec. 5.6 SSIM of the decoded volume "
+             "(relative eb 1e-4) against the input, on the 1024^3 porous cylinder"),
+    "eval_projections64": dict(
+        base="projections64",
+        desc="per projection: Sec. 5.2 metrics of the ROI (raw-100 < 57000) against the dilated "
+             "ROI, with the average Hausdorff distance, and SSIM of the decode (eb 4) against "
+             "the input"),
+}
+
+
+def eval_cpu(xs, cfg, budget_s):
+    """The metric oracles (numpy/scipy, one core) on a bounded sample: the
+    masks and the decode of the sample come from the oracle too."""
+    import oracle
+    from oracle import metrics as M
+    if len(xs) == 1 and xs[0].dim() == 3 and xs[0].shape[0] > 64:
+        z = xs[0].shape[0]
+        items = [xs[0][z // 2 - 8: z // 2 + 8].cpu().numpy()]
+        sample = "16 middle slices of the volume"
+    else:
+        items = [x.cpu().numpy() for x in xs[:4]]
+        sample = "the first 4 items"
+    prepared = []
+    for x in items:
+        A = oracle.mask(x, **dict(cfg, dilate=0))
+        B = oracle.mask(x, **dict(cfg, dilate=1))
+        y = oracle.decode(oracle.compress(x, **cfg), x.shape, x.dtype)
+        L = float(x.max() - x.min()) if x.dtype == np.float32 else 65535.0
+        prepared.append((x, A, B, y, L))
+    done, t0, i = 0, time.perf_counter(), 0
+    while True:
+        x, A, B, y, L = prepared[i % len(prepared)]
+        M.roi_metrics(A, B)
+        M.ssim(x, y, L)
+        done += x.nbytes
+        i += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": round(done / dt / 1e9, 5), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{sample}, metrics repeated for ~{budget_s:.0f} s: {i} items, "
+                      f"{done / 1e6:.0f} MB in {dt:.1f} s"}
+
+
+def run_eval(args, rank, world, local_rank):
+    import torch
+    import paper_2602_15917_gb300 as roix
+
+    ev = EVAL[args.workload]
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    xs = make_inputs(ev["base"], dev, seed=args.seed)
+    cfg = WORKLOADS[ev["base"]]["cfg"]
+    rx = roix.Roix(local_rank)
+    main = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(main)
+    A, B, Y, L = [], [], [], []
+    for x in xs:
+        a, _ = rx.extract_roi(x, **dict(cfg, dilate=0))
+        b, _ = rx.extract_roi(x, **dict(cfg, dilate=1))
+        buf = rx.compress_bytes(x, **cfg)
+        y = rx.decode(buf, x.shape, x.dtype)
+        rx.sync()
+        A.append(a)
+        B.append(b)
+        Y.append(y)
+        L.append(float((x.max() - x.min()).item()) if x.dtype == torch.float32 else 65535.0)
+    torch.cuda.synchronize()
+    outs = [torch.zeros(roix.C.sizeof(roix.RoiMetrics), dtype=torch.uint8, device=dev) for _ in xs]
+    ss = torch.zeros(len(xs), dtype=torch.float64, device=dev)
+    s_ptr = main.cuda_stream
+    Lb = rx.L
+
+    def quality():
+        for k, x in enumerate(xs):
+            rx._check(Lb.roix_roi_quality(rx.ctx, A[k].data_ptr(), B[k].data_ptr(),
+                                          roix.dims_of(x.shape), 1, outs[k].data_ptr(), s_ptr))
+
+    def similarity():
+        for k, x in enumerate(xs):
+            rx._check(Lb.roix_ssim(rx.ctx, x.data_ptr(), Y[k].data_ptr(), roix._dtype_code(x),
+                                   roix.dims_of(x.shape), L[k], ss[k:k + 1].data_ptr(), s_ptr))
+
+    for _ in range(args.warmup):
+        quality()
+        similarity()
+    rx.sync(main)
+    ev_ = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    tq = ts = 0.0
+    with Clocks(local_rank) as clk:
+        for _ in range(args.steps):
+            ev_[0].record(main)
+            quality()
+            ev_[1].record(main)
+            similarity()
+            ev_[2].record(main)
+            ev_[2].synchronize()
+            tq += ev_[0].elapsed_time(ev_[1])
+            ts += ev_[1].elapsed_time(ev_[2])
+    rx.sync(main)
+    tq /= args.steps
+    ts /= args.steps
+    N = sum(x.numel() for x in xs)
+    in_bytes = sum(x.numel() * x.element_size() for x in xs)
+    m0 = roix.RoiMetrics.from_buffer_copy(bytes(outs[0].cpu().numpy()))
+    # algorithmic work: masks read once (2 N/8) plus, per direction, the row
+    # distances g written and read (8 N) and the squared distances written and
+    # read (8 N, volumes only); SSIM: per valid position 2 x 5 moments x 11
+    # taps (multiply-add = 2 flops) + about 20 flops
+    vol = xs[0].dim() == 3 and xs[0].shape[0] > 1
+    q_bytes = 2 * N / 8 + 2 * (8 * N + (8 * N if vol else 0))
+    pos = sum((x.shape[-1] - 10) * (x.shape[-2] - 10) * (x.shape[0] if x.dim() == 3 else 1)
+              for x in xs)
+    s_flops = pos * (2 * 5 * 11 * 2 + 20)
+    peak, kind = load_peaks()
+    fp64_peak = 1.25e12  # nominal dense FP64 of the part (non-tensor), no measured figure
+    q_gbs = q_bytes / (tq / 1e3) / 1e9
+    s_tfl = s_flops / (ts / 1e3) / 1e12
+    dom = "roi_quality" if tq >= ts else "ssim"
+    roofline = ({"bound": "hbm", "kernel": "roi_quality (confusion + distance transform)",
+                 "achieved": round(q_gbs, 1), "peak": peak, "peak_source": kind, "unit": "GB/s",
+                 "frac": round(q_gbs / peak, 4), "traffic": None}
+                if dom == "roi_quality" else
+                {"bound": "alu", "kernel": "ssim (binary64 moments)", "achieved": round(s_tfl, 4),
+                 "peak": 1.25, "peak_source": "nominal FP64 of the part", "unit": "TFLOP/s",
+                 "frac": round(s_tfl / 1.25, 4), "traffic": None})
+    roofline["stages_ms"] = {"roi_quality": round(tq, 4), "ssim": round(ts, 4)}
+    roofline["roi_quality_gbs"] = round(q_gbs, 1)
+    roofline["ssim_fp64_tflops"] = round(s_tfl, 4)
+    ms = tq + ts
+    result = {
+        "metric": "GB/s in (Sec. 5.2 ROI metrics with AHD + Sec. 5.6 SSIM)",
+        "value": round(in_bytes / (ms / 1e3) / 1e9, 2), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 sums", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": ev["desc"], "items": len(xs),
+                   "first_item": {"dsc": m0.dsc, "iou": m0.iou, "kappa": m0.kappa,
+                                  "ahd": m0.ahd, "ssim": float(ss[0].item())}},
+        "e2e": None, "roofline": roofline,
+        "cpu_baseline": (eval_cpu(xs, cfg, args.cpu_budget) if world == 1 and not args.no_cpu
+                         else None),
+        "gpu_launches": None, "clocks": clk.summary(),
+    }
+    rx.close()
+    return result
+
+
 # --------------------------------------------------------------- serving
 SERVE_CLASSES = [  # (share, kind, settings)
     (0.70, "proj2048", WORKLOADS["projections64"]["cfg"]),
@@ -802,6 +955,17 @@ def run_reference(args, rank, world):
     if rank != 0:
         return None
     import torch
+    if args.workload in EVAL:
+        ev = EVAL[args.workload]
+        xs = make_inputs(ev["base"], "cpu", seed=args.seed)
+        c = eval_cpu(xs, WORKLOADS[ev["base"]]["cfg"], args.cpu_budget)
+        return {"metric": "GB/s in (Sec. 5.2 ROI metrics with AHD + Sec. 5.6 SSIM)",
+                "value": c["value"], "unit": "GB/s", "n_gpus": world, "steps": 1, "warmup": 0,
+                "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64 sums", "data": "synthetic",
+                "impl": "reference", "config": {"workload": args.workload, "desc": ev["desc"]},
+                "cpu_baseline": c, "e2e": {"value": c["value"], "unit": "GB/s",
+                                           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     if args.workload in PAPER8:
         pc = PAPER8[args.workload]
         xs = make_inputs(pc["base"], "cpu", seed=args.seed)
@@ -855,7 +1019,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="projections64",
-                    choices=sorted(WORKLOADS) + sorted(PAPER8) + ["serve"])
+                    choices=sorted(WORKLOADS) + sorted(PAPER8) + sorted(EVAL) + ["serve"])
     ap.add_argument("--serve-seconds", type=float, default=15.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-budget-gb", type=int, default=120)
@@ -882,6 +1046,7 @@ def main():
             dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
         res = (run_serve(args, rank, world, local_rank) if args.workload == "serve"
                else run_paper8(args, rank, world, local_rank) if args.workload in PAPER8
+               else run_eval(args, rank, world, local_rank) if args.workload in EVAL
                else run_ours(args, rank, world, local_rank))
         if world > 1:
             import torch.distributed as dist

@@ -229,6 +229,27 @@ typedef struct {
 roix_status roix_greedy_quantize_batch(roix_ctx* ctx, uint32_t n, const roix_greedy_item* items,
                                        double eabs, void* stream);
 
+/* Paper-mode region of interest of an 8-bit image (Sec. 4.1.3-4.2.2), every
+ * 2D slice (z) on its own:
+ *  1. multi-Otsu with three classes [0, t1], (t1, t2], (t2, 255] on the
+ *     slice's 256-bin histogram: the pair t1 < t2 of [0, 254] maximising the
+ *     sum over the classes of (sum of values)^2 / count (the between-class
+ *     variance up to constants; binary64, empty classes add 0), ties to the
+ *     smallest (t1, t2);
+ *  2. M = [I_n > t1];
+ *  3. holes filled: background 4-connected to no slice border becomes object
+ *     (the region inside the external contours);
+ *  4. the largest 8-connected object of the filled mask by pixel count, ties
+ *     to the one holding the smallest raster index;
+ *  5. one span per row: [x_start, x_end) from its leftmost to its rightmost
+ *     pixel, gaps included.
+ * mask_out: the spans in the layout of roix_mask_words; *popcount_dev: their
+ * pixel count (uint64); thresholds_dev (may be NULL): (t1, t2) per slice as
+ * uint32. Workspace about 50 bytes per row and 14 per pixel. */
+roix_status roix_extract_roi_paper(roix_ctx* ctx, const uint8_t* img, roix_dims dims,
+                                   uint32_t* mask_out, uint64_t* popcount_dev,
+                                   uint32_t* thresholds_dev, void* stream);
+
 /* ------------------------------------------------ evaluation metrics */
 /* Sec. 5.2: quality of a predicted ROI A against a ground truth B, both bit
  * masks in the layout of roix_mask_words. Counts TP = |A and B|, FP = |A and

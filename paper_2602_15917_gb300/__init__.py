@@ -142,6 +142,7 @@ def lib():
                 "roix_greedy_quantize_batch": (st, [P, C.c_uint32, C.POINTER(GreedyItem),
                                                     C.c_double, P]),
                 "roix_roi_quality": (st, [P, P, P, D, C.c_int, P, P]),
+                "roix_extract_roi_paper": (st, [P, P, D, P, P, P, P]),
                 "roix_ssim": (st, [P, P, P, i32, D, C.c_double, P, P]),
             }
             for name, (res, args) in sig.items():
@@ -162,7 +163,7 @@ def symbols():
             "roix_server_create", "roix_server_submit", "roix_server_poll", "roix_server_drain",
             "roix_server_get_stats", "roix_server_destroy", "roix_normalize8",
             "roix_greedy_quantize", "roix_greedy_quantize_batch", "roix_roi_quality",
-            "roix_ssim"]
+            "roix_ssim", "roix_extract_roi_paper"]
 
 
 def _dtype_code(t: torch.Tensor) -> int:
@@ -383,6 +384,19 @@ class Roix:
         self._check(self.L.roix_greedy_quantize_batch(self.ctx, len(items), arr, float(eabs),
                                                       _stream(stream)))
         return outs, n[:len(items)]
+
+    def extract_roi_paper(self, img: torch.Tensor, stream=None):
+        """Paper-mode ROI of a uint8 image (every 2D slice): mask words,
+        pixel count [1] and the (t1, t2) thresholds per slice."""
+        d = dims_of(img.shape)
+        words = int(self.L.roix_mask_words(d))
+        mask = torch.empty(max(words, 1), dtype=torch.int32, device=img.device)
+        pop = torch.zeros(1, dtype=torch.uint64, device=img.device)
+        thr = torch.zeros((max(int(d.nz), 1), 2), dtype=torch.int32, device=img.device)
+        self._check(self.L.roix_extract_roi_paper(self.ctx, img.data_ptr(), d, mask.data_ptr(),
+                                                  pop.data_ptr(), thr.data_ptr(),
+                                                  _stream(stream)))
+        return mask[:words], pop, thr
 
     def roi_quality(self, pred: torch.Tensor, truth: torch.Tensor, shape, distances=True,
                     stream=None) -> dict:

@@ -13,7 +13,8 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libroix.so")
 SOURCES = ["roix_api.cu", "k_mask.cu", "k_encode.cu", "k_decode.cu", "k_ccl.cu", "roix_server.cu", "roix_static.cu",
-           "k_greedy.cu", "k_metrics.cu"]
+           "k_greedy.cu", "k_metrics.cu",
+           "k_paper_roi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

@@ -25,9 +25,14 @@ __device__ __forceinline__ u32 starts_of(u32 v, u32 prev) { return v & ~((v << 1
 __device__ __forceinline__ u32 lasts_of(u32 v, u32 next) { return v & ~((v >> 1) | (next << 31)); }
 
 // ---- 1. runs per row (warp per row)
+// word w of row `row`, complemented when inv (the background), bits >= nx clear
+__device__ __forceinline__ u32 word_at(const Desc& d, const u32* row, u64 w, u32 inv) {
+  return (__ldg(row + w) ^ inv) & last_word_mask(d, w);
+}
+
 __global__ void __launch_bounds__(kThreads) k_run_count(Desc d, const u32* __restrict__ T,
                                                         u32* __restrict__ row_runs,
-                                                        u32* __restrict__ out) {
+                                                        u32* __restrict__ out, u32 inv) {
   const int lane = threadIdx.x & 31;
   for (u64 r = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < d.rows;
        r += ((u64)gridDim.x * blockDim.x) >> 5) {
@@ -35,8 +40,8 @@ __global__ void __launch_bounds__(kThreads) k_run_count(Desc d, const u32* __res
     u32 c = 0;
     for (u64 w = lane; w < d.W; w += 32) out[r * d.W + w] = 0u;  // the kept mask starts empty
     for (u64 w = lane; w < d.W; w += 32) {
-      const u32 v = __ldg(row + w) & last_word_mask(d, w);
-      const u32 p = w ? (__ldg(row + w - 1) & last_word_mask(d, w - 1)) : 0u;
+      const u32 v = word_at(d, row, w, inv);
+      const u32 p = w ? word_at(d, row, w - 1, inv) : 0u;
       c += __popc(starts_of(v, p));
     }
     c = warp_sum(c);
@@ -90,7 +95,8 @@ __global__ void __launch_bounds__(kThreads) k_run_fill(Desc d, const u32* __rest
                                                        uint16_t* __restrict__ xs,
                                                        uint16_t* __restrict__ xe,
                                                        u32* __restrict__ par,
-                                                       unsigned long long* __restrict__ size) {
+                                                       unsigned long long* __restrict__ size,
+                                                       u32 inv) {
   const int lane = threadIdx.x & 31;
   for (u64 r = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < d.rows;
        r += ((u64)gridDim.x * blockDim.x) >> 5) {
@@ -100,9 +106,9 @@ __global__ void __launch_bounds__(kThreads) k_run_fill(Desc d, const u32* __rest
       const u64 w = w0 + lane;
       u32 st = 0u, ls = 0u;
       if (w < d.W) {
-        const u32 v = __ldg(row + w) & last_word_mask(d, w);
-        const u32 p = w ? (__ldg(row + w - 1) & last_word_mask(d, w - 1)) : 0u;
-        const u32 nx = w + 1 < d.W ? (__ldg(row + w + 1) & last_word_mask(d, w + 1)) : 0u;
+        const u32 v = word_at(d, row, w, inv);
+        const u32 p = w ? word_at(d, row, w - 1, inv) : 0u;
+        const u32 nx = w + 1 < d.W ? word_at(d, row, w + 1, inv) : 0u;
         st = starts_of(v, p);
         ls = lasts_of(v, nx);
       }
@@ -166,7 +172,10 @@ __global__ void __launch_bounds__(kThreads) k_run_union(Desc d, const u64* __res
                                                         u32* par) {
   const int lane = threadIdx.x & 31;
   const u64 nruns = *total;
-  const int ext = d.conn == 26 ? 1 : 0;  // diagonal neighbours in x for 26-connectivity
+  // diagonal neighbours in x for 26- (3D) and 8-connectivity (2D, in-plane);
+  // 4 and 8 join rows of the same slice only
+  const int ext = (d.conn == 26 || d.conn == 8) ? 1 : 0;
+  const bool planar = d.conn == 4 || d.conn == 8;
   for (u64 r = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < d.rows;
        r += ((u64)gridDim.x * blockDim.x) >> 5) {
     const u64 b0 = off[r], b1 = r + 1 < d.rows ? off[r + 1] : nruns;
@@ -177,7 +186,7 @@ __global__ void __launch_bounds__(kThreads) k_run_union(Desc d, const u64* __res
     int64_t nb[4];
     int nn = 0;
     if (y > 0) nb[nn++] = (int64_t)r - 1;
-    if (z > 0) {
+    if (z > 0 && !planar) {
       const int64_t rz = (int64_t)r - (int64_t)d.ny;
       if (d.conn == 26 && y > 0) nb[nn++] = rz - 1;
       nb[nn++] = rz;
@@ -285,18 +294,140 @@ __global__ void __launch_bounds__(kThreads) k_run_keep(Desc d, const u64* __rest
   }
 }
 
+// ---- paper mode (planar connectivity, per slice)
+// row of run i: the last row whose first run index is <= i
+__device__ __forceinline__ u64 row_of_run(const u64* off, u64 rows, u64 i) {
+  u64 lo = 0, hi = rows;
+  while (hi - lo > 1) {
+    const u64 mid = (lo + hi) >> 1;
+    if (off[mid] <= i) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void or_run(u32* row, u32 s, u32 e) {
+  for (u32 w = s >> 5; w <= (e - 1) >> 5; ++w) {
+    const u32 a = w == (s >> 5) ? (s & 31) : 0u;
+    const u32 b = w == ((e - 1) >> 5) ? ((e - 1) & 31) : 31u;
+    const u32 m = (b == 31 ? 0xffffffffu : ((1u << (b + 1)) - 1u)) & ~((1u << a) - 1u);
+    atomicOr(row + w, m);
+  }
+}
+
+// components touching the border of their slice (first / last row of the
+// slice, first / last column): their roots are flagged (after flattening)
+__global__ void __launch_bounds__(kThreads) k_run_border(Desc d, const u64* __restrict__ off,
+                                                         const u64* total, const u32* par,
+                                                         const uint16_t* __restrict__ xs,
+                                                         const uint16_t* __restrict__ xe,
+                                                         u32* flag) {
+  const u64 n = *total;
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (u64)gridDim.x * blockDim.x) {
+    const u64 r = row_of_run(off, d.rows, i);
+    const u64 y = r % d.ny;
+    if (y == 0 || y + 1 == d.ny || xs[i] == 0 || (u64)xe[i] == d.nx) flag[par[i]] = 1u;
+  }
+}
+
+// the runs whose root is flagged, OR-ed into `out` (zeroed by the count pass)
+__global__ void __launch_bounds__(kThreads) k_run_keep_flagged(Desc d, const u64* __restrict__ off,
+                                                               const u64* total, const u32* par,
+                                                               const uint16_t* __restrict__ xs,
+                                                               const uint16_t* __restrict__ xe,
+                                                               const u32* flag, u32* out) {
+  const u64 n = *total;
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (u64)gridDim.x * blockDim.x) {
+    if (!flag[par[i]]) continue;
+    or_run(out + row_of_run(off, d.rows, i) * d.W, xs[i], xe[i]);
+  }
+}
+
+// largest component of every slice (ties: the smallest root)
+__global__ void __launch_bounds__(kThreads) k_run_best_z(Desc d, const u64* __restrict__ off,
+                                                         const u64* total, const u32* par,
+                                                         const unsigned long long* size,
+                                                         unsigned long long* best) {
+  const u64 n = *total;
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (u64)gridDim.x * blockDim.x)
+    if (par[i] == (u32)i) atomicMax(best + row_of_run(off, d.rows, i) / d.ny, size[i]);
+}
+
+__global__ void __launch_bounds__(kThreads) k_run_best_root_z(Desc d, const u64* __restrict__ off,
+                                                              const u64* total, const u32* par,
+                                                              const unsigned long long* size,
+                                                              const unsigned long long* best,
+                                                              u32* best_root) {
+  const u64 n = *total;
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (u64)gridDim.x * blockDim.x) {
+    if (par[i] != (u32)i) continue;
+    const u64 z = row_of_run(off, d.rows, i) / d.ny;
+    if (size[i] == best[z]) atomicMax(best_root + z, 0xffffffffu - (u32)i);  // smallest root
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_run_keep_z(Desc d, const u64* __restrict__ off,
+                                                         const u64* total, const u32* par,
+                                                         const uint16_t* __restrict__ xs,
+                                                         const uint16_t* __restrict__ xe,
+                                                         const u32* best_root, u32* out) {
+  const u64 n = *total;
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (u64)gridDim.x * blockDim.x) {
+    const u64 r = row_of_run(off, d.rows, i);
+    if (par[i] != 0xffffffffu - best_root[r / d.ny]) continue;
+    or_run(out + r * d.W, xs[i], xe[i]);
+  }
+}
+
 }  // namespace
+
+// Paper mode, planar connectivity per slice (d.conn = 4 or 8):
+//  keep_border = 1: the components of (T complemented when inv) that touch
+//  their slice's border, into `out`; keep_border = 0: the largest component of
+//  every slice. w.size doubles as the flag array (after the sizes are used)
+//  and w.best / w.best_root hold nz entries (zeroed by the caller).
+void launch_ccl_planar(const Launch& L, const Desc& d, const u32* T, u32 inv, int keep_border,
+                       u32* out, const CclWs& w) {
+  const unsigned gw = (unsigned)umin((d.rows + 7) / 8, (u64)L.sms * 8);
+  const unsigned gr = (unsigned)L.sms * 4;
+  if (d.rows == 0) return;
+  k_run_count<<<gw, kThreads, 0, L.stream>>>(d, T, w.row_runs, out, inv);
+  const u64 tiles = (d.rows + kThreads * kScanPer - 1) / (kThreads * kScanPer);
+  k_run_scan<<<(unsigned)umin(tiles, (u64)L.sms * 4), kThreads, 0, L.stream>>>(
+      d.rows, w.row_runs, w.row_off, w.lb, w.ctr, w.status, w.total);
+  k_run_fill<<<gw, kThreads, 0, L.stream>>>(d, T, w.row_off, w.xs, w.xe, w.par, w.size, inv);
+  k_run_union<<<gw, kThreads, 0, L.stream>>>(d, w.row_off, w.total, w.xs, w.xe, w.par);
+  k_run_sizes<<<gr, kThreads, 0, L.stream>>>(w.total, w.par, w.xs, w.xe, w.size);
+  if (keep_border) {
+    u32* flag = reinterpret_cast<u32*>(w.size);  // sizes are not needed here
+    cudaMemsetAsync(flag, 0, 4 * (size_t)ccl_max_runs(d), L.stream);
+    k_run_border<<<gr, kThreads, 0, L.stream>>>(d, w.row_off, w.total, w.par, w.xs, w.xe, flag);
+    k_run_keep_flagged<<<gr, kThreads, 0, L.stream>>>(d, w.row_off, w.total, w.par, w.xs, w.xe,
+                                                      flag, out);
+  } else {
+    k_run_best_z<<<gr, kThreads, 0, L.stream>>>(d, w.row_off, w.total, w.par, w.size, w.best);
+    k_run_best_root_z<<<gr, kThreads, 0, L.stream>>>(d, w.row_off, w.total, w.par, w.size,
+                                                     w.best, w.best_root);
+    k_run_keep_z<<<gr, kThreads, 0, L.stream>>>(d, w.row_off, w.total, w.par, w.xs, w.xe,
+                                                w.best_root, out);
+  }
+}
 
 void launch_keep_largest(const Launch& L, const Desc& d, const u32* T, u32* out,
                          const CclWs& w) {
   const unsigned gw = (unsigned)umin((d.rows + 7) / 8, (u64)L.sms * 8);
   const unsigned gr = (unsigned)L.sms * 4;
   if (d.rows == 0) return;
-  k_run_count<<<gw, kThreads, 0, L.stream>>>(d, T, w.row_runs, out);
+  k_run_count<<<gw, kThreads, 0, L.stream>>>(d, T, w.row_runs, out, 0u);
   const u64 tiles = (d.rows + kThreads * kScanPer - 1) / (kThreads * kScanPer);
   k_run_scan<<<(unsigned)umin(tiles, (u64)L.sms * 4), kThreads, 0, L.stream>>>(
       d.rows, w.row_runs, w.row_off, w.lb, w.ctr, w.status, w.total);
-  k_run_fill<<<gw, kThreads, 0, L.stream>>>(d, T, w.row_off, w.xs, w.xe, w.par, w.size);
+  k_run_fill<<<gw, kThreads, 0, L.stream>>>(d, T, w.row_off, w.xs, w.xe, w.par, w.size, 0u);
   k_run_union<<<gw, kThreads, 0, L.stream>>>(d, w.row_off, w.total, w.xs, w.xe, w.par);
   k_run_sizes<<<gr, kThreads, 0, L.stream>>>(w.total, w.par, w.xs, w.xe, w.size);
   k_run_best_size<<<gr, kThreads, 0, L.stream>>>(w.total, w.par, w.size, w.best);

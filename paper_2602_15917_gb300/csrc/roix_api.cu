@@ -1018,3 +1018,79 @@ roix_status roix_ssim(roix_ctx* ctx, const void* x, const void* y, roix_dtype dt
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? ROIX_OK : cuda_fail(ctx, e, "ssim launch");
 }
+
+// ---------------------------------------------------- paper-mode ROI
+roix_status roix_extract_roi_paper(roix_ctx* ctx, const uint8_t* img, roix_dims dims,
+                                   uint32_t* mask_out, uint64_t* popcount_dev,
+                                   uint32_t* thresholds_dev, void* stream) {
+  if (!ctx) return ROIX_EINVAL;
+  Desc d;
+  roix_status s = make_desc(ctx, ROIX_U8, dims, nullptr, nullptr, nullptr, &d);
+  if (s) return s;
+  if (!popcount_dev || (d.N && (!img || !mask_out))) return fail(ctx, ROIX_EINVAL, "null buffer");
+  if (!ccl_fits(d)) return fail(ctx, ROIX_EINVAL, "too many rows x runs");
+  DeviceGuard g(ctx->device);
+  const u64 rows = d.rows, W = d.W, nz = dims.nz, maxr = ccl_max_runs(d);
+  const u64 ctiles = (rows + 2047) / 2048;
+  Arena a;
+  const size_t st_off = a.take(kStateBytes);
+  const size_t zb = a.take(0);
+  const size_t cf = a.take(4 * (ctiles + 1));  // look-back flags of the run-count scan
+  const size_t cv = a.take(32);                 // total, scan tickets
+  const size_t ze = a.take(0);
+  const size_t best = a.take(8 * nz + 16);
+  const size_t broot = a.take(4 * nz + 16);
+  const size_t ca = a.take(8 * 2 * (ctiles + 1));
+  const size_t hist = a.take(4 * 256 * nz + 16);
+  const size_t thr = a.take(8 * nz + 16);
+  const size_t T = a.take(4 * rows * W + 16);
+  const size_t BB = a.take(4 * rows * W + 16);
+  const size_t K = a.take(4 * rows * W + 16);
+  const size_t rr = a.take(4 * rows + 16);
+  const size_t ro = a.take(8 * rows + 16);
+  const size_t xs = a.take(2 * maxr + 16);
+  const size_t xe = a.take(2 * maxr + 16);
+  const size_t par = a.take(4 * maxr + 16);
+  const size_t sz = a.take(8 * maxr + 16);
+  if ((s = ensure_ws(ctx, a.take(0)))) return s;
+  cudaStream_t cs = (cudaStream_t)stream;
+  Launch L{cs, ctx->sms};
+  State* st = (State*)(ctx->ws + st_off);
+  char* ws = ctx->ws;
+  cudaMemsetAsync(popcount_dev, 0, 8, cs);
+  if (d.N == 0) {
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? ROIX_OK : cuda_fail(ctx, e, "paper roi launch");
+  }
+  u32* th = thresholds_dev ? thresholds_dev : (u32*)(ws + thr);
+  launch_paper_hist_otsu(L, img, dims.nx, dims.ny, nz, (u32*)(ws + hist), th);
+  launch_paper_binarize(L, img, dims.nx, dims.ny, nz, th, (u32*)(ws + T));
+  CclWs w;
+  w.row_runs = (u32*)(ws + rr);
+  w.row_off = (u64*)(ws + ro);
+  w.xs = (uint16_t*)(ws + xs);
+  w.xe = (uint16_t*)(ws + xe);
+  w.par = (u32*)(ws + par);
+  w.size = (unsigned long long*)(ws + sz);
+  w.total = (u64*)(ws + cv);
+  w.ctr = (u32*)(ws + cv + 8);
+  w.best = (unsigned long long*)(ws + best);
+  w.best_root = (u32*)(ws + broot);
+  w.lb = lb_at<1>(ws, cf, ca, ctiles);
+  w.status = &st->status;
+  // background reaching the slice border (4-connected), from the complement of M
+  Desc d4 = d;
+  d4.conn = 4;
+  launch_init(L, st, 1, ws + zb, ze - zb);
+  launch_ccl_planar(L, d4, (const u32*)(ws + T), ~0u, 1, (u32*)(ws + BB), w);
+  // the filled mask is its complement; its largest 8-connected object per slice
+  Desc d8 = d;
+  d8.conn = 8;
+  cudaMemsetAsync(ws + zb, 0, ze - zb, cs);
+  cudaMemsetAsync(ws + best, 0, 8 * nz, cs);
+  cudaMemsetAsync(ws + broot, 0, 4 * nz, cs);
+  launch_ccl_planar(L, d8, (const u32*)(ws + BB), ~0u, 0, (u32*)(ws + K), w);
+  launch_paper_spans(L, (const u32*)(ws + K), rows, W, mask_out, (u64*)popcount_dev);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ROIX_OK : cuda_fail(ctx, e, "paper roi launch");
+}

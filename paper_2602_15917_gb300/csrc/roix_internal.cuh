@@ -553,6 +553,18 @@ struct GreedyBatch {
 };
 void launch_greedy(const Launch& L, const GreedyBatch& B);
 
+// ------------------------------------------------ paper-mode ROI
+// Planar union-find (d.conn = 4 or 8): components of T (complemented when
+// inv = ~0u) touching their slice border (keep_border) or the largest of every
+// slice, into `out`; w.best / w.best_root hold one entry per slice, zeroed.
+void launch_ccl_planar(const Launch& L, const Desc& d, const u32* T, u32 inv, int keep_border,
+                       u32* out, const CclWs& w);
+void launch_paper_hist_otsu(const Launch& L, const u8* img, u64 nx, u64 ny, u64 nz, u32* hist,
+                            u32* thr);
+void launch_paper_binarize(const Launch& L, const u8* img, u64 nx, u64 ny, u64 nz,
+                           const u32* thr, u32* T);
+void launch_paper_spans(const Launch& L, const u32* K, u64 rows, u64 W, u32* D, u64* popcount);
+
 // ------------------------------------------------ evaluation metrics
 size_t roi_quality_ws_bytes(u64 nx, u64 ny, u64 nz, int distances);
 void launch_roi_quality(const Launch& L, const u32* A, const u32* B, u64 nx, u64 ny, u64 nz,
