@@ -77,6 +77,8 @@ def lib():
             L.oracle_pack.restype = u64
             L.oracle_compress.argtypes = [P, C.POINTER(_Params), u64, u64, u64,
                                           C.POINTER(C.c_void_p), C.POINTER(u64)]
+            L.oracle_compress_slabs.argtypes = [P, C.POINTER(_Params), u64, u64, u64, u64,
+                                                C.POINTER(C.c_void_p), C.POINTER(u64)]
             L.oracle_free.argtypes = [P]
             L.oracle_free.restype = None
             L.oracle_decode.argtypes = [P, u64, P, i32, u64, u64, u64]
@@ -245,6 +247,31 @@ def compress(x: np.ndarray, **cfg) -> np.ndarray:
     finally:
         L.oracle_free(out)
     return buf
+
+
+def compress_slabs(x: np.ndarray, slab_z: int, **cfg):
+    """A volume in z-slabs of slab_z slices, one container per slab (the mask
+    and the error bound are the whole volume's); returns a list of uint8 arrays."""
+    x = np.ascontiguousarray(x)
+    p = params(_dtype_code(x), **cfg)
+    nx, ny, nz = _dims(x)
+    ns = (nz + slab_z - 1) // slab_z
+    outs = (C.c_void_p * max(ns, 1))()
+    sizes = (C.c_uint64 * max(ns, 1))()
+    L = lib()
+    rc = L.oracle_compress_slabs(_ptr(x), C.byref(p), nx, ny, nz, int(slab_z), outs, sizes)
+    res = []
+    try:
+        if rc != 0:
+            raise RuntimeError(f"oracle_compress_slabs failed ({rc})")
+        for k in range(ns):
+            res.append(np.ctypeslib.as_array(C.cast(outs[k], C.POINTER(C.c_uint8)),
+                                             shape=(sizes[k],)).copy())
+    finally:
+        for k in range(ns):
+            if outs[k]:
+                L.oracle_free(outs[k])
+    return res
 
 
 def decode(buf: np.ndarray, shape, dtype) -> np.ndarray:

@@ -457,28 +457,48 @@ uint64_t oracle_pack(const uint16_t* sym, uint64_t n, const uint8_t* len,
 }
 
 // ------------------------------------------------------------------ container
-// Whole compression path: threshold -> (largest) -> dilate -> compact ->
-// error bound -> quantise -> predict -> histogram -> codebook -> pack ->
-// container. On success *out is a malloc'd buffer (free with oracle_free).
-int oracle_compress(const void* in, const OracleParams* p, uint64_t nx,
-                    uint64_t ny, uint64_t nz, uint8_t** out, uint64_t* out_size) {
-  *out = nullptr;
-  *out_size = 0;
-  if (p->dtype != DT_F32 && p->dtype != DT_U16) return ERR_INVAL;  // linear quantiser only
-  uint64_t N = nx * ny * nz, rows = ny * nz;
-  uint32_t R = p->radius, S = 2 * R, C = p->chunk;
-  std::vector<uint8_t> T(N), D(N);
+}  // extern "C"
+
+namespace {
+
+// Mask D of the whole volume: threshold -> (largest) -> dilation.
+void full_mask(const void* in, const OracleParams* p, uint64_t nx, uint64_t ny, uint64_t nz,
+               std::vector<uint8_t>& D) {
+  uint64_t N = nx * ny * nz;
+  std::vector<uint8_t> T(N);
+  D.assign(N, 0);
   oracle_threshold(in, p, nx, ny, nz, T.data());
   if (p->keep) oracle_keep_largest(T.data(), nx, ny, nz, p->connectivity);
   oracle_dilate(T.data(), nx, ny, nz, p->dilate, D.data());
+}
+
+// Error-bound constants from the retained values of the volume under D.
+void bound_of(const void* in, const OracleParams* p, uint64_t nx, uint64_t ny, uint64_t nz,
+              const uint8_t* D, OracleEb* e) {
+  uint64_t N = nx * ny * nz, rows = ny * nz;
   size_t esz = p->dtype == DT_F32 ? 4 : 2;
   std::vector<uint8_t> P(N * esz + 4);
   std::vector<uint16_t> counts(rows + 1), bounds(rows * (nx + 1) + 1);
   uint64_t nb = 0;
-  uint64_t n = (uint64_t)oracle_compact(in, p->dtype, nx, ny, nz, D.data(), P.data(),
+  uint64_t n = (uint64_t)oracle_compact(in, p->dtype, nx, ny, nz, D, P.data(), counts.data(),
+                                        bounds.data(), &nb);
+  oracle_eb(P.data(), p->dtype, n, p->eb_mode, p->eb_value, e);
+}
+
+// The container of the voxels of `in` (nx x ny x nz) retained by D, with the
+// error-bound constants e: compact -> quantise -> predict -> histogram ->
+// codebook -> pack -> container. *out is malloc'd.
+int encode_container(const void* in, const OracleParams* p, uint64_t nx, uint64_t ny,
+                     uint64_t nz, const uint8_t* D, const OracleEb& e, uint8_t** out,
+                     uint64_t* out_size) {
+  uint64_t N = nx * ny * nz, rows = ny * nz;
+  uint32_t R = p->radius, S = 2 * R, C = p->chunk;
+  size_t esz = p->dtype == DT_F32 ? 4 : 2;
+  std::vector<uint8_t> P(N * esz + 4);
+  std::vector<uint16_t> counts(rows + 1), bounds(rows * (nx + 1) + 1);
+  uint64_t nb = 0;
+  uint64_t n = (uint64_t)oracle_compact(in, p->dtype, nx, ny, nz, D, P.data(),
                                         counts.data(), bounds.data(), &nb);
-  OracleEb e;
-  oracle_eb(P.data(), p->dtype, n, p->eb_mode, p->eb_value, &e);
   std::vector<int32_t> q(n + 1);
   std::vector<uint8_t> ol(n + 1);
   oracle_quantize(P.data(), p->dtype, n, &e, p->dark, q.data(), ol.data());
@@ -560,6 +580,48 @@ int oracle_compress(const void* in, const OracleParams* p, uint64_t nx,
   *out = (uint8_t*)std::malloc(total);
   std::memcpy(*out, o.b.data(), total);
   *out_size = total;
+  return ERR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Whole compression path: mask, error bound, container. On success *out is a
+// malloc'd buffer (free with oracle_free).
+int oracle_compress(const void* in, const OracleParams* p, uint64_t nx,
+                    uint64_t ny, uint64_t nz, uint8_t** out, uint64_t* out_size) {
+  *out = nullptr;
+  *out_size = 0;
+  if (p->dtype != DT_F32 && p->dtype != DT_U16) return ERR_INVAL;  // linear quantiser only
+  std::vector<uint8_t> D;
+  full_mask(in, p, nx, ny, nz, D);
+  OracleEb e;
+  bound_of(in, p, nx, ny, nz, D.data(), &e);
+  return encode_container(in, p, nx, ny, nz, D.data(), e, out, out_size);
+}
+
+// A volume in z-slabs of slab_z slices (the last may be shorter), one
+// container per slab: the mask is the whole volume's (the dilation crosses
+// slab borders), the error bound comes from the retained values of the whole
+// volume, and each slab's stream starts afresh. keep = 1 is refused (a slab
+// is not a volume of its own). outs[s] / sizes[s] for s < ceil(nz / slab_z).
+int oracle_compress_slabs(const void* in, const OracleParams* p, uint64_t nx, uint64_t ny,
+                          uint64_t nz, uint64_t slab_z, uint8_t** outs, uint64_t* sizes) {
+  if (p->dtype != DT_F32 && p->dtype != DT_U16) return ERR_INVAL;
+  if (p->keep || slab_z == 0) return ERR_INVAL;
+  std::vector<uint8_t> D;
+  full_mask(in, p, nx, ny, nz, D);
+  OracleEb e;
+  bound_of(in, p, nx, ny, nz, D.data(), &e);
+  const uint64_t plane = nx * ny;
+  const size_t esz = p->dtype == DT_F32 ? 4 : 2;
+  for (uint64_t z0 = 0, s = 0; z0 < nz; z0 += slab_z, ++s) {
+    const uint64_t dz = std::min(slab_z, nz - z0);
+    int rc = encode_container((const uint8_t*)in + z0 * plane * esz, p, nx, ny, dz,
+                              D.data() + z0 * plane, e, &outs[s], &sizes[s]);
+    if (rc) return rc;
+  }
   return ERR_OK;
 }
 

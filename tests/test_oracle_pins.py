@@ -598,3 +598,30 @@ def test_uint8_threshold_and_compact():
 def test_uint8_refused_by_linear_path():
     with pytest.raises(Exception):
         oracle.compress(np.zeros((4, 4), np.uint8))
+
+
+# --------------------------------------------------------------- z-slabs
+@pytest.mark.parametrize("cfg", [dict(eb=1e-3, eb_mode="abs", dilate=1),
+                                 dict(eb=1e-3, eb_mode="rel", dilate=1),
+                                 dict(eb=1e-2, eb_mode="rel", dilate=0)])
+def test_slabs_decode_like_the_whole_volume(cfg):
+    x = phantom.ellipsoids(shape=(21, 18, 23), seed=8).numpy()
+    whole = oracle.compress(x, **cfg)
+    want = oracle.decode(whole, x.shape, np.float32)
+    for slab_z in (1, 4, 7, 21, 40):
+        conts = oracle.compress_slabs(x, slab_z, **cfg)
+        assert len(conts) == -(-21 // slab_z)
+        got = np.concatenate([oracle.decode(c, (oracle.header(c)["nz"],) + x.shape[1:], np.float32)
+                              for c in conts])
+        # the dilation crosses slab borders and the bound is the volume's: the
+        # decoded values equal the whole-volume decode voxel for voxel
+        assert np.array_equal(got.view(np.uint32), want.view(np.uint32)), slab_z
+        assert sum(oracle.header(c)["n"] for c in conts) == oracle.header(whole)["n"]
+        assert all(oracle.header(c)["eb_abs"] == oracle.header(whole)["eb_abs"] for c in conts)
+    assert np.array_equal(oracle.compress_slabs(x, 21, **cfg)[0], whole)
+
+
+def test_slabs_refuse_keep():
+    x = phantom.ellipsoids(shape=(8, 8, 8), seed=1).numpy()
+    with pytest.raises(RuntimeError):
+        oracle.compress_slabs(x, 4, keep="largest")
