@@ -950,6 +950,221 @@ def run_serve(args, rank, world, local_rank):
     }
 
 
+# ------------------------------------------------- 2048^3 volume in z-slabs
+SLABS = {
+    "cube2048_slabs": dict(
+        n=2048, slab=64, sweep=(1e-2, 1e-3, 1e-4, 1e-5), e2e_eb=1e-4,
+        desc="2048^3 float32 porous cylinder r=800 (~20%), pores 2..30 (5%), lognormal "
+             "texture, noise 0.005 (32 GiB in HBM); 64-slice z-slabs (whole-volume mask and "
+             "bound, one container per slab); relative eb sweep 1e-2, 1e-3, 1e-4, 1e-5; "
+             "ROI > 0.1 + 1-voxel dilation",
+        cfg=dict(eb_mode="rel", cmp="gt", threshold=0.1, dilate=1, fill=0.0, radius=512,
+                 chunk=4096)),
+}
+
+
+def slab_stage_bytes(N, nx, hdrs):
+    """Algorithmic bytes per stage of one slab-compression call (float32)."""
+    esz = 4
+    rows = N // nx
+    n = sum(h["n"] for h in hdrs)
+    nb = sum(h["n_bounds"] for h in hdrs)
+    nout = sum(h["n_outliers"] for h in hdrs)
+    nw = sum(h["payload_words"] for h in hdrs)
+    nch = sum(h["n_chunks"] for h in hdrs)
+    S = 2 * hdrs[0]["radius"]
+    return {"reset": 0.0, "threshold": N * esz + N / 8,
+            "front": N / 8 + 2 * n * esz + 2 * nb + 2 * rows,
+            "symbols": n * esz + 2 * n + 12 * nout, "codebook": len(hdrs) * 13 * S,
+            "pack": 2 * n + 4 * nw + 8 * nch, "finalize": len(hdrs) * 256 + 12 * nout}
+
+
+def slab_cpu(sc, budget_s, seed=0):
+    """The oracle as it stands on one host core: oracle.compress_slabs on
+    whole 2048 x 2048 slices from the cylinder's middle (8 per call)."""
+    import oracle
+    import phantom
+    n = sc["n"]
+    z0 = n // 2 - 4
+    x = phantom.porous_cylinder(n, radius=n * 400.0 / 1024, texture=True, seed=seed,
+                                z_range=(z0, z0 + 8)).numpy()
+    cfg = dict(sc["cfg"], eb=sc["e2e_eb"])
+    done, t0, i = 0, time.perf_counter(), 0
+    while True:
+        oracle.compress_slabs(x, 8, **cfg)
+        done += x.nbytes
+        i += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": round(done / dt / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"8 middle slices (2048^2 each) as one slab, rel eb {sc['e2e_eb']}, "
+                      f"repeated for ~{budget_s:.0f} s: {i} calls, {done / 1e6:.0f} MB in "
+                      f"{dt:.1f} s"}
+
+
+def run_slabs(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    import oracle
+    import phantom
+    import paper_2602_15917_gb300 as roix
+
+    sc = SLABS[args.workload]
+    n, slab = sc["n"], sc["slab"]
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    x = phantom.porous_cylinder(n, radius=n * 400.0 / 1024, texture=True, seed=args.seed,
+                                device=dev)
+    torch.cuda.synchronize()
+    in_bytes = x.numel() * 4
+    rx = roix.Roix(local_rank)
+    main = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(main)
+    ns = (n + slab - 1) // slab
+    cap = slab * n * n * 4 // 4 + (1 << 20)
+    outs = [torch.empty(cap, dtype=torch.uint8, device=dev) for _ in range(ns)]
+    sizes = torch.zeros(ns, dtype=torch.uint64, device=dev)
+    cfgs = [dict(sc["cfg"], eb=eb) for eb in sc["sweep"]]
+    rx.reserve(rx.slabs_workspace_size(x.shape, slab, cap=cap, **cfgs[0]))
+
+    def one(cfg, inp=None):
+        rx.compress_slabs(x if inp is None else inp, slab, outs=outs, caps=[cap] * ns,
+                          sizes=sizes, stream=main, **cfg)
+
+    # per eb: one checked call (sizes, CR) outside the timed region
+    sweep = []
+    for cfg in cfgs:
+        one(cfg)
+        rx.sync(main)
+        sz = [int(v) for v in sizes.cpu().numpy()]
+        sweep.append({"eb_rel": cfg["eb"], "bytes_out": sum(sz),
+                      "compression_ratio": round(in_bytes / max(sum(sz), 1), 3)})
+
+    def step():
+        for cfg in cfgs:
+            one(cfg)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local_rank) as clk:
+        e0.record(main)
+        for _ in range(args.steps):
+            step()
+        e1.record(main)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    rx.sync(main)
+    t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_step = float(t.item()) / args.steps
+    value = len(cfgs) * in_bytes * world / (ms_step / 1e3) / 1e9
+    # per eb: device time of one call (latency) over the steps
+    for j, cfg in enumerate(cfgs):
+        ts = []
+        for _ in range(max(3, args.steps // 2)):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(main)
+            one(cfg)
+            b.record(main)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        sweep[j]["ms_p50"] = round(float(np.percentile(ts, 50)), 3)
+        sweep[j]["GBps"] = round(in_bytes / (sweep[j]["ms_p50"] / 1e3) / 1e9, 1)
+    rx.sync(main)
+
+    # end to end at one eb: the volume uploaded from pinned host memory into
+    # the device buffer, compressed, every slab's container read back
+    cfg_e = dict(sc["cfg"], eb=sc["e2e_eb"])
+    one(cfg_e)
+    rx.sync(main)
+    sz = [int(v) for v in sizes.cpu().numpy()]
+    host_in = torch.empty(x.shape, dtype=torch.float32).pin_memory()
+    host_in.copy_(x)
+    host_out = torch.empty(sum(sz) + 16 * ns, dtype=torch.uint8).pin_memory()
+    host_sizes = torch.empty(ns, dtype=torch.uint64).pin_memory()
+
+    def e2e_step():
+        x.copy_(host_in, non_blocking=True)
+        one(cfg_e)
+        host_sizes.copy_(sizes, non_blocking=True)
+        o = 0
+        for k in range(ns):
+            host_out[o:o + sz[k]].copy_(outs[k][:sz[k]], non_blocking=True)
+            o += sz[k]
+
+    e2e_step()
+    torch.cuda.synchronize()
+    k_e2e = max(2, min(args.steps, 5))
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / k_e2e
+    rx.sync(main)
+    te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_s = float(te.item())
+    e2e = {"value": round(in_bytes * world / e2e_s / 1e9, 2), "unit": "GB/s",
+           "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": sum(sz) + 8 * ns,
+           "how": "rel eb %g: the 32 GiB volume uploaded from pinned host memory, compressed "
+                  "in slabs, every container read back to pinned memory, serially" % sc["e2e_eb"]}
+
+    # dominant kernel: per-stage events of one call at the e2e bound
+    rx.profile(True)
+    stage_ms = np.zeros(8)
+    reps = 3
+    for _ in range(reps):
+        one(cfg_e)
+        st = rx.profile_read(8)
+        stage_ms[:len(st)] += st
+    rx.profile(False)
+    rx.sync(main)
+    stage_ms /= reps
+    names = ["reset", "threshold", "front", "symbols", "codebook", "pack", "finalize"]
+    hdrs = [oracle.header(outs[k][:256].cpu().numpy()) for k in range(ns)]
+    alg = slab_stage_bytes(x.numel(), n, hdrs)
+    dom = int(np.argmax(stage_ms[:7]))
+    peak, peak_kind = load_peaks()
+    ach = alg[names[dom]] / (stage_ms[dom] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": names[dom], "achieved": round(ach, 1),
+                "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
+                "frac": round(ach / peak, 4), "traffic": None,
+                "algorithmic_bytes_per_step": round(alg[names[dom]]),
+                "stage_ms_per_call": {k: round(float(v), 4) for k, v in zip(names, stage_ms)},
+                "stage_gbs": {k: round(alg[k] / (float(v) / 1e3) / 1e9, 1)
+                              for k, v in zip(names, stage_ms) if v > 0}}
+    launches = (2 + 5 * ((ns + 63) // 64)) * len(cfgs) * args.steps
+    result = None
+    if rank == 0:
+        cpu = slab_cpu(sc, args.cpu_budget, args.seed) if world == 1 and not args.no_cpu else None
+        result = {
+            "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "desc": sc["desc"], "slabs": ns,
+                       "bytes_in_per_call": in_bytes, "calls_per_step": len(cfgs),
+                       "sweep": sweep, "path": "roix_compress_slabs: 7 launches per call "
+                       "(32 slabs in one group)", "l2": "inputs larger than L2 (129 MB)",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
+            "gpu_launches": launches, "clocks": clk.summary(),
+        }
+    rx.close()
+    return result
+
+
 # ---------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
     if rank != 0:
@@ -966,6 +1181,22 @@ def run_reference(args, rank, world):
                 "impl": "reference", "config": {"workload": args.workload, "desc": ev["desc"]},
                 "cpu_baseline": c, "e2e": {"value": c["value"], "unit": "GB/s",
                                            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    if args.workload in SLABS:
+        sc = SLABS[args.workload]
+        per_step = max(1.0, args.cpu_budget / max(1, args.steps + args.warmup))
+        for _ in range(args.warmup):
+            slab_cpu(sc, per_step, args.seed)
+        vals = [slab_cpu(sc, per_step, args.seed) for _ in range(args.steps)]
+        gbs = float(np.mean([v["value"] for v in vals]))
+        return {"metric": METRIC, "value": round(gbs, 4), "unit": "GB/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic", "impl": "reference",
+                "config": {"workload": args.workload, "desc": sc["desc"]},
+                "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s", "cores": 1,
+                                 "kind": "oracle", "sample": vals[-1]["sample"]},
+                "e2e": {"value": round(gbs, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
     if args.workload in PAPER8:
         pc = PAPER8[args.workload]
         xs = make_inputs(pc["base"], "cpu", seed=args.seed)
@@ -1019,7 +1250,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="projections64",
-                    choices=sorted(WORKLOADS) + sorted(PAPER8) + sorted(EVAL) + ["serve"])
+                    choices=sorted(WORKLOADS) + sorted(PAPER8) + sorted(EVAL) + sorted(SLABS)
+                    + ["serve"])
     ap.add_argument("--serve-seconds", type=float, default=15.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-budget-gb", type=int, default=120)
@@ -1047,6 +1279,7 @@ def main():
         res = (run_serve(args, rank, world, local_rank) if args.workload == "serve"
                else run_paper8(args, rank, world, local_rank) if args.workload in PAPER8
                else run_eval(args, rank, world, local_rank) if args.workload in EVAL
+               else run_slabs(args, rank, world, local_rank) if args.workload in SLABS
                else run_ours(args, rank, world, local_rank))
         if world > 1:
             import torch.distributed as dist

@@ -336,6 +336,38 @@ roix_status roix_compress_batch(roix_ctx* ctx, uint32_t n, const roix_item* item
                                 roix_dtype dtype, const roix_roi* roi, const roix_eb* eb,
                                 const roix_params* params, void* stream);
 
+/* A volume in z-slabs (no paper counterpart; the streaming form of
+ * roix_compress for volumes of tens of GB, e.g. 2048^3 float32 in 64-slice
+ * slabs). The volume is cut into ns = ceil(nz / slab_z) slabs of slab_z slices
+ * (the last may be shorter); slab s (slices [s*slab_z, s*slab_z + dz_s)) gets a
+ * container of its own, decodable alone by roix_decode as an nx x ny x dz_s
+ * volume. What makes the slabs one volume:
+ *  - the mask D is the whole volume's: the dilation of a slab's border slices
+ *    sees the neighbouring slab's T (Sec. 4.1.4 binarisation of the whole scan);
+ *  - the error bound is the whole volume's: with a relative bound, E_abs =
+ *    value * (max - min) over the finite retained values of all slabs, and
+ *    every container carries that E_abs and that range;
+ *  - each slab's pixel section, prediction (q[-1] = 0), histogram, codebook and
+ *    payload are its own, so the slabs decode independently.
+ * The slabs' decodes, stacked, equal the decode of roix_compress's container
+ * for the whole volume voxel for voxel; with slab_z >= nz the single container
+ * is roix_compress's, byte for byte. keep = 1 is refused (ROIX_EINVAL): the
+ * largest object of a slab is not the volume's. float32 and uint16 only.
+ *  outs, caps: HOST arrays of ns entries: 16-byte aligned device buffers and
+ *              their sizes in bytes;
+ *  sizes_dev:  ns uint64 on the device: each container's size (the size needed
+ *              with ROIX_ECAPACITY when it exceeds its cap).
+ * Workspace: roix_slabs_workspace_size (cap = the largest slab cap); about
+ * (esz + 2) bytes per voxel plus the whole volume's bit mask. */
+roix_status roix_compress_slabs(roix_ctx* ctx, const void* in, roix_dtype dtype, roix_dims dims,
+                                uint64_t slab_z, const roix_roi* roi, const roix_eb* eb,
+                                const roix_params* params, void* const* outs,
+                                const uint64_t* caps, uint64_t* sizes_dev, void* stream);
+/* Workspace bytes roix_compress_slabs needs when every slab's cap is `cap`
+ * (0 for invalid arguments). */
+size_t roix_slabs_workspace_size(roix_dtype dtype, roix_dims dims, uint64_t slab_z,
+                                 const roix_roi* roi, const roix_params* params, uint64_t cap);
+
 /* --------------------------------------------------------------- serving
  * A serving loop for compression requests that arrive over time (no paper
  * counterpart; a deployment form of roix_compress_batch). The server holds

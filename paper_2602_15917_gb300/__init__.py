@@ -144,6 +144,9 @@ def lib():
                 "roix_roi_quality": (st, [P, P, P, D, C.c_int, P, P]),
                 "roix_extract_roi_paper": (st, [P, P, D, P, P, P, P]),
                 "roix_ssim": (st, [P, P, P, i32, D, C.c_double, P, P]),
+                "roix_compress_slabs": (st, [P, P, i32, D, u64, R, E, PR, C.POINTER(P),
+                                             C.POINTER(u64), P, P]),
+                "roix_slabs_workspace_size": (C.c_size_t, [i32, D, u64, R, PR, u64]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -163,7 +166,8 @@ def symbols():
             "roix_server_create", "roix_server_submit", "roix_server_poll", "roix_server_drain",
             "roix_server_get_stats", "roix_server_destroy", "roix_normalize8",
             "roix_greedy_quantize", "roix_greedy_quantize_batch", "roix_roi_quality",
-            "roix_ssim", "roix_extract_roi_paper"]
+            "roix_ssim", "roix_extract_roi_paper", "roix_compress_slabs",
+            "roix_slabs_workspace_size"]
 
 
 def _dtype_code(t: torch.Tensor) -> int:
@@ -297,6 +301,41 @@ class Roix:
             self.ctx, n, arr, _dtype_code(xs[0]), C.byref(roi_of(**cfg)), C.byref(eb_of(**cfg)),
             C.byref(params_of(**cfg)), _stream(stream)))
         return outs, sizes
+
+    def slabs_workspace_size(self, shape, slab_z: int, dtype=torch.float32, cap=None,
+                             **cfg) -> int:
+        code = F32 if dtype == torch.float32 else U16
+        d = dims_of(shape)
+        if cap is None:
+            cap = self.bound((min(int(slab_z), int(d.nz)), d.ny, d.nx), dtype, **cfg)
+        return int(self.L.roix_slabs_workspace_size(code, d, int(slab_z), C.byref(roi_of(**cfg)),
+                                                    C.byref(params_of(**cfg)), int(cap)))
+
+    def compress_slabs(self, x: torch.Tensor, slab_z: int, outs=None, caps=None,
+                       sizes: torch.Tensor | None = None, stream=None, **cfg):
+        """Enqueues the compression of the 3D tensor x in z-slabs of slab_z
+        slices (whole-volume mask and error bound, one container per slab);
+        returns (outs, sizes) with sizes a uint64 device tensor, one per slab."""
+        assert x.is_cuda and x.is_contiguous() and x.dim() == 3
+        nz = int(x.shape[0])
+        ns = (nz + int(slab_z) - 1) // int(slab_z) if nz and int(slab_z) > 0 else 0
+        if outs is None:
+            if caps is None:
+                caps = []
+                for k in range(ns):  # the worst case: every voxel retained, every value a record
+                    dz = min(int(slab_z), nz - k * int(slab_z))
+                    caps.append(self.bound((dz, x.shape[1], x.shape[2]), x.dtype, **cfg))
+            outs = [torch.empty(c, dtype=torch.uint8, device=x.device) for c in caps]
+        caps = [o.numel() for o in outs] if caps is None else caps
+        if sizes is None:
+            sizes = torch.zeros(max(ns, 1), dtype=torch.uint64, device=x.device)
+        po = (C.c_void_p * max(ns, 1))(*[o.data_ptr() for o in outs])
+        pc = (C.c_uint64 * max(ns, 1))(*[int(c) for c in caps])
+        self._check(self.L.roix_compress_slabs(
+            self.ctx, x.data_ptr(), _dtype_code(x), dims_of(x.shape), int(slab_z),
+            C.byref(roi_of(**cfg)), C.byref(eb_of(**cfg)), C.byref(params_of(**cfg)), po, pc,
+            sizes.data_ptr(), _stream(stream)))
+        return outs, sizes[:ns]
 
     def compress_bytes(self, x: torch.Tensor, **cfg) -> torch.Tensor:
         """compress + sync; returns the container as a uint8 device tensor. An

@@ -2,6 +2,8 @@
 // linear lattice of Sec. 4.3), 1D Lorenzo prediction with symbolisation and a
 // histogram, the canonical Huffman codebook, the chunked bit packer and the
 // container finaliser.
+#include <type_traits>
+
 #include "roix_internal.cuh"
 
 namespace roix {
@@ -147,26 +149,9 @@ __device__ __forceinline__ u32 symbol_of(int c, int prev, bool out, u32 R) {
   return (dd + R - 1u < 2u * R - 1u) ? dd + R : 0u;
 }
 
-// bits 0..15 of v spread to the even positions 0, 2, ..., 30
-__device__ __forceinline__ u32 spread16(u32 v) {
-  v &= 0xffffu;
-  v = (v | (v << 8)) & 0x00ff00ffu;
-  v = (v | (v << 4)) & 0x0f0f0f0fu;
-  v = (v | (v << 2)) & 0x33333333u;
-  v = (v | (v << 1)) & 0x55555555u;
-  return v;
-}
-
-// Persistent blocks take tiles of kQuantTile values; each warp owns a
-// contiguous span of the tile and walks it 64 values (a pair per lane) per
-// step, so loads and symbol stores are coalesced vectors and the predecessor
-// of a step's first value is the warp's own last value of the step before.
-// Loads of four steps are issued before any is used. Symbol-0 positions
-// (records) are marked in a shared bitmap, counted, placed by the look-back
-// and written in order. The histogram lives in shared memory per block and is
-// flushed once at the end.
-// Tiles of every item, in order: prefix of ceil(n_i / kQuantTile) over the
-// items (n_i found by the compaction), computed by each block at start.
+// Segments of kQuantTile values, every item's segments in order: prefix of
+// ceil(n_i / per) / group over the items (n_i found by the compaction),
+// computed by each block at start.
 __device__ __forceinline__ void tile_prefix(const Batch& B, u64* pre, u64 per, u64 group) {
   if (threadIdx.x == 0) {
     u64 acc = 0;
@@ -181,152 +166,254 @@ __device__ __forceinline__ void tile_prefix(const Batch& B, u64* pre, u64 per, u
   __syncthreads();
 }
 
+// Per-lane vector of one step: V consecutive values (one 16-byte load of the
+// pixel section, or an 8-byte load of staged codes with their outlier word).
+template <typename TV, bool FROM_Q>
+struct SymVec {
+  static constexpr int V = FROM_Q ? 2 : 16 / (int)sizeof(TV);
+  TV x[V];
+  int q[V];
+  u32 o;
+};
+
+template <typename TV, bool FROM_Q>
+__device__ __forceinline__ void sym_load(const Src<TV, FROM_Q>& src, u64 k0, u64 n,
+                                         SymVec<TV, FROM_Q>& r) {
+  constexpr int V = SymVec<TV, FROM_Q>::V;
+  r.o = 0u;
+  if constexpr (FROM_Q) {
+    if (k0 + V <= n) {
+      const int2 v = __ldg(reinterpret_cast<const int2*>(src.q + k0));
+      r.q[0] = v.x;
+      r.q[1] = v.y;
+    } else {
+#pragma unroll
+      for (int j = 0; j < V; ++j) r.q[j] = k0 + j < n ? __ldg(src.q + k0 + j) : 0;
+    }
+    r.o = k0 < n ? (__ldg(src.obits + (k0 >> 5)) >> (k0 & 31)) & 3u : 0u;  // V = 2, k0 even
+  } else {
+    if (k0 + V <= n) {
+      const uint4 v = __ldg(reinterpret_cast<const uint4*>(src.P + k0));
+      const u32 w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int j = 0; j < V; ++j) {
+        if constexpr (sizeof(TV) == 4) r.x[j] = __uint_as_float(w[j]);
+        else r.x[j] = (TV)((w[j >> 1] >> (16 * (j & 1))) & 0xffffu);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < V; ++j) r.x[j] = k0 + j < n ? __ldg(src.P + k0 + j) : TV(0);
+    }
+  }
+}
+
+// Code of element j of a loaded vector (0 and out = true for an outlier).
+template <typename TV, bool FROM_Q>
+__device__ __forceinline__ int sym_eval(const Src<TV, FROM_Q>& src,
+                                        const SymVec<TV, FROM_Q>& r, int j, bool& out) {
+  if constexpr (FROM_Q) {
+    out = ((r.o >> j) & 1u) != 0u;
+    return out ? 0 : r.q[j];
+  } else if constexpr (sizeof(TV) == 4) {
+    return quant_f32(r.x[j], src.e, out);
+  } else {
+    out = false;
+    return quant_u16_fd(r.x[j], src.dark, src.e.eb_int, src.fd);
+  }
+}
+
+// One warp's histogram (shared memory) added to the item's global one.
+__device__ __forceinline__ void flush_hist(u32* h, unsigned long long* g, u32 S, int lane) {
+  __syncwarp();
+  for (u32 i = lane; i < S; i += 32) {
+    const u32 v = h[i];
+    if (v) {
+      atomicAdd(g + i, (unsigned long long)v);
+      h[i] = 0;
+    }
+  }
+  __syncwarp();
+}
+
+// Persistent warps, each on its own: a warp takes the next segment of
+// kQuantTile values (global ticket, every item's segments in order) and walks
+// it in steps of 32 V values, lane l holding V consecutive values of a step
+// (one vector load each; the loads of kBatch steps are issued before any is
+// used). Codes are formed on the fly from the pixel section (or read from the
+// staged codes); the predecessor of a lane's first value comes from the lane
+// before it, of lane 0's from the warp's previous step, of the segment's first
+// from value base - 1, quantised again. Symbols leave as one vector store per
+// lane and step; the histogram is the warp's own in shared memory (no block
+// barrier anywhere in the loop) and goes to the item's global histogram when
+// the warp moves to another item. Symbol-0 positions (records) are kept as a
+// 128-bit mask per lane; the segment's record count is placed by a warp-level
+// decoupled look-back and the records are written in value order.
 template <typename TV, bool FROM_Q>
 __global__ void __launch_bounds__(kThreads) k_symbols(const __grid_constant__ Batch B) {
-  using R = typename Src<TV, FROM_Q>::R;
-  constexpr u32 kSpan = kQuantTile / (kThreads / 32);  // values per warp and tile
-  constexpr int kSteps = kSpan / 64;
-  constexpr int kBatch = 4;
-  __shared__ u32 h[kMaxSym];
-  __shared__ u32 bitmap[kQuantTile / 32];
-  __shared__ u32 scratch[40];
-  __shared__ u64 s_tile, s_base;
+  using Vec = SymVec<TV, FROM_Q>;
+  constexpr int V = Vec::V;
+  constexpr u32 kStep = 32u * V;                 // values per warp and step
+  constexpr int kSteps = (int)(kQuantTile / kStep);
+  constexpr int kBatch = V >= 8 ? 4 : (kSteps < 8 ? kSteps : 8);  // loads in flight per lane
+  static_assert(kQuantTile / 32 == 128, "128 values per lane and segment: two mask words");
+  static_assert(kSteps % kBatch == 0 && 64 % V == 0, "whole batches, steps within one word");
+  extern __shared__ u32 hsm[];  // [warps][S]
   __shared__ u64 pre[kMaxBatch + 1];
-  static_assert(kQuantTile / 32 == kThreads, "one bitmap word per thread");
-  static_assert(kSteps % kBatch == 0, "whole batches");
   const u32 R_ = B.c.R, S = B.c.S;
-  for (u32 i = threadIdx.x; i < S; i += blockDim.x) h[i] = 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  u32* h = hsm + (u32)warp * S;
+  for (u32 i = lane; i < S; i += 32) h[i] = 0;
   tile_prefix(B, pre, kQuantTile, 1);
   const u64 total = pre[B.n];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   u32 cur = 0xffffffffu;
+  u32 since_flush = 0;
   Src<TV, FROM_Q> src{};
   u64 n = 0;
   while (true) {
-    if (threadIdx.x == 0) s_tile = atomicAdd(&B.ctr[1], 1u);
-    __syncthreads();
-    const u64 gt = s_tile;
+    u64 gt = 0;
+    if (lane == 0) gt = atomicAdd(&B.ctr[1], 1u);
+    gt = __shfl_sync(0xffffffffu, gt, 0);
     if (gt >= total) break;
     const u32 item = find_item(pre, B.n, gt);
     const Item& I = B.it[item];
-    if (item != cur) {  // histogram of the previous item out, the next one's settings in
-      if (cur != 0xffffffffu) {
-        unsigned long long* hg = B.it[cur].hist;
-        for (u32 i = threadIdx.x; i < S; i += blockDim.x)
-          if (h[i]) {
-            atomicAdd(hg + i, (unsigned long long)h[i]);
-            h[i] = 0;
-          }
+    if (item != cur || since_flush >= (1u << 19)) {  // 2^19 segments keep u32 counts exact
+      if (cur != 0xffffffffu) flush_hist(h, B.it[cur].hist, S, lane);
+      since_flush = 0;
+      if (item != cur) {
+        cur = item;
+        const Desc d = desc_of(B, I);
+        src.P = (const TV*)I.P;
+        src.q = I.q;
+        src.obits = I.obits;
+        src.dark = d.dark;
+        if constexpr (!FROM_Q) {
+          src.e = make_eb(d, I.rst->vmin_key, I.rst->vmax_key);
+          src.fd = FastDiv(2u * (u32)src.e.eb_int);
+        }
+        n = umin(I.sizes[0], I.N);
       }
-      cur = item;
-      const Desc d = desc_of(B, I);
-      src.P = (const TV*)I.P;
-      src.q = I.q;
-      src.obits = I.obits;
-      src.dark = d.dark;
-      if constexpr (!FROM_Q) {
-        src.e = make_eb(d, I.st->vmin_key, I.st->vmax_key);
-        src.fd = FastDiv(2u * (u32)src.e.eb_int);
-      }
-      n = umin(I.sizes[0], I.N);
-      __syncthreads();
     }
+    ++since_flush;
     const u64 t = gt - pre[item];
-    const u64 ntiles = (n + kQuantTile - 1) / kQuantTile;
-    uint16_t* __restrict__ sym = I.sym;
+    const u64 nseg = (n + kQuantTile - 1) / kQuantTile;
     const u64 base = t * kQuantTile;
-    const u64 span = base + (u64)warp * kSpan;
-    bitmap[threadIdx.x] = 0u;
-    // code of the value just before the warp's span
-    int carry = 0;
-    if (lane == 0 && span > 0 && span < n) {
-      bool op;
-      carry = src.code(span - 1, op);
+    uint16_t* __restrict__ sym = I.sym;
+    int carry = 0;  // code of value base - 1 (0 for an outlier or none)
+    if (lane == 0 && base > 0) {
+      bool o;
+      carry = src.code(base - 1, o);
     }
     carry = __shfl_sync(0xffffffffu, carry, 0);
-    __syncthreads();
-    for (int b0 = 0; b0 < kSteps; b0 += kBatch) {
-      R ra[kBatch], rb[kBatch];
+    u64 rm0 = 0, rm1 = 0;  // record positions: bit s * V + j
+    // one step: V codes per lane, deltas, symbols, histogram, record bits;
+    // GUARD = the segment reaches past n (the item's last segment)
+    auto step = [&](auto guard_tag, const int st, const Vec& r) {
+      constexpr bool GUARD = decltype(guard_tag)::value;
+      const u64 k0 = base + (u64)st * kStep + (u64)lane * V;
+      int c[V];
+      bool o[V];
 #pragma unroll
-      for (int j = 0; j < kBatch; ++j) {
-        const u64 k0 = span + 64 * (u64)(b0 + j) + 2 * lane;
-        if (k0 + 1 < n) {
-          src.load2(k0, ra[j], rb[j]);
-        } else {
-          ra[j] = k0 < n ? src.load1(k0) : R{TV(0), 0, 0u};
-          rb[j] = R{TV(0), 0, 0u};
+      for (int j = 0; j < V; ++j) {
+        if (!GUARD || k0 + j < n) c[j] = sym_eval<TV, FROM_Q>(src, r, j, o[j]);
+        else {
+          c[j] = 0;
+          o[j] = false;
         }
       }
+      int prev = __shfl_up_sync(0xffffffffu, c[V - 1], 1);
+      if (lane == 0) prev = carry;
+      carry = __shfl_sync(0xffffffffu, c[V - 1], 31);
+      u32 sv[V];
+      u32 rb = 0;
 #pragma unroll
-      for (int j = 0; j < kBatch; ++j) {
-        const int it = b0 + j;
-        const u64 k0 = span + 64 * (u64)it + 2 * lane, k1 = k0 + 1;
-        bool o0 = false, o1 = false;
-        const int c0 = k0 < n ? src.eval(ra[j], o0) : 0;
-        const int c1 = k1 < n ? src.eval(rb[j], o1) : 0;
-        int prev = __shfl_up_sync(0xffffffffu, c1, 1);
-        if (lane == 0) prev = carry;
-        carry = __shfl_sync(0xffffffffu, c1, 31);
-        const u32 s0 = k0 < n ? symbol_of(c0, prev, o0, R_) : 1u;
-        const u32 s1 = k1 < n ? symbol_of(c1, c0, o1, R_) : 1u;
-        if (k1 < n) {
-          *reinterpret_cast<u32*>(sym + k0) = s0 | (s1 << 16);
-        } else if (k0 < n) {
-          sym[k0] = (uint16_t)s0;
+      for (int j = 0; j < V; ++j) {
+        const bool in = !GUARD || k0 + j < n;
+        sv[j] = symbol_of(c[j], j ? c[j - 1] : prev, o[j], R_);
+        if (in) {
+          atomicAdd(&h[sv[j]], 1u);
+          rb |= (sv[j] == 0u ? 1u : 0u) << j;
         }
-        const bool r0 = k0 < n && s0 == 0, r1 = k1 < n && s1 == 0;
-        const u32 bb0 = __ballot_sync(0xffffffffu, r0), bb1 = __ballot_sync(0xffffffffu, r1);
-        if ((bb0 | bb1) && lane < 2) {  // records are rare: the bitmap starts zeroed
-          const u32 wi = warp * (kSpan / 32) + 2 * it + lane;
-          const u32 sh = lane ? 16u : 0u;
-          bitmap[wi] = spread16(bb0 >> sh) | (spread16(bb1 >> sh) << 1);
+      }
+      if (!GUARD || k0 + V <= n) {
+        if constexpr (V == 8) {
+          *reinterpret_cast<uint4*>(sym + k0) =
+              make_uint4(sv[0] | (sv[1] << 16), sv[2] | (sv[3] << 16), sv[4] | (sv[5] << 16),
+                         sv[6] | (sv[7] << 16));
+        } else if constexpr (V == 4) {
+          *reinterpret_cast<uint2*>(sym + k0) =
+              make_uint2(sv[0] | (sv[1] << 16), sv[2] | (sv[3] << 16));
+        } else {
+          *reinterpret_cast<u32*>(sym + k0) = sv[0] | (sv[1] << 16);
         }
-        // histogram: deltas of noisy data rarely repeat within a warp, so plain
-        // shared-memory atomics beat warp aggregation here
-        if (k0 < n) atomicAdd(&h[s0], 1u);
-        if (k1 < n) atomicAdd(&h[s1], 1u);
+      } else {
+#pragma unroll
+        for (int j = 0; j < V; ++j)
+          if (k0 + j < n) sym[k0 + j] = (uint16_t)sv[j];
+      }
+      const int bit = st * V;
+      if (bit < 64) rm0 |= (u64)rb << bit;
+      else rm1 |= (u64)rb << (bit - 64);
+    };
+    if (base + kQuantTile <= n) {  // a whole segment: no bounds checks
+#pragma unroll
+      for (int b0 = 0; b0 < kSteps; b0 += kBatch) {
+        Vec r[kBatch];
+#pragma unroll
+        for (int i = 0; i < kBatch; ++i)
+          sym_load<TV, FROM_Q>(src, base + (u64)(b0 + i) * kStep + (u64)lane * V, ~0ull, r[i]);
+#pragma unroll
+        for (int i = 0; i < kBatch; ++i) step(std::false_type{}, b0 + i, r[i]);
+      }
+    } else {
+      for (int b0 = 0; b0 < kSteps; b0 += kBatch) {
+        Vec r[kBatch];
+#pragma unroll
+        for (int i = 0; i < kBatch; ++i)
+          sym_load<TV, FROM_Q>(src, base + (u64)(b0 + i) * kStep + (u64)lane * V, n, r[i]);
+#pragma unroll
+        for (int i = 0; i < kBatch; ++i) step(std::true_type{}, b0 + i, r[i]);
       }
     }
-    __syncthreads();
-    // records of this tile, in order
-    const u32 word = bitmap[threadIdx.x];
-    u32 tot;
-    const u32 off = block_excl_scan<u32>(__popc(word), scratch, &tot);
-    if (warp == 0) {
-      u64 mine[1] = {tot}, excl[1];
+    // records of the segment, placed by the look-back, written in value order
+    const u32 mine_n = warp_sum((u32)(__popcll(rm0) + __popcll(rm1)));
+    u64 rbase;
+    {
+      u64 mine[1] = {mine_n}, excl[1];
       lookback_warp<1>(I.lbq, t, mine, excl, B.status);
-      if (lane == 0) {
-        s_base = excl[0];
-        if (t == ntiles - 1) I.st->nout = excl[0] + tot;
-      }
+      rbase = excl[0];
+      if (lane == 0 && t == nseg - 1) I.st->nout = excl[0] + mine_n;
     }
-    __syncthreads();
-    if (word) {
-      u64 idx = s_base + off;
-      u32 wv = word;
-      while (wv) {
-        const int j = __ffs(wv) - 1;
-        wv &= wv - 1;
-        const u64 k = base + (u64)threadIdx.x * 32 + j;
-        bool out;
-        const int c = src.code(k, out);
-        if (idx < I.rec_cap) {
-          I.rk[idx] = k | (out ? (1ull << 63) : 0ull);
-          I.rv[idx] = out ? src.raw_bits(k) : (u32)c;
-        } else {
-          atomicExch(&I.st->cap_flag, 1u);
+    if (mine_n) {
+      u64 run = rbase;
+      for (int st = 0; st < kSteps; ++st) {
+        const int bit = st * V;
+        const u32 bits =
+            (u32)((bit < 64 ? (rm0 >> bit) : (rm1 >> (bit - 64))) & ((1ull << V) - 1ull));
+        const u32 cn = __popc(bits);
+        const u32 inc = warp_incl_scan(cn);
+        const u32 tot = __shfl_sync(0xffffffffu, inc, 31);
+        if (tot == 0) continue;
+        u64 idx = run + inc - cn;
+        u32 bb = bits;
+        while (bb) {
+          const int j = __ffs(bb) - 1;
+          bb &= bb - 1;
+          const u64 k = base + (u64)st * kStep + (u64)lane * V + j;
+          bool out;
+          const int c = src.code(k, out);
+          if (idx < I.rec_cap) {
+            I.rk[idx] = k | (out ? (1ull << 63) : 0ull);
+            I.rv[idx] = out ? src.raw_bits(k) : (u32)c;
+          } else {
+            atomicExch(&I.st->cap_flag, 1u);
+          }
+          ++idx;
         }
-        ++idx;
+        run += tot;
       }
     }
-    __syncthreads();
   }
-  __syncthreads();
-  if (cur != 0xffffffffu) {
-    unsigned long long* hg = B.it[cur].hist;
-    for (u32 i = threadIdx.x; i < S; i += blockDim.x)
-      if (h[i]) atomicAdd(hg + i, (unsigned long long)h[i]);
-  }
+  if (cur != 0xffffffffu) flush_hist(h, B.it[cur].hist, S, lane);
 }
 
 // ------------------------------------------------------------- codebook
@@ -338,17 +425,16 @@ __global__ void __launch_bounds__(kThreads) k_symbols(const __grid_constant__ Ba
 constexpr int kCbThreads = 1024;
 
 __device__ void bitonic_sort(u64* key, u32 M) {
+  // one thread per compare-exchange pair (M / 2 pairs per stage)
   for (u32 k = 2; k <= M; k <<= 1) {
     for (u32 j = k >> 1; j > 0; j >>= 1) {
-      for (u32 i = threadIdx.x; i < M; i += blockDim.x) {
-        const u32 l = i ^ j;
-        if (l > i) {
-          const u64 a = key[i], b = key[l];
-          const bool up = (i & k) == 0;
-          if ((a > b) == up) {
-            key[i] = b;
-            key[l] = a;
-          }
+      for (u32 p = threadIdx.x; p < M / 2; p += blockDim.x) {
+        const u32 i = 2 * j * (p / j) + (p % j), l = i + j;
+        const u64 a = key[i], b = key[l];
+        const bool up = (i & k) == 0;
+        if ((a > b) == up) {
+          key[i] = b;
+          key[l] = a;
         }
       }
       __syncthreads();
@@ -421,9 +507,10 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__
   for (u32 i = m + tid; i < M; i += kCbThreads) key[i] = ~0ull;
   __syncthreads();
   CB_MARK(1)
-  if (m <= (u32)kCbThreads) {
+  if (m <= 128u) {
     // rank of each (count, symbol) key among the m distinct keys: one key per
-    // thread, every thread reads the keys in the same order (smem broadcast)
+    // thread, every thread reads the keys in the same order (smem broadcast);
+    // O(m^2) work, so only for small alphabets
     u64 mine = tid < (int)m ? key[tid] : 0ull;
     u32 rank = 0;
     if (tid < (int)m)  // only the warps holding keys read them
@@ -442,47 +529,41 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__
     }
   } else if (m >= 2) {
     // two-queue construction: leaves 0..m-1 in sorted order, internal m..2m-2.
-    // Both queue fronts live in registers; an empty queue reads as the
-    // sentinel ~0 (weights are below 2^48), so "leaf if wl <= wi" keeps the
-    // leaf-first tie rule. The next front is loaded right after a pop.
+    // The fronts of both queues live in register windows (three leaves, two
+    // internal nodes) refilled from shared memory by loads issued before the
+    // comparison that needs them; an empty slot reads as the sentinel ~0
+    // (weights are below 2^48), so "leaf if wl <= wi" keeps the leaf-first tie
+    // rule. Branch-free selects keep the dependent chain per pop short.
     if (tid == 0) {
       constexpr u64 kNone = ~0ull;
       u32 lf = 0, in = 0, created = 0;
-      u64 wl = key[0] >> 16, wi = kNone;
-      u64 wl_next = m > 1 ? (key[1] >> 16) : kNone;  // the leaf after the front, prefetched
+      u64 L0 = key[0] >> 16, L1 = m > 1 ? key[1] >> 16 : kNone, L2 = m > 2 ? key[2] >> 16 : kNone;
+      u64 I0 = kNone, I1 = kNone;
       for (u32 t = 0; t + 1 < m; ++t) {
-        int32_t pa, pb;
-        u64 wa, wb;
-        if (wl <= wi) {
-          pa = (int32_t)lf;
-          wa = wl;
-          ++lf;
-          wl = wl_next;
-          wl_next = lf + 1 < m ? (key[lf + 1] >> 16) : kNone;
-        } else {
-          pa = (int32_t)(m + in);
-          wa = wi;
-          ++in;
-          wi = in < created ? wint[in] : kNone;
+        int32_t p2[2];
+        u64 wsum = 0;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const u64 nextL = lf + 3 < m ? key[lf + 3] >> 16 : kNone;
+          const u64 nextI = in + 2 < created ? wint[in + 2] : kNone;
+          const bool takeL = L0 <= I0;
+          p2[k] = takeL ? (int32_t)lf : (int32_t)(m + in);
+          wsum += takeL ? L0 : I0;
+          L0 = takeL ? L1 : L0;
+          L1 = takeL ? L2 : L1;
+          L2 = takeL ? nextL : L2;
+          I0 = takeL ? I0 : I1;
+          I1 = takeL ? I1 : nextI;
+          lf += takeL ? 1u : 0u;
+          in += takeL ? 0u : 1u;
         }
-        if (wl <= wi) {
-          pb = (int32_t)lf;
-          wb = wl;
-          ++lf;
-          wl = wl_next;
-          wl_next = lf + 1 < m ? (key[lf + 1] >> 16) : kNone;
-        } else {
-          pb = (int32_t)(m + in);
-          wb = wi;
-          ++in;
-          wi = in < created ? wint[in] : kNone;
-        }
-        const u64 w2 = wa + wb;
-        wint[created] = w2;
-        par[pa] = (int32_t)(m + created);
-        par[pb] = (int32_t)(m + created);
+        wint[created] = wsum;
+        par[p2[0]] = (int32_t)(m + created);
+        par[p2[1]] = (int32_t)(m + created);
         ++created;
-        if (in == created - 1) wi = w2;  // the queue was empty: the new node is its front
+        const u32 q = created - in;  // internal nodes waiting, the new one included
+        if (q == 1) I0 = wsum;
+        else if (q == 2) I1 = wsum;
       }
       par[2 * m - 2] = -1;
     }
@@ -585,7 +666,7 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__
         s_carry[tid] = acc;
       }
       __syncthreads();
-      if (s < S) codes_ws[s] = l ? s_next[l] + wcnt[warp][l] + below : 0u;
+      if (s < S) codes_ws[s] = l ? (l << 24) | (s_next[l] + wcnt[warp][l] + below) : 0u;
       __syncthreads();
     }
   }
@@ -598,153 +679,131 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__
 }
 
 // ------------------------------------------------------------------- pack
-// Persistent blocks take ranges of kPackRange chunks of C symbols, in order.
-// Pass 1 sums the code lengths of every chunk of the range (block scans; the
-// per-thread bit offsets are kept in shared memory); one look-back per range
-// gives the range's word offset. Pass 2 re-reads each chunk (from L2), shifts
-// every thread's codes through a 64-bit register, stores the words that lie
-// wholly inside its bit range and OR-s only its first and last (shared)
-// words into the shared buffer, which is copied out with coalesced stores.
+// Persistent warps, each on its own chunk of C symbols (global ticket, every
+// item's chunks in order), in rounds of 256 symbols: lane l holds symbols
+// [8 l, 8 l + 8) of a round (one coalesced 16-byte load) and looks their
+// length << 24 | code up in the item's code table, copied into the warp's own
+// shared memory. Pass 1 sums the lengths; a warp-level decoupled look-back
+// gives the chunk's word offset in the payload. Pass 2 gives every code its
+// bit offset (lane sums scanned across the warp) and ORs it, MSB first, into
+// a ring of words in the warp's shared memory (a code spans at most two
+// words); after each round the words that are complete are stored with
+// coalesced stores and cleared. No block barrier in the loop.
+constexpr u32 kPackRing = 256;  // words per warp ring: one round is at most 193 open words
 
-template <int EPT>
-__device__ __forceinline__ void load_syms(const uint16_t* __restrict__ sym, u64 k0, u64 n,
-                                          uint16_t (&sv)[EPT]) {
-  if constexpr (EPT % 8 == 0) {
-    if (k0 + EPT <= n) {
+__device__ __forceinline__ void pack_load8(const uint16_t* __restrict__ sym, u64 k, u64 n,
+                                           u32 (&s8)[8]) {
+  if (k + 8 <= n) {
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(sym + k));
+    const u32 w4[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-      for (int j = 0; j < EPT; j += 8) {
-        const uint4 v = __ldg(reinterpret_cast<const uint4*>(sym + k0 + j));
-        const u32 w4[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          sv[j + 2 * q] = (uint16_t)(w4[q] & 0xffffu);
-          sv[j + 2 * q + 1] = (uint16_t)(w4[q] >> 16);
-        }
-      }
-      return;
+    for (int q = 0; q < 4; ++q) {
+      s8[2 * q] = w4[q] & 0xffffu;
+      s8[2 * q + 1] = w4[q] >> 16;
     }
-  }
+  } else {
 #pragma unroll
-  for (int j = 0; j < EPT; ++j) sv[j] = k0 + j < n ? __ldg(sym + k0 + j) : (uint16_t)0;
+    for (int q = 0; q < 8; ++q) s8[q] = k + q < n ? (u32)__ldg(sym + k + q) : 0xffffffffu;
+  }
 }
 
-template <int EPT>  // symbols per thread = C / 256
-__global__ void __launch_bounds__(kThreads, 4) k_pack(const __grid_constant__ Batch B) {
-  extern __shared__ u32 wbuf[];  // C * 24 / 32 + 2 words
-  constexpr u32 kPackWordsMax = EPT * kThreads * kLMax / 32 + 2;
-  __shared__ uint8_t slen[kMaxSym];
-  __shared__ u32 scode[kMaxSym];
-  __shared__ u32 boffs[kPackRange][kThreads];
-  __shared__ u32 cwords[kPackRange];
-  __shared__ u32 scratch[40];
-  __shared__ u64 s_tile, s_base;
+__global__ void __launch_bounds__(kThreads) k_pack(const __grid_constant__ Batch B) {
+  extern __shared__ u32 tsm[];  // [warps][S] length << 24 | code, then [warps][kPackRing]
   __shared__ u64 pre[kMaxBatch + 1];
   const u32 C = B.c.C, S = B.c.S;
-  tile_prefix(B, pre, C, kPackRange);
-  const u64 total = pre[B.n];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  u32* tab = tsm + (u32)warp * S;
+  u32* ring = tsm + (kThreads / 32) * S + (u32)warp * kPackRing;
+  for (u32 i = lane; i < kPackRing; i += 32) ring[i] = 0u;
+  tile_prefix(B, pre, C, 1);
+  const u64 total = pre[B.n];
+  const u32 rounds = C / 256;
   u32 cur = 0xffffffffu;
-  u64 n = 0, nchunks = 0, nranges = 0;
+  u64 n = 0, nchunks = 0, cap = 0;
   Layout Lo{};
   const uint16_t* __restrict__ sym = nullptr;
   uint8_t* out = nullptr;
-  u64 cap = 0;
   while (true) {
-    if (threadIdx.x == 0) s_tile = atomicAdd(&B.ctr[2], 1u);
-    __syncthreads();
-    const u64 gr = s_tile;
-    if (gr >= total) break;
-    const u32 item = find_item(pre, B.n, gr);
+    u64 gt = 0;
+    if (lane == 0) gt = atomicAdd(&B.ctr[2], 1u);
+    gt = __shfl_sync(0xffffffffu, gt, 0);
+    if (gt >= total) break;
+    const u32 item = find_item(pre, B.n, gt);
     const Item& I = B.it[item];
-    if (item != cur) {  // the item's code table into shared memory
+    if (item != cur) {  // the item's code table into the warp's shared memory
       cur = item;
-      for (u32 i = threadIdx.x; i < S; i += blockDim.x) {
-        slen[i] = I.lens[i];
-        scode[i] = I.codes[i];
-      }
+      __syncwarp();
+      for (u32 i = lane; i < S; i += 32) tab[i] = __ldg(I.codes + i);
+      __syncwarp();
       n = umin(I.sizes[0], I.N);
       nchunks = (n + C - 1) / C;
-      nranges = (nchunks + kPackRange - 1) / kPackRange;
       Lo = make_layout(S, I.rows, I.sizes[1], I.st->nout, nchunks, 0);
       sym = I.sym;
       out = I.out;
       cap = I.cap;
-      __syncthreads();
     }
-    const u64 r = gr - pre[item];
-    const u64 c_lo = r * kPackRange;
-    const u32 nc = (u32)umin(kPackRange, nchunks - c_lo);
-    // pass 1: bits per thread and chunk
-    for (u32 c = 0; c < nc; ++c) {
-      const u64 k0 = (c_lo + c) * C + (u64)threadIdx.x * EPT;
-      uint16_t sv[EPT];
-      load_syms<EPT>(sym, k0, n, sv);
-      u32 bits = 0;
+    const u64 t = gt - pre[item];
+    const u64 c0 = t * C + (u64)lane * 8;
+    // pass 1: bits of the chunk
+    u32 bits = 0;
+    for (u32 r = 0; r < rounds; ++r) {
+      u32 s8[8];
+      pack_load8(sym, c0 + (u64)r * 256, n, s8);
 #pragma unroll
-      for (int j = 0; j < EPT; ++j) bits += (k0 + j < n) ? slen[sv[j]] : 0u;
-      u32 total;
-      boffs[c][threadIdx.x] = block_excl_scan<u32>(bits, scratch, &total);
-      if (threadIdx.x == 0) cwords[c] = (total + 31) >> 5;
+      for (int q = 0; q < 8; ++q) bits += s8[q] != 0xffffffffu ? tab[s8[q]] >> 24 : 0u;
     }
-    __syncthreads();
-    if (warp == 0) {
-      u32 rw = lane < nc ? cwords[lane] : 0u;
-      rw = warp_sum(rw);
-      u64 mine[1] = {rw}, excl[1];
-      lookback_warp<1>(I.lbp, r, mine, excl, B.status);
-      if (lane == 0) {
-        s_base = excl[0];
-        if (r == nranges - 1) I.st->nwords = excl[0] + rw;
-      }
+    const u32 chunk_bits = warp_sum(bits);
+    const u32 words = (chunk_bits + 31) >> 5;
+    u64 cbase;
+    {
+      u64 mine[1] = {words}, excl[1];
+      lookback_warp<1>(I.lbp, t, mine, excl, B.status);
+      cbase = excl[0];
     }
-    __syncthreads();
-    // pass 2: pack and copy out each chunk
-    u64 cbase = s_base;
-    for (u32 c = 0; c < nc; ++c) {
-      const u64 t = c_lo + c;
-      const u32 words = cwords[c];
-      if (threadIdx.x == 0) {
-        const u64 o = Lo.off_chunks + 8 * t;
-        if (o + 8 <= cap) *reinterpret_cast<u64*>(out + o) = cbase;
-      }
-      for (u32 i = threadIdx.x; i <= words && i < kPackWordsMax; i += blockDim.x) wbuf[i] = 0;
-      __syncthreads();
-      const u64 k0 = t * C + (u64)threadIdx.x * EPT;
-      uint16_t sv[EPT];
-      load_syms<EPT>(sym, k0, n, sv);
-      const u32 boff = boffs[c][threadIdx.x];
-      u64 acc = 0;
-      u32 nacc = boff & 31;  // leading bits belong to earlier threads (zeros here)
-      u32 wi = boff >> 5;
-      bool shared_first = (boff & 31) != 0;
-      u32 mybits = 0;
+    if (lane == 0) {
+      const u64 o = Lo.off_chunks + 8 * t;
+      if (o + 8 <= cap) *reinterpret_cast<u64*>(out + o) = cbase;
+      if (t == nchunks - 1) I.st->nwords = cbase + words;
+    }
+    const u64 pay = Lo.off_payload + 4 * cbase;  // byte offset of the chunk's first word
+    // pass 2: deposit every code at its bit offset, store the complete words
+    u32 run = 0, flushed = 0;
+    for (u32 r = 0; r < rounds && run < chunk_bits; ++r) {
+      u32 s8[8], e8[8];
+      pack_load8(sym, c0 + (u64)r * 256, n, s8);
+      u32 lb = 0;
 #pragma unroll
-      for (int j = 0; j < EPT; ++j) {
-        if (k0 + j < n) {
-          const u32 l = slen[sv[j]];
-          mybits += l;
-          acc = (acc << l) | scode[sv[j]];
-          nacc += l;
-          if (nacc >= 32) {
-            const u32 wv = (u32)(acc >> (nacc - 32));
-            if (shared_first) atomicOr(&wbuf[wi], wv);
-            else wbuf[wi] = wv;
-            shared_first = false;
-            ++wi;
-            nacc -= 32;
-            acc &= (1ull << nacc) - 1ull;
+      for (int q = 0; q < 8; ++q) {
+        e8[q] = s8[q] != 0xffffffffu ? tab[s8[q]] : 0u;
+        lb += e8[q] >> 24;
+      }
+      const u32 inc = warp_incl_scan(lb);
+      u32 off = run + inc - lb;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const u32 l = e8[q] >> 24, c = e8[q] & 0xffffffu;
+        if (l) {
+          const u32 w = off >> 5, sh = off & 31, end = sh + l;
+          if (end <= 32) {
+            atomicOr(&ring[w & (kPackRing - 1)], c << (32 - end));
+          } else {
+            atomicOr(&ring[w & (kPackRing - 1)], c >> (end - 32));
+            atomicOr(&ring[(w + 1) & (kPackRing - 1)], c << (64 - end));
           }
+          off += l;
         }
       }
-      if (mybits && nacc > (shared_first ? (boff & 31) : 0u))
-        atomicOr(&wbuf[wi], (u32)(acc << (32 - nacc)));
-      __syncthreads();
-      for (u32 i = threadIdx.x; i < words; i += blockDim.x) {
-        const u64 o = Lo.off_payload + 4 * (cbase + i);
-        if (o + 4 <= cap) *reinterpret_cast<u32*>(out + o) = wbuf[i];
+      run += __shfl_sync(0xffffffffu, inc, 31);
+      __syncwarp();
+      const u32 complete = run == chunk_bits ? (run + 31) >> 5 : run >> 5;  // last word padded
+      for (u32 i = flushed + lane; i < complete; i += 32) {
+        const u64 o = pay + 4 * (u64)i;
+        u32* slot = &ring[i & (kPackRing - 1)];
+        if (o + 4 <= cap) *reinterpret_cast<u32*>(out + o) = *slot;
+        *slot = 0u;
       }
-      cbase += words;
-      __syncthreads();
+      flushed = complete;
+      __syncwarp();
     }
   }
 }
@@ -774,7 +833,7 @@ __global__ void __launch_bounds__(kThreads) k_finalize(const __grid_constant__ B
   if (gtid == 0) {
     uint8_t h[kHeaderBytes];
     for (u32 i = 0; i < kHeaderBytes; ++i) h[i] = 0;
-    const roix_eb_info e = I.info_in ? *I.info_in : make_eb(d, st->vmin_key, st->vmax_key);
+    const roix_eb_info e = I.info_in ? *I.info_in : make_eb(d, I.rst->vmin_key, I.rst->vmax_key);
     h[0] = 'R'; h[1] = 'O'; h[2] = 'I'; h[3] = 'X';
     const uint16_t ver = kVersion;
     put_bytes(h, 4, &ver, 2);
@@ -903,10 +962,14 @@ void launch_quantize_stage(const Launch& L, const Desc& d, const void* P, u64 n_
 void launch_symbols(const Launch& L, const Batch& B, u64 tiles_cap) {
   if (tiles_cap == 0) return;
   const bool from_q = B.it[0].q != nullptr;
+  const size_t smem = (size_t)(kThreads / 32) * B.c.S * 4;  // one histogram per warp
   auto run = [&](auto kernel) {
-    u64 grid = (u64)grid_for((const void*)kernel, kThreads, 0, L.sms);
-    if (grid > tiles_cap) grid = tiles_cap;
-    kernel<<<(unsigned)grid, kThreads, 0, L.stream>>>(B);
+    cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    u64 grid = (u64)grid_for((const void*)kernel, kThreads, smem, L.sms);
+    const u64 need = (tiles_cap + kThreads / 32 - 1) / (kThreads / 32);  // a segment per warp
+    if (grid > need) grid = need;
+    kernel<<<(unsigned)grid, kThreads, smem, L.stream>>>(B);
   };
   if (B.c.dtype == ROIX_F32) {
     if (from_q) run(k_symbols<float, true>);
@@ -926,24 +989,14 @@ void launch_codebook(const Launch& L, const Batch& B) {
 
 void launch_pack(const Launch& L, const Batch& B, u64 ranges_cap) {
   if (ranges_cap == 0) return;
-  const size_t smem = ((size_t)B.c.C * kLMax / 32 + 2) * 4;
-  auto run = [&](auto kernel) {
-    cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    u64 grid = (u64)grid_for((const void*)kernel, kThreads, smem, L.sms);
-    if (grid > ranges_cap) grid = ranges_cap;
-    kernel<<<(unsigned)grid, kThreads, smem, L.stream>>>(B);
-  };
-  switch (B.c.C / kThreads) {
-    case 1: run(k_pack<1>); break;
-    case 2: run(k_pack<2>); break;
-    case 4: run(k_pack<4>); break;
-    case 8: run(k_pack<8>); break;
-    case 16: run(k_pack<16>); break;
-    case 32: run(k_pack<32>); break;
-    case 64: run(k_pack<64>); break;
-    default: break;  // rejected on the host
-  }
+  // one code table and one word ring per warp
+  const size_t smem = (size_t)(kThreads / 32) * (B.c.S + kPackRing) * 4;
+  cudaFuncSetAttribute((const void*)k_pack, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem);
+  u64 grid = (u64)grid_for((const void*)k_pack, kThreads, smem, L.sms);
+  const u64 need = (ranges_cap + kThreads / 32 - 1) / (kThreads / 32);  // a chunk per warp
+  if (grid > need) grid = need;
+  k_pack<<<(unsigned)grid, kThreads, smem, L.stream>>>(B);
 }
 
 void launch_finalize(const Launch& L, const Batch& B) {

@@ -116,23 +116,190 @@ __device__ __forceinline__ void thr_segment_vec(const Desc& d, const TV* __restr
   if ((u32)lane < nw) T[r * d.W + (x0 >> 5) + lane] = mine;
 }
 
-// Warps take the batch's 1024-voxel row segments in order (all items).
+// Flat form for rows that are not 16-byte aligned (nx * size % 16 != 0) of a
+// 16-byte aligned volume with nx >= 256: the volume is read as one flat array
+// in aligned 16-byte vectors, 1024 voxels per step of a warp, and turned into
+// flat words (bit b of flat word j = voxel 32 j + b, lane j holding word j);
+// each mask word of a row, whose 32 voxels start anywhere in the flat array,
+// is then a funnel shift of two flat words fetched by shuffles. A warp takes a
+// span of kFlatSpan voxels; the words starting in a step are formed once the
+// next step's first flat word is known.
+constexpr u32 kFlatSpan = 8192;
+
 template <typename TV>
+__device__ __forceinline__ u32 flat_words(const Desc& d, const TV* __restrict__ in, u64 a,
+                                          int lane) {
+  constexpr int kPer = 16 / sizeof(TV);
+  constexpr int kLoads = 1024 / (32 * kPer);
+  constexpr int kLanesPerWord = 32 / kPer;
+  constexpr int kWordsPerLoad = 32 / kLanesPerWord;
+  const u64 N = d.rows * d.nx;
+  uint4 v[kLoads];
+#pragma unroll
+  for (int i = 0; i < kLoads; ++i) {
+    const u64 x = a + (u64)i * (32 * kPer) + (u64)lane * kPer;
+    if (x + kPer <= N) {
+      v[i] = __ldg(reinterpret_cast<const uint4*>(in + x));
+    } else {  // the volume's last, partial vector (or past the end): bytes packed by hand
+      u32 w[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+      for (int k = 0; k < kPer; ++k) {
+        if (x + k < N) {
+          u32 b;
+          if constexpr (sizeof(TV) == 4) b = __float_as_uint(__ldg(in + x + k));
+          else b = (u32)__ldg(in + x + k);
+          w[(k * sizeof(TV)) / 4] |= b << (8 * ((k * sizeof(TV)) % 4));
+        }
+      }
+      v[i] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+  u32 mine = 0;
+#pragma unroll
+  for (int i = 0; i < kLoads; ++i) {
+    const u64 x = a + (u64)i * (32 * kPer) + (u64)lane * kPer;
+    u32 bits = 0;
+    if constexpr (sizeof(TV) == 4) {
+      bits = (pass_f32(__uint_as_float(v[i].x), d) ? 1u : 0u) |
+             (pass_f32(__uint_as_float(v[i].y), d) ? 2u : 0u) |
+             (pass_f32(__uint_as_float(v[i].z), d) ? 4u : 0u) |
+             (pass_f32(__uint_as_float(v[i].w), d) ? 8u : 0u);
+    } else if constexpr (sizeof(TV) == 2) {
+      const u32 q[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        bits |= (pass_u16(q[k] & 0xffffu, d) ? 1u : 0u) << (2 * k);
+        bits |= (pass_u16(q[k] >> 16, d) ? 1u : 0u) << (2 * k + 1);
+      }
+    } else {
+      const u32 q[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          bits |= (pass_u16((q[k] >> (8 * b)) & 0xffu, d) ? 1u : 0u) << (4 * k + b);
+    }
+    if (x + kPer > N) bits &= x < N ? (1u << (u32)(N - x)) - 1u : 0u;  // voxels past the end
+    u32 t = bits << (kPer * (lane & (kLanesPerWord - 1)));
+#pragma unroll
+    for (int o = 1; o < kLanesPerWord; o <<= 1) t |= __shfl_xor_sync(0xffffffffu, t, o);
+    const u32 wv = __shfl_sync(0xffffffffu, t, kLanesPerWord * (lane & (kWordsPerLoad - 1)));
+    if (lane / kWordsPerLoad == i) mine = wv;
+  }
+  return mine;
+}
+
+// Mask words of the rows whose voxels x = 32 w .. start in flat step [a, a +
+// 1024): F = that step's flat words (lane j: word j), f32 = the next step's
+// word 0. r / rs: a row containing voxel a and its first flat index.
+__device__ __forceinline__ void flat_emit(const Desc& d, u32* __restrict__ T, u64 a, u32 F,
+                                          u32 f32, u64 r, u64 rs, int lane) {
+  const u64 nx = d.nx, W = d.W;
+  const u64 lim = umin(a + 1024, d.rows * nx);  // word starts lie in [a, lim)
+  // count the words per row (at most 5 rows: nx >= 256)
+  u32 cnt[5];
+  u64 wlo[5];
+  u32 total = 0;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const u64 rk = r + k, sk = rs + (u64)k * nx;
+    cnt[k] = 0;
+    wlo[k] = 0;
+    if (rk < d.rows && sk < lim) {
+      const u64 lo = a > sk ? (a - sk + 31) >> 5 : 0;
+      const u64 hi = umin(W, (lim - sk + 31) >> 5);  // words with start < lim
+      if (hi > lo) {
+        cnt[k] = (u32)(hi - lo);
+        wlo[k] = lo;
+      }
+    }
+    total += cnt[k];
+  }
+  for (u32 o0 = 0; o0 < total; o0 += 32) {
+    const u32 o = o0 + lane;
+    u64 row = 0, w = 0;
+    bool have = false;
+    u32 acc = 0;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      if (!have && o < acc + cnt[k]) {
+        row = r + k;
+        w = wlo[k] + (o - acc);
+        have = true;
+      }
+      acc += cnt[k];
+    }
+    const u64 s = have ? row * nx + 32 * w : a;
+    const u32 off = (u32)(s - a), j = off >> 5, sh = off & 31;
+    const u32 lo = __shfl_sync(0xffffffffu, F, j & 31);
+    u32 hi = __shfl_sync(0xffffffffu, F, (j + 1) & 31);
+    if (j == 31) hi = f32;
+    if (have) {
+      u32 v = sh ? __funnelshift_r(lo, hi, sh) : lo;
+      v &= last_mask(d, w);
+      T[row * W + w] = v;
+    }
+  }
+}
+
+template <typename TV>
+__device__ __forceinline__ void thr_flat_span(const Desc& d, const TV* __restrict__ in,
+                                              u32* __restrict__ T, u64 span, int lane) {
+  const u64 N = d.rows * d.nx;
+  const u64 a0 = span * kFlatSpan;
+  const u64 a1 = umin(a0 + kFlatSpan, N);
+  u64 r = a0 / d.nx, rs = r * d.nx;  // row holding voxel a0
+  u32 F = flat_words<TV>(d, in, a0, lane);
+  for (u64 a = a0; a < a1; a += 1024) {
+    const u64 an = a + 1024;
+    // next step's flat words (the step after the span only for its word 0)
+    u32 Fn = 0;
+    if (an < N) {
+      if (an < a1) {
+        Fn = flat_words<TV>(d, in, an, lane);
+      } else {
+        const u64 x = an + lane;
+        bool p = false;
+        if (x < N) {
+          if constexpr (sizeof(TV) == 4) p = pass_f32(__ldg(in + x), d);
+          else p = pass_u16(__ldg(in + x), d);
+        }
+        Fn = __ballot_sync(0xffffffffu, p);
+      }
+    }
+    flat_emit(d, T, a, F, __shfl_sync(0xffffffffu, Fn, 0), r, rs, lane);
+    F = Fn;
+    while (rs + d.nx <= an && r + 1 < d.rows) {  // the row holding the next step's first voxel
+      rs += d.nx;
+      ++r;
+    }
+  }
+}
+
+// Warps take the batch's work units in order (all items): 1024-voxel row
+// segments of the row-form items, or kFlatSpan-voxel spans of the flat-form
+// items (FLAT; a launch of its own, so that each form keeps its registers).
+template <typename TV, bool FLAT>
 __global__ void __launch_bounds__(kThreads) k_threshold(const __grid_constant__ Batch B) {
   const int lane = threadIdx.x & 31;
   const u64 warp = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
-  const u64 total = B.seg0[B.n];
+  const u64* pre = FLAT ? B.fseg0 : B.seg0;
+  const u64 total = pre[B.n];
   for (u64 s = warp; s < total; s += nwarps) {
-    const u32 i = find_item(B.seg0, B.n, s);
+    const u32 i = find_item(pre, B.n, s);
     const Item& I = B.it[i];
-    const u64 local = s - B.seg0[i];
-    const u64 spr = (I.nx + 1023) >> 10;
-    const u64 r = local / spr;
-    const u32 x0 = (u32)(local - r * spr) << 10;
+    const u64 local = s - pre[i];
     const Desc d = desc_of(B, I);
-    if (I.vec) thr_segment_vec<TV>(d, (const TV*)I.in, I.T, r, x0, lane);
-    else thr_segment<TV>(d, (const TV*)I.in, I.T, r, x0, lane);
+    if constexpr (FLAT) {
+      thr_flat_span<TV>(d, (const TV*)I.in, I.T, local, lane);
+    } else {
+      const u64 spr = (I.nx + 1023) >> 10;
+      const u64 r = local / spr;
+      const u32 x0 = (u32)(local - r * spr) << 10;
+      if (I.vec) thr_segment_vec<TV>(d, (const TV*)I.in, I.T, r, x0, lane);
+      else thr_segment<TV>(d, (const TV*)I.in, I.T, r, x0, lane);
+    }
   }
 }
 
@@ -273,7 +440,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_front(const __grid_constant__ B
     const u32 item = find_item(B.ftile0, B.n, gt);
     const Item& I = B.it[item];
     if (item != cur) {  // flush the value range of the previous item
-      flush_range(cur == 0xffffffffu ? nullptr : B.it[cur].st, kmin, kmax, lane);
+      flush_range(cur == 0xffffffffu ? nullptr : B.it[cur].rst, kmin, kmax, lane);
       cur = item;
     }
     const Desc d = desc_of(B, I);
@@ -289,6 +456,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_front(const __grid_constant__ B
     const u64 bounds_cap = I.bounds_cap;
     u64* sizes_out = I.sizes;
     const LookBack<2> lb = I.lbf;
+    const u32 zhalo = I.zhalo;  // z-slab: T continues across the slab's z borders
     const u32 W = (u32)d.W;
     const FastDiv divW(W);
     u32* Dw = smem_dyn;                                 // [rpt * W]
@@ -313,8 +481,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_front(const __grid_constant__ B
         u32 f = 0u;
         if (rr >= 0 && rr < (int64_t)d.rows) {
           const u64 z = (u64)rr / d.ny, y = (u64)rr - z * d.ny;
-          f = 16u | (y > 0 ? 1u : 0u) | (y + 1 < d.ny ? 2u : 0u) | (z > 0 ? 4u : 0u) |
-              (z + 1 < d.nz ? 8u : 0u);
+          f = 16u | (y > 0 ? 1u : 0u) | (y + 1 < d.ny ? 2u : 0u) |
+              ((z > 0 || (zhalo & 1u)) ? 4u : 0u) | ((z + 1 < d.nz || (zhalo & 2u)) ? 8u : 0u);
         }
         bflag[j] = f;
       }
@@ -536,7 +704,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_front(const __grid_constant__ B
     }
     __syncthreads();
   }
-  flush_range(cur == 0xffffffffu ? nullptr : B.it[cur].st, kmin, kmax, lane);
+  flush_range(cur == 0xffffffffu ? nullptr : B.it[cur].rst, kmin, kmax, lane);
 }
 
 int occupancy_grid(const void* fn, int threads, size_t smem, int sms) {
@@ -549,18 +717,25 @@ int occupancy_grid(const void* fn, int threads, size_t smem, int sms) {
 }  // namespace
 
 void launch_threshold(const Launch& L, const Batch& B) {
-  const u64 segs = B.seg0[B.n];
-  if (segs == 0) return;
-  const u64 warps_per_block = kThreads / 32;
-  u64 blocks = (segs + warps_per_block - 1) / warps_per_block;
-  const u64 cap = (u64)L.sms * 8;  // 8 blocks of 256 threads per SM in flight
-  if (blocks > cap) blocks = cap;
-  if (B.c.dtype == ROIX_F32)
-    k_threshold<float><<<(unsigned)blocks, kThreads, 0, L.stream>>>(B);
-  else if (B.c.dtype == ROIX_U16)
-    k_threshold<unsigned short><<<(unsigned)blocks, kThreads, 0, L.stream>>>(B);
-  else
-    k_threshold<unsigned char><<<(unsigned)blocks, kThreads, 0, L.stream>>>(B);
+  auto run = [&](auto kernel, u64 units, u64 per_warp) {
+    if (units == 0) return;
+    const u64 warps_per_block = kThreads / 32;
+    u64 blocks = (units + warps_per_block - 1) / warps_per_block;
+    const u64 cap = (u64)L.sms * per_warp;  // blocks of 256 threads per SM in flight
+    if (blocks > cap) blocks = cap;
+    kernel<<<(unsigned)blocks, kThreads, 0, L.stream>>>(B);
+  };
+  const u64 segs = B.seg0[B.n], spans = B.fseg0[B.n];
+  if (B.c.dtype == ROIX_F32) {
+    run(k_threshold<float, false>, segs, 8);
+    run(k_threshold<float, true>, spans, 4);
+  } else if (B.c.dtype == ROIX_U16) {
+    run(k_threshold<unsigned short, false>, segs, 8);
+    run(k_threshold<unsigned short, true>, spans, 4);
+  } else {
+    run(k_threshold<unsigned char, false>, segs, 8);
+    run(k_threshold<unsigned char, true>, spans, 4);
+  }
 }
 
 void launch_dilate(const Launch& L, const Desc& d, const u32* T, u32* D, u64* popcount) {

@@ -293,27 +293,30 @@ bool rows_vector_aligned(const void* in, roix_dtype dt, u64 nx) {
   return (nx * dtype_bytes(dt)) % 16 == 0;
 }
 
-// Fills the batch structure for the plan; pointers into `ws`. Item fields for
-// outputs and inputs are set by the caller.
+// Fills the batch structure for items [first, first + n) of the plan;
+// pointers into `ws`. Item fields for outputs and inputs are set by the
+// caller. The batch's work tickets live in the state of its first item (all
+// states but the context status word are zeroed per call).
 void fill_batch(Batch& B, const Desc& c, const BatchPlan& bp, const roix_dims* dims, char* ws,
-                u32 n) {
+                u32 n, u32 first = 0) {
   std::memset(&B, 0, sizeof(B));
   B.c = c;
   B.n = n;
   State* st = (State*)ws;
   B.status = &st[0].status;
-  B.ctr = &st[0].ctr_front;
+  B.ctr = &st[first].ctr_front;
   u64 seg = 0, ft = 0;
   for (u32 i = 0; i < n; ++i) {
-    const ItemPlan& p = bp.items[i];
+    const ItemPlan& p = bp.items[first + i];
     Item& I = B.it[i];
-    I.nx = dims[i].nx;
-    I.ny = dims[i].ny;
-    I.nz = dims[i].nz;
+    I.nx = dims[first + i].nx;
+    I.ny = dims[first + i].ny;
+    I.nz = dims[first + i].nz;
     I.rows = I.ny * I.nz;
     I.W = (I.nx + 31) / 32;
     I.N = p.n_cap;
-    I.st = st + i;
+    I.st = st + first + i;
+    I.rst = I.st;
     I.T = p.T ? (u32*)(ws + p.T) : nullptr;
     I.P = p.P ? (void*)(ws + p.P) : nullptr;
     I.sym = (uint16_t*)(ws + p.sym);
@@ -340,6 +343,28 @@ void fill_batch(Batch& B, const Desc& c, const BatchPlan& bp, const roix_dims* d
 
 }  // namespace
 
+// Binarisation work units: 1024-voxel row segments when the rows are 16-byte
+// aligned and fill whole segments (nx a multiple of 1024) or are short (nx <
+// 256); kFlatSpan-voxel spans of the flat array for any other 16-byte aligned
+// volume.
+void roix::set_threshold_units(Batch& B) {
+  constexpr u64 kFlatSpanHost = 8192;
+  u64 seg = 0, fseg = 0;
+  for (u32 i = 0; i < B.n; ++i) {
+    Item& I = B.it[i];
+    const roix_dtype dt = (roix_dtype)B.c.dtype;
+    I.vec = rows_vector_aligned(I.in, dt, I.nx) ? 1u : 0u;
+    I.flat = (!(I.vec && I.nx % 1024 == 0) && I.nx >= 256 && aligned(I.in, 16)) ? 1u : 0u;
+    B.seg0[i] = seg;
+    B.fseg0[i] = fseg;
+    const u64 N = I.nx * I.ny * I.nz;
+    if (I.flat) fseg += (N + kFlatSpanHost - 1) / kFlatSpanHost;
+    else seg += I.rows * ((I.nx + 1023) / 1024);
+  }
+  B.seg0[B.n] = seg;
+  B.fseg0[B.n] = fseg;
+}
+
 // One-item batch for the binarisation kernel alone.
 void roix::make_threshold_batch(Batch& B, const Desc& d, const void* in, u32* T) {
   std::memset(&B, 0, sizeof(B));
@@ -354,8 +379,7 @@ void roix::make_threshold_batch(Batch& B, const Desc& d, const void* in, u32* T)
   I.N = d.N;
   I.in = in;
   I.T = T;
-  I.vec = rows_vector_aligned(in, (roix_dtype)d.dtype, d.nx) ? 1u : 0u;
-  B.seg0[1] = d.rows * ((d.nx + 1023) / 1024);
+  set_threshold_units(B);
 }
 
 namespace {
@@ -701,9 +725,9 @@ roix_status enqueue_group(roix_ctx* ctx, const Desc& c, const roix_item* items, 
   for (u32 i = 0; i < n; ++i) {
     Item& I = B.it[i];
     I.in = items[i].in;
-    I.vec = rows_vector_aligned(items[i].in, (roix_dtype)c.dtype, I.nx) ? 1u : 0u;
     set_container(I, c, items[i].out, items[i].cap, (u64*)items[i].size_dev);
   }
+  set_threshold_units(B);
   if (profile) {
     ctx->nev = 0;
     mark(ctx, cs);
@@ -800,6 +824,144 @@ roix_status roix_compress_batch(roix_ctx* ctx, uint32_t n, const roix_item* item
       return s;
   }
   return ROIX_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// ------------------------------------------------------------- z-slabs
+// A volume cut into z-slabs of slab_z slices, each slab an item of its own
+// (own container, stream, histogram and codebook) while the mask and the
+// error bound are the whole volume's: one binarisation of the whole volume
+// into one contiguous T, slab items whose T points at their first plane with
+// the neighbouring planes marked as present (the dilation crosses the slab
+// borders), and one value range shared by every slab.
+struct SlabPlan {
+  std::vector<roix_dims> dims;
+  std::vector<u64> ncaps, caps;
+  BatchPlan bp;
+  size_t T_off = 0, total = 0;
+};
+
+SlabPlan plan_slabs(const Desc& d, u64 slab_z, const uint64_t* caps, u64 cap_all) {
+  SlabPlan sp;
+  const u64 ns = d.nz ? (d.nz + slab_z - 1) / slab_z : 0;
+  sp.dims.resize(ns);
+  sp.ncaps.resize(ns);
+  sp.caps.resize(ns);
+  for (u64 s = 0; s < ns; ++s) {
+    const u64 dz = umin(slab_z, d.nz - s * slab_z);
+    sp.dims[s] = roix_dims{d.nx, d.ny, dz};
+    sp.ncaps[s] = d.nx * d.ny * dz;
+    sp.caps[s] = caps ? caps[s] : cap_all;
+  }
+  sp.bp = plan_batch(d, sp.dims.data(), sp.ncaps.data(), sp.caps.data(), (u32)ns, false, true);
+  Arena a;
+  a.off = sp.bp.total;
+  sp.T_off = a.take(4 * d.rows * d.W + 16);
+  sp.total = a.take(0);
+  return sp;
+}
+
+roix_status slab_desc(roix_ctx* ctx, roix_dtype dtype, roix_dims dims, uint64_t slab_z,
+                      const roix_roi* roi, const roix_eb* eb, const roix_params* params,
+                      Desc* d) {
+  if (!roi || !eb || !params) return fail(ctx, ROIX_EINVAL, "null parameter struct");
+  if (dtype != ROIX_F32 && dtype != ROIX_U16)
+    return fail(ctx, ROIX_EINVAL, "slabs: float32 or uint16 only");
+  roix_status s = make_desc(ctx, dtype, dims, roi, eb, params, d);
+  if (s) return s;
+  if (d->keep) return fail(ctx, ROIX_EINVAL, "slabs: keep = 1 is refused (a slab is not a volume)");
+  if (slab_z == 0) return fail(ctx, ROIX_EINVAL, "slab_z must be >= 1");
+  return ROIX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t roix_slabs_workspace_size(roix_dtype dtype, roix_dims dims, uint64_t slab_z,
+                                 const roix_roi* roi, const roix_params* params, uint64_t cap) {
+  Desc d;
+  const roix_eb eb{0, 1.0};
+  if (slab_desc(nullptr, dtype, dims, slab_z, roi, &eb, params, &d) != ROIX_OK) return 0;
+  return plan_slabs(d, slab_z, nullptr, cap).total;
+}
+
+roix_status roix_compress_slabs(roix_ctx* ctx, const void* in, roix_dtype dtype, roix_dims dims,
+                                uint64_t slab_z, const roix_roi* roi, const roix_eb* eb,
+                                const roix_params* params, void* const* outs,
+                                const uint64_t* caps, uint64_t* sizes_dev, void* stream) {
+  if (!ctx) return ROIX_EINVAL;
+  Desc d;
+  roix_status s = slab_desc(ctx, dtype, dims, slab_z, roi, eb, params, &d);
+  if (s) return s;
+  const u64 ns = d.nz ? (d.nz + slab_z - 1) / slab_z : 0;
+  if (ns == 0) return ROIX_OK;
+  if (!outs || !caps || !sizes_dev) return fail(ctx, ROIX_EINVAL, "null outs, caps or sizes_dev");
+  if (d.N && !in) return fail(ctx, ROIX_EINVAL, "null input");
+  const size_t esz = dtype_bytes(dtype);
+  if (!aligned(in, esz)) return fail(ctx, ROIX_EINVAL, "misaligned input");
+  for (u64 k = 0; k < ns; ++k)
+    if (!outs[k] || !aligned(outs[k], 16))
+      return fail(ctx, ROIX_EINVAL, "every slab output must be a 16-byte aligned buffer");
+  DeviceGuard g(ctx->device);
+  const SlabPlan sp = plan_slabs(d, slab_z, caps, 0);
+  if ((s = ensure_ws(ctx, sp.total))) return s;
+  cudaStream_t cs = (cudaStream_t)stream;
+  Launch L{cs, ctx->sms};
+  char* ws = ctx->ws;
+  State* st = (State*)ws;
+  u32* T = (u32*)(ws + sp.T_off);
+  const u64 plane_words = d.ny * d.W;
+  const bool profile = ctx->profile != 0;
+  if (profile) {
+    ctx->nev = 0;
+    mark(ctx, cs);
+  }
+  launch_init(L, st, (u32)ns, ws + sp.bp.zero_begin, sp.bp.zero_end - sp.bp.zero_begin);
+  if (profile) mark(ctx, cs);
+  {
+    static thread_local Batch Bt;
+    make_threshold_batch(Bt, d, in, T);
+    launch_threshold(L, Bt);
+  }
+  if (profile) mark(ctx, cs);
+  // groups of up to kMaxBatch slabs, all sharing the range kept in state 0
+  const u32 ngroups = (u32)((ns + kMaxBatch - 1) / kMaxBatch);
+  std::vector<Batch> G(ngroups);
+  std::vector<u64> gq(ngroups, 0), gp(ngroups, 0);
+  for (u32 gi = 0; gi < ngroups; ++gi) {
+    const u32 first = gi * kMaxBatch;
+    const u32 m = (u32)umin(kMaxBatch, ns - first);
+    Batch& B = G[gi];
+    fill_batch(B, d, sp.bp, sp.dims.data(), ws, m, first);
+    for (u32 i = 0; i < m; ++i) {
+      const u64 k = first + i;
+      const u64 z0 = k * slab_z;
+      Item& I = B.it[i];
+      I.in = (const char*)in + z0 * d.ny * d.nx * esz;
+      I.T = T + z0 * plane_words;
+      I.zhalo = (z0 > 0 ? 1u : 0u) | (z0 + I.nz < d.nz ? 2u : 0u);
+      I.rst = st;
+      set_container(I, d, outs[k], caps[k], (u64*)sizes_dev + k);
+      gq[gi] += sp.bp.items[k].qtiles;
+      gp[gi] += sp.bp.items[k].pranges;
+    }
+  }
+  for (u32 gi = 0; gi < ngroups; ++gi) launch_front(L, G[gi]);
+  if (profile) mark(ctx, cs);
+  for (u32 gi = 0; gi < ngroups; ++gi) launch_symbols(L, G[gi], gq[gi]);
+  if (profile) mark(ctx, cs);
+  for (u32 gi = 0; gi < ngroups; ++gi) launch_codebook(L, G[gi]);
+  if (profile) mark(ctx, cs);
+  for (u32 gi = 0; gi < ngroups; ++gi) launch_pack(L, G[gi], gp[gi]);
+  if (profile) mark(ctx, cs);
+  for (u32 gi = 0; gi < ngroups; ++gi) launch_finalize(L, G[gi]);
+  if (profile) mark(ctx, cs);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ROIX_OK : cuda_fail(ctx, e, "compress_slabs launch");
 }
 
 roix_status roix_decode(roix_ctx* ctx, const void* in, uint64_t size, void* out,

@@ -301,6 +301,8 @@ struct Item {
   u64 cap;
   u64* size_dev;                       // container size (output)
   State* st;
+  State* rst;                          // state holding the value range (st, or a state
+                                       // shared by the z-slabs of one volume)
   u32* T;                              // thresholded mask (fused path)
   void* P;                             // pixel section
   uint16_t* sym;
@@ -325,6 +327,9 @@ struct Item {
   LookBack<1> lbp;                     // pack ranges
   u32 rpt;                             // rows per front tile
   u32 vec;                             // rows are 16-byte aligned (vector loads)
+  u32 flat;                            // binarisation reads the volume as a flat array
+  u32 zhalo;                           // z-slab: bit 0 = T holds the plane before z = 0,
+                                       // bit 1 = T holds the plane after z = nz - 1
   u64 ftiles;                          // front tiles
 };
 
@@ -333,7 +338,8 @@ struct Batch {
   u32 n;                               // items
   u32* status;                         // context status word
   u32* ctr;                            // [4] tickets: front, symbols, pack, spare
-  u64 seg0[kMaxBatch + 1];             // prefix of threshold row segments
+  u64 seg0[kMaxBatch + 1];             // prefix of threshold row segments (row-form items)
+  u64 fseg0[kMaxBatch + 1];            // prefix of threshold flat spans (flat-form items)
   u64 ftile0[kMaxBatch + 1];           // prefix of front tiles
   Item it[kMaxBatch];
 };
@@ -458,6 +464,9 @@ roix_status make_desc(roix_ctx* ctx, roix_dtype dtype, roix_dims dims, const roi
 
 // Host: a one-item batch for the binarisation kernel alone (roix_api.cu).
 void make_threshold_batch(Batch& B, const Desc& d, const void* in, u32* T);
+// Host: the binarisation work units of every item (B.seg0), from each item's
+// input pointer and geometry; sets the items' vec / flat forms.
+void set_threshold_units(Batch& B);
 
 // ------------------------------------------------------ launch functions
 struct Launch {
@@ -472,8 +481,8 @@ void launch_front(const Launch& L, const Batch& B);
 size_t front_smem(u32 rpt, u64 W, int dilate);
 
 // coder kernels (k_encode.cu)
-constexpr u32 kQuantTile = 8192;  // elements per quantiser tile
-constexpr u32 kPackRange = 8;     // chunks per pack ticket
+constexpr u32 kQuantTile = 4096;  // values per symbol segment (one warp's unit of work)
+constexpr u32 kPackRange = 1;     // chunks per pack ticket (one warp's unit of work)
 void launch_init(const Launch& L, State* st, u32 nstates, void* zero, size_t zero_bytes);
 void launch_quantize_stage(const Launch& L, const Desc& d, const void* P, u64 n_cap,
                            const u64* n_dev, int32_t* q, u32* obits, roix_eb_info* info_out,

@@ -84,3 +84,17 @@ def test_server_create_without_gpu_fails_cleanly(libpath):
     h = C.c_void_p()
     bad = roix.ServerConfig(1 << 30, 0, 8)  # no lanes
     assert roix.lib().roix_server_create(0, C.byref(bad), C.byref(h)) == 1
+
+
+def test_slab_workspace_size_checks_arguments(libpath):
+    import paper_2602_15917_gb300 as roix
+    L = roix.lib()
+    d = roix.dims_of((70, 30, 40))
+    p = roix.params_of()
+    ok = L.roix_slabs_workspace_size(1, d, 16, C.byref(roix.roi_of()), C.byref(p), 1 << 20)
+    # at least the pixel sections and symbols of every slab and the whole mask
+    assert ok >= 70 * 30 * 40 * 6 + 70 * 30 * 2 * 4
+    assert L.roix_slabs_workspace_size(1, d, 0, C.byref(roix.roi_of()), C.byref(p), 0) == 0
+    assert L.roix_slabs_workspace_size(1, d, 16, C.byref(roix.roi_of(keep="largest")),
+                                       C.byref(p), 0) == 0
+    assert L.roix_slabs_workspace_size(3, d, 16, C.byref(roix.roi_of()), C.byref(p), 0) == 0

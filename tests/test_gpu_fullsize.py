@@ -99,3 +99,88 @@ def test_cube1024_properties_and_sampled_rows(rx):
         want = np.where(o.astype(bool), P, (q.astype(np.float32) * np.float32(hdr["two_eb"])))
         assert np.array_equal(yc[z, yy].numpy()[Dm.astype(bool)].view(np.uint32),
                               want.astype(np.float32).view(np.uint32))
+
+
+def test_cube2048_slabs_properties_and_sampled_rows():
+    """2048^3 float32 textured porous cylinder (32 GiB in HBM), 64-slice
+    z-slabs, relative bound 1e-4, in the launch configuration bench.py times.
+    Per slab, on every voxel: retained count = popcount of threshold + 3x3x3
+    dilation (recomputed by torch with a one-slice halo from the neighbouring
+    slabs), decoded values within E_abs of the input on retained voxels and the
+    fill elsewhere; the whole-volume range and the E_abs constants derived from
+    it by the oracle are in every header; sampled rows are recomputed by the
+    oracle from their 3x3 neighbourhood of input rows."""
+    import paper_2602_15917_gb300 as roix
+    free, _ = torch.cuda.mem_get_info()
+    if free < 140 << 30:
+        pytest.skip("needs about 140 GB of free device memory")
+    n, slab = 2048, 64
+    cfg = dict(eb=1e-4, eb_mode="rel", cmp="gt", threshold=0.1, dilate=1, fill=0.0,
+               radius=512, chunk=4096)
+    x = phantom.porous_cylinder(n, radius=800.0, texture=True, seed=0, device="cuda")
+    rx = roix.Roix(0)
+    ns = n // slab
+    cap = slab * n * n * 4 // 4
+    outs = [torch.empty(cap, dtype=torch.uint8, device="cuda") for _ in range(ns)]
+    rx.reserve(rx.slabs_workspace_size(x.shape, slab, cap=cap, **cfg))
+    outs, sizes = rx.compress_slabs(x, slab, outs=outs, **cfg)
+    rx.sync()
+    sizes = [int(v) for v in sizes.cpu().numpy()]
+    hdrs = [oracle.header(o[:256].cpu().numpy()) for o in outs]
+    # whole-volume range of the retained values, slab by slab
+    vmin, vmax, Ds = float("inf"), float("-inf"), []
+    for k in range(ns):
+        z0, z1 = k * slab, (k + 1) * slab
+        h0, h1 = max(0, z0 - 1), min(n, z1 + 1)
+        T = (x[h0:h1] > 0.1).float()[None, None]
+        D = torch.nn.functional.max_pool3d(T, 3, stride=1, padding=1)[0, 0, z0 - h0:z0 - h0 + slab] > 0
+        del T
+        assert int(D.sum().item()) == hdrs[k]["n"], k
+        if hdrs[k]["n"]:
+            xs_ = x[z0:z1][D]
+            xs_ = xs_[torch.isfinite(xs_)]
+            vmin = min(vmin, float(xs_.min().item()))
+            vmax = max(vmax, float(xs_.max().item()))
+            del xs_
+        Ds.append(D.cpu())
+        del D
+    e = oracle.error_bound(np.array([vmin, vmax], np.float32), "rel", cfg["eb"])
+    for h in hdrs:
+        assert h["vmin"] == vmin and h["vmax"] == vmax
+        assert (h["eb_abs"], h["two_eb"], h["inv2eb"], h["bound"]) == \
+            (e.eb_abs, np.float32(e.two_eb), np.float32(e.inv2eb), np.float32(e.bound))
+    # decoded values, slab by slab
+    for k in range(ns):
+        z0 = k * slab
+        y = rx.decode(outs[k][:sizes[k]], (slab, n, n), torch.float32)
+        rx.sync()
+        D = Ds[k].cuda()
+        xk = x[z0:z0 + slab]
+        fin = D & torch.isfinite(xk)
+        assert float((xk[fin].double() - y[fin].double()).abs().max().item()) <= e.eb_abs
+        assert bool((y[~D] == 0).all().item())
+        del y, D, fin
+    # sampled rows against the oracle
+    rng = np.random.default_rng(7)
+    zs = rng.integers(590, 1458, 24)
+    zs[:6] = [0, 63, 64, 597, 1023, 2047]
+    ys = rng.integers(0, n, 24)
+    for z, yy in zip(zs.tolist(), ys.tolist()):
+        k = z // slab
+        buf = outs[k][:sizes[k]].cpu().numpy()
+        z0, z1 = max(0, z - 1), min(n, z + 2)
+        y0, y1 = max(0, yy - 1), min(n, yy + 2)
+        block = x[z0:z1, y0:y1].cpu().numpy()
+        Dm = oracle.mask(block, **cfg)[z - z0, yy - y0]
+        row = x[z:z + 1, yy:yy + 1].cpu().numpy()
+        P, counts, bounds = oracle.compact(row, Dm[None, None])
+        assert np.array_equal(_row_from_container(buf, hdrs[k], (z - k * slab) * n + yy), bounds)
+        q, o = oracle.quantize(P, e)
+        want = np.where(o.astype(bool), P, (q.astype(np.float32) * np.float32(e.two_eb)))
+        got = rx.decode(outs[k][:sizes[k]], (slab, n, n), torch.float32)[z - k * slab, yy]
+        rx.sync()
+        assert np.array_equal(got.cpu().numpy()[Dm.astype(bool)].view(np.uint32),
+                              want.astype(np.float32).view(np.uint32))
+    rx.close()
+    del x, outs
+    torch.cuda.empty_cache()

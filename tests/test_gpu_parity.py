@@ -363,3 +363,49 @@ def test_keep_largest_repeatable(rx):
         rx.sync()
         assert int(pop.item()) == int(D.sum())
         assert np.array_equal(_unpack_mask(mask, x.shape), D)
+
+
+# Rows that are not 16-byte aligned, nx >= 256: the binarisation reads the
+# volume as one flat array (aligned vectors, mask words by funnel shifts).
+FLAT_CASES = [((3, 7, 257), np.float32), ((2, 5, 1023), np.float32), ((1, 9, 1025), np.float32),
+              ((4, 3, 333), np.float32), ((1, 1, 300), np.float32), ((2, 6, 300), np.uint16),
+              ((1, 11, 511), np.uint16), ((3, 4, 1001), np.uint16), ((2, 5, 2047), np.uint16),
+              ((5, 7, 270), np.uint8), ((1, 3, 4097), np.uint8)]
+
+
+@pytest.mark.parametrize("shape,dt", FLAT_CASES, ids=[f"{s}-{d.__name__}" for s, d in FLAT_CASES])
+def test_flat_binarisation_masks(rx, shape, dt):
+    rng = np.random.default_rng(sum(shape))
+    if dt == np.float32:
+        x = rng.standard_normal(shape).astype(np.float32)
+        cfgs = [dict(threshold=0.3, dilate=0), dict(threshold=0.3, dilate=1),
+                dict(cmp="lt", threshold=-1.0, dilate=0)]
+    elif dt == np.uint16:
+        x = rng.integers(0, 65536, shape).astype(np.uint16)
+        cfgs = [dict(cmp="lt", threshold=30000, dark=100, dilate=0),
+                dict(cmp="gt", threshold=60000, dark=0, dilate=1)]
+    else:
+        x = rng.integers(0, 256, shape).astype(np.uint8)
+        cfgs = [dict(threshold=128, dilate=0), dict(cmp="lt", threshold=20, dilate=1)]
+    xt = torch.from_numpy(x).cuda()
+    for cfg in cfgs:
+        words, pop = rx.extract_roi(xt, **cfg)
+        rx.sync()
+        want = oracle.mask(x, **cfg)
+        assert np.array_equal(_unpack_mask(words, x.shape), want), cfg
+        assert int(pop.item()) == int(want.sum())
+
+
+def test_flat_binarisation_in_fused_and_batch(rx):
+    xs = [phantom.projection(s, i, seed=7).numpy() for i, s in enumerate([257, 301, 515, 999])]
+    cfg = dict(eb=4, cmp="lt", threshold=57000, dark=100, dilate=0, fill=60100)
+    for x in xs:
+        ref, got = _compress_both(rx, x, **cfg)
+        _assert_same_container(ref, got)
+    outs, sizes = rx.compress_batch([torch.from_numpy(x).cuda() for x in xs], **cfg)
+    rx.sync()
+    for x, o, sz in zip(xs, outs, sizes.cpu().numpy()):
+        _assert_same_container(oracle.compress(x, **cfg), o[:int(sz)].cpu().numpy())
+    x = phantom.ellipsoids(shape=(6, 40, 290), seed=3).numpy()
+    ref, got = _compress_both(rx, x, eb=1e-3, eb_mode="rel")
+    _assert_same_container(ref, got)
