@@ -36,6 +36,26 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "GB/s in (quantize+ROI+encode) vs HBM peak, batched/served vs plain; p50/p99 latency"
+# kernels of one fused group: reset, binarisation, compaction count, scan and write,
+# symbols, codebook, pack count, pack scan, records, pack, finalise (+1 when flat-form items are
+# binarised next to row-form ones)
+LAUNCHES_PER_GROUP = 12
+
+
+def group_launches(xs) -> int:
+    """Kernel launches of one fused group of items (the library's rule for
+    the two binarisation forms: flat when a 16-byte aligned volume has nx >=
+    256 and its rows are not aligned or do not fill 1024-voxel segments)."""
+    flat = row = False
+    for x in xs:
+        nx = x.shape[-1]
+        ptr = x.data_ptr()
+        vec = ptr % 16 == 0 and (nx * x.element_size()) % 16 == 0
+        if not (vec and nx % 1024 == 0) and nx >= 256 and ptr % 16 == 0:
+            flat = True
+        else:
+            row = True
+    return LAUNCHES_PER_GROUP - 1 + int(flat) + int(row)
 
 WORKLOADS = {
     "projections64": dict(
@@ -203,11 +223,17 @@ def run_ours(args, rank, world, local_rank):
         c.reserve(need)  # no workspace growth once the graph holds its pointers
     main = torch.cuda.Stream(dev)  # graphs must be captured off the legacy default stream
     torch.cuda.set_stream(main)
+    # launch shapes picked by the autotuner on this very workload (no output byte changes)
+    t0 = time.perf_counter()
+    tuning = ctxs[0].tune(xs, outs=outs, caps=caps, sizes=sizes, reps=3, stream=main, **cfg)
+    tune_s = time.perf_counter() - t0
+    for c in ctxs[1:]:
+        c.set_tuning(**tuning)
 
     if args.path == "batch":
         def step(inputs):
             ctxs[0].compress_batch(inputs, outs=outs, caps=caps, sizes=sizes, stream=main, **cfg)
-        launches_per_step = 7 * ((len(xs) + 63) // 64)
+        launches_per_step = sum(group_launches(xs[g:g + 64]) for g in range(0, len(xs), 64))
     else:
         def step(inputs):
             for s in streams:
@@ -218,7 +244,7 @@ def run_ours(args, rank, world, local_rank):
                                  stream=streams[k], **cfg)
             for s in streams:
                 main.wait_stream(s)
-        launches_per_step = 7 * len(xs)
+        launches_per_step = sum(group_launches([x]) for x in xs)
 
     # correctness of the measured configuration: one step, sizes vs a re-run
     step(xs)
@@ -409,12 +435,13 @@ def run_ours(args, rank, world, local_rank):
             "config": {"workload": args.workload, "desc": wl["desc"], "items": len(xs),
                        "bytes_in_per_step": in_bytes, "bytes_out_per_step": out_bytes,
                        "compression_ratio": round(in_bytes / max(out_bytes, 1), 3),
-                       "path": ("roix_compress_batch: 7 launches per 64 items" if
+                       "path": ("roix_compress_batch: %d launches per 64 items" % LAUNCHES_PER_GROUP if
                                 args.path == "batch" else "plain calls on %d streams" % nstreams)
                                + (", one CUDA graph per step" if graph is not None else ""),
                        "l2": "inputs larger than L2 (129 MB)" if in_bytes > 129e6
                        else "inputs smaller than L2: not flushed",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}",
+                       "tuning": dict(tuning, seconds=round(tune_s, 2))},
             "e2e": {k: (round(v, 2) if isinstance(v, float) else v) for k, v in e2e.items()},
             "latency": latency,
             "roofline": roofline,
@@ -1026,6 +1053,11 @@ def run_slabs(args, rank, world, local_rank):
     outs = [torch.empty(cap, dtype=torch.uint8, device=dev) for _ in range(ns)]
     sizes = torch.zeros(ns, dtype=torch.uint64, device=dev)
     cfgs = [dict(sc["cfg"], eb=eb) for eb in sc["sweep"]]
+    # launch shapes tuned on one slab compressed as a volume of its own
+    t0 = time.perf_counter()
+    tuning = rx.tune([x[:slab]], outs=outs[:1], caps=[cap], sizes=sizes[:1], reps=3,
+                     stream=main, **dict(cfgs[0], eb=sc["e2e_eb"]))
+    tune_s = time.perf_counter() - t0
     rx.reserve(rx.slabs_workspace_size(x.shape, slab, cap=cap, **cfgs[0]))
 
     def one(cfg, inp=None):
@@ -1144,7 +1176,7 @@ def run_slabs(args, rank, world, local_rank):
                 "stage_ms_per_call": {k: round(float(v), 4) for k, v in zip(names, stage_ms)},
                 "stage_gbs": {k: round(alg[k] / (float(v) / 1e3) / 1e9, 1)
                               for k, v in zip(names, stage_ms) if v > 0}}
-    launches = (2 + 5 * ((ns + 63) // 64)) * len(cfgs) * args.steps
+    launches = (2 + (LAUNCHES_PER_GROUP - 2) * ((ns + 63) // 64)) * len(cfgs) * args.steps
     result = None
     if rank == 0:
         cpu = slab_cpu(sc, args.cpu_budget, args.seed) if world == 1 and not args.no_cpu else None
@@ -1155,9 +1187,11 @@ def run_slabs(args, rank, world, local_rank):
             "data": "synthetic",
             "config": {"workload": args.workload, "desc": sc["desc"], "slabs": ns,
                        "bytes_in_per_call": in_bytes, "calls_per_step": len(cfgs),
-                       "sweep": sweep, "path": "roix_compress_slabs: 7 launches per call "
-                       "(32 slabs in one group)", "l2": "inputs larger than L2 (129 MB)",
-                       "parallelism": f"replicas x{world}"},
+                       "sweep": sweep, "path": "roix_compress_slabs: %d launches per call "
+                       "(32 slabs in one group)" % LAUNCHES_PER_GROUP,
+                       "l2": "inputs larger than L2 (129 MB)",
+                       "parallelism": f"replicas x{world}",
+                       "tuning": dict(tuning, seconds=round(tune_s, 2))},
             "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
             "gpu_launches": launches, "clocks": clk.summary(),
         }

@@ -421,6 +421,35 @@ roix_status roix_server_get_stats(roix_server* s, roix_server_stats* out);
 /* Finishes the pending requests, then releases the lanes. */
 roix_status roix_server_destroy(roix_server* s);
 
+/* ------------------------------------------------------------ autotuner
+ * Launch shapes of the compression kernels (no paper counterpart). None of
+ * them changes an output byte: they set the compaction tile size and how many
+ * blocks of the binarisation, symbol and pack kernels are resident per SM. */
+typedef struct {
+  uint32_t front_words;         /* mask words per compaction tile, 256..16384 (2048) */
+  uint32_t thr_blocks_per_sm;   /* binarisation, row form, 1..32 (8) */
+  uint32_t flat_blocks_per_sm;  /* binarisation, flat form, 1..32 (4) */
+  uint32_t sym_blocks_per_sm;   /* symbols, 0..32, 0 = as many as fit (0) */
+  uint32_t pack_blocks_per_sm;  /* pack, 0..32, 0 = as many as fit (0) */
+} roix_tuning;
+roix_status roix_get_tuning(const roix_ctx* ctx, roix_tuning* out);
+/* ROIX_EINVAL for values out of range (nothing changed). */
+roix_status roix_set_tuning(roix_ctx* ctx, const roix_tuning* t);
+/* Picks the context's launch shapes for a workload: times roix_compress_batch
+ * on the caller's items (real inputs and output buffers; containers are
+ * overwritten) for the candidates of one parameter at a time, in pipeline
+ * order, keeping a value only when the median of `reps` calls (0 = 5) is at
+ * least 1 % faster. cache_path (NULL: the ROIX_TUNE_CACHE environment
+ * variable, if set): a JSON file of tuned shapes keyed by device name, dtype
+ * and shape class (x extent and voxels per item rounded up to powers of two,
+ * item count bucket, dilation, keep); an entry found there is applied without
+ * timing and a new result is written back. Synchronises `stream`; the
+ * workspace may grow (do it before capturing graphs). *out (may be NULL)
+ * receives the result. */
+roix_status roix_tune(roix_ctx* ctx, uint32_t n, const roix_item* items, roix_dtype dtype,
+                      const roix_roi* roi, const roix_eb* eb, const roix_params* params,
+                      uint32_t reps, const char* cache_path, roix_tuning* out, void* stream);
+
 /* The fused path: the same bytes as the four stages, in fewer passes. */
 roix_status roix_compress(roix_ctx* ctx, const void* in, roix_dtype dtype, roix_dims dims,
                           const roix_roi* roi, const roix_eb* eb, const roix_params* params,

@@ -90,6 +90,12 @@ class ServerStats(C.Structure):
                 ("lane_bytes", C.c_uint64)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [(k, C.c_uint32) for k in ("front_words", "thr_blocks_per_sm",
+                                          "flat_blocks_per_sm", "sym_blocks_per_sm",
+                                          "pack_blocks_per_sm")]
+
+
 class EbInfo(C.Structure):
     _fields_ = [("eb_abs", C.c_double), ("vmin", C.c_double), ("vmax", C.c_double),
                 ("two_eb", C.c_float), ("inv2eb", C.c_float), ("bound", C.c_float),
@@ -147,6 +153,10 @@ def lib():
                 "roix_compress_slabs": (st, [P, P, i32, D, u64, R, E, PR, C.POINTER(P),
                                              C.POINTER(u64), P, P]),
                 "roix_slabs_workspace_size": (C.c_size_t, [i32, D, u64, R, PR, u64]),
+                "roix_get_tuning": (st, [P, C.POINTER(Tuning)]),
+                "roix_set_tuning": (st, [P, C.POINTER(Tuning)]),
+                "roix_tune": (st, [P, C.c_uint32, C.POINTER(Item), i32, R, E, PR, C.c_uint32,
+                                   C.c_char_p, C.POINTER(Tuning), P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -167,7 +177,7 @@ def symbols():
             "roix_server_get_stats", "roix_server_destroy", "roix_normalize8",
             "roix_greedy_quantize", "roix_greedy_quantize_batch", "roix_roi_quality",
             "roix_ssim", "roix_extract_roi_paper", "roix_compress_slabs",
-            "roix_slabs_workspace_size"]
+            "roix_slabs_workspace_size", "roix_get_tuning", "roix_set_tuning", "roix_tune"]
 
 
 def _dtype_code(t: torch.Tensor) -> int:
@@ -259,6 +269,39 @@ class Roix:
         cap = self.bound(shape, dtype, **cfg) if cap is None else cap
         return int(self.L.roix_workspace_size(code, dims_of(shape), C.byref(roi_of(**cfg)),
                                               C.byref(params_of(**cfg)), int(cap)))
+
+    # ------------------------------------------------------------- autotuner
+    def get_tuning(self) -> dict:
+        t = Tuning()
+        self._check(self.L.roix_get_tuning(self.ctx, C.byref(t)))
+        return {k: getattr(t, k) for k, _ in Tuning._fields_}
+
+    def set_tuning(self, **kw):
+        cur = self.get_tuning()
+        cur.update(kw)
+        self._check(self.L.roix_set_tuning(self.ctx, C.byref(Tuning(**cur))))
+
+    def tune(self, xs, outs=None, caps=None, sizes=None, reps: int = 5, cache: str | None = None,
+             stream=None, **cfg) -> dict:
+        """roix_tune on the batch xs (as compress_batch); returns the tuning."""
+        n = len(xs)
+        dev = xs[0].device
+        if outs is None:
+            caps = [x.numel() * x.element_size() + 65536 for x in xs] if caps is None else caps
+            outs = [torch.empty(c, dtype=torch.uint8, device=dev) for c in caps]
+        caps = [o.numel() for o in outs] if caps is None else caps
+        if sizes is None:
+            sizes = torch.zeros(n, dtype=torch.uint64, device=dev)
+        arr = (Item * n)()
+        for i, x in enumerate(xs):
+            arr[i] = Item(x.data_ptr(), dims_of(x.shape), outs[i].data_ptr(), int(caps[i]),
+                          sizes.data_ptr() + 8 * i)
+        t = Tuning()
+        self._check(self.L.roix_tune(self.ctx, n, arr, _dtype_code(xs[0]), C.byref(roi_of(**cfg)),
+                                     C.byref(eb_of(**cfg)), C.byref(params_of(**cfg)), int(reps),
+                                     cache.encode() if cache else None, C.byref(t),
+                                     _stream(stream)))
+        return {k: getattr(t, k) for k, _ in Tuning._fields_}
 
     # ------------------------------------------------------------ fused path
     def compress(self, x: torch.Tensor, out: torch.Tensor | None = None, cap: int | None = None,

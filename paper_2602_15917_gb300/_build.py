@@ -14,7 +14,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libroix.so")
 SOURCES = ["roix_api.cu", "k_mask.cu", "k_encode.cu", "k_decode.cu", "k_ccl.cu", "roix_server.cu", "roix_static.cu",
            "k_greedy.cu", "k_metrics.cu",
-           "k_paper_roi.cu"]
+           "k_paper_roi.cu", "roix_tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

@@ -245,9 +245,10 @@ __device__ __forceinline__ void flush_hist(u32* h, unsigned long long* g, u32 S,
 // from value base - 1, quantised again. Symbols leave as one vector store per
 // lane and step; the histogram is the warp's own in shared memory (no block
 // barrier anywhere in the loop) and goes to the item's global histogram when
-// the warp moves to another item. Symbol-0 positions (records) are kept as a
-// 128-bit mask per lane; the segment's record count is placed by a warp-level
-// decoupled look-back and the records are written in value order.
+// the warp moves to another item. Symbol-0 positions (records) are only
+// counted here, per pack chunk (an atomic per lane and step that has one);
+// they are written by k_records once their offsets are known, so that no
+// segment waits for another.
 template <typename TV, bool FROM_Q>
 __global__ void __launch_bounds__(kThreads) k_symbols(const __grid_constant__ Batch B) {
   using Vec = SymVec<TV, FROM_Q>;
@@ -255,11 +256,11 @@ __global__ void __launch_bounds__(kThreads) k_symbols(const __grid_constant__ Ba
   constexpr u32 kStep = 32u * V;                 // values per warp and step
   constexpr int kSteps = (int)(kQuantTile / kStep);
   constexpr int kBatch = V >= 8 ? 4 : (kSteps < 8 ? kSteps : 8);  // loads in flight per lane
-  static_assert(kQuantTile / 32 == 128, "128 values per lane and segment: two mask words");
-  static_assert(kSteps % kBatch == 0 && 64 % V == 0, "whole batches, steps within one word");
+  static_assert(kQuantTile % kStep == 0 && kSteps % kBatch == 0, "whole steps and batches");
   extern __shared__ u32 hsm[];  // [warps][S]
   __shared__ u64 pre[kMaxBatch + 1];
   const u32 R_ = B.c.R, S = B.c.S;
+  const u32 csh = (u32)(__ffs((int)B.c.C) - 1);  // log2 of the pack chunk
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   u32* h = hsm + (u32)warp * S;
   for (u32 i = lane; i < S; i += 32) h[i] = 0;
@@ -295,7 +296,6 @@ __global__ void __launch_bounds__(kThreads) k_symbols(const __grid_constant__ Ba
     }
     ++since_flush;
     const u64 t = gt - pre[item];
-    const u64 nseg = (n + kQuantTile - 1) / kQuantTile;
     const u64 base = t * kQuantTile;
     uint16_t* __restrict__ sym = I.sym;
     int carry = 0;  // code of value base - 1 (0 for an outlier or none)
@@ -304,7 +304,8 @@ __global__ void __launch_bounds__(kThreads) k_symbols(const __grid_constant__ Ba
       carry = src.code(base - 1, o);
     }
     carry = __shfl_sync(0xffffffffu, carry, 0);
-    u64 rm0 = 0, rm1 = 0;  // record positions: bit s * V + j
+    u32* __restrict__ crec = I.crec;
+    u32* __restrict__ rbits = I.rbits;
     // one step: V codes per lane, deltas, symbols, histogram, record bits;
     // GUARD = the segment reaches past n (the item's last segment)
     auto step = [&](auto guard_tag, const int st, const Vec& r) {
@@ -350,9 +351,15 @@ __global__ void __launch_bounds__(kThreads) k_symbols(const __grid_constant__ Ba
         for (int j = 0; j < V; ++j)
           if (k0 + j < n) sym[k0 + j] = (uint16_t)sv[j];
       }
-      const int bit = st * V;
-      if (bit < 64) rm0 |= (u64)rb << bit;
-      else rm1 |= (u64)rb << (bit - 64);
+      if (rb) atomicAdd(crec + (k0 >> csh), (u32)__popc(rb));  // records of the pack chunk
+      // record bitmap: bit k % 32 of word k / 32 (the 32 / V lanes of a word OR-ed)
+      {
+        constexpr int kLanesPerWord = 32 / V;
+        u32 wv = rb << (u32)(k0 & 31);
+#pragma unroll
+        for (int o = 1; o < kLanesPerWord; o <<= 1) wv |= __shfl_xor_sync(0xffffffffu, wv, o);
+        if ((lane & (kLanesPerWord - 1)) == 0 && (!GUARD || k0 < n)) rbits[k0 >> 5] = wv;
+      }
     };
     if (base + kQuantTile <= n) {  // a whole segment: no bounds checks
 #pragma unroll
@@ -372,44 +379,6 @@ __global__ void __launch_bounds__(kThreads) k_symbols(const __grid_constant__ Ba
           sym_load<TV, FROM_Q>(src, base + (u64)(b0 + i) * kStep + (u64)lane * V, n, r[i]);
 #pragma unroll
         for (int i = 0; i < kBatch; ++i) step(std::true_type{}, b0 + i, r[i]);
-      }
-    }
-    // records of the segment, placed by the look-back, written in value order
-    const u32 mine_n = warp_sum((u32)(__popcll(rm0) + __popcll(rm1)));
-    u64 rbase;
-    {
-      u64 mine[1] = {mine_n}, excl[1];
-      lookback_warp<1>(I.lbq, t, mine, excl, B.status);
-      rbase = excl[0];
-      if (lane == 0 && t == nseg - 1) I.st->nout = excl[0] + mine_n;
-    }
-    if (mine_n) {
-      u64 run = rbase;
-      for (int st = 0; st < kSteps; ++st) {
-        const int bit = st * V;
-        const u32 bits =
-            (u32)((bit < 64 ? (rm0 >> bit) : (rm1 >> (bit - 64))) & ((1ull << V) - 1ull));
-        const u32 cn = __popc(bits);
-        const u32 inc = warp_incl_scan(cn);
-        const u32 tot = __shfl_sync(0xffffffffu, inc, 31);
-        if (tot == 0) continue;
-        u64 idx = run + inc - cn;
-        u32 bb = bits;
-        while (bb) {
-          const int j = __ffs(bb) - 1;
-          bb &= bb - 1;
-          const u64 k = base + (u64)st * kStep + (u64)lane * V + j;
-          bool out;
-          const int c = src.code(k, out);
-          if (idx < I.rec_cap) {
-            I.rk[idx] = k | (out ? (1ull << 63) : 0ull);
-            I.rv[idx] = out ? src.raw_bits(k) : (u32)c;
-          } else {
-            atomicExch(&I.st->cap_flag, 1u);
-          }
-          ++idx;
-        }
-        run += tot;
       }
     }
   }
@@ -442,6 +411,33 @@ __device__ void bitonic_sort(u64* key, u32 M) {
   }
 }
 
+// Same network for M <= blockDim.x keys with thread i holding key i in a
+// register: distances below 32 by warp shuffles (no barrier), larger ones
+// through shared memory.
+__device__ void bitonic_sort_reg(u64* key, u32 M) {
+  const u32 i = threadIdx.x;
+  u64 v = i < M ? key[i] : ~0ull;
+  for (u32 k = 2; k <= M; k <<= 1) {
+    for (u32 j = k >> 1; j > 0; j >>= 1) {
+      u64 o;
+      if (j >= 32) {
+        __syncthreads();
+        if (i < M) key[i] = v;
+        __syncthreads();
+        o = i < M ? key[i ^ j] : ~0ull;
+      } else {
+        o = __shfl_xor_sync(0xffffffffu, v, j);
+      }
+      const bool up = (i & k) == 0, lower = (i & j) == 0;
+      const u64 lo = v < o ? v : o, hi = v < o ? o : v;
+      v = (up == lower) ? lo : hi;
+    }
+  }
+  __syncthreads();
+  if (i < M) key[i] = v;
+  __syncthreads();
+}
+
 __host__ __device__ __forceinline__ u32 next_pow2(u32 v) {
   u32 p = 1;
   while (p < v) p <<= 1;
@@ -470,6 +466,74 @@ __device__ long long g_cb_probe[16];
 #else
 #define CB_MARK(i)
 #endif
+
+// Two-queue Huffman construction (van Leeuwen 1976) by one thread: leaves
+// 0..m-1 sorted ascending (weights lw), internal nodes m..2m-2 created in
+// order (weights wi), par[] receives every node's parent. Each iteration pops
+// the two lightest fronts, a leaf winning ties, and creates one node. The
+// fronts live in register windows (four leaves, three internal nodes); the
+// loads that refill them are issued at the top of an iteration and consumed
+// only at its end, after both pops, so shared-memory latency stays off the
+// chain of compares and selects. An empty slot holds the sentinel ~0.
+template <typename W>
+__device__ __forceinline__ W sel3(u32 k, W a, W b, W c) {
+  return k == 0 ? a : (k == 1 ? b : c);
+}
+
+template <typename W, typename LeafW>
+__device__ __forceinline__ void huffman_merge_impl(LeafW leaf, W* wi, int32_t* par, u32 m) {
+  constexpr W kNone = ~W(0);
+  u32 lf = 0, in = 0, created = 0;
+  W A0 = leaf(0), A1 = m > 1 ? leaf(1) : kNone, A2 = m > 2 ? leaf(2) : kNone,
+    A3 = m > 3 ? leaf(3) : kNone;
+  W I0 = kNone, I1 = kNone, I2 = kNone;
+  for (u32 t = 0; t + 1 < m; ++t) {
+    // refills for after this iteration (at most two of each queue consumed)
+    const W la4 = lf + 4 < m ? leaf(lf + 4) : kNone;
+    const W la5 = lf + 5 < m ? leaf(lf + 5) : kNone;
+    const W lb3 = in + 3 < created ? wi[in + 3] : kNone;
+    const W lb4 = in + 4 < created ? wi[in + 4] : kNone;
+    // pop 1
+    const bool t1 = A0 <= I0;
+    const W f1 = t1 ? A0 : I0;
+    const int32_t p1 = t1 ? (int32_t)lf : (int32_t)(m + in);
+    const W a0 = t1 ? A1 : A0, i0 = t1 ? I0 : I1;
+    // pop 2
+    const bool t2 = a0 <= i0;
+    const W f2 = t2 ? a0 : i0;
+    const u32 lf1 = lf + (t1 ? 1u : 0u), in1 = in + (t1 ? 0u : 1u);
+    const int32_t p2 = t2 ? (int32_t)lf1 : (int32_t)(m + in1);
+    const u32 cl = (t1 ? 1u : 0u) + (t2 ? 1u : 0u), ci = 2u - cl;
+    const W ws = f1 + f2;
+    // windows shifted by what was consumed
+    const W nA0 = sel3(cl, A0, A1, A2), nA1 = sel3(cl, A1, A2, A3), nA2 = sel3(cl, A2, A3, la4),
+            nA3 = sel3(cl, A3, la4, la5);
+    W nI0 = sel3(ci, I0, I1, I2), nI1 = sel3(ci, I1, I2, lb3), nI2 = sel3(ci, I2, lb3, lb4);
+    lf += cl;
+    in += ci;
+    wi[created] = ws;
+    par[p1] = (int32_t)(m + created);
+    par[p2] = (int32_t)(m + created);
+    ++created;
+    const u32 q = created - in;  // internal nodes waiting, the new one included
+    nI0 = q == 1 ? ws : nI0;
+    nI1 = q == 2 ? ws : nI1;
+    nI2 = q == 3 ? ws : nI2;
+    A0 = nA0; A1 = nA1; A2 = nA2; A3 = nA3;
+    I0 = nI0; I1 = nI1; I2 = nI2;
+  }
+  par[2 * m - 2] = -1;
+}
+
+template <typename W>
+__device__ __forceinline__ void huffman_merge(const W* lw, W* wi, int32_t* par, u32 m) {
+  huffman_merge_impl<W>([&](u32 i) { return lw[i]; }, wi, par, m);
+}
+
+// 64-bit weights straight from the (count << 16 | symbol) keys
+__device__ __forceinline__ void huffman_merge_key(const u64* key, u64* wi, int32_t* par, u32 m) {
+  huffman_merge_impl<u64>([&](u32 i) { return key[i] >> 16; }, wi, par, m);
+}
 
 __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__ Batch B) {
   extern __shared__ __align__(16) unsigned char cb_smem[];
@@ -518,8 +582,10 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__
     __syncthreads();
     if (tid < (int)m) key[rank] = mine;
     __syncthreads();
+  } else if (M <= (u32)kCbThreads) {
+    bitonic_sort_reg(key, M);  // ascending (count, symbol)
   } else {
-    bitonic_sort(key, M);  // ascending (count, symbol)
+    bitonic_sort(key, M);
   }
   CB_MARK(2)
   if (m == 1) {
@@ -528,44 +594,25 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__
       bl[1] = 1;
     }
   } else if (m >= 2) {
-    // two-queue construction: leaves 0..m-1 in sorted order, internal m..2m-2.
-    // The fronts of both queues live in register windows (three leaves, two
-    // internal nodes) refilled from shared memory by loads issued before the
-    // comparison that needs them; an empty slot reads as the sentinel ~0
-    // (weights are below 2^48), so "leaf if wl <= wi" keeps the leaf-first tie
-    // rule. Branch-free selects keep the dependent chain per pop short.
-    if (tid == 0) {
-      constexpr u64 kNone = ~0ull;
-      u32 lf = 0, in = 0, created = 0;
-      u64 L0 = key[0] >> 16, L1 = m > 1 ? key[1] >> 16 : kNone, L2 = m > 2 ? key[2] >> 16 : kNone;
-      u64 I0 = kNone, I1 = kNone;
-      for (u32 t = 0; t + 1 < m; ++t) {
-        int32_t p2[2];
-        u64 wsum = 0;
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          const u64 nextL = lf + 3 < m ? key[lf + 3] >> 16 : kNone;
-          const u64 nextI = in + 2 < created ? wint[in + 2] : kNone;
-          const bool takeL = L0 <= I0;
-          p2[k] = takeL ? (int32_t)lf : (int32_t)(m + in);
-          wsum += takeL ? L0 : I0;
-          L0 = takeL ? L1 : L0;
-          L1 = takeL ? L2 : L1;
-          L2 = takeL ? nextL : L2;
-          I0 = takeL ? I0 : I1;
-          I1 = takeL ? I1 : nextI;
-          lf += takeL ? 1u : 0u;
-          in += takeL ? 0u : 1u;
-        }
-        wint[created] = wsum;
-        par[p2[0]] = (int32_t)(m + created);
-        par[p2[1]] = (int32_t)(m + created);
-        ++created;
-        const u32 q = created - in;  // internal nodes waiting, the new one included
-        if (q == 1) I0 = wsum;
-        else if (q == 2) I1 = wsum;
-      }
-      par[2 * m - 2] = -1;
+    // two-queue construction (thread 0), 32-bit weights when the total fits
+    const u64 tot_w = [&] {
+      u64 acc = 0;
+      for (u32 i = tid; i < m; i += kCbThreads) acc += key[i] >> 16;
+      acc = warp_sum(acc);
+      if ((tid & 31) == 0) scratch[tid >> 5] = (u32)umin(acc, 0xffffffffull);
+      __syncthreads();
+      u64 all = 0;
+      for (int w = 0; w < kCbThreads / 32; ++w) all += scratch[w];
+      __syncthreads();
+      return all;
+    }();
+    if (tot_w < 0xffffffffull) {
+      u32* lw = reinterpret_cast<u32*>(dep);  // leaf weights (dep is free until the depths)
+      for (u32 i = tid; i < m; i += kCbThreads) lw[i] = (u32)(key[i] >> 16);
+      __syncthreads();
+      if (tid == 0) huffman_merge<u32>(lw, reinterpret_cast<u32*>(wint), par, m);
+    } else {
+      if (tid == 0) huffman_merge_key(key, wint, par, m);
     }
     __syncthreads();
     CB_MARK(3)
@@ -574,19 +621,25 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__
     for (u32 i = tid; i < nodes; i += kCbThreads) dep[i] = par[i] >= 0 ? 1 : 0;
     __syncthreads();
     for (u32 round = 0; (1u << round) < nodes; ++round) {
-      int32_t na[(2 * kMaxSym + kCbThreads - 1) / kCbThreads];
-      int32_t nd[(2 * kMaxSym + kCbThreads - 1) / kCbThreads];
-      int cnt = 0;
-      for (u32 i = tid; i < nodes; i += kCbThreads, ++cnt) {
-        const int32_t a = par[i];
-        nd[cnt] = a >= 0 ? dep[i] + dep[a] : dep[i];
-        na[cnt] = a >= 0 ? par[a] : -1;
+      constexpr int kPer = (2 * kMaxSym + kCbThreads - 1) / kCbThreads;
+      int32_t na[kPer], nd[kPer];
+#pragma unroll
+      for (int c = 0; c < kPer; ++c) {
+        const u32 i = tid + (u32)c * kCbThreads;
+        if (i < nodes) {
+          const int32_t a = par[i];
+          nd[c] = a >= 0 ? dep[i] + dep[a] : dep[i];
+          na[c] = a >= 0 ? par[a] : -1;
+        }
       }
       __syncthreads();
-      cnt = 0;
-      for (u32 i = tid; i < nodes; i += kCbThreads, ++cnt) {
-        dep[i] = nd[cnt];
-        par[i] = na[cnt];
+#pragma unroll
+      for (int c = 0; c < kPer; ++c) {
+        const u32 i = tid + (u32)c * kCbThreads;
+        if (i < nodes) {
+          dep[i] = nd[c];
+          par[i] = na[c];
+        }
       }
       __syncthreads();
     }
@@ -679,50 +732,26 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__
 }
 
 // ------------------------------------------------------------------- pack
-// Persistent warps, each on its own chunk of C symbols (global ticket, every
-// item's chunks in order), in rounds of 256 symbols: lane l holds symbols
-// [8 l, 8 l + 8) of a round (one coalesced 16-byte load) and looks their
-// length << 24 | code up in the item's code table, copied into the warp's own
-// shared memory. Pass 1 sums the lengths; a warp-level decoupled look-back
-// gives the chunk's word offset in the payload. Pass 2 gives every code its
-// bit offset (lane sums scanned across the warp) and ORs it, MSB first, into
-// a ring of words in the warp's shared memory (a code spans at most two
-// words); after each round the words that are complete are stored with
-// coalesced stores and cleared. No block barrier in the loop.
-constexpr u32 kPackRing = 256;  // words per warp ring: one round is at most 193 open words
+// Three passes, none waiting on another block: k_pack_count sums the code
+// lengths of every chunk, k_pack_scan turns the chunks' word and record
+// counts into offsets (one block per item), and k_pack writes every chunk's
+// words at its offset; k_records writes the records of the chunks that have
+// any. Chunks are taken from global tickets in order.
 
-__device__ __forceinline__ void pack_load8(const uint16_t* __restrict__ sym, u64 k, u64 n,
-                                           u32 (&s8)[8]) {
-  if (k + 8 <= n) {
-    const uint4 v = __ldg(reinterpret_cast<const uint4*>(sym + k));
-    const u32 w4[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      s8[2 * q] = w4[q] & 0xffffu;
-      s8[2 * q + 1] = w4[q] >> 16;
-    }
-  } else {
-#pragma unroll
-    for (int q = 0; q < 8; ++q) s8[q] = k + q < n ? (u32)__ldg(sym + k + q) : 0xffffffffu;
-  }
-}
-
-__global__ void __launch_bounds__(kThreads) k_pack(const __grid_constant__ Batch B) {
-  extern __shared__ u32 tsm[];  // [warps][S] length << 24 | code, then [warps][kPackRing]
+// Warps, one chunk at a time: lane l holds symbols [8 l, 8 l + 8) of each
+// round of 256 (coalesced 16-byte loads); the code lengths come from the
+// item's table in the warp's shared memory.
+__global__ void __launch_bounds__(kThreads) k_pack_count(const __grid_constant__ Batch B) {
+  extern __shared__ u32 lsm[];  // [warps][S] code lengths
   __shared__ u64 pre[kMaxBatch + 1];
   const u32 C = B.c.C, S = B.c.S;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  u32* tab = tsm + (u32)warp * S;
-  u32* ring = tsm + (kThreads / 32) * S + (u32)warp * kPackRing;
-  for (u32 i = lane; i < kPackRing; i += 32) ring[i] = 0u;
+  u32* len = lsm + (u32)warp * S;
   tile_prefix(B, pre, C, 1);
   const u64 total = pre[B.n];
-  const u32 rounds = C / 256;
   u32 cur = 0xffffffffu;
-  u64 n = 0, nchunks = 0, cap = 0;
-  Layout Lo{};
+  u64 n = 0;
   const uint16_t* __restrict__ sym = nullptr;
-  uint8_t* out = nullptr;
   while (true) {
     u64 gt = 0;
     if (lane == 0) gt = atomicAdd(&B.ctr[2], 1u);
@@ -730,81 +759,231 @@ __global__ void __launch_bounds__(kThreads) k_pack(const __grid_constant__ Batch
     if (gt >= total) break;
     const u32 item = find_item(pre, B.n, gt);
     const Item& I = B.it[item];
-    if (item != cur) {  // the item's code table into the warp's shared memory
+    if (item != cur) {
       cur = item;
       __syncwarp();
-      for (u32 i = lane; i < S; i += 32) tab[i] = __ldg(I.codes + i);
+      for (u32 i = lane; i < S; i += 32) len[i] = __ldg(I.codes + i) >> 24;
       __syncwarp();
       n = umin(I.sizes[0], I.N);
-      nchunks = (n + C - 1) / C;
-      Lo = make_layout(S, I.rows, I.sizes[1], I.st->nout, nchunks, 0);
       sym = I.sym;
-      out = I.out;
-      cap = I.cap;
     }
     const u64 t = gt - pre[item];
     const u64 c0 = t * C + (u64)lane * 8;
-    // pass 1: bits of the chunk
     u32 bits = 0;
-    for (u32 r = 0; r < rounds; ++r) {
-      u32 s8[8];
-      pack_load8(sym, c0 + (u64)r * 256, n, s8);
+    for (u32 r = 0; r < C / 256; ++r) {
+      const u64 k = c0 + (u64)r * 256;
+      if (k + 8 <= n) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(sym + k));
+        bits += len[v.x & 0xffffu] + len[v.x >> 16] + len[v.y & 0xffffu] + len[v.y >> 16] +
+                len[v.z & 0xffffu] + len[v.z >> 16] + len[v.w & 0xffffu] + len[v.w >> 16];
+      } else {
 #pragma unroll
-      for (int q = 0; q < 8; ++q) bits += s8[q] != 0xffffffffu ? tab[s8[q]] >> 24 : 0u;
-    }
-    const u32 chunk_bits = warp_sum(bits);
-    const u32 words = (chunk_bits + 31) >> 5;
-    u64 cbase;
-    {
-      u64 mine[1] = {words}, excl[1];
-      lookback_warp<1>(I.lbp, t, mine, excl, B.status);
-      cbase = excl[0];
-    }
-    if (lane == 0) {
-      const u64 o = Lo.off_chunks + 8 * t;
-      if (o + 8 <= cap) *reinterpret_cast<u64*>(out + o) = cbase;
-      if (t == nchunks - 1) I.st->nwords = cbase + words;
-    }
-    const u64 pay = Lo.off_payload + 4 * cbase;  // byte offset of the chunk's first word
-    // pass 2: deposit every code at its bit offset, store the complete words
-    u32 run = 0, flushed = 0;
-    for (u32 r = 0; r < rounds && run < chunk_bits; ++r) {
-      u32 s8[8], e8[8];
-      pack_load8(sym, c0 + (u64)r * 256, n, s8);
-      u32 lb = 0;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        e8[q] = s8[q] != 0xffffffffu ? tab[s8[q]] : 0u;
-        lb += e8[q] >> 24;
+        for (int q = 0; q < 8; ++q)
+          if (k + q < n) bits += len[__ldg(sym + k + q)];
       }
-      const u32 inc = warp_incl_scan(lb);
-      u32 off = run + inc - lb;
+    }
+    bits = warp_sum(bits);
+    if (lane == 0) I.cw[t] = (bits + 31) >> 5;
+  }
+}
+
+// One block per item: exclusive scans of the chunks' words and records, the
+// totals into the item's state, the chunk table into the container.
+__global__ void __launch_bounds__(kCbThreads) k_pack_scan(const __grid_constant__ Batch B) {
+  __shared__ u64 scratch[40];
+  const Item& I = B.it[blockIdx.x];
+  const u32 C = B.c.C, S = B.c.S;
+  const u64 n = umin(I.sizes[0], I.N);
+  const u64 nchunks = (n + C - 1) / C;
+  u64 wcarry, rcarry;
+  block_scan2(I.cw, I.crec, nchunks, I.cwoff, I.crecoff, scratch, &wcarry, &rcarry);
+  __syncthreads();  // the offsets below are read by other threads than their writers
+  State* st = I.st;
+  if (threadIdx.x == 0) {
+    st->nout = rcarry;
+    st->nwords = wcarry;
+    if (rcarry > I.rec_cap) st->cap_flag = 1u;
+  }
+  const Layout Lo = make_layout(S, I.rows, I.sizes[1], rcarry, nchunks, wcarry);
+  uint8_t* out = I.out;
+  const u64 cap = I.cap;
+  for (u64 t = threadIdx.x; t < nchunks; t += blockDim.x) {
+    const u64 o = Lo.off_chunks + 8 * t;
+    if (o + 8 <= cap) *reinterpret_cast<u64*>(out + o) = I.cwoff[t];
+  }
+}
+
+// Warps, one chunk at a time, only chunks that hold records: the symbol-0
+// positions of the chunk in order, from the record bitmap the symbol kernel
+// wrote (lane l with words l, l + 32, ...; a warp scan of their popcounts),
+// each written as (k | kind << 63, payload) at the chunk's record offset; the
+// code or the raw value is formed again from the pixel section (or the staged
+// codes).
+template <typename TV, bool FROM_Q>
+__global__ void __launch_bounds__(kThreads) k_records(const __grid_constant__ Batch B) {
+  __shared__ u64 pre[kMaxBatch + 1];
+  const u32 C = B.c.C;
+  const int lane = threadIdx.x & 31;
+  tile_prefix(B, pre, C, 1);
+  const u64 total = pre[B.n];
+  const u64 warp0 = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
+  u32 cur = 0xffffffffu;
+  Src<TV, FROM_Q> src{};
+  u64 n = 0;
+  for (u64 gt = warp0; gt < total; gt += nwarps) {
+    const u32 item = find_item(pre, B.n, gt);
+    const Item& I = B.it[item];
+    const u64 t = gt - pre[item];
+    if (I.crec[t] == 0u) continue;
+    if (item != cur) {
+      cur = item;
+      const Desc d = desc_of(B, I);
+      src.P = (const TV*)I.P;
+      src.q = I.q;
+      src.obits = I.obits;
+      src.dark = d.dark;
+      if constexpr (!FROM_Q) {
+        src.e = make_eb(d, I.rst->vmin_key, I.rst->vmax_key);
+        src.fd = FastDiv(2u * (u32)src.e.eb_int);
+      }
+      n = umin(I.sizes[0], I.N);
+    }
+    const u32* __restrict__ rbits = I.rbits;
+    u64 idx = I.crecoff[t];
+    const u64 w0 = t * (C / 32), nwords = (umin(n, (t + 1) * (u64)C) - t * C + 31) / 32;
+    for (u64 j0 = 0; j0 < nwords; j0 += 32) {
+      const u64 j = j0 + lane;
+      u32 zm = j < nwords ? __ldg(rbits + w0 + j) : 0u;
+      const u32 cnt = __popc(zm);
+      const u32 inc = warp_incl_scan(cnt);
+      u64 o = idx + inc - cnt;
+      while (zm) {
+        const int q = __ffs(zm) - 1;
+        zm &= zm - 1;
+        const u64 k = (w0 + j) * 32 + q;
+        bool out;
+        const int c = src.code(k, out);
+        if (o < I.rec_cap) {
+          I.rk[o] = k | (out ? (1ull << 63) : 0ull);
+          I.rv[o] = out ? src.raw_bits(k) : (u32)c;
+        }
+        ++o;
+      }
+      idx += __shfl_sync(0xffffffffu, inc, 31);
+    }
+  }
+}
+
+// Persistent blocks, one chunk of C symbols at a time: thread i loads its
+// EPT = C / 256 consecutive symbols (16-byte loads) and keeps their length <<
+// 24 | code entries (from the item's code table in shared memory) in
+// registers; a block scan of the per-thread bit counts gives each thread its
+// bit offset; each thread assembles its words of the chunk's stream (MSB
+// first) in a shared buffer, OR-ing only the words it shares with its
+// neighbours; the words are stored with coalesced stores at the chunk's
+// offset.
+template <int EPT>
+__global__ void __launch_bounds__(kThreads) k_pack(const __grid_constant__ Batch B) {
+  extern __shared__ unsigned long long wb[];  // [C * kLMax / 64 + 2]
+  __shared__ u32 tab[kMaxSym];
+  __shared__ u32 scratch[40];
+  __shared__ u64 s_tile;
+  __shared__ u64 pre[kMaxBatch + 1];
+  const u32 C = B.c.C, S = B.c.S;
+  const int tid = threadIdx.x;
+  tile_prefix(B, pre, C, 1);
+  const u64 total = pre[B.n];
+  const u32 wb_words = C * kLMax / 64 + 2;
+  for (u32 i = tid; i < wb_words; i += blockDim.x) wb[i] = 0ull;
+  u32 cur = 0xffffffffu;
+  u64 n = 0, cap = 0, pay0 = 0;
+  const uint16_t* __restrict__ sym = nullptr;
+  uint8_t* out = nullptr;
+  while (true) {
+    if (tid == 0) s_tile = atomicAdd(&B.ctr[3], 1u);
+    __syncthreads();
+    const u64 gt = s_tile;
+    if (gt >= total) break;
+    const u32 item = find_item(pre, B.n, gt);
+    const Item& I = B.it[item];
+    if (item != cur) {  // the item's code table into shared memory
+      cur = item;
+      for (u32 i = tid; i < S; i += blockDim.x) tab[i] = __ldg(I.codes + i);
+      n = umin(I.sizes[0], I.N);
+      const u64 nchunks = (n + C - 1) / C;
+      pay0 = make_layout(S, I.rows, I.sizes[1], I.st->nout, nchunks, 0).off_payload;
+      sym = I.sym;
+      out = I.out;
+      cap = I.cap;
+      __syncthreads();
+    }
+    const u64 t = gt - pre[item];
+    const u64 k0 = t * C + (u64)tid * EPT;
+    u32 e[EPT];
+    u32 bits = 0;
+    if constexpr (EPT % 8 == 0) {
+      if (k0 + EPT <= n) {
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const u32 l = e8[q] >> 24, c = e8[q] & 0xffffffu;
-        if (l) {
-          const u32 w = off >> 5, sh = off & 31, end = sh + l;
-          if (end <= 32) {
-            atomicOr(&ring[w & (kPackRing - 1)], c << (32 - end));
-          } else {
-            atomicOr(&ring[w & (kPackRing - 1)], c >> (end - 32));
-            atomicOr(&ring[(w + 1) & (kPackRing - 1)], c << (64 - end));
+        for (int j = 0; j < EPT; j += 8) {
+          const uint4 v = __ldg(reinterpret_cast<const uint4*>(sym + k0 + j));
+          const u32 w4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            e[j + 2 * q] = tab[w4[q] & 0xffffu];
+            e[j + 2 * q + 1] = tab[w4[q] >> 16];
           }
-          off += l;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < EPT; ++j) e[j] = k0 + j < n ? tab[__ldg(sym + k0 + j)] : 0u;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < EPT; ++j) e[j] = k0 + j < n ? tab[__ldg(sym + k0 + j)] : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < EPT; ++j) bits += e[j] >> 24;
+    u32 cbits;
+    const u32 off = block_excl_scan<u32>(bits, scratch, &cbits);
+    const u32 words = (cbits + 31) >> 5;
+    // the thread's codes are contiguous in the chunk's stream [off, off +
+    // bits): they are shifted MSB first through a 64-bit register; words that
+    // lie wholly in the thread's range are stored, the first and last (which
+    // may be shared with the neighbouring threads) are OR-ed
+    if (bits) {
+      u32* wb32 = reinterpret_cast<u32*>(wb);
+      u32 w = off >> 5;
+      const u32 pos = off & 31;
+      u64 acc = 0;
+      u32 nacc = pos;  // the leading pos bits of word w belong to earlier threads
+      bool shared_first = pos != 0;
+#pragma unroll
+      for (int j = 0; j < EPT; ++j) {
+        const u32 l = e[j] >> 24;
+        acc = (acc << l) | (e[j] & 0xffffffu);
+        nacc += l;
+        if (nacc >= 32) {
+          const u32 word = (u32)(acc >> (nacc - 32));
+          if (shared_first) atomicOr(&wb32[w], word);
+          else wb32[w] = word;
+          shared_first = false;
+          ++w;
+          nacc -= 32;
+          acc &= (1ull << nacc) - 1ull;
         }
       }
-      run += __shfl_sync(0xffffffffu, inc, 31);
-      __syncwarp();
-      const u32 complete = run == chunk_bits ? (run + 31) >> 5 : run >> 5;  // last word padded
-      for (u32 i = flushed + lane; i < complete; i += 32) {
-        const u64 o = pay + 4 * (u64)i;
-        u32* slot = &ring[i & (kPackRing - 1)];
-        if (o + 4 <= cap) *reinterpret_cast<u32*>(out + o) = *slot;
-        *slot = 0u;
-      }
-      flushed = complete;
-      __syncwarp();
+      if (nacc > (shared_first ? pos : 0u)) atomicOr(&wb32[w], (u32)(acc << (32 - nacc)));
     }
+    __syncthreads();
+    const u64 pay = pay0 + 4 * I.cwoff[t];  // byte offset of the chunk's first word
+    const u32* wb32 = reinterpret_cast<const u32*>(wb);
+    for (u32 i = tid; i < words; i += blockDim.x) {
+      const u64 o = pay + 4 * (u64)i;
+      if (o + 4 <= cap) *reinterpret_cast<u32*>(out + o) = wb32[i];
+    }
+    __syncthreads();
+    for (u32 i = tid; i < (words + 1) / 2; i += blockDim.x) wb[i] = 0ull;
   }
 }
 
@@ -967,6 +1146,7 @@ void launch_symbols(const Launch& L, const Batch& B, u64 tiles_cap) {
     cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     u64 grid = (u64)grid_for((const void*)kernel, kThreads, smem, L.sms);
+    if (L.t.sym_blocks_per_sm) grid = umin(grid, (u64)L.t.sym_blocks_per_sm * L.sms);
     const u64 need = (tiles_cap + kThreads / 32 - 1) / (kThreads / 32);  // a segment per warp
     if (grid > need) grid = need;
     kernel<<<(unsigned)grid, kThreads, smem, L.stream>>>(B);
@@ -989,14 +1169,46 @@ void launch_codebook(const Launch& L, const Batch& B) {
 
 void launch_pack(const Launch& L, const Batch& B, u64 ranges_cap) {
   if (ranges_cap == 0) return;
-  // one code table and one word ring per warp
-  const size_t smem = (size_t)(kThreads / 32) * (B.c.S + kPackRing) * 4;
-  cudaFuncSetAttribute((const void*)k_pack, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)smem);
-  u64 grid = (u64)grid_for((const void*)k_pack, kThreads, smem, L.sms);
-  const u64 need = (ranges_cap + kThreads / 32 - 1) / (kThreads / 32);  // a chunk per warp
-  if (grid > need) grid = need;
-  k_pack<<<(unsigned)grid, kThreads, smem, L.stream>>>(B);
+  const u64 wpb = kThreads / 32;
+  {  // chunk sizes
+    const size_t smem = (size_t)wpb * B.c.S * 4;
+    cudaFuncSetAttribute((const void*)k_pack_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    u64 grid = (u64)grid_for((const void*)k_pack_count, kThreads, smem, L.sms);
+    grid = umin(grid, (ranges_cap + wpb - 1) / wpb);
+    k_pack_count<<<(unsigned)grid, kThreads, smem, L.stream>>>(B);
+  }
+  k_pack_scan<<<B.n, kCbThreads, 0, L.stream>>>(B);
+  {  // records (chunks that hold any)
+    const bool from_q = B.it[0].q != nullptr;
+    const u64 grid = umin((ranges_cap + wpb - 1) / wpb, (u64)L.sms * 8);
+    if (B.c.dtype == ROIX_F32) {
+      if (from_q) k_records<float, true><<<(unsigned)grid, kThreads, 0, L.stream>>>(B);
+      else k_records<float, false><<<(unsigned)grid, kThreads, 0, L.stream>>>(B);
+    } else {
+      if (from_q) k_records<unsigned short, true><<<(unsigned)grid, kThreads, 0, L.stream>>>(B);
+      else k_records<unsigned short, false><<<(unsigned)grid, kThreads, 0, L.stream>>>(B);
+    }
+  }
+  const size_t smem = ((size_t)B.c.C * kLMax / 64 + 2) * 8;  // the chunk's stream
+  auto run = [&](auto kernel) {
+    cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    u64 grid = (u64)grid_for((const void*)kernel, kThreads, smem, L.sms);
+    if (L.t.pack_blocks_per_sm) grid = umin(grid, (u64)L.t.pack_blocks_per_sm * L.sms);
+    if (grid > ranges_cap) grid = ranges_cap;
+    kernel<<<(unsigned)grid, kThreads, smem, L.stream>>>(B);
+  };
+  switch (B.c.C / kThreads) {
+    case 1: run(k_pack<1>); break;
+    case 2: run(k_pack<2>); break;
+    case 4: run(k_pack<4>); break;
+    case 8: run(k_pack<8>); break;
+    case 16: run(k_pack<16>); break;
+    case 32: run(k_pack<32>); break;
+    case 64: run(k_pack<64>); break;
+    default: break;  // rejected on the host
+  }
 }
 
 void launch_finalize(const Launch& L, const Batch& B) {

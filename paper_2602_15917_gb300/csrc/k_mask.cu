@@ -116,15 +116,16 @@ __device__ __forceinline__ void thr_segment_vec(const Desc& d, const TV* __restr
   if ((u32)lane < nw) T[r * d.W + (x0 >> 5) + lane] = mine;
 }
 
-// Flat form for rows that are not 16-byte aligned (nx * size % 16 != 0) of a
-// 16-byte aligned volume with nx >= 256: the volume is read as one flat array
-// in aligned 16-byte vectors, 1024 voxels per step of a warp, and turned into
-// flat words (bit b of flat word j = voxel 32 j + b, lane j holding word j);
-// each mask word of a row, whose 32 voxels start anywhere in the flat array,
-// is then a funnel shift of two flat words fetched by shuffles. A warp takes a
-// span of kFlatSpan voxels; the words starting in a step are formed once the
-// next step's first flat word is known.
-constexpr u32 kFlatSpan = 8192;
+// Flat form for a 16-byte aligned volume with nx >= 256 whose rows are not
+// 16-byte aligned or do not fill whole 1024-voxel segments: the volume is read
+// as one flat array in aligned 16-byte vectors, 1024 voxels per step of a
+// warp, and turned into flat words (bit b of flat word j = voxel 32 j + b,
+// lane j holding word j); each mask word of a row, whose 32 voxels start
+// anywhere in the flat array, is then a funnel shift of two flat words fetched
+// by shuffles. A warp's unit is one step of kFlatSpan voxels (independent
+// units keep many steps' loads in flight); the first flat word after the step
+// comes from a ballot over 32 more voxels.
+constexpr u32 kFlatSpan = 1024;
 
 template <typename TV>
 __device__ __forceinline__ u32 flat_words(const Desc& d, const TV* __restrict__ in, u64 a,
@@ -191,53 +192,52 @@ __device__ __forceinline__ u32 flat_words(const Desc& d, const TV* __restrict__ 
 
 // Mask words of the rows whose voxels x = 32 w .. start in flat step [a, a +
 // 1024): F = that step's flat words (lane j: word j), f32 = the next step's
-// word 0. r / rs: a row containing voxel a and its first flat index.
+// word 0; r / rel0: the row holding voxel a and its first voxel's position
+// relative to a (<= 0). Positions within the step are 32-bit (nx >= 256, so at
+// most five rows start words in a step).
 __device__ __forceinline__ void flat_emit(const Desc& d, u32* __restrict__ T, u64 a, u32 F,
-                                          u32 f32, u64 r, u64 rs, int lane) {
-  const u64 nx = d.nx, W = d.W;
-  const u64 lim = umin(a + 1024, d.rows * nx);  // word starts lie in [a, lim)
-  // count the words per row (at most 5 rows: nx >= 256)
-  u32 cnt[5];
-  u64 wlo[5];
-  u32 total = 0;
+                                          u32 f32, u64 r, int rel0, int lim, int lane) {
+  const int nx = (int)d.nx, W = (int)d.W;
+  int cnt[5], wlo[5];
+  int total = 0;
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
-    const u64 rk = r + k, sk = rs + (u64)k * nx;
-    cnt[k] = 0;
-    wlo[k] = 0;
-    if (rk < d.rows && sk < lim) {
-      const u64 lo = a > sk ? (a - sk + 31) >> 5 : 0;
-      const u64 hi = umin(W, (lim - sk + 31) >> 5);  // words with start < lim
-      if (hi > lo) {
-        cnt[k] = (u32)(hi - lo);
-        wlo[k] = lo;
-      }
+    const int rel = rel0 + k * nx;  // row r + k starts at a + rel
+    int lo = 0, hi = 0;
+    if (r + k < d.rows && rel < lim) {
+      lo = rel >= 0 ? 0 : (-rel + 31) >> 5;
+      hi = min(W, (lim - rel + 31) >> 5);  // words with start < lim
+      if (hi < lo) hi = lo;
     }
+    cnt[k] = hi - lo;
+    wlo[k] = lo;
     total += cnt[k];
   }
-  for (u32 o0 = 0; o0 < total; o0 += 32) {
-    const u32 o = o0 + lane;
-    u64 row = 0, w = 0;
-    bool have = false;
-    u32 acc = 0;
+  int pre[5];  // words of the rows before row r + k (constant indices: registers)
+  pre[0] = 0;
 #pragma unroll
-    for (int k = 0; k < 5; ++k) {
-      if (!have && o < acc + cnt[k]) {
-        row = r + k;
-        w = wlo[k] + (o - acc);
-        have = true;
+  for (int k = 1; k < 5; ++k) pre[k] = pre[k - 1] + cnt[k - 1];
+  for (int o0 = 0; o0 < total; o0 += 32) {
+    const int o = o0 + lane;
+    int k = 0, acc = 0, wl = wlo[0];
+#pragma unroll
+    for (int q = 1; q < 5; ++q)
+      if (o >= pre[q]) {
+        k = q;
+        acc = pre[q];
+        wl = wlo[q];
       }
-      acc += cnt[k];
-    }
-    const u64 s = have ? row * nx + 32 * w : a;
-    const u32 off = (u32)(s - a), j = off >> 5, sh = off & 31;
+    const bool have = o < total;
+    const int w = wl + (o - acc);
+    const int off = have ? rel0 + k * nx + 32 * w : 0;  // in [0, 1024)
+    const u32 j = (u32)off >> 5, sh = (u32)off & 31;
     const u32 lo = __shfl_sync(0xffffffffu, F, j & 31);
     u32 hi = __shfl_sync(0xffffffffu, F, (j + 1) & 31);
     if (j == 31) hi = f32;
     if (have) {
       u32 v = sh ? __funnelshift_r(lo, hi, sh) : lo;
-      v &= last_mask(d, w);
-      T[row * W + w] = v;
+      v &= last_mask(d, (u64)w);
+      T[(r + k) * d.W + w] = v;
     }
   }
 }
@@ -246,41 +246,31 @@ template <typename TV>
 __device__ __forceinline__ void thr_flat_span(const Desc& d, const TV* __restrict__ in,
                                               u32* __restrict__ T, u64 span, int lane) {
   const u64 N = d.rows * d.nx;
-  const u64 a0 = span * kFlatSpan;
-  const u64 a1 = umin(a0 + kFlatSpan, N);
-  u64 r = a0 / d.nx, rs = r * d.nx;  // row holding voxel a0
-  u32 F = flat_words<TV>(d, in, a0, lane);
-  for (u64 a = a0; a < a1; a += 1024) {
-    const u64 an = a + 1024;
-    // next step's flat words (the step after the span only for its word 0)
-    u32 Fn = 0;
-    if (an < N) {
-      if (an < a1) {
-        Fn = flat_words<TV>(d, in, an, lane);
-      } else {
-        const u64 x = an + lane;
-        bool p = false;
-        if (x < N) {
-          if constexpr (sizeof(TV) == 4) p = pass_f32(__ldg(in + x), d);
-          else p = pass_u16(__ldg(in + x), d);
-        }
-        Fn = __ballot_sync(0xffffffffu, p);
-      }
-    }
-    flat_emit(d, T, a, F, __shfl_sync(0xffffffffu, Fn, 0), r, rs, lane);
-    F = Fn;
-    while (rs + d.nx <= an && r + 1 < d.rows) {  // the row holding the next step's first voxel
-      rs += d.nx;
-      ++r;
-    }
+  const u64 a = span * kFlatSpan;
+  // the row holding voxel a: a / nx by a binary64 quotient (exact to within one
+  // for a < 2^52), then corrected
+  u64 r = (u64)((double)a / (double)d.nx);
+  while (r * d.nx > a) --r;
+  while ((r + 1) * d.nx <= a) ++r;
+  const int rel0 = (int)((long long)(r * d.nx) - (long long)a);
+  const int lim = (int)umin(1024, N - a);
+  const u32 F = flat_words<TV>(d, in, a, lane);
+  // the first flat word after the step: a ballot over its 32 voxels
+  const u64 x = a + 1024 + lane;
+  bool p = false;
+  if (x < N) {
+    if constexpr (sizeof(TV) == 4) p = pass_f32(__ldg(in + x), d);
+    else p = pass_u16(__ldg(in + x), d);
   }
+  const u32 f32 = __ballot_sync(0xffffffffu, p);
+  flat_emit(d, T, a, F, f32, r, rel0, lim, lane);
 }
 
 // Warps take the batch's work units in order (all items): 1024-voxel row
-// segments of the row-form items, or kFlatSpan-voxel spans of the flat-form
+// segments of the row-form items, or kFlatSpan-voxel steps of the flat-form
 // items (FLAT; a launch of its own, so that each form keeps its registers).
 template <typename TV, bool FLAT>
-__global__ void __launch_bounds__(kThreads) k_threshold(const __grid_constant__ Batch B) {
+__global__ void __launch_bounds__(kThreads, FLAT ? 4 : 1) k_threshold(const __grid_constant__ Batch B) {
   const int lane = threadIdx.x & 31;
   const u64 warp = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
@@ -421,17 +411,18 @@ struct FrontSmem {
   u32 scratch[40];
 };
 
-template <typename TV>
-__global__ void __launch_bounds__(kThreads, 4) k_front(const __grid_constant__ Batch B) {
+// The compaction runs in three launches, none of whose blocks waits on
+// another: k_front_count forms the retained words of each tile of rows
+// (dilated from T, stored to the item's D when dilating), the rows' boundary
+// counts (into the container), each row's offsets within its tile and the
+// tile's totals; k_front_scan turns the tiles' totals into offsets;
+// k_front_write has warps take rows and write their boundaries and values.
+__global__ void __launch_bounds__(kThreads, 4) k_front_count(const __grid_constant__ Batch B) {
   extern __shared__ u32 smem_dyn[];
   __shared__ FrontSmem sh;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const u32 below = (1u << lane) - 1u;
   const int dilate = B.c.dilate;
   const u64 total_tiles = B.ftile0[B.n];
-  u32 kmin = 0xffffffffu, kmax = 0u;
-  u32 cur = 0xffffffffu;  // item whose range the block accumulates
-
   while (true) {
     if (threadIdx.x == 0) sh.tile = atomicAdd(&B.ctr[0], 1u);
     __syncthreads();
@@ -439,31 +430,20 @@ __global__ void __launch_bounds__(kThreads, 4) k_front(const __grid_constant__ B
     if (gt >= total_tiles) break;
     const u32 item = find_item(B.ftile0, B.n, gt);
     const Item& I = B.it[item];
-    if (item != cur) {  // flush the value range of the previous item
-      flush_range(cur == 0xffffffffu ? nullptr : B.it[cur].rst, kmin, kmax, lane);
-      cur = item;
-    }
     const Desc d = desc_of(B, I);
     const u64 t = gt - B.ftile0[item];
-    const u64 ntiles = I.ftiles;
     const u32 rpt = I.rpt;
-    const TV* __restrict__ in = (const TV*)I.in;
     const u32* __restrict__ T = I.T;
-    TV* __restrict__ P = (TV*)I.P;
     uint16_t* __restrict__ counts = I.counts;
     const u64 counts_cap = I.counts_cap;
-    uint16_t* __restrict__ bounds = I.bounds;
-    const u64 bounds_cap = I.bounds_cap;
-    u64* sizes_out = I.sizes;
-    const LookBack<2> lb = I.lbf;
     const u32 zhalo = I.zhalo;  // z-slab: T continues across the slab's z borders
     const u32 W = (u32)d.W;
     const FastDiv divW(W);
     u32* Dw = smem_dyn;                                 // [rpt * W]
-    u32* rowcnt = Dw + (u64)rpt * W;                    // [rpt]
-    u32* bflag = rowcnt + rpt;                          // [rpt + 2]
-    uint16_t* blist = (uint16_t*)(bflag + rpt + 2);     // [8][kListCap] row boundary lists
-    u32* U = (u32*)(blist + (kThreads / 32) * kListCap);  // [rpt + 2][W] when dilating
+    u32* rowcnt = Dw + (u64)rpt * W;                    // [rpt] boundaries per row
+    u32* rown = rowcnt + rpt;                           // [rpt] retained voxels per row
+    u32* bflag = rown + rpt;                            // [rpt + 2]
+    u32* U = bflag + rpt + 2;                           // [rpt + 2][W] when dilating
     const bool end_extra = (d.nx & 31) == 0;  // boundary at x = nx lives past the last word
     const u64 zstride = d.ny * (u64)W;
     const u64 r0 = t * rpt;
@@ -538,7 +518,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_front(const __grid_constant__ B
     {
       u32 cn = 0, cb = 0;
       if (!any)
-        for (u32 lr = rbeg + lane; lr < rend; lr += 32) rowcnt[lr] = 0;
+        for (u32 lr = rbeg + lane; lr < rend; lr += 32) {
+          rowcnt[lr] = 0;
+          rown[lr] = 0;
+        }
       for (u32 lr = any ? rbeg : rend; lr < rend; ++lr) {
         const u32* drow = Dw + lr * W;
         u32 rn = 0, rb = 0;
@@ -551,7 +534,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_front(const __grid_constant__ B
         }
         rn = warp_sum(rn);
         rb = warp_sum(rb);
-        if (lane == 0) rowcnt[lr] = rb;
+        if (lane == 0) {
+          rowcnt[lr] = rb;
+          rown[lr] = rn;
+        }
         cn += rn;
         cb += rb;
       }
@@ -571,38 +557,123 @@ __global__ void __launch_bounds__(kThreads, 4) k_front(const __grid_constant__ B
         sh.wn[lane] = ia - a;
         sh.wb[lane] = ib - b;
       }
-      u64 mine[2] = {tn, tb}, excl[2];
-      lookback_warp<2>(lb, t, mine, excl, B.status);
       if (lane == 0) {
-        sh.base_n = excl[0];
-        sh.base_nb = excl[1];
-        if (t == ntiles - 1) {
-          sizes_out[0] = excl[0] + tn;
-          sizes_out[1] = excl[1] + tb;
-        }
+        I.ftn[t] = (u32)tn;
+        I.ftb[t] = (u32)tb;
       }
     }
     __syncthreads();
-
-    // ---- per row: boundaries (x positions where D turns on / off), then the
-    // values of each run [x_start, x_end) copied with coalesced loads/stores
+    // each row's offsets within the tile (a warp walks its own rows in order)
     {
-      u64 on = sh.base_n + sh.wn[warp];
-      u64 ob = sh.base_nb + sh.wb[warp];
-      uint16_t* lst = blist + warp * kListCap;
-      for (u32 lr = any ? rbeg : rend; lr < rend; ++lr) {
-        const u32 nbr = rowcnt[lr];
-        if (nbr == 0) continue;  // no boundary: nothing retained in this row
-        const u32* drow = Dw + lr * W;
-        const TV* irow = in + (r0 + lr) * d.nx;
+      u32 on = sh.wn[warp], ob = sh.wb[warp];
+      for (u32 lr = rbeg; lr < rend; ++lr) {
+        if (lane == 0) {
+          I.rno[r0 + lr] = on;
+          I.rbo[r0 + lr] = ob;
+        }
+        on += rown[lr];
+        ob += rowcnt[lr];
+      }
+    }
+    // the rows' boundary counts into the container, the retained words to D
+    for (u32 lr = threadIdx.x; lr < nrows; lr += blockDim.x) {
+      const u64 r = r0 + lr;
+      if (r < counts_cap) counts[r] = (uint16_t)rowcnt[lr];
+    }
+    if (dilate)  // (Dw holds nothing when the band is empty)
+      for (u32 i = threadIdx.x; i < nw; i += blockDim.x) I.D[r0 * W + i] = any ? Dw[i] : 0u;
+    __syncthreads();
+  }
+}
+
+// One block per item: exclusive scans of the tiles' retained voxels and
+// boundaries; the totals are the item's n and nb.
+__global__ void __launch_bounds__(1024) k_front_scan(const __grid_constant__ Batch B) {
+  __shared__ u64 scratch[40];
+  const Item& I = B.it[blockIdx.x];
+  u64 cn, cb;
+  block_scan2(I.ftn, I.ftb, I.ftiles, I.ftno, I.ftbo, scratch, &cn, &cb);
+  if (threadIdx.x == 0) {
+    I.sizes[0] = cn;
+    I.sizes[1] = cb;
+  }
+}
+
+// Warps take kRowsPerTicket consecutive rows of the batch (all items' rows in
+// order) per ticket: lane j looks up row j's item, boundary count and offsets (the
+// tile's offset plus the row's offset in its tile); then the warp walks the
+// rows that retain anything: the boundaries (x positions where D turns on or
+// off) are written in order, and the values of each run [x_start, x_end) are
+// copied with coalesced loads and stores while the value range is gathered.
+constexpr u32 kRowsPerTicket = 8;
+
+template <typename TV>
+__global__ void __launch_bounds__(kThreads, 4) k_front_write(const __grid_constant__ Batch B) {
+  __shared__ uint16_t blist_all[kThreads / 32][kListCap];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const u32 below = (1u << lane) - 1u;
+  uint16_t* lst = blist_all[warp];
+  const u64 total_rows = B.row0[B.n];
+  u32 kmin = 0xffffffffu, kmax = 0u;
+  u32 cur = 0xffffffffu;  // item whose range the warp accumulates
+  while (true) {
+    u64 g0 = 0;
+    if (lane == 0) g0 = atomicAdd(&B.ctr[4], kRowsPerTicket);
+    g0 = __shfl_sync(0xffffffffu, g0, 0);
+    if (g0 >= total_rows) break;
+    // lane j < kRowsPerTicket: row g0 + j's item, boundary count, offsets
+    const u64 g = lane < (int)kRowsPerTicket ? g0 + lane : total_rows;
+    u32 my_item = 0, my_nbr = 0;
+    u64 my_on = 0, my_ob = 0;
+    if (g < total_rows) {
+      my_item = find_item(B.row0, B.n, g);
+      const Item& I = B.it[my_item];
+      const u64 r = g - B.row0[my_item];
+      const u64 t = r / I.rpt;
+      my_nbr = r < I.counts_cap ? (u32)I.counts[r] : 0xffffffffu;
+      my_on = I.ftno[t] + I.rno[r];
+      my_ob = I.ftbo[t] + I.rbo[r];
+    }
+    u32 todo = __ballot_sync(0xffffffffu, g < total_rows && my_nbr != 0u);
+    while (todo) {
+      const int j = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const u32 item = __shfl_sync(0xffffffffu, my_item, j);
+      u32 nbr = __shfl_sync(0xffffffffu, my_nbr, j);
+      u64 on = __shfl_sync(0xffffffffu, my_on, j);
+      const u64 ob = __shfl_sync(0xffffffffu, my_ob, j);
+      const Item& I = B.it[item];
+      if (item != cur) {  // flush the value range of the previous item
+        flush_range(cur == 0xffffffffu ? nullptr : B.it[cur].rst, kmin, kmax, lane);
+        cur = item;
+      }
+      const Desc d = desc_of(B, I);
+      const u64 r = g0 + j - B.row0[item];
+      const u32 W = (u32)d.W;
+      const bool end_extra = (d.nx & 31) == 0;
+      const u32* drow = (B.c.dilate ? I.D : I.T) + r * W;
+      const TV* irow = (const TV*)I.in + r * d.nx;
+      TV* __restrict__ P = (TV*)I.P;
+      uint16_t* __restrict__ bounds = I.bounds;
+      const u64 bounds_cap = I.bounds_cap;
+      if (nbr == 0xffffffffu) {  // container too small for the counts: count again
+        u32 rb = 0;
+        for (u32 w = lane; w < W; w += 32) {
+          const u32 dv = __ldg(drow + w) & last_mask(d, w);
+          const u32 pv = w ? __ldg(drow + w - 1) & last_mask(d, w - 1) : 0u;
+          rb += __popc(dv ^ ((dv << 1) | (pv >> 31))) + ((end_extra && w == W - 1) ? (dv >> 31) : 0u);
+        }
+        nbr = warp_sum(rb);
+        if (nbr == 0) continue;
+      }
         const bool fast = nbr <= kListCap;
         u32 bo = 0;
         for (u32 w0 = 0; w0 < W; w0 += 32) {
           const u32 w = w0 + lane;
           u32 ev = 0u, ex = 0u;
           if (w < W) {
-            const u32 dv = drow[w];
-            const u32 pv = w ? drow[w - 1] : 0u;
+            const u32 dv = __ldg(drow + w) & last_mask(d, w);
+            const u32 pv = w ? __ldg(drow + w - 1) & last_mask(d, w - 1) : 0u;
             ev = dv ^ ((dv << 1) | (pv >> 31));
             ex = (end_extra && w == W - 1) ? (dv >> 31) : 0u;
           }
@@ -636,15 +707,15 @@ __global__ void __launch_bounds__(kThreads, 4) k_front(const __grid_constant__ B
               on += len;
               continue;
             }
-            for (u32 e0 = 0; e0 < len; e0 += 128) {
-              TV v[4];
+            for (u32 e0 = 0; e0 < len; e0 += 256) {
+              TV v[8];
 #pragma unroll
-              for (int j = 0; j < 4; ++j) {
+              for (int j = 0; j < 8; ++j) {
                 const u32 e = e0 + j * 32 + lane;
                 v[j] = e < len ? __ldg(src + e) : TV(0);
               }
 #pragma unroll
-              for (int j = 0; j < 4; ++j) {
+              for (int j = 0; j < 8; ++j) {
                 const u32 e = e0 + j * 32 + lane;
                 if (e < len) {
                   dst[e] = v[j];
@@ -666,7 +737,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_front(const __grid_constant__ B
         } else {
           // many short runs: lanes take the bits of one word at a time
           for (u32 w0 = 0; w0 < W; w0 += 32) {
-            const u32 dv_l = w0 + lane < W ? drow[w0 + lane] : 0u;
+            const u32 dv_l = w0 + lane < W ? __ldg(drow + w0 + lane) & last_mask(d, w0 + lane) : 0u;
             const u32 pn = __popc(dv_l);
             const u32 sn = warp_incl_scan(pn) - pn;
             u32 nz = __ballot_sync(0xffffffffu, dv_l != 0u);
@@ -693,16 +764,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_front(const __grid_constant__ B
             on += __shfl_sync(0xffffffffu, sn + pn, 31);
           }
         }
-        ob += nbr;
-        __syncwarp();
-      }
+      __syncwarp();
     }
-    // ---- per-row boundary counts
-    for (u32 lr = threadIdx.x; lr < nrows; lr += blockDim.x) {
-      const u64 r = r0 + lr;
-      if (r < counts_cap) counts[r] = (uint16_t)rowcnt[lr];
-    }
-    __syncthreads();
   }
   flush_range(cur == 0xffffffffu ? nullptr : B.it[cur].rst, kmin, kmax, lane);
 }
@@ -726,15 +789,17 @@ void launch_threshold(const Launch& L, const Batch& B) {
     kernel<<<(unsigned)blocks, kThreads, 0, L.stream>>>(B);
   };
   const u64 segs = B.seg0[B.n], spans = B.fseg0[B.n];
+  const u64 rb = L.t.thr_blocks_per_sm ? L.t.thr_blocks_per_sm : 8;
+  const u64 fb = L.t.flat_blocks_per_sm ? L.t.flat_blocks_per_sm : 4;
   if (B.c.dtype == ROIX_F32) {
-    run(k_threshold<float, false>, segs, 8);
-    run(k_threshold<float, true>, spans, 4);
+    run(k_threshold<float, false>, segs, rb);
+    run(k_threshold<float, true>, spans, fb);
   } else if (B.c.dtype == ROIX_U16) {
-    run(k_threshold<unsigned short, false>, segs, 8);
-    run(k_threshold<unsigned short, true>, spans, 4);
+    run(k_threshold<unsigned short, false>, segs, rb);
+    run(k_threshold<unsigned short, true>, spans, fb);
   } else {
-    run(k_threshold<unsigned char, false>, segs, 8);
-    run(k_threshold<unsigned char, true>, spans, 4);
+    run(k_threshold<unsigned char, false>, segs, rb);
+    run(k_threshold<unsigned char, true>, spans, fb);
   }
 }
 
@@ -755,8 +820,7 @@ void launch_dilate(const Launch& L, const Desc& d, const u32* T, u32* D, u64* po
 }
 
 size_t front_smem(u32 rpt, u64 W, int dilate) {
-  return (size_t)rpt * W * 4 + (size_t)rpt * 8 + 8 + (size_t)(kThreads / 32) * kListCap * 2 +
-         (dilate ? (size_t)(rpt + 2) * W * 4 : 0);
+  return (size_t)rpt * W * 4 + (size_t)rpt * 12 + 8 + (dilate ? (size_t)(rpt + 2) * W * 4 : 0);
 }
 
 void launch_front(const Launch& L, const Batch& B) {
@@ -767,18 +831,23 @@ void launch_front(const Launch& L, const Batch& B) {
     const size_t s = front_smem(B.it[i].rpt, B.it[i].W, B.c.dilate);
     if (s > smem) smem = s;
   }
-  const void* fn = B.c.dtype == ROIX_F32   ? (const void*)k_front<float>
-                   : B.c.dtype == ROIX_U16 ? (const void*)k_front<unsigned short>
-                                           : (const void*)k_front<unsigned char>;
-  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  u64 grid = (u64)occupancy_grid(fn, kThreads, smem, L.sms);
+  cudaFuncSetAttribute((const void*)k_front_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem);
+  u64 grid = (u64)occupancy_grid((const void*)k_front_count, kThreads, smem, L.sms);
   if (grid > tiles) grid = tiles;
-  if (B.c.dtype == ROIX_F32)
-    k_front<float><<<(unsigned)grid, kThreads, smem, L.stream>>>(B);
-  else if (B.c.dtype == ROIX_U16)
-    k_front<unsigned short><<<(unsigned)grid, kThreads, smem, L.stream>>>(B);
-  else
-    k_front<unsigned char><<<(unsigned)grid, kThreads, smem, L.stream>>>(B);
+  k_front_count<<<(unsigned)grid, kThreads, smem, L.stream>>>(B);
+  k_front_scan<<<B.n, 1024, 0, L.stream>>>(B);
+  auto run = [&](auto kernel) {
+    u64 g = (u64)occupancy_grid((const void*)kernel, kThreads, 0, L.sms);
+    const u64 need = (B.row0[B.n] + kRowsPerTicket * (kThreads / 32) - 1) /
+                     (kRowsPerTicket * (kThreads / 32));
+    if (g > need) g = need;
+    if (g < 1) g = 1;
+    kernel<<<(unsigned)g, kThreads, 0, L.stream>>>(B);
+  };
+  if (B.c.dtype == ROIX_F32) run(k_front_write<float>);
+  else if (B.c.dtype == ROIX_U16) run(k_front_write<unsigned short>);
+  else run(k_front_write<unsigned char>);
 }
 
 }  // namespace roix

@@ -122,6 +122,7 @@ roix_status roix::make_desc(roix_ctx* ctx, roix_dtype dtype, roix_dims dims, con
   d->W = (dims.nx + 31) / 32;
   d->N = dims.nx * dims.ny * dims.nz;
   d->dtype = dtype;
+  d->front_words = ctx ? ctx->tune.front_words : 2048;
   if (roi) {
     if (roi->cmp != 0 && roi->cmp != 1) return fail(ctx, ROIX_EINVAL, "roi.cmp must be 0 or 1");
     if (roi->keep != 0 && roi->keep != 1) return fail(ctx, ROIX_EINVAL, "roi.keep must be 0 or 1");
@@ -182,7 +183,7 @@ bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 size_t dtype_bytes(int dt) { return dt == ROIX_F32 ? 4 : dt == ROIX_U16 ? 2 : 1; }
 
 u32 front_rows_per_tile(const Desc& d) {
-  const u64 target_words = 2048;
+  const u64 target_words = d.front_words ? d.front_words : 2048;
   u64 rpt = d.W ? target_words / d.W : 1;
   if (rpt < 1) rpt = 1;
   if (rpt > d.rows) rpt = d.rows ? d.rows : 1;
@@ -195,8 +196,8 @@ u32 front_rows_per_tile(const Desc& d) {
 // every item), then every item's data (look-back values, mask, pixel section,
 // symbols, records, code tables).
 struct ItemPlan {
-  size_t ff, qf, pf, hist;  // zeroed
-  size_t fa, qa, pa, T, P, sym, rk, rv, lens, codes;
+  size_t crec, hist;  // zeroed
+  size_t ftn, ftb, ftno, ftbo, rno, rbo, Dm, cw, cwoff, crecoff, rbits, T, P, sym, rk, rv, lens, codes;
   // largest-component scratch (keep = 1): zeroed flags and counters, then data
   size_t cf, cvars, ca, crr, cro, cxs, cxe, cpar, csize, T2;
   u64 ctiles;
@@ -207,7 +208,7 @@ struct ItemPlan {
 struct BatchPlan {
   size_t zero_begin = 0, zero_end = 0, total = 0;
   std::vector<ItemPlan> items;
-  u64 qtiles = 0, pranges = 0;
+  u64 qtiles = 0, pranges = 0;  // symbol segments, pack chunks
 };
 
 BatchPlan plan_batch(const Desc& c, const roix_dims* dims, const u64* n_caps, const u64* caps,
@@ -233,9 +234,7 @@ BatchPlan plan_batch(const Desc& c, const roix_dims* dims, const u64* n_caps, co
     p.pchunks = c.C ? (p.n_cap + c.C - 1) / c.C : 0;
     p.pranges = (p.pchunks + kPackRange - 1) / kPackRange;
     p.rec_cap = umin(p.n_cap, caps[i] / 12 + 1);
-    p.ff = a.take(4 * (p.ftiles + 1));
-    p.qf = a.take(4 * (p.qtiles + 1));
-    p.pf = a.take(4 * (p.pranges + 1));
+    p.crec = a.take(4 * (p.pchunks + 1));
     p.hist = a.take(8 * (size_t)c.S);
     if (c.keep) {
       const u64 rows = dims[i].ny * dims[i].nz;
@@ -250,9 +249,17 @@ BatchPlan plan_batch(const Desc& c, const roix_dims* dims, const u64* n_caps, co
   for (u32 i = 0; i < n; ++i) {
     ItemPlan& p = bp.items[i];
     const u64 rows = dims[i].ny * dims[i].nz, W = (dims[i].nx + 31) / 32;
-    p.fa = a.take(8 * 4 * (p.ftiles + 1));
-    p.qa = a.take(8 * 2 * (p.qtiles + 1));
-    p.pa = a.take(8 * 2 * (p.pranges + 1));
+    p.ftn = a.take(4 * (p.ftiles + 1));
+    p.ftb = a.take(4 * (p.ftiles + 1));
+    p.ftno = a.take(8 * (p.ftiles + 1));
+    p.ftbo = a.take(8 * (p.ftiles + 1));
+    p.Dm = c.dilate ? a.take(4 * rows * W + 16) : 0;
+    p.rno = a.take(4 * rows + 16);
+    p.rbo = a.take(4 * rows + 16);
+    p.cw = a.take(4 * (p.pchunks + 1));
+    p.cwoff = a.take(8 * (p.pchunks + 1));
+    p.crecoff = a.take(8 * (p.pchunks + 1));
+    p.rbits = a.take(4 * (p.n_cap / 32 + 2));
     p.T = need_T ? a.take(4 * rows * W + 16) : 0;
     p.P = need_P ? a.take(esz * p.n_cap + 16) : 0;
     p.sym = a.take(2 * p.n_cap + 16);
@@ -305,7 +312,7 @@ void fill_batch(Batch& B, const Desc& c, const BatchPlan& bp, const roix_dims* d
   State* st = (State*)ws;
   B.status = &st[0].status;
   B.ctr = &st[first].ctr_front;
-  u64 seg = 0, ft = 0;
+  u64 seg = 0, ft = 0, rw = 0;
   for (u32 i = 0; i < n; ++i) {
     const ItemPlan& p = bp.items[first + i];
     Item& I = B.it[i];
@@ -327,28 +334,40 @@ void fill_batch(Batch& B, const Desc& c, const BatchPlan& bp, const roix_dims* d
     I.lens = (uint8_t*)(ws + p.lens);
     I.codes = (u32*)(ws + p.codes);
     I.sizes = &I.st->n;
-    I.lbf = lb_at<2>(ws, p.ff, p.fa, p.ftiles);
-    I.lbq = lb_at<1>(ws, p.qf, p.qa, p.qtiles);
-    I.lbp = lb_at<1>(ws, p.pf, p.pa, p.pranges);
+    I.ftn = (u32*)(ws + p.ftn);
+    I.ftb = (u32*)(ws + p.ftb);
+    I.ftno = (u64*)(ws + p.ftno);
+    I.ftbo = (u64*)(ws + p.ftbo);
+    I.D = p.Dm ? (u32*)(ws + p.Dm) : nullptr;
+    I.rno = (u32*)(ws + p.rno);
+    I.rbo = (u32*)(ws + p.rbo);
+    I.crec = (u32*)(ws + p.crec);
+    I.cw = (u32*)(ws + p.cw);
+    I.cwoff = (u64*)(ws + p.cwoff);
+    I.crecoff = (u64*)(ws + p.crecoff);
+    I.rbits = (u32*)(ws + p.rbits);
     I.rpt = p.rpt;
     I.ftiles = p.ftiles;
     B.seg0[i] = seg;
     B.ftile0[i] = ft;
+    B.row0[i] = rw;
     seg += I.rows * ((I.nx + 1023) / 1024);
     ft += p.ftiles;
+    rw += I.rows;
   }
   B.seg0[n] = seg;
   B.ftile0[n] = ft;
+  B.row0[n] = rw;
 }
 
 }  // namespace
 
 // Binarisation work units: 1024-voxel row segments when the rows are 16-byte
 // aligned and fill whole segments (nx a multiple of 1024) or are short (nx <
-// 256); kFlatSpan-voxel spans of the flat array for any other 16-byte aligned
+// 256); kFlatSpan-voxel steps of the flat array for any other 16-byte aligned
 // volume.
 void roix::set_threshold_units(Batch& B) {
-  constexpr u64 kFlatSpanHost = 8192;
+  constexpr u64 kFlatSpanHost = 1024;
   u64 seg = 0, fseg = 0;
   for (u32 i = 0; i < B.n; ++i) {
     Item& I = B.it[i];
@@ -572,7 +591,7 @@ roix_status roix_extract_roi(roix_ctx* ctx, const void* in, roix_dtype dtype, ro
   BatchPlan bp = plan_batch(dp, &dims, &ncap, &cap, 1, true, false);
   if ((s = ensure_ws(ctx, bp.total))) return s;
   cudaStream_t cs = (cudaStream_t)stream;
-  Launch L{cs, ctx->sms};
+  Launch L{cs, ctx->sms, ctx->tune};
   u32* T = (u32*)(ctx->ws + bp.items[0].T);
   launch_init(L, (State*)ctx->ws, 1, ctx->ws + bp.zero_begin, bp.zero_end - bp.zero_begin);
   cudaMemsetAsync(popcount_dev, 0, 8, cs);
@@ -608,7 +627,7 @@ roix_status roix_compact(roix_ctx* ctx, const void* in, roix_dtype dtype, roix_d
   BatchPlan bp = plan_batch(d, &dims, &ncap, &cap, 1, false, false);
   if ((s = ensure_ws(ctx, bp.total))) return s;
   cudaStream_t cs = (cudaStream_t)stream;
-  Launch L{cs, ctx->sms};
+  Launch L{cs, ctx->sms, ctx->tune};
   static thread_local Batch B;
   fill_batch(B, d, bp, &dims, ctx->ws, 1);
   Item& I = B.it[0];
@@ -649,7 +668,7 @@ roix_status roix_quantize(roix_ctx* ctx, const void* pixels, roix_dtype dtype, u
   const size_t st_off = a.take(kStateBytes);
   if ((s = ensure_ws(ctx, a.take(0)))) return s;
   cudaStream_t cs = (cudaStream_t)stream;
-  Launch L{cs, ctx->sms};
+  Launch L{cs, ctx->sms, ctx->tune};
   State* st = (State*)(ctx->ws + st_off);
   launch_init(L, st, 1, nullptr, 0);
   launch_quantize_stage(L, d, pixels, n_cap, (const u64*)n_dev, q_out, outlier_bits_out,
@@ -679,7 +698,7 @@ roix_status roix_encode(roix_ctx* ctx, const int32_t* q, const uint32_t* outlier
   BatchPlan bp = plan_batch(d, &dims, &ncap64, &cap64, 1, false, false);
   if ((s = ensure_ws(ctx, bp.total))) return s;
   cudaStream_t cs = (cudaStream_t)stream;
-  Launch L{cs, ctx->sms};
+  Launch L{cs, ctx->sms, ctx->tune};
   static thread_local Batch B;
   fill_batch(B, d, bp, &dims, ctx->ws, 1);
   Item& I = B.it[0];
@@ -719,7 +738,7 @@ roix_status enqueue_group(roix_ctx* ctx, const Desc& c, const roix_item* items, 
   BatchPlan bp = plan_batch(c, dims.data(), ncaps.data(), caps.data(), n, true, true);
   roix_status s = ensure_ws(ctx, bp.total);
   if (s) return s;
-  Launch L{cs, ctx->sms};
+  Launch L{cs, ctx->sms, ctx->tune};
   static thread_local Batch B;
   fill_batch(B, c, bp, dims.data(), ctx->ws, n);
   for (u32 i = 0; i < n; ++i) {
@@ -910,7 +929,7 @@ roix_status roix_compress_slabs(roix_ctx* ctx, const void* in, roix_dtype dtype,
   const SlabPlan sp = plan_slabs(d, slab_z, caps, 0);
   if ((s = ensure_ws(ctx, sp.total))) return s;
   cudaStream_t cs = (cudaStream_t)stream;
-  Launch L{cs, ctx->sms};
+  Launch L{cs, ctx->sms, ctx->tune};
   char* ws = ctx->ws;
   State* st = (State*)ws;
   u32* T = (u32*)(ws + sp.T_off);
@@ -996,7 +1015,7 @@ roix_status roix_decode(roix_ctx* ctx, const void* in, uint64_t size, void* out,
   const size_t rv = a.take(8 * (d.rows + 1));
   if ((s = ensure_ws(ctx, a.take(0)))) return s;
   cudaStream_t cs = (cudaStream_t)stream;
-  Launch L{cs, ctx->sms};
+  Launch L{cs, ctx->sms, ctx->tune};
   char* ws = ctx->ws;
   State* st = (State*)(ws + st_off);
   launch_init(L, st, 1, ws + zb, ze - zb);
@@ -1040,7 +1059,7 @@ roix_status roix_normalize8(roix_ctx* ctx, const void* in, roix_dtype dtype, roi
   const size_t key = a.take(16);
   if ((s = ensure_ws(ctx, a.take(0)))) return s;
   cudaStream_t cs = (cudaStream_t)stream;
-  Launch L{cs, ctx->sms};
+  Launch L{cs, ctx->sms, ctx->tune};
   cudaMemsetAsync(ctx->ws + key, 0, 4, cs);
   if (d.N == 0) {
     if (imax_dev) cudaMemsetAsync(imax_dev, 0, 8, cs);
@@ -1091,7 +1110,7 @@ roix_status roix_greedy_quantize_batch(roix_ctx* ctx, uint32_t n, const roix_gre
   roix_status s;
   if ((s = ensure_ws(ctx, a.take(0)))) return s;
   cudaStream_t cs = (cudaStream_t)stream;
-  Launch L{cs, ctx->sms};
+  Launch L{cs, ctx->sms, ctx->tune};
   static thread_local GreedyBatch B;
   const double ef = std::floor(eabs);
   for (u32 k0 = 0; k0 < n; k0 += kGreedyMaxItems) {
@@ -1152,7 +1171,7 @@ roix_status roix_roi_quality(roix_ctx* ctx, const uint32_t* pred_mask, const uin
   ar.take(kStateBytes);
   const size_t off = ar.take(roi_quality_ws_bytes(dims.nx, dims.ny, dims.nz, distances));
   if ((s = ensure_ws(ctx, ar.take(0)))) return s;
-  Launch L{(cudaStream_t)stream, ctx->sms};
+  Launch L{(cudaStream_t)stream, ctx->sms, ctx->tune};
   launch_roi_quality(L, pred_mask, truth_mask, dims.nx, dims.ny, dims.nz, distances,
                      ctx->ws + off, out_dev);
   cudaError_t e = cudaGetLastError();
@@ -1175,7 +1194,7 @@ roix_status roix_ssim(roix_ctx* ctx, const void* x, const void* y, roix_dtype dt
   ar.take(kStateBytes);
   const size_t off = ar.take(64);
   if ((s = ensure_ws(ctx, ar.take(0)))) return s;
-  Launch L{(cudaStream_t)stream, ctx->sms};
+  Launch L{(cudaStream_t)stream, ctx->sms, ctx->tune};
   launch_ssim(L, dtype, x, y, dims.nx, dims.ny, dims.nz, data_range, ctx->ws + off, ssim_dev);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? ROIX_OK : cuda_fail(ctx, e, "ssim launch");
@@ -1216,7 +1235,7 @@ roix_status roix_extract_roi_paper(roix_ctx* ctx, const uint8_t* img, roix_dims 
   const size_t sz = a.take(8 * maxr + 16);
   if ((s = ensure_ws(ctx, a.take(0)))) return s;
   cudaStream_t cs = (cudaStream_t)stream;
-  Launch L{cs, ctx->sms};
+  Launch L{cs, ctx->sms, ctx->tune};
   State* st = (State*)(ctx->ws + st_off);
   char* ws = ctx->ws;
   cudaMemsetAsync(popcount_dev, 0, 8, cs);

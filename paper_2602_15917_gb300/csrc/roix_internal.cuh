@@ -199,6 +199,51 @@ __device__ T block_excl_scan(T v, T* scratch, T* total) {
   return out;
 }
 
+// Exclusive scans of two count arrays a[0..n), b[0..n) into ao, bo by one
+// block: thread i sums its contiguous range of ceil(n / blockDim) entries
+// (eight loads in flight), one block scan combines the sums, each thread
+// writes its range. Returns the totals (in every thread). `scratch` holds 33
+// u64. Writers and later readers of ao / bo in the same block need a barrier.
+__device__ __forceinline__ void block_scan2(const u32* __restrict__ a, const u32* __restrict__ b,
+                                            u64 n, u64* __restrict__ ao, u64* __restrict__ bo,
+                                            u64* scratch, u64* ta, u64* tb) {
+  const u64 per = (n + blockDim.x - 1) / blockDim.x;
+  const u64 lo = umin(n, (u64)threadIdx.x * per), hi = umin(n, lo + per);
+  u64 sa = 0, sb = 0;
+  for (u64 i0 = lo; i0 < hi; i0 += 8) {
+    u32 va[8], vb[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      va[k] = i0 + k < hi ? __ldg(a + i0 + k) : 0u;
+      vb[k] = i0 + k < hi ? __ldg(b + i0 + k) : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      sa += va[k];
+      sb += vb[k];
+    }
+  }
+  u64 ea = block_excl_scan<u64>(sa, scratch, ta);
+  u64 eb = block_excl_scan<u64>(sb, scratch, tb);
+  for (u64 i0 = lo; i0 < hi; i0 += 8) {
+    u32 va[8], vb[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      va[k] = i0 + k < hi ? __ldg(a + i0 + k) : 0u;
+      vb[k] = i0 + k < hi ? __ldg(b + i0 + k) : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (i0 + k < hi) {
+        ao[i0 + k] = ea;
+        bo[i0 + k] = eb;
+      }
+      ea += va[k];
+      eb += vb[k];
+    }
+  }
+}
+
 // ------------------------------------------------------------ fast division
 // Division of 32-bit numerators by an invariant divisor with a multiply-high
 // and shifts (Granlund & Montgomery 1994, round-up method).
@@ -264,6 +309,7 @@ __host__ __device__ __forceinline__ Layout make_layout(u64 S, u64 rows, u64 nb, 
 struct State {
   u32 status;                          // context status word (state 0 only)
   u32 ctr_front, ctr_quant, ctr_pack;  // dynamic tile counters (state 0: batch tickets)
+  u32 ctr_write, ctr_front2;           // pack-write and compaction-write tickets
   u64 n, nb, nout, nwords;             // sizes found on the device
   u32 vmin_key, vmax_key;              // range of retained finite values
   u32 cap_flag, pad0;
@@ -284,6 +330,7 @@ struct Desc {
   int eb_mode;
   double eb_value;
   u32 R, S, C;
+  u32 front_words;             // compaction tile size (mask words), from the tuning
 };
 
 // ------------------------------------------------------------------ batches
@@ -322,9 +369,18 @@ struct Item {
   const uint16_t* counts_src;          // staged geometry to copy into the container
   const uint16_t* bounds_src;
   u64* sizes;                          // [n, nb]
-  LookBack<2> lbf;                     // front tiles
-  LookBack<1> lbq;                     // symbol tiles
-  LookBack<1> lbp;                     // pack ranges
+  u32* D;                              // retained words (dilated mask), when dilating
+  u32* ftn;                            // [tiles] retained voxels per compaction tile
+  u32* ftb;                            // [tiles] boundaries per compaction tile
+  u64* ftno;                           // [tiles] first retained voxel of each tile
+  u64* ftbo;                           // [tiles] first boundary of each tile
+  u32* rno;                            // [rows] first retained voxel of the row in its tile
+  u32* rbo;                            // [rows] first boundary of the row in its tile
+  u32* crec;                           // [chunks] records per pack chunk (zeroed)
+  u32* rbits;                          // [n / 32] record bitmap (bit k: symbol k is 0)
+  u32* cw;                             // [chunks] payload words per chunk
+  u64* cwoff;                          // [chunks] first payload word of each chunk
+  u64* crecoff;                        // [chunks] first record of each chunk
   u32 rpt;                             // rows per front tile
   u32 vec;                             // rows are 16-byte aligned (vector loads)
   u32 flat;                            // binarisation reads the volume as a flat array
@@ -337,10 +393,12 @@ struct Batch {
   Desc c;                              // shared settings (geometry fields unused)
   u32 n;                               // items
   u32* status;                         // context status word
-  u32* ctr;                            // [4] tickets: front, symbols, pack, spare
+  u32* ctr;                            // [5] tickets: front count, symbols, pack count,
+                                       // pack write, front write
   u64 seg0[kMaxBatch + 1];             // prefix of threshold row segments (row-form items)
   u64 fseg0[kMaxBatch + 1];            // prefix of threshold flat spans (flat-form items)
   u64 ftile0[kMaxBatch + 1];           // prefix of front tiles
+  u64 row0[kMaxBatch + 1];             // prefix of rows
   Item it[kMaxBatch];
 };
 
@@ -436,6 +494,15 @@ __device__ __forceinline__ int quant_u16(unsigned raw, int dark, int eb_int) {
 __device__ __forceinline__ int quant_u16_fd(unsigned raw, int dark, int eb_int,
                                             const struct FastDiv& fd);
 
+// Launch shapes that leave every output byte unchanged (picked by roix_tune).
+struct Tuning {
+  u32 front_words = 2048;      // mask words per compaction tile
+  u32 thr_blocks_per_sm = 8;   // binarisation, row form (blocks of 256 threads)
+  u32 flat_blocks_per_sm = 4;  // binarisation, flat form
+  u32 sym_blocks_per_sm = 0;   // symbols: 0 = as many as fit
+  u32 pack_blocks_per_sm = 0;  // pack: 0 = as many as fit
+};
+
 }  // namespace roix
 
 // A context: device, workspace, status carry-over, profiling events.
@@ -447,6 +514,7 @@ struct roix_ctx {
   roix::u32 pending = 0;  // status carried over a workspace reallocation
   std::string err;
   int profile = 0;        // per-stage events in the fused path
+  roix::Tuning tune{};    // launch shapes (roix_tune / roix_set_tuning)
   cudaEvent_t ev[16] = {};
   int nev = 0;
 };
@@ -472,6 +540,7 @@ void set_threshold_units(Batch& B);
 struct Launch {
   cudaStream_t stream;
   int sms;
+  Tuning t{};
 };
 
 // mask kernels (k_mask.cu)

@@ -157,7 +157,8 @@ def test_cube2048_slabs_properties_and_sampled_rows():
         D = Ds[k].cuda()
         xk = x[z0:z0 + slab]
         fin = D & torch.isfinite(xk)
-        assert float((xk[fin].double() - y[fin].double()).abs().max().item()) <= e.eb_abs
+        if bool(fin.any().item()):
+            assert float((xk[fin].double() - y[fin].double()).abs().max().item()) <= e.eb_abs
         assert bool((y[~D] == 0).all().item())
         del y, D, fin
     # sampled rows against the oracle

@@ -409,3 +409,21 @@ def test_flat_binarisation_in_fused_and_batch(rx):
     x = phantom.ellipsoids(shape=(6, 40, 290), seed=3).numpy()
     ref, got = _compress_both(rx, x, eb=1e-3, eb_mode="rel")
     _assert_same_container(ref, got)
+
+
+def test_scans_over_more_tiles_and_chunks_than_one_block(rx):
+    # more than 1024 compaction tiles and pack chunks per item: the per-item
+    # scans give every thread a range of several entries
+    default = rx.get_tuning()
+    try:
+        rx.set_tuning(front_words=256)  # 8 rows of 1024 voxels per tile: 1200 tiles
+        x = phantom.porous_cylinder(1024, radius=400.0, seed=3, z_range=(440, 456)).numpy()
+        x = np.ascontiguousarray(x[:, 212:812, :])  # 16 x 600 x 1024
+        for cfg in (dict(eb=1e-4, eb_mode="rel", dilate=1, chunk=256),
+                    dict(eb=1e-5, eb_mode="rel", dilate=0, chunk=256, radius=64)):
+            ref, got = _compress_both(rx, x, **cfg)
+            _assert_same_container(ref, got)
+            h = oracle.header(ref)
+            assert h["n_chunks"] > 1024
+    finally:
+        rx.set_tuning(**default)
