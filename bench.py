@@ -223,9 +223,11 @@ def run_ours(args, rank, world, local_rank):
         c.reserve(need)  # no workspace growth once the graph holds its pointers
     main = torch.cuda.Stream(dev)  # graphs must be captured off the legacy default stream
     torch.cuda.set_stream(main)
-    # launch shapes picked by the autotuner on this very workload (no output byte changes)
+    # launch shapes picked by the autotuner on this very workload (no output byte changes);
+    # --tune 0 keeps the default shapes (e.g. for profiling runs)
     t0 = time.perf_counter()
-    tuning = ctxs[0].tune(xs, outs=outs, caps=caps, sizes=sizes, reps=3, stream=main, **cfg)
+    tuning = (ctxs[0].tune(xs, outs=outs, caps=caps, sizes=sizes, reps=3, stream=main, **cfg)
+              if args.tune else ctxs[0].get_tuning())
     tune_s = time.perf_counter() - t0
     for c in ctxs[1:]:
         c.set_tuning(**tuning)
@@ -1055,8 +1057,9 @@ def run_slabs(args, rank, world, local_rank):
     cfgs = [dict(sc["cfg"], eb=eb) for eb in sc["sweep"]]
     # launch shapes tuned on one slab compressed as a volume of its own
     t0 = time.perf_counter()
-    tuning = rx.tune([x[:slab]], outs=outs[:1], caps=[cap], sizes=sizes[:1], reps=3,
-                     stream=main, **dict(cfgs[0], eb=sc["e2e_eb"]))
+    tuning = (rx.tune([x[:slab]], outs=outs[:1], caps=[cap], sizes=sizes[:1], reps=3,
+                      stream=main, **dict(cfgs[0], eb=sc["e2e_eb"])) if args.tune
+              else rx.get_tuning())
     tune_s = time.perf_counter() - t0
     rx.reserve(rx.slabs_workspace_size(x.shape, slab, cap=cap, **cfgs[0]))
 
@@ -1297,6 +1300,8 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--tune", type=int, default=1,
+                    help="1: launch shapes from the autotuner on the workload; 0: defaults")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))

@@ -222,6 +222,23 @@ __device__ __forceinline__ int sym_eval(const Src<TV, FROM_Q>& src,
   }
 }
 
+// Error-bound constants of every item of the batch, formed once per block
+// (one thread per item) into shared memory: warps that move between items
+// then read them instead of repeating the binary64 derivation.
+struct ItemEb {
+  roix_eb_info e;
+  FastDiv fd;
+};
+
+__device__ __forceinline__ void items_eb(const Batch& B, ItemEb* out) {
+  for (u32 i = threadIdx.x; i < B.n; i += blockDim.x) {
+    const Item& I = B.it[i];
+    const Desc d = desc_of(B, I);
+    out[i].e = make_eb(d, I.rst->vmin_key, I.rst->vmax_key);
+    out[i].fd = FastDiv(2u * (u32)out[i].e.eb_int);
+  }
+}
+
 // One warp's histogram (shared memory) added to the item's global one.
 __device__ __forceinline__ void flush_hist(u32* h, unsigned long long* g, u32 S, int lane) {
   __syncwarp();
@@ -259,6 +276,8 @@ __global__ void __launch_bounds__(kThreads) k_symbols(const __grid_constant__ Ba
   static_assert(kQuantTile % kStep == 0 && kSteps % kBatch == 0, "whole steps and batches");
   extern __shared__ u32 hsm[];  // [warps][S]
   __shared__ u64 pre[kMaxBatch + 1];
+  __shared__ ItemEb ieb[kMaxBatch];
+  if constexpr (!FROM_Q) items_eb(B, ieb);
   const u32 R_ = B.c.R, S = B.c.S;
   const u32 csh = (u32)(__ffs((int)B.c.C) - 1);  // log2 of the pack chunk
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -288,8 +307,8 @@ __global__ void __launch_bounds__(kThreads) k_symbols(const __grid_constant__ Ba
         src.obits = I.obits;
         src.dark = d.dark;
         if constexpr (!FROM_Q) {
-          src.e = make_eb(d, I.rst->vmin_key, I.rst->vmax_key);
-          src.fd = FastDiv(2u * (u32)src.e.eb_int);
+          src.e = ieb[item].e;
+          src.fd = ieb[item].fd;
         }
         n = umin(I.sizes[0], I.N);
       }
@@ -740,18 +759,13 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__
 
 // Warps, one chunk at a time: lane l holds symbols [8 l, 8 l + 8) of each
 // round of 256 (coalesced 16-byte loads); the code lengths come from the
-// item's table in the warp's shared memory.
+// item's byte table (2R bytes, read through L1).
 __global__ void __launch_bounds__(kThreads) k_pack_count(const __grid_constant__ Batch B) {
-  extern __shared__ u32 lsm[];  // [warps][S] code lengths
   __shared__ u64 pre[kMaxBatch + 1];
-  const u32 C = B.c.C, S = B.c.S;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  u32* len = lsm + (u32)warp * S;
+  const u32 C = B.c.C;
+  const int lane = threadIdx.x & 31;
   tile_prefix(B, pre, C, 1);
   const u64 total = pre[B.n];
-  u32 cur = 0xffffffffu;
-  u64 n = 0;
-  const uint16_t* __restrict__ sym = nullptr;
   while (true) {
     u64 gt = 0;
     if (lane == 0) gt = atomicAdd(&B.ctr[2], 1u);
@@ -759,14 +773,9 @@ __global__ void __launch_bounds__(kThreads) k_pack_count(const __grid_constant__
     if (gt >= total) break;
     const u32 item = find_item(pre, B.n, gt);
     const Item& I = B.it[item];
-    if (item != cur) {
-      cur = item;
-      __syncwarp();
-      for (u32 i = lane; i < S; i += 32) len[i] = __ldg(I.codes + i) >> 24;
-      __syncwarp();
-      n = umin(I.sizes[0], I.N);
-      sym = I.sym;
-    }
+    const u64 n = umin(I.sizes[0], I.N);
+    const uint16_t* __restrict__ sym = I.sym;
+    const uint8_t* __restrict__ len = I.lens;  // 2R bytes: stays in L1
     const u64 t = gt - pre[item];
     const u64 c0 = t * C + (u64)lane * 8;
     u32 bits = 0;
@@ -774,42 +783,18 @@ __global__ void __launch_bounds__(kThreads) k_pack_count(const __grid_constant__
       const u64 k = c0 + (u64)r * 256;
       if (k + 8 <= n) {
         const uint4 v = __ldg(reinterpret_cast<const uint4*>(sym + k));
-        bits += len[v.x & 0xffffu] + len[v.x >> 16] + len[v.y & 0xffffu] + len[v.y >> 16] +
-                len[v.z & 0xffffu] + len[v.z >> 16] + len[v.w & 0xffffu] + len[v.w >> 16];
+        bits += __ldg(len + (v.x & 0xffffu)) + __ldg(len + (v.x >> 16)) +
+                __ldg(len + (v.y & 0xffffu)) + __ldg(len + (v.y >> 16)) +
+                __ldg(len + (v.z & 0xffffu)) + __ldg(len + (v.z >> 16)) +
+                __ldg(len + (v.w & 0xffffu)) + __ldg(len + (v.w >> 16));
       } else {
 #pragma unroll
         for (int q = 0; q < 8; ++q)
-          if (k + q < n) bits += len[__ldg(sym + k + q)];
+          if (k + q < n) bits += __ldg(len + __ldg(sym + k + q));
       }
     }
     bits = warp_sum(bits);
     if (lane == 0) I.cw[t] = (bits + 31) >> 5;
-  }
-}
-
-// One block per item: exclusive scans of the chunks' words and records, the
-// totals into the item's state, the chunk table into the container.
-__global__ void __launch_bounds__(kCbThreads) k_pack_scan(const __grid_constant__ Batch B) {
-  __shared__ u64 scratch[40];
-  const Item& I = B.it[blockIdx.x];
-  const u32 C = B.c.C, S = B.c.S;
-  const u64 n = umin(I.sizes[0], I.N);
-  const u64 nchunks = (n + C - 1) / C;
-  u64 wcarry, rcarry;
-  block_scan2(I.cw, I.crec, nchunks, I.cwoff, I.crecoff, scratch, &wcarry, &rcarry);
-  __syncthreads();  // the offsets below are read by other threads than their writers
-  State* st = I.st;
-  if (threadIdx.x == 0) {
-    st->nout = rcarry;
-    st->nwords = wcarry;
-    if (rcarry > I.rec_cap) st->cap_flag = 1u;
-  }
-  const Layout Lo = make_layout(S, I.rows, I.sizes[1], rcarry, nchunks, wcarry);
-  uint8_t* out = I.out;
-  const u64 cap = I.cap;
-  for (u64 t = threadIdx.x; t < nchunks; t += blockDim.x) {
-    const u64 o = Lo.off_chunks + 8 * t;
-    if (o + 8 <= cap) *reinterpret_cast<u64*>(out + o) = I.cwoff[t];
   }
 }
 
@@ -822,6 +807,8 @@ __global__ void __launch_bounds__(kCbThreads) k_pack_scan(const __grid_constant_
 template <typename TV, bool FROM_Q>
 __global__ void __launch_bounds__(kThreads) k_records(const __grid_constant__ Batch B) {
   __shared__ u64 pre[kMaxBatch + 1];
+  __shared__ ItemEb ieb[kMaxBatch];
+  if constexpr (!FROM_Q) items_eb(B, ieb);
   const u32 C = B.c.C;
   const int lane = threadIdx.x & 31;
   tile_prefix(B, pre, C, 1);
@@ -844,8 +831,8 @@ __global__ void __launch_bounds__(kThreads) k_records(const __grid_constant__ Ba
       src.obits = I.obits;
       src.dark = d.dark;
       if constexpr (!FROM_Q) {
-        src.e = make_eb(d, I.rst->vmin_key, I.rst->vmax_key);
-        src.fd = FastDiv(2u * (u32)src.e.eb_int);
+        src.e = ieb[item].e;
+        src.fd = ieb[item].fd;
       }
       n = umin(I.sizes[0], I.N);
     }
@@ -897,7 +884,7 @@ __global__ void __launch_bounds__(kThreads) k_pack(const __grid_constant__ Batch
   const u32 wb_words = C * kLMax / 64 + 2;
   for (u32 i = tid; i < wb_words; i += blockDim.x) wb[i] = 0ull;
   u32 cur = 0xffffffffu;
-  u64 n = 0, cap = 0, pay0 = 0;
+  u64 n = 0, cap = 0, pay0 = 0, tab0 = 0;
   const uint16_t* __restrict__ sym = nullptr;
   uint8_t* out = nullptr;
   while (true) {
@@ -912,7 +899,9 @@ __global__ void __launch_bounds__(kThreads) k_pack(const __grid_constant__ Batch
       for (u32 i = tid; i < S; i += blockDim.x) tab[i] = __ldg(I.codes + i);
       n = umin(I.sizes[0], I.N);
       const u64 nchunks = (n + C - 1) / C;
-      pay0 = make_layout(S, I.rows, I.sizes[1], I.st->nout, nchunks, 0).off_payload;
+      const Layout Lo = make_layout(S, I.rows, I.sizes[1], I.st->nout, nchunks, 0);
+      pay0 = Lo.off_payload;
+      tab0 = Lo.off_chunks;
       sym = I.sym;
       out = I.out;
       cap = I.cap;
@@ -976,7 +965,10 @@ __global__ void __launch_bounds__(kThreads) k_pack(const __grid_constant__ Batch
       if (nacc > (shared_first ? pos : 0u)) atomicOr(&wb32[w], (u32)(acc << (32 - nacc)));
     }
     __syncthreads();
-    const u64 pay = pay0 + 4 * I.cwoff[t];  // byte offset of the chunk's first word
+    const u64 cw0 = I.cwoff[t];
+    if (tid == 0 && tab0 + 8 * t + 8 <= cap)  // the chunk table entry
+      *reinterpret_cast<u64*>(out + tab0 + 8 * t) = cw0;
+    const u64 pay = pay0 + 4 * cw0;  // byte offset of the chunk's first word
     const u32* wb32 = reinterpret_cast<const u32*>(wb);
     for (u32 i = tid; i < words; i += blockDim.x) {
       const u64 o = pay + 4 * (u64)i;
@@ -1171,14 +1163,11 @@ void launch_pack(const Launch& L, const Batch& B, u64 ranges_cap) {
   if (ranges_cap == 0) return;
   const u64 wpb = kThreads / 32;
   {  // chunk sizes
-    const size_t smem = (size_t)wpb * B.c.S * 4;
-    cudaFuncSetAttribute((const void*)k_pack_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    u64 grid = (u64)grid_for((const void*)k_pack_count, kThreads, smem, L.sms);
+    u64 grid = (u64)grid_for((const void*)k_pack_count, kThreads, 0, L.sms);
     grid = umin(grid, (ranges_cap + wpb - 1) / wpb);
-    k_pack_count<<<(unsigned)grid, kThreads, smem, L.stream>>>(B);
+    k_pack_count<<<(unsigned)grid, kThreads, 0, L.stream>>>(B);
   }
-  k_pack_scan<<<B.n, kCbThreads, 0, L.stream>>>(B);
+  launch_scan_pairs(L, B, 1, (ranges_cap + kScanTile - 1) / kScanTile + B.n);
   {  // records (chunks that hold any)
     const bool from_q = B.it[0].q != nullptr;
     const u64 grid = umin((ranges_cap + wpb - 1) / wpb, (u64)L.sms * 8);

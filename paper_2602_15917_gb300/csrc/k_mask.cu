@@ -274,12 +274,18 @@ __global__ void __launch_bounds__(kThreads, FLAT ? 4 : 1) k_threshold(const __gr
   const int lane = threadIdx.x & 31;
   const u64 warp = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
-  const u64* pre = FLAT ? B.fseg0 : B.seg0;
-  const u64 total = pre[B.n];
+  const u64 total = FLAT ? B.fseg0[B.n] : B.seg0[B.n];
   for (u64 s = warp; s < total; s += nwarps) {
-    const u32 i = find_item(pre, B.n, s);
+    u32 i;
+    u64 local;
+    if constexpr (FLAT) {
+      i = find_item(B.fseg0, B.n, s);
+      local = s - B.fseg0[i];
+    } else {
+      i = find_item(B.seg0, B.n, s);
+      local = s - B.seg0[i];
+    }
     const Item& I = B.it[i];
-    const u64 local = s - pre[i];
     const Desc d = desc_of(B, I);
     if constexpr (FLAT) {
       thr_flat_span<TV>(d, (const TV*)I.in, I.T, local, lane);
@@ -403,6 +409,68 @@ __device__ __forceinline__ void copy_run_u8(const u8* __restrict__ src, u8* __re
   }
   const u32 done = hb + 16 * n16;
   if ((u32)lane < len - done) dst[done + lane] = __ldg(src + done + lane);
+}
+
+// Range key of one value (float32: order-preserving bits of a finite value;
+// uint16: value + 1, so that 0 means none).
+template <typename TV>
+__device__ __forceinline__ void range_add(TV v, u32& kmin, u32& kmax) {
+  if constexpr (sizeof(TV) == 4) {
+    if (isfinite(v)) {
+      const u32 kq = f32_key(__fadd_rn(v, 0.0f));
+      kmin = min(kmin, kq);
+      kmax = max(kmax, kq);
+    }
+  } else {
+    kmin = min(kmin, (u32)v + 1u);
+    kmax = max(kmax, (u32)v + 1u);
+  }
+}
+
+// Copy of one run of float32 or uint16 values by a warp, gathering their
+// range: element copies up to the first 16-byte boundary of the destination
+// and after the last one; in between every lane writes aligned 16-byte chunks
+// funnel-shifted out of five aligned source words, two chunks in flight.
+template <typename TV>
+__device__ __forceinline__ void copy_run_vec(const TV* __restrict__ src, TV* __restrict__ dst,
+                                             u32 len, int lane, u32& kmin, u32& kmax) {
+  constexpr u32 kPer = 16 / sizeof(TV);
+  const u32 head = (u32)(((16u - ((uintptr_t)dst & 15u)) & 15u) / sizeof(TV));
+  const u32 hb = umin(head, len);
+  if ((u32)lane < hb) {
+    const TV v = __ldg(src + lane);
+    dst[lane] = v;
+    range_add<TV>(v, kmin, kmax);
+  }
+  const u32 n16 = (len - hb) / kPer;
+  const uintptr_t sa = (uintptr_t)(src + hb);
+  const u32 sh = (u32)(sa & 3u) * 8u;
+  const u32* sw = reinterpret_cast<const u32*>(sa & ~(uintptr_t)3);
+  uint4* dw = reinterpret_cast<uint4*>(dst + hb);
+  for (u32 k = lane; k < n16; k += 32) {
+    const u32 w0 = __ldg(sw + 4 * k), w1 = __ldg(sw + 4 * k + 1), w2 = __ldg(sw + 4 * k + 2),
+              w3 = __ldg(sw + 4 * k + 3);
+    const u32 w4 = sh ? __ldg(sw + 4 * k + 4) : 0u;
+    const uint4 v = make_uint4(__funnelshift_r(w0, w1, sh), __funnelshift_r(w1, w2, sh),
+                               __funnelshift_r(w2, w3, sh), __funnelshift_r(w3, w4, sh));
+    dw[k] = v;
+    const u32 q[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if constexpr (sizeof(TV) == 4) {
+        range_add<float>(__uint_as_float(q[i]), kmin, kmax);
+      } else {
+        range_add<unsigned short>((unsigned short)(q[i] & 0xffffu), kmin, kmax);
+        range_add<unsigned short>((unsigned short)(q[i] >> 16), kmin, kmax);
+      }
+    }
+  }
+  const u32 done = hb + kPer * n16;
+  for (u32 e = done + lane; e < len; e += 32) {
+    const TV v = __ldg(src + e);
+    dst[e] = v;
+    range_add<TV>(v, kmin, kmax);
+  }
 }
 
 struct FrontSmem {
@@ -586,16 +654,88 @@ __global__ void __launch_bounds__(kThreads, 4) k_front_count(const __grid_consta
   }
 }
 
-// One block per item: exclusive scans of the tiles' retained voxels and
-// boundaries; the totals are the item's n and nb.
-__global__ void __launch_bounds__(1024) k_front_scan(const __grid_constant__ Batch B) {
+// Exclusive scans of two counts per tile or chunk, several blocks per item:
+// a block takes kScanTile entries (8 consecutive ones per thread), scans them,
+// and a decoupled look-back over the item's few scan tiles gives its offset.
+// MODE 0: compaction tiles (ftn, ftb -> ftno, ftbo; totals n, nb); MODE 1:
+// pack chunks (cw, crec -> cwoff, crecoff; totals nwords, nout).
+template <int MODE>
+__global__ void __launch_bounds__(1024) k_scan_pairs(const __grid_constant__ Batch B) {
+  __shared__ u64 pre[kMaxBatch + 1];
   __shared__ u64 scratch[40];
-  const Item& I = B.it[blockIdx.x];
-  u64 cn, cb;
-  block_scan2(I.ftn, I.ftb, I.ftiles, I.ftno, I.ftbo, scratch, &cn, &cb);
-  if (threadIdx.x == 0) {
-    I.sizes[0] = cn;
-    I.sizes[1] = cb;
+  __shared__ u64 s_tile, s_ex[2];
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid == 0) {
+    u64 acc = 0;
+    for (u32 i = 0; i < B.n; ++i) {
+      pre[i] = acc;
+      const Item& I = B.it[i];
+      const u64 cnt =
+          MODE == 0 ? I.ftiles : (umin(I.sizes[0], I.N) + B.c.C - 1) / B.c.C;
+      acc += (cnt + kScanTile - 1) / kScanTile;
+    }
+    pre[B.n] = acc;
+  }
+  __syncthreads();
+  const u64 total = pre[B.n];
+  while (true) {
+    if (tid == 0) s_tile = atomicAdd(&B.ctr[5 + MODE], 1u);
+    __syncthreads();
+    const u64 gt = s_tile;
+    if (gt >= total) break;
+    const u32 item = find_item(pre, B.n, gt);
+    const Item& I = B.it[item];
+    const u64 t = gt - pre[item];
+    const u64 cnt = MODE == 0 ? I.ftiles : (umin(I.sizes[0], I.N) + B.c.C - 1) / B.c.C;
+    const u64 ntiles = (cnt + kScanTile - 1) / kScanTile;
+    const u32* __restrict__ a = MODE == 0 ? I.ftn : I.cw;
+    const u32* __restrict__ b = MODE == 0 ? I.ftb : I.crec;
+    u64* __restrict__ ao = MODE == 0 ? I.ftno : I.cwoff;
+    u64* __restrict__ bo = MODE == 0 ? I.ftbo : I.crecoff;
+    const u64 i0 = t * kScanTile + (u64)tid * 8;
+    u32 va[8], vb[8];
+    u64 sa = 0, sb = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      va[k] = i0 + k < cnt ? __ldg(a + i0 + k) : 0u;
+      vb[k] = i0 + k < cnt ? __ldg(b + i0 + k) : 0u;
+      sa += va[k];
+      sb += vb[k];
+    }
+    u64 ta, tb;
+    u64 ea = block_excl_scan<u64>(sa, scratch, &ta);
+    u64 eb = block_excl_scan<u64>(sb, scratch, &tb);
+    if (tid < 32) {
+      u64 mine[2] = {ta, tb}, excl[2];
+      lookback_warp<2>(MODE == 0 ? I.lbsf : I.lbsp, t, mine, excl, B.status);
+      if (lane == 0) {
+        s_ex[0] = excl[0];
+        s_ex[1] = excl[1];
+        if (t == ntiles - 1) {
+          if (MODE == 0) {
+            I.sizes[0] = excl[0] + ta;
+            I.sizes[1] = excl[1] + tb;
+          } else {
+            I.st->nwords = excl[0] + ta;
+            I.st->nout = excl[1] + tb;
+            if (excl[1] + tb > I.rec_cap) I.st->cap_flag = 1u;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    ea += s_ex[0];
+    eb += s_ex[1];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (i0 + k < cnt) {
+        ao[i0 + k] = ea;
+        bo[i0 + k] = eb;
+      }
+      ea += va[k];
+      eb += vb[k];
+    }
+    __syncthreads();
   }
 }
 
@@ -704,33 +844,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_front_write(const __grid_consta
             const u32 len = xe - xs;
             if constexpr (sizeof(TV) == 1) {
               copy_run_u8(reinterpret_cast<const u8*>(src), reinterpret_cast<u8*>(dst), len, lane);
-              on += len;
-              continue;
-            }
-            for (u32 e0 = 0; e0 < len; e0 += 256) {
-              TV v[8];
-#pragma unroll
-              for (int j = 0; j < 8; ++j) {
-                const u32 e = e0 + j * 32 + lane;
-                v[j] = e < len ? __ldg(src + e) : TV(0);
-              }
-#pragma unroll
-              for (int j = 0; j < 8; ++j) {
-                const u32 e = e0 + j * 32 + lane;
-                if (e < len) {
-                  dst[e] = v[j];
-                  if constexpr (sizeof(TV) == 4) {
-                    if (isfinite(v[j])) {
-                      const u32 kq = f32_key(__fadd_rn(v[j], 0.0f));
-                      kmin = min(kmin, kq);
-                      kmax = max(kmax, kq);
-                    }
-                  } else {
-                    kmin = min(kmin, (u32)v[j] + 1u);
-                    kmax = max(kmax, (u32)v[j] + 1u);
-                  }
-                }
-              }
+            } else {
+              copy_run_vec<TV>(src, dst, len, lane, kmin, kmax);
             }
             on += len;
           }
@@ -779,12 +894,23 @@ int occupancy_grid(const void* fn, int threads, size_t smem, int sms) {
 
 }  // namespace
 
+void launch_scan_pairs(const Launch& L, const Batch& B, int mode, u64 tiles_cap) {
+  if (tiles_cap == 0) return;
+  const u64 grid = umin(tiles_cap, (u64)L.sms * 2);
+  if (mode == 0) k_scan_pairs<0><<<(unsigned)grid, 1024, 0, L.stream>>>(B);
+  else k_scan_pairs<1><<<(unsigned)grid, 1024, 0, L.stream>>>(B);
+}
+
 void launch_threshold(const Launch& L, const Batch& B) {
-  auto run = [&](auto kernel, u64 units, u64 per_warp) {
+  // blocks per SM: the tuned value, but never more than fit at once (a second
+  // partial wave of equally loaded blocks would leave SMs idle at the end)
+  auto run = [&](auto kernel, u64 units, u64 per_sm) {
     if (units == 0) return;
     const u64 warps_per_block = kThreads / 32;
     u64 blocks = (units + warps_per_block - 1) / warps_per_block;
-    const u64 cap = (u64)L.sms * per_warp;  // blocks of 256 threads per SM in flight
+    int fit = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, (const void*)kernel, kThreads, 0);
+    const u64 cap = (u64)L.sms * umax(1, umin(per_sm, (u64)(fit > 0 ? fit : 1)));
     if (blocks > cap) blocks = cap;
     kernel<<<(unsigned)blocks, kThreads, 0, L.stream>>>(B);
   };
@@ -836,7 +962,9 @@ void launch_front(const Launch& L, const Batch& B) {
   u64 grid = (u64)occupancy_grid((const void*)k_front_count, kThreads, smem, L.sms);
   if (grid > tiles) grid = tiles;
   k_front_count<<<(unsigned)grid, kThreads, smem, L.stream>>>(B);
-  k_front_scan<<<B.n, 1024, 0, L.stream>>>(B);
+  u64 scan_tiles = 0;
+  for (u32 i = 0; i < B.n; ++i) scan_tiles += (B.it[i].ftiles + kScanTile - 1) / kScanTile;
+  launch_scan_pairs(L, B, 0, scan_tiles);
   auto run = [&](auto kernel) {
     u64 g = (u64)occupancy_grid((const void*)kernel, kThreads, 0, L.sms);
     const u64 need = (B.row0[B.n] + kRowsPerTicket * (kThreads / 32) - 1) /

@@ -196,7 +196,9 @@ u32 front_rows_per_tile(const Desc& d) {
 // every item), then every item's data (look-back values, mask, pixel section,
 // symbols, records, code tables).
 struct ItemPlan {
-  size_t crec, hist;  // zeroed
+  size_t crec, hist, sff, sfp;  // zeroed
+  size_t sfa, spa;
+  u64 stf, stp;  // scan tiles of the compaction and of the pack
   size_t ftn, ftb, ftno, ftbo, rno, rbo, Dm, cw, cwoff, crecoff, rbits, T, P, sym, rk, rv, lens, codes;
   // largest-component scratch (keep = 1): zeroed flags and counters, then data
   size_t cf, cvars, ca, crr, cro, cxs, cxe, cpar, csize, T2;
@@ -236,6 +238,10 @@ BatchPlan plan_batch(const Desc& c, const roix_dims* dims, const u64* n_caps, co
     p.rec_cap = umin(p.n_cap, caps[i] / 12 + 1);
     p.crec = a.take(4 * (p.pchunks + 1));
     p.hist = a.take(8 * (size_t)c.S);
+    p.stf = (p.ftiles + kScanTile - 1) / kScanTile;
+    p.stp = (p.pchunks + kScanTile - 1) / kScanTile;
+    p.sff = a.take(4 * (p.stf + 1));
+    p.sfp = a.take(4 * (p.stp + 1));
     if (c.keep) {
       const u64 rows = dims[i].ny * dims[i].nz;
       p.ctiles = (rows + 2047) / 2048;
@@ -249,6 +255,8 @@ BatchPlan plan_batch(const Desc& c, const roix_dims* dims, const u64* n_caps, co
   for (u32 i = 0; i < n; ++i) {
     ItemPlan& p = bp.items[i];
     const u64 rows = dims[i].ny * dims[i].nz, W = (dims[i].nx + 31) / 32;
+    p.sfa = a.take(8 * 2 * 2 * (p.stf + 1));
+    p.spa = a.take(8 * 2 * 2 * (p.stp + 1));
     p.ftn = a.take(4 * (p.ftiles + 1));
     p.ftb = a.take(4 * (p.ftiles + 1));
     p.ftno = a.take(8 * (p.ftiles + 1));
@@ -334,6 +342,8 @@ void fill_batch(Batch& B, const Desc& c, const BatchPlan& bp, const roix_dims* d
     I.lens = (uint8_t*)(ws + p.lens);
     I.codes = (u32*)(ws + p.codes);
     I.sizes = &I.st->n;
+    I.lbsf = lb_at<2>(ws, p.sff, p.sfa, p.stf);
+    I.lbsp = lb_at<2>(ws, p.sfp, p.spa, p.stp);
     I.ftn = (u32*)(ws + p.ftn);
     I.ftb = (u32*)(ws + p.ftb);
     I.ftno = (u64*)(ws + p.ftno);

@@ -310,6 +310,7 @@ struct State {
   u32 status;                          // context status word (state 0 only)
   u32 ctr_front, ctr_quant, ctr_pack;  // dynamic tile counters (state 0: batch tickets)
   u32 ctr_write, ctr_front2;           // pack-write and compaction-write tickets
+  u32 ctr_scan_f, ctr_scan_p;          // tile scans of the compaction and of the pack
   u64 n, nb, nout, nwords;             // sizes found on the device
   u32 vmin_key, vmax_key;              // range of retained finite values
   u32 cap_flag, pad0;
@@ -374,6 +375,7 @@ struct Item {
   u32* ftb;                            // [tiles] boundaries per compaction tile
   u64* ftno;                           // [tiles] first retained voxel of each tile
   u64* ftbo;                           // [tiles] first boundary of each tile
+  LookBack<2> lbsf, lbsp;              // look-backs of the tile scans (8192 entries a tile)
   u32* rno;                            // [rows] first retained voxel of the row in its tile
   u32* rbo;                            // [rows] first boundary of the row in its tile
   u32* crec;                           // [chunks] records per pack chunk (zeroed)
@@ -393,8 +395,8 @@ struct Batch {
   Desc c;                              // shared settings (geometry fields unused)
   u32 n;                               // items
   u32* status;                         // context status word
-  u32* ctr;                            // [5] tickets: front count, symbols, pack count,
-                                       // pack write, front write
+  u32* ctr;                            // [7] tickets: front count, symbols, pack count,
+                                       // pack write, front write, front scan, pack scan
   u64 seg0[kMaxBatch + 1];             // prefix of threshold row segments (row-form items)
   u64 fseg0[kMaxBatch + 1];            // prefix of threshold flat spans (flat-form items)
   u64 ftile0[kMaxBatch + 1];           // prefix of front tiles
@@ -544,6 +546,12 @@ struct Launch {
 };
 
 // mask kernels (k_mask.cu)
+constexpr u32 kScanTile = 8192;  // entries per block of the tile scans
+// Exclusive scans of the pairs (ftn, ftb) over compaction tiles (mode 0: into
+// ftno, ftbo and the item's n, nb) or (cw, crec) over pack chunks (mode 1:
+// into cwoff, crecoff and the item's nwords, nout); tiles_cap bounds the scan
+// tiles of the batch.
+void launch_scan_pairs(const Launch& L, const Batch& B, int mode, u64 tiles_cap);
 void launch_threshold(const Launch& L, const Batch& B);
 void launch_dilate(const Launch& L, const Desc& d, const u32* T, u32* D, u64* popcount);
 void launch_front(const Launch& L, const Batch& B);
