@@ -153,13 +153,20 @@ __device__ __forceinline__ u32 symbol_of(int c, int prev, bool out, u32 R) {
 // ceil(n_i / per) / group over the items (n_i found by the compaction),
 // computed by each block at start.
 __device__ __forceinline__ void tile_prefix(const Batch& B, u64* pre, u64 per, u64 group) {
+  // every item's count read by a thread of its own (the loads overlap), the
+  // prefix summed by one thread from shared memory
+  for (u32 i = threadIdx.x; i < B.n; i += blockDim.x) {
+    const Item& I = B.it[i];
+    const u64 n = umin(I.sizes[0], I.N);
+    pre[i + 1] = ((n + per - 1) / per + group - 1) / group;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     u64 acc = 0;
     for (u32 i = 0; i < B.n; ++i) {
+      const u64 c = pre[i + 1];
       pre[i] = acc;
-      const Item& I = B.it[i];
-      const u64 n = umin(I.sizes[0], I.N);
-      acc += ((n + per - 1) / per + group - 1) / group;
+      acc += c;
     }
     pre[B.n] = acc;
   }

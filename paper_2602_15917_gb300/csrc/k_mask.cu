@@ -665,14 +665,18 @@ __global__ void __launch_bounds__(1024) k_scan_pairs(const __grid_constant__ Bat
   __shared__ u64 scratch[40];
   __shared__ u64 s_tile, s_ex[2];
   const int tid = threadIdx.x, lane = tid & 31;
+  for (u32 i = tid; i < B.n; i += blockDim.x) {  // counts read in parallel
+    const Item& I = B.it[i];
+    const u64 cnt = MODE == 0 ? I.ftiles : (umin(I.sizes[0], I.N) + B.c.C - 1) / B.c.C;
+    pre[i + 1] = (cnt + kScanTile - 1) / kScanTile;
+  }
+  __syncthreads();
   if (tid == 0) {
     u64 acc = 0;
     for (u32 i = 0; i < B.n; ++i) {
+      const u64 c = pre[i + 1];
       pre[i] = acc;
-      const Item& I = B.it[i];
-      const u64 cnt =
-          MODE == 0 ? I.ftiles : (umin(I.sizes[0], I.N) + B.c.C - 1) / B.c.C;
-      acc += (cnt + kScanTile - 1) / kScanTile;
+      acc += c;
     }
     pre[B.n] = acc;
   }
