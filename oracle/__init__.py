@@ -44,7 +44,8 @@ class _Params(C.Structure):
     _fields_ = [("dtype", C.c_int32), ("eb_mode", C.c_int32), ("eb_value", C.c_double),
                 ("cmp", C.c_int32), ("keep", C.c_int32), ("connectivity", C.c_int32),
                 ("dilate", C.c_int32), ("threshold", C.c_double), ("dark", C.c_double),
-                ("fill", C.c_double), ("radius", C.c_uint32), ("chunk", C.c_uint32)]
+                ("fill", C.c_double), ("radius", C.c_uint32), ("chunk", C.c_uint32),
+                ("order", C.c_uint32)]
 
 
 class Eb(C.Structure):
@@ -68,7 +69,7 @@ def lib():
             L.oracle_eb.argtypes = [P, i32, u64, i32, d, C.POINTER(Eb)]
             L.oracle_eb.restype = None
             L.oracle_quantize.argtypes = [P, i32, u64, C.POINTER(Eb), d, P, P]
-            L.oracle_lorenzo.argtypes = [P, P, P, i32, u64, u32, P, P, P]
+            L.oracle_lorenzo.argtypes = [P, P, P, i32, u64, u32, u32, P, P, P]
             L.oracle_lorenzo.restype = u64
             L.oracle_histogram.argtypes = [P, u64, u32, P]
             L.oracle_histogram.restype = None
@@ -117,10 +118,12 @@ def _dtype_code(x: np.ndarray) -> int:
 
 
 def params(dtype: int, eb=1e-3, eb_mode="abs", cmp="gt", threshold=0.1, keep="all",
-           connectivity=26, dilate=1, dark=0.0, fill=0.0, radius=512, chunk=4096) -> _Params:
+           connectivity=26, dilate=1, dark=0.0, fill=0.0, radius=512, chunk=4096,
+           predictor=1) -> _Params:
     return _Params(dtype, 0 if eb_mode == "abs" else 1, float(eb), 0 if cmp == "gt" else 1,
                    0 if keep == "all" else 1, int(connectivity), int(dilate),
-                   float(threshold), float(dark), float(fill), int(radius), int(chunk))
+                   float(threshold), float(dark), float(fill), int(radius), int(chunk),
+                   int(predictor))
 
 
 # ------------------------------------------------------------------- stages
@@ -189,8 +192,9 @@ def quantize(P: np.ndarray, e: Eb, dark: float = 0.0):
     return q[:P.size].copy(), o[:P.size].copy()
 
 
-def lorenzo(q: np.ndarray, outl: np.ndarray, P: np.ndarray, radius: int = 512):
-    """1D prediction + symbols; returns (sym, record keys, record payloads)."""
+def lorenzo(q: np.ndarray, outl: np.ndarray, P: np.ndarray, radius: int = 512, order: int = 1):
+    """1D Lorenzo prediction of the given order (1, or 2 for the two-layer form)
+    + symbols; returns (sym, record keys, record payloads)."""
     n = q.size
     q = np.ascontiguousarray(q, np.int32)
     outl = np.ascontiguousarray(outl, np.uint8)
@@ -199,7 +203,7 @@ def lorenzo(q: np.ndarray, outl: np.ndarray, P: np.ndarray, radius: int = 512):
     rk = np.zeros(max(n, 1), np.uint64)
     rv = np.zeros(max(n, 1), np.uint32)
     m = lib().oracle_lorenzo(_ptr(q), _ptr(outl), _ptr(P), _dtype_code(P), n, int(radius),
-                             _ptr(sym), _ptr(rk), _ptr(rv))
+                             int(order), _ptr(sym), _ptr(rk), _ptr(rv))
     return sym[:n].copy(), rk[:m].copy(), rv[:m].copy()
 
 
@@ -294,7 +298,7 @@ def header(buf: np.ndarray) -> dict:
                 fill=f(40, "<f8"), eb_value=f(48, "<f8"), eb_abs=f(56, "<f8"),
                 two_eb=f(64, "<f4"), inv2eb=f(68, "<f4"), bound=f(72, "<f4"),
                 eb_int=f(76, "<i4"), radius=f(80, "<u4"), chunk=f(84, "<u4"),
-                lmax=f(88, "<u4"), n=f(96, "<u8"), n_outliers=f(104, "<u8"),
+                lmax=f(88, "<u4"), order=max(1, f(92, "<u4")), n=f(96, "<u8"), n_outliers=f(104, "<u8"),
                 n_bounds=f(112, "<u8"), n_chunks=f(120, "<u8"), payload_words=f(128, "<u8"),
                 vmin=f(136, "<f8"), vmax=f(144, "<f8"), off_lens=f(152, "<u8"),
                 off_counts=f(160, "<u8"), off_bounds=f(168, "<u8"), off_outk=f(176, "<u8"),

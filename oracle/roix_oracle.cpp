@@ -79,6 +79,7 @@ struct OracleParams {
   double fill;           // value of non-ROI voxels after reconstruction
   uint32_t radius;       // R: symbol alphabet is 2R
   uint32_t chunk;        // C: symbols per independently decodable chunk
+  uint32_t order;        // Lorenzo order along the pixel section: 1 (0 reads as 1) or 2
 };
 
 // Error-bound constants (Sec. 4.2.3: E_abs; relative mode as in Sz3, Sec. 4.3).
@@ -88,6 +89,8 @@ struct OracleEb {
   float two_eb, inv2eb, bound;
   int32_t eb_int;        // uint16 path: integer half-width
 };
+
+static uint32_t order_of(const OracleParams* p) { return p->order == 2 ? 2u : 1u; }
 
 // ---------------------------------------------------------------- threshold
 // Sec. 4.1.1 M = I - B (B constant = dark), Sec. 4.1.3-4.1.4: M(x,y) = 1 where
@@ -306,16 +309,20 @@ int oracle_quantize(const void* P, int32_t dtype, uint64_t n, const OracleEb* e,
 }
 
 // ---------------------------------------------------------------- prediction
-// 1D Lorenzo over the pixel section: d = q[k] - q[k-1] (q[-1] = 0, an outlier
-// counts as 0). Symbol d + R when |d| < R, else symbol 0 with a record
-// (k | kind << 63, payload): kind 0 keeps q[k], kind 1 keeps the raw value bits.
-// Returns the number of records.
+// 1D Lorenzo over the pixel section (Sz3-style prediction, Sec. 4.3), in exact
+// integer arithmetic. Order 1 predicts q[k-1]; order 2 (the two-layer
+// Lorenzo) predicts 2 q[k-1] - q[k-2], i.e. extrapolates the last difference;
+// q[-1] = q[-2] = 0 and an outlier counts as 0. The residual d = q[k] - pred
+// is coded as symbol d + R when |d| < R, else as symbol 0 with a record
+// (k | kind << 63, payload): kind 0 keeps q[k], kind 1 keeps the raw value
+// bits. Returns the number of records.
 uint64_t oracle_lorenzo(const int32_t* q, const uint8_t* outl, const void* P,
-                        int32_t dtype, uint64_t n, uint32_t R, uint16_t* sym,
+                        int32_t dtype, uint64_t n, uint32_t R, uint32_t order, uint16_t* sym,
                         uint64_t* rec_key, uint32_t* rec_val) {
   uint64_t m = 0;
-  int64_t prev = 0;
+  int64_t prev1 = 0, prev2 = 0;  // q[k-1], q[k-2]
   for (uint64_t k = 0; k < n; ++k) {
+    int64_t c;
     if (outl[k]) {
       sym[k] = 0;
       rec_key[m] = k | (uint64_t(1) << 63);
@@ -324,19 +331,22 @@ uint64_t oracle_lorenzo(const int32_t* q, const uint8_t* outl, const void* P,
       else bits = ((const uint16_t*)P)[k];
       rec_val[m] = bits;
       m++;
-      prev = 0;
-      continue;
-    }
-    int64_t d = (int64_t)q[k] - prev;
-    if (d > -(int64_t)R && d < (int64_t)R) {
-      sym[k] = (uint16_t)(d + R);
+      c = 0;
     } else {
-      sym[k] = 0;
-      rec_key[m] = k;
-      rec_val[m] = (uint32_t)q[k];
-      m++;
+      c = q[k];
+      const int64_t pred = order == 2 ? 2 * prev1 - prev2 : prev1;
+      const int64_t d = c - pred;
+      if (d > -(int64_t)R && d < (int64_t)R) {
+        sym[k] = (uint16_t)(d + R);
+      } else {
+        sym[k] = 0;
+        rec_key[m] = k;
+        rec_val[m] = (uint32_t)q[k];
+        m++;
+      }
     }
-    prev = q[k];
+    prev2 = prev1;
+    prev1 = c;
   }
   return m;
 }
@@ -505,7 +515,7 @@ int encode_container(const void* in, const OracleParams* p, uint64_t nx, uint64_
   std::vector<uint16_t> sym(n + 1);
   std::vector<uint64_t> rk(n + 1);
   std::vector<uint32_t> rv(n + 1);
-  uint64_t nout = oracle_lorenzo(q.data(), ol.data(), P.data(), p->dtype, n, R,
+  uint64_t nout = oracle_lorenzo(q.data(), ol.data(), P.data(), p->dtype, n, R, order_of(p),
                                  sym.data(), rk.data(), rv.data());
   std::vector<uint64_t> hist(S);
   oracle_histogram(sym.data(), n, S, hist.data());
@@ -552,6 +562,7 @@ int encode_container(const void* in, const OracleParams* p, uint64_t nx, uint64_
   o.put<uint32_t>(80, R);
   o.put<uint32_t>(84, C);
   o.put<uint32_t>(88, kLMax);
+  o.put<uint32_t>(92, order_of(p));
   o.put<uint64_t>(96, n);
   o.put<uint64_t>(104, nout);
   o.put<uint64_t>(112, nb);
@@ -649,7 +660,8 @@ int oracle_decode(const uint8_t* buf, uint64_t size, void* outv, int32_t dtype,
   get(4, &version, 2); get(6, &dt, 1);
   get(8, &hx, 4); get(12, &hy, 4); get(16, &hz, 4);
   get(32, &dark, 8); get(40, &fill, 8); get(64, &two_eb, 4); get(76, &eb_int, 4);
-  get(80, &R, 4); get(84, &C, 4); get(88, &lmax, 4);
+  uint32_t order = 0;
+  get(80, &R, 4); get(84, &C, 4); get(88, &lmax, 4); get(92, &order, 4);
   get(96, &n, 8); get(104, &nout, 8); get(112, &nb, 8); get(120, &nchunks, 8);
   get(128, &nwords, 8);
   get(152, &off_lens, 8); get(160, &off_counts, 8); get(168, &off_bounds, 8);
@@ -657,6 +669,8 @@ int oracle_decode(const uint8_t* buf, uint64_t size, void* outv, int32_t dtype,
   get(200, &off_payload, 8); get(208, &total, 8);
   if (version != 1 || dt != dtype || hx != nx || hy != ny || hz != nz) return ERR_CORRUPT;
   if (total > size || lmax != kLMax || R < 2 || R > 32768 || C == 0) return ERR_CORRUPT;
+  if (order > 2) return ERR_CORRUPT;
+  if (order == 0) order = 1;
   uint64_t N = nx * ny * nz, rows = ny * nz, S = 2ull * R;
   if (dtype == DT_U16 && !(fill >= 0.0 && fill <= 65535.0 && fill == std::floor(fill)))
     return ERR_CORRUPT;
@@ -724,12 +738,14 @@ int oracle_decode(const uint8_t* buf, uint64_t size, void* outv, int32_t dtype,
   std::vector<uint8_t> raw_kind(n + 1, 0);
   std::vector<uint32_t> raw_bits(n + 1, 0);
   uint64_t r = 0;
-  int64_t prev = 0;
+  int64_t prev1 = 0, prev2 = 0;
   for (uint64_t k = 0; k < n; ++k) {
     int64_t c;
     if (sym[k] != 0) {
       if (sym[k] >= S) return ERR_CORRUPT;
-      c = prev + (int64_t)sym[k] - (int64_t)R;
+      const int64_t pred = order == 2 ? 2 * prev1 - prev2 : prev1;
+      c = pred + (int64_t)sym[k] - (int64_t)R;
+      if (c < INT32_MIN || c > INT32_MAX) return ERR_CORRUPT;
     } else {
       if (r >= nout || (rk[r] & ~(uint64_t(1) << 63)) != k) return ERR_CORRUPT;
       if (rk[r] >> 63) {
@@ -742,7 +758,8 @@ int oracle_decode(const uint8_t* buf, uint64_t size, void* outv, int32_t dtype,
       r++;
     }
     q[k] = (int32_t)c;
-    prev = c;
+    prev2 = prev1;
+    prev1 = c;
   }
   if (r != nout) return ERR_CORRUPT;
   // rows from the geometry

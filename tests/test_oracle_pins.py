@@ -260,6 +260,71 @@ def test_lorenzo_inverts_and_records_sit_on_symbol_zero(R):
     assert np.array_equal(rv[kinds], P[outl.astype(bool)].view(np.uint32))
 
 
+def _inverse_lorenzo2(sym, rk, rv, R):
+    """Independent inverse of the two-layer Lorenzo: c = 2 c[k-1] - c[k-2] + d."""
+    rec = {int(k) & ((1 << 63) - 1): (int(k) >> 63, int(v)) for k, v in zip(rk, rv)}
+    out, p1, p2 = [], 0, 0
+    for k, s in enumerate(sym.tolist()):
+        if s:
+            c = 2 * p1 - p2 + s - R
+        else:
+            kind, v = rec[k]
+            c = 0 if kind else int(np.array(v, np.uint32).view(np.int32))
+        out.append(c)
+        p2, p1 = p1, c
+    return np.array(out, np.int64)
+
+
+@pytest.mark.parametrize("R", [2, 16, 512])
+def test_lorenzo2_inverts_and_records_sit_on_symbol_zero(R):
+    rng = np.random.default_rng(R + 7)
+    q = np.cumsum(np.cumsum(rng.integers(-R, R, 500))).astype(np.int32)
+    outl = (rng.random(500) < 0.05).astype(np.uint8)
+    q[outl.astype(bool)] = 0
+    P = rng.standard_normal(500).astype(np.float32)
+    sym, rk, rv = oracle.lorenzo(q, outl, P, R, order=2)
+    assert np.array_equal(_inverse_lorenzo2(sym, rk, rv, R), q.astype(np.int64))
+    keys = rk & np.uint64((1 << 63) - 1)
+    assert np.array_equal(keys, np.flatnonzero(sym == 0).astype(np.uint64))
+    kinds = (rk >> np.uint64(63)).astype(bool)
+    assert np.array_equal(np.flatnonzero(outl), keys[kinds].astype(np.int64))
+
+
+def test_lorenzo2_closed_forms():
+    # second differences of a quadratic are constant (2a); of a line, zero; the
+    # first two residuals are q0 and q1 - 2 q0 (q[-1] = q[-2] = 0)
+    R = 512
+    k = np.arange(300, dtype=np.int64)
+    for a, b, c0 in [(1, -3, 7), (-2, 40, -100), (0, 5, 11)]:
+        q = (a * k * k + b * k + c0).astype(np.int32)
+        z = np.zeros(q.size, np.uint8)
+        P = np.zeros(q.size, np.float32)
+        sym, rk, rv = oracle.lorenzo(q, z, P, R, order=2)
+        assert (sym[2:].astype(np.int64) == 2 * a + R).all()
+        assert int(sym[0]) == c0 + R and int(sym[1]) == (a + b + c0) - 2 * c0 + R
+        assert rk.size == 0
+        # order 1 on the same line: constant first difference b (a = 0 case)
+        if a == 0:
+            s1, _, _ = oracle.lorenzo(q, z, P, R, order=1)
+            assert (s1[1:].astype(np.int64) == b + R).all()
+
+
+@pytest.mark.parametrize("cfg", [dict(eb=1e-3, eb_mode="abs"), dict(eb=1e-4, eb_mode="rel"),
+                                 dict(eb=1e-5, eb_mode="rel", radius=16)])
+def test_predictor_changes_the_stream_not_the_values(cfg):
+    # the codes are the same under either predictor, so the decoded values are
+    # bit-identical; only the symbols (and the size) differ
+    x = phantom.porous_cylinder(40, radius=15, texture=True, seed=4).numpy()
+    b1 = oracle.compress(x, predictor=1, **cfg)
+    b2 = oracle.compress(x, predictor=2, **cfg)
+    assert oracle.header(b1)["order"] == 1 and oracle.header(b2)["order"] == 2
+    y1 = oracle.decode(b1, x.shape, np.float32)
+    y2 = oracle.decode(b2, x.shape, np.float32)
+    assert np.array_equal(y1.view(np.uint32), y2.view(np.uint32))
+    D = oracle.mask(x, **cfg).astype(bool)
+    assert _exact_within(x[D], y2[D], oracle.header(b2)["eb_abs"])
+
+
 def test_histogram_is_bincount():
     sym = np.random.default_rng(1).integers(0, 64, 1000).astype(np.uint16)
     assert np.array_equal(oracle.histogram(sym, 64), np.bincount(sym, minlength=64))
