@@ -206,7 +206,7 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     wl = WORKLOADS[args.workload]
-    cfg = wl["cfg"]
+    cfg = dict(wl["cfg"], predictor=args.predictor)
     xs = make_inputs(args.workload, dev, seed=args.seed)
     torch.cuda.synchronize()
     in_bytes = sum(x.numel() * x.element_size() for x in xs)
@@ -435,6 +435,7 @@ def run_ours(args, rank, world, local_rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u16" if esz == 2 else "f32", "data": "synthetic",
             "config": {"workload": args.workload, "desc": wl["desc"], "items": len(xs),
+                       "predictor": args.predictor,
                        "bytes_in_per_step": in_bytes, "bytes_out_per_step": out_bytes,
                        "compression_ratio": round(in_bytes / max(out_bytes, 1), 3),
                        "path": ("roix_compress_batch: %d launches per 64 items" % LAUNCHES_PER_GROUP if
@@ -1054,7 +1055,7 @@ def run_slabs(args, rank, world, local_rank):
     cap = slab * n * n * 4 // 4 + (1 << 20)
     outs = [torch.empty(cap, dtype=torch.uint8, device=dev) for _ in range(ns)]
     sizes = torch.zeros(ns, dtype=torch.uint64, device=dev)
-    cfgs = [dict(sc["cfg"], eb=eb) for eb in sc["sweep"]]
+    cfgs = [dict(sc["cfg"], eb=eb, predictor=args.predictor) for eb in sc["sweep"]]
     # launch shapes tuned on one slab compressed as a volume of its own
     t0 = time.perf_counter()
     tuning = (rx.tune([x[:slab]], outs=outs[:1], caps=[cap], sizes=sizes[:1], reps=3,
@@ -1117,7 +1118,7 @@ def run_slabs(args, rank, world, local_rank):
 
     # end to end at one eb: the volume uploaded from pinned host memory into
     # the device buffer, compressed, every slab's container read back
-    cfg_e = dict(sc["cfg"], eb=sc["e2e_eb"])
+    cfg_e = dict(sc["cfg"], eb=sc["e2e_eb"], predictor=args.predictor)
     one(cfg_e)
     rx.sync(main)
     sz = [int(v) for v in sizes.cpu().numpy()]
@@ -1300,6 +1301,8 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--predictor", type=int, default=1, choices=[1, 2],
+                    help="Lorenzo order of the prediction (2: two-layer)")
     ap.add_argument("--tune", type=int, default=1,
                     help="1: launch shapes from the autotuner on the workload; 0: defaults")
     args = ap.parse_args()

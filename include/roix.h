@@ -98,6 +98,9 @@ typedef struct {
                        two in [256, 16384] (default 4096) */
   double fill;      /* value of non-retained voxels after decoding (uint16:
                        integer in [0, 65535]) */
+  uint32_t predictor; /* 1D Lorenzo order along the pixel section: 0 or 1 = first
+                       order (predict q[k-1]), 2 = two-layer Lorenzo (predict
+                       2 q[k-1] - q[k-2]); stored in the container header */
 } roix_params;
 
 /* Error-bound constants as computed on the device (written by roix_quantize,

@@ -50,7 +50,8 @@ class Eb(C.Structure):
 
 
 class Params(C.Structure):
-    _fields_ = [("radius", C.c_uint32), ("chunk", C.c_uint32), ("fill", C.c_double)]
+    _fields_ = [("radius", C.c_uint32), ("chunk", C.c_uint32), ("fill", C.c_double),
+                ("predictor", C.c_uint32)]
 
 
 class Item(C.Structure):
@@ -210,8 +211,8 @@ def eb_of(eb=1e-3, eb_mode="abs", **_) -> Eb:
     return Eb(0 if eb_mode == "abs" else 1, float(eb))
 
 
-def params_of(radius=512, chunk=4096, fill=0.0, **_) -> Params:
-    return Params(int(radius), int(chunk), float(fill))
+def params_of(radius=512, chunk=4096, fill=0.0, predictor=1, **_) -> Params:
+    return Params(int(radius), int(chunk), float(fill), int(predictor))
 
 
 def _stream(stream) -> int:

@@ -16,7 +16,7 @@ constexpr u32 kLutBits = 12;
 enum {
   P_OK = 0, P_N, P_NOUT, P_NB, P_NCH, P_NW, P_OFF_LENS, P_OFF_COUNTS, P_OFF_BOUNDS, P_OFF_OUTK,
   P_OFF_OUTV, P_OFF_CHUNKS, P_OFF_PAYLOAD, P_R, P_C, P_S, P_TWO_EB, P_EB_INT, P_DARK, P_FILL,
-  P_ZEROS, P_VOX
+  P_ZEROS, P_VOX, P_ORDER
 };
 
 // Naturally aligned read: header fields sit at multiples of their size and
@@ -43,13 +43,15 @@ __global__ void k_dec_header(Desc d, const uint8_t* in, u64 size, u32* status, u
   const uint16_t ver = rd<uint16_t>(in, 4);
   const u32 nx = rd<u32>(in, 8), ny = rd<u32>(in, 12), nz = rd<u32>(in, 16);
   const u32 R = rd<u32>(in, 80), C = rd<u32>(in, 84), lmax = rd<u32>(in, 88);
+  const u32 order = rd<u32>(in, 92);  // Lorenzo order (0 reads as 1)
   const u64 n = rd<u64>(in, 96), nout = rd<u64>(in, 104), nb = rd<u64>(in, 112);
   const u64 nch = rd<u64>(in, 120), nw = rd<u64>(in, 128);
   const double dark = rd<double>(in, 32), fill = rd<double>(in, 40);
   bool ok = ver == kVersion && in[6] == (uint8_t)d.dtype && nx == d.nx && ny == d.ny &&
             nz == d.nz && lmax == kLMax && R >= 2 && R <= kMaxRadius && C >= 256 &&
             C <= 16384 && (C & (C - 1)) == 0 && n <= d.N && nout <= n &&
-            nb <= d.rows * (d.nx + 1) && nch == (n + C - 1) / C && nch <= max_chunks;
+            nb <= d.rows * (d.nx + 1) && nch == (n + C - 1) / C && nch <= max_chunks &&
+            order <= 2;
   if (ok && d.dtype == ROIX_U16)
     ok = fill >= 0.0 && fill <= 65535.0 && fill == floor(fill) && dark >= 0.0 &&
          dark <= 65535.0 && dark == floor(dark);
@@ -86,6 +88,7 @@ __global__ void k_dec_header(Desc d, const uint8_t* in, u64 size, u32* status, u
   plan[P_EB_INT] = (u64)(int64_t)rd<int32_t>(in, 76);
   plan[P_DARK] = (u64)(int64_t)dark;
   plan[P_FILL] = __double_as_longlong(fill);
+  plan[P_ORDER] = order == 2 ? 2 : 1;
   plan[P_OK] = 1;
 }
 
@@ -299,6 +302,11 @@ __global__ void __launch_bounds__(kThreads) k_dec_symbols(const uint8_t* in, u32
     const u64 k0 = j * C, k1 = min(n, k0 + C);
     bool reset = false, bad = false;
     long long acc = 0;
+    // order 2: the chunk's affine map of the state (c[k-1], c[k-2]), composed
+    // element by element in wrapping 64-bit arithmetic (exact modulo 2^64, and
+    // every true code fits in 32 bits)
+    const bool two = plan[P_ORDER] == 2;
+    u64 m11 = 1, m12 = 0, m21 = 0, m22 = 1, o1 = 0, o2 = 0;
     for (u64 k = k0; k < k1; ++k) {
       while (have <= 32 && wp < w1) {
         buf |= (u64)words[wp++] << (32 - have);
@@ -329,6 +337,29 @@ __global__ void __launch_bounds__(kThreads) k_dec_symbols(const uint8_t* in, u32
       buf <<= l;
       have -= (int)l;
       sym[k] = (uint16_t)s;
+      if (two) {
+        // element map: c' = a c1 + b c2 + v, (c1, c2) -> (c', c1); non-record:
+        // (a, b, v) = (2, -1, s - R); record: (0, 0, payload) (set below)
+        u64 ea = 2, eb = ~0ull, ev = (u64)((long long)s - (long long)R);
+        if (!s) {
+          u64 key;
+          u32 val;
+          if (!find_record(in, plan, k, key, val)) {
+            bad = true;
+            break;
+          }
+          ea = 0;
+          eb = 0;
+          ev = (key >> 63) ? 0ull : (u64)(long long)(int32_t)val;
+        }
+        const u64 n11 = ea * m11 + eb * m21, n12 = ea * m12 + eb * m22, no1 = ea * o1 + eb * o2 + ev;
+        m21 = m11;
+        m22 = m12;
+        o2 = o1;
+        m11 = n11;
+        m12 = n12;
+        o1 = no1;
+      }
       if (s) {
         acc += (long long)s - (long long)R;
       } else {
@@ -347,8 +378,18 @@ __global__ void __launch_bounds__(kThreads) k_dec_symbols(const uint8_t* in, u32
       corrupt(status, plan);
       break;
     }
-    agg[2 * j] = reset ? 1ull : 0ull;
-    agg[2 * j + 1] = (u64)acc;
+    if (two) {
+      u64* g = agg + 6 * j;
+      g[0] = m11;
+      g[1] = m12;
+      g[2] = m21;
+      g[3] = m22;
+      g[4] = o1;
+      g[5] = o2;
+    } else {
+      agg[2 * j] = reset ? 1ull : 0ull;
+      agg[2 * j + 1] = (u64)acc;
+    }
   }
   zeros = warp_sum(zeros);
   if ((threadIdx.x & 31) == 0 && zeros) atomicAdd((unsigned long long*)&plan[P_ZEROS], zeros);
@@ -360,7 +401,7 @@ __global__ void __launch_bounds__(1024) k_dec_carry(u32* status, u64* plan, cons
   __shared__ u64 sv[1024];
   __shared__ u32 sr[1024];
   __shared__ u64 s_carry;
-  if (!plan[P_OK]) return;
+  if (!plan[P_OK] || plan[P_ORDER] != 1) return;
   const u64 nch = plan[P_NCH];
   if (threadIdx.x == 0) {
     s_carry = 0;
@@ -421,7 +462,7 @@ __global__ void __launch_bounds__(kThreads) k_dec_values(const uint8_t* in, u32*
   __shared__ u64 sv[kThreads];
   __shared__ u32 sr[kThreads];
   __shared__ u64 s_run;
-  if (!plan[P_OK]) return;
+  if (!plan[P_OK] || plan[P_ORDER] != 1) return;
   const u64 n = plan[P_N], nch = plan[P_NCH];
   const u32 C = (u32)plan[P_C], R = (u32)plan[P_R];
   const float two_eb = __uint_as_float((u32)plan[P_TWO_EB]);
@@ -492,6 +533,115 @@ __global__ void __launch_bounds__(kThreads) k_dec_values(const uint8_t* in, u32*
   }
 }
 
+// ------------------------------------------------- two-layer Lorenzo
+// Composition of the chunks' affine maps in order (one block, Hillis-Steele
+// per 1024 chunks, carried across): chunk j starts from the state that the
+// maps of chunks 0..j-1 give the zero state, i.e. the offset of their
+// composition.
+struct Map2 {
+  u64 m11, m12, m21, m22, o1, o2;
+};
+__device__ __forceinline__ Map2 after(const Map2& g, const Map2& f) {  // g after f
+  Map2 r;
+  r.m11 = g.m11 * f.m11 + g.m12 * f.m21;
+  r.m12 = g.m11 * f.m12 + g.m12 * f.m22;
+  r.m21 = g.m21 * f.m11 + g.m22 * f.m21;
+  r.m22 = g.m21 * f.m12 + g.m22 * f.m22;
+  r.o1 = g.m11 * f.o1 + g.m12 * f.o2 + g.o1;
+  r.o2 = g.m21 * f.o1 + g.m22 * f.o2 + g.o2;
+  return r;
+}
+
+__global__ void __launch_bounds__(1024) k_dec_carry2(u32* status, u64* plan, const u64* agg,
+                                                     u64* carry) {
+  __shared__ Map2 sm[1024];
+  __shared__ Map2 s_run;
+  if (!plan[P_OK] || plan[P_ORDER] != 2) return;
+  const u64 nch = plan[P_NCH];
+  if (threadIdx.x == 0) {
+    s_run = Map2{1, 0, 0, 1, 0, 0};
+    if (plan[P_ZEROS] != plan[P_NOUT]) corrupt(status, plan);
+  }
+  __syncthreads();
+  for (u64 c0 = 0; c0 < nch; c0 += 1024) {
+    const u64 j = c0 + threadIdx.x;
+    Map2 f{1, 0, 0, 1, 0, 0};
+    if (j < nch) {
+      const u64* g = agg + 6 * j;
+      f = Map2{g[0], g[1], g[2], g[3], g[4], g[5]};
+    }
+    sm[threadIdx.x] = f;
+    __syncthreads();
+    for (u32 dd = 1; dd < 1024; dd <<= 1) {  // inclusive: map of chunks c0..j
+      Map2 p{1, 0, 0, 1, 0, 0};
+      const bool has = threadIdx.x >= dd;
+      if (has) p = sm[threadIdx.x - dd];
+      __syncthreads();
+      if (has) {
+        f = after(f, p);
+        sm[threadIdx.x] = f;
+      }
+      __syncthreads();
+    }
+    const Map2 run = s_run;
+    const Map2 ex = threadIdx.x ? after(sm[threadIdx.x - 1], run) : run;
+    if (j < nch) {
+      carry[2 * j] = ex.o1;
+      carry[2 * j + 1] = ex.o2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 1023) s_run = after(sm[1023], run);
+    __syncthreads();
+  }
+}
+
+// One thread per chunk: codes from the chunk's starting state, c = 2 c1 - c2 +
+// d (records set c), dequantised.
+template <typename TV>
+__global__ void __launch_bounds__(kThreads) k_dec_values2(const uint8_t* in, u32* status,
+                                                          u64* plan, const uint16_t* sym,
+                                                          const u64* carry, TV* vals) {
+  if (!plan[P_OK] || plan[P_ORDER] != 2) return;
+  const u64 n = plan[P_N], nch = plan[P_NCH];
+  const u32 C = (u32)plan[P_C], R = (u32)plan[P_R];
+  const float two_eb = __uint_as_float((u32)plan[P_TWO_EB]);
+  const long long eb_int = (long long)plan[P_EB_INT], dark = (long long)plan[P_DARK];
+  for (u64 j = (u64)blockIdx.x * blockDim.x + threadIdx.x; j < nch;
+       j += (u64)gridDim.x * blockDim.x) {
+    u64 c1 = carry[2 * j], c2 = carry[2 * j + 1];
+    const u64 k0 = j * C, k1 = min(n, k0 + C);
+    for (u64 k = k0; k < k1; ++k) {
+      const u32 s = sym[k];
+      u64 c;
+      bool raw = false;
+      u32 rawbits = 0;
+      if (s) {
+        c = 2 * c1 - c2 + (u64)((long long)s - (long long)R);
+      } else {
+        u64 key;
+        u32 val;
+        if (!find_record(in, plan, k, key, val)) {
+          corrupt(status, plan);
+          return;
+        }
+        raw = (key >> 63) != 0;
+        rawbits = val;
+        c = raw ? 0ull : (u64)(long long)(int32_t)val;
+      }
+      const long long cv = (long long)c;
+      if constexpr (sizeof(TV) == 4) {
+        vals[k] = raw ? __uint_as_float(rawbits) : __fmul_rn(__int2float_rn((int)cv), two_eb);
+      } else {
+        long long x = (eb_int == 0 ? cv : 2 * eb_int * cv) + dark;
+        x = x < 0 ? 0 : (x > 65535 ? 65535 : x);
+        vals[k] = (TV)x;
+      }
+      c2 = c1;
+      c1 = c;
+    }
+  }
+}
+
 // ----------------------------------------------------------------- scatter
 // One warp per row: gaps get the fill value, runs their values in order.
 template <typename TV>
@@ -541,13 +691,20 @@ void launch_decode(const Launch& L, const Desc& d, const uint8_t* in, u64 size, 
     unsigned g = (unsigned)umin((max_chunks + kThreads - 1) / kThreads, (u64)L.sms * 4);
     k_dec_symbols<<<g, kThreads, 0, L.stream>>>(in, ws.status, ws.plan, tab, ws.sym, ws.agg);
     k_dec_carry<<<1, 1024, 0, L.stream>>>(ws.status, ws.plan, ws.agg, ws.carry);
+    k_dec_carry2<<<1, 1024, 0, L.stream>>>(ws.status, ws.plan, ws.agg, ws.carry);
     unsigned gv = (unsigned)umin(max_chunks, (u64)L.sms * 8);
-    if (d.dtype == ROIX_F32)
+    unsigned g2 = (unsigned)umin((max_chunks + kThreads - 1) / kThreads, (u64)L.sms * 8);
+    if (d.dtype == ROIX_F32) {
       k_dec_values<float><<<gv, kThreads, 0, L.stream>>>(in, ws.status, ws.plan, ws.sym, ws.carry,
                                                           (float*)ws.vals);
-    else
+      k_dec_values2<float><<<g2, kThreads, 0, L.stream>>>(in, ws.status, ws.plan, ws.sym,
+                                                           ws.carry, (float*)ws.vals);
+    } else {
       k_dec_values<unsigned short><<<gv, kThreads, 0, L.stream>>>(
           in, ws.status, ws.plan, ws.sym, ws.carry, (unsigned short*)ws.vals);
+      k_dec_values2<unsigned short><<<g2, kThreads, 0, L.stream>>>(
+          in, ws.status, ws.plan, ws.sym, ws.carry, (unsigned short*)ws.vals);
+    }
   }
   if (d.rows) {
     unsigned g = (unsigned)umin((d.rows + 7) / 8, (u64)L.sms * 8);

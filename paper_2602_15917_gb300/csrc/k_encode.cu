@@ -140,6 +140,14 @@ struct Src {
   }
 };
 
+// Symbol of the two-layer residual d = c - (2 p1 - p2), exact in 64 bits: d + R
+// when -R < d < R, else 0.
+__device__ __forceinline__ u32 symbol2_of(int c, int p1, int p2, bool out, u32 R) {
+  if (out) return 0u;
+  const long long d = (long long)c - (2ll * p1 - (long long)p2);
+  return (d > -(long long)R && d < (long long)R) ? (u32)(d + R) : 0u;
+}
+
 // Symbol of a delta: d + R when -R < d < R, else 0. Codes lie in
 // [-2^30, 2^30], so the true delta lies in [-2^31, 2^31]; its two's-complement
 // wrap to 0x80000000 at the extremes still fails the unsigned range test.
@@ -273,7 +281,7 @@ __device__ __forceinline__ void flush_hist(u32* h, unsigned long long* g, u32 S,
 // counted here, per pack chunk (an atomic per lane and step that has one);
 // they are written by k_records once their offsets are known, so that no
 // segment waits for another.
-template <typename TV, bool FROM_Q>
+template <typename TV, bool FROM_Q, int ORDER>
 __global__ void __launch_bounds__(kThreads) k_symbols(const __grid_constant__ Batch B) {
   using Vec = SymVec<TV, FROM_Q>;
   constexpr int V = Vec::V;
@@ -324,12 +332,14 @@ __global__ void __launch_bounds__(kThreads) k_symbols(const __grid_constant__ Ba
     const u64 t = gt - pre[item];
     const u64 base = t * kQuantTile;
     uint16_t* __restrict__ sym = I.sym;
-    int carry = 0;  // code of value base - 1 (0 for an outlier or none)
+    int carry = 0, carry2 = 0;  // codes of values base - 1, base - 2 (0: outlier or none)
     if (lane == 0 && base > 0) {
       bool o;
       carry = src.code(base - 1, o);
+      if (ORDER == 2 && base > 1) carry2 = src.code(base - 2, o);
     }
     carry = __shfl_sync(0xffffffffu, carry, 0);
+    if (ORDER == 2) carry2 = __shfl_sync(0xffffffffu, carry2, 0);
     u32* __restrict__ crec = I.crec;
     u32* __restrict__ rbits = I.rbits;
     // one step: V codes per lane, deltas, symbols, histogram, record bits;
@@ -348,14 +358,24 @@ __global__ void __launch_bounds__(kThreads) k_symbols(const __grid_constant__ Ba
         }
       }
       int prev = __shfl_up_sync(0xffffffffu, c[V - 1], 1);
-      if (lane == 0) prev = carry;
+      int prev2 = 0;
+      if constexpr (ORDER == 2) prev2 = __shfl_up_sync(0xffffffffu, c[V - 2], 1);
+      if (lane == 0) {
+        prev = carry;
+        prev2 = carry2;
+      }
+      if constexpr (ORDER == 2) carry2 = __shfl_sync(0xffffffffu, c[V - 2], 31);
       carry = __shfl_sync(0xffffffffu, c[V - 1], 31);
       u32 sv[V];
       u32 rb = 0;
 #pragma unroll
       for (int j = 0; j < V; ++j) {
         const bool in = !GUARD || k0 + j < n;
-        sv[j] = symbol_of(c[j], j ? c[j - 1] : prev, o[j], R_);
+        if constexpr (ORDER == 2)
+          sv[j] = symbol2_of(c[j], j ? c[j - 1] : prev, j > 1 ? c[j - 2] : (j ? prev : prev2),
+                             o[j], R_);
+        else
+          sv[j] = symbol_of(c[j], j ? c[j - 1] : prev, o[j], R_);
         if (in) {
           atomicAdd(&h[sv[j]], 1u);
           rb |= (sv[j] == 0u ? 1u : 0u) << j;
@@ -1035,6 +1055,7 @@ __global__ void __launch_bounds__(kThreads) k_finalize(const __grid_constant__ B
     put_bytes(h, 72, &e.bound, 4);
     put_bytes(h, 76, &e.eb_int, 4);
     put_bytes(h, 80, &d.R, 4);
+    put_bytes(h, 92, &d.order, 4);
     put_bytes(h, 84, &d.C, 4);
     const u32 lmax = kLMax;
     put_bytes(h, 88, &lmax, 4);
@@ -1151,11 +1172,21 @@ void launch_symbols(const Launch& L, const Batch& B, u64 tiles_cap) {
     kernel<<<(unsigned)grid, kThreads, smem, L.stream>>>(B);
   };
   if (B.c.dtype == ROIX_F32) {
-    if (from_q) run(k_symbols<float, true>);
-    else run(k_symbols<float, false>);
+    if (B.c.order == 2) {
+      if (from_q) run(k_symbols<float, true, 2>);
+      else run(k_symbols<float, false, 2>);
+    } else {
+      if (from_q) run(k_symbols<float, true, 1>);
+      else run(k_symbols<float, false, 1>);
+    }
   } else {
-    if (from_q) run(k_symbols<unsigned short, true>);
-    else run(k_symbols<unsigned short, false>);
+    if (B.c.order == 2) {
+      if (from_q) run(k_symbols<unsigned short, true, 2>);
+      else run(k_symbols<unsigned short, false, 2>);
+    } else {
+      if (from_q) run(k_symbols<unsigned short, true, 1>);
+      else run(k_symbols<unsigned short, false, 1>);
+    }
   }
 }
 

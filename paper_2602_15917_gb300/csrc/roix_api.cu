@@ -168,10 +168,12 @@ roix_status roix::make_desc(roix_ctx* ctx, roix_dtype dtype, roix_dims dims, con
     if (dtype == ROIX_U16 &&
         !(prm->fill >= 0.0 && prm->fill <= 65535.0 && prm->fill == std::floor(prm->fill)))
       return fail(ctx, ROIX_EINVAL, "params.fill must be an integer in [0, 65535] for uint16");
+    if (prm->predictor > 2) return fail(ctx, ROIX_EINVAL, "params.predictor must be 0, 1 or 2");
     d->R = prm->radius;
     d->S = 2 * prm->radius;
     d->C = C;
     d->fill = prm->fill;
+    d->order = prm->predictor == 2 ? 2u : 1u;
   }
   return ROIX_OK;
 }
@@ -1018,8 +1020,8 @@ roix_status roix_decode(roix_ctx* ctx, const void* in, uint64_t size, void* out,
   const size_t db = a.take(8 * 2 * (row_tiles + 1));
   const size_t dv = a.take(8 * 2 * (row_tiles + 1));
   const size_t sym = a.take(2 * d.N + 16);
-  const size_t agg = a.take(16 * (max_chunks + 1));
-  const size_t carry = a.take(8 * (max_chunks + 1));
+  const size_t agg = a.take(48 * (max_chunks + 1));    // order 1: 2 words a chunk, order 2: 6
+  const size_t carry = a.take(16 * (max_chunks + 1));  // order 1: 1 word a chunk, order 2: 2
   const size_t vals = a.take(esz * d.N + 16);
   const size_t rb = a.take(8 * (d.rows + 1));
   const size_t rv = a.take(8 * (d.rows + 1));

@@ -332,6 +332,7 @@ struct Desc {
   double eb_value;
   u32 R, S, C;
   u32 front_words;             // compaction tile size (mask words), from the tuning
+  u32 order;                   // Lorenzo order of the prediction: 1 or 2
 };
 
 // ------------------------------------------------------------------ batches

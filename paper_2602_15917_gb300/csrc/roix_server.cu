@@ -33,9 +33,15 @@ namespace {
 using Clock = std::chrono::steady_clock;
 
 bool same_settings(const roix_request& a, const roix_request& b) {
-  return a.dtype == b.dtype && std::memcmp(&a.roi, &b.roi, sizeof(roix_roi)) == 0 &&
-         std::memcmp(&a.eb, &b.eb, sizeof(roix_eb)) == 0 &&
-         std::memcmp(&a.params, &b.params, sizeof(roix_params)) == 0;
+  // field by field: the structs may carry padding bytes of any value
+  const roix_roi &ra = a.roi, &rb = b.roi;
+  return a.dtype == b.dtype && ra.cmp == rb.cmp && ra.keep == rb.keep &&
+         ra.connectivity == rb.connectivity && ra.dilate == rb.dilate &&
+         std::memcmp(&ra.threshold, &rb.threshold, 8) == 0 &&
+         std::memcmp(&ra.dark, &rb.dark, 8) == 0 && a.eb.mode == b.eb.mode &&
+         std::memcmp(&a.eb.value, &b.eb.value, 8) == 0 && a.params.radius == b.params.radius &&
+         a.params.chunk == b.params.chunk && std::memcmp(&a.params.fill, &b.params.fill, 8) == 0 &&
+         (a.params.predictor == 2) == (b.params.predictor == 2);
 }
 
 struct Pending {

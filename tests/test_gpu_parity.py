@@ -427,3 +427,73 @@ def test_scans_over_more_tiles_and_chunks_than_one_block(rx):
             assert h["n_chunks"] > 1024
     finally:
         rx.set_tuning(**default)
+
+
+# The two-layer Lorenzo (predictor = 2): containers equal the oracle's, the
+# decoder inverts it bit for bit.
+P2_CASES = [
+    ("ellipsoids48", lambda: phantom.ellipsoids(48, seed=21).numpy(), {}),
+    ("ragged_rel", lambda: phantom.porous_cylinder(40, radius=15, texture=True, seed=2).numpy(),
+     dict(eb=1e-4, eb_mode="rel")),
+    ("tight_R2", lambda: phantom.ellipsoids(shape=(9, 20, 33), seed=22).numpy(),
+     dict(eb=1e-5, radius=2)),
+    ("chunk256", lambda: phantom.ellipsoids(40, seed=23).numpy(), dict(chunk=256, radius=64)),
+    ("chunk16384", lambda: phantom.ellipsoids(48, seed=24).numpy(), dict(chunk=16384)),
+    ("noise", lambda: phantom.random_field((6, 20, 90), seed=25, smooth=False),
+     dict(threshold=-0.5, eb=1e-2)),
+    ("all_roi", lambda: phantom.random_field((4, 9, 70), seed=26), dict(threshold=-1e30)),
+]
+
+
+@pytest.mark.parametrize("name,make,cfg", P2_CASES, ids=[c[0] for c in P2_CASES])
+def test_predictor2_containers_and_decode(rx, name, make, cfg):
+    x = make()
+    cfg = dict(cfg, predictor=2)
+    ref, got = _compress_both(rx, x, **cfg)
+    _assert_same_container(ref, got)
+    assert oracle.header(got)["order"] == 2
+    y = rx.decode(torch.from_numpy(got).cuda(), x.shape, torch.float32)
+    rx.sync()
+    assert np.array_equal(y.cpu().numpy().view(np.uint32),
+                          oracle.decode(ref, x.shape, np.float32).view(np.uint32))
+
+
+def test_predictor2_specials_uint16_staged_batch_slabs(rx):
+    f = phantom.ellipsoids(shape=(6, 16, 40), seed=27).numpy()
+    f[2, 3, 5:10] = [np.nan, np.inf, -np.inf, 3e38, 1e-42]
+    cfg = dict(eb=1e-3, threshold=-1e30, predictor=2)
+    ref, got = _compress_both(rx, f, **cfg)
+    _assert_same_container(ref, got)
+    y = rx.decode(torch.from_numpy(got).cuda(), f.shape, torch.float32)
+    rx.sync()
+    assert np.array_equal(y.cpu().numpy().view(np.uint32),
+                          oracle.decode(ref, f.shape, np.float32).view(np.uint32))
+    # uint16
+    p = phantom.projection(150, 3, seed=9).numpy()
+    cu = dict(eb=4, cmp="lt", threshold=57000, dark=100, dilate=0, fill=60100, predictor=2)
+    ref, got = _compress_both(rx, p, **cu)
+    _assert_same_container(ref, got)
+    y = rx.decode(torch.from_numpy(got).cuda(), p.shape, torch.uint16)
+    rx.sync()
+    assert np.array_equal(y.cpu().numpy(), oracle.decode(ref, p.shape, np.uint16))
+    # staged chain (codes first) gives the same bytes
+    xt = torch.from_numpy(f).cuda()
+    mask, _ = rx.extract_roi(xt, **cfg)
+    pixels, counts, bounds, sizes = rx.compact(xt, mask)
+    q, ob, info = rx.quantize(pixels, n_cap=f.size, n_dev=sizes[:1], **cfg)
+    out, size = rx.encode(q, ob, pixels, f.size, sizes, counts, bounds, info, f.shape,
+                          torch.float32, **cfg)
+    rx.sync()
+    _assert_same_container(oracle.compress(f, **cfg), out[:int(size.item())].cpu().numpy())
+    # batch and z-slabs
+    xs = [phantom.ellipsoids(shape=(5, 20, 30 + 7 * i), seed=30 + i).numpy() for i in range(3)]
+    outs, sz = rx.compress_batch([torch.from_numpy(v).cuda() for v in xs], eb=1e-3, predictor=2)
+    rx.sync()
+    for v, o, s_ in zip(xs, outs, sz.cpu().numpy()):
+        _assert_same_container(oracle.compress(v, eb=1e-3, predictor=2), o[:int(s_)].cpu().numpy())
+    v = phantom.porous_cylinder(32, radius=12, seed=5).numpy()
+    so, ss = rx.compress_slabs(torch.from_numpy(v).cuda(), 7, eb=1e-4, eb_mode="rel", predictor=2)
+    rx.sync()
+    for r_, o, s_ in zip(oracle.compress_slabs(v, 7, eb=1e-4, eb_mode="rel", predictor=2), so,
+                         ss.cpu().numpy()):
+        _assert_same_container(r_, o[:int(s_)].cpu().numpy())
