@@ -12,15 +12,39 @@ namespace {
 
 constexpr int kThreads = 256;
 
-__device__ __forceinline__ bool pass_f32(float x, const Desc& d) {
-  if (d.thr_never) return false;
-  return d.cmp == 0 ? (x > d.thr_f) : (x < d.thr_f);
+// Threshold test (Sec. 4.1.1) in one form for either direction. float32: x
+// passes when s x > t, s = -1 turning x < thr into -x > -thr exactly (NaN never
+// passes; no threshold gives t = +inf). Integer values: the values above
+// dark + thr, or below it, are one interval [lo, lo + span] of [0, 65535], so
+// raw passes when raw - lo, taken unsigned, is at most span (none: lo = 65536,
+// span = 0). Formed once per work unit from the settings.
+struct PassTest {
+  float s, t;
+  u32 lo, span;
+};
+
+__device__ __forceinline__ PassTest pass_test(const Desc& d) {
+  PassTest p;
+  p.s = d.cmp == 0 ? 1.0f : -1.0f;
+  p.t = d.thr_never ? __int_as_float(0x7f800000) : (d.cmp == 0 ? d.thr_f : -d.thr_f);
+  long long lo = 0, hi = 65535;
+  if (d.cmp == 0) lo = (long long)d.dark + d.thr_i + 1;
+  else hi = (long long)d.dark + d.thr_i - 1;
+  if (lo < 0) lo = 0;
+  if (hi > 65535) hi = 65535;
+  if (d.thr_never || lo > hi) {
+    p.lo = 65536u;
+    p.span = 0u;
+  } else {
+    p.lo = (u32)lo;
+    p.span = (u32)(hi - lo);
+  }
+  return p;
 }
-__device__ __forceinline__ bool pass_u16(unsigned raw, const Desc& d) {
-  if (d.thr_never) return false;
-  int v = (int)raw - d.dark;
-  return d.cmp == 0 ? (v > d.thr_i) : (v < d.thr_i);
+__device__ __forceinline__ bool passes(const PassTest& p, float x) {
+  return __fmul_rn(x, p.s) > p.t;
 }
+__device__ __forceinline__ bool passes(const PassTest& p, u32 raw) { return raw - p.lo <= p.span; }
 
 __device__ __forceinline__ u32 last_mask(const Desc& d, u64 w) {
   u32 rem = (u32)(d.nx & 31);
@@ -35,6 +59,7 @@ __device__ __forceinline__ u32 last_mask(const Desc& d, u64 w) {
 template <typename TV>
 __device__ __forceinline__ void thr_segment(const Desc& d, const TV* __restrict__ in,
                                             u32* __restrict__ T, u64 r, u32 x0, int lane) {
+  const PassTest pt = pass_test(d);
   const u32 nx = (u32)d.nx;
   const u32 nw = min(32u, (nx - x0 + 31) >> 5);
   const TV* row = in + r * d.nx;
@@ -50,8 +75,8 @@ __device__ __forceinline__ void thr_segment(const Desc& d, const TV* __restrict_
     for (int j = 0; j < 8; ++j) {
       const u32 x = x0 + (i + j) * 32 + lane;
       bool p;
-      if constexpr (sizeof(TV) == 4) p = pass_f32(v[j], d);
-      else p = pass_u16(v[j], d);
+      if constexpr (sizeof(TV) == 4) p = passes(pt, v[j]);
+      else p = passes(pt, (u32)v[j]);
       const u32 bl = __ballot_sync(0xffffffffu, p && x < nx);
       if (lane == (int)(i + j)) mine = bl;
     }
@@ -67,6 +92,7 @@ __device__ __forceinline__ void thr_segment(const Desc& d, const TV* __restrict_
 template <typename TV>
 __device__ __forceinline__ void thr_segment_vec(const Desc& d, const TV* __restrict__ in,
                                                 u32* __restrict__ T, u64 r, u32 x0, int lane) {
+  const PassTest pt = pass_test(d);
   constexpr int kPer = 16 / sizeof(TV);  // voxels per lane and load
   constexpr int kLoads = 1024 / (32 * kPer);      // loads per segment
   constexpr int kLanesPerWord = 32 / kPer;        // lanes contributing to one word
@@ -87,16 +113,16 @@ __device__ __forceinline__ void thr_segment_vec(const Desc& d, const TV* __restr
     u32 bits = 0;
     if (x < nx) {
       if constexpr (sizeof(TV) == 4) {
-        bits = (pass_f32(__uint_as_float(v[i].x), d) ? 1u : 0u) |
-               (pass_f32(__uint_as_float(v[i].y), d) ? 2u : 0u) |
-               (pass_f32(__uint_as_float(v[i].z), d) ? 4u : 0u) |
-               (pass_f32(__uint_as_float(v[i].w), d) ? 8u : 0u);
+        bits = (passes(pt, __uint_as_float(v[i].x)) ? 1u : 0u) |
+               (passes(pt, __uint_as_float(v[i].y)) ? 2u : 0u) |
+               (passes(pt, __uint_as_float(v[i].z)) ? 4u : 0u) |
+               (passes(pt, __uint_as_float(v[i].w)) ? 8u : 0u);
       } else if constexpr (sizeof(TV) == 2) {
         const u32 q[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          bits |= (pass_u16(q[k] & 0xffffu, d) ? 1u : 0u) << (2 * k);
-          bits |= (pass_u16(q[k] >> 16, d) ? 1u : 0u) << (2 * k + 1);
+          bits |= (passes(pt, q[k] & 0xffffu) ? 1u : 0u) << (2 * k);
+          bits |= (passes(pt, q[k] >> 16) ? 1u : 0u) << (2 * k + 1);
         }
       } else {
         const u32 q[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
@@ -104,7 +130,7 @@ __device__ __forceinline__ void thr_segment_vec(const Desc& d, const TV* __restr
         for (int k = 0; k < 4; ++k)
 #pragma unroll
           for (int b = 0; b < 4; ++b)
-            bits |= (pass_u16((q[k] >> (8 * b)) & 0xffu, d) ? 1u : 0u) << (4 * k + b);
+            bits |= (passes(pt, (q[k] >> (8 * b)) & 0xffu) ? 1u : 0u) << (4 * k + b);
       }
     }
     u32 t = bits << (kPer * (lane & (kLanesPerWord - 1)));
@@ -130,6 +156,7 @@ constexpr u32 kFlatSpan = 1024;
 template <typename TV>
 __device__ __forceinline__ u32 flat_words(const Desc& d, const TV* __restrict__ in, u64 a,
                                           int lane) {
+  const PassTest pt = pass_test(d);
   constexpr int kPer = 16 / sizeof(TV);
   constexpr int kLoads = 1024 / (32 * kPer);
   constexpr int kLanesPerWord = 32 / kPer;
@@ -161,16 +188,16 @@ __device__ __forceinline__ u32 flat_words(const Desc& d, const TV* __restrict__ 
     const u64 x = a + (u64)i * (32 * kPer) + (u64)lane * kPer;
     u32 bits = 0;
     if constexpr (sizeof(TV) == 4) {
-      bits = (pass_f32(__uint_as_float(v[i].x), d) ? 1u : 0u) |
-             (pass_f32(__uint_as_float(v[i].y), d) ? 2u : 0u) |
-             (pass_f32(__uint_as_float(v[i].z), d) ? 4u : 0u) |
-             (pass_f32(__uint_as_float(v[i].w), d) ? 8u : 0u);
+      bits = (passes(pt, __uint_as_float(v[i].x)) ? 1u : 0u) |
+             (passes(pt, __uint_as_float(v[i].y)) ? 2u : 0u) |
+             (passes(pt, __uint_as_float(v[i].z)) ? 4u : 0u) |
+             (passes(pt, __uint_as_float(v[i].w)) ? 8u : 0u);
     } else if constexpr (sizeof(TV) == 2) {
       const u32 q[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        bits |= (pass_u16(q[k] & 0xffffu, d) ? 1u : 0u) << (2 * k);
-        bits |= (pass_u16(q[k] >> 16, d) ? 1u : 0u) << (2 * k + 1);
+        bits |= (passes(pt, q[k] & 0xffffu) ? 1u : 0u) << (2 * k);
+        bits |= (passes(pt, q[k] >> 16) ? 1u : 0u) << (2 * k + 1);
       }
     } else {
       const u32 q[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
@@ -178,7 +205,7 @@ __device__ __forceinline__ u32 flat_words(const Desc& d, const TV* __restrict__ 
       for (int k = 0; k < 4; ++k)
 #pragma unroll
         for (int b = 0; b < 4; ++b)
-          bits |= (pass_u16((q[k] >> (8 * b)) & 0xffu, d) ? 1u : 0u) << (4 * k + b);
+          bits |= (passes(pt, (q[k] >> (8 * b)) & 0xffu) ? 1u : 0u) << (4 * k + b);
     }
     if (x + kPer > N) bits &= x < N ? (1u << (u32)(N - x)) - 1u : 0u;  // voxels past the end
     u32 t = bits << (kPer * (lane & (kLanesPerWord - 1)));
@@ -244,14 +271,12 @@ __device__ __forceinline__ void flat_emit(const Desc& d, u32* __restrict__ T, u6
 
 template <typename TV>
 __device__ __forceinline__ void thr_flat_span(const Desc& d, const TV* __restrict__ in,
-                                              u32* __restrict__ T, u64 span, int lane) {
+                                              u32* __restrict__ T, u64 span, u64 m_nx,
+                                              int lane) {
+  const PassTest pt = pass_test(d);
   const u64 N = d.rows * d.nx;
   const u64 a = span * kFlatSpan;
-  // the row holding voxel a: a / nx by a binary64 quotient (exact to within one
-  // for a < 2^52), then corrected
-  u64 r = (u64)((double)a / (double)d.nx);
-  while (r * d.nx > a) --r;
-  while ((r + 1) * d.nx <= a) ++r;
+  const u64 r = div_by(a, d.nx, m_nx);  // the row holding voxel a
   const int rel0 = (int)((long long)(r * d.nx) - (long long)a);
   const int lim = (int)umin(1024, N - a);
   const u32 F = flat_words<TV>(d, in, a, lane);
@@ -259,8 +284,8 @@ __device__ __forceinline__ void thr_flat_span(const Desc& d, const TV* __restric
   const u64 x = a + 1024 + lane;
   bool p = false;
   if (x < N) {
-    if constexpr (sizeof(TV) == 4) p = pass_f32(__ldg(in + x), d);
-    else p = pass_u16(__ldg(in + x), d);
+    if constexpr (sizeof(TV) == 4) p = passes(pt, __ldg(in + x));
+    else p = passes(pt, (u32)__ldg(in + x));
   }
   const u32 f32 = __ballot_sync(0xffffffffu, p);
   flat_emit(d, T, a, F, f32, r, rel0, lim, lane);
@@ -270,7 +295,7 @@ __device__ __forceinline__ void thr_flat_span(const Desc& d, const TV* __restric
 // segments of the row-form items, or kFlatSpan-voxel steps of the flat-form
 // items (FLAT; a launch of its own, so that each form keeps its registers).
 template <typename TV, bool FLAT>
-__global__ void __launch_bounds__(kThreads, FLAT ? 4 : 1) k_threshold(const __grid_constant__ Batch B) {
+__global__ void __launch_bounds__(kThreads, 4) k_threshold(const __grid_constant__ Batch B) {
   const int lane = threadIdx.x & 31;
   const u64 warp = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
@@ -288,10 +313,10 @@ __global__ void __launch_bounds__(kThreads, FLAT ? 4 : 1) k_threshold(const __gr
     const Item& I = B.it[i];
     const Desc d = desc_of(B, I);
     if constexpr (FLAT) {
-      thr_flat_span<TV>(d, (const TV*)I.in, I.T, local, lane);
+      thr_flat_span<TV>(d, (const TV*)I.in, I.T, local, I.m_nx, lane);
     } else {
       const u64 spr = (I.nx + 1023) >> 10;
-      const u64 r = local / spr;
+      const u64 r = spr == 1 ? local : div_by(local, spr, I.m_spr);
       const u32 x0 = (u32)(local - r * spr) << 10;
       if (I.vec) thr_segment_vec<TV>(d, (const TV*)I.in, I.T, r, x0, lane);
       else thr_segment<TV>(d, (const TV*)I.in, I.T, r, x0, lane);
@@ -750,13 +775,112 @@ __global__ void __launch_bounds__(1024) k_scan_pairs(const __grid_constant__ Bat
 // off) are written in order, and the values of each run [x_start, x_end) are
 // copied with coalesced loads and stores while the value range is gathered.
 constexpr u32 kRowsPerTicket = 8;
+constexpr u32 kRunCap = 128;  // runs a warp gathers before copying them
+
+// Runs of one warp waiting to be copied: source and destination byte
+// addresses, length in elements.
+struct RunList {
+  u64 src[kRunCap], dst[kRunCap];
+  u32 len[kRunCap];
+  u32 cpre[kRunCap + 1];  // prefix of the runs' 16-byte destination chunks
+  u32 ppre[kRunCap + 1];  // prefix of the runs' head and tail elements
+};
+
+// Largest i < n with pre[i] <= x (pre[0] = 0, nondecreasing).
+__device__ __forceinline__ u32 run_of(const u32* pre, u32 n, u32 x) {
+  u32 lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const u32 mid = (lo + hi) >> 1;
+    if (pre[mid] <= x) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Copies the gathered runs with the whole warp at once: every lane takes
+// 16-byte destination chunks across all runs (funnel-shifted out of five
+// aligned source words), then the runs' unaligned head and tail elements;
+// loads of many runs are in flight together. The value range is gathered.
+template <typename TV>
+__device__ void flush_runs(RunList& rl, u32 nr, int lane, u32& kmin, u32& kmax) {
+  constexpr u32 kPer = 16 / sizeof(TV);
+  __syncwarp();
+  // per run: head elements (to the destination's 16-byte boundary), chunks
+  u32 cacc = 0, pacc = 0;
+  for (u32 i0 = 0; i0 < nr; i0 += 32) {
+    const u32 i = i0 + lane;
+    u32 ch = 0, pc = 0;
+    if (i < nr) {
+      const u32 len = rl.len[i];
+      const u32 h = umin((u32)(((16u - (rl.dst[i] & 15u)) & 15u) / sizeof(TV)), len);
+      ch = (len - h) / kPer;
+      pc = len - ch * kPer;
+    }
+    const u32 ci = warp_incl_scan(ch), pi = warp_incl_scan(pc);
+    if (i < nr) {
+      rl.cpre[i] = cacc + ci - ch;
+      rl.ppre[i] = pacc + pi - pc;
+    }
+    cacc += __shfl_sync(0xffffffffu, ci, 31);
+    pacc += __shfl_sync(0xffffffffu, pi, 31);
+  }
+  if (lane == 0) {
+    rl.cpre[nr] = cacc;
+    rl.ppre[nr] = pacc;
+  }
+  __syncwarp();
+  // whole 16-byte chunks
+  for (u32 u = lane; u < cacc; u += 32) {
+    const u32 i = run_of(rl.cpre, nr, u);
+    const u32 k = u - rl.cpre[i];
+    const u32 len = rl.len[i];
+    const u64 db = rl.dst[i];
+    const u32 h = umin((u32)(((16u - (db & 15u)) & 15u) / sizeof(TV)), len);
+    const uintptr_t sa = (uintptr_t)rl.src[i] + (uintptr_t)(h + k * kPer) * sizeof(TV);
+    const u32 sh = (u32)(sa & 3u) * 8u;
+    const u32* sw = reinterpret_cast<const u32*>(sa & ~(uintptr_t)3);
+    const u32 w0 = __ldg(sw), w1 = __ldg(sw + 1), w2 = __ldg(sw + 2), w3 = __ldg(sw + 3);
+    const u32 w4 = sh ? __ldg(sw + 4) : 0u;
+    const uint4 v = make_uint4(__funnelshift_r(w0, w1, sh), __funnelshift_r(w1, w2, sh),
+                               __funnelshift_r(w2, w3, sh), __funnelshift_r(w3, w4, sh));
+    *reinterpret_cast<uint4*>(db + (u64)h * sizeof(TV) + 16ull * k) = v;
+    const u32 q[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if constexpr (sizeof(TV) == 4) {
+        range_add<float>(__uint_as_float(q[j]), kmin, kmax);
+      } else {
+        range_add<unsigned short>((unsigned short)(q[j] & 0xffffu), kmin, kmax);
+        range_add<unsigned short>((unsigned short)(q[j] >> 16), kmin, kmax);
+      }
+    }
+  }
+  // head and tail elements
+  for (u32 e = lane; e < pacc; e += 32) {
+    const u32 i = run_of(rl.ppre, nr, e);
+    const u32 k = e - rl.ppre[i];
+    const u32 len = rl.len[i];
+    const u64 db = rl.dst[i];
+    const u32 h = umin((u32)(((16u - (db & 15u)) & 15u) / sizeof(TV)), len);
+    const u32 mid = (len - h) / kPer * kPer;
+    const u32 x = k < h ? k : h + mid + (k - h);  // element index within the run
+    const TV vv = __ldg(reinterpret_cast<const TV*>(rl.src[i]) + x);
+    reinterpret_cast<TV*>(db)[x] = vv;
+    range_add<TV>(vv, kmin, kmax);
+  }
+  __syncwarp();
+}
+
 
 template <typename TV>
 __global__ void __launch_bounds__(kThreads, 4) k_front_write(const __grid_constant__ Batch B) {
   __shared__ uint16_t blist_all[kThreads / 32][kListCap];
+  __shared__ RunList runs_all[sizeof(TV) == 1 ? 1 : kThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const u32 below = (1u << lane) - 1u;
   uint16_t* lst = blist_all[warp];
+  RunList& rl = runs_all[sizeof(TV) == 1 ? 0 : warp];
+  u32 nruns = 0;  // runs gathered and not yet copied
   const u64 total_rows = B.row0[B.n];
   u32 kmin = 0xffffffffu, kmax = 0u;
   u32 cur = 0xffffffffu;  // item whose range the warp accumulates
@@ -773,7 +897,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_front_write(const __grid_consta
       my_item = find_item(B.row0, B.n, g);
       const Item& I = B.it[my_item];
       const u64 r = g - B.row0[my_item];
-      const u64 t = r / I.rpt;
+      const u64 t = div_by(r, I.rpt, I.m_rpt);
       my_nbr = r < I.counts_cap ? (u32)I.counts[r] : 0xffffffffu;
       my_on = I.ftno[t] + I.rno[r];
       my_ob = I.ftbo[t] + I.rbo[r];
@@ -787,7 +911,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_front_write(const __grid_consta
       u64 on = __shfl_sync(0xffffffffu, my_on, j);
       const u64 ob = __shfl_sync(0xffffffffu, my_ob, j);
       const Item& I = B.it[item];
-      if (item != cur) {  // flush the value range of the previous item
+      if (item != cur) {  // copy the previous item's runs, flush its value range
+        if constexpr (sizeof(TV) != 1) {
+          if (nruns) flush_runs<TV>(rl, nruns, lane, kmin, kmax);
+          nruns = 0;
+        }
         flush_range(cur == 0xffffffffu ? nullptr : B.it[cur].rst, kmin, kmax, lane);
         cur = item;
       }
@@ -849,7 +977,16 @@ __global__ void __launch_bounds__(kThreads, 4) k_front_write(const __grid_consta
             if constexpr (sizeof(TV) == 1) {
               copy_run_u8(reinterpret_cast<const u8*>(src), reinterpret_cast<u8*>(dst), len, lane);
             } else {
-              copy_run_vec<TV>(src, dst, len, lane, kmin, kmax);
+              if (nruns == kRunCap) {  // the list is full: copy what it holds
+                flush_runs<TV>(rl, nruns, lane, kmin, kmax);
+                nruns = 0;
+              }
+              if (lane == 0) {
+                rl.src[nruns] = (u64)(uintptr_t)src;
+                rl.dst[nruns] = (u64)(uintptr_t)dst;
+                rl.len[nruns] = len;
+              }
+              ++nruns;
             }
             on += len;
           }
@@ -884,6 +1021,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_front_write(const __grid_consta
           }
         }
       __syncwarp();
+    }
+    if constexpr (sizeof(TV) != 1) {  // the ticket's runs
+      if (nruns) flush_runs<TV>(rl, nruns, lane, kmin, kmax);
+      nruns = 0;
     }
   }
   flush_range(cur == 0xffffffffu ? nullptr : B.it[cur].rst, kmin, kmax, lane);

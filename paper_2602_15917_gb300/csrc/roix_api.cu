@@ -359,6 +359,7 @@ void fill_batch(Batch& B, const Desc& c, const BatchPlan& bp, const roix_dims* d
     I.crecoff = (u64*)(ws + p.crecoff);
     I.rbits = (u32*)(ws + p.rbits);
     I.rpt = p.rpt;
+    I.m_rpt = recip64(p.rpt);
     I.ftiles = p.ftiles;
     B.seg0[i] = seg;
     B.ftile0[i] = ft;
@@ -386,6 +387,8 @@ void roix::set_threshold_units(Batch& B) {
     const roix_dtype dt = (roix_dtype)B.c.dtype;
     I.vec = rows_vector_aligned(I.in, dt, I.nx) ? 1u : 0u;
     I.flat = (!(I.vec && I.nx % 1024 == 0) && I.nx >= 256 && aligned(I.in, 16)) ? 1u : 0u;
+    I.m_nx = recip64(I.nx);
+    I.m_spr = recip64((I.nx + 1023) / 1024);
     B.seg0[i] = seg;
     B.fseg0[i] = fseg;
     const u64 N = I.nx * I.ny * I.nz;

@@ -247,6 +247,20 @@ __device__ __forceinline__ void block_scan2(const u32* __restrict__ a, const u32
 // ------------------------------------------------------------ fast division
 // Division of 32-bit numerators by an invariant divisor with a multiply-high
 // and shifts (Granlund & Montgomery 1994, round-up method).
+// floor((2^64 - 1) / d), the multiplier of div_by (host side, once per item).
+__host__ __device__ inline u64 recip64(u64 d) { return d ? ~0ull / d : 0ull; }
+
+// floor(a / d) for d >= 1 from m = recip64(d). With m = (2^64 - 1 - rho) / d,
+// 0 <= rho < d: a m / 2^64 = a / d - a (1 + rho) / (d 2^64) > a / d - 1, so the
+// high word of a m is floor(a / d) or one less, and one remainder test fixes it.
+// Integer pipes only (a binary64 or 64-bit division would run on the FP64 pipe,
+// which is narrow on this part).
+__device__ __forceinline__ u64 div_by(u64 a, u64 d, u64 m) {
+  u64 q = __umul64hi(a, m);
+  if (a - q * d >= d) ++q;
+  return q;
+}
+
 struct FastDiv {
   u32 d, m, s;
   __host__ __device__ FastDiv(u32 div = 1) : d(div ? div : 1), m(0), s(0) {
@@ -390,6 +404,8 @@ struct Item {
   u32 zhalo;                           // z-slab: bit 0 = T holds the plane before z = 0,
                                        // bit 1 = T holds the plane after z = nz - 1
   u64 ftiles;                          // front tiles
+  u64 m_nx, m_spr, m_rpt;              // recip64 of nx, of the 1024-voxel segments per
+                                       // row and of rpt (divisions by multiply-high)
 };
 
 struct Batch {
