@@ -226,7 +226,7 @@ def run_ours(args, rank, world, local_rank):
     # launch shapes picked by the autotuner on this very workload (no output byte changes);
     # --tune 0 keeps the default shapes (e.g. for profiling runs)
     t0 = time.perf_counter()
-    tuning = (ctxs[0].tune(xs, outs=outs, caps=caps, sizes=sizes, reps=3, stream=main, **cfg)
+    tuning = (ctxs[0].tune(xs, outs=outs, caps=caps, sizes=sizes, reps=7, stream=main, **cfg)
               if args.tune else ctxs[0].get_tuning())
     tune_s = time.perf_counter() - t0
     for c in ctxs[1:]:
@@ -1058,7 +1058,7 @@ def run_slabs(args, rank, world, local_rank):
     cfgs = [dict(sc["cfg"], eb=eb, predictor=args.predictor) for eb in sc["sweep"]]
     # launch shapes tuned on one slab compressed as a volume of its own
     t0 = time.perf_counter()
-    tuning = (rx.tune([x[:slab]], outs=outs[:1], caps=[cap], sizes=sizes[:1], reps=3,
+    tuning = (rx.tune([x[:slab]], outs=outs[:1], caps=[cap], sizes=sizes[:1], reps=7,
                       stream=main, **dict(cfgs[0], eb=sc["e2e_eb"])) if args.tune
               else rx.get_tuning())
     tune_s = time.perf_counter() - t0

@@ -426,14 +426,18 @@ roix_status roix_server_destroy(roix_server* s);
 
 /* ------------------------------------------------------------ autotuner
  * Launch shapes of the compression kernels (no paper counterpart). None of
- * them changes an output byte: they set the compaction tile size and how many
- * blocks of the binarisation, symbol and pack kernels are resident per SM. */
+ * them changes an output byte: they set the compaction tile size and counting
+ * kernel and how many blocks of the binarisation, symbol and pack kernels are
+ * resident per SM. */
 typedef struct {
   uint32_t front_words;         /* mask words per compaction tile, 256..16384 (2048) */
   uint32_t thr_blocks_per_sm;   /* binarisation, row form, 1..32 (8) */
   uint32_t flat_blocks_per_sm;  /* binarisation, flat form, 1..32 (4) */
   uint32_t sym_blocks_per_sm;   /* symbols, 0..32, 0 = as many as fit (0) */
   uint32_t pack_blocks_per_sm;  /* pack, 0..32, 0 = as many as fit (0) */
+  uint32_t front_kernel;        /* compaction counts: 0 = a block per tile, its rows staged
+                                   in shared memory; 1 = a warp per tile, rows walked with a
+                                   register window (0) */
 } roix_tuning;
 roix_status roix_get_tuning(const roix_ctx* ctx, roix_tuning* out);
 /* ROIX_EINVAL for values out of range (nothing changed). */

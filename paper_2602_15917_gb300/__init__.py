@@ -94,7 +94,7 @@ class ServerStats(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [(k, C.c_uint32) for k in ("front_words", "thr_blocks_per_sm",
                                           "flat_blocks_per_sm", "sym_blocks_per_sm",
-                                          "pack_blocks_per_sm")]
+                                          "pack_blocks_per_sm", "front_kernel")]
 
 
 class EbInfo(C.Structure):

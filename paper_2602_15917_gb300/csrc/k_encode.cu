@@ -160,13 +160,15 @@ __device__ __forceinline__ u32 symbol_of(int c, int prev, bool out, u32 R) {
 // Segments of kQuantTile values, every item's segments in order: prefix of
 // ceil(n_i / per) / group over the items (n_i found by the compaction),
 // computed by each block at start.
-__device__ __forceinline__ void tile_prefix(const Batch& B, u64* pre, u64 per, u64 group) {
+__device__ __forceinline__ void tile_prefix(const Batch& B, u64* pre, u64 per, u64 group,
+                                            u64* counts = nullptr) {
   // every item's count read by a thread of its own (the loads overlap), the
   // prefix summed by one thread from shared memory
   for (u32 i = threadIdx.x; i < B.n; i += blockDim.x) {
     const Item& I = B.it[i];
     const u64 n = umin(I.sizes[0], I.N);
     pre[i + 1] = ((n + per - 1) / per + group - 1) / group;
+    if (counts) counts[i] = n;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -789,38 +791,47 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__
 // item's byte table (2R bytes, read through L1).
 __global__ void __launch_bounds__(kThreads) k_pack_count(const __grid_constant__ Batch B) {
   __shared__ u64 pre[kMaxBatch + 1];
+  __shared__ u64 nn[kMaxBatch];
   const u32 C = B.c.C;
   const int lane = threadIdx.x & 31;
-  tile_prefix(B, pre, C, 1);
+  tile_prefix(B, pre, C, 1, nn);
   const u64 total = pre[B.n];
-  while (true) {
-    u64 gt = 0;
-    if (lane == 0) gt = atomicAdd(&B.ctr[2], 1u);
-    gt = __shfl_sync(0xffffffffu, gt, 0);
-    if (gt >= total) break;
+  const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
+  constexpr u32 kIn = 4;  // vector loads of a lane in flight at once
+  for (u64 gt = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5; gt < total; gt += nwarps) {
     const u32 item = find_item(pre, B.n, gt);
     const Item& I = B.it[item];
-    const u64 n = umin(I.sizes[0], I.N);
+    const u64 n = nn[item];
     const uint16_t* __restrict__ sym = I.sym;
     const uint8_t* __restrict__ len = I.lens;  // 2R bytes: stays in L1
     const u64 t = gt - pre[item];
     const u64 c0 = t * C + (u64)lane * 8;
+    const u32 steps = C / 256;  // 8 symbols per lane and step
     u32 bits = 0;
-    for (u32 r = 0; r < C / 256; ++r) {
-      const u64 k = c0 + (u64)r * 256;
-      if (k + 8 <= n) {
-        const uint4 v = __ldg(reinterpret_cast<const uint4*>(sym + k));
-        bits += __ldg(len + (v.x & 0xffffu)) + __ldg(len + (v.x >> 16)) +
-                __ldg(len + (v.y & 0xffffu)) + __ldg(len + (v.y >> 16)) +
-                __ldg(len + (v.z & 0xffffu)) + __ldg(len + (v.z >> 16)) +
-                __ldg(len + (v.w & 0xffffu)) + __ldg(len + (v.w >> 16));
-      } else {
+    if (t * C + C <= n) {  // a full chunk: no bounds tests
+      for (u32 r0 = 0; r0 < steps; r0 += kIn) {
+        uint4 v[kIn];
+#pragma unroll
+        for (u32 q = 0; q < kIn; ++q)
+          if (r0 + q < steps)
+            v[q] = __ldg(reinterpret_cast<const uint4*>(sym + c0 + (u64)(r0 + q) * 256));
+#pragma unroll
+        for (u32 q = 0; q < kIn; ++q)
+          if (r0 + q < steps)
+            bits += __ldg(len + (v[q].x & 0xffffu)) + __ldg(len + (v[q].x >> 16)) +
+                    __ldg(len + (v[q].y & 0xffffu)) + __ldg(len + (v[q].y >> 16)) +
+                    __ldg(len + (v[q].z & 0xffffu)) + __ldg(len + (v[q].z >> 16)) +
+                    __ldg(len + (v[q].w & 0xffffu)) + __ldg(len + (v[q].w >> 16));
+      }
+    } else {
+      for (u32 r = 0; r < steps; ++r) {
+        const u64 k = c0 + (u64)r * 256;
 #pragma unroll
         for (int q = 0; q < 8; ++q)
           if (k + q < n) bits += __ldg(len + __ldg(sym + k + q));
       }
     }
-    bits = warp_sum(bits);
+    bits = __reduce_add_sync(0xffffffffu, bits);
     if (lane == 0) I.cw[t] = (bits + 31) >> 5;
   }
 }

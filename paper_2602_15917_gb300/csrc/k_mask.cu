@@ -498,19 +498,26 @@ __device__ __forceinline__ void copy_run_vec(const TV* __restrict__ src, TV* __r
   }
 }
 
+// The compaction runs in three launches, none of whose blocks waits on
+// another: a counting kernel forms the retained words of each tile of rows
+// (dilated from T, stored to the item's D when dilating), the rows' boundary
+// counts (into the container), each row's offsets within its tile and the
+// tile's totals; k_scan_pairs turns the tiles' totals into offsets;
+// k_front_write has warps take rows and write their boundaries and values.
+// Two counting kernels give the same results: k_front_count_blk (rows staged
+// by a block, better for narrow rows without dilation) and k_front_count (a
+// warp per tile, better for dilated volumes); the tuning picks one.
 struct FrontSmem {
   u32 wn[kThreads / 32], wb[kThreads / 32];  // per-warp totals, then offsets
   u64 base_n, base_nb, tile;
   u32 scratch[40];
 };
 
-// The compaction runs in three launches, none of whose blocks waits on
-// another: k_front_count forms the retained words of each tile of rows
-// (dilated from T, stored to the item's D when dilating), the rows' boundary
-// counts (into the container), each row's offsets within its tile and the
-// tile's totals; k_front_scan turns the tiles' totals into offsets;
-// k_front_write has warps take rows and write their boundaries and values.
-__global__ void __launch_bounds__(kThreads, 4) k_front_count(const __grid_constant__ Batch B) {
+// k_front_count_blk: a block per tile (tickets in order). The block stages
+// the tile's band of mask rows in shared memory (three loads per word for the
+// z part of the dilation), forms the retained words from the staged band,
+// then its warps count whole rows and one warp scans the per-warp totals.
+__global__ void __launch_bounds__(kThreads, 4) k_front_count_blk(const __grid_constant__ Batch B) {
   extern __shared__ u32 smem_dyn[];
   __shared__ FrontSmem sh;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -676,6 +683,213 @@ __global__ void __launch_bounds__(kThreads, 4) k_front_count(const __grid_consta
     if (dilate)  // (Dw holds nothing when the band is empty)
       for (u32 i = threadIdx.x; i < nw; i += blockDim.x) I.D[r0 * W + i] = any ? Dw[i] : 0u;
     __syncthreads();
+  }
+}
+
+// Raw mask loads of one word of one row: T of the row and, when dilating, of
+// the rows one slice before and after (present only where those slices are).
+struct URaw {
+  u32 c, zlo, zhi;
+};
+
+template <bool DIL>
+__device__ __forceinline__ void u_issue(const u32* p, bool ok, bool zlo, bool zhi, u64 zstride,
+                                        URaw& q) {
+  q.c = q.zlo = q.zhi = 0u;
+  if (ok) {
+    q.c = __ldg(p);
+    if constexpr (DIL) {
+      if (zlo) q.zlo = __ldg(p - zstride);
+      if (zhi) q.zhi = __ldg(p + zstride);
+    }
+  }
+}
+
+__device__ __forceinline__ u32 u_of(const URaw& q) { return q.c | q.zlo | q.zhi; }
+
+// k_front_count: one warp per tile, no block barriers. The warp walks the
+// tile's rows in 32-word columns (lane = word); the 3x3x3 dilation is
+// separable: U = OR over z of T (three loads), V = OR of U over the rows y-1,
+// y, y+1 (a window of three rows in registers, the next row's loads issued one
+// row ahead), D = V dilated in x (neighbour words by shuffles; for rows of
+// more than one column, lanes 0 and 31 also hold the words just outside the
+// column). Per row one warp reduction of the packed counts gives the retained
+// voxels and boundaries; the tile's rows are then scanned in parallel for
+// their offsets within the tile.
+constexpr u32 kMaxTileRows = 256;  // rows of a compaction tile, at most
+
+template <bool DIL>
+__device__ __forceinline__ void front_count_tile(const Batch& B, const Item& I, const Desc& d,
+                                                 u64 t, u32* rown, u32* rowcnt, int lane) {
+  const u64 W = d.W;
+  const u32 rpt = I.rpt;
+  const u64 r0 = t * rpt;
+  const u32 nrows = (u32)umin(rpt, d.rows - r0);
+  const bool end_extra = (d.nx & 31) == 0;  // boundary at x = nx lives past the last word
+  const bool multi = W > 32;                // rows span more than one column
+  const u64 zstride = d.ny * W;
+  const u32* __restrict__ T = I.T;
+  u32* __restrict__ Dm = I.D;
+  const u32 zhalo = I.zhalo;  // z-slab: T continues across the slab's z borders
+  // slice position of the first row
+  const u64 zc064 = div_by(r0, d.ny, I.m_ny);
+  const u32 ny = (u32)d.ny, nz = (u32)d.nz;  // slice sizes fit 32 bits
+  const u32 zc0 = (u32)zc064, yc0 = (u32)(r0 - zc064 * d.ny);
+  // rows from r0 on that exist (loads past the item's last row are skipped)
+  const u64 avail = d.rows - r0;
+  for (u32 w0 = 0; w0 < (u32)W; w0 += 32) {
+    const u32 w = w0 + lane;
+    const bool wv = w < W;
+    const u32 lmask = wv ? last_mask(d, w) : 0u;
+    // lanes 0 and 31 also hold the word left / right of the column
+    const u32 hw = lane == 0 ? w0 - 1u : w0 + 32u;
+    const bool hv = multi && ((lane == 0 && w0 > 0) || (DIL && lane == 31 && (u64)w0 + 32 < W));
+    // issue position: row r0 + ii with slice coordinates (zi, yi)
+    const u32* pw = T + r0 * W + w;   // this lane's word of the issue row
+    const u32* ph = T + r0 * W + hw;  // the halo word of the issue row
+    u64 ii = 0;
+    u32 zi = zc0, yi = yc0;
+    bool zl = zc0 > 0 || (zhalo & 1u), zh = zc0 + 1 < nz || (zhalo & 2u);
+    auto issue = [&](URaw& q, URaw& hq) {
+      const bool ok = ii < avail;
+      u_issue<DIL>(pw, ok && wv, zl, zh, zstride, q);
+      if (multi) u_issue<DIL>(ph, ok && hv, zl, zh, zstride, hq);
+      ++ii;
+      pw += W;
+      ph += W;
+      if (++yi == ny) {
+        yi = 0;
+        ++zi;
+        zl = true;
+        zh = zi + 1 < nz || (zhalo & 2u);
+      }
+    };
+    u32 um = 0u, hm = 0u;  // U of the row above (used only when it is in the slice)
+    if (DIL && yc0 > 0) {
+      URaw a, ha;
+      u_issue<DIL>(pw - W, wv, zl, zh, zstride, a);
+      um = u_of(a);
+      if (multi) {
+        u_issue<DIL>(ph - W, hv, zl, zh, zstride, ha);
+        hm = u_of(ha);
+      }
+    }
+    // two load buffers used in turn (no register copies of loads in flight):
+    // dilating, the buffer read at row r holds row r + 1 and row r + 2 is
+    // issued into the other; otherwise it holds row r and row r + 1 is issued
+    URaw qa, hqa{0u, 0u, 0u}, qb, hqb{0u, 0u, 0u};
+    issue(qa, hqa);  // row r0
+    u32 uc = 0u, hc = 0u;
+    if (DIL) {
+      uc = u_of(qa);
+      hc = u_of(hqa);
+      issue(qa, hqa);  // row r0 + 1
+    }
+    u32 y = yc0;
+    u32* pd_out = DIL ? Dm + r0 * W + w : nullptr;
+    auto step = [&](u32 lr, const URaw& cur, const URaw& hcur, URaw& nxt, URaw& hnxt) {
+      issue(nxt, hnxt);
+      u32 v, vh = 0u;
+      if constexpr (DIL) {
+        const u32 up = u_of(cur);
+        const bool ym = y > 0, yp = y + 1 < ny;
+        v = uc | (ym ? um : 0u) | (yp ? up : 0u);
+        um = uc;
+        uc = up;
+        if (multi) {
+          const u32 hp = u_of(hcur);
+          vh = hc | (ym ? hm : 0u) | (yp ? hp : 0u);
+          hm = hc;
+          hc = hp;
+        }
+      } else {
+        v = u_of(cur);
+        if (multi) vh = u_of(hcur);
+      }
+      if (++y == ny) y = 0;
+      // retained word of this lane, and the top bit of the word left of it
+      u32 hlo = 0u, hhi = 0u;  // words w0 - 1 and w0 + 32 (zero for one column)
+      if (multi) {
+        hlo = __shfl_sync(0xffffffffu, vh, 0);
+        hhi = __shfl_sync(0xffffffffu, vh, 31);
+      }
+      u32 dv, ptop;
+      if constexpr (DIL) {
+        const u32 vlo = __shfl_up_sync(0xffffffffu, v, 1);
+        const u32 vhi = __shfl_down_sync(0xffffffffu, v, 1);
+        const u32 lo = lane == 0 ? hlo : vlo;
+        const u32 hi = lane == 31 ? hhi : vhi;
+        dv = (v | (v << 1) | (lo >> 31) | (v >> 1) | (hi << 31)) & lmask;
+        const u32 pd = __shfl_up_sync(0xffffffffu, dv, 1);
+        // bit 31 of the dilated word w0 - 1 (never the last word of the row)
+        ptop = lane == 0 ? ((hlo >> 31) | (hlo >> 30) | (w0 > 0 ? v : 0u)) & 1u : pd >> 31;
+      } else {
+        dv = v & lmask;
+        const u32 pd = __shfl_up_sync(0xffffffffu, dv, 1);
+        ptop = lane == 0 ? hlo >> 31 : pd >> 31;
+      }
+      // (lanes past the row's last word count nothing: the carried top bit of
+      // the last word is the x = nx boundary, counted by end_extra)
+      const u32 nb = wv ? __popc(dv ^ ((dv << 1) | ptop)) +
+                              ((end_extra && w == W - 1) ? (dv >> 31) : 0u)
+                        : 0u;
+      // both at most 1025 per column
+      const u32 packed = __reduce_add_sync(0xffffffffu, __popc(dv) | (nb << 16));
+      if (lane == 0) {
+        const u32 a0 = w0 ? rown[lr] : 0u, b0 = w0 ? rowcnt[lr] : 0u;
+        rown[lr] = a0 + (packed & 0xffffu);
+        rowcnt[lr] = b0 + (packed >> 16);
+      }
+      if (DIL) {
+        if (wv) *pd_out = dv;
+        pd_out += W;
+      }
+    };
+    for (u32 lr = 0; lr < nrows; lr += 2) {
+      step(lr, qa, hqa, qb, hqb);
+      if (lr + 1 < nrows) step(lr + 1, qb, hqb, qa, hqa);
+    }
+  }
+  __syncwarp();
+  // the rows' offsets within the tile, their boundary counts, the tile totals
+  uint16_t* __restrict__ counts = I.counts;
+  const u64 counts_cap = I.counts_cap;
+  u32 on = 0, ob = 0;
+  for (u32 b = 0; b < nrows; b += 32) {
+    const u32 lr = b + lane;
+    const u32 n_ = lr < nrows ? rown[lr] : 0u, c_ = lr < nrows ? rowcnt[lr] : 0u;
+    const u32 in_ = warp_incl_scan(n_), ic = warp_incl_scan(c_);
+    if (lr < nrows) {
+      const u64 r = r0 + lr;
+      I.rno[r] = on + in_ - n_;
+      I.rbo[r] = ob + ic - c_;
+      if (r < counts_cap) counts[r] = (uint16_t)c_;
+    }
+    on += __shfl_sync(0xffffffffu, in_, 31);
+    ob += __shfl_sync(0xffffffffu, ic, 31);
+  }
+  if (lane == 0) {
+    I.ftn[t] = on;
+    I.ftb[t] = ob;
+  }
+  __syncwarp();
+}
+
+template <bool DIL>
+__global__ void __launch_bounds__(kThreads, 4) k_front_count(const __grid_constant__ Batch B) {
+  __shared__ u32 rows_all[kThreads / 32][2 * kMaxTileRows];  // per warp: row totals
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  u32* rown = rows_all[warp];
+  u32* rowcnt = rown + kMaxTileRows;
+  const u64 total_tiles = B.ftile0[B.n];
+  const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
+  for (u64 gt = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5; gt < total_tiles;
+       gt += nwarps) {
+    const u32 item = find_item(B.ftile0, B.n, gt);
+    const Item& I = B.it[item];
+    const Desc d = desc_of(B, I);
+    const u64 t = gt - B.ftile0[item];
+    front_count_tile<DIL>(B, I, d, t, rown, rowcnt, lane);
   }
 }
 
@@ -957,17 +1171,21 @@ __global__ void __launch_bounds__(kThreads, 4) k_front_write(const __grid_consta
             ev &= ev - 1;
             if (ob + o < bounds_cap) bounds[ob + o] = (uint16_t)x;
             else set_status(B.status, ROIX_ECAPACITY);
-            if (fast) lst[o] = (uint16_t)x;
+            if (fast && o < kListCap) lst[o] = (uint16_t)x;
             ++o;
           }
           if (ex) {
             if (ob + o < bounds_cap) bounds[ob + o] = (uint16_t)d.nx;
             else set_status(B.status, ROIX_ECAPACITY);
-            if (fast) lst[o] = (uint16_t)d.nx;
+            if (fast && o < kListCap) lst[o] = (uint16_t)d.nx;
           }
           bo += __shfl_sync(0xffffffffu, inc, 31);
         }
         __syncwarp();
+        if (bo != nbr) {  // the row's count disagrees with its mask: copy nothing
+          set_status(B.status, ROIX_ECORRUPT);
+          continue;
+        }
         if (fast) {
           for (u32 i = 0; i < nbr; i += 2) {
             const u32 xs = lst[i], xe = lst[i + 1];
@@ -1090,6 +1308,7 @@ void launch_dilate(const Launch& L, const Desc& d, const u32* T, u32* D, u64* po
                                                             FastDiv((u32)d.W));
 }
 
+
 size_t front_smem(u32 rpt, u64 W, int dilate) {
   return (size_t)rpt * W * 4 + (size_t)rpt * 12 + 8 + (dilate ? (size_t)(rpt + 2) * W * 4 : 0);
 }
@@ -1097,16 +1316,27 @@ size_t front_smem(u32 rpt, u64 W, int dilate) {
 void launch_front(const Launch& L, const Batch& B) {
   const u64 tiles = B.ftile0[B.n];
   if (tiles == 0) return;
-  size_t smem = 0;
-  for (u32 i = 0; i < B.n; ++i) {
-    const size_t s = front_smem(B.it[i].rpt, B.it[i].W, B.c.dilate);
-    if (s > smem) smem = s;
+  if (L.t.front_kernel == 0) {
+    size_t smem = 0;
+    for (u32 i = 0; i < B.n; ++i) {
+      const size_t s = front_smem(B.it[i].rpt, B.it[i].W, B.c.dilate);
+      if (s > smem) smem = s;
+    }
+    cudaFuncSetAttribute((const void*)k_front_count_blk,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    u64 grid = (u64)occupancy_grid((const void*)k_front_count_blk, kThreads, smem, L.sms);
+    if (grid > tiles) grid = tiles;
+    k_front_count_blk<<<(unsigned)grid, kThreads, smem, L.stream>>>(B);
+  } else {
+    auto count = [&](auto kernel) {
+      u64 grid = (u64)occupancy_grid((const void*)kernel, kThreads, 0, L.sms);
+      const u64 need = (tiles + kThreads / 32 - 1) / (kThreads / 32);
+      if (grid > need) grid = need;
+      kernel<<<(unsigned)grid, kThreads, 0, L.stream>>>(B);
+    };
+    if (B.c.dilate) count(k_front_count<true>);
+    else count(k_front_count<false>);
   }
-  cudaFuncSetAttribute((const void*)k_front_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)smem);
-  u64 grid = (u64)occupancy_grid((const void*)k_front_count, kThreads, smem, L.sms);
-  if (grid > tiles) grid = tiles;
-  k_front_count<<<(unsigned)grid, kThreads, smem, L.stream>>>(B);
   u64 scan_tiles = 0;
   for (u32 i = 0; i < B.n; ++i) scan_tiles += (B.it[i].ftiles + kScanTile - 1) / kScanTile;
   launch_scan_pairs(L, B, 0, scan_tiles);

@@ -404,8 +404,8 @@ struct Item {
   u32 zhalo;                           // z-slab: bit 0 = T holds the plane before z = 0,
                                        // bit 1 = T holds the plane after z = nz - 1
   u64 ftiles;                          // front tiles
-  u64 m_nx, m_spr, m_rpt;              // recip64 of nx, of the 1024-voxel segments per
-                                       // row and of rpt (divisions by multiply-high)
+  u64 m_nx, m_spr, m_rpt, m_ny;        // recip64 of nx, of the 1024-voxel segments per
+                                       // row, of rpt and of ny (divisions by multiply-high)
 };
 
 struct Batch {
@@ -520,6 +520,7 @@ struct Tuning {
   u32 flat_blocks_per_sm = 4;  // binarisation, flat form
   u32 sym_blocks_per_sm = 0;   // symbols: 0 = as many as fit
   u32 pack_blocks_per_sm = 0;  // pack: 0 = as many as fit
+  u32 front_kernel = 0;        // compaction counts: 0 = block per tile, 1 = warp per tile
 };
 
 }  // namespace roix
@@ -554,6 +555,7 @@ void make_threshold_batch(Batch& B, const Desc& d, const void* in, u32* T);
 // Host: the binarisation work units of every item (B.seg0), from each item's
 // input pointer and geometry; sets the items' vec / flat forms.
 void set_threshold_units(Batch& B);
+size_t front_smem(u32 rpt, u64 W, int dilate);
 
 // ------------------------------------------------------ launch functions
 struct Launch {
@@ -572,7 +574,6 @@ void launch_scan_pairs(const Launch& L, const Batch& B, int mode, u64 tiles_cap)
 void launch_threshold(const Launch& L, const Batch& B);
 void launch_dilate(const Launch& L, const Desc& d, const u32* T, u32* D, u64* popcount);
 void launch_front(const Launch& L, const Batch& B);
-size_t front_smem(u32 rpt, u64 W, int dilate);
 
 // coder kernels (k_encode.cu)
 constexpr u32 kQuantTile = 4096;  // values per symbol segment (one warp's unit of work)

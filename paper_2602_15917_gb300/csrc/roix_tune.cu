@@ -37,6 +37,7 @@ std::vector<Param> params_list() {
       {"front_words", &Tuning::front_words, {512, 1024, 2048, 4096, 8192}},
       {"sym_blocks_per_sm", &Tuning::sym_blocks_per_sm, {0, 1, 2, 3}},
       {"pack_blocks_per_sm", &Tuning::pack_blocks_per_sm, {0, 1, 2, 4}},
+      {"front_kernel", &Tuning::front_kernel, {0, 1}},
   };
 }
 
@@ -124,7 +125,7 @@ void cache_store(const char* path, const std::string& key, const Tuning& t, doub
 bool tuning_ok(const Tuning& t) {
   return t.front_words >= 256 && t.front_words <= 16384 && t.thr_blocks_per_sm >= 1 &&
          t.thr_blocks_per_sm <= 32 && t.flat_blocks_per_sm >= 1 && t.flat_blocks_per_sm <= 32 &&
-         t.sym_blocks_per_sm <= 32 && t.pack_blocks_per_sm <= 32;
+         t.sym_blocks_per_sm <= 32 && t.pack_blocks_per_sm <= 32 && t.front_kernel <= 1;
 }
 
 }  // namespace
@@ -138,6 +139,7 @@ roix_status roix_get_tuning(const roix_ctx* ctx, roix_tuning* out) {
   out->flat_blocks_per_sm = ctx->tune.flat_blocks_per_sm;
   out->sym_blocks_per_sm = ctx->tune.sym_blocks_per_sm;
   out->pack_blocks_per_sm = ctx->tune.pack_blocks_per_sm;
+  out->front_kernel = ctx->tune.front_kernel;
   return ROIX_OK;
 }
 
@@ -149,6 +151,7 @@ roix_status roix_set_tuning(roix_ctx* ctx, const roix_tuning* t) {
   r.flat_blocks_per_sm = t->flat_blocks_per_sm;
   r.sym_blocks_per_sm = t->sym_blocks_per_sm;
   r.pack_blocks_per_sm = t->pack_blocks_per_sm;
+  r.front_kernel = t->front_kernel;
   if (!tuning_ok(r)) {
     ctx->err = "tuning values out of range";
     return ROIX_EINVAL;

@@ -33,7 +33,16 @@ def rx():
     r.close()
 
 
-def test_projections64_batch_equals_oracle(rx):
+@pytest.fixture(params=[0, 1], ids=["front_blk", "front_warp"])
+def front_kernel(rx, request):
+    # both compaction counting kernels (the autotuner may pick either)
+    default = rx.get_tuning()
+    rx.set_tuning(front_kernel=request.param)
+    yield request.param
+    rx.set_tuning(**default)
+
+
+def test_projections64_batch_equals_oracle(rx, front_kernel):
     cfg = dict(eb=4, eb_mode="abs", cmp="lt", threshold=57000, dark=100, dilate=0,
                fill=60100, radius=512, chunk=4096)
     xs = [phantom.projection(s, i, seed=0, device="cuda")
@@ -54,7 +63,7 @@ def _row_from_container(buf: np.ndarray, hdr: dict, row: int):
         np.uint16)
 
 
-def test_cube1024_properties_and_sampled_rows(rx):
+def test_cube1024_properties_and_sampled_rows(rx, front_kernel):
     n = 1024
     cfg = dict(eb=1e-4, eb_mode="rel", cmp="gt", threshold=0.1, dilate=1, fill=0.0,
                radius=512, chunk=4096)

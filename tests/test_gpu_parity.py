@@ -167,6 +167,40 @@ def test_staged_chain_matches_oracle_and_fused(rx):
     assert np.array_equal(fused, got)
 
 
+# Row widths that are multiples of 32 voxels (the x = nx boundary is carried
+# past the last word) with word counts that are not multiples of 32, and
+# columns of more than one warp width: every mask pattern the per-row counts
+# and offsets must get right, dilated or not, in the fused and staged paths.
+WORD_EDGE_SHAPES = [(3, 40, 96), (2, 9, 64), (2, 5, 1056), (1, 7, 2048), (2, 6, 1000), (3, 4, 32)]
+
+
+@pytest.mark.parametrize("shape", WORD_EDGE_SHAPES, ids=["x".join(map(str, s)) for s in WORD_EDGE_SHAPES])
+@pytest.mark.parametrize("dilate", [0, 1])
+@pytest.mark.parametrize("front_kernel", [0, 1])
+def test_row_widths_at_word_edges(rx, shape, dilate, front_kernel):
+    x = phantom.ellipsoids(shape=shape, seed=11).numpy()
+    x[:, :, -1] = 1.0  # retained last column: rows end inside the ROI
+    x[:, 0, :] = 1.0
+    cfg = dict(eb=1e-3, threshold=0.1, dilate=dilate)
+    default = rx.get_tuning()
+    try:
+        rx.set_tuning(front_kernel=front_kernel)
+        ref, got = _compress_both(rx, x, **cfg)
+        _assert_same_container(ref, got)
+        xt = torch.from_numpy(x).cuda()
+        mask, _ = rx.extract_roi(xt, **cfg)
+        pixels, counts, bounds, sizes = rx.compact(xt, mask)
+        rx.sync()
+    finally:
+        rx.set_tuning(**default)
+    P, c_ref, b_ref = oracle.compact(x, oracle.mask(x, **cfg))
+    n, nb = (int(v) for v in sizes.cpu().numpy())
+    assert n == P.size and nb == b_ref.size
+    assert np.array_equal(pixels[:n].cpu().numpy(), P)
+    assert np.array_equal(counts.cpu().numpy(), c_ref)
+    assert np.array_equal(bounds[:nb].cpu().numpy(), b_ref)
+
+
 def test_staged_uint16(rx):
     x = phantom.projection(180, 4, seed=2).numpy()
     cfg = dict(eb=4, cmp="lt", threshold=57000, dark=100, dilate=0, fill=60100)
@@ -411,12 +445,14 @@ def test_flat_binarisation_in_fused_and_batch(rx):
     _assert_same_container(ref, got)
 
 
-def test_scans_over_more_tiles_and_chunks_than_one_block(rx):
+@pytest.mark.parametrize("front_kernel", [0, 1])
+def test_scans_over_more_tiles_and_chunks_than_one_block(rx, front_kernel):
     # more than 1024 compaction tiles and pack chunks per item: the per-item
     # scans give every thread a range of several entries
     default = rx.get_tuning()
     try:
-        rx.set_tuning(front_words=256)  # 8 rows of 1024 voxels per tile: 1200 tiles
+        # 8 rows of 1024 voxels per tile: 1200 tiles
+        rx.set_tuning(front_words=256, front_kernel=front_kernel)
         x = phantom.porous_cylinder(1024, radius=400.0, seed=3, z_range=(440, 456)).numpy()
         x = np.ascontiguousarray(x[:, 212:812, :])  # 16 x 600 x 1024
         for cfg in (dict(eb=1e-4, eb_mode="rel", dilate=1, chunk=256),

@@ -44,7 +44,8 @@ def _check_batch(rx, xs, cfg):
 @pytest.mark.parametrize("setting", [
     dict(front_words=256), dict(front_words=16384), dict(thr_blocks_per_sm=1, flat_blocks_per_sm=1),
     dict(thr_blocks_per_sm=32, flat_blocks_per_sm=32), dict(sym_blocks_per_sm=1, pack_blocks_per_sm=1),
-    dict(sym_blocks_per_sm=32, pack_blocks_per_sm=32)])
+    dict(sym_blocks_per_sm=32, pack_blocks_per_sm=32), dict(front_kernel=1),
+    dict(front_kernel=1, front_words=256), dict(front_kernel=1, front_words=16384)])
 def test_any_setting_keeps_the_bytes(rx, setting):
     default = rx.get_tuning()
     try:
@@ -60,7 +61,8 @@ def test_any_setting_keeps_the_bytes(rx, setting):
 def test_set_tuning_rejects_out_of_range(rx):
     import paper_2602_15917_gb300 as roix
     before = rx.get_tuning()
-    for bad in (dict(front_words=100), dict(thr_blocks_per_sm=0), dict(pack_blocks_per_sm=33)):
+    for bad in (dict(front_words=100), dict(thr_blocks_per_sm=0), dict(pack_blocks_per_sm=33),
+                dict(front_kernel=2)):
         with pytest.raises(roix.RoixError) as ei:
             rx.set_tuning(**bad)
         assert ei.value.status == 1
@@ -77,6 +79,7 @@ def test_tune_picks_candidates_caches_and_keeps_bytes(rx, tmp_path):
     assert t["flat_blocks_per_sm"] in (2, 3, 4, 8)
     assert t["sym_blocks_per_sm"] in (0, 1, 2, 3)
     assert t["pack_blocks_per_sm"] in (0, 1, 2, 4)
+    assert t["front_kernel"] in (0, 1)
     assert rx.get_tuning() == t
     entries = json.load(open(cache))
     assert len(entries) == 1
