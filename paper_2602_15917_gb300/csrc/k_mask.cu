@@ -1043,29 +1043,54 @@ __device__ void flush_runs(RunList& rl, u32 nr, int lane, u32& kmin, u32& kmax) 
     rl.ppre[nr] = pacc;
   }
   __syncwarp();
-  // whole 16-byte chunks
-  for (u32 u = lane; u < cacc; u += 32) {
-    const u32 i = run_of(rl.cpre, nr, u);
-    const u32 k = u - rl.cpre[i];
-    const u32 len = rl.len[i];
-    const u64 db = rl.dst[i];
-    const u32 h = umin((u32)(((16u - (db & 15u)) & 15u) / sizeof(TV)), len);
-    const uintptr_t sa = (uintptr_t)rl.src[i] + (uintptr_t)(h + k * kPer) * sizeof(TV);
-    const u32 sh = (u32)(sa & 3u) * 8u;
-    const u32* sw = reinterpret_cast<const u32*>(sa & ~(uintptr_t)3);
-    const u32 w0 = __ldg(sw), w1 = __ldg(sw + 1), w2 = __ldg(sw + 2), w3 = __ldg(sw + 3);
-    const u32 w4 = sh ? __ldg(sw + 4) : 0u;
-    const uint4 v = make_uint4(__funnelshift_r(w0, w1, sh), __funnelshift_r(w1, w2, sh),
-                               __funnelshift_r(w2, w3, sh), __funnelshift_r(w3, w4, sh));
-    *reinterpret_cast<uint4*>(db + (u64)h * sizeof(TV) + 16ull * k) = v;
-    const u32 q[4] = {v.x, v.y, v.z, v.w};
+  // whole 16-byte chunks, four per lane at a time (their loads issued together)
+  constexpr int kU = 4;
+  for (u32 u0 = lane; u0 < cacc; u0 += 32 * kU) {
+    u32 w[kU][5];
+    u64 dq[kU];
+    u32 shq[kU];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if constexpr (sizeof(TV) == 4) {
-        range_add<float>(__uint_as_float(q[j]), kmin, kmax);
-      } else {
-        range_add<unsigned short>((unsigned short)(q[j] & 0xffffu), kmin, kmax);
-        range_add<unsigned short>((unsigned short)(q[j] >> 16), kmin, kmax);
+    for (int q = 0; q < kU; ++q) {
+      const u32 u = u0 + 32u * q;
+      dq[q] = 0;
+      shq[q] = 0;
+#pragma unroll
+      for (int e = 0; e < 5; ++e) w[q][e] = 0u;
+      if (u < cacc) {
+        const u32 i = run_of(rl.cpre, nr, u);
+        const u32 k = u - rl.cpre[i];
+        const u32 len = rl.len[i];
+        const u64 db = rl.dst[i];
+        const u32 h = umin((u32)(((16u - (db & 15u)) & 15u) / sizeof(TV)), len);
+        const uintptr_t sa = (uintptr_t)rl.src[i] + (uintptr_t)(h + k * kPer) * sizeof(TV);
+        shq[q] = (u32)(sa & 3u) * 8u;
+        const u32* sw = reinterpret_cast<const u32*>(sa & ~(uintptr_t)3);
+        w[q][0] = __ldg(sw);
+        w[q][1] = __ldg(sw + 1);
+        w[q][2] = __ldg(sw + 2);
+        w[q][3] = __ldg(sw + 3);
+        if (shq[q]) w[q][4] = __ldg(sw + 4);
+        dq[q] = db + (u64)h * sizeof(TV) + 16ull * k;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kU; ++q) {
+      if (u0 + 32u * q < cacc) {
+        const u32 sh = shq[q];
+        const uint4 v = make_uint4(
+            __funnelshift_r(w[q][0], w[q][1], sh), __funnelshift_r(w[q][1], w[q][2], sh),
+            __funnelshift_r(w[q][2], w[q][3], sh), __funnelshift_r(w[q][3], w[q][4], sh));
+        *reinterpret_cast<uint4*>(dq[q]) = v;
+        const u32 qq[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if constexpr (sizeof(TV) == 4) {
+            range_add<float>(__uint_as_float(qq[j]), kmin, kmax);
+          } else {
+            range_add<unsigned short>((unsigned short)(qq[j] & 0xffffu), kmin, kmax);
+            range_add<unsigned short>((unsigned short)(qq[j] >> 16), kmin, kmax);
+          }
+        }
       }
     }
   }
