@@ -1094,18 +1094,34 @@ __device__ void flush_runs(RunList& rl, u32 nr, int lane, u32& kmin, u32& kmax) 
       }
     }
   }
-  // head and tail elements
-  for (u32 e = lane; e < pacc; e += 32) {
-    const u32 i = run_of(rl.ppre, nr, e);
-    const u32 k = e - rl.ppre[i];
-    const u32 len = rl.len[i];
-    const u64 db = rl.dst[i];
-    const u32 h = umin((u32)(((16u - (db & 15u)) & 15u) / sizeof(TV)), len);
-    const u32 mid = (len - h) / kPer * kPer;
-    const u32 x = k < h ? k : h + mid + (k - h);  // element index within the run
-    const TV vv = __ldg(reinterpret_cast<const TV*>(rl.src[i]) + x);
-    reinterpret_cast<TV*>(db)[x] = vv;
-    range_add<TV>(vv, kmin, kmax);
+  // head and tail elements, four per lane at a time
+  for (u32 e0 = lane; e0 < pacc; e0 += 32 * kU) {
+    TV vq[kU];
+    TV* dp[kU];
+#pragma unroll
+    for (int q = 0; q < kU; ++q) {
+      const u32 e = e0 + 32u * q;
+      dp[q] = nullptr;
+      vq[q] = TV(0);
+      if (e < pacc) {
+        const u32 i = run_of(rl.ppre, nr, e);
+        const u32 k = e - rl.ppre[i];
+        const u32 len = rl.len[i];
+        const u64 db = rl.dst[i];
+        const u32 h = umin((u32)(((16u - (db & 15u)) & 15u) / sizeof(TV)), len);
+        const u32 mid = (len - h) / kPer * kPer;
+        const u32 x = k < h ? k : h + mid + (k - h);  // element index within the run
+        vq[q] = __ldg(reinterpret_cast<const TV*>(rl.src[i]) + x);
+        dp[q] = reinterpret_cast<TV*>(db) + x;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kU; ++q) {
+      if (dp[q]) {
+        *dp[q] = vq[q];
+        range_add<TV>(vq[q], kmin, kmax);
+      }
+    }
   }
   __syncwarp();
 }
