@@ -57,6 +57,27 @@ def group_launches(xs) -> int:
             row = True
     return LAUNCHES_PER_GROUP - 1 + int(flat) + int(row)
 
+# DRAM bytes per step of each stage (dram__bytes_read.sum + dram__bytes_write.sum,
+# summed over the stage's kernels, one launch each), from one ncu capture of the
+# current kernels in the tuned launch configuration this script times for the
+# workload: profiles/kernels_projections64_full.md, profiles/kernels_cube512_full.md.
+# Keyed by the tuning the capture ran with (tile size, counting kernel); another
+# tuning, or a workload without a capture, reports null.
+TRAFFIC_MB = {
+    ("projections64", 2048, 0): {"threshold": 254.68, "front": 127.28, "symbols": 88.10,
+                                 "codebook": 0.57, "pack": 133.90},
+    ("cube512", 2048, 0): {"threshold": 553.65, "front": 216.46, "symbols": 132.23,
+                           "codebook": 0.06, "pack": 128.52},
+}
+
+
+def captured_traffic(workload, tuning, stage):
+    """Bytes per step of `stage` from the ncu capture of this workload and
+    tuning, or None."""
+    t = TRAFFIC_MB.get((workload, tuning.get("front_words"), tuning.get("front_kernel")))
+    return None if t is None or stage not in t else round(t[stage] * 1e6)
+
+
 WORKLOADS = {
     "projections64": dict(
         desc="64 uint16 projections, sides U{512..2048}, I0=60000, dark 100, eb=4 abs, "
@@ -420,7 +441,8 @@ def run_ours(args, rank, world, local_rank):
     ach = alg[names[dom]] / (stage_ms[dom] / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": names[dom], "achieved": round(ach, 1),
                 "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
-                "frac": round(ach / peak, 4), "traffic": None,
+                "frac": round(ach / peak, 4),
+                "traffic": captured_traffic(args.workload, tuning, names[dom]),
                 "algorithmic_bytes_per_step": round(alg[names[dom]]),
                 "stage_ms_per_step": {n: round(float(v), 4) for n, v in zip(names, stage_ms)},
                 "stage_gbs": {n: round(alg[n] / (float(v) / 1e3) / 1e9, 1)
