@@ -780,11 +780,11 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__
 }
 
 // ------------------------------------------------------------------- pack
-// Three passes, none waiting on another block: k_pack_count sums the code
-// lengths of every chunk, k_pack_scan turns the chunks' word and record
-// counts into offsets (one block per item), and k_pack writes every chunk's
-// words at its offset; k_records writes the records of the chunks that have
-// any. Chunks are taken from global tickets in order.
+// Passes none of whose blocks waits on another: k_pack_count sums the code
+// lengths of every chunk, k_scan_pairs<1> turns the chunks' word and record
+// counts into offsets, and k_pack writes every chunk's words at its offset
+// (chunks from global tickets in order); k_records writes the records of the
+// chunks that have any.
 
 // Warps, one chunk at a time: lane l holds symbols [8 l, 8 l + 8) of each
 // round of 256 (coalesced 16-byte loads); the code lengths come from the

@@ -1,6 +1,6 @@
 // Region-of-interest kernels: binarisation (Sec. 4.1.1, 4.1.3-4.1.4), the
 // cube dilation of the retained set, and the extraction of row geometry and
-// pixel section (Sec. 4.2.2) by a single-pass decoupled look-back compaction.
+// pixel section (Sec. 4.2.2) by a compaction in count, scan and write passes.
 //
 // Mask layout: rows = ny*nz rows of W = ceil(nx/32) uint32 words; voxel x of a
 // row is bit x%32 of word x/32; bits at x >= nx are 0.
@@ -387,13 +387,9 @@ __global__ void __launch_bounds__(kThreads) k_dilate(Desc d, const u32* __restri
 }
 
 // ------------------------------------------------------------ compaction
-// Persistent blocks take tiles of `rpt` consecutive rows in increasing order.
-// Per tile: stage the mask rows it needs (three bands of rpt+2 rows for the
-// dilation) in shared memory, form the retained words D and the transition
-// words E (boundaries), count both per warp, obtain the tile's output offsets
-// from the decoupled look-back, then write the pixel values, the boundaries
-// and the per-row boundary counts. Lanes map to the 32 bits of a word, so
-// both the value loads and the compacted stores are coalesced.
+// Tiles of `rpt` consecutive rows: a counting kernel forms each tile's retained
+// words and per-row counts, a scan turns the tile totals into offsets, and
+// k_front_write writes every row's boundaries and values at its offset.
 constexpr u32 kListCap = 512;  // boundaries of one row kept per warp for run copies
 
 // Range of the retained finite values of one item: warp-reduced per-thread

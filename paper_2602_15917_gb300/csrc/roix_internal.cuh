@@ -412,8 +412,9 @@ struct Batch {
   Desc c;                              // shared settings (geometry fields unused)
   u32 n;                               // items
   u32* status;                         // context status word
-  u32* ctr;                            // [7] tickets: front count, symbols, pack count,
-                                       // pack write, front write, front scan, pack scan
+  u32* ctr;                            // [7] tickets: front count (block kernel), symbols,
+                                       // (unused), pack write, front write, front scan,
+                                       // pack scan
   u64 seg0[kMaxBatch + 1];             // prefix of threshold row segments (row-form items)
   u64 fseg0[kMaxBatch + 1];            // prefix of threshold flat spans (flat-form items)
   u64 ftile0[kMaxBatch + 1];           // prefix of front tiles
