@@ -218,6 +218,19 @@ def stage_bytes(xs, outs, sizes, cfg):
     return tot
 
 
+def reduce_over_ranks(value, world, op="max", device=None):
+    """The ranks' `value` combined over the process group: the largest ("max":
+    the slowest rank sets the job's time) or the sum ("sum": every rank's units
+    count toward the job's throughput). One process: `value` itself."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 # ---------------------------------------------------------------- ours
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -303,11 +316,7 @@ def run_ours(args, rank, world, local_rank):
     ms_total = e0.elapsed_time(e1)
     for c, s in zip(ctxs, streams):
         c.sync(s)
-    # max over ranks
-    t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_total = float(t.item())
+    ms_total = reduce_over_ranks(ms_total, world, "max", dev)
     ms_step = ms_total / args.steps
     # latency of one step (the batch completes as a unit): events per step
     step_ms = []
@@ -401,11 +410,7 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
     t0 = time.perf_counter()
     e2e_run(args.steps)
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_s = float(te.item())
+    e2e_s = reduce_over_ranks((time.perf_counter() - t0) / args.steps, world, "max", dev)
     for c, s_ in zip(ctxs, streams):
         c.sync(s_)
     e2e = {"value": in_bytes * world / e2e_s / 1e9, "unit": "GB/s",
