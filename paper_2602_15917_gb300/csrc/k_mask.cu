@@ -448,52 +448,6 @@ __device__ __forceinline__ void range_add(TV v, u32& kmin, u32& kmax) {
   }
 }
 
-// Copy of one run of float32 or uint16 values by a warp, gathering their
-// range: element copies up to the first 16-byte boundary of the destination
-// and after the last one; in between every lane writes aligned 16-byte chunks
-// funnel-shifted out of five aligned source words, two chunks in flight.
-template <typename TV>
-__device__ __forceinline__ void copy_run_vec(const TV* __restrict__ src, TV* __restrict__ dst,
-                                             u32 len, int lane, u32& kmin, u32& kmax) {
-  constexpr u32 kPer = 16 / sizeof(TV);
-  const u32 head = (u32)(((16u - ((uintptr_t)dst & 15u)) & 15u) / sizeof(TV));
-  const u32 hb = umin(head, len);
-  if ((u32)lane < hb) {
-    const TV v = __ldg(src + lane);
-    dst[lane] = v;
-    range_add<TV>(v, kmin, kmax);
-  }
-  const u32 n16 = (len - hb) / kPer;
-  const uintptr_t sa = (uintptr_t)(src + hb);
-  const u32 sh = (u32)(sa & 3u) * 8u;
-  const u32* sw = reinterpret_cast<const u32*>(sa & ~(uintptr_t)3);
-  uint4* dw = reinterpret_cast<uint4*>(dst + hb);
-  for (u32 k = lane; k < n16; k += 32) {
-    const u32 w0 = __ldg(sw + 4 * k), w1 = __ldg(sw + 4 * k + 1), w2 = __ldg(sw + 4 * k + 2),
-              w3 = __ldg(sw + 4 * k + 3);
-    const u32 w4 = sh ? __ldg(sw + 4 * k + 4) : 0u;
-    const uint4 v = make_uint4(__funnelshift_r(w0, w1, sh), __funnelshift_r(w1, w2, sh),
-                               __funnelshift_r(w2, w3, sh), __funnelshift_r(w3, w4, sh));
-    dw[k] = v;
-    const u32 q[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      if constexpr (sizeof(TV) == 4) {
-        range_add<float>(__uint_as_float(q[i]), kmin, kmax);
-      } else {
-        range_add<unsigned short>((unsigned short)(q[i] & 0xffffu), kmin, kmax);
-        range_add<unsigned short>((unsigned short)(q[i] >> 16), kmin, kmax);
-      }
-    }
-  }
-  const u32 done = hb + kPer * n16;
-  for (u32 e = done + lane; e < len; e += 32) {
-    const TV v = __ldg(src + e);
-    dst[e] = v;
-    range_add<TV>(v, kmin, kmax);
-  }
-}
-
 // The compaction runs in three launches, none of whose blocks waits on
 // another: a counting kernel forms the retained words of each tile of rows
 // (dilated from T, stored to the item's D when dilating), the rows' boundary
