@@ -407,31 +407,6 @@ __device__ __forceinline__ void flush_range(State* st, u32& kmin, u32& kmax, int
   kmax = 0u;
 }
 
-// Copy of one run of 8-bit values by a warp: byte copies up to the first
-// 16-byte boundary of the destination and after the last one; in between
-// every lane writes aligned 16-byte chunks, funnel-shifting them out of five
-// aligned source words (each holding at least one byte of the run).
-__device__ __forceinline__ void copy_run_u8(const u8* __restrict__ src, u8* __restrict__ dst,
-                                            u32 len, int lane) {
-  const u32 head = (u32)((16u - ((uintptr_t)dst & 15u)) & 15u);
-  const u32 hb = umin(head, len);
-  if ((u32)lane < hb) dst[lane] = __ldg(src + lane);
-  const u32 n16 = (len - hb) >> 4;
-  const uintptr_t sa = (uintptr_t)(src + hb);
-  const u32 sh = (u32)(sa & 3u) * 8u;
-  const u32* sw = reinterpret_cast<const u32*>(sa & ~(uintptr_t)3);
-  uint4* dw = reinterpret_cast<uint4*>(dst + hb);
-  for (u32 k = lane; k < n16; k += 32) {
-    const u32 w0 = __ldg(sw + 4 * k), w1 = __ldg(sw + 4 * k + 1), w2 = __ldg(sw + 4 * k + 2),
-              w3 = __ldg(sw + 4 * k + 3);
-    const u32 w4 = sh ? __ldg(sw + 4 * k + 4) : 0u;
-    dw[k] = make_uint4(__funnelshift_r(w0, w1, sh), __funnelshift_r(w1, w2, sh),
-                       __funnelshift_r(w2, w3, sh), __funnelshift_r(w3, w4, sh));
-  }
-  const u32 done = hb + 16 * n16;
-  if ((u32)lane < len - done) dst[done + lane] = __ldg(src + done + lane);
-}
-
 // Range key of one value (float32: order-preserving bits of a finite value;
 // uint16: value + 1, so that 0 means none).
 template <typename TV>
@@ -1031,14 +1006,16 @@ __device__ void flush_runs(RunList& rl, u32 nr, int lane, u32& kmin, u32& kmax) 
             __funnelshift_r(w[q][0], w[q][1], sh), __funnelshift_r(w[q][1], w[q][2], sh),
             __funnelshift_r(w[q][2], w[q][3], sh), __funnelshift_r(w[q][3], w[q][4], sh));
         *reinterpret_cast<uint4*>(dq[q]) = v;
-        const u32 qq[4] = {v.x, v.y, v.z, v.w};
+        if constexpr (sizeof(TV) != 1) {  // (8-bit values carry no range)
+          const u32 qq[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          if constexpr (sizeof(TV) == 4) {
-            range_add<float>(__uint_as_float(qq[j]), kmin, kmax);
-          } else {
-            range_add<unsigned short>((unsigned short)(qq[j] & 0xffffu), kmin, kmax);
-            range_add<unsigned short>((unsigned short)(qq[j] >> 16), kmin, kmax);
+          for (int j = 0; j < 4; ++j) {
+            if constexpr (sizeof(TV) == 4) {
+              range_add<float>(__uint_as_float(qq[j]), kmin, kmax);
+            } else {
+              range_add<unsigned short>((unsigned short)(qq[j] & 0xffffu), kmin, kmax);
+              range_add<unsigned short>((unsigned short)(qq[j] >> 16), kmin, kmax);
+            }
           }
         }
       }
@@ -1069,7 +1046,7 @@ __device__ void flush_runs(RunList& rl, u32 nr, int lane, u32& kmin, u32& kmax) 
     for (int q = 0; q < kU; ++q) {
       if (dp[q]) {
         *dp[q] = vq[q];
-        range_add<TV>(vq[q], kmin, kmax);
+        if constexpr (sizeof(TV) != 1) range_add<TV>(vq[q], kmin, kmax);
       }
     }
   }
@@ -1080,11 +1057,11 @@ __device__ void flush_runs(RunList& rl, u32 nr, int lane, u32& kmin, u32& kmax) 
 template <typename TV>
 __global__ void __launch_bounds__(kThreads, 4) k_front_write(const __grid_constant__ Batch B) {
   __shared__ uint16_t blist_all[kThreads / 32][kListCap];
-  __shared__ RunList runs_all[sizeof(TV) == 1 ? 1 : kThreads / 32];
+  __shared__ RunList runs_all[kThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const u32 below = (1u << lane) - 1u;
   uint16_t* lst = blist_all[warp];
-  RunList& rl = runs_all[sizeof(TV) == 1 ? 0 : warp];
+  RunList& rl = runs_all[warp];
   u32 nruns = 0;  // runs gathered and not yet copied
   const u64 total_rows = B.row0[B.n];
   u32 kmin = 0xffffffffu, kmax = 0u;
@@ -1117,10 +1094,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_front_write(const __grid_consta
       const u64 ob = __shfl_sync(0xffffffffu, my_ob, j);
       const Item& I = B.it[item];
       if (item != cur) {  // copy the previous item's runs, flush its value range
-        if constexpr (sizeof(TV) != 1) {
-          if (nruns) flush_runs<TV>(rl, nruns, lane, kmin, kmax);
-          nruns = 0;
-        }
+        if (nruns) flush_runs<TV>(rl, nruns, lane, kmin, kmax);
+        nruns = 0;
         flush_range(cur == 0xffffffffu ? nullptr : B.it[cur].rst, kmin, kmax, lane);
         cur = item;
       }
@@ -1183,20 +1158,16 @@ __global__ void __launch_bounds__(kThreads, 4) k_front_write(const __grid_consta
             const TV* src = irow + xs;
             TV* dst = P + on;
             const u32 len = xe - xs;
-            if constexpr (sizeof(TV) == 1) {
-              copy_run_u8(reinterpret_cast<const u8*>(src), reinterpret_cast<u8*>(dst), len, lane);
-            } else {
-              if (nruns == kRunCap) {  // the list is full: copy what it holds
-                flush_runs<TV>(rl, nruns, lane, kmin, kmax);
-                nruns = 0;
-              }
-              if (lane == 0) {
-                rl.src[nruns] = (u64)(uintptr_t)src;
-                rl.dst[nruns] = (u64)(uintptr_t)dst;
-                rl.len[nruns] = len;
-              }
-              ++nruns;
+            if (nruns == kRunCap) {  // the list is full: copy what it holds
+              flush_runs<TV>(rl, nruns, lane, kmin, kmax);
+              nruns = 0;
             }
+            if (lane == 0) {
+              rl.src[nruns] = (u64)(uintptr_t)src;
+              rl.dst[nruns] = (u64)(uintptr_t)dst;
+              rl.len[nruns] = len;
+            }
+            ++nruns;
             on += len;
           }
         } else {
@@ -1231,10 +1202,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_front_write(const __grid_consta
         }
       __syncwarp();
     }
-    if constexpr (sizeof(TV) != 1) {  // the ticket's runs
-      if (nruns) flush_runs<TV>(rl, nruns, lane, kmin, kmax);
-      nruns = 0;
-    }
+    if (nruns) flush_runs<TV>(rl, nruns, lane, kmin, kmax);  // the ticket's runs
+    nruns = 0;
   }
   flush_range(cur == 0xffffffffu ? nullptr : B.it[cur].rst, kmin, kmax, lane);
 }
