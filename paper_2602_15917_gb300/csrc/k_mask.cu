@@ -907,8 +907,8 @@ __global__ void __launch_bounds__(1024) k_scan_pairs(const __grid_constant__ Bat
   }
 }
 
-// Warps take kRowsPerTicket consecutive rows of the batch (all items' rows in
-// order) per ticket: lane j looks up row j's item, boundary count and offsets (the
+// Warps take up to kRowsPerTicket consecutive rows of the batch (all items' rows
+// in order) per ticket: lane j looks up row j's item, boundary count and offsets (the
 // tile's offset plus the row's offset in its tile); then the warp walks the
 // rows that retain anything: the boundaries (x positions where D turns on or
 // off) are written in order, and the values of each run [x_start, x_end) are
@@ -1066,13 +1066,18 @@ __global__ void __launch_bounds__(kThreads, 4) k_front_write(const __grid_consta
   const u64 total_rows = B.row0[B.n];
   u32 kmin = 0xffffffffu, kmax = 0u;
   u32 cur = 0xffffffffu;  // item whose range the warp accumulates
+  // rows per ticket: kRowsPerTicket, fewer when the batch has too few rows to
+  // give every warp about two tickets (a warp walks a ticket's rows one after
+  // another, so short batches finish sooner spread over more warps)
+  const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
+  const u32 per = (u32)umax(1, umin(kRowsPerTicket, total_rows / (2 * nwarps)));
   while (true) {
     u64 g0 = 0;
-    if (lane == 0) g0 = atomicAdd(&B.ctr[4], kRowsPerTicket);
+    if (lane == 0) g0 = atomicAdd(&B.ctr[4], per);
     g0 = __shfl_sync(0xffffffffu, g0, 0);
     if (g0 >= total_rows) break;
-    // lane j < kRowsPerTicket: row g0 + j's item, boundary count, offsets
-    const u64 g = lane < (int)kRowsPerTicket ? g0 + lane : total_rows;
+    // lane j < per: row g0 + j's item, boundary count, offsets
+    const u64 g = lane < (int)per ? g0 + lane : total_rows;
     u32 my_item = 0, my_nbr = 0;
     u64 my_on = 0, my_ob = 0;
     if (g < total_rows) {
@@ -1302,8 +1307,7 @@ void launch_front(const Launch& L, const Batch& B) {
   launch_scan_pairs(L, B, 0, scan_tiles);
   auto run = [&](auto kernel) {
     u64 g = (u64)occupancy_grid((const void*)kernel, kThreads, 0, L.sms);
-    const u64 need = (B.row0[B.n] + kRowsPerTicket * (kThreads / 32) - 1) /
-                     (kRowsPerTicket * (kThreads / 32));
+    const u64 need = (B.row0[B.n] + (kThreads / 32) - 1) / (kThreads / 32);  // a row per warp
     if (g > need) g = need;
     if (g < 1) g = 1;
     kernel<<<(unsigned)g, kThreads, 0, L.stream>>>(B);
