@@ -64,10 +64,10 @@ def group_launches(xs) -> int:
 # Keyed by the tuning the capture ran with (tile size, counting kernel); another
 # tuning, or a workload without a capture, reports null.
 TRAFFIC_MB = {
-    ("projections64", 2048, 0): {"threshold": 254.68, "front": 127.28, "symbols": 88.10,
-                                 "codebook": 0.57, "pack": 133.90},
-    ("cube512", 2048, 0): {"threshold": 553.65, "front": 216.46, "symbols": 132.23,
-                           "codebook": 0.06, "pack": 128.52},
+    ("projections64", 2048, 0): {"threshold": 254.53, "front": 128.20, "symbols": 88.09,
+                                 "codebook": 0.57, "pack": 133.76},
+    ("cube512", 2048, 0): {"threshold": 553.91, "front": 218.25, "symbols": 132.45,
+                           "codebook": 0.06, "pack": 128.58},
 }
 
 
