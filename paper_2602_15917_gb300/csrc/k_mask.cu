@@ -641,7 +641,6 @@ __device__ __forceinline__ u32 u_of(const URaw& q) { return q.c | q.zlo | q.zhi;
 // column). Per row one warp reduction of the packed counts gives the retained
 // voxels and boundaries; the tile's rows are then scanned in parallel for
 // their offsets within the tile.
-constexpr u32 kMaxTileRows = 256;  // rows of a compaction tile, at most
 
 template <bool DIL>
 __device__ __forceinline__ void front_count_tile(const Batch& B, const Item& I, const Desc& d,

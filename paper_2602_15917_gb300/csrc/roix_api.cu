@@ -185,11 +185,10 @@ bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 size_t dtype_bytes(int dt) { return dt == ROIX_F32 ? 4 : dt == ROIX_U16 ? 2 : 1; }
 
 u32 front_rows_per_tile(const Desc& d) {
-  constexpr u64 kMaxTileRowsHost = 256;
   const u64 target_words = d.front_words ? d.front_words : 2048;
   u64 rpt = d.W ? target_words / d.W : 1;
   if (rpt < 1) rpt = 1;
-  if (rpt > kMaxTileRowsHost) rpt = kMaxTileRowsHost;  // one warp's row totals in shared memory
+  if (rpt > kMaxTileRows) rpt = kMaxTileRows;
   if (rpt > d.rows) rpt = d.rows ? d.rows : 1;
   return (u32)rpt;
 }

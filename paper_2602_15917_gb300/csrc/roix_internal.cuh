@@ -356,6 +356,9 @@ struct Desc {
 // through prefix sums; every item has its own state, look-back descriptors,
 // histogram, codebook and container. A single volume is a batch of one.
 constexpr int kMaxBatch = 64;
+// Rows of a compaction tile, at most: the warp-per-tile counting kernel keeps
+// one warp's row totals (2 x 4 bytes a row) in shared memory.
+constexpr u32 kMaxTileRows = 256;
 
 struct Item {
   u64 nx, ny, nz, rows, W, N;          // geometry
