@@ -278,6 +278,12 @@ class Roix:
         return {k: getattr(t, k) for k, _ in Tuning._fields_}
 
     def set_tuning(self, **kw):
+        """roix_set_tuning with the given fields changed: front_words (mask words
+        per compaction tile), thr_blocks_per_sm / flat_blocks_per_sm
+        (binarisation, row and flat forms), sym_blocks_per_sm,
+        pack_blocks_per_sm (0: as many as fit), front_kernel (compaction
+        counts: 0 a block per tile, 1 a warp per tile). None of them changes an
+        output byte; values out of range raise RoixError (status 1)."""
         cur = self.get_tuning()
         cur.update(kw)
         self._check(self.L.roix_set_tuning(self.ctx, C.byref(Tuning(**cur))))
