@@ -58,16 +58,31 @@ def test_slabs_equal_oracle(rx, ci, slab_z):
     _same(oracle.compress_slabs(x, slab_z, **cfg), _run(rx, x, slab_z, **cfg))
 
 
+@pytest.fixture(params=[0, 1], ids=["front_blk", "front_warp"])
+def front_kernel(rx, request):
+    # both compaction counting kernels: the dilation reads the neighbouring
+    # slabs' mask planes in each (the autotuner may pick either)
+    default = rx.get_tuning()
+    rx.set_tuning(front_kernel=request.param)
+    yield request.param
+    rx.set_tuning(**default)
+
+
 @pytest.mark.parametrize("shape,slab_z", [((40, 33, 100), 16), ((17, 64, 32), 5),
-                                          ((9, 70, 1), 2), ((130, 20, 45), 64)])
-def test_slabs_ragged_shapes(rx, shape, slab_z):
-    x = phantom.porous_cylinder(max(shape), radius=max(shape) * 0.35, seed=3).numpy()
-    x = np.ascontiguousarray(x[:shape[0], :shape[1], :shape[2]])
+                                          ((9, 70, 1), 2), ((130, 20, 45), 64),
+                                          ((12, 9, 1100), 5)])
+def test_slabs_ragged_shapes(rx, front_kernel, shape, slab_z):
     cfg = dict(eb=1e-4, eb_mode="rel", dilate=1)
+    if max(shape) <= 130:
+        x = phantom.porous_cylinder(max(shape), radius=max(shape) * 0.35, seed=3).numpy()
+        x = np.ascontiguousarray(x[:shape[0], :shape[1], :shape[2]])
+    else:  # rows of more than 32 mask words, many short runs across the slab borders
+        x = np.random.default_rng(3).random(shape, dtype=np.float32)
+        cfg["threshold"] = 0.98
     _same(oracle.compress_slabs(x, slab_z, **cfg), _run(rx, x, slab_z, **cfg))
 
 
-def test_slabs_textured_cylinder_sweep(rx):
+def test_slabs_textured_cylinder_sweep(rx, front_kernel):
     # the 2048^3 workload's phantom at 96^3, 16-slice slabs, the eb sweep
     x = phantom.porous_cylinder(96, radius=37.5, texture=True, seed=1).numpy()
     for eb in (1e-2, 1e-3, 1e-4, 1e-5):
