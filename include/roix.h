@@ -127,6 +127,23 @@ size_t roix_workspace_size(roix_dtype dtype, roix_dims dims, const roix_roi* roi
 /* Waits for `stream`, returns the first device-side error since the last call
  * (or ROIX_ECUDA) and clears it. */
 roix_status roix_sync(roix_ctx* ctx, void* stream);
+
+/* Bounded device waits. Some kernels wait on another block of the same launch
+ * (the look-back of the tile scans of compaction and packing, the decoder's
+ * row scans, the run scan of the largest-component step). Each wait gives up
+ * after `polls` polls (0: the default, 2^22, several hundred milliseconds),
+ * records ROIX_ETIMEOUT in the context status and lets its launch end; the
+ * later kernels of the same call then do nothing, so no output is formed from
+ * the missing prefix. roix_sync returns ROIX_ETIMEOUT and clears it, and the
+ * context stays usable. Not in the paper: it is how the library keeps a GPU
+ * from hanging. */
+roix_status roix_set_wait_limit(roix_ctx* ctx, uint32_t polls);
+/* Test hook for the bounded waits (no paper counterpart). While `on` is
+ * nonzero, the first tile of every tile scan that the context launches
+ * (compaction and pack scans of the first item of a batch, decoder row scans)
+ * never publishes its prefix: a flag that nobody sets, so the tile after it
+ * waits until its limit runs out. Off by default. */
+roix_status roix_debug_hold_scans(roix_ctx* ctx, int on);
 const char* roix_last_error(const roix_ctx* ctx);
 const char* roix_status_string(roix_status s);
 /* Words of a bit mask: rows = ny*nz rows of ceil(nx/32) uint32 words; voxel x
@@ -292,20 +309,21 @@ roix_status roix_ssim(roix_ctx* ctx, const void* x, const void* y, roix_dtype dt
                       roix_dims dims, double data_range, double* ssim_dev, void* stream);
 
 /* Allocation-free variant of roix_extract_roi, for callers that cannot
- * allocate device memory when they need a mask: code recording a CUDA graph in
- * global capture mode (where cudaMalloc is refused), acquisition loops that
- * must never block on the device synchronisation that cudaMalloc/cudaFree
- * imply, and processes whose device memory all belongs to another allocator or
- * a fixed budget. The paper has no counterpart; this is an interface choice.
+ * allocate device memory when they need a mask: acquisition loops that must
+ * never block on the device synchronisation that cudaMalloc/cudaFree imply,
+ * and processes whose device memory all belongs to another allocator or a
+ * fixed budget. The paper has no counterpart; this is an interface choice.
  * Same inputs, outputs and results as roix_extract_roi, without a context: it
  * runs on the calling thread's current CUDA device. Its scratch (the mask
  * before dilation) is a 32 MiB device array in the library itself, present on
  * every GPU that loads the library until the process exits; volumes needing
  * more than 2^23 mask words (ny*nz*ceil(nx/32)) return ROIX_EINVAL before
- * anything is enqueued. The first call on a device looks up the array's
- * device address; make that first call before any stream capture. All calls
- * share the array: calls that overlap on the GPU (other streams or host
- * threads on the same device) race and must be serialised by the caller.
+ * anything is enqueued. The array's device address is looked up on every call
+ * whose stream is not capturing (so a device reset, which may move the array,
+ * is followed); a call on a capturing stream reuses the last address found on
+ * that device, so make the first call on a device before any stream capture.
+ * All calls share the array: calls that overlap on the GPU (other streams or
+ * host threads on the same device) race and must be serialised by the caller.
  * Nothing is allocated: no cudaMalloc, no cudaFree. */
 roix_status roix_extract_roi_static(const void* in, roix_dtype dtype, roix_dims dims,
                                     const roix_roi* roi, uint32_t* mask_out,

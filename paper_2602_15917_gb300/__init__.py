@@ -123,6 +123,8 @@ def lib():
                 "roix_reserve": (st, [P, C.c_size_t]),
                 "roix_workspace_size": (C.c_size_t, [i32, D, R, PR, u64]),
                 "roix_sync": (st, [P, P]),
+                "roix_set_wait_limit": (st, [P, C.c_uint32]),
+                "roix_debug_hold_scans": (st, [P, C.c_int]),
                 "roix_last_error": (C.c_char_p, [P]),
                 "roix_status_string": (C.c_char_p, [st]),
                 "roix_mask_words": (u64, [D]),
@@ -170,7 +172,7 @@ def lib():
 def symbols():
     """Names of the entry points the binding knows (all declared in roix.h)."""
     return ["roix_ctx_create", "roix_ctx_destroy", "roix_reserve", "roix_workspace_size",
-            "roix_sync", "roix_last_error", "roix_status_string", "roix_mask_words",
+            "roix_sync", "roix_set_wait_limit", "roix_debug_hold_scans", "roix_last_error", "roix_status_string", "roix_mask_words",
             "roix_compress_bound", "roix_extract_roi", "roix_compact", "roix_quantize",
             "roix_encode", "roix_decode", "roix_compress", "roix_profile",
             "roix_profile_read", "roix_extract_roi_static", "roix_compress_batch",
@@ -249,6 +251,16 @@ class Roix:
 
     def sync(self, stream=None):
         self._check(self.L.roix_sync(self.ctx, _stream(stream)))
+
+    def set_wait_limit(self, polls: int = 0):
+        """roix_set_wait_limit: polls of a bounded device wait before it gives
+        up with ROIX_ETIMEOUT (0: the library's default)."""
+        self._check(self.L.roix_set_wait_limit(self.ctx, int(polls)))
+
+    def debug_hold_scans(self, on: bool = True):
+        """roix_debug_hold_scans: test hook that leaves the first tile of every
+        tile scan unpublished, so that the bounded waits run out."""
+        self._check(self.L.roix_debug_hold_scans(self.ctx, int(on)))
 
     def reserve(self, nbytes: int):
         self._check(self.L.roix_reserve(self.ctx, int(nbytes)))

@@ -53,7 +53,8 @@ __global__ void __launch_bounds__(kThreads) k_run_count(Desc d, const u32* __res
 constexpr u32 kScanPer = 8;
 __global__ void __launch_bounds__(kThreads) k_run_scan(u64 rows, const u32* __restrict__ cnt,
                                                        u64* __restrict__ off, LookBack<1> lb,
-                                                       u32* ctr, u32* status, u64* total) {
+                                                       u32* ctr, u32* status, u64* total,
+                                                       u32 limit) {
   __shared__ u64 scratch[40];
   __shared__ u64 s_tile, s_base;
   const u64 ntiles = (rows + kThreads * kScanPer - 1) / (kThreads * kScanPer);
@@ -73,7 +74,7 @@ __global__ void __launch_bounds__(kThreads) k_run_scan(u64 rows, const u32* __re
     const u64 ex = block_excl_scan<u64>(sum, scratch, &tot);
     if (warp == 0) {
       u64 mine[1] = {tot}, excl[1];
-      lookback_warp<1>(lb, t, mine, excl, status);
+      lookback_warp<1>(lb, t, mine, excl, status, limit);
       if (lane == 0) {
         s_base = excl[0];
         if (t == ntiles - 1) *total = excl[0] + tot;
@@ -399,7 +400,7 @@ void launch_ccl_planar(const Launch& L, const Desc& d, const u32* T, u32 inv, in
   k_run_count<<<gw, kThreads, 0, L.stream>>>(d, T, w.row_runs, out, inv);
   const u64 tiles = (d.rows + kThreads * kScanPer - 1) / (kThreads * kScanPer);
   k_run_scan<<<(unsigned)umin(tiles, (u64)L.sms * 4), kThreads, 0, L.stream>>>(
-      d.rows, w.row_runs, w.row_off, w.lb, w.ctr, w.status, w.total);
+      d.rows, w.row_runs, w.row_off, w.lb, w.ctr, w.status, w.total, d.spin_limit);
   k_run_fill<<<gw, kThreads, 0, L.stream>>>(d, T, w.row_off, w.xs, w.xe, w.par, w.size, inv);
   k_run_union<<<gw, kThreads, 0, L.stream>>>(d, w.row_off, w.total, w.xs, w.xe, w.par);
   k_run_sizes<<<gr, kThreads, 0, L.stream>>>(w.total, w.par, w.xs, w.xe, w.size);
@@ -426,7 +427,7 @@ void launch_keep_largest(const Launch& L, const Desc& d, const u32* T, u32* out,
   k_run_count<<<gw, kThreads, 0, L.stream>>>(d, T, w.row_runs, out, 0u);
   const u64 tiles = (d.rows + kThreads * kScanPer - 1) / (kThreads * kScanPer);
   k_run_scan<<<(unsigned)umin(tiles, (u64)L.sms * 4), kThreads, 0, L.stream>>>(
-      d.rows, w.row_runs, w.row_off, w.lb, w.ctr, w.status, w.total);
+      d.rows, w.row_runs, w.row_off, w.lb, w.ctr, w.status, w.total, d.spin_limit);
   k_run_fill<<<gw, kThreads, 0, L.stream>>>(d, T, w.row_off, w.xs, w.xe, w.par, w.size, 0u);
   k_run_union<<<gw, kThreads, 0, L.stream>>>(d, w.row_off, w.total, w.xs, w.xe, w.par);
   k_run_sizes<<<gr, kThreads, 0, L.stream>>>(w.total, w.par, w.xs, w.xe, w.size);

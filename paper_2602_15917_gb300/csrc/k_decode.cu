@@ -186,16 +186,16 @@ __global__ void __launch_bounds__(kThreads) k_dec_rows(Desc d, const uint8_t* in
     for (u32 j = 0; j < RPT; ++j) {
       const u64 r = r0 + j;
       c[j] = r < d.rows ? rd<uint16_t>(in, off_counts + 2 * r) : 0u;
-      if (c[j] & 1u) s_bad = 1;
+      if (c[j] & 1u) s_bad |= 1;
       csum += c[j];
     }
     u32 ctot;
     const u32 cex = block_excl_scan<u32>(csum, scratch, &ctot);
     if (threadIdx.x == 0) {
       u64 mine[1] = {ctot}, ex[1];
-      lookback<1>(lbb, t, mine, ex, status);
+      if (lookback<1>(lbb, t, mine, ex, status, d.spin_limit, d.hold_scans != 0)) s_bad |= 2;
       s_bb = ex[0];
-      if (t == ntiles - 1 && ex[0] + ctot != nb) s_bad = 1;
+      if (t == ntiles - 1 && ex[0] + ctot != nb) s_bad |= 1;
     }
     __syncthreads();
     u64 b = s_bb + cex;
@@ -209,13 +209,13 @@ __global__ void __launch_bounds__(kThreads) k_dec_rows(Desc d, const uint8_t* in
         u32 prevx = 0;
         for (u32 i = 0; i < c[j]; i += 2) {
           if (b + i + 1 >= nb) {
-            s_bad = 1;
+            s_bad |= 1;
             break;
           }
           const u32 xs = rd<uint16_t>(in, off_bounds + 2 * (b + i));
           const u32 xe = rd<uint16_t>(in, off_bounds + 2 * (b + i + 1));
           if (xs < prevx || xe <= xs || xe > d.nx || (i > 0 && xs == prevx)) {
-            s_bad = 1;
+            s_bad |= 1;
             break;
           }
           vox[j] += xe - xs;
@@ -230,9 +230,9 @@ __global__ void __launch_bounds__(kThreads) k_dec_rows(Desc d, const uint8_t* in
     const u64 vex = block_excl_scan<u64>(vsum, scratch64, &vtot);
     if (threadIdx.x == 0) {
       u64 mine[1] = {vtot}, ex[1];
-      lookback<1>(lbv, t, mine, ex, status);
+      if (lookback<1>(lbv, t, mine, ex, status, d.spin_limit, d.hold_scans != 0)) s_bad |= 2;
       s_vb = ex[0];
-      if (t == ntiles - 1 && ex[0] + vtot != plan[P_N]) s_bad = 1;
+      if (t == ntiles - 1 && ex[0] + vtot != plan[P_N]) s_bad |= 1;
     }
     __syncthreads();
     u64 v = s_vb + vex;
@@ -241,7 +241,12 @@ __global__ void __launch_bounds__(kThreads) k_dec_rows(Desc d, const uint8_t* in
       if (r < d.rows) row_voff[r] = v;
       v += vox[j];
     }
-    if (s_bad && threadIdx.x == 0) corrupt(status, plan);
+    if (s_bad && threadIdx.x == 0) {
+      // a wait that gave up (status ROIX_ETIMEOUT) or an inconsistent container:
+      // the later kernels do nothing
+      if (s_bad & 2) plan[P_OK] = 0;
+      else corrupt(status, plan);
+    }
     __syncthreads();
   }
 }

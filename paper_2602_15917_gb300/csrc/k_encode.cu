@@ -285,6 +285,7 @@ __device__ __forceinline__ void flush_hist(u32* h, unsigned long long* g, u32 S,
 // segment waits for another.
 template <typename TV, bool FROM_Q, int ORDER>
 __global__ void __launch_bounds__(kThreads) k_symbols(const __grid_constant__ Batch B) {
+  if (halted(B.status)) return;  // a tile scan of this call gave up
   using Vec = SymVec<TV, FROM_Q>;
   constexpr int V = Vec::V;
   constexpr u32 kStep = 32u * V;                 // values per warp and step
@@ -584,6 +585,7 @@ __device__ __forceinline__ void huffman_merge_key(const u64* key, u64* wi, int32
 }
 
 __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__ Batch B) {
+  if (halted(B.status)) return;  // a tile scan of this call gave up
   extern __shared__ __align__(16) unsigned char cb_smem[];
   CB_MARK(0)
   const Item& I = B.it[blockIdx.x];
@@ -790,6 +792,7 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__
 // round of 256 (coalesced 16-byte loads); the code lengths come from the
 // item's byte table (2R bytes, read through L1).
 __global__ void __launch_bounds__(kThreads) k_pack_count(const __grid_constant__ Batch B) {
+  if (halted(B.status)) return;  // a tile scan of this call gave up
   __shared__ u64 pre[kMaxBatch + 1];
   __shared__ u64 nn[kMaxBatch];
   const u32 C = B.c.C;
@@ -844,6 +847,7 @@ __global__ void __launch_bounds__(kThreads) k_pack_count(const __grid_constant__
 // codes).
 template <typename TV, bool FROM_Q>
 __global__ void __launch_bounds__(kThreads) k_records(const __grid_constant__ Batch B) {
+  if (halted(B.status)) return;  // a tile scan of this call gave up
   __shared__ u64 pre[kMaxBatch + 1];
   __shared__ ItemEb ieb[kMaxBatch];
   if constexpr (!FROM_Q) items_eb(B, ieb);
@@ -910,6 +914,7 @@ __global__ void __launch_bounds__(kThreads) k_records(const __grid_constant__ Ba
 // offset.
 template <int EPT>
 __global__ void __launch_bounds__(kThreads) k_pack(const __grid_constant__ Batch B) {
+  if (halted(B.status)) return;  // a tile scan of this call gave up
   extern __shared__ unsigned long long wb[];  // [C * kLMax / 64 + 2]
   __shared__ u32 tab[kMaxSym];
   __shared__ u32 scratch[40];
@@ -1024,6 +1029,7 @@ __device__ __forceinline__ void put_bytes(uint8_t* h, u32 off, const void* src, 
 }
 
 __global__ void __launch_bounds__(kThreads) k_finalize(const __grid_constant__ Batch B) {
+  if (halted(B.status)) return;  // a tile scan of this call gave up
   const Item& I = B.it[blockIdx.y];
   const Desc d = desc_of(B, I);
   State* st = I.st;

@@ -824,6 +824,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_front_count(const __grid_consta
 // pack chunks (cw, crec -> cwoff, crecoff; totals nwords, nout).
 template <int MODE>
 __global__ void __launch_bounds__(1024) k_scan_pairs(const __grid_constant__ Batch B) {
+  if (MODE == 1 && halted(B.status)) return;  // the compaction scan of this call gave up
   __shared__ u64 pre[kMaxBatch + 1];
   __shared__ u64 scratch[40];
   __shared__ u64 s_tile, s_ex[2];
@@ -874,7 +875,8 @@ __global__ void __launch_bounds__(1024) k_scan_pairs(const __grid_constant__ Bat
     u64 eb = block_excl_scan<u64>(sb, scratch, &tb);
     if (tid < 32) {
       u64 mine[2] = {ta, tb}, excl[2];
-      lookback_warp<2>(MODE == 0 ? I.lbsf : I.lbsp, t, mine, excl, B.status);
+      lookback_warp<2>(MODE == 0 ? I.lbsf : I.lbsp, t, mine, excl, B.status, B.c.spin_limit,
+                       B.c.hold_scans && item == 0);
       if (lane == 0) {
         s_ex[0] = excl[0];
         s_ex[1] = excl[1];
@@ -1055,6 +1057,7 @@ __device__ void flush_runs(RunList& rl, u32 nr, int lane, u32& kmin, u32& kmax) 
 
 template <typename TV>
 __global__ void __launch_bounds__(kThreads, 4) k_front_write(const __grid_constant__ Batch B) {
+  if (halted(B.status)) return;  // a tile scan of this call gave up
   __shared__ uint16_t blist_all[kThreads / 32][kListCap];
   __shared__ RunList runs_all[kThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1122,88 +1125,88 @@ __global__ void __launch_bounds__(kThreads, 4) k_front_write(const __grid_consta
         nbr = warp_sum(rb);
         if (nbr == 0) continue;
       }
-        const bool fast = nbr <= kListCap;
-        u32 bo = 0;
+      const bool fast = nbr <= kListCap;
+      u32 bo = 0;
+      for (u32 w0 = 0; w0 < W; w0 += 32) {
+        const u32 w = w0 + lane;
+        u32 ev = 0u, ex = 0u;
+        if (w < W) {
+          const u32 dv = __ldg(drow + w) & last_mask(d, w);
+          const u32 pv = w ? __ldg(drow + w - 1) & last_mask(d, w - 1) : 0u;
+          ev = dv ^ ((dv << 1) | (pv >> 31));
+          ex = (end_extra && w == W - 1) ? (dv >> 31) : 0u;
+        }
+        const u32 pb = __popc(ev) + ex;
+        const u32 inc = warp_incl_scan(pb);
+        u32 o = bo + inc - pb;
+        while (ev) {
+          const u32 x = w * 32 + (__ffs(ev) - 1);
+          ev &= ev - 1;
+          if (ob + o < bounds_cap) bounds[ob + o] = (uint16_t)x;
+          else set_status(B.status, ROIX_ECAPACITY);
+          if (fast && o < kListCap) lst[o] = (uint16_t)x;
+          ++o;
+        }
+        if (ex) {
+          if (ob + o < bounds_cap) bounds[ob + o] = (uint16_t)d.nx;
+          else set_status(B.status, ROIX_ECAPACITY);
+          if (fast && o < kListCap) lst[o] = (uint16_t)d.nx;
+        }
+        bo += __shfl_sync(0xffffffffu, inc, 31);
+      }
+      __syncwarp();
+      if (bo != nbr) {  // the row's count disagrees with its mask: copy nothing
+        set_status(B.status, ROIX_ECORRUPT);
+        continue;
+      }
+      if (fast) {
+        for (u32 i = 0; i < nbr; i += 2) {
+          const u32 xs = lst[i], xe = lst[i + 1];
+          const TV* src = irow + xs;
+          TV* dst = P + on;
+          const u32 len = xe - xs;
+          if (nruns == kRunCap) {  // the list is full: copy what it holds
+            flush_runs<TV>(rl, nruns, lane, kmin, kmax);
+            nruns = 0;
+          }
+          if (lane == 0) {
+            rl.src[nruns] = (u64)(uintptr_t)src;
+            rl.dst[nruns] = (u64)(uintptr_t)dst;
+            rl.len[nruns] = len;
+          }
+          ++nruns;
+          on += len;
+        }
+      } else {
+        // many short runs: lanes take the bits of one word at a time
         for (u32 w0 = 0; w0 < W; w0 += 32) {
-          const u32 w = w0 + lane;
-          u32 ev = 0u, ex = 0u;
-          if (w < W) {
-            const u32 dv = __ldg(drow + w) & last_mask(d, w);
-            const u32 pv = w ? __ldg(drow + w - 1) & last_mask(d, w - 1) : 0u;
-            ev = dv ^ ((dv << 1) | (pv >> 31));
-            ex = (end_extra && w == W - 1) ? (dv >> 31) : 0u;
-          }
-          const u32 pb = __popc(ev) + ex;
-          const u32 inc = warp_incl_scan(pb);
-          u32 o = bo + inc - pb;
-          while (ev) {
-            const u32 x = w * 32 + (__ffs(ev) - 1);
-            ev &= ev - 1;
-            if (ob + o < bounds_cap) bounds[ob + o] = (uint16_t)x;
-            else set_status(B.status, ROIX_ECAPACITY);
-            if (fast && o < kListCap) lst[o] = (uint16_t)x;
-            ++o;
-          }
-          if (ex) {
-            if (ob + o < bounds_cap) bounds[ob + o] = (uint16_t)d.nx;
-            else set_status(B.status, ROIX_ECAPACITY);
-            if (fast && o < kListCap) lst[o] = (uint16_t)d.nx;
-          }
-          bo += __shfl_sync(0xffffffffu, inc, 31);
-        }
-        __syncwarp();
-        if (bo != nbr) {  // the row's count disagrees with its mask: copy nothing
-          set_status(B.status, ROIX_ECORRUPT);
-          continue;
-        }
-        if (fast) {
-          for (u32 i = 0; i < nbr; i += 2) {
-            const u32 xs = lst[i], xe = lst[i + 1];
-            const TV* src = irow + xs;
-            TV* dst = P + on;
-            const u32 len = xe - xs;
-            if (nruns == kRunCap) {  // the list is full: copy what it holds
-              flush_runs<TV>(rl, nruns, lane, kmin, kmax);
-              nruns = 0;
-            }
-            if (lane == 0) {
-              rl.src[nruns] = (u64)(uintptr_t)src;
-              rl.dst[nruns] = (u64)(uintptr_t)dst;
-              rl.len[nruns] = len;
-            }
-            ++nruns;
-            on += len;
-          }
-        } else {
-          // many short runs: lanes take the bits of one word at a time
-          for (u32 w0 = 0; w0 < W; w0 += 32) {
-            const u32 dv_l = w0 + lane < W ? __ldg(drow + w0 + lane) & last_mask(d, w0 + lane) : 0u;
-            const u32 pn = __popc(dv_l);
-            const u32 sn = warp_incl_scan(pn) - pn;
-            u32 nz = __ballot_sync(0xffffffffu, dv_l != 0u);
-            while (nz) {
-              const int k = __ffs(nz) - 1;
-              nz &= nz - 1;
-              const u32 dv = __shfl_sync(0xffffffffu, dv_l, k);
-              const u32 so = __shfl_sync(0xffffffffu, sn, k);
-              if ((dv >> lane) & 1u) {
-                const TV v = __ldg(irow + (u64)(w0 + k) * 32 + lane);
-                P[on + so + __popc(dv & below)] = v;
-                if constexpr (sizeof(TV) == 4) {
-                  if (isfinite(v)) {
-                    const u32 kq = f32_key(__fadd_rn(v, 0.0f));
-                    kmin = min(kmin, kq);
-                    kmax = max(kmax, kq);
-                  }
-                } else {
-                  kmin = min(kmin, (u32)v + 1u);
-                  kmax = max(kmax, (u32)v + 1u);
+          const u32 dv_l = w0 + lane < W ? __ldg(drow + w0 + lane) & last_mask(d, w0 + lane) : 0u;
+          const u32 pn = __popc(dv_l);
+          const u32 sn = warp_incl_scan(pn) - pn;
+          u32 nz = __ballot_sync(0xffffffffu, dv_l != 0u);
+          while (nz) {
+            const int k = __ffs(nz) - 1;
+            nz &= nz - 1;
+            const u32 dv = __shfl_sync(0xffffffffu, dv_l, k);
+            const u32 so = __shfl_sync(0xffffffffu, sn, k);
+            if ((dv >> lane) & 1u) {
+              const TV v = __ldg(irow + (u64)(w0 + k) * 32 + lane);
+              P[on + so + __popc(dv & below)] = v;
+              if constexpr (sizeof(TV) == 4) {
+                if (isfinite(v)) {
+                  const u32 kq = f32_key(__fadd_rn(v, 0.0f));
+                  kmin = min(kmin, kq);
+                  kmax = max(kmax, kq);
                 }
+              } else {
+                kmin = min(kmin, (u32)v + 1u);
+                kmax = max(kmax, (u32)v + 1u);
               }
             }
-            on += __shfl_sync(0xffffffffu, sn + pn, 31);
           }
+          on += __shfl_sync(0xffffffffu, sn + pn, 31);
         }
+      }
       __syncwarp();
     }
     if (nruns) flush_runs<TV>(rl, nruns, lane, kmin, kmax);  // the ticket's runs

@@ -123,6 +123,8 @@ roix_status roix::make_desc(roix_ctx* ctx, roix_dtype dtype, roix_dims dims, con
   d->N = dims.nx * dims.ny * dims.nz;
   d->dtype = dtype;
   d->front_words = ctx ? ctx->tune.front_words : 2048;
+  d->spin_limit = ctx ? ctx->spin_limit : 0u;
+  d->hold_scans = ctx ? (ctx->hold_scans ? 1u : 0u) : 0u;
   if (roi) {
     if (roi->cmp != 0 && roi->cmp != 1) return fail(ctx, ROIX_EINVAL, "roi.cmp must be 0 or 1");
     if (roi->keep != 0 && roi->keep != 1) return fail(ctx, ROIX_EINVAL, "roi.keep must be 0 or 1");
@@ -568,6 +570,18 @@ roix_status roix_sync(roix_ctx* ctx, void* stream) {
     ctx->err = std::string("device reported: ") + roix_status_string((roix_status)st);
     return (roix_status)st;
   }
+  return ROIX_OK;
+}
+
+roix_status roix_set_wait_limit(roix_ctx* ctx, uint32_t polls) {
+  if (!ctx) return ROIX_EINVAL;
+  ctx->spin_limit = polls;
+  return ROIX_OK;
+}
+
+roix_status roix_debug_hold_scans(roix_ctx* ctx, int on) {
+  if (!ctx) return ROIX_EINVAL;
+  ctx->hold_scans = on ? 1 : 0;
   return ROIX_OK;
 }
 

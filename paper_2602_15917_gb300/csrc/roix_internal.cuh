@@ -55,10 +55,14 @@ __device__ __forceinline__ u32 ld_relaxed32(const u32* p) {
 // taken in increasing order from an atomic counter: a tile publishes its
 // aggregate, walks back over predecessors until one has published an
 // inclusive prefix, then publishes its own inclusive prefix. NV 64-bit sums
-// are carried. Every wait is bounded: after kSpinLimit polls the tile gives up,
-// records ROIX_ETIMEOUT and treats the missing value as 0 (results invalid,
-// the kernel still ends).
+// are carried. Every wait is bounded: after `limit` polls (0: kSpinLimit) the
+// tile gives up, records ROIX_ETIMEOUT, treats the missing value as 0 and
+// returns true (results invalid, the kernel still ends; the kernels after it
+// in the same call see the status and do nothing).
 constexpr u32 kSpinLimit = 1u << 22;
+__host__ __device__ __forceinline__ u32 spin_limit_of(u32 limit) {
+  return limit ? limit : kSpinLimit;
+}
 
 template <int NV>
 struct LookBack {
@@ -67,15 +71,20 @@ struct LookBack {
   u64* inc;    // [tiles * NV]
 };
 
+// hold: tile 0 publishes nothing (a flag that nobody sets; test hook for the
+// bounded waits of the tiles after it)
 template <int NV>
-__device__ void lookback(LookBack<NV> lb, u64 t, const u64 (&mine)[NV], u64 (&excl)[NV],
-                         u32* status) {
+__device__ bool lookback(LookBack<NV> lb, u64 t, const u64 (&mine)[NV], u64 (&excl)[NV],
+                         u32* status, u32 limit, bool hold = false) {
   for (int i = 0; i < NV; ++i) excl[i] = 0;
   if (t == 0) {
+    if (hold) return false;
     for (int i = 0; i < NV; ++i) st_relaxed(&lb.inc[i], mine[i]);
     st_release(&lb.flags[0], 2u);
-    return;
+    return false;
   }
+  limit = spin_limit_of(limit);
+  bool timed_out = false;
   for (int i = 0; i < NV; ++i) st_relaxed(&lb.agg[t * NV + i], mine[i]);
   st_release(&lb.flags[t], 1u);
   u64 j = t - 1;
@@ -83,8 +92,9 @@ __device__ void lookback(LookBack<NV> lb, u64 t, const u64 (&mine)[NV], u64 (&ex
   while (true) {
     u32 f = ld_acquire(&lb.flags[j]);
     if (f == 0) {
-      if (++spins > kSpinLimit) {
+      if (++spins > limit) {
         set_status(status, ROIX_ETIMEOUT);
+        timed_out = true;
         break;
       }
       __nanosleep(64);
@@ -100,6 +110,7 @@ __device__ void lookback(LookBack<NV> lb, u64 t, const u64 (&mine)[NV], u64 (&ex
   }
   for (int i = 0; i < NV; ++i) st_relaxed(&lb.inc[t * NV + i], excl[i] + mine[i]);
   st_release(&lb.flags[t], 2u);
+  return timed_out;
 }
 
 // Warp-parallel form (Merrill & Garland's window variant): all 32 lanes of one
@@ -108,17 +119,19 @@ __device__ void lookback(LookBack<NV> lb, u64 t, const u64 (&mine)[NV], u64 (&ex
 // published; their aggregates and that prefix are summed by a warp reduction.
 // Returns the exclusive prefix in every lane. Bounded like lookback().
 template <int NV>
-__device__ void lookback_warp(LookBack<NV> lb, u64 t, const u64 (&mine)[NV], u64 (&excl)[NV],
-                              u32* status) {
+__device__ bool lookback_warp(LookBack<NV> lb, u64 t, const u64 (&mine)[NV], u64 (&excl)[NV],
+                              u32* status, u32 limit, bool hold = false) {
   const int lane = threadIdx.x & 31;
   for (int i = 0; i < NV; ++i) excl[i] = 0;
   if (t == 0) {
-    if (lane == 0) {
+    if (lane == 0 && !hold) {
       for (int i = 0; i < NV; ++i) st_relaxed(&lb.inc[i], mine[i]);
       st_release(&lb.flags[0], 2u);
     }
-    return;
+    return false;
   }
+  limit = spin_limit_of(limit);
+  bool timed_out = false;
   if (lane == 0) {
     for (int i = 0; i < NV; ++i) st_relaxed(&lb.agg[t * NV + i], mine[i]);
     st_release(&lb.flags[t], 1u);
@@ -133,8 +146,9 @@ __device__ void lookback_warp(LookBack<NV> lb, u64 t, const u64 (&mine)[NV], u64
     const int first = incl ? __ffs(incl) - 1 : 32;
     const u32 need = first == 32 ? 0xffffffffu : (0xffffffffu >> (31 - first));
     if (zero & need) {
-      if (++spins > kSpinLimit) {
+      if (++spins > limit) {
         if (lane == 0) set_status(status, ROIX_ETIMEOUT);
+        timed_out = true;
         break;
       }
       __nanosleep(32);
@@ -156,6 +170,14 @@ __device__ void lookback_warp(LookBack<NV> lb, u64 t, const u64 (&mine)[NV], u64
     for (int i = 0; i < NV; ++i) st_relaxed(&lb.inc[t * NV + i], excl[i] + mine[i]);
     st_release(&lb.flags[t], 2u);
   }
+  return timed_out;
+}
+
+// A kernel of the compression path that runs after a tile scan: true when a
+// bounded wait of this call gave up (ROIX_ETIMEOUT), so that nothing is
+// computed from the scan's invalid offsets.
+__device__ __forceinline__ bool halted(const u32* status) {
+  return ld_relaxed32(status) == (u32)ROIX_ETIMEOUT;
 }
 
 // ------------------------------------------------------------------- scans
@@ -347,6 +369,8 @@ struct Desc {
   u32 R, S, C;
   u32 front_words;             // compaction tile size (mask words), from the tuning
   u32 order;                   // Lorenzo order of the prediction: 1 or 2
+  u32 spin_limit;              // polls of a bounded device wait (0: kSpinLimit)
+  u32 hold_scans;              // test hook: the first tile of each tile scan never publishes
 };
 
 // ------------------------------------------------------------------ batches
@@ -424,6 +448,9 @@ struct Batch {
   u64 row0[kMaxBatch + 1];             // prefix of rows
   Item it[kMaxBatch];
 };
+// Kernels take the batch by value as a __grid_constant__ parameter: it must
+// stay within the 32,764 bytes of kernel parameters a launch may carry.
+static_assert(sizeof(Batch) <= 32764, "Batch exceeds the kernel parameter limit");
 
 __device__ __forceinline__ Desc desc_of(const Batch& B, const Item& I) {
   Desc d = B.c;
@@ -539,6 +566,8 @@ struct roix_ctx {
   std::string err;
   int profile = 0;        // per-stage events in the fused path
   roix::Tuning tune{};    // launch shapes (roix_tune / roix_set_tuning)
+  roix::u32 spin_limit = 0;  // polls of a bounded device wait (0: the default)
+  int hold_scans = 0;        // test hook (roix_debug_hold_scans)
   cudaEvent_t ev[16] = {};
   int nev = 0;
 };

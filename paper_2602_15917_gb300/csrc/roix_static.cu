@@ -1,13 +1,12 @@
 // Allocation-free ROI extraction: roix_extract_roi_static.
 //
 // Some callers cannot allocate device memory at the moment they need a mask:
-// code that is recording a CUDA graph in global capture mode (cudaMalloc is
-// refused there), acquisition loops that must never stall on the implicit
-// device synchronisation of cudaMalloc/cudaFree, and processes whose device
-// memory is entirely handed out by another allocator or a fixed HBM budget.
-// This entry point serves them: it keeps its scratch (the thresholded bit
-// mask before dilation) in one file-scope device array instead of a context
-// workspace, and allocates nothing.
+// acquisition loops that must never stall on the implicit device
+// synchronisation of cudaMalloc/cudaFree, and processes whose device memory is
+// entirely handed out by another allocator or a fixed HBM budget. This entry
+// point serves them: it keeps its scratch (the thresholded bit mask before
+// dilation) in one file-scope device array instead of a context workspace,
+// and allocates nothing.
 //
 // The array is kStaticScratchBytes = 32 MiB on every GPU that loads the
 // library, held until the process exits. It fits the mask of a volume with at
@@ -37,15 +36,22 @@ void* g_scratch_addr[kMaxDevices] = {};
 int g_scratch_sms[kMaxDevices] = {};
 
 // Device address of the array on the current device. In host code the
-// array's name is only a host-side stand-in, so the address is looked up once
-// per device, with that device current, and cached.
-cudaError_t scratch_for_current_device(void** addr, int* sms) {
+// array's name is only a host-side stand-in, so the address is looked up with
+// that device current. The lookup is repeated on every call whose stream is
+// not capturing (a device reset reloads the module, possibly elsewhere); a
+// call on a capturing stream uses the address of the last lookup on that
+// device, and the first call on a device must come before any stream capture.
+cudaError_t scratch_for_current_device(cudaStream_t stream, void** addr, int* sms) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  const bool capturing =
+      cudaStreamIsCapturing(stream, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone;
+  if (capturing) cudaGetLastError();  // clear a refusal of the query itself
   std::lock_guard<std::mutex> lock(g_setup_mu);
-  if (!g_scratch_addr[dev]) {
+  if (!capturing || !g_scratch_addr[dev]) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_static_scratch);
     if (e != cudaSuccess) return e;
@@ -71,13 +77,13 @@ extern "C" roix_status roix_extract_roi_static(const void* in, roix_dtype dtype,
   if (d.rows * d.W > kStaticMaxWords) return ROIX_EINVAL;  // beyond the static scratch
   if (d.keep) return ROIX_EINVAL;
   if ((d.N && (!in || !mask_out)) || !popcount_dev) return ROIX_EINVAL;
+  cudaStream_t cs = (cudaStream_t)stream;
   void* scratch = nullptr;
   int sms = 0;
-  if (scratch_for_current_device(&scratch, &sms) != cudaSuccess) {
+  if (scratch_for_current_device(cs, &scratch, &sms) != cudaSuccess) {
     cudaGetLastError();
     return ROIX_ECUDA;
   }
-  cudaStream_t cs = (cudaStream_t)stream;
   Launch L{cs, sms};
   if (cudaMemsetAsync(popcount_dev, 0, 8, cs) != cudaSuccess) {
     cudaGetLastError();
