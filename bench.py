@@ -58,24 +58,21 @@ def group_launches(xs) -> int:
     return LAUNCHES_PER_GROUP - 1 + int(flat) + int(row)
 
 # DRAM bytes per step of each stage (dram__bytes_read.sum + dram__bytes_write.sum,
-# summed over the stage's kernels, one launch each), from one ncu capture of the
-# current kernels in the tuned launch configuration this script times for the
-# workload: profiles/kernels_projections64_full.md, profiles/kernels_cube512_full.md.
-# Keyed by the tuning the capture ran with (tile size, counting kernel); another
-# tuning, or a workload without a capture, reports null.
-TRAFFIC_MB = {
-    ("projections64", 2048, 0): {"threshold": 254.53, "front": 128.20, "symbols": 88.09,
-                                 "codebook": 0.57, "pack": 133.76},
-    ("cube512", 2048, 0): {"threshold": 553.91, "front": 218.25, "symbols": 132.45,
-                           "codebook": 0.06, "pack": 128.58},
-}
+# summed over the stage's kernels, one launch each) from an ncu capture of the
+# current kernels, keyed by workload and the tuning the capture ran with (tile
+# size, counting kernel), with the capture it came from. A workload, tuning or
+# kernel without such a capture reports null: an entry is removed whenever a
+# kernel of its stage changes.
+TRAFFIC_MB = {}
 
 
 def captured_traffic(workload, tuning, stage):
-    """Bytes per step of `stage` from the ncu capture of this workload and
-    tuning, or None."""
+    """(bytes per step of `stage`, capture name) from the ncu capture of this
+    workload and tuning, or (None, None)."""
     t = TRAFFIC_MB.get((workload, tuning.get("front_words"), tuning.get("front_kernel")))
-    return None if t is None or stage not in t else round(t[stage] * 1e6)
+    if t is None or stage not in t:
+        return None, None
+    return round(t[stage] * 1e6), t["source"]
 
 
 WORKLOADS = {
@@ -232,20 +229,22 @@ def reduce_over_ranks(value, world, op="max", device=None):
 
 
 # ---------------------------------------------------------------- ours
-def run_ours(args, rank, world, local_rank):
+STAGES = ["reset", "threshold", "front", "symbols", "codebook", "pack", "finalize"]
+
+
+def measure(args, workload, xs, cfg, path, dev, world, local_rank, tuning=None, e2e=False):
+    """Times one workload's step (one batch of xs) on the device: `path`
+    "batch" is one roix_compress_batch call per 64 items, "plain" one
+    roix_compress call per item (spread over up to args.streams contexts and
+    streams); either is captured in a CUDA graph. Returns the measurement
+    (value, ms_per_step, latency, clocks, roofline, ...) with the device
+    containers of the last step."""
     import torch
     import torch.distributed as dist
     import paper_2602_15917_gb300 as roix
 
-    dev = torch.device("cuda", local_rank)
-    torch.cuda.set_device(dev)
-    wl = WORKLOADS[args.workload]
-    cfg = dict(wl["cfg"], predictor=args.predictor)
-    xs = make_inputs(args.workload, dev, seed=args.seed)
-    torch.cuda.synchronize()
     in_bytes = sum(x.numel() * x.element_size() for x in xs)
-    esz = xs[0].element_size()
-    nstreams = min(args.streams, len(xs))
+    nstreams = min(args.streams, len(xs)) if path == "plain" else 1
     ctxs = [roix.Roix(local_rank) for _ in range(nstreams)]
     streams = [torch.cuda.Stream(dev) for _ in range(nstreams)]
     caps = [x.numel() * x.element_size() + 65536 for x in xs]
@@ -260,32 +259,35 @@ def run_ours(args, rank, world, local_rank):
     # launch shapes picked by the autotuner on this very workload (no output byte changes);
     # --tune 0 keeps the default shapes (e.g. for profiling runs)
     t0 = time.perf_counter()
-    tuning = (ctxs[0].tune(xs, outs=outs, caps=caps, sizes=sizes, reps=7, stream=main, **cfg)
-              if args.tune else ctxs[0].get_tuning())
+    if tuning is None:
+        tuning = (ctxs[0].tune(xs, outs=outs, caps=caps, sizes=sizes, reps=7, stream=main, **cfg)
+                  if args.tune else ctxs[0].get_tuning())
+    tuning = {k: v for k, v in tuning.items() if k != "seconds"}
     tune_s = time.perf_counter() - t0
-    for c in ctxs[1:]:
+    for c in ctxs:
         c.set_tuning(**tuning)
 
-    if args.path == "batch":
-        def step(inputs):
-            ctxs[0].compress_batch(inputs, outs=outs, caps=caps, sizes=sizes, stream=main, **cfg)
+    if path == "batch":
+        def step(inputs, outs_=outs, sizes_=sizes):
+            ctxs[0].compress_batch(inputs, outs=outs_, caps=caps, sizes=sizes_, stream=main, **cfg)
         launches_per_step = sum(group_launches(xs[g:g + 64]) for g in range(0, len(xs), 64))
     else:
-        def step(inputs):
-            for s in streams:
-                s.wait_stream(main)
+        def step(inputs, outs_=outs, sizes_=sizes):
+            for s_ in streams:
+                s_.wait_stream(main)
             for i, x in enumerate(inputs):
                 k = i % nstreams
-                ctxs[k].compress(x, out=outs[i], cap=caps[i], size=sizes[i:i + 1],
+                ctxs[k].compress(x, out=outs_[i], cap=caps[i], size=sizes_[i:i + 1],
                                  stream=streams[k], **cfg)
-            for s in streams:
-                main.wait_stream(s)
+            for s_ in streams:
+                main.wait_stream(s_)
         launches_per_step = sum(group_launches([x]) for x in xs)
 
-    # correctness of the measured configuration: one step, sizes vs a re-run
+    # one untimed step outside any graph; its status is checked
     step(xs)
-    for c, s in zip(ctxs, streams):
-        c.sync(s)
+    torch.cuda.synchronize()
+    for c in ctxs:
+        c.sync()
     graph = None
     if args.graph:
         try:
@@ -314,8 +316,8 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         dist.barrier()
     ms_total = e0.elapsed_time(e1)
-    for c, s in zip(ctxs, streams):
-        c.sync(s)
+    for c in ctxs:
+        c.sync()
     ms_total = reduce_over_ranks(ms_total, world, "max", dev)
     ms_step = ms_total / args.steps
     # latency of one step (the batch completes as a unit): events per step
@@ -329,16 +331,68 @@ def run_ours(args, rank, world, local_rank):
         step_ms.append(a.elapsed_time(b))
     latency = {"p50_ms": round(float(np.percentile(step_ms, 50)), 4),
                "p99_ms": round(float(np.percentile(step_ms, 99)), 4),
-               "of": "one step (the whole batch) from launch to completion"}
+               "of": "one step (%s) from launch to completion" %
+                     ("the whole batch" if len(xs) > 1 else "one volume")}
     value = in_bytes * world / (ms_step / 1e3) / 1e9
     out_bytes = int(sizes.sum().item())
 
-    # end to end: every step copies its inputs from pinned host memory (one
-    # contiguous buffer, one copy), compresses them and reads the containers
-    # back to pinned host memory. Two device buffer sets let step k+1's upload
-    # overlap step k's compression and step k-1's read-back (copy stream +
-    # compute stream, events between them).
-    sz_list = [int(v) for v in sizes.cpu().numpy()]
+    e2e_res = None
+    if e2e:
+        e2e_res = measure_e2e(args, xs, cfg, path, ctxs, main, caps, outs, sizes,
+                              graph is not None, dev, world, in_bytes)
+
+    # dominant stage: per-stage CUDA events on the launching stream between
+    # the kernels of one step (a profiling pass after the timed region)
+    prof = ctxs[0]
+    prof.profile(True)
+    stage_ms = np.zeros(8)
+    reps = 3
+    for _ in range(reps):
+        if path == "batch":
+            step(xs)
+            st = prof.profile_read(8)
+            stage_ms[:len(st)] += st
+        else:
+            for i, x in enumerate(xs):
+                prof.compress(x, out=outs[i], cap=caps[i], size=sizes[i:i + 1], stream=main, **cfg)
+                st = prof.profile_read(8)
+                stage_ms[:len(st)] += st
+    prof.profile(False)
+    torch.cuda.synchronize()
+    for c in ctxs:
+        c.sync()
+    stage_ms /= reps
+    dom = int(np.argmax(stage_ms[:7]))
+    peak, peak_kind = load_peaks()
+    alg = stage_bytes(xs, outs, sizes.cpu().numpy(), cfg)
+    ach = alg[STAGES[dom]] / (stage_ms[dom] / 1e3) / 1e9
+    traffic, traffic_src = captured_traffic(workload, tuning, STAGES[dom])
+    roofline = {"bound": "hbm", "kernel": STAGES[dom], "achieved": round(ach, 1),
+                "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
+                "frac": round(ach / peak, 4), "traffic": traffic, "traffic_source": traffic_src,
+                "algorithmic_bytes_per_step": round(alg[STAGES[dom]]),
+                "stage_ms_per_step": {n: round(float(v), 4) for n, v in zip(STAGES, stage_ms)},
+                "stage_gbs": {n: round(alg[n] / (float(v) / 1e3) / 1e9, 1)
+                              for n, v in zip(STAGES, stage_ms) if v > 0}}
+    for c in ctxs:
+        c.close()
+    return {"value": value, "ms_per_step": ms_step, "in_bytes": in_bytes, "out_bytes": out_bytes,
+            "latency": latency, "clocks": clk.summary(), "roofline": roofline,
+            "launches_per_step": launches_per_step, "graph": graph is not None,
+            "tuning": dict(tuning, seconds=round(tune_s, 2)), "nstreams": nstreams,
+            "outs": outs, "sizes": sizes, "e2e": e2e_res}
+
+
+def measure_e2e(args, xs, cfg, path, ctxs, main, caps, outs, sizes, use_graph, dev, world,
+                in_bytes):
+    """The same step end to end through host buffers: every step copies its
+    inputs from pinned host memory (one contiguous buffer, one copy) and reads
+    the containers back to pinned host memory, learning their sizes on the
+    way: the step's size array is copied first and, once it has arrived, each
+    container is read back with exactly its size. Two device buffer sets let
+    step k+1's upload overlap step k's compression and step k-1's read-back
+    (copy streams + compute stream, events between them)."""
+    import torch
     offs, tot = [], 0
     for x in xs:
         offs.append(tot)
@@ -352,13 +406,13 @@ def run_ours(args, rank, world, local_rank):
                for x, o in zip(xs, offs)] for b in range(2)]
     outs2 = [outs, [torch.empty_like(o) for o in outs]]
     sizes2 = [sizes, torch.zeros_like(sizes)]
-    host_out = torch.empty(sum(sz_list) + 16 * len(xs), dtype=torch.uint8).pin_memory()
-    host_sizes = torch.empty(len(xs), dtype=torch.uint64).pin_memory()
+    host_out = torch.empty(sum(caps), dtype=torch.uint8).pin_memory()
+    host_sizes = [torch.empty(len(xs), dtype=torch.int64).pin_memory() for _ in range(2)]
     up = torch.cuda.Stream(dev)    # host -> device uploads
     down = torch.cuda.Stream(dev)  # device -> host read-backs (own FIFO, so uploads never wait)
 
     def compute(b):
-        if args.path == "batch":
+        if path == "batch":
             ctxs[0].compress_batch(dev_in[b], outs=outs2[b], caps=caps, sizes=sizes2[b],
                                    stream=main, **cfg)
         else:
@@ -367,7 +421,7 @@ def run_ours(args, rank, world, local_rank):
                                  stream=main, **cfg)
 
     graphs = [None, None]
-    if graph is not None:
+    if use_graph:
         for b in range(2):
             compute(b)  # warm-up outside capture
             torch.cuda.synchronize()
@@ -377,9 +431,25 @@ def run_ours(args, rank, world, local_rank):
             graphs[b] = gb
     ev_up = [torch.cuda.Event() for _ in range(2)]
     ev_done = [torch.cuda.Event() for _ in range(2)]
+    ev_sizes = [torch.cuda.Event() for _ in range(2)]
     ev_read = [torch.cuda.Event() for _ in range(2)]
+    d2h = [0]
+
+    def read_back(b):
+        # the sizes of step b have arrived: read each container with its size
+        ev_sizes[b].synchronize()
+        szs = host_sizes[b].tolist()
+        with torch.cuda.stream(down):
+            o = 0
+            for i in range(len(xs)):
+                n = int(szs[i])
+                host_out[o:o + n].copy_(outs2[b][i][:n], non_blocking=True)
+                o += n
+            ev_read[b].record(down)
+        d2h[0] += sum(szs) + 8 * len(xs)
 
     def e2e_run(k_steps):
+        pending = None
         for k in range(k_steps):
             b = k % 2
             with torch.cuda.stream(up):
@@ -397,91 +467,160 @@ def run_ours(args, rank, world, local_rank):
             ev_done[b].record(main)
             with torch.cuda.stream(down):
                 down.wait_event(ev_done[b])
-                host_sizes.copy_(sizes2[b], non_blocking=True)
-                o = 0
-                for i in range(len(xs)):
-                    host_out[o:o + sz_list[i]].copy_(outs2[b][i][:sz_list[i]], non_blocking=True)
-                    o += sz_list[i]
-                ev_read[b].record(down)
+                host_sizes[b].copy_(sizes2[b].view(torch.int64), non_blocking=True)
+                ev_sizes[b].record(down)
+            if pending is not None:
+                read_back(pending)
+            pending = b
+        if pending is not None:
+            read_back(pending)
         torch.cuda.synchronize()
 
     e2e_run(max(2, args.warmup))
     if world > 1:
+        import torch.distributed as dist
         dist.barrier()
+    d2h[0] = 0
     t0 = time.perf_counter()
     e2e_run(args.steps)
     e2e_s = reduce_over_ranks((time.perf_counter() - t0) / args.steps, world, "max", dev)
-    for c, s_ in zip(ctxs, streams):
-        c.sync(s_)
-    e2e = {"value": in_bytes * world / e2e_s / 1e9, "unit": "GB/s",
-           "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": sum(sz_list) + 8 * len(xs),
-           "how": "one pinned host buffer per step uploaded on a copy stream, containers read "
-                  "back to pinned memory; double-buffered so upload, compression and read-back "
-                  "of consecutive steps overlap"}
-
-    # dominant kernel: per-stage CUDA events on the launching stream between
-    # the kernels of one step (a profiling pass after the timed region)
-    prof = ctxs[0]
-    prof.profile(True)
-    stage_ms = np.zeros(8)
-    reps = 3
-    for _ in range(reps):
-        if args.path == "batch":
-            step(xs)
-            st = prof.profile_read(8)
-            stage_ms[:len(st)] += st
-        else:
-            for i, x in enumerate(xs):
-                prof.compress(x, out=outs[i], cap=caps[i], size=sizes[i:i + 1], stream=main,
-                              **cfg)
-                st = prof.profile_read(8)
-                stage_ms[:len(st)] += st
-    prof.profile(False)
-    torch.cuda.synchronize()
-    stage_ms /= reps
-    names = ["reset", "threshold", "front", "symbols", "codebook", "pack", "finalize"]
-    dom = int(np.argmax(stage_ms[:7]))
-    peak, peak_kind = load_peaks()
-    alg = stage_bytes(xs, outs, sizes.cpu().numpy(), cfg)
-    ach = alg[names[dom]] / (stage_ms[dom] / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": names[dom], "achieved": round(ach, 1),
-                "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
-                "frac": round(ach / peak, 4),
-                "traffic": captured_traffic(args.workload, tuning, names[dom]),
-                "algorithmic_bytes_per_step": round(alg[names[dom]]),
-                "stage_ms_per_step": {n: round(float(v), 4) for n, v in zip(names, stage_ms)},
-                "stage_gbs": {n: round(alg[n] / (float(v) / 1e3) / 1e9, 1)
-                              for n, v in zip(names, stage_ms) if v > 0}}
-
-    result = None
-    if rank == 0:
-        cpu = cpu_baseline(args, xs, cfg) if world == 1 and not args.no_cpu else None
-        result = {
-            "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "u16" if esz == 2 else "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "desc": wl["desc"], "items": len(xs),
-                       "predictor": args.predictor,
-                       "bytes_in_per_step": in_bytes, "bytes_out_per_step": out_bytes,
-                       "compression_ratio": round(in_bytes / max(out_bytes, 1), 3),
-                       "path": ("roix_compress_batch: %d launches per 64 items" % LAUNCHES_PER_GROUP if
-                                args.path == "batch" else "plain calls on %d streams" % nstreams)
-                               + (", one CUDA graph per step" if graph is not None else ""),
-                       "l2": "inputs larger than L2 (129 MB)" if in_bytes > 129e6
-                       else "inputs smaller than L2: not flushed",
-                       "parallelism": f"replicas x{world}",
-                       "tuning": dict(tuning, seconds=round(tune_s, 2))},
-            "e2e": {k: (round(v, 2) if isinstance(v, float) else v) for k, v in e2e.items()},
-            "latency": latency,
-            "roofline": roofline,
-            "cpu_baseline": cpu,
-            "gpu_launches": launches_per_step * args.steps,
-            "clocks": clk.summary(),
-        }
     for c in ctxs:
-        c.close()
+        c.sync(main)
+    return {"value": in_bytes * world / e2e_s / 1e9, "unit": "GB/s",
+            "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": int(d2h[0] / args.steps),
+            "how": "one pinned host buffer per step uploaded on a copy stream; the step's "
+                   "container sizes copied back first, then each container with its size "
+                   "to pinned memory; double-buffered so upload, compression and read-back of "
+                   "consecutive steps overlap"}
+
+
+def matches_oracle(xs, outs, sizes, cfg, budget_s=20.0):
+    """The GPU containers of the first items (up to ~budget_s of oracle work)
+    against the oracle's, byte for byte; returns (all equal, items compared)."""
+    import oracle
+    szs = sizes.cpu().numpy()
+    ok, n, t0 = True, 0, time.perf_counter()
+    for x, o, sz in zip(xs, outs, szs):
+        ref = oracle.compress(x.cpu().numpy(), **cfg)
+        got = o[:int(sz)].cpu().numpy()
+        ok = ok and got.size == ref.size and bool(np.array_equal(got, ref))
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    return ok, n
+
+
+def sub_line(m, xs, cfg, desc, path_desc):
+    """A measurement as a sub-object of the JSON line."""
+    return {"value": round(m["value"], 2), "unit": "GB/s", "ms_per_step": round(m["ms_per_step"], 4),
+            "desc": desc, "items": len(xs), "path": path_desc,
+            "compression_ratio": round(m["in_bytes"] / max(m["out_bytes"], 1), 3),
+            "latency": m["latency"], "clocks": m["clocks"], "roofline": m["roofline"],
+            "tuning": m["tuning"], "gpu_launches_per_step": m["launches_per_step"]}
+
+
+def path_text(path, m):
+    return (("roix_compress_batch: %d launches per 64 items" % LAUNCHES_PER_GROUP) if path == "batch"
+            else "roix_compress per item on %d streams" % m["nstreams"]) + \
+        (", one CUDA graph per step" if m["graph"] else "")
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    wl = WORKLOADS[args.workload]
+    cfg = dict(wl["cfg"], predictor=args.predictor)
+    xs = make_inputs(args.workload, dev, seed=args.seed)
+    torch.cuda.synchronize()
+    nitems = len(xs)
+    esz = xs[0].element_size()
+    m = measure(args, args.workload, xs, cfg, args.path, dev, world, local_rank, e2e=True)
+    check, cpu = None, None
+    if rank == 0:
+        # the measured containers against the oracle, and the oracle's own speed
+        if nitems == 1 and xs[0].dim() == 3 and xs[0].shape[0] > 64:
+            check = volume_sample_check(xs[0], cfg, dev)
+        else:
+            ok, n = matches_oracle(xs, m["outs"], m["sizes"], cfg)
+            check = {"cr_matches_oracle": ok, "compared": f"first {n} items, byte for byte"}
+        if world == 1 and not args.no_cpu:
+            cpu = cpu_baseline(args, xs, cfg)
+    del m["outs"], m["sizes"]
+    extras = {}
+    if args.workload == "projections64" and args.path == "batch" and args.extras:
+        # the same items through the plain per-item path, same tuning
+        mp = measure(args, args.workload, xs, cfg, "plain", dev, world, local_rank,
+                     tuning=m["tuning"])
+        extras["plain_same_items"] = sub_line(mp, xs, cfg, wl["desc"], path_text("plain", mp))
+        del mp
+        del xs
+        torch.cuda.empty_cache()
+        # the plain per-volume path on the 1024^3 volume
+        wv = WORKLOADS["cube1024"]
+        cv = dict(wv["cfg"], predictor=args.predictor)
+        xv = make_inputs("cube1024", dev, seed=args.seed)
+        mv = measure(args, "cube1024", xv, cv, "plain", dev, world, local_rank)
+        extras["plain_volume"] = sub_line(mv, xv, cv, wv["desc"], path_text("plain", mv))
+        del mv
+        if rank == 0:
+            extras["plain_volume"].update(volume_sample_check(xv[0], cv, dev))
+        del xv
+        torch.cuda.empty_cache()
+        # the served form: a shortened Poisson trace
+        sa = argparse.Namespace(**vars(args))
+        sa.serve_seconds, sa.serve_saturate_s = args.extras_serve_s, 2.0
+        sv = run_serve(sa, rank, world, local_rank)
+        extras["served"] = {"value": sv["value"], "unit": "GB/s",
+                            "value_is": sv["config"]["value_is"], "desc": sv["config"]["desc"],
+                            "latency": sv["latency"], "open_loop": sv["open_loop"],
+                            "clocks": sv["clocks"]}
+        torch.cuda.empty_cache()
+    if rank != 0:
+        return None
+    result = {
+        "metric": METRIC, "value": round(m["value"], 2), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(m["ms_per_step"], 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u16" if esz == 2 else "f32", "data": "synthetic",
+        "cr_matches_oracle": check["cr_matches_oracle"],
+        "config": {"workload": args.workload, "desc": wl["desc"], "items": nitems,
+                   "predictor": args.predictor,
+                   "bytes_in_per_step": m["in_bytes"], "bytes_out_per_step": m["out_bytes"],
+                   "compression_ratio": round(m["in_bytes"] / max(m["out_bytes"], 1), 3),
+                   "path": path_text(args.path, m),
+                   "l2": "inputs larger than L2 (129 MB)" if m["in_bytes"] > 129e6
+                   else "inputs smaller than L2: not flushed",
+                   "parallelism": f"replicas x{world}", "tuning": m["tuning"]},
+        "e2e": {k: (round(v, 2) if isinstance(v, float) else v) for k, v in m["e2e"].items()},
+        "latency": m["latency"],
+        "roofline": m["roofline"],
+        "oracle_check": check,
+        "cpu_baseline": cpu,
+        "gpu_launches": m["launches_per_step"] * args.steps,
+        "clocks": m["clocks"],
+    }
+    result.update(extras)
     return result
+
+
+def volume_sample_check(x, cfg, dev):
+    """A large volume's check against the oracle: its 16 middle slices
+    compressed by the GPU and by the oracle, byte for byte."""
+    import paper_2602_15917_gb300 as roix
+    z = x.shape[0]
+    xs = x[z // 2 - 8: z // 2 + 8].contiguous()
+    r = roix.Roix(dev.index if dev.index is not None else 0)
+    got = r.compress_bytes(xs, **cfg)
+    r.close()
+    ok, n = matches_oracle([xs], [got], _sizes_of([got]), cfg)
+    return {"cr_matches_oracle": ok, "compared": "16 middle slices of the volume, byte for byte"}
+
+
+def _sizes_of(bufs):
+    import torch
+    return torch.tensor([b.numel() for b in bufs], dtype=torch.int64)
 
 
 def cpu_baseline(args, xs, cfg, budget_s: float = None):
@@ -1330,6 +1469,11 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--predictor", type=int, default=1, choices=[1, 2],
                     help="Lorenzo order of the prediction (2: two-layer)")
+    ap.add_argument("--extras", type=int, default=1,
+                    help="projections64 batch line: also time the same items through the plain "
+                         "path, the plain 1024^3 volume and a shortened serving trace")
+    ap.add_argument("--extras-serve-s", type=float, default=4.0,
+                    help="length of the shortened serving trace (s)")
     ap.add_argument("--tune", type=int, default=1,
                     help="1: launch shapes from the autotuner on the workload; 0: defaults")
     args = ap.parse_args()

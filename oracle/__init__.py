@@ -71,6 +71,8 @@ def lib():
             L.oracle_quantize.argtypes = [P, i32, u64, C.POINTER(Eb), d, P, P]
             L.oracle_lorenzo.argtypes = [P, P, P, i32, u64, u32, u32, P, P, P]
             L.oracle_lorenzo.restype = u64
+            L.oracle_interp.argtypes = [P, P, P, i32, u64, u32, u32, P, P, P]
+            L.oracle_interp.restype = u64
             L.oracle_histogram.argtypes = [P, u64, u32, P]
             L.oracle_histogram.restype = None
             L.oracle_codebook.argtypes = [P, u32, P, P]
@@ -80,6 +82,9 @@ def lib():
                                           C.POINTER(C.c_void_p), C.POINTER(u64)]
             L.oracle_compress_slabs.argtypes = [P, C.POINTER(_Params), u64, u64, u64, u64,
                                                 C.POINTER(C.c_void_p), C.POINTER(u64)]
+            L.oracle_encode_slab.argtypes = [P, C.POINTER(_Params), u64, u64, u64, u64, u64,
+                                             C.POINTER(Eb), C.POINTER(C.c_void_p),
+                                             C.POINTER(u64)]
             L.oracle_free.argtypes = [P]
             L.oracle_free.restype = None
             L.oracle_decode.argtypes = [P, u64, P, i32, u64, u64, u64]
@@ -207,6 +212,22 @@ def lorenzo(q: np.ndarray, outl: np.ndarray, P: np.ndarray, radius: int = 512, o
     return sym[:n].copy(), rk[:m].copy(), rv[:m].copy()
 
 
+def interp(q: np.ndarray, outl: np.ndarray, P: np.ndarray, radius: int = 512,
+           chunk: int = 4096):
+    """Interpolation prediction (the Sz3-style predictor = 3) over blocks of
+    `chunk` codes + symbols; returns (sym, record keys, record payloads)."""
+    n = q.size
+    q = np.ascontiguousarray(q, np.int32)
+    outl = np.ascontiguousarray(outl, np.uint8)
+    P = np.ascontiguousarray(P)
+    sym = np.zeros(max(n, 1), np.uint16)
+    rk = np.zeros(max(n, 1), np.uint64)
+    rv = np.zeros(max(n, 1), np.uint32)
+    m = lib().oracle_interp(_ptr(q), _ptr(outl), _ptr(P), _dtype_code(P), n, int(radius),
+                            int(chunk), _ptr(sym), _ptr(rk), _ptr(rv))
+    return sym[:n].copy(), rk[:m].copy(), rv[:m].copy()
+
+
 def histogram(sym: np.ndarray, nsym: int) -> np.ndarray:
     sym = np.ascontiguousarray(sym, np.uint16)
     h = np.zeros(nsym, np.uint64)
@@ -276,6 +297,28 @@ def compress_slabs(x: np.ndarray, slab_z: int, **cfg):
             if outs[k]:
                 L.oracle_free(outs[k])
     return res
+
+
+def encode_slab(xbuf: np.ndarray, z0: int, dz: int, e: Eb, **cfg) -> np.ndarray:
+    """One z-slab's container from its slices alone: xbuf holds the slab's dz
+    slices starting at slice z0 (0 or 1) with the volume's neighbouring slice
+    on each side where the volume has one; e = the whole volume's error-bound
+    constants. Equals that slab's container of compress_slabs."""
+    xbuf = np.ascontiguousarray(xbuf)
+    p = params(_dtype_code(xbuf), **cfg)
+    nx, ny, nzb = _dims(xbuf)
+    out = C.c_void_p()
+    size = C.c_uint64(0)
+    L = lib()
+    rc = L.oracle_encode_slab(_ptr(xbuf), C.byref(p), nx, ny, nzb, int(z0), int(dz),
+                              C.byref(e), C.byref(out), C.byref(size))
+    if rc != 0:
+        raise RuntimeError(f"oracle_encode_slab failed ({rc})")
+    try:
+        buf = np.ctypeslib.as_array(C.cast(out, C.POINTER(C.c_uint8)), shape=(size.value,)).copy()
+    finally:
+        L.oracle_free(out)
+    return buf
 
 
 def decode(buf: np.ndarray, shape, dtype) -> np.ndarray:

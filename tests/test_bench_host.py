@@ -4,20 +4,36 @@ from __future__ import annotations
 import bench
 
 
-def test_traffic_only_for_the_captured_workload_and_tuning():
+def test_traffic_only_for_the_captured_workload_and_tuning(monkeypatch):
+    table = {("projections64", 2048, 0): {"front": 128.2, "source": "ncu capture X"}}
+    monkeypatch.setattr(bench, "TRAFFIC_MB", table)
     t = {"front_words": 2048, "front_kernel": 0}
-    assert bench.captured_traffic("projections64", t, "front") == round(
-        bench.TRAFFIC_MB[("projections64", 2048, 0)]["front"] * 1e6)
+    assert bench.captured_traffic("projections64", t, "front") == (128200000, "ncu capture X")
     # another tile size or counting kernel ran other launches: no figure
-    assert bench.captured_traffic("projections64", dict(t, front_words=4096), "front") is None
-    assert bench.captured_traffic("projections64", dict(t, front_kernel=1), "front") is None
+    assert bench.captured_traffic("projections64", dict(t, front_words=4096), "front") == (None, None)
+    assert bench.captured_traffic("projections64", dict(t, front_kernel=1), "front") == (None, None)
     # a workload without a capture, a stage without a figure
-    assert bench.captured_traffic("cube1024", t, "threshold") is None
-    assert bench.captured_traffic("projections64", t, "finalize") is None
+    assert bench.captured_traffic("cube1024", t, "threshold") == (None, None)
+    assert bench.captured_traffic("projections64", t, "finalize") == (None, None)
 
 
 def test_captured_traffic_is_at_most_a_few_times_the_input():
     # the stages of one step move at most a few times the step's input bytes
-    inputs = {"projections64": 241.85, "cube512": 536.87}
+    inputs = {"projections64": 241.85, "cube512": 536.87, "cube1024": 4294.97}
     for (wl, _, _), st in bench.TRAFFIC_MB.items():
-        assert 0 < sum(st.values()) < 3 * inputs[wl]
+        assert isinstance(st["source"], str) and st["source"]
+        vals = [v for k, v in st.items() if k != "source"]
+        assert 0 < sum(vals) < 3 * inputs[wl]
+
+
+def test_sub_line_keeps_the_measurement_fields():
+    m = {"value": 1234.567, "ms_per_step": 0.123456, "in_bytes": 1000, "out_bytes": 100,
+         "latency": {"p50_ms": 1}, "clocks": {"sm_mhz": 2070}, "roofline": {"frac": 0.5},
+         "tuning": {"front_words": 2048}, "launches_per_step": 12, "nstreams": 8, "graph": True}
+    line = bench.sub_line(m, [0, 1], {}, "d", bench.path_text("plain", m))
+    assert line["value"] == 1234.57 and line["ms_per_step"] == 0.1235
+    assert line["compression_ratio"] == 10.0 and line["items"] == 2
+    assert line["path"] == "roix_compress per item on 8 streams, one CUDA graph per step"
+    for k in ("latency", "clocks", "roofline", "tuning"):
+        assert line[k] == m[k]
+

@@ -53,16 +53,21 @@ def _held_then_released(rx, x: np.ndarray, tuning=None, **cfg):
         rx.debug_hold_scans(True)
         rx.compress(xd, **cfg)
         _expect_timeout(rx)
-        # the same context, hook off: the oracle's container again
+        # the same context, hook off and the default limit (1000 polls is too
+        # short for a scan tile that waits on a busy predecessor): the oracle's
+        # container again
         rx.debug_hold_scans(False)
+        rx.set_wait_limit(0)
         got = rx.compress_bytes(xd, **cfg).cpu().numpy()
         assert got.size == ref.size and np.array_equal(got, ref)
         # decoder row scans (more than one 1024-row tile)
         buf = torch.from_numpy(ref).cuda()
+        rx.set_wait_limit(1000)
         rx.debug_hold_scans(True)
         rx.decode(buf, x.shape, torch.from_numpy(x[:0]).dtype)
         _expect_timeout(rx)
         rx.debug_hold_scans(False)
+        rx.set_wait_limit(0)
         y = rx.decode(buf, x.shape, torch.from_numpy(x[:0]).dtype)
         rx.sync()
         y_ref = oracle.decode(ref, x.shape, x.dtype)
