@@ -71,8 +71,6 @@ def lib():
             L.oracle_quantize.argtypes = [P, i32, u64, C.POINTER(Eb), d, P, P]
             L.oracle_lorenzo.argtypes = [P, P, P, i32, u64, u32, u32, P, P, P]
             L.oracle_lorenzo.restype = u64
-            L.oracle_interp.argtypes = [P, P, P, i32, u64, u32, u32, P, P, P]
-            L.oracle_interp.restype = u64
             L.oracle_histogram.argtypes = [P, u64, u32, P]
             L.oracle_histogram.restype = None
             L.oracle_codebook.argtypes = [P, u32, P, P]
@@ -209,22 +207,6 @@ def lorenzo(q: np.ndarray, outl: np.ndarray, P: np.ndarray, radius: int = 512, o
     rv = np.zeros(max(n, 1), np.uint32)
     m = lib().oracle_lorenzo(_ptr(q), _ptr(outl), _ptr(P), _dtype_code(P), n, int(radius),
                              int(order), _ptr(sym), _ptr(rk), _ptr(rv))
-    return sym[:n].copy(), rk[:m].copy(), rv[:m].copy()
-
-
-def interp(q: np.ndarray, outl: np.ndarray, P: np.ndarray, radius: int = 512,
-           chunk: int = 4096):
-    """Interpolation prediction (the Sz3-style predictor = 3) over blocks of
-    `chunk` codes + symbols; returns (sym, record keys, record payloads)."""
-    n = q.size
-    q = np.ascontiguousarray(q, np.int32)
-    outl = np.ascontiguousarray(outl, np.uint8)
-    P = np.ascontiguousarray(P)
-    sym = np.zeros(max(n, 1), np.uint16)
-    rk = np.zeros(max(n, 1), np.uint64)
-    rv = np.zeros(max(n, 1), np.uint32)
-    m = lib().oracle_interp(_ptr(q), _ptr(outl), _ptr(P), _dtype_code(P), n, int(radius),
-                            int(chunk), _ptr(sym), _ptr(rk), _ptr(rv))
     return sym[:n].copy(), rk[:m].copy(), rv[:m].copy()
 
 

@@ -90,9 +90,7 @@ struct OracleEb {
   int32_t eb_int;        // uint16 path: integer half-width
 };
 
-static uint32_t order_of(const OracleParams* p) {
-  return p->order == 2 ? 2u : (p->order == 3 ? 3u : 1u);
-}
+static uint32_t order_of(const OracleParams* p) { return p->order == 2 ? 2u : 1u; }
 
 // ---------------------------------------------------------------- threshold
 // Sec. 4.1.1 M = I - B (B constant = dark), Sec. 4.1.3-4.1.4: M(x,y) = 1 where
@@ -353,59 +351,6 @@ uint64_t oracle_lorenzo(const int32_t* q, const uint8_t* outl, const void* P,
   return m;
 }
 
-// Interpolation prediction, the Sz3-style alternative to the Lorenzo predictor
-// (Sec. 4.3: Sz3 is prediction-based and runs on the 1D array), restated on
-// the integer codes. The stream is cut into blocks of C codes (the coder's
-// chunks). In a block of L codes, position 0 is predicted as 0; position i > 0,
-// whose stride s is the largest power of two dividing i, is predicted by
-// linear interpolation between its neighbours at distance s, floor((q[i-s] +
-// q[i+s]) / 2), or by q[i-s] alone when i + s is past the block. Both
-// neighbours are multiples of 2s (or 0), so a decoder that fills a block from
-// the coarsest stride down to 1 always has them. An outlier counts as 0 and the
-// residuals, symbols and records are as in oracle_lorenzo.
-uint64_t oracle_interp(const int32_t* q, const uint8_t* outl, const void* P, int32_t dtype,
-                       uint64_t n, uint32_t R, uint32_t C, uint16_t* sym, uint64_t* rec_key,
-                       uint32_t* rec_val) {
-  uint64_t m = 0;
-  auto code = [&](uint64_t k) -> int64_t { return outl[k] ? 0 : (int64_t)q[k]; };
-  for (uint64_t k = 0; k < n; ++k) {
-    if (outl[k]) {
-      sym[k] = 0;
-      rec_key[m] = k | (uint64_t(1) << 63);
-      uint32_t bits = 0;
-      if (dtype == DT_F32) std::memcpy(&bits, (const float*)P + k, 4);
-      else bits = ((const uint16_t*)P)[k];
-      rec_val[m] = bits;
-      m++;
-      continue;
-    }
-    const uint64_t b0 = k - k % C;                           // first code of the block
-    const uint64_t L = std::min<uint64_t>(C, n - b0);       // codes in the block
-    const uint64_t i = k - b0;
-    int64_t pred = 0;
-    if (i > 0) {
-      const uint64_t s = i & (~i + 1);  // largest power of two dividing i
-      const int64_t left = code(b0 + i - s);
-      if (i + s < L) {
-        const int64_t sum = left + code(b0 + i + s);
-        pred = sum >= 0 ? sum / 2 : -((-sum + 1) / 2);  // floor of sum / 2
-      } else {
-        pred = left;
-      }
-    }
-    const int64_t d = (int64_t)q[k] - pred;
-    if (d > -(int64_t)R && d < (int64_t)R) {
-      sym[k] = (uint16_t)(d + R);
-    } else {
-      sym[k] = 0;
-      rec_key[m] = k;
-      rec_val[m] = (uint32_t)q[k];
-      m++;
-    }
-  }
-  return m;
-}
-
 void oracle_histogram(const uint16_t* sym, uint64_t n, uint32_t S, uint64_t* hist) {
   for (uint32_t s = 0; s < S; ++s) hist[s] = 0;
   for (uint64_t k = 0; k < n; ++k) hist[sym[k]]++;
@@ -570,11 +515,8 @@ int encode_container(const void* in, const OracleParams* p, uint64_t nx, uint64_
   std::vector<uint16_t> sym(n + 1);
   std::vector<uint64_t> rk(n + 1);
   std::vector<uint32_t> rv(n + 1);
-  uint64_t nout = order_of(p) == 3
-                      ? oracle_interp(q.data(), ol.data(), P.data(), p->dtype, n, R, C, sym.data(),
-                                      rk.data(), rv.data())
-                      : oracle_lorenzo(q.data(), ol.data(), P.data(), p->dtype, n, R, order_of(p),
-                                       sym.data(), rk.data(), rv.data());
+  uint64_t nout = oracle_lorenzo(q.data(), ol.data(), P.data(), p->dtype, n, R, order_of(p),
+                                 sym.data(), rk.data(), rv.data());
   std::vector<uint64_t> hist(S);
   oracle_histogram(sym.data(), n, S, hist.data());
   std::vector<uint8_t> len(S);
@@ -751,7 +693,7 @@ int oracle_decode(const uint8_t* buf, uint64_t size, void* outv, int32_t dtype,
   get(200, &off_payload, 8); get(208, &total, 8);
   if (version != 1 || dt != dtype || hx != nx || hy != ny || hz != nz) return ERR_CORRUPT;
   if (total > size || lmax != kLMax || R < 2 || R > 32768 || C == 0) return ERR_CORRUPT;
-  if (order > 3) return ERR_CORRUPT;
+  if (order > 2) return ERR_CORRUPT;
   if (order == 0) order = 1;
   uint64_t N = nx * ny * nz, rows = ny * nz, S = 2ull * R;
   if (dtype == DT_U16 && !(fill >= 0.0 && fill <= 65535.0 && fill == std::floor(fill)))
@@ -821,15 +763,10 @@ int oracle_decode(const uint8_t* buf, uint64_t size, void* outv, int32_t dtype,
   std::vector<uint32_t> raw_bits(n + 1, 0);
   uint64_t r = 0;
   int64_t prev1 = 0, prev2 = 0;
-  std::vector<uint8_t> from_record(order == 3 ? n + 1 : 0, 0);
   for (uint64_t k = 0; k < n; ++k) {
     int64_t c;
     if (sym[k] != 0) {
       if (sym[k] >= S) return ERR_CORRUPT;
-      if (order == 3) {  // the residual for now; the prediction is added below
-        q[k] = (int32_t)((int64_t)sym[k] - (int64_t)R);
-        continue;
-      }
       const int64_t pred = order == 2 ? 2 * prev1 - prev2 : prev1;
       c = pred + (int64_t)sym[k] - (int64_t)R;
       if (c < INT32_MIN || c > INT32_MAX) return ERR_CORRUPT;
@@ -843,39 +780,12 @@ int oracle_decode(const uint8_t* buf, uint64_t size, void* outv, int32_t dtype,
         c = (int32_t)rv[r];
       }
       r++;
-      if (order == 3) from_record[k] = 1;
     }
     q[k] = (int32_t)c;
     prev2 = prev1;
     prev1 = c;
   }
   if (r != nout) return ERR_CORRUPT;
-  if (order == 3) {
-    // every block from its coarsest stride down to 1 (the decoding order of
-    // oracle_interp): position 0, then i = s, 3s, 5s, ... for each stride s
-    for (uint64_t b0 = 0; b0 < n; b0 += C) {
-      const uint64_t L = std::min<uint64_t>(C, n - b0);
-      uint64_t top = 1;
-      while (2 * top < L) top *= 2;
-      for (uint64_t s = top; s >= 1 && L > 1; s /= 2) {
-        for (uint64_t i = s; i < L; i += 2 * s) {
-          const uint64_t k = b0 + i;
-          if (from_record[k]) continue;
-          const int64_t left = q[b0 + i - s];
-          int64_t pred;
-          if (i + s < L) {
-            const int64_t sum = left + (int64_t)q[b0 + i + s];
-            pred = sum >= 0 ? sum / 2 : -((-sum + 1) / 2);
-          } else {
-            pred = left;
-          }
-          const int64_t c = pred + (int64_t)q[k];
-          if (c < INT32_MIN || c > INT32_MAX) return ERR_CORRUPT;
-          q[k] = (int32_t)c;
-        }
-      }
-    }
-  }
   // rows from the geometry
   uint64_t k = 0, b = 0;
   for (uint64_t row = 0; row < rows; ++row) {

@@ -309,92 +309,6 @@ def test_lorenzo2_closed_forms():
             assert (s1[1:].astype(np.int64) == b + R).all()
 
 
-def _inverse_interp(sym, rk, rv, R, C):
-    """Independent inverse of the interpolation predictor: each block of C
-    codes filled by a recursive midpoint split (the code of the far end first,
-    then the middle of every interval from the end points), the Python way."""
-    rec = {int(k) & ((1 << 63) - 1): (int(k) >> 63, int(v)) for k, v in zip(rk, rv)}
-    n = sym.size
-    out = np.zeros(n, np.int64)
-
-    def value(k, pred):
-        s_ = int(sym[k])
-        if s_:
-            return pred + s_ - R
-        kind, v = rec[k]
-        return 0 if kind else int(np.array(v, np.uint32).view(np.int32))
-
-    for b0 in range(0, n, C):
-        L = min(C, n - b0)
-        out[b0] = value(b0, 0)
-        top = 1
-        while 2 * top < L:
-            top *= 2
-        # the intervals [a, a + 2 s] of the coarsest level, left to right
-        stack = [(0, 2 * top)]
-        while stack:
-            a, b = stack.pop()
-            mid = (a + b) // 2
-            if mid == a:
-                continue
-            if mid < L:
-                left = int(out[b0 + a])
-                pred = (left + int(out[b0 + b])) // 2 if b < L else left
-                out[b0 + mid] = value(b0 + mid, pred)
-                stack.append((mid, b))
-            stack.append((a, mid))
-    return out
-
-
-@pytest.mark.parametrize("R,C", [(2, 256), (16, 256), (512, 4096), (512, 256)])
-def test_interp_inverts_and_records_sit_on_symbol_zero(R, C):
-    rng = np.random.default_rng(R + C)
-    n = 3 * C + 77  # ragged last block
-    q = np.cumsum(rng.integers(-R, R, n)).astype(np.int32)
-    outl = (rng.random(n) < 0.05).astype(np.uint8)
-    q[outl.astype(bool)] = 0
-    P = rng.standard_normal(n).astype(np.float32)
-    sym, rk, rv = oracle.interp(q, outl, P, R, C)
-    assert np.array_equal(_inverse_interp(sym, rk, rv, R, C), q.astype(np.int64))
-    keys = rk & np.uint64((1 << 63) - 1)
-    assert np.array_equal(keys, np.flatnonzero(sym == 0).astype(np.uint64))
-    assert (sym < 2 * R).all()
-    kinds = (rk >> np.uint64(63)).astype(bool)
-    assert np.array_equal(np.flatnonzero(outl), keys[kinds].astype(np.int64))
-    assert np.array_equal(rv[kinds], P[outl.astype(bool)].view(np.uint32))
-
-
-def test_interp_closed_forms():
-    # a line is interpolated exactly wherever both neighbours exist; at the far
-    # end of a block (right neighbour missing) the residual is slope * stride;
-    # a parabola a i^2 leaves -a s^2 at stride s; block starts carry the code
-    R, C = 2048, 256
-    n = 2 * C + 100
-    i = np.arange(n, dtype=np.int64) % C
-    z = np.zeros(n, np.uint8)
-    P = np.zeros(n, np.float32)
-    for a, b in [(3, 7), (-5, 100), (0, -40)]:
-        q = (a * i + b).astype(np.int32)
-        sym, rk, rv = oracle.interp(q, z, P, R, C)
-        assert rk.size == 0
-        for k in range(n):
-            b0 = k - k % C
-            L = min(C, n - b0)
-            ii = k - b0
-            s_ = ii & -ii if ii else 0
-            want = b if ii == 0 else (0 if ii + s_ < L else a * s_)
-            assert int(sym[k]) - R == want, (a, b, k)
-    q = (i * i).astype(np.int32)
-    R = 32768  # every residual -s^2 (s <= 128) fits: no records
-    sym, rk, _ = oracle.interp(q, z, P, R, C)
-    assert rk.size == 0
-    for k in range(n):
-        ii = k % C
-        L = min(C, n - (k - ii))
-        if ii and ii + (ii & -ii) < L:
-            assert int(sym[k]) - R == -(ii & -ii) ** 2
-
-
 @pytest.mark.parametrize("cfg", [dict(eb=1e-3, eb_mode="abs"), dict(eb=1e-4, eb_mode="rel"),
                                  dict(eb=1e-5, eb_mode="rel", radius=16)])
 def test_predictor_changes_the_stream_not_the_values(cfg):
@@ -403,14 +317,10 @@ def test_predictor_changes_the_stream_not_the_values(cfg):
     x = phantom.porous_cylinder(40, radius=15, texture=True, seed=4).numpy()
     b1 = oracle.compress(x, predictor=1, **cfg)
     b2 = oracle.compress(x, predictor=2, **cfg)
-    b3 = oracle.compress(x, predictor=3, chunk=256, **cfg)
     assert oracle.header(b1)["order"] == 1 and oracle.header(b2)["order"] == 2
-    assert oracle.header(b3)["order"] == 3
     y1 = oracle.decode(b1, x.shape, np.float32)
     y2 = oracle.decode(b2, x.shape, np.float32)
-    y3 = oracle.decode(b3, x.shape, np.float32)
     assert np.array_equal(y1.view(np.uint32), y2.view(np.uint32))
-    assert np.array_equal(y1.view(np.uint32), y3.view(np.uint32))
     D = oracle.mask(x, **cfg).astype(bool)
     assert _exact_within(x[D], y2[D], oracle.header(b2)["eb_abs"])
 
