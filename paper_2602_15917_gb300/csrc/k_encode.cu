@@ -516,72 +516,166 @@ __device__ long long g_cb_probe[16];
 #define CB_MARK(i)
 #endif
 
-// Two-queue Huffman construction (van Leeuwen 1976) by one thread: leaves
-// 0..m-1 sorted ascending (weights lw), internal nodes m..2m-2 created in
-// order (weights wi), par[] receives every node's parent. Each iteration pops
-// the two lightest fronts, a leaf winning ties, and creates one node. The
-// fronts live in register windows (four leaves, three internal nodes); the
-// loads that refill them are issued at the top of an iteration and consumed
-// only at its end, after both pops, so shared-memory latency stays off the
-// chain of compares and selects. An empty slot holds the sentinel ~0.
-template <typename W>
-__device__ __forceinline__ W sel3(u32 k, W a, W b, W c) {
-  return k == 0 ? a : (k == 1 ? b : c);
-}
+// Two-queue Huffman construction (van Leeuwen 1976) by one warp, in rounds.
+// The sequential form pops the two lightest fronts of the leaf queue (leaves
+// 0..m-1 sorted ascending) and of the internal queue (nodes m.. in creation
+// order), a leaf winning ties, and appends their sum to the internal queue.
+// Every node created from now on weighs at least 2 x_min (x_min = the lighter
+// front), so every known leaf or internal node of weight <= T = 2 x_min is
+// popped before any of them, in merged order (weight, leaves before internal
+// nodes on a tie, queue order within a queue); a round therefore takes those
+// K nodes at once (K rounded down to even; the odd one waits for the next
+// round), merges the two runs (merge path: each lane finds where its share of
+// the merged order starts by a binary search on the diagonal, then merges its
+// share; a leaf goes first when it is no heavier than the internal node) and
+// pairs merged positions 2p, 2p + 1 into new nodes m + created + p, which is
+// the sequential algorithm's order of pops and of creations. When K < 2 the two
+// lightest fronts are popped as one sequential step. Rounds: about
+// log2(total weight / lightest leaf) plus those steps. par[] receives every
+// node's parent; mid[] (2m entries) is scratch; rstart[] (rounds + 1 entries)
+// receives each round's first created node and *nrounds their number, for the
+// depths. All 32 lanes call it.
+constexpr u64 kNoWeight = ~0ull;
 
-template <typename W, typename LeafW>
-__device__ __forceinline__ void huffman_merge_impl(LeafW leaf, W* wi, int32_t* par, u32 m) {
-  constexpr W kNone = ~W(0);
-  u32 lf = 0, in = 0, created = 0;
-  W A0 = leaf(0), A1 = m > 1 ? leaf(1) : kNone, A2 = m > 2 ? leaf(2) : kNone,
-    A3 = m > 3 ? leaf(3) : kNone;
-  W I0 = kNone, I1 = kNone, I2 = kNone;
-  for (u32 t = 0; t + 1 < m; ++t) {
-    // refills for after this iteration (at most two of each queue consumed)
-    const W la4 = lf + 4 < m ? leaf(lf + 4) : kNone;
-    const W la5 = lf + 5 < m ? leaf(lf + 5) : kNone;
-    const W lb3 = in + 3 < created ? wi[in + 3] : kNone;
-    const W lb4 = in + 4 < created ? wi[in + 4] : kNone;
-    // pop 1
-    const bool t1 = A0 <= I0;
-    const W f1 = t1 ? A0 : I0;
-    const int32_t p1 = t1 ? (int32_t)lf : (int32_t)(m + in);
-    const W a0 = t1 ? A1 : A0, i0 = t1 ? I0 : I1;
-    // pop 2
-    const bool t2 = a0 <= i0;
-    const W f2 = t2 ? a0 : i0;
-    const u32 lf1 = lf + (t1 ? 1u : 0u), in1 = in + (t1 ? 0u : 1u);
-    const int32_t p2 = t2 ? (int32_t)lf1 : (int32_t)(m + in1);
-    const u32 cl = (t1 ? 1u : 0u) + (t2 ? 1u : 0u), ci = 2u - cl;
-    const W ws = f1 + f2;
-    // windows shifted by what was consumed
-    const W nA0 = sel3(cl, A0, A1, A2), nA1 = sel3(cl, A1, A2, A3), nA2 = sel3(cl, A2, A3, la4),
-            nA3 = sel3(cl, A3, la4, la5);
-    W nI0 = sel3(ci, I0, I1, I2), nI1 = sel3(ci, I1, I2, lb3), nI2 = sel3(ci, I2, lb3, lb4);
-    lf += cl;
-    in += ci;
-    wi[created] = ws;
-    par[p1] = (int32_t)(m + created);
-    par[p2] = (int32_t)(m + created);
-    ++created;
-    const u32 q = created - in;  // internal nodes waiting, the new one included
-    nI0 = q == 1 ? ws : nI0;
-    nI1 = q == 2 ? ws : nI1;
-    nI2 = q == 3 ? ws : nI2;
-    A0 = nA0; A1 = nA1; A2 = nA2; A3 = nA3;
-    I0 = nI0; I1 = nI1; I2 = nI2;
+// Number of a[lo..hi) (ascending) that are <= t (le) or < t (!le), by the warp:
+// two rounds of 32 probes (ranges up to 1024; longer ones continue by 32^2).
+template <typename F>
+__device__ __forceinline__ u32 warp_count_below(F a, u32 lo, u32 hi, u64 t, bool le, int lane) {
+  u32 base = lo;
+  u32 len = hi - lo;
+  while (len > 32) {
+    const u32 stride = (len + 31) / 32;
+    const u32 i = base + (u32)lane * stride;
+    bool in = false;
+    if (i < base + len) {
+      const u64 v = a(i);
+      in = le ? v <= t : v < t;
+    }
+    const u32 b = __ballot_sync(0xffffffffu, in);
+    const u32 k = (u32)__popc(b);  // probes in the prefix (the array ascends)
+    if (k == 0) return base - lo;
+    const u32 nb = base + (k - 1) * stride;  // the last probe inside the prefix
+    len = min(stride, base + len - nb);
+    base = nb;
   }
-  par[2 * m - 2] = -1;
+  bool in = false;
+  if ((u32)lane < len) {
+    const u64 v = a(base + lane);
+    in = le ? v <= t : v < t;
+  }
+  return base - lo + (u32)__popc(__ballot_sync(0xffffffffu, in));
 }
 
-template <typename W>
-__device__ __forceinline__ void huffman_merge(const W* lw, W* wi, int32_t* par, u32 m) {
-  huffman_merge_impl<W>([&](u32 i) { return lw[i]; }, wi, par, m);
+__device__ void huffman_merge_warp(const u64* key, u64* wi, int32_t* par, int32_t* mid,
+                                   u32* rstart, u32* nrounds, u32 m) {
+  const int lane = threadIdx.x & 31;
+  auto lw = [&](u32 i) -> u64 { return key[i] >> 16; };
+  auto iw = [&](u32 i) -> u64 { return wi[i]; };
+  u32 lf = 0, in = 0, created = 0, rounds = 0;
+  while (created + 1 < m) {
+    if (lane == 0) rstart[rounds] = created;  // first node of this round
+    ++rounds;
+    const u64 a0 = lf < m ? lw(lf) : kNoWeight;
+    const u64 b0 = in < created ? wi[in] : kNoWeight;
+    const u64 xmin = a0 < b0 ? a0 : b0;
+    const u64 T = xmin > (kNoWeight >> 1) ? kNoWeight : 2 * xmin;
+    const u32 na = warp_count_below(lw, lf, m, T, true, lane);
+    const u32 nb = warp_count_below(iw, in, created, T, true, lane);
+    const u32 K = na + nb;
+    if (K < 2) {
+      // one sequential step: the two lightest fronts, a leaf winning ties
+      u32 l = lf, q = in;
+      int32_t id[2];
+      u64 w[2];
+      for (int t = 0; t < 2; ++t) {
+        const u64 la = l < m ? lw(l) : kNoWeight, ib = q < created ? wi[q] : kNoWeight;
+        if (la <= ib) {
+          id[t] = (int32_t)l;
+          w[t] = la;
+          ++l;
+        } else {
+          id[t] = (int32_t)(m + q);
+          w[t] = ib;
+          ++q;
+        }
+      }
+      if (lane == 0) {
+        wi[created] = w[0] + w[1];
+        par[id[0]] = (int32_t)(m + created);
+        par[id[1]] = (int32_t)(m + created);
+      }
+      __syncwarp();
+      lf = l;
+      in = q;
+      ++created;
+      continue;
+    }
+    const u32 P = K >> 1, out = 2 * P;
+    // merge path: lane l writes merged positions [o0, o1); its start splits
+    // into ia leaves and o0 - ia internal nodes (a leaf goes first when it is
+    // no heavier than the internal node); then a sequential merge
+    const u32 per = (out + 31) >> 5;
+    const u32 o0 = min(out, (u32)lane * per), o1 = min(out, o0 + per);
+    u32 lo = o0 > nb ? o0 - nb : 0u, hi = min(o0, na);
+    while (lo < hi) {  // the largest ia with leaf ia - 1 before internal o0 - ia
+      const u32 c = (lo + hi + 1) >> 1;
+      const u32 jb = o0 - c;
+      if (jb >= nb || lw(lf + c - 1) <= wi[in + jb]) lo = c;
+      else hi = c - 1;
+    }
+    u32 ia = lo, ib = o0 - lo, taken = 0;
+    u64 wa = ia < na ? lw(lf + ia) : kNoWeight, wb = ib < nb ? wi[in + ib] : kNoWeight;
+    for (u32 o = o0; o < o1; ++o) {
+      if (ia < na && (ib >= nb || wa <= wb)) {
+        mid[o] = (int32_t)(lf + ia);
+        ++ia;
+        ++taken;
+        wa = ia < na ? lw(lf + ia) : kNoWeight;
+      } else {
+        mid[o] = (int32_t)(m + in + ib);
+        ++ib;
+        wb = ib < nb ? wi[in + ib] : kNoWeight;
+      }
+    }
+    const u32 ca = warp_sum(taken);  // leaves among the paired nodes
+    __syncwarp();
+    for (u32 p = lane; p < P; p += 32) {
+      const u32 x = (u32)mid[2 * p], y = (u32)mid[2 * p + 1];
+      const u64 wx = x < m ? lw(x) : wi[x - m], wy = y < m ? lw(y) : wi[y - m];
+      wi[created + p] = wx + wy;
+      par[x] = (int32_t)(m + created + p);
+      par[y] = (int32_t)(m + created + p);
+    }
+    __syncwarp();
+    lf += ca;
+    in += out - ca;
+    created += P;
+  }
+  if (lane == 0) {
+    par[2 * m - 2] = -1;
+    rstart[rounds] = created;
+    *nrounds = rounds;
+  }
+  __syncwarp();
 }
 
-// 64-bit weights straight from the (count << 16 | symbol) keys
-__device__ __forceinline__ void huffman_merge_key(const u64* key, u64* wi, int32_t* par, u32 m) {
-  huffman_merge_impl<u64>([&](u32 i) { return key[i] >> 16; }, wi, par, m);
+// Depth of every node (its distance to the root) from the rounds of
+// huffman_merge_warp: a node's parent was created in a later round, so the
+// rounds are taken last to first, each round's nodes in parallel, then the
+// leaves. dep[] receives 2m - 1 depths. All 32 lanes call it.
+__device__ void huffman_depths_warp(const int32_t* par, int32_t* dep, const u32* rstart,
+                                    u32 nrounds, u32 m) {
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) dep[2 * m - 2] = 0;
+  __syncwarp();
+  for (int r = (int)nrounds - 1; r >= 0; --r) {
+    for (u32 v = rstart[r] + (u32)lane; v < rstart[r + 1]; v += 32) {
+      if (v + 2 < m) dep[m + v] = dep[par[m + v]] + 1;  // the root (v = m - 2) keeps 0
+    }
+    __syncwarp();
+  }
+  for (u32 i = lane; i < m; i += 32) dep[i] = dep[par[i]] + 1;
+  __syncwarp();
 }
 
 __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__ Batch B) {
@@ -644,56 +738,18 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__
       bl[1] = 1;
     }
   } else if (m >= 2) {
-    // two-queue construction (thread 0), 32-bit weights when the total fits
-    const u64 tot_w = [&] {
-      u64 acc = 0;
-      for (u32 i = tid; i < m; i += kCbThreads) acc += key[i] >> 16;
-      acc = warp_sum(acc);
-      if ((tid & 31) == 0) scratch[tid >> 5] = (u32)umin(acc, 0xffffffffull);
-      __syncthreads();
-      u64 all = 0;
-      for (int w = 0; w < kCbThreads / 32; ++w) all += scratch[w];
-      __syncthreads();
-      return all;
-    }();
-    if (tot_w < 0xffffffffull) {
-      u32* lw = reinterpret_cast<u32*>(dep);  // leaf weights (dep is free until the depths)
-      for (u32 i = tid; i < m; i += kCbThreads) lw[i] = (u32)(key[i] >> 16);
-      __syncthreads();
-      if (tid == 0) huffman_merge<u32>(lw, reinterpret_cast<u32*>(wint), par, m);
-    } else {
-      if (tid == 0) huffman_merge_key(key, wint, par, m);
+    // two-queue construction by warp 0, in rounds (dep is scratch until the
+    // depths, bl holds the rounds' first nodes until the lengths are counted)
+    __shared__ u32 s_rounds;
+    if (tid < 32) {
+      huffman_merge_warp(key, wint, par, dep, bl, &s_rounds, m);
+      CB_MARK(3)
+      huffman_depths_warp(par, dep, bl, s_rounds, m);
     }
     __syncthreads();
-    CB_MARK(3)
-    // depth = distance to the root, by pointer jumping
-    const u32 nodes = 2 * m - 1;
-    for (u32 i = tid; i < nodes; i += kCbThreads) dep[i] = par[i] >= 0 ? 1 : 0;
-    __syncthreads();
-    for (u32 round = 0; (1u << round) < nodes; ++round) {
-      constexpr int kPer = (2 * kMaxSym + kCbThreads - 1) / kCbThreads;
-      int32_t na[kPer], nd[kPer];
-#pragma unroll
-      for (int c = 0; c < kPer; ++c) {
-        const u32 i = tid + (u32)c * kCbThreads;
-        if (i < nodes) {
-          const int32_t a = par[i];
-          nd[c] = a >= 0 ? dep[i] + dep[a] : dep[i];
-          na[c] = a >= 0 ? par[a] : -1;
-        }
-      }
-      __syncthreads();
-#pragma unroll
-      for (int c = 0; c < kPer; ++c) {
-        const u32 i = tid + (u32)c * kCbThreads;
-        if (i < nodes) {
-          dep[i] = nd[c];
-          par[i] = na[c];
-        }
-      }
-      __syncthreads();
-    }
     CB_MARK(4)
+    for (u32 i = tid; i < bl_entries(S); i += kCbThreads) bl[i] = 0;
+    __syncthreads();
     if (tid == 0) s_maxl = 0;
     __syncthreads();
     for (u32 i = tid; i < m; i += kCbThreads) {
@@ -849,8 +905,6 @@ template <typename TV, bool FROM_Q>
 __global__ void __launch_bounds__(kThreads) k_records(const __grid_constant__ Batch B) {
   if (halted(B.status)) return;  // a tile scan of this call gave up
   __shared__ u64 pre[kMaxBatch + 1];
-  __shared__ ItemEb ieb[kMaxBatch];
-  if constexpr (!FROM_Q) items_eb(B, ieb);
   const u32 C = B.c.C;
   const int lane = threadIdx.x & 31;
   tile_prefix(B, pre, C, 1);
@@ -865,7 +919,7 @@ __global__ void __launch_bounds__(kThreads) k_records(const __grid_constant__ Ba
     const Item& I = B.it[item];
     const u64 t = gt - pre[item];
     if (I.crec[t] == 0u) continue;
-    if (item != cur) {
+    if (item != cur) {  // the item's error-bound constants, formed only for chunks with records
       cur = item;
       const Desc d = desc_of(B, I);
       src.P = (const TV*)I.P;
@@ -873,8 +927,8 @@ __global__ void __launch_bounds__(kThreads) k_records(const __grid_constant__ Ba
       src.obits = I.obits;
       src.dark = d.dark;
       if constexpr (!FROM_Q) {
-        src.e = ieb[item].e;
-        src.fd = ieb[item].fd;
+        src.e = make_eb(d, I.rst->vmin_key, I.rst->vmax_key);
+        src.fd = FastDiv(2u * (u32)src.e.eb_int);
       }
       n = umin(I.sizes[0], I.N);
     }

@@ -144,77 +144,71 @@ __device__ __forceinline__ void thr_segment_vec(const Desc& d, const TV* __restr
 
 // Flat form for a 16-byte aligned volume with nx >= 256 whose rows are not
 // 16-byte aligned or do not fill whole 1024-voxel segments: the volume is read
-// as one flat array in aligned 16-byte vectors, 1024 voxels per step of a
-// warp, and turned into flat words (bit b of flat word j = voxel 32 j + b,
-// lane j holding word j); each mask word of a row, whose 32 voxels start
-// anywhere in the flat array, is then a funnel shift of two flat words fetched
-// by shuffles. A warp's unit is one step of kFlatSpan voxels (independent
-// units keep many steps' loads in flight); the first flat word after the step
-// comes from a ballot over 32 more voxels.
+// as one flat array in steps of kFlatSpan voxels. In a step, lane j forms flat
+// word j (bit b = voxel 32 j + b of the step) from its own 16-byte vectors,
+// without shuffles; each mask word of a row, whose 32 voxels start anywhere in
+// the flat array, is then a funnel shift of two flat words fetched by
+// shuffles. Warps take contiguous ranges of steps (every item's steps in
+// order) and carry the item, its pass test and the row holding the step's
+// first voxel from step to step; the next step's words are loaded before the
+// current step's mask words are written, and give the first flat word after
+// the step (at the end of a warp's range, a ballot over its 32 voxels does).
 constexpr u32 kFlatSpan = 1024;
 
+// The kPer pass bits of one 16-byte vector of values (bit k = element k).
 template <typename TV>
-__device__ __forceinline__ u32 flat_words(const Desc& d, const TV* __restrict__ in, u64 a,
-                                          int lane) {
-  const PassTest pt = pass_test(d);
+__device__ __forceinline__ u32 vec_pass_bits(const PassTest& pt, const uint4& v) {
+  u32 bits = 0;
+  if constexpr (sizeof(TV) == 4) {
+    bits = (passes(pt, __uint_as_float(v.x)) ? 1u : 0u) |
+           (passes(pt, __uint_as_float(v.y)) ? 2u : 0u) |
+           (passes(pt, __uint_as_float(v.z)) ? 4u : 0u) |
+           (passes(pt, __uint_as_float(v.w)) ? 8u : 0u);
+  } else if constexpr (sizeof(TV) == 2) {
+    const u32 q[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      bits |= (passes(pt, q[k] & 0xffffu) ? 1u : 0u) << (2 * k);
+      bits |= (passes(pt, q[k] >> 16) ? 1u : 0u) << (2 * k + 1);
+    }
+  } else {
+    const u32 q[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+        bits |= (passes(pt, (q[k] >> (8 * b)) & 0xffu) ? 1u : 0u) << (4 * k + b);
+  }
+  return bits;
+}
+
+// The flat word of voxels [x0, x0 + 32) (x0 a multiple of 32, the volume
+// 16-byte aligned): 16-byte loads when all 32 lie inside, else one value at a
+// time (voxels at or past N give 0).
+template <typename TV>
+__device__ __forceinline__ u32 flat_word(const PassTest& pt, const TV* __restrict__ in, u64 x0,
+                                         u64 N) {
   constexpr int kPer = 16 / sizeof(TV);
-  constexpr int kLoads = 1024 / (32 * kPer);
-  constexpr int kLanesPerWord = 32 / kPer;
-  constexpr int kWordsPerLoad = 32 / kLanesPerWord;
-  const u64 N = d.rows * d.nx;
-  uint4 v[kLoads];
+  constexpr int kVec = 32 / kPer;
+  u32 bits = 0;
+  if (x0 + 32 <= N) {
+    const uint4* p = reinterpret_cast<const uint4*>(in + x0);
+    uint4 v[kVec];
 #pragma unroll
-  for (int i = 0; i < kLoads; ++i) {
-    const u64 x = a + (u64)i * (32 * kPer) + (u64)lane * kPer;
-    if (x + kPer <= N) {
-      v[i] = __ldg(reinterpret_cast<const uint4*>(in + x));
-    } else {  // the volume's last, partial vector (or past the end): bytes packed by hand
-      u32 w[4] = {0u, 0u, 0u, 0u};
+    for (int i = 0; i < kVec; ++i) v[i] = __ldg(p + i);
 #pragma unroll
-      for (int k = 0; k < kPer; ++k) {
-        if (x + k < N) {
-          u32 b;
-          if constexpr (sizeof(TV) == 4) b = __float_as_uint(__ldg(in + x + k));
-          else b = (u32)__ldg(in + x + k);
-          w[(k * sizeof(TV)) / 4] |= b << (8 * ((k * sizeof(TV)) % 4));
-        }
+    for (int i = 0; i < kVec; ++i) bits |= vec_pass_bits<TV>(pt, v[i]) << (i * kPer);
+  } else {
+    for (u32 k = 0; k < 32; ++k) {
+      if (x0 + k < N) {
+        bool q;
+        if constexpr (sizeof(TV) == 4) q = passes(pt, __ldg(in + x0 + k));
+        else q = passes(pt, (u32)__ldg(in + x0 + k));
+        bits |= (q ? 1u : 0u) << k;
       }
-      v[i] = make_uint4(w[0], w[1], w[2], w[3]);
     }
   }
-  u32 mine = 0;
-#pragma unroll
-  for (int i = 0; i < kLoads; ++i) {
-    const u64 x = a + (u64)i * (32 * kPer) + (u64)lane * kPer;
-    u32 bits = 0;
-    if constexpr (sizeof(TV) == 4) {
-      bits = (passes(pt, __uint_as_float(v[i].x)) ? 1u : 0u) |
-             (passes(pt, __uint_as_float(v[i].y)) ? 2u : 0u) |
-             (passes(pt, __uint_as_float(v[i].z)) ? 4u : 0u) |
-             (passes(pt, __uint_as_float(v[i].w)) ? 8u : 0u);
-    } else if constexpr (sizeof(TV) == 2) {
-      const u32 q[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        bits |= (passes(pt, q[k] & 0xffffu) ? 1u : 0u) << (2 * k);
-        bits |= (passes(pt, q[k] >> 16) ? 1u : 0u) << (2 * k + 1);
-      }
-    } else {
-      const u32 q[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-          bits |= (passes(pt, (q[k] >> (8 * b)) & 0xffu) ? 1u : 0u) << (4 * k + b);
-    }
-    if (x + kPer > N) bits &= x < N ? (1u << (u32)(N - x)) - 1u : 0u;  // voxels past the end
-    u32 t = bits << (kPer * (lane & (kLanesPerWord - 1)));
-#pragma unroll
-    for (int o = 1; o < kLanesPerWord; o <<= 1) t |= __shfl_xor_sync(0xffffffffu, t, o);
-    const u32 wv = __shfl_sync(0xffffffffu, t, kLanesPerWord * (lane & (kWordsPerLoad - 1)));
-    if (lane / kWordsPerLoad == i) mine = wv;
-  }
-  return mine;
+  return bits;
 }
 
 // Mask words of the rows whose voxels x = 32 w .. start in flat step [a, a +
@@ -269,58 +263,80 @@ __device__ __forceinline__ void flat_emit(const Desc& d, u32* __restrict__ T, u6
   }
 }
 
+// A warp's contiguous range [s0, s1) of the batch's flat steps.
 template <typename TV>
-__device__ __forceinline__ void thr_flat_span(const Desc& d, const TV* __restrict__ in,
-                                              u32* __restrict__ T, u64 span, u64 m_nx,
-                                              int lane) {
-  const PassTest pt = pass_test(d);
-  const u64 N = d.rows * d.nx;
-  const u64 a = span * kFlatSpan;
-  const u64 r = div_by(a, d.nx, m_nx);  // the row holding voxel a
-  const int rel0 = (int)((long long)(r * d.nx) - (long long)a);
-  const int lim = (int)umin(1024, N - a);
-  const u32 F = flat_words<TV>(d, in, a, lane);
-  // the first flat word after the step: a ballot over its 32 voxels
-  const u64 x = a + 1024 + lane;
-  bool p = false;
-  if (x < N) {
-    if constexpr (sizeof(TV) == 4) p = passes(pt, __ldg(in + x));
-    else p = passes(pt, (u32)__ldg(in + x));
+__device__ __forceinline__ void thr_flat_range(const Batch& B, u64 s0, u64 s1, int lane) {
+  u64 s = s0;
+  while (s < s1) {
+    // enter the item holding step s
+    const u32 i = find_item(B.fseg0, B.n, s);
+    const Item& I = B.it[i];
+    const Desc d = desc_of(B, I);
+    const PassTest pt = pass_test(d);
+    const TV* __restrict__ in = (const TV*)I.in;
+    u32* __restrict__ T = I.T;
+    const u64 N = d.rows * d.nx;
+    const u64 end = umin(s1, B.fseg0[i + 1]);  // the warp's steps of this item
+    u64 a = (s - B.fseg0[i]) * kFlatSpan;
+    u64 r = div_by(a, d.nx, I.m_nx);  // the row holding voxel a
+    int rel0 = (int)((long long)(r * d.nx) - (long long)a);
+    const int nx = (int)d.nx;
+    u32 F = flat_word<TV>(pt, in, a + 32u * (u32)lane, N);
+    for (; s < end; ++s) {
+      const u64 an = a + kFlatSpan;
+      u32 Fn = 0, f32;
+      if (s + 1 < end) {  // the next step is this warp's: its words now
+        Fn = flat_word<TV>(pt, in, an + 32u * (u32)lane, N);
+        f32 = __shfl_sync(0xffffffffu, Fn, 0);
+      } else {  // the first flat word after the step: a ballot over its 32 voxels
+        const u64 x = an + lane;
+        bool p = false;
+        if (x < N) {
+          if constexpr (sizeof(TV) == 4) p = passes(pt, __ldg(in + x));
+          else p = passes(pt, (u32)__ldg(in + x));
+        }
+        f32 = __ballot_sync(0xffffffffu, p);
+      }
+      const int lim = (int)umin(kFlatSpan, N - a);
+      flat_emit(d, T, a, F, f32, r, rel0, lim, lane);
+      F = Fn;
+      a = an;
+      rel0 -= (int)kFlatSpan;
+      while (rel0 <= -nx) {  // nx >= 256: at most four rows start in a step
+        rel0 += nx;
+        ++r;
+      }
+    }
   }
-  const u32 f32 = __ballot_sync(0xffffffffu, p);
-  flat_emit(d, T, a, F, f32, r, rel0, lim, lane);
 }
 
-// Warps take the batch's work units in order (all items): 1024-voxel row
-// segments of the row-form items, or kFlatSpan-voxel steps of the flat-form
-// items (FLAT; a launch of its own, so that each form keeps its registers).
+// Warps take the batch's work units (all items, in order): 1024-voxel row
+// segments of the row-form items, strided over the warps, or contiguous ranges
+// of the kFlatSpan-voxel steps of the flat-form items (FLAT; a launch of its
+// own, so that each form keeps its registers).
 template <typename TV, bool FLAT>
 __global__ void __launch_bounds__(kThreads, 4) k_threshold(const __grid_constant__ Batch B) {
   const int lane = threadIdx.x & 31;
   const u64 warp = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
-  const u64 total = FLAT ? B.fseg0[B.n] : B.seg0[B.n];
+  if constexpr (FLAT) {
+    const u64 total = B.fseg0[B.n];
+    const u64 per = (total + nwarps - 1) / nwarps;
+    const u64 s0 = warp * per;
+    if (s0 < total) thr_flat_range<TV>(B, s0, umin(total, s0 + per), lane);
+    return;
+  }
+  const u64 total = B.seg0[B.n];
   for (u64 s = warp; s < total; s += nwarps) {
-    u32 i;
-    u64 local;
-    if constexpr (FLAT) {
-      i = find_item(B.fseg0, B.n, s);
-      local = s - B.fseg0[i];
-    } else {
-      i = find_item(B.seg0, B.n, s);
-      local = s - B.seg0[i];
-    }
+    const u32 i = find_item(B.seg0, B.n, s);
+    const u64 local = s - B.seg0[i];
     const Item& I = B.it[i];
     const Desc d = desc_of(B, I);
-    if constexpr (FLAT) {
-      thr_flat_span<TV>(d, (const TV*)I.in, I.T, local, I.m_nx, lane);
-    } else {
-      const u64 spr = (I.nx + 1023) >> 10;
-      const u64 r = spr == 1 ? local : div_by(local, spr, I.m_spr);
-      const u32 x0 = (u32)(local - r * spr) << 10;
-      if (I.vec) thr_segment_vec<TV>(d, (const TV*)I.in, I.T, r, x0, lane);
-      else thr_segment<TV>(d, (const TV*)I.in, I.T, r, x0, lane);
-    }
+    const u64 spr = (I.nx + 1023) >> 10;
+    const u64 r = spr == 1 ? local : div_by(local, spr, I.m_spr);
+    const u32 x0 = (u32)(local - r * spr) << 10;
+    if (I.vec) thr_segment_vec<TV>(d, (const TV*)I.in, I.T, r, x0, lane);
+    else thr_segment<TV>(d, (const TV*)I.in, I.T, r, x0, lane);
   }
 }
 
