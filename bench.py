@@ -36,17 +36,26 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "GB/s in (quantize+ROI+encode) vs HBM peak, batched/served vs plain; p50/p99 latency"
-# kernels of one fused group: reset, binarisation, compaction count, scan and write,
-# symbols, codebook, pack count, pack scan, records, pack, finalise (+1 when flat-form items are
-# binarised next to row-form ones)
-LAUNCHES_PER_GROUP = 12
+# kernels of one fused group: reset, binarisation (one launch per form: row or
+# flat), compaction count, compaction write, symbols, codebook, pack count,
+# pack, finalise; plus a tile-scan launch for the compaction when some item has
+# more tiles than the counting kernel scans itself (IN_SCAN_MAX), and a chunk
+# scan and a records launch when some item has more pack chunks than that
+LAUNCHES_PER_GROUP = 8
+IN_SCAN_MAX = 1024
 
 
-def group_launches(xs) -> int:
-    """Kernel launches of one fused group of items (the library's rule for
-    the two binarisation forms: flat when a 16-byte aligned volume has nx >=
-    256 and its rows are not aligned or do not fill 1024-voxel segments)."""
-    flat = row = False
+def group_launches(xs, cfg=None, tuning=None) -> int:
+    """Kernel launches of one fused group of items (the library's rules: the
+    flat binarisation form when a 16-byte aligned volume has nx >= 256 and its
+    rows are not aligned or do not fill 1024-voxel segments; a tile scan
+    launch only for items with more than IN_SCAN_MAX compaction tiles or pack
+    chunks)."""
+    cfg = cfg or {}
+    tuning = tuning or {}
+    fw = tuning.get("front_words", 2048) or 2048
+    C = cfg.get("chunk", 4096)
+    flat = row = scan0 = scan1 = False
     for x in xs:
         nx = x.shape[-1]
         ptr = x.data_ptr()
@@ -55,7 +64,12 @@ def group_launches(xs) -> int:
             flat = True
         else:
             row = True
-    return LAUNCHES_PER_GROUP - 1 + int(flat) + int(row)
+        rows = x.numel() // nx
+        W = (nx + 31) // 32
+        rpt = max(1, min(256, fw // W, rows))
+        scan0 |= -(-rows // rpt) > IN_SCAN_MAX
+        scan1 |= -(-x.numel() // C) > IN_SCAN_MAX
+    return LAUNCHES_PER_GROUP + int(flat) + int(row) + int(scan0) + 2 * int(scan1)
 
 # DRAM bytes per step of each stage (dram__bytes_read.sum + dram__bytes_write.sum,
 # summed over the stage's kernels, one launch each) from an ncu capture of the
@@ -270,7 +284,8 @@ def measure(args, workload, xs, cfg, path, dev, world, local_rank, tuning=None, 
     if path == "batch":
         def step(inputs, outs_=outs, sizes_=sizes):
             ctxs[0].compress_batch(inputs, outs=outs_, caps=caps, sizes=sizes_, stream=main, **cfg)
-        launches_per_step = sum(group_launches(xs[g:g + 64]) for g in range(0, len(xs), 64))
+        launches_per_step = sum(group_launches(xs[g:g + 64], cfg, tuning)
+                                for g in range(0, len(xs), 64))
     else:
         def step(inputs, outs_=outs, sizes_=sizes):
             for s_ in streams:
@@ -281,7 +296,7 @@ def measure(args, workload, xs, cfg, path, dev, world, local_rank, tuning=None, 
                                  stream=streams[k], **cfg)
             for s_ in streams:
                 main.wait_stream(s_)
-        launches_per_step = sum(group_launches([x]) for x in xs)
+        launches_per_step = sum(group_launches([x], cfg, tuning) for x in xs)
 
     # one untimed step outside any graph; its status is checked
     step(xs)
@@ -520,7 +535,7 @@ def sub_line(m, xs, cfg, desc, path_desc):
 
 
 def path_text(path, m):
-    return (("roix_compress_batch: %d launches per 64 items" % LAUNCHES_PER_GROUP) if path == "batch"
+    return (("roix_compress_batch: %d launches per step" % m["launches_per_step"]) if path == "batch"
             else "roix_compress per item on %d streams" % m["nstreams"]) + \
         (", one CUDA graph per step" if m["graph"] else "")
 
@@ -1346,7 +1361,12 @@ def run_slabs(args, rank, world, local_rank):
                 "stage_ms_per_call": {k: round(float(v), 4) for k, v in zip(names, stage_ms)},
                 "stage_gbs": {k: round(alg[k] / (float(v) / 1e3) / 1e9, 1)
                               for k, v in zip(names, stage_ms) if v > 0}}
-    launches = (2 + (LAUNCHES_PER_GROUP - 2) * ((ns + 63) // 64)) * len(cfgs) * args.steps
+    # reset and one binarisation of the whole volume, then per group of up to 64
+    # slabs: compaction count, its tile scan (slabs have more than IN_SCAN_MAX
+    # tiles), write, symbols, codebook, pack count, its chunk scan, records,
+    # pack, finalise
+    per_call = 2 + 10 * ((ns + 63) // 64)
+    launches = per_call * len(cfgs) * args.steps
     result = None
     if rank == 0:
         cpu = slab_cpu(sc, args.cpu_budget, args.seed) if world == 1 and not args.no_cpu else None
@@ -1358,7 +1378,7 @@ def run_slabs(args, rank, world, local_rank):
             "config": {"workload": args.workload, "desc": sc["desc"], "slabs": ns,
                        "bytes_in_per_call": in_bytes, "calls_per_step": len(cfgs),
                        "sweep": sweep, "path": "roix_compress_slabs: %d launches per call "
-                       "(32 slabs in one group)" % LAUNCHES_PER_GROUP,
+                       "(32 slabs in one group)" % per_call,
                        "l2": "inputs larger than L2 (129 MB)",
                        "parallelism": f"replicas x{world}",
                        "tuning": dict(tuning, seconds=round(tune_s, 2))},

@@ -281,8 +281,8 @@ __device__ __forceinline__ void flush_hist(u32* h, unsigned long long* g, u32 S,
 // barrier anywhere in the loop) and goes to the item's global histogram when
 // the warp moves to another item. Symbol-0 positions (records) are only
 // counted here, per pack chunk (an atomic per lane and step that has one);
-// they are written by k_records once their offsets are known, so that no
-// segment waits for another.
+// they are written by k_pack_count once the codebook kernel has turned the
+// counts into offsets, so that no segment waits for another.
 template <typename TV, bool FROM_Q, int ORDER>
 __global__ void __launch_bounds__(kThreads) k_symbols(const __grid_constant__ Batch B) {
   if (halted(B.status)) return;  // a tile scan of this call gave up
@@ -834,19 +834,41 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__
     lens_ws[s] = len[s];
     if (kHeaderBytes + s < cap) out[kHeaderBytes + s] = len[s];
   }
+  // the records of an item with at most kInScanMax chunks: per-chunk counts
+  // (from the symbol kernel) into offsets (larger items: k_scan_pairs<1>)
+  if (I.pscan) {
+    __shared__ u64 scratch64[40];
+    const u64 n = umin(I.sizes[0], I.N);
+    const u64 nch = (n + B.c.C - 1) / B.c.C;
+    const u64 nout = block_scan1(I.crec, nch, I.crecoff, scratch64);
+    if (tid == 0) {
+      I.st->nout = nout;
+      if (nout > I.rec_cap) I.st->cap_flag = 1u;
+    }
+  }
   CB_MARK(7)
 }
 
 // ------------------------------------------------------------------- pack
 // Passes none of whose blocks waits on another: k_pack_count sums the code
-// lengths of every chunk, k_scan_pairs<1> turns the chunks' word and record
-// counts into offsets, and k_pack writes every chunk's words at its offset
-// (chunks from global tickets in order); k_records writes the records of the
-// chunks that have any.
+// lengths of every chunk; the chunks' word and record counts become offsets
+// (for items with at most kInScanMax chunks in the codebook kernel and in
+// k_pack_count, which then also writes their records; for larger items in
+// k_scan_pairs<1>, followed by k_records), and k_pack writes every chunk's
+// words at its offset (chunks from global tickets in order).
 
 // Warps, one chunk at a time: lane l holds symbols [8 l, 8 l + 8) of each
 // round of 256 (coalesced 16-byte loads); the code lengths come from the
-// item's byte table (2R bytes, read through L1).
+// item's byte table (2R bytes, read through L1). For an item with at most
+// kInScanMax chunks the warp also writes the chunk's records, if it holds
+// any: the symbol-0 positions in order, from the
+// record bitmap the symbol kernel wrote (lane l with words l, l + 32, ...; a
+// warp scan of their popcounts), each as (k | kind << 63, payload) at the
+// chunk's record offset (scanned by the codebook kernel); the code or the raw
+// value is formed again from the pixel section (or the staged codes). For an
+// item with at most kInScanMax chunks, the warp that counts the item's last
+// chunk scans the chunks' word counts into their offsets.
+template <typename TV, bool FROM_Q>
 __global__ void __launch_bounds__(kThreads) k_pack_count(const __grid_constant__ Batch B) {
   if (halted(B.status)) return;  // a tile scan of this call gave up
   __shared__ u64 pre[kMaxBatch + 1];
@@ -857,6 +879,8 @@ __global__ void __launch_bounds__(kThreads) k_pack_count(const __grid_constant__
   const u64 total = pre[B.n];
   const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
   constexpr u32 kIn = 4;  // vector loads of a lane in flight at once
+  u32 cur = 0xffffffffu;  // item whose records source is set
+  Src<TV, FROM_Q> src{};
   for (u64 gt = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5; gt < total; gt += nwarps) {
     const u32 item = find_item(pre, B.n, gt);
     const Item& I = B.it[item];
@@ -892,15 +916,59 @@ __global__ void __launch_bounds__(kThreads) k_pack_count(const __grid_constant__
     }
     bits = __reduce_add_sync(0xffffffffu, bits);
     if (lane == 0) I.cw[t] = (bits + 31) >> 5;
+    if (I.pscan && I.crec[t] != 0u) {  // the chunk's records (a small item's)
+      if (item != cur) {
+        cur = item;
+        const Desc d = desc_of(B, I);
+        src.P = (const TV*)I.P;
+        src.q = I.q;
+        src.obits = I.obits;
+        src.dark = d.dark;
+        if constexpr (!FROM_Q) {
+          src.e = make_eb(d, I.rst->vmin_key, I.rst->vmax_key);
+          src.fd = FastDiv(2u * (u32)src.e.eb_int);
+        }
+      }
+      const u32* __restrict__ rbits = I.rbits;
+      u64 idx = I.crecoff[t];
+      const u64 w0 = t * (C / 32), nwords = (umin(n, (t + 1) * (u64)C) - t * C + 31) / 32;
+      for (u64 j0 = 0; j0 < nwords; j0 += 32) {
+        const u64 j = j0 + lane;
+        u32 zm = j < nwords ? __ldg(rbits + w0 + j) : 0u;
+        const u32 cnt = __popc(zm);
+        const u32 inc = warp_incl_scan(cnt);
+        u64 o = idx + inc - cnt;
+        while (zm) {
+          const int q = __ffs(zm) - 1;
+          zm &= zm - 1;
+          const u64 k = (w0 + j) * 32 + q;
+          bool out;
+          const int c = src.code(k, out);
+          if (o < I.rec_cap) {
+            I.rk[o] = k | (out ? (1ull << 63) : 0ull);
+            I.rv[o] = out ? src.raw_bits(k) : (u32)c;
+          }
+          ++o;
+        }
+        idx += __shfl_sync(0xffffffffu, inc, 31);
+      }
+    }
+    const u64 nch = pre[item + 1] - pre[item];
+    if (I.pscan && count_done(&I.st->done_pack, nch)) {  // the item's chunk offsets
+      u64 tw, tr;
+      warp_scan2(I.cw, nullptr, nch, I.cwoff, nullptr, tw, tr);
+      if (lane == 0) I.st->nwords = tw;
+    }
   }
 }
 
-// Warps, one chunk at a time, only chunks that hold records: the symbol-0
-// positions of the chunk in order, from the record bitmap the symbol kernel
-// wrote (lane l with words l, l + 32, ...; a warp scan of their popcounts),
-// each written as (k | kind << 63, payload) at the chunk's record offset; the
-// code or the raw value is formed again from the pixel section (or the staged
-// codes).
+// Warps, one chunk at a time, only chunks that hold records of items with
+// more than kInScanMax chunks (k_pack_count writes those of the others): the
+// symbol-0 positions of the chunk in order, from the record bitmap the symbol
+// kernel wrote (lane l with words l, l + 32, ...; a warp scan of their
+// popcounts), each written as (k | kind << 63, payload) at the chunk's record
+// offset (from k_scan_pairs<1>); the code or the raw value is formed again from
+// the pixel section (or the staged codes).
 template <typename TV, bool FROM_Q>
 __global__ void __launch_bounds__(kThreads) k_records(const __grid_constant__ Batch B) {
   if (halted(B.status)) return;  // a tile scan of this call gave up
@@ -918,7 +986,7 @@ __global__ void __launch_bounds__(kThreads) k_records(const __grid_constant__ Ba
     const u32 item = find_item(pre, B.n, gt);
     const Item& I = B.it[item];
     const u64 t = gt - pre[item];
-    if (I.crec[t] == 0u) continue;
+    if (I.pscan || I.crec[t] == 0u) continue;
     if (item != cur) {  // the item's error-bound constants, formed only for chunks with records
       cur = item;
       const Desc d = desc_of(B, I);
@@ -1271,13 +1339,28 @@ void launch_codebook(const Launch& L, const Batch& B) {
 void launch_pack(const Launch& L, const Batch& B, u64 ranges_cap) {
   if (ranges_cap == 0) return;
   const u64 wpb = kThreads / 32;
-  {  // chunk sizes
-    u64 grid = (u64)grid_for((const void*)k_pack_count, kThreads, 0, L.sms);
-    grid = umin(grid, (ranges_cap + wpb - 1) / wpb);
-    k_pack_count<<<(unsigned)grid, kThreads, 0, L.stream>>>(B);
+  {  // chunk sizes and records
+    const bool from_q = B.it[0].q != nullptr;
+    auto count = [&](auto kernel) {
+      u64 grid = (u64)grid_for((const void*)kernel, kThreads, 0, L.sms);
+      grid = umin(grid, (ranges_cap + wpb - 1) / wpb);
+      kernel<<<(unsigned)grid, kThreads, 0, L.stream>>>(B);
+    };
+    if (B.c.dtype == ROIX_F32) {
+      if (from_q) count(k_pack_count<float, true>);
+      else count(k_pack_count<float, false>);
+    } else {
+      if (from_q) count(k_pack_count<unsigned short, true>);
+      else count(k_pack_count<unsigned short, false>);
+    }
   }
-  launch_scan_pairs(L, B, 1, (ranges_cap + kScanTile - 1) / kScanTile + B.n);
-  {  // records (chunks that hold any)
+  // chunk and record offsets, then records, of the items too large for the
+  // in-kernel scans
+  u64 scan_tiles = 0;
+  for (u32 i = 0; i < B.n; ++i)
+    if (!B.it[i].pscan) scan_tiles += (B.it[i].N + B.c.C - 1) / B.c.C / kScanTile + 1;
+  launch_scan_pairs(L, B, 1, scan_tiles);
+  if (scan_tiles) {
     const bool from_q = B.it[0].q != nullptr;
     const u64 grid = umin((ranges_cap + wpb - 1) / wpb, (u64)L.sms * 8);
     if (B.c.dtype == ROIX_F32) {

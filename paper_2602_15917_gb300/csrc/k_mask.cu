@@ -602,6 +602,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_front_count_blk(const __grid_co
         I.ftn[t] = (u32)tn;
         I.ftb[t] = (u32)tb;
       }
+      if (I.fscan && count_done(&I.st->done_front, I.ftiles)) {  // the item's tile scan
+        u64 an, ab;
+        warp_scan2(I.ftn, I.ftb, I.ftiles, I.ftno, I.ftbo, an, ab);
+        if (lane == 0) {
+          I.sizes[0] = an;
+          I.sizes[1] = ab;
+        }
+      }
     }
     __syncthreads();
     // each row's offsets within the tile (a warp walks its own rows in order)
@@ -812,6 +820,14 @@ __device__ __forceinline__ void front_count_tile(const Batch& B, const Item& I, 
     I.ftn[t] = on;
     I.ftb[t] = ob;
   }
+  if (I.fscan && count_done(&I.st->done_front, I.ftiles)) {  // the item's tile scan
+    u64 an, ab;
+    warp_scan2(I.ftn, I.ftb, I.ftiles, I.ftno, I.ftbo, an, ab);
+    if (lane == 0) {
+      I.sizes[0] = an;
+      I.sizes[1] = ab;
+    }
+  }
   __syncwarp();
 }
 
@@ -848,7 +864,8 @@ __global__ void __launch_bounds__(1024) k_scan_pairs(const __grid_constant__ Bat
   for (u32 i = tid; i < B.n; i += blockDim.x) {  // counts read in parallel
     const Item& I = B.it[i];
     const u64 cnt = MODE == 0 ? I.ftiles : (umin(I.sizes[0], I.N) + B.c.C - 1) / B.c.C;
-    pre[i + 1] = (cnt + kScanTile - 1) / kScanTile;
+    const bool done = MODE == 0 ? I.fscan != 0 : I.pscan != 0;  // scanned by the counting kernel
+    pre[i + 1] = done ? 0 : (cnt + kScanTile - 1) / kScanTile;
   }
   __syncthreads();
   if (tid == 0) {
@@ -1321,7 +1338,8 @@ void launch_front(const Launch& L, const Batch& B) {
     else count(k_front_count<false>);
   }
   u64 scan_tiles = 0;
-  for (u32 i = 0; i < B.n; ++i) scan_tiles += (B.it[i].ftiles + kScanTile - 1) / kScanTile;
+  for (u32 i = 0; i < B.n; ++i)
+    if (!B.it[i].fscan) scan_tiles += (B.it[i].ftiles + kScanTile - 1) / kScanTile;
   launch_scan_pairs(L, B, 0, scan_tiles);
   auto run = [&](auto kernel) {
     u64 g = (u64)occupancy_grid((const void*)kernel, kThreads, 0, L.sms);

@@ -365,6 +365,8 @@ void fill_batch(Batch& B, const Desc& c, const BatchPlan& bp, const roix_dims* d
     I.m_rpt = recip64(p.rpt);
     I.m_ny = recip64(I.ny);
     I.ftiles = p.ftiles;
+    I.fscan = p.ftiles <= kInScanMax ? 1u : 0u;
+    I.pscan = p.pchunks <= kInScanMax ? 1u : 0u;
     B.seg0[i] = seg;
     B.ftile0[i] = ft;
     B.row0[i] = rw;

@@ -266,6 +266,35 @@ __device__ __forceinline__ void block_scan2(const u32* __restrict__ a, const u32
   }
 }
 
+// Exclusive scan of one count array a[0..n) into ao by one block (as
+// block_scan2); returns the total in every thread.
+__device__ __forceinline__ u64 block_scan1(const u32* __restrict__ a, u64 n,
+                                           u64* __restrict__ ao, u64* scratch) {
+  const u64 per = (n + blockDim.x - 1) / blockDim.x;
+  const u64 lo = umin(n, (u64)threadIdx.x * per), hi = umin(n, lo + per);
+  u64 sa = 0;
+  for (u64 i0 = lo; i0 < hi; i0 += 8) {
+    u32 va[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) va[k] = i0 + k < hi ? __ldg(a + i0 + k) : 0u;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sa += va[k];
+  }
+  u64 ta;
+  u64 ea = block_excl_scan<u64>(sa, scratch, &ta);
+  for (u64 i0 = lo; i0 < hi; i0 += 8) {
+    u32 va[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) va[k] = i0 + k < hi ? __ldg(a + i0 + k) : 0u;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (i0 + k < hi) ao[i0 + k] = ea;
+      ea += va[k];
+    }
+  }
+  return ta;
+}
+
 // ------------------------------------------------------------ fast division
 // Division of 32-bit numerators by an invariant divisor with a multiply-high
 // and shifts (Granlund & Montgomery 1994, round-up method).
@@ -350,6 +379,7 @@ struct State {
   u64 n, nb, nout, nwords;             // sizes found on the device
   u32 vmin_key, vmax_key;              // range of retained finite values
   u32 cap_flag, pad0;
+  u32 done_front, done_pack;           // tiles / chunks counted (the last one scans)
   u64 total;
   roix_eb_info eb;
 };
@@ -431,6 +461,10 @@ struct Item {
   u32 zhalo;                           // z-slab: bit 0 = T holds the plane before z = 0,
                                        // bit 1 = T holds the plane after z = nz - 1
   u64 ftiles;                          // front tiles
+  u32 fscan;                           // the counting kernel scans the tile totals
+                                       // (ftiles <= kInScanMax), not k_scan_pairs<0>
+  u32 pscan;                           // k_pack_count scans the chunk word counts
+                                       // (chunks <= kInScanMax), not k_scan_pairs<1>
   u64 m_nx, m_spr, m_rpt, m_ny;        // recip64 of nx, of the 1024-voxel segments per
                                        // row, of rpt and of ny (divisions by multiply-high)
 };
@@ -599,6 +633,57 @@ struct Launch {
 
 // mask kernels (k_mask.cu)
 constexpr u32 kScanTile = 8192;  // entries per block of the tile scans
+// Items with at most this many compaction tiles (pack chunks) have their tile
+// scan done inside the counting kernel, by the warp that counts the item's
+// last tile; larger ones go through k_scan_pairs.
+constexpr u32 kInScanMax = 1024;
+
+// Exclusive scans of two u32 arrays a, b (b may be null) of an item's nt
+// entries into u64 ao, bo by one warp (loads in batches of 8 per lane, through
+// L2: the entries were written by other blocks of the running kernel); returns
+// the totals.
+__device__ __forceinline__ void warp_scan2(const u32* a, const u32* b, u64 nt, u64* ao,
+                                           u64* bo, u64& ta, u64& tb) {
+  const int lane = threadIdx.x & 31;
+  u64 ca = 0, cb = 0;
+  for (u64 i0 = 0; i0 < nt; i0 += 256) {
+    u32 va[8], vb[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const u64 i = i0 + (u64)k * 32 + lane;
+      va[k] = i < nt ? __ldcg(a + i) : 0u;
+      vb[k] = (b && i < nt) ? __ldcg(b + i) : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const u64 i = i0 + (u64)k * 32 + lane;
+      const u32 ia = warp_incl_scan(va[k]), ib = warp_incl_scan(vb[k]);
+      if (i < nt) {
+        ao[i] = ca + ia - va[k];
+        if (bo) bo[i] = cb + ib - vb[k];
+      }
+      ca += __shfl_sync(0xffffffffu, ia, 31);
+      cb += __shfl_sync(0xffffffffu, ib, 31);
+    }
+  }
+  ta = ca;
+  tb = cb;
+}
+
+// One more tile (chunk) of an item counted: true in the warp that counted the
+// last of its `total`, which may then read every tile's totals. Called by all
+// lanes of a warp after lane 0 wrote the tile's totals.
+__device__ __forceinline__ bool count_done(u32* done, u64 total) {
+  u32 old = 0;
+  if ((threadIdx.x & 31) == 0) {
+    __threadfence();  // the tile's totals before the count
+    old = atomicAdd(done, 1u);
+  }
+  old = __shfl_sync(0xffffffffu, old, 0);
+  const bool last = (u64)old + 1 == total;
+  if (last) __threadfence();  // the other tiles' totals after the count
+  return last;
+}
 // Exclusive scans of the pairs (ftn, ftb) over compaction tiles (mode 0: into
 // ftno, ftbo and the item's n, nb) or (cw, crec) over pack chunks (mode 1:
 // into cwoff, crecoff and the item's nwords, nout); tiles_cap bounds the scan
