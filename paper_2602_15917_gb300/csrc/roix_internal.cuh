@@ -314,11 +314,13 @@ __device__ __forceinline__ u64 div_by(u64 a, u64 d, u64 m) {
 
 struct FastDiv {
   u32 d, m, s;
-  __host__ __device__ FastDiv(u32 div = 1) : d(div ? div : 1), m(0), s(0) {
+  u32 p2;  // d is a power of two (= 2^s)
+  __host__ __device__ FastDiv(u32 div = 1) : d(div ? div : 1), m(0), s(0), p2(0) {
     u32 l = 0;
     while ((1ull << l) < d) ++l;
     s = l;
     m = l ? (u32)(((1ull << 32) * ((1ull << l) - d)) / d + 1) : 0u;
+    p2 = (d & (d - 1)) == 0 ? 1u : 0u;
   }
   __device__ __forceinline__ u32 div(u32 n) const {
     if (s == 0) return n;
@@ -332,6 +334,7 @@ __device__ __forceinline__ int quant_u16_fd(unsigned raw, int dark, int eb_int,
   const int v = (int)raw - dark;  // in [-65535, 65535]
   if (eb_int == 0) return v;
   const int num = v + eb_int;
+  if (fd.p2) return num >> fd.s;  // floor of num / 2^s (arithmetic shift)
   return num >= 0 ? (int)fd.div((u32)num) : -(int)fd.div((u32)(-num + 2 * eb_int - 1));
 }
 
