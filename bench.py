@@ -1161,6 +1161,146 @@ def run_serve(args, rank, world, local_rank):
     }
 
 
+# ------------------------------------------------------------- decoding
+DECODE = {
+    "decode_projections64": dict(base="projections64"),
+    "decode_cube1024": dict(base="cube1024"),
+}
+
+
+def decode_cpu(xs, conts, budget_s):
+    """The oracle's decoder on one host core over the containers in order
+    (~budget_s of work); GB/s of decoded output."""
+    import oracle
+    done, t0, i = 0, time.perf_counter(), 0
+    while True:
+        x, c = xs[i % len(xs)], conts[i % len(conts)]
+        oracle.decode(c, tuple(x.shape), np.float32 if x.element_size() == 4 else np.uint16)
+        done += x.numel() * x.element_size()
+        i += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": round(done / dt / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"containers in order until ~{budget_s:.0f} s: {i} decodes, "
+                      f"{done / 1e6:.0f} MB out in {dt:.1f} s"}
+
+
+def run_decode(args, rank, world, local_rank):
+    """roix_decode of the workload's containers (compressed once, untimed): a
+    step decodes every container (one call per item, spread over contexts and
+    streams, captured in a CUDA graph); GB/s of decoded output. The decoded
+    items are checked against the oracle's decoder (bit for bit) on a sample."""
+    import torch
+    import torch.distributed as dist
+    import oracle
+    import paper_2602_15917_gb300 as roix
+    dc = DECODE[args.workload]
+    wl = WORKLOADS[dc["base"]]
+    cfg = dict(wl["cfg"], predictor=args.predictor)
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    xs = make_inputs(dc["base"], dev, seed=args.seed)
+    rc = roix.Roix(local_rank)
+    outs, sizes = rc.compress_batch(xs, **cfg)
+    rc.sync()
+    szs = [int(v) for v in sizes.cpu().numpy()]
+    conts = [o[:z].clone() for o, z in zip(outs, szs)]
+    del outs
+    rc.close()
+    torch.cuda.synchronize()
+    out_bytes = sum(x.numel() * x.element_size() for x in xs)
+    in_bytes = sum(szs)
+    # one context and stream per container (up to 64): each decode keeps only a
+    # few blocks busy, so the items' decodes run side by side
+    nstreams = min(len(xs), 64)
+    ctxs = [roix.Roix(local_rank) for _ in range(nstreams)]
+    streams = [torch.cuda.Stream(dev) for _ in range(nstreams)]
+    ys = [torch.empty_like(x) for x in xs]
+    main = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(main)
+
+    def step():
+        for s_ in streams:
+            s_.wait_stream(main)
+        for i, (x, c) in enumerate(zip(xs, conts)):
+            k = i % nstreams
+            ctxs[k].decode(c, x.shape, x.dtype, out=ys[i], stream=streams[k])
+        for s_ in streams:
+            main.wait_stream(s_)
+
+    step()  # workspaces sized outside the graph
+    torch.cuda.synchronize()
+    for c, s_ in zip(ctxs, streams):
+        c.sync(s_)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=main, capture_error_mode="thread_local"):
+        step()
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local_rank) as clk:
+        e0.record(main)
+        for _ in range(args.steps):
+            graph.replay()
+        e1.record(main)
+        torch.cuda.synchronize()
+    ms_step = reduce_over_ranks(e0.elapsed_time(e1) / args.steps, world, "max", dev)
+    for c, s_ in zip(ctxs, streams):
+        c.sync(s_)
+    step_ms = []
+    for _ in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(main)
+        graph.replay()
+        b.record(main)
+        b.synchronize()
+        step_ms.append(a.elapsed_time(b))
+    # the decodes against the oracle's decoder, bit for bit (a sample of items)
+    ok, nchk, t0 = True, 0, time.perf_counter()
+    for x, c, y in zip(xs, conts, ys):
+        want = oracle.decode(c.cpu().numpy(), tuple(x.shape),
+                             np.float32 if x.element_size() == 4 else np.uint16)
+        ok = ok and np.array_equal(y.cpu().numpy().view(np.uint8), want.view(np.uint8))
+        nchk += 1
+        if time.perf_counter() - t0 > 20.0:
+            break
+    peak, kind = load_peaks()
+    alg = in_bytes + out_bytes  # read the containers, write the values
+    ach = alg / (ms_step / 1e3) / 1e9
+    value = out_bytes * world / (ms_step / 1e3) / 1e9
+    result = None
+    if rank == 0:
+        cpu = (decode_cpu([x.cpu() for x in xs[:4]], [c.cpu().numpy() for c in conts[:4]],
+                          args.cpu_budget) if world == 1 and not args.no_cpu else None)
+        result = {
+            "metric": "GB/s out (decode of the containers)", "value": round(value, 2),
+            "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u16" if xs[0].element_size() == 2 else "f32",
+            "data": "synthetic", "decode_matches_oracle": ok,
+            "config": {"workload": args.workload, "desc": "decode of: " + wl["desc"],
+                       "items": len(xs), "container_bytes": in_bytes, "bytes_out_per_step": out_bytes,
+                       "path": "roix_decode per item on %d streams, one CUDA graph per step" % nstreams,
+                       "checked": f"{nchk} decodes against the oracle's, bit for bit"},
+            "latency": {"p50_ms": round(float(np.percentile(step_ms, 50)), 4),
+                        "p99_ms": round(float(np.percentile(step_ms, 99)), 4),
+                        "of": "one step (every container) from launch to completion"},
+            "roofline": {"bound": "hbm", "kernel": "decode (all launches)", "achieved": round(ach, 1),
+                         "peak": peak, "peak_source": kind, "unit": "GB/s",
+                         "frac": round(ach / peak, 4), "traffic": None, "traffic_source": None,
+                         "algorithmic_bytes_per_step": alg},
+            "cpu_baseline": cpu, "clocks": clk.summary(),
+            "gpu_launches": None,
+        }
+    for c in ctxs:
+        c.close()
+    return result
+
+
 # ------------------------------------------------- 2048^3 volume in z-slabs
 SLABS = {
     "cube2048_slabs": dict(
@@ -1405,6 +1545,32 @@ def run_reference(args, rank, world):
                 "impl": "reference", "config": {"workload": args.workload, "desc": ev["desc"]},
                 "cpu_baseline": c, "e2e": {"value": c["value"], "unit": "GB/s",
                                            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    if args.workload in DECODE:
+        import oracle
+        base = DECODE[args.workload]["base"]
+        cfg = WORKLOADS[base]["cfg"]
+        xs = make_inputs(base, "cpu", seed=args.seed)
+        if len(xs) == 1 and xs[0].dim() == 3 and xs[0].shape[0] > 64:  # a slab of a large volume
+            z = xs[0].shape[0]
+            xs = [xs[0][z // 2 - 8: z // 2 + 8].contiguous()]
+        else:
+            xs = xs[:4]
+        conts = [oracle.compress(x.numpy(), **cfg) for x in xs]
+        per_step = max(1.0, args.cpu_budget / max(1, args.steps + args.warmup))
+        for _ in range(args.warmup):
+            decode_cpu(xs, conts, per_step)
+        vals = [decode_cpu(xs, conts, per_step) for _ in range(args.steps)]
+        gbs = float(np.mean([v["value"] for v in vals]))
+        return {"metric": "GB/s out (decode of the containers)", "value": round(gbs, 4),
+                "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "u16" if xs[0].element_size() == 2 else "f32",
+                "data": "synthetic", "impl": "reference",
+                "config": {"workload": args.workload, "desc": "decode of: " + WORKLOADS[base]["desc"]},
+                "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s", "cores": 1,
+                                 "kind": "oracle", "sample": vals[-1]["sample"]},
+                "e2e": {"value": round(gbs, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
     if args.workload in SLABS:
         sc = SLABS[args.workload]
         per_step = max(1.0, args.cpu_budget / max(1, args.steps + args.warmup))
@@ -1475,6 +1641,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="projections64",
                     choices=sorted(WORKLOADS) + sorted(PAPER8) + sorted(EVAL) + sorted(SLABS)
+                    + sorted(DECODE)
                     + ["serve"])
     ap.add_argument("--serve-seconds", type=float, default=15.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
@@ -1513,6 +1680,7 @@ def main():
                else run_paper8(args, rank, world, local_rank) if args.workload in PAPER8
                else run_eval(args, rank, world, local_rank) if args.workload in EVAL
                else run_slabs(args, rank, world, local_rank) if args.workload in SLABS
+               else run_decode(args, rank, world, local_rank) if args.workload in DECODE
                else run_ours(args, rank, world, local_rank))
         if world > 1:
             import torch.distributed as dist

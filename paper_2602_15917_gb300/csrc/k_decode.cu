@@ -26,6 +26,10 @@ __device__ __forceinline__ T rd(const uint8_t* p, u64 off) {
   return *reinterpret_cast<const T*>(p + off);
 }
 
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ void corrupt(u32* status, u64* plan) {
   set_status(status, ROIX_ECORRUPT);
   plan[P_OK] = 0;
@@ -99,6 +103,7 @@ __global__ void k_dec_header(Desc d, const uint8_t* in, u64 size, u32* status, u
 // length, 0 = longer code). Lengths whose Kraft sum exceeds 1 are corrupt.
 struct DecTable {
   u32 first[kLMax + 2], count[kLMax + 2], index0[kLMax + 2];
+  u32 limit[kLMax + 2];  // end of the length-l codes, left-justified to kLMax bits
   uint16_t by_code[kMaxSym];
   u32 lut[1u << kLutBits];
 };
@@ -135,6 +140,9 @@ __global__ void __launch_bounds__(1024) k_dec_table(const uint8_t* in, u32* stat
       tab->first[l] = first[l];
       tab->count[l] = cnt[l];
       tab->index0[l] = idx0[l];
+      // canonical codes: every length-l code, left-justified, lies below every
+      // longer one, so these ends do not decrease with l
+      tab->limit[l] = l ? (first[l] + cnt[l]) << (kLMax - l) : 0u;
     }
   }
   __syncthreads();
@@ -251,33 +259,48 @@ __global__ void __launch_bounds__(kThreads) k_dec_rows(Desc d, const uint8_t* in
   }
 }
 
-// ---------------------------------------------------------------- symbols
-// One thread per chunk: canonical decode through the lookup table (codes of up
-// to 12 bits) or the per-length first-code search. The chunk's aggregate for
-// the segmented sum: (whether it holds a record, the code sum since the last
-// record or since the chunk start); a record's own value is looked up.
-__device__ __forceinline__ bool find_record(const uint8_t* in, const u64* plan, u64 k, u64& key,
-                                            u32& val) {
-  const u64 nout = plan[P_NOUT], ok_ = plan[P_OFF_OUTK], ov = plan[P_OFF_OUTV];
+// ---------------------------------------------------------------- records
+// First record at or after position k (lower bound of the keys).
+__device__ __forceinline__ u64 first_record(const uint8_t* in, const u64* plan, u64 k) {
+  const u64 nout = plan[P_NOUT], ok_ = plan[P_OFF_OUTK];
   u64 lo = 0, hi = nout;
   while (lo < hi) {
     const u64 mid = (lo + hi) >> 1;
-    const u64 kk = rd<u64>(in, ok_ + 8 * mid) & ~(1ull << 63);
-    if (kk < k) lo = mid + 1;
+    if ((rd<u64>(in, ok_ + 8 * mid) & ~(1ull << 63)) < k) lo = mid + 1;
     else hi = mid;
   }
-  if (lo >= nout) return false;
-  key = rd<u64>(in, ok_ + 8 * lo);
-  if ((key & ~(1ull << 63)) != k) return false;
-  val = rd<u32>(in, ov + 4 * lo);
-  return true;
+  return lo;
 }
 
+// The records of one chunk in order: the first one at or after the chunk's
+// first symbol 0 is found once by binary search, each later symbol 0 of the
+// chunk takes the next record (records are sorted by position).
+struct RecordCursor {
+  const uint8_t* in;
+  const u64* plan;
+  u64 idx = ~0ull;
+  __device__ bool next(u64 k, u64& key, u32& val) {
+    if (idx == ~0ull) idx = first_record(in, plan, k);
+    if (idx >= plan[P_NOUT]) return false;
+    key = rd<u64>(in, plan[P_OFF_OUTK] + 8 * idx);
+    if ((key & ~(1ull << 63)) != k) return false;
+    val = rd<u32>(in, plan[P_OFF_OUTV] + 4 * idx);
+    ++idx;
+    return true;
+  }
+};
+
+// ---------------------------------------------------------------- symbols
+// One thread per chunk: canonical decode through the lookup table (codes of up
+// to 12 bits) or the per-length first-code search, the payload read one line
+// ahead into L1. The chunk's aggregate for the segmented sum: (whether it
+// holds a record, the code sum since the last record or since the chunk
+// start); a record's own value comes from the chunk's record cursor.
 __global__ void __launch_bounds__(kThreads) k_dec_symbols(const uint8_t* in, u32* status,
                                                           u64* plan, const DecTable* tab,
                                                           uint16_t* sym, u64* agg) {
   __shared__ u32 lut[1u << kLutBits];
-  __shared__ u32 first[kLMax + 2], count[kLMax + 2], index0[kLMax + 2];
+  __shared__ u32 first[kLMax + 2], count[kLMax + 2], index0[kLMax + 2], limit[kLMax + 2];
   __shared__ uint16_t by_code[kMaxSym];
   if (!plan[P_OK]) return;
   const u64 n = plan[P_N], nch = plan[P_NCH], nw = plan[P_NW];
@@ -289,6 +312,7 @@ __global__ void __launch_bounds__(kThreads) k_dec_symbols(const uint8_t* in, u32
     first[threadIdx.x] = tab->first[threadIdx.x];
     count[threadIdx.x] = tab->count[threadIdx.x];
     index0[threadIdx.x] = tab->index0[threadIdx.x];
+    limit[threadIdx.x] = tab->limit[threadIdx.x];
   }
   __syncthreads();
   u64 zeros = 0;
@@ -312,8 +336,13 @@ __global__ void __launch_bounds__(kThreads) k_dec_symbols(const uint8_t* in, u32
     // every true code fits in 32 bits)
     const bool two = plan[P_ORDER] == 2;
     u64 m11 = 1, m12 = 0, m21 = 0, m22 = 1, o1 = 0, o2 = 0;
+    RecordCursor rc{in, plan};
+    // the payload is read one 128-byte line ahead into L1, so that the bit
+    // buffer's refills do not wait on L2 or HBM
+    for (u64 p = w0; p < umin(w1, w0 + 64); p += 32) prefetch_l1(words + p);
     for (u64 k = k0; k < k1; ++k) {
       while (have <= 32 && wp < w1) {
+        if ((wp & 31) == 0 && wp + 64 < w1) prefetch_l1(words + wp + 64);
         buf |= (u64)words[wp++] << (32 - have);
         have += 32;
       }
@@ -323,36 +352,39 @@ __global__ void __launch_bounds__(kThreads) k_dec_symbols(const uint8_t* in, u32
         l = e & 0xffu;
         s = e >> 8;
       } else {
-        u32 code = 0;
-        bool found = false;
-        for (u32 ll = 1; ll <= kLMax && (int)ll <= have; ++ll) {
-          code = (code << 1) | (u32)((buf >> (64 - ll)) & 1ull);
-          if (count[ll] && code >= first[ll] && code - first[ll] < count[ll]) {
-            s = by_code[index0[ll] + code - first[ll]];
-            l = ll;
-            found = true;
-            break;
-          }
+        // a longer code: its length is the first l whose left-justified end
+        // exceeds the next kLMax bits (binary search over the lengths)
+        const u32 v = (u32)(buf >> (64 - kLMax));
+        u32 lo = 1, hi = kLMax;
+        while (lo < hi) {
+          const u32 mid = (lo + hi) >> 1;
+          if (v < limit[mid]) hi = mid;
+          else lo = mid + 1;
         }
-        if (!found) {
+        if (v >= limit[lo] || (int)lo > have) {  // no code of the table, or past the stream
           bad = true;
           break;
         }
+        l = lo;
+        s = by_code[index0[l] + (v >> (kLMax - l)) - first[l]];
       }
       buf <<= l;
       have -= (int)l;
       sym[k] = (uint16_t)s;
+      u64 key = 0;
+      u32 val = 0;
+      if (!s) {  // the next record of the chunk
+        ++zeros;
+        if (!rc.next(k, key, val)) {
+          bad = true;
+          break;
+        }
+      }
       if (two) {
         // element map: c' = a c1 + b c2 + v, (c1, c2) -> (c', c1); non-record:
-        // (a, b, v) = (2, -1, s - R); record: (0, 0, payload) (set below)
+        // (a, b, v) = (2, -1, s - R); record: (0, 0, payload)
         u64 ea = 2, eb = ~0ull, ev = (u64)((long long)s - (long long)R);
         if (!s) {
-          u64 key;
-          u32 val;
-          if (!find_record(in, plan, k, key, val)) {
-            bad = true;
-            break;
-          }
           ea = 0;
           eb = 0;
           ev = (key >> 63) ? 0ull : (u64)(long long)(int32_t)val;
@@ -368,13 +400,6 @@ __global__ void __launch_bounds__(kThreads) k_dec_symbols(const uint8_t* in, u32
       if (s) {
         acc += (long long)s - (long long)R;
       } else {
-        ++zeros;
-        u64 key;
-        u32 val;
-        if (!find_record(in, plan, k, key, val)) {
-          bad = true;
-          break;
-        }
         reset = true;
         acc = (key >> 63) ? 0 : (long long)(int32_t)val;
       }
@@ -463,45 +488,62 @@ __global__ void __launch_bounds__(1024) k_dec_carry(u32* status, u64* plan, cons
 template <typename TV>
 __global__ void __launch_bounds__(kThreads) k_dec_values(const uint8_t* in, u32* status,
                                                          u64* plan, const uint16_t* sym,
-                                                         const u64* carry, TV* vals) {
+                                                         const u64* agg, const u64* carry,
+                                                         TV* vals) {
   __shared__ u64 sv[kThreads];
   __shared__ u32 sr[kThreads];
-  __shared__ u64 s_run;
+  __shared__ u64 s_run, s_rec;
+  __shared__ u32 s_wz[kThreads / 32];
   if (!plan[P_OK] || plan[P_ORDER] != 1) return;
   const u64 n = plan[P_N], nch = plan[P_NCH];
   const u32 C = (u32)plan[P_C], R = (u32)plan[P_R];
   const float two_eb = __uint_as_float((u32)plan[P_TWO_EB]);
   const long long eb_int = (long long)plan[P_EB_INT], dark = (long long)plan[P_DARK];
+  const u64 ok_ = plan[P_OFF_OUTK], ov = plan[P_OFF_OUTV], nout = plan[P_NOUT];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (u64 j = blockIdx.x; j < nch; j += gridDim.x) {
-    if (threadIdx.x == 0) s_run = carry[j];
-    __syncthreads();
     const u64 k0 = j * C, k1 = min(n, k0 + C);
+    if (threadIdx.x == 0) {
+      s_run = carry[j];
+      // the chunk's first record, found once (the chunk holds one if it reset)
+      s_rec = agg[2 * j] ? first_record(in, plan, k0) : 0ull;
+    }
+    __syncthreads();
     for (u64 b0 = k0; b0 < k1; b0 += kThreads) {
       const u64 k = b0 + threadIdx.x;
       u32 r = 0;
       u64 v = 0;
       u32 rawbits = 0;
       bool raw = false;
-      if (k < k1) {
-        const u32 s = sym[k];
-        if (s) {
-          v = (u64)((long long)s - (long long)R);
+      const u32 s = k < k1 ? sym[k] : 1u;
+      // a symbol 0 takes the record after the zeros before it in the chunk
+      const u32 bz = __ballot_sync(0xffffffffu, s == 0u);
+      if (lane == 0) s_wz[warp] = (u32)__popc(bz);
+      __syncthreads();
+      u64 zb = 0, zt = 0;
+      for (int q = 0; q < kThreads / 32; ++q) {
+        if (q < warp) zb += s_wz[q];
+        zt += s_wz[q];
+      }
+      if (s) {
+        v = (u64)((long long)s - (long long)R);
+      } else {
+        const u64 idx = s_rec + zb + (u64)__popc(bz & ((1u << lane) - 1u));
+        const u64 key = idx < nout ? rd<u64>(in, ok_ + 8 * idx) : ~0ull;
+        if ((key & ~(1ull << 63)) != k) {
+          corrupt(status, plan);
         } else {
-          u64 key;
-          u32 val;
-          if (!find_record(in, plan, k, key, val)) {
-            corrupt(status, plan);
-          } else {
-            r = 1;
-            raw = (key >> 63) != 0;
-            rawbits = val;
-            v = raw ? 0ull : (u64)(long long)(int32_t)val;
-          }
+          const u32 val = rd<u32>(in, ov + 4 * idx);
+          r = 1;
+          raw = (key >> 63) != 0;
+          rawbits = val;
+          v = raw ? 0ull : (u64)(long long)(int32_t)val;
         }
       }
       sr[threadIdx.x] = r;
       sv[threadIdx.x] = v;
       __syncthreads();
+      if (threadIdx.x == 0) s_rec += zt;  // read by every thread before the barrier above
       for (u32 dd = 1; dd < kThreads; dd <<= 1) {
         u32 pr = 0;
         u64 pv = 0;
@@ -615,6 +657,7 @@ __global__ void __launch_bounds__(kThreads) k_dec_values2(const uint8_t* in, u32
        j += (u64)gridDim.x * blockDim.x) {
     u64 c1 = carry[2 * j], c2 = carry[2 * j + 1];
     const u64 k0 = j * C, k1 = min(n, k0 + C);
+    RecordCursor rc{in, plan};
     for (u64 k = k0; k < k1; ++k) {
       const u32 s = sym[k];
       u64 c;
@@ -625,7 +668,7 @@ __global__ void __launch_bounds__(kThreads) k_dec_values2(const uint8_t* in, u32
       } else {
         u64 key;
         u32 val;
-        if (!find_record(in, plan, k, key, val)) {
+        if (!rc.next(k, key, val)) {
           corrupt(status, plan);
           return;
         }
@@ -700,13 +743,13 @@ void launch_decode(const Launch& L, const Desc& d, const uint8_t* in, u64 size, 
     unsigned gv = (unsigned)umin(max_chunks, (u64)L.sms * 8);
     unsigned g2 = (unsigned)umin((max_chunks + kThreads - 1) / kThreads, (u64)L.sms * 8);
     if (d.dtype == ROIX_F32) {
-      k_dec_values<float><<<gv, kThreads, 0, L.stream>>>(in, ws.status, ws.plan, ws.sym, ws.carry,
-                                                          (float*)ws.vals);
+      k_dec_values<float><<<gv, kThreads, 0, L.stream>>>(in, ws.status, ws.plan, ws.sym, ws.agg,
+                                                          ws.carry, (float*)ws.vals);
       k_dec_values2<float><<<g2, kThreads, 0, L.stream>>>(in, ws.status, ws.plan, ws.sym,
                                                            ws.carry, (float*)ws.vals);
     } else {
       k_dec_values<unsigned short><<<gv, kThreads, 0, L.stream>>>(
-          in, ws.status, ws.plan, ws.sym, ws.carry, (unsigned short*)ws.vals);
+          in, ws.status, ws.plan, ws.sym, ws.agg, ws.carry, (unsigned short*)ws.vals);
       k_dec_values2<unsigned short><<<g2, kThreads, 0, L.stream>>>(
           in, ws.status, ws.plan, ws.sym, ws.carry, (unsigned short*)ws.vals);
     }
