@@ -290,7 +290,227 @@ struct RecordCursor {
   }
 };
 
-// ---------------------------------------------------------------- symbols
+// ------------------------------------------------------- codeword reading
+// A reader of a chunk's bit stream from any bit position: an MSB-first 64-bit
+// buffer refilled from the payload words [wp, w1) through L1.
+struct BitReader {
+  const u32* words;
+  u64 wp, w1, buf;
+  int have;
+  __device__ __forceinline__ void refill() {
+    while (have <= 32 && wp < w1) {
+      buf |= (u64)__ldg(words + wp++) << (32 - have);
+      have += 32;
+    }
+  }
+  // positioned at bit `bit` of the stream that starts at word w0
+  __device__ __forceinline__ void init(const u32* w, u64 w0, u64 word1, u64 bit) {
+    words = w;
+    w1 = word1;
+    wp = w0 + (bit >> 5);
+    buf = 0;
+    have = 0;
+    refill();
+    const int skip = (int)(bit & 31);
+    if (have >= skip) {
+      buf <<= skip;
+      have -= skip;
+    } else {
+      have = 0;
+    }
+  }
+};
+
+// Canonical decoding tables in shared memory.
+struct DecShared {
+  const u32* lut;
+  const u32* first;
+  const u32* index0;
+  const u32* limit;
+  const uint16_t* by_code;
+};
+
+// One codeword at the reader's position: its symbol and length, or false when
+// the bits are no code of the table or too few remain. Codes of up to
+// kLutBits bits come from the lookup table; for a longer one its length is
+// the first l whose left-justified end exceeds the next kLMax bits (binary
+// search over the lengths).
+__device__ __forceinline__ bool dec_code(BitReader& br, const DecShared& t, u32& s, u32& l) {
+  br.refill();
+  const u32 e = t.lut[(u32)(br.buf >> (64 - kLutBits))];
+  if (e && (int)(e & 0xffu) <= br.have) {
+    l = e & 0xffu;
+    s = e >> 8;
+  } else {
+    const u32 v = (u32)(br.buf >> (64 - kLMax));
+    u32 lo = 1, hi = kLMax;
+    while (lo < hi) {
+      const u32 mid = (lo + hi) >> 1;
+      if (v < t.limit[mid]) hi = mid;
+      else lo = mid + 1;
+    }
+    if (v >= t.limit[lo] || (int)lo > br.have) return false;
+    l = lo;
+    s = t.by_code[t.index0[l] + (v >> (kLMax - l)) - t.first[l]];
+  }
+  br.buf <<= l;
+  br.have -= (int)l;
+  return true;
+}
+
+// ----------------------------------------------------- symbols, order 1
+// A warp per chunk, with no change to the stream: lane l decodes the codewords
+// that start in the l-th of 32 equal slices of the chunk's bits, from a start
+// that is a guess except for lane 0 (the slice's first bit). A Huffman code
+// resynchronises: a decode begun inside a codeword soon meets the true
+// boundaries. In rounds, each lane restarts from the position where the
+// previous lane's decode left its slice, until no start changes; lane 0 starts
+// at a true boundary, so then every start is one (by induction) and the
+// lanes' codeword counts are exact. A warp scan of the counts places each
+// lane's symbols; a last pass writes them (the first L of the chunk), takes the
+// records of its symbols 0 in order (from the chunk's first record plus the
+// zeros before it) and forms the lane's part of the chunk aggregate, and the
+// parts are combined in lane order.
+__global__ void __launch_bounds__(kThreads) k_dec_symbols_w(const uint8_t* in, u32* status,
+                                                            u64* plan, const DecTable* tab,
+                                                            uint16_t* sym, u64* agg) {
+  __shared__ u32 lut[1u << kLutBits];
+  __shared__ u32 first[kLMax + 2], count[kLMax + 2], index0[kLMax + 2], limit[kLMax + 2];
+  __shared__ uint16_t by_code[kMaxSym];
+  if (!plan[P_OK] || plan[P_ORDER] != 1) return;
+  const u64 n = plan[P_N], nch = plan[P_NCH], nw = plan[P_NW];
+  const u32 C = (u32)plan[P_C], R = (u32)plan[P_R], S = (u32)plan[P_S];
+  const u64 off_ch = plan[P_OFF_CHUNKS], off_pl = plan[P_OFF_PAYLOAD];
+  const u64 nout = plan[P_NOUT], ok_ = plan[P_OFF_OUTK], ov = plan[P_OFF_OUTV];
+  for (u32 i = threadIdx.x; i < (1u << kLutBits); i += blockDim.x) lut[i] = tab->lut[i];
+  for (u32 i = threadIdx.x; i < S; i += blockDim.x) by_code[i] = tab->by_code[i];
+  if (threadIdx.x < kLMax + 2) {
+    first[threadIdx.x] = tab->first[threadIdx.x];
+    count[threadIdx.x] = tab->count[threadIdx.x];
+    index0[threadIdx.x] = tab->index0[threadIdx.x];
+    limit[threadIdx.x] = tab->limit[threadIdx.x];
+  }
+  __syncthreads();
+  const DecShared t{lut, first, index0, limit, by_code};
+  const int lane = threadIdx.x & 31;
+  const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
+  const u32* words = reinterpret_cast<const u32*>(in + off_pl);
+  u64 zeros = 0;
+  for (u64 j = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < nch; j += nwarps) {
+    const u64 w0 = rd<u64>(in, off_ch + 8 * j);
+    const u64 w1 = j + 1 < nch ? rd<u64>(in, off_ch + 8 * (j + 1)) : nw;
+    if (w0 > w1 || w1 > nw) {
+      if (lane == 0) corrupt(status, plan);
+      break;
+    }
+    const u64 k0 = j * C;
+    const u32 L = (u32)umin((u64)C, n - k0);
+    const u64 bmax = 32 * (w1 - w0);
+    const u64 g = (bmax + 31) / 32;
+    const u64 seg_lo = umin((u64)lane * g, bmax), seg_hi = umin(seg_lo + g, bmax);
+    // codewords starting in [st, seg_hi): their number, their symbols 0, the end
+    auto scan = [&](u64 st, u32& cnt, u32& zc, u64& end) {
+      cnt = 0;
+      zc = 0;
+      u64 pos = st;
+      if (pos < seg_hi) {
+        BitReader br;
+        br.init(words, w0, w1, pos);
+        while (pos < seg_hi) {
+          u32 sv, l;
+          if (!dec_code(br, t, sv, l)) {  // a guessed start inside no codeword: slide a bit
+            ++pos;
+            br.init(words, w0, w1, pos);
+            continue;
+          }
+          ++cnt;
+          zc += sv == 0 ? 1u : 0u;
+          pos += l;
+        }
+      }
+      end = pos;
+    };
+    u64 start = lane == 0 ? 0 : seg_lo;
+    u32 cnt, zc;
+    u64 end;
+    scan(start, cnt, zc, end);
+    for (int round = 0; round < 32; ++round) {
+      u64 ns = __shfl_up_sync(0xffffffffu, end, 1);
+      if (lane == 0) ns = 0;
+      const bool changed = ns != start;
+      if (!__ballot_sync(0xffffffffu, changed)) break;
+      if (changed) {
+        start = ns;
+        scan(start, cnt, zc, end);
+      }
+    }
+    const u32 ci = warp_incl_scan(cnt), zi = warp_incl_scan(zc);
+    const u32 base = ci - cnt, zbase = zi - zc;
+    const u32 total = __shfl_sync(0xffffffffu, ci, 31);
+    const bool any_zero = __ballot_sync(0xffffffffu, zc != 0u) != 0u;
+    u64 rec0 = 0;
+    if (any_zero) {  // the chunk's first record (lane 0 searches, the warp shares it)
+      if (lane == 0) rec0 = first_record(in, plan, k0);
+      rec0 = __shfl_sync(0xffffffffu, rec0, 0);
+    }
+    bool bad = total < L;
+    bool reset = false;
+    long long acc = 0;
+    if (!bad && base < L) {
+      const u32 todo = min(cnt, L - base);
+      BitReader br;
+      br.init(words, w0, w1, start);
+      u64 ridx = rec0 + zbase;
+      for (u32 i = 0; i < todo; ++i) {
+        u32 sv, l;
+        if (!dec_code(br, t, sv, l)) {
+          bad = true;
+          break;
+        }
+        const u64 k = k0 + base + i;
+        sym[k] = (uint16_t)sv;
+        if (sv) {
+          acc += (long long)sv - (long long)R;
+        } else {
+          ++zeros;
+          const u64 key = ridx < nout ? rd<u64>(in, ok_ + 8 * ridx) : ~0ull;
+          if ((key & ~(1ull << 63)) != k) {
+            bad = true;
+            break;
+          }
+          const u32 val = rd<u32>(in, ov + 4 * ridx);
+          ++ridx;
+          reset = true;
+          acc = (key >> 63) ? 0 : (long long)(int32_t)val;
+        }
+      }
+    }
+    if (__ballot_sync(0xffffffffu, bad)) {
+      if (lane == 0) corrupt(status, plan);
+      break;
+    }
+    // the lanes' parts in order: (r1, v1) then (r2, v2) -> (r1 | r2, r2 ? v2 : v1 + v2)
+    u32 r = reset ? 1u : 0u;
+    u64 v = (u64)acc;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const u32 r2 = __shfl_down_sync(0xffffffffu, r, d);
+      const u64 v2 = __shfl_down_sync(0xffffffffu, v, d);
+      if (lane + d < 32) {
+        v = r2 ? v2 : v + v2;
+        r |= r2;
+      }
+    }
+    if (lane == 0) {
+      agg[2 * j] = r;
+      agg[2 * j + 1] = v;
+    }
+  }
+  zeros = warp_sum(zeros);
+  if (lane == 0 && zeros) atomicAdd((unsigned long long*)&plan[P_ZEROS], zeros);
+}
+
+// ------------------------------------------------------ symbols, order 2
 // One thread per chunk: canonical decode through the lookup table (codes of up
 // to 12 bits) or the per-length first-code search, the payload read one line
 // ahead into L1. The chunk's aggregate for the segmented sum: (whether it
@@ -302,7 +522,7 @@ __global__ void __launch_bounds__(kThreads) k_dec_symbols(const uint8_t* in, u32
   __shared__ u32 lut[1u << kLutBits];
   __shared__ u32 first[kLMax + 2], count[kLMax + 2], index0[kLMax + 2], limit[kLMax + 2];
   __shared__ uint16_t by_code[kMaxSym];
-  if (!plan[P_OK]) return;
+  if (!plan[P_OK] || plan[P_ORDER] == 1) return;  // order 1: k_dec_symbols_w
   const u64 n = plan[P_N], nch = plan[P_NCH], nw = plan[P_NW];
   const u32 C = (u32)plan[P_C], R = (u32)plan[P_R], S = (u32)plan[P_S];
   const u64 off_ch = plan[P_OFF_CHUNKS], off_pl = plan[P_OFF_PAYLOAD];
@@ -738,6 +958,12 @@ void launch_decode(const Launch& L, const Desc& d, const uint8_t* in, u64 size, 
   if (max_chunks) {
     unsigned g = (unsigned)umin((max_chunks + kThreads - 1) / kThreads, (u64)L.sms * 4);
     k_dec_symbols<<<g, kThreads, 0, L.stream>>>(in, ws.status, ws.plan, tab, ws.sym, ws.agg);
+    {  // order 1: a warp per chunk
+      const u64 wpb = kThreads / 32;
+      const unsigned gw = (unsigned)umin((max_chunks + wpb - 1) / wpb, (u64)L.sms * 8);
+      k_dec_symbols_w<<<gw, kThreads, 0, L.stream>>>(in, ws.status, ws.plan, tab, ws.sym,
+                                                      ws.agg);
+    }
     k_dec_carry<<<1, 1024, 0, L.stream>>>(ws.status, ws.plan, ws.agg, ws.carry);
     k_dec_carry2<<<1, 1024, 0, L.stream>>>(ws.status, ws.plan, ws.agg, ws.carry);
     unsigned gv = (unsigned)umin(max_chunks, (u64)L.sms * 8);
