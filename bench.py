@@ -37,11 +37,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "GB/s in (quantize+ROI+encode) vs HBM peak, batched/served vs plain; p50/p99 latency"
 # kernels of one fused group: reset, binarisation (one launch per form: row or
-# flat), compaction count, compaction write, symbols, codebook, pack count,
-# pack, finalise; plus a tile-scan launch for the compaction when some item has
-# more tiles than the counting kernel scans itself (IN_SCAN_MAX), and a chunk
-# scan and a records launch when some item has more pack chunks than that
-LAUNCHES_PER_GROUP = 8
+# flat), compaction count, compaction write, symbols, codebook, pack,
+# finalise; plus a tile-scan launch for the compaction when some item has more
+# tiles than the counting kernel scans itself (IN_SCAN_MAX)
+LAUNCHES_PER_GROUP = 7
 IN_SCAN_MAX = 1024
 
 
@@ -49,13 +48,11 @@ def group_launches(xs, cfg=None, tuning=None) -> int:
     """Kernel launches of one fused group of items (the library's rules: the
     flat binarisation form when a 16-byte aligned volume has nx >= 256 and its
     rows are not aligned or do not fill 1024-voxel segments; a tile scan
-    launch only for items with more than IN_SCAN_MAX compaction tiles or pack
-    chunks)."""
+    launch only for items with more than IN_SCAN_MAX compaction tiles)."""
     cfg = cfg or {}
     tuning = tuning or {}
     fw = tuning.get("front_words", 2048) or 2048
-    C = cfg.get("chunk", 4096)
-    flat = row = scan0 = scan1 = False
+    flat = row = scan0 = False
     for x in xs:
         nx = x.shape[-1]
         ptr = x.data_ptr()
@@ -68,8 +65,7 @@ def group_launches(xs, cfg=None, tuning=None) -> int:
         W = (nx + 31) // 32
         rpt = max(1, min(256, fw // W, rows))
         scan0 |= -(-rows // rpt) > IN_SCAN_MAX
-        scan1 |= -(-x.numel() // C) > IN_SCAN_MAX
-    return LAUNCHES_PER_GROUP + int(flat) + int(row) + int(scan0) + 2 * int(scan1)
+    return LAUNCHES_PER_GROUP + int(flat) + int(row) + int(scan0)
 
 # DRAM bytes per step of each stage (dram__bytes_read.sum + dram__bytes_write.sum,
 # summed over the stage's kernels, one launch each) from an ncu capture of the
@@ -158,8 +154,58 @@ def make_inputs(workload: str, device, seed: int = 0):
     raise ValueError(workload)
 
 
+class _Nvml:
+    """Read-only NVML queries through ctypes (SM clock, its maximum, power,
+    clock event reasons); None when the library is not there."""
+
+    SW_POWER_CAP, HW_SLOWDOWN, SW_THERMAL, HW_THERMAL = 0x4, 0x8, 0x20, 0x40
+
+    def __init__(self, index: int):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.dev = ctypes.c_void_p()
+        bus = self._bus_id(index)  # the CUDA device's PCI address (NVML indices may differ)
+        if bus is not None:
+            rc = self.lib.nvmlDeviceGetHandleByPciBusId_v2(bus, ctypes.byref(self.dev))
+        else:
+            rc = self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(self.dev))
+        if rc != 0:
+            raise OSError("no NVML device for CUDA device %d" % index)
+        self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    @staticmethod
+    def _bus_id(index: int):
+        try:
+            import torch
+            p = torch.cuda.get_device_properties(index)
+            return b"%08x:%02x:%02x.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+        except Exception:
+            return None
+
+    def max_sm(self):
+        mx = self.ct.c_uint()
+        self.lib.nvmlDeviceGetMaxClockInfo(self.dev, 1, self.ct.byref(mx))
+        return mx.value
+
+    def sample(self):
+        """(SM MHz, clock event reason bits), two driver queries."""
+        ct = self.ct
+        sm, rs = ct.c_uint(), ct.c_ulonglong()
+        if self.lib.nvmlDeviceGetClockInfo(self.dev, 1, ct.byref(sm)) != 0:
+            return None
+        self.reasons_fn(self.dev, ct.byref(rs))
+        return sm.value, rs.value
+
+
 class Clocks:
-    """nvidia-smi samples (200 ms) while the timed region runs."""
+    """SM clock and clock event reasons sampled while the timed region runs:
+    NVML about every millisecond from a thread (short regions get samples
+    too; the first sample is taken before the region starts timing), else
+    nvidia-smi every 200 ms."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -168,9 +214,23 @@ class Clocks:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
+        self.nvml = None
         self.lines = []
+        self.samples = []
+        self.stop = threading.Event()
 
     def __enter__(self):
+        try:
+            self.nvml = _Nvml(self.index)
+        except (OSError, AttributeError):
+            self.nvml = None
+        if self.nvml is not None:
+            self.mx = self.nvml.max_sm()
+            self.ready = threading.Event()
+            self.t = threading.Thread(target=self._poll, daemon=True)
+            self.t.start()
+            self.ready.wait(1.0)
+            return self
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
@@ -182,11 +242,26 @@ class Clocks:
             self.proc = None
         return self
 
+    def _poll(self):
+        first = True
+        while True:
+            v = self.nvml.sample()
+            if first:  # the caller starts timing after this one
+                first = False
+                self.ready.set()
+            elif v is not None:
+                self.samples.append(v)
+            if self.stop.wait(0.0005):
+                return
+
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
     def __exit__(self, *a):
+        if self.nvml is not None:
+            self.stop.set()
+            self.t.join(timeout=5)
         if self.proc:
             self.proc.terminate()
             try:
@@ -196,21 +271,33 @@ class Clocks:
 
     def summary(self):
         sm, mx, reasons = [], 0.0, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            f = [v.strip() for v in ln.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                mx = max(mx, float(f[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
+        if self.nvml is not None:
+            bits = [("sw_power_cap", _Nvml.SW_POWER_CAP), ("hw_slowdown", _Nvml.HW_SLOWDOWN),
+                    ("sw_thermal_slowdown", _Nvml.SW_THERMAL),
+                    ("hw_thermal_slowdown", _Nvml.HW_THERMAL)]
+            mx = float(self.mx)
+            for c, r in self.samples:
+                sm.append(float(c))
+                reasons.update(nm for nm, b in bits if r & b)
+            src = "nvml"
+        else:
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for ln in self.lines:
+                f = [v.strip() for v in ln.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx = max(mx, float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+            src = "nvidia-smi"
         return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": mx or None, "reasons": sorted(reasons), "samples": len(sm)}
+                "sm_max_mhz": mx or None, "reasons": sorted(reasons), "samples": len(sm),
+                "source": src}
 
 
 def stage_bytes(xs, outs, sizes, cfg):
@@ -1509,9 +1596,8 @@ def run_slabs(args, rank, world, local_rank):
                               for k, v in zip(names, stage_ms) if v > 0}}
     # reset and one binarisation of the whole volume, then per group of up to 64
     # slabs: compaction count, its tile scan (slabs have more than IN_SCAN_MAX
-    # tiles), write, symbols, codebook, pack count, its chunk scan, records,
-    # pack, finalise
-    per_call = 2 + 10 * ((ns + 63) // 64)
+    # tiles), write, symbols, codebook, pack, finalise
+    per_call = 2 + 7 * ((ns + 63) // 64)
     launches = per_call * len(cfgs) * args.steps
     result = None
     if rank == 0:

@@ -281,8 +281,8 @@ __device__ __forceinline__ void flush_hist(u32* h, unsigned long long* g, u32 S,
 // barrier anywhere in the loop) and goes to the item's global histogram when
 // the warp moves to another item. Symbol-0 positions (records) are only
 // counted here, per pack chunk (an atomic per lane and step that has one);
-// they are written by k_pack_count once the codebook kernel has turned the
-// counts into offsets, so that no segment waits for another.
+// they are written by k_pack once the codebook kernel has turned the counts
+// into offsets, so that no segment waits for another.
 template <typename TV, bool FROM_Q, int ORDER>
 __global__ void __launch_bounds__(kThreads) k_symbols(const __grid_constant__ Batch B) {
   if (halted(B.status)) return;  // a tile scan of this call gave up
@@ -825,7 +825,9 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__
         s_carry[tid] = acc;
       }
       __syncthreads();
-      if (s < S) codes_ws[s] = l ? (l << 24) | (s_next[l] + wcnt[warp][l] + below) : 0u;
+      // the pack kernel's entry: the code left-justified in 32 bits, its
+      // length in the low byte (lengths are at most 24, so the two never meet)
+      if (s < S) codes_ws[s] = l ? ((s_next[l] + wcnt[warp][l] + below) << (32u - l)) | l : 0u;
       __syncthreads();
     }
   }
@@ -834,9 +836,9 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__
     lens_ws[s] = len[s];
     if (kHeaderBytes + s < cap) out[kHeaderBytes + s] = len[s];
   }
-  // the records of an item with at most kInScanMax chunks: per-chunk counts
-  // (from the symbol kernel) into offsets (larger items: k_scan_pairs<1>)
-  if (I.pscan) {
+  // the item's records: per-chunk counts (from the symbol kernel) into
+  // offsets, and their total
+  {
     __shared__ u64 scratch64[40];
     const u64 n = umin(I.sizes[0], I.N);
     const u64 nch = (n + B.c.C - 1) / B.c.C;
@@ -850,208 +852,101 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__
 }
 
 // ------------------------------------------------------------------- pack
-// Passes none of whose blocks waits on another: k_pack_count sums the code
-// lengths of every chunk; the chunks' word and record counts become offsets
-// (for items with at most kInScanMax chunks in the codebook kernel and in
-// k_pack_count, which then also writes their records; for larger items in
-// k_scan_pairs<1>, followed by k_records), and k_pack writes every chunk's
-// words at its offset (chunks from global tickets in order).
+// One pass over the symbols, chunks from global tickets in order (every
+// item's chunks in order). A block forms its chunk's codes and bit offsets,
+// publishes the chunk's payload word count to a decoupled look-back over the
+// item's chunks, assembles the words in shared memory meanwhile, then takes
+// the chunk's first word from the look-back and stores the words and the
+// chunk table entry; the chunk's records go to the offsets the codebook
+// kernel scanned. A ticket is held only by a running block, which publishes
+// its count before it waits, so every wait ends; it is bounded all the same
+// (ROIX_ETIMEOUT).
 
-// Warps, one chunk at a time: lane l holds symbols [8 l, 8 l + 8) of each
-// round of 256 (coalesced 16-byte loads); the code lengths come from the
-// item's byte table (2R bytes, read through L1). For an item with at most
-// kInScanMax chunks the warp also writes the chunk's records, if it holds
-// any: the symbol-0 positions in order, from the
-// record bitmap the symbol kernel wrote (lane l with words l, l + 32, ...; a
-// warp scan of their popcounts), each as (k | kind << 63, payload) at the
-// chunk's record offset (scanned by the codebook kernel); the code or the raw
-// value is formed again from the pixel section (or the staged codes). For an
-// item with at most kInScanMax chunks, the warp that counts the item's last
-// chunk scans the chunks' word counts into their offsets.
+// The records of chunk t: its symbol-0 positions in order, from the record
+// bitmap the symbol kernel wrote (thread i with a contiguous share of the
+// chunk's bitmap words, a block scan of their popcounts), each written as
+// (k | kind << 63, payload) from offset rec0 on; the code or the raw value is
+// formed again from the pixel section (or the staged codes). Called by the
+// whole block.
 template <typename TV, bool FROM_Q>
-__global__ void __launch_bounds__(kThreads) k_pack_count(const __grid_constant__ Batch B) {
-  if (halted(B.status)) return;  // a tile scan of this call gave up
-  __shared__ u64 pre[kMaxBatch + 1];
-  __shared__ u64 nn[kMaxBatch];
+__device__ void pack_records(const Batch& B, const Item& I, const ItemEb& eb, u64 t, u64 n,
+                             u64 rec0, u32* scratch) {
   const u32 C = B.c.C;
-  const int lane = threadIdx.x & 31;
-  tile_prefix(B, pre, C, 1, nn);
-  const u64 total = pre[B.n];
-  const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
-  constexpr u32 kIn = 4;  // vector loads of a lane in flight at once
-  u32 cur = 0xffffffffu;  // item whose records source is set
+  const u64 w0 = t * (C / 32);
+  const u32 nw = (u32)((umin(n, (t + 1) * (u64)C) - t * (u64)C + 31) / 32);
+  const u32 per = (nw + blockDim.x - 1) / blockDim.x;
+  const u32 j0 = min(nw, threadIdx.x * per), j1 = min(nw, j0 + per);
+  const u32* __restrict__ rbits = I.rbits;
+  u32 cnt = 0;
+  for (u32 j = j0; j < j1; ++j) cnt += __popc(__ldg(rbits + w0 + j));
+  u32 tot;
+  u64 o = rec0 + block_excl_scan<u32>(cnt, scratch, &tot);
+  if (cnt == 0) return;
   Src<TV, FROM_Q> src{};
-  for (u64 gt = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5; gt < total; gt += nwarps) {
-    const u32 item = find_item(pre, B.n, gt);
-    const Item& I = B.it[item];
-    const u64 n = nn[item];
-    const uint16_t* __restrict__ sym = I.sym;
-    const uint8_t* __restrict__ len = I.lens;  // 2R bytes: stays in L1
-    const u64 t = gt - pre[item];
-    const u64 c0 = t * C + (u64)lane * 8;
-    const u32 steps = C / 256;  // 8 symbols per lane and step
-    u32 bits = 0;
-    if (t * C + C <= n) {  // a full chunk: no bounds tests
-      for (u32 r0 = 0; r0 < steps; r0 += kIn) {
-        uint4 v[kIn];
-#pragma unroll
-        for (u32 q = 0; q < kIn; ++q)
-          if (r0 + q < steps)
-            v[q] = __ldg(reinterpret_cast<const uint4*>(sym + c0 + (u64)(r0 + q) * 256));
-#pragma unroll
-        for (u32 q = 0; q < kIn; ++q)
-          if (r0 + q < steps)
-            bits += __ldg(len + (v[q].x & 0xffffu)) + __ldg(len + (v[q].x >> 16)) +
-                    __ldg(len + (v[q].y & 0xffffu)) + __ldg(len + (v[q].y >> 16)) +
-                    __ldg(len + (v[q].z & 0xffffu)) + __ldg(len + (v[q].z >> 16)) +
-                    __ldg(len + (v[q].w & 0xffffu)) + __ldg(len + (v[q].w >> 16));
-      }
-    } else {
-      for (u32 r = 0; r < steps; ++r) {
-        const u64 k = c0 + (u64)r * 256;
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-          if (k + q < n) bits += __ldg(len + __ldg(sym + k + q));
-      }
-    }
-    bits = __reduce_add_sync(0xffffffffu, bits);
-    if (lane == 0) I.cw[t] = (bits + 31) >> 5;
-    if (I.pscan && I.crec[t] != 0u) {  // the chunk's records (a small item's)
-      if (item != cur) {
-        cur = item;
-        const Desc d = desc_of(B, I);
-        src.P = (const TV*)I.P;
-        src.q = I.q;
-        src.obits = I.obits;
-        src.dark = d.dark;
-        if constexpr (!FROM_Q) {
-          src.e = make_eb(d, I.rst->vmin_key, I.rst->vmax_key);
-          src.fd = FastDiv(2u * (u32)src.e.eb_int);
-        }
-      }
-      const u32* __restrict__ rbits = I.rbits;
-      u64 idx = I.crecoff[t];
-      const u64 w0 = t * (C / 32), nwords = (umin(n, (t + 1) * (u64)C) - t * C + 31) / 32;
-      for (u64 j0 = 0; j0 < nwords; j0 += 32) {
-        const u64 j = j0 + lane;
-        u32 zm = j < nwords ? __ldg(rbits + w0 + j) : 0u;
-        const u32 cnt = __popc(zm);
-        const u32 inc = warp_incl_scan(cnt);
-        u64 o = idx + inc - cnt;
-        while (zm) {
-          const int q = __ffs(zm) - 1;
-          zm &= zm - 1;
-          const u64 k = (w0 + j) * 32 + q;
-          bool out;
-          const int c = src.code(k, out);
-          if (o < I.rec_cap) {
-            I.rk[o] = k | (out ? (1ull << 63) : 0ull);
-            I.rv[o] = out ? src.raw_bits(k) : (u32)c;
-          }
-          ++o;
-        }
-        idx += __shfl_sync(0xffffffffu, inc, 31);
-      }
-    }
-    const u64 nch = pre[item + 1] - pre[item];
-    if (I.pscan && count_done(&I.st->done_pack, nch)) {  // the item's chunk offsets
-      u64 tw, tr;
-      warp_scan2(I.cw, nullptr, nch, I.cwoff, nullptr, tw, tr);
-      if (lane == 0) I.st->nwords = tw;
-    }
+  src.P = (const TV*)I.P;
+  src.q = I.q;
+  src.obits = I.obits;
+  src.dark = B.c.dark;
+  if constexpr (!FROM_Q) {
+    src.e = eb.e;
+    src.fd = eb.fd;
   }
-}
-
-// Warps, one chunk at a time, only chunks that hold records of items with
-// more than kInScanMax chunks (k_pack_count writes those of the others): the
-// symbol-0 positions of the chunk in order, from the record bitmap the symbol
-// kernel wrote (lane l with words l, l + 32, ...; a warp scan of their
-// popcounts), each written as (k | kind << 63, payload) at the chunk's record
-// offset (from k_scan_pairs<1>); the code or the raw value is formed again from
-// the pixel section (or the staged codes).
-template <typename TV, bool FROM_Q>
-__global__ void __launch_bounds__(kThreads) k_records(const __grid_constant__ Batch B) {
-  if (halted(B.status)) return;  // a tile scan of this call gave up
-  __shared__ u64 pre[kMaxBatch + 1];
-  const u32 C = B.c.C;
-  const int lane = threadIdx.x & 31;
-  tile_prefix(B, pre, C, 1);
-  const u64 total = pre[B.n];
-  const u64 warp0 = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
-  u32 cur = 0xffffffffu;
-  Src<TV, FROM_Q> src{};
-  u64 n = 0;
-  for (u64 gt = warp0; gt < total; gt += nwarps) {
-    const u32 item = find_item(pre, B.n, gt);
-    const Item& I = B.it[item];
-    const u64 t = gt - pre[item];
-    if (I.pscan || I.crec[t] == 0u) continue;
-    if (item != cur) {  // the item's error-bound constants, formed only for chunks with records
-      cur = item;
-      const Desc d = desc_of(B, I);
-      src.P = (const TV*)I.P;
-      src.q = I.q;
-      src.obits = I.obits;
-      src.dark = d.dark;
-      if constexpr (!FROM_Q) {
-        src.e = make_eb(d, I.rst->vmin_key, I.rst->vmax_key);
-        src.fd = FastDiv(2u * (u32)src.e.eb_int);
+  for (u32 j = j0; j < j1; ++j) {
+    u32 zm = __ldg(rbits + w0 + j);
+    while (zm) {
+      const int q = __ffs(zm) - 1;
+      zm &= zm - 1;
+      const u64 k = (w0 + j) * 32 + q;
+      bool out;
+      const int c = src.code(k, out);
+      if (o < I.rec_cap) {
+        I.rk[o] = k | (out ? (1ull << 63) : 0ull);
+        I.rv[o] = out ? src.raw_bits(k) : (u32)c;
       }
-      n = umin(I.sizes[0], I.N);
-    }
-    const u32* __restrict__ rbits = I.rbits;
-    u64 idx = I.crecoff[t];
-    const u64 w0 = t * (C / 32), nwords = (umin(n, (t + 1) * (u64)C) - t * C + 31) / 32;
-    for (u64 j0 = 0; j0 < nwords; j0 += 32) {
-      const u64 j = j0 + lane;
-      u32 zm = j < nwords ? __ldg(rbits + w0 + j) : 0u;
-      const u32 cnt = __popc(zm);
-      const u32 inc = warp_incl_scan(cnt);
-      u64 o = idx + inc - cnt;
-      while (zm) {
-        const int q = __ffs(zm) - 1;
-        zm &= zm - 1;
-        const u64 k = (w0 + j) * 32 + q;
-        bool out;
-        const int c = src.code(k, out);
-        if (o < I.rec_cap) {
-          I.rk[o] = k | (out ? (1ull << 63) : 0ull);
-          I.rv[o] = out ? src.raw_bits(k) : (u32)c;
-        }
-        ++o;
-      }
-      idx += __shfl_sync(0xffffffffu, inc, 31);
+      ++o;
     }
   }
 }
 
 // Persistent blocks, one chunk of C symbols at a time: thread i loads its
-// EPT = C / 256 consecutive symbols (16-byte loads) and keeps their length <<
-// 24 | code entries (from the item's code table in shared memory) in
-// registers; a block scan of the per-thread bit counts gives each thread its
-// bit offset; each thread assembles its words of the chunk's stream (MSB
-// first) in a shared buffer, OR-ing only the words it shares with its
-// neighbours; the words are stored with coalesced stores at the chunk's
-// offset.
+// EPT = C / 256 consecutive symbols (16-byte loads) and keeps their table
+// entries (code left-justified, length in the low byte; the item's table in
+// shared memory) in registers; a block scan of the per-thread bit counts
+// gives each thread its bit offset; each thread ORs its codes into the
+// chunk's words (MSB first) in a shared buffer: the word being filled stays
+// in a register, a code is placed by one shift (and the part that runs past
+// the word by one funnel shift), and a full word leaves by one shared OR (so
+// the words shared with the neighbouring threads need no other care); warp 0
+// waits for the chunk's word offset; the words are stored with coalesced
+// stores at that offset.
 template <int EPT>
-__global__ void __launch_bounds__(kThreads) k_pack(const __grid_constant__ Batch B) {
+__global__ void __launch_bounds__(kThreads, EPT <= 16 ? 5 : 1) k_pack(const __grid_constant__ Batch B) {
   if (halted(B.status)) return;  // a tile scan of this call gave up
   extern __shared__ unsigned long long wb[];  // [C * kLMax / 64 + 2]
   __shared__ u32 tab[kMaxSym];
   __shared__ u32 scratch[40];
   __shared__ u64 s_tile;
   __shared__ u64 pre[kMaxBatch + 1];
+  __shared__ u64 nval[kMaxBatch], pay0s[kMaxBatch], tab0s[kMaxBatch];
+  __shared__ u64 s_w0;     // the chunk's first payload word (from the look-back)
+  __shared__ ItemEb s_eb;  // error-bound constants of the item whose records are written
+  __shared__ u32 s_ebi;
   const u32 C = B.c.C, S = B.c.S;
   const int tid = threadIdx.x;
-  tile_prefix(B, pre, C, 1);
+  tile_prefix(B, pre, C, 1, nval);
+  // per item: byte offsets of the payload and of the chunk table
+  for (u32 i = tid; i < B.n; i += blockDim.x) {
+    const Item& I = B.it[i];
+    const Layout Lo = make_layout(S, I.rows, I.sizes[1], I.st->nout, (nval[i] + C - 1) / C, 0);
+    pay0s[i] = Lo.off_payload;
+    tab0s[i] = Lo.off_chunks;
+  }
   const u64 total = pre[B.n];
   const u32 wb_words = C * kLMax / 64 + 2;
   for (u32 i = tid; i < wb_words; i += blockDim.x) wb[i] = 0ull;
+  if (tid == 0) s_ebi = 0xffffffffu;
   u32 cur = 0xffffffffu;
-  u64 n = 0, cap = 0, pay0 = 0, tab0 = 0;
-  const uint16_t* __restrict__ sym = nullptr;
-  uint8_t* out = nullptr;
+  constexpr int NV = EPT % 8 == 0 ? EPT / 8 : 1;  // 16-byte loads per thread
   while (true) {
     if (tid == 0) s_tile = atomicAdd(&B.ctr[3], 1u);
     __syncthreads();
@@ -1059,90 +954,117 @@ __global__ void __launch_bounds__(kThreads) k_pack(const __grid_constant__ Batch
     if (gt >= total) break;
     const u32 item = find_item(pre, B.n, gt);
     const Item& I = B.it[item];
+    const u64 n = nval[item];
+    const uint16_t* __restrict__ sym = I.sym;
+    const u32 t = (u32)(gt - pre[item]);  // chunk of the item (n < 2^32 C)
+    const u64 k0 = (u64)t * C + (u64)tid * EPT;
+    // the chunk's symbols and word offset are requested before the item's
+    // code table is (re)loaded, so that the two latencies overlap
+    const bool whole = EPT % 8 == 0 && k0 + EPT <= n;
+    uint4 raw[NV];
+    if (whole) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) raw[v] = __ldg(reinterpret_cast<const uint4*>(sym + k0 + 8 * v));
+    }
+    const u32 nrec = __ldg(I.crec + t);
     if (item != cur) {  // the item's code table into shared memory
       cur = item;
       for (u32 i = tid; i < S; i += blockDim.x) tab[i] = __ldg(I.codes + i);
-      n = umin(I.sizes[0], I.N);
-      const u64 nchunks = (n + C - 1) / C;
-      const Layout Lo = make_layout(S, I.rows, I.sizes[1], I.st->nout, nchunks, 0);
-      pay0 = Lo.off_payload;
-      tab0 = Lo.off_chunks;
-      sym = I.sym;
-      out = I.out;
-      cap = I.cap;
       __syncthreads();
     }
-    const u64 t = gt - pre[item];
-    const u64 k0 = t * C + (u64)tid * EPT;
     u32 e[EPT];
     u32 bits = 0;
-    if constexpr (EPT % 8 == 0) {
-      if (k0 + EPT <= n) {
+    if (whole) {
 #pragma unroll
-        for (int j = 0; j < EPT; j += 8) {
-          const uint4 v = __ldg(reinterpret_cast<const uint4*>(sym + k0 + j));
-          const u32 w4[4] = {v.x, v.y, v.z, v.w};
+      for (int v = 0; v < NV; ++v) {
+        const u32 w4[4] = {raw[v].x, raw[v].y, raw[v].z, raw[v].w};
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            e[j + 2 * q] = tab[w4[q] & 0xffffu];
-            e[j + 2 * q + 1] = tab[w4[q] >> 16];
-          }
+        for (int q = 0; q < 4; ++q) {
+          e[8 * v + 2 * q] = tab[w4[q] & 0xffffu];
+          e[8 * v + 2 * q + 1] = tab[w4[q] >> 16];
         }
-      } else {
-#pragma unroll
-        for (int j = 0; j < EPT; ++j) e[j] = k0 + j < n ? tab[__ldg(sym + k0 + j)] : 0u;
       }
     } else {
 #pragma unroll
       for (int j = 0; j < EPT; ++j) e[j] = k0 + j < n ? tab[__ldg(sym + k0 + j)] : 0u;
     }
 #pragma unroll
-    for (int j = 0; j < EPT; ++j) bits += e[j] >> 24;
+    for (int j = 0; j < EPT; ++j) bits += e[j] & 0xffu;
     u32 cbits;
     const u32 off = block_excl_scan<u32>(bits, scratch, &cbits);
     const u32 words = (cbits + 31) >> 5;
+    const bool hold = B.c.hold_scans && item == 0;  // test hook: chunk 0 never publishes
+    if (tid == 0) {
+      const u64 mine[1] = {words};
+      lookback_publish<1>(I.lbp, t, mine, hold);
+    }
     // the thread's codes are contiguous in the chunk's stream [off, off +
-    // bits): they are shifted MSB first through a 64-bit register; words that
-    // lie wholly in the thread's range are stored, the first and last (which
-    // may be shared with the neighbouring threads) are OR-ed
+    // bits): `acc` holds word w's bits from position `fill` on (MSB first)
     if (bits) {
       u32* wb32 = reinterpret_cast<u32*>(wb);
-      u32 w = off >> 5;
-      const u32 pos = off & 31;
-      u64 acc = 0;
-      u32 nacc = pos;  // the leading pos bits of word w belong to earlier threads
-      bool shared_first = pos != 0;
+      u32 w = off >> 5, fill = off & 31u, acc = 0u;
 #pragma unroll
       for (int j = 0; j < EPT; ++j) {
-        const u32 l = e[j] >> 24;
-        acc = (acc << l) | (e[j] & 0xffffffu);
-        nacc += l;
-        if (nacc >= 32) {
-          const u32 word = (u32)(acc >> (nacc - 32));
-          if (shared_first) atomicOr(&wb32[w], word);
-          else wb32[w] = word;
-          shared_first = false;
+        const u32 l = e[j] & 0xffu;
+        const u32 cj = e[j] & 0xffffff00u;  // the code's bits, from bit 31 down
+        acc |= cj >> fill;
+        const u32 nf = fill + l;
+        if (nf >= 32u) {  // word w is full (fill >= 8 here: l <= 24)
+          atomicOr(&wb32[w], acc);
           ++w;
-          nacc -= 32;
-          acc &= (1ull << nacc) - 1ull;
+          acc = __funnelshift_r(0u, cj, fill);  // the code's bits past word w
         }
+        fill = nf & 31u;
       }
-      if (nacc > (shared_first ? pos : 0u)) atomicOr(&wb32[w], (u32)(acc << (32 - nacc)));
+      if (fill) atomicOr(&wb32[w], acc);
+    }
+    if (tid < 32) {  // the chunk's first word: the words of the item's chunks before it
+      const u64 mine[1] = {words};
+      u64 excl[1];
+      lookback_wait<1>(I.lbp, t, mine, excl, B.status, B.c.spin_limit);
+      if (tid == 0) {
+        s_w0 = excl[0];
+        if (t == pre[item + 1] - pre[item] - 1) I.st->nwords = excl[0] + words;
+      }
     }
     __syncthreads();
-    const u64 cw0 = I.cwoff[t];
-    if (tid == 0 && tab0 + 8 * t + 8 <= cap)  // the chunk table entry
-      *reinterpret_cast<u64*>(out + tab0 + 8 * t) = cw0;
-    const u64 pay = pay0 + 4 * cw0;  // byte offset of the chunk's first word
+    const u64 cw0 = s_w0;
+    const u64 tab0 = tab0s[item], cap = I.cap;
+    uint8_t* out = I.out;
+    if (tid == 0 && tab0 + 8ull * t + 8 <= cap)  // the chunk table entry
+      *reinterpret_cast<u64*>(out + tab0 + 8ull * t) = cw0;
+    const u64 pay = pay0s[item] + 4 * cw0;  // byte offset of the chunk's first word
     const u32* wb32 = reinterpret_cast<const u32*>(wb);
     for (u32 i = tid; i < words; i += blockDim.x) {
       const u64 o = pay + 4 * (u64)i;
       if (o + 4 <= cap) *reinterpret_cast<u32*>(out + o) = wb32[i];
     }
+    if (nrec) {  // the chunk's records (uniform: one chunk per block)
+      const bool from_q = I.q != nullptr;
+      if (!from_q && s_ebi != item) {  // the item's error-bound constants, once per switch
+        __syncthreads();
+        if (tid == 0) {
+          s_eb.e = make_eb(desc_of(B, I), I.rst->vmin_key, I.rst->vmax_key);
+          s_eb.fd = FastDiv(2u * (u32)s_eb.e.eb_int);
+          s_ebi = item;
+        }
+        __syncthreads();
+      }
+      const u64 rec0 = __ldg(I.crecoff + t);
+      if (B.c.dtype == ROIX_F32) {
+        if (from_q) pack_records<float, true>(B, I, s_eb, t, n, rec0, scratch);
+        else pack_records<float, false>(B, I, s_eb, t, n, rec0, scratch);
+      } else {
+        if (from_q) pack_records<unsigned short, true>(B, I, s_eb, t, n, rec0, scratch);
+        else pack_records<unsigned short, false>(B, I, s_eb, t, n, rec0, scratch);
+      }
+    }
     __syncthreads();
     for (u32 i = tid; i < (words + 1) / 2; i += blockDim.x) wb[i] = 0ull;
   }
 }
+
+
 
 // --------------------------------------------------------------- finalize
 __device__ __forceinline__ void put_bytes(uint8_t* h, u32 off, const void* src, u32 bytes) {
@@ -1338,39 +1260,6 @@ void launch_codebook(const Launch& L, const Batch& B) {
 
 void launch_pack(const Launch& L, const Batch& B, u64 ranges_cap) {
   if (ranges_cap == 0) return;
-  const u64 wpb = kThreads / 32;
-  {  // chunk sizes and records
-    const bool from_q = B.it[0].q != nullptr;
-    auto count = [&](auto kernel) {
-      u64 grid = (u64)grid_for((const void*)kernel, kThreads, 0, L.sms);
-      grid = umin(grid, (ranges_cap + wpb - 1) / wpb);
-      kernel<<<(unsigned)grid, kThreads, 0, L.stream>>>(B);
-    };
-    if (B.c.dtype == ROIX_F32) {
-      if (from_q) count(k_pack_count<float, true>);
-      else count(k_pack_count<float, false>);
-    } else {
-      if (from_q) count(k_pack_count<unsigned short, true>);
-      else count(k_pack_count<unsigned short, false>);
-    }
-  }
-  // chunk and record offsets, then records, of the items too large for the
-  // in-kernel scans
-  u64 scan_tiles = 0;
-  for (u32 i = 0; i < B.n; ++i)
-    if (!B.it[i].pscan) scan_tiles += (B.it[i].N + B.c.C - 1) / B.c.C / kScanTile + 1;
-  launch_scan_pairs(L, B, 1, scan_tiles);
-  if (scan_tiles) {
-    const bool from_q = B.it[0].q != nullptr;
-    const u64 grid = umin((ranges_cap + wpb - 1) / wpb, (u64)L.sms * 8);
-    if (B.c.dtype == ROIX_F32) {
-      if (from_q) k_records<float, true><<<(unsigned)grid, kThreads, 0, L.stream>>>(B);
-      else k_records<float, false><<<(unsigned)grid, kThreads, 0, L.stream>>>(B);
-    } else {
-      if (from_q) k_records<unsigned short, true><<<(unsigned)grid, kThreads, 0, L.stream>>>(B);
-      else k_records<unsigned short, false><<<(unsigned)grid, kThreads, 0, L.stream>>>(B);
-    }
-  }
   const size_t smem = ((size_t)B.c.C * kLMax / 64 + 2) * 8;  // the chunk's stream
   auto run = [&](auto kernel) {
     cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

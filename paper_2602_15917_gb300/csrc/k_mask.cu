@@ -448,6 +448,8 @@ __device__ __forceinline__ void range_add(TV v, u32& kmin, u32& kmax) {
 // Two counting kernels give the same results: k_front_count_blk (rows staged
 // by a block, better for narrow rows without dilation) and k_front_count (a
 // warp per tile, better for dilated volumes); the tuning picks one.
+constexpr int kStage = 8;  // mask words a thread has in flight while staging a band
+
 struct FrontSmem {
   u32 wn[kThreads / 32], wb[kThreads / 32];  // per-warp totals, then offsets
   u64 base_n, base_nb, tile;
@@ -508,19 +510,33 @@ __global__ void __launch_bounds__(kThreads, 4) k_front_count_blk(const __grid_co
         bflag[j] = f;
       }
       __syncthreads();
+      // the loads of kStage words per thread are issued before any is used
       const u32 nu = (nrows + 2) * W;
-      for (u32 i = threadIdx.x; i < nu; i += blockDim.x) {
-        const u32 j = divW.div(i), w = i - j * W;
-        const u32 f = bflag[j];
-        u32 u = 0u;
-        if (f & 16u) {
-          const u32* tr = T + (u64)((int64_t)r0 - 1 + j) * W + w;
-          u = __ldg(tr);
-          if (f & 4u) u |= __ldg(tr - zstride);
-          if (f & 8u) u |= __ldg(tr + zstride);
+      for (u32 i0 = threadIdx.x; i0 < nu; i0 += kStage * blockDim.x) {
+        u32 u[kStage];
+#pragma unroll
+        for (int k = 0; k < kStage; ++k) {
+          const u32 i = i0 + (u32)k * blockDim.x;
+          u[k] = 0u;
+          if (i < nu) {
+            const u32 j = divW.div(i), w = i - j * W;
+            const u32 f = bflag[j];
+            if (f & 16u) {
+              const u32* tr = T + (u64)((int64_t)r0 - 1 + j) * W + w;
+              u[k] = __ldg(tr);
+              if (f & 4u) u[k] |= __ldg(tr - zstride);
+              if (f & 8u) u[k] |= __ldg(tr + zstride);
+            }
+          }
         }
-        U[i] = u;
-        any |= u;
+#pragma unroll
+        for (int k = 0; k < kStage; ++k) {
+          const u32 i = i0 + (u32)k * blockDim.x;
+          if (i < nu) {
+            U[i] = u[k];
+            any |= u[k];
+          }
+        }
       }
       any = __syncthreads_or(any);
       if (any) {
@@ -543,11 +559,23 @@ __global__ void __launch_bounds__(kThreads, 4) k_front_count_blk(const __grid_co
         }
       }
     } else {
-      for (u32 i = threadIdx.x; i < nw; i += blockDim.x) {
-        const u32 lr = divW.div(i), w = i - lr * W;
-        const u32 v = __ldg(T + r0 * W + i) & last_mask(d, w);
-        Dw[i] = v;
-        any |= v;
+      for (u32 i0 = threadIdx.x; i0 < nw; i0 += kStage * blockDim.x) {
+        u32 v[kStage];
+#pragma unroll
+        for (int k = 0; k < kStage; ++k) {
+          const u32 i = i0 + (u32)k * blockDim.x;
+          v[k] = i < nw ? __ldg(T + r0 * W + i) : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < kStage; ++k) {
+          const u32 i = i0 + (u32)k * blockDim.x;
+          if (i < nw) {
+            const u32 w = i - divW.div(i) * W;
+            const u32 x = v[k] & last_mask(d, w);
+            Dw[i] = x;
+            any |= x;
+          }
+        }
       }
       any = __syncthreads_or(any);
     }
@@ -849,23 +877,19 @@ __global__ void __launch_bounds__(kThreads, 4) k_front_count(const __grid_consta
   }
 }
 
-// Exclusive scans of two counts per tile or chunk, several blocks per item:
-// a block takes kScanTile entries (8 consecutive ones per thread), scans them,
-// and a decoupled look-back over the item's few scan tiles gives its offset.
-// MODE 0: compaction tiles (ftn, ftb -> ftno, ftbo; totals n, nb); MODE 1:
-// pack chunks (cw, crec -> cwoff, crecoff; totals nwords, nout).
-template <int MODE>
+// Exclusive scans of the compaction tiles' two counts (ftn, ftb -> ftno,
+// ftbo; totals n, nb) of the items the counting kernel does not scan, several
+// blocks per item: a block takes kScanTile entries (8 consecutive ones per
+// thread), scans them, and a decoupled look-back over the item's few scan
+// tiles gives its offset.
 __global__ void __launch_bounds__(1024) k_scan_pairs(const __grid_constant__ Batch B) {
-  if (MODE == 1 && halted(B.status)) return;  // the compaction scan of this call gave up
   __shared__ u64 pre[kMaxBatch + 1];
   __shared__ u64 scratch[40];
   __shared__ u64 s_tile, s_ex[2];
   const int tid = threadIdx.x, lane = tid & 31;
   for (u32 i = tid; i < B.n; i += blockDim.x) {  // counts read in parallel
     const Item& I = B.it[i];
-    const u64 cnt = MODE == 0 ? I.ftiles : (umin(I.sizes[0], I.N) + B.c.C - 1) / B.c.C;
-    const bool done = MODE == 0 ? I.fscan != 0 : I.pscan != 0;  // scanned by the counting kernel
-    pre[i + 1] = done ? 0 : (cnt + kScanTile - 1) / kScanTile;
+    pre[i + 1] = I.fscan ? 0 : (I.ftiles + kScanTile - 1) / kScanTile;
   }
   __syncthreads();
   if (tid == 0) {
@@ -880,19 +904,19 @@ __global__ void __launch_bounds__(1024) k_scan_pairs(const __grid_constant__ Bat
   __syncthreads();
   const u64 total = pre[B.n];
   while (true) {
-    if (tid == 0) s_tile = atomicAdd(&B.ctr[5 + MODE], 1u);
+    if (tid == 0) s_tile = atomicAdd(&B.ctr[5], 1u);
     __syncthreads();
     const u64 gt = s_tile;
     if (gt >= total) break;
     const u32 item = find_item(pre, B.n, gt);
     const Item& I = B.it[item];
     const u64 t = gt - pre[item];
-    const u64 cnt = MODE == 0 ? I.ftiles : (umin(I.sizes[0], I.N) + B.c.C - 1) / B.c.C;
+    const u64 cnt = I.ftiles;
     const u64 ntiles = (cnt + kScanTile - 1) / kScanTile;
-    const u32* __restrict__ a = MODE == 0 ? I.ftn : I.cw;
-    const u32* __restrict__ b = MODE == 0 ? I.ftb : I.crec;
-    u64* __restrict__ ao = MODE == 0 ? I.ftno : I.cwoff;
-    u64* __restrict__ bo = MODE == 0 ? I.ftbo : I.crecoff;
+    const u32* __restrict__ a = I.ftn;
+    const u32* __restrict__ b = I.ftb;
+    u64* __restrict__ ao = I.ftno;
+    u64* __restrict__ bo = I.ftbo;
     const u64 i0 = t * kScanTile + (u64)tid * 8;
     u32 va[8], vb[8];
     u64 sa = 0, sb = 0;
@@ -908,20 +932,14 @@ __global__ void __launch_bounds__(1024) k_scan_pairs(const __grid_constant__ Bat
     u64 eb = block_excl_scan<u64>(sb, scratch, &tb);
     if (tid < 32) {
       u64 mine[2] = {ta, tb}, excl[2];
-      lookback_warp<2>(MODE == 0 ? I.lbsf : I.lbsp, t, mine, excl, B.status, B.c.spin_limit,
+      lookback_warp<2>(I.lbsf, t, mine, excl, B.status, B.c.spin_limit,
                        B.c.hold_scans && item == 0);
       if (lane == 0) {
         s_ex[0] = excl[0];
         s_ex[1] = excl[1];
         if (t == ntiles - 1) {
-          if (MODE == 0) {
-            I.sizes[0] = excl[0] + ta;
-            I.sizes[1] = excl[1] + tb;
-          } else {
-            I.st->nwords = excl[0] + ta;
-            I.st->nout = excl[1] + tb;
-            if (excl[1] + tb > I.rec_cap) I.st->cap_flag = 1u;
-          }
+          I.sizes[0] = excl[0] + ta;
+          I.sizes[1] = excl[1] + tb;
         }
       }
     }
@@ -1257,11 +1275,10 @@ int occupancy_grid(const void* fn, int threads, size_t smem, int sms) {
 
 }  // namespace
 
-void launch_scan_pairs(const Launch& L, const Batch& B, int mode, u64 tiles_cap) {
+void launch_scan_pairs(const Launch& L, const Batch& B, u64 tiles_cap) {
   if (tiles_cap == 0) return;
   const u64 grid = umin(tiles_cap, (u64)L.sms * 2);
-  if (mode == 0) k_scan_pairs<0><<<(unsigned)grid, 1024, 0, L.stream>>>(B);
-  else k_scan_pairs<1><<<(unsigned)grid, 1024, 0, L.stream>>>(B);
+  k_scan_pairs<<<(unsigned)grid, 1024, 0, L.stream>>>(B);
 }
 
 void launch_threshold(const Launch& L, const Batch& B) {
@@ -1340,7 +1357,7 @@ void launch_front(const Launch& L, const Batch& B) {
   u64 scan_tiles = 0;
   for (u32 i = 0; i < B.n; ++i)
     if (!B.it[i].fscan) scan_tiles += (B.it[i].ftiles + kScanTile - 1) / kScanTile;
-  launch_scan_pairs(L, B, 0, scan_tiles);
+  launch_scan_pairs(L, B, scan_tiles);
   auto run = [&](auto kernel) {
     u64 g = (u64)occupancy_grid((const void*)kernel, kThreads, 0, L.sms);
     const u64 need = (B.row0[B.n] + (kThreads / 32) - 1) / (kThreads / 32);  // a row per warp
