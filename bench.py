@@ -37,10 +37,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "GB/s in (quantize+ROI+encode) vs HBM peak, batched/served vs plain; p50/p99 latency"
 # kernels of one fused group: reset, binarisation (one launch per form: row or
-# flat), compaction count, compaction write, symbols, codebook, pack,
-# finalise; plus a tile-scan launch for the compaction when some item has more
-# tiles than the counting kernel scans itself (IN_SCAN_MAX)
-LAUNCHES_PER_GROUP = 7
+# flat), compaction count, compaction write, symbols, codebook, pack count,
+# pack, finalise; plus a tile-scan launch for the compaction when some item has
+# more tiles than the counting kernel scans itself (IN_SCAN_MAX), and a chunk
+# scan and a records launch when some item has more pack chunks than that
+LAUNCHES_PER_GROUP = 8
 IN_SCAN_MAX = 1024
 
 
@@ -48,11 +49,13 @@ def group_launches(xs, cfg=None, tuning=None) -> int:
     """Kernel launches of one fused group of items (the library's rules: the
     flat binarisation form when a 16-byte aligned volume has nx >= 256 and its
     rows are not aligned or do not fill 1024-voxel segments; a tile scan
-    launch only for items with more than IN_SCAN_MAX compaction tiles)."""
+    launch only for items with more than IN_SCAN_MAX compaction tiles or pack
+    chunks)."""
     cfg = cfg or {}
     tuning = tuning or {}
     fw = tuning.get("front_words", 2048) or 2048
-    flat = row = scan0 = False
+    C = cfg.get("chunk", 4096)
+    flat = row = scan0 = scan1 = False
     for x in xs:
         nx = x.shape[-1]
         ptr = x.data_ptr()
@@ -65,7 +68,8 @@ def group_launches(xs, cfg=None, tuning=None) -> int:
         W = (nx + 31) // 32
         rpt = max(1, min(256, fw // W, rows))
         scan0 |= -(-rows // rpt) > IN_SCAN_MAX
-    return LAUNCHES_PER_GROUP + int(flat) + int(row) + int(scan0)
+        scan1 |= -(-x.numel() // C) > IN_SCAN_MAX
+    return LAUNCHES_PER_GROUP + int(flat) + int(row) + int(scan0) + 2 * int(scan1)
 
 # DRAM bytes per step of each stage (dram__bytes_read.sum + dram__bytes_write.sum,
 # summed over the stage's kernels, one launch each) from an ncu capture of the
@@ -1596,8 +1600,9 @@ def run_slabs(args, rank, world, local_rank):
                               for k, v in zip(names, stage_ms) if v > 0}}
     # reset and one binarisation of the whole volume, then per group of up to 64
     # slabs: compaction count, its tile scan (slabs have more than IN_SCAN_MAX
-    # tiles), write, symbols, codebook, pack, finalise
-    per_call = 2 + 7 * ((ns + 63) // 64)
+    # tiles), write, symbols, codebook, pack count, its chunk scan, records,
+    # pack, finalise
+    per_call = 2 + 10 * ((ns + 63) // 64)
     launches = per_call * len(cfgs) * args.steps
     result = None
     if rank == 0:

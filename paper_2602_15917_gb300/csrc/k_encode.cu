@@ -183,13 +183,14 @@ __device__ __forceinline__ void tile_prefix(const Batch& B, u64* pre, u64 per, u
   __syncthreads();
 }
 
-// Per-lane vector of one step: V consecutive values (one 16-byte load of the
-// pixel section, or an 8-byte load of staged codes with their outlier word).
+// Per-lane vector of one step: V consecutive values kept as the raw words of
+// one 16-byte load of the pixel section (elements unpacked when used, so that
+// a lane's loads in flight take four registers each), or two staged codes and
+// their outlier bits.
 template <typename TV, bool FROM_Q>
 struct SymVec {
   static constexpr int V = FROM_Q ? 2 : 16 / (int)sizeof(TV);
-  TV x[V];
-  int q[V];
+  u32 w[FROM_Q ? 2 : 4];
   u32 o;
 };
 
@@ -201,25 +202,30 @@ __device__ __forceinline__ void sym_load(const Src<TV, FROM_Q>& src, u64 k0, u64
   if constexpr (FROM_Q) {
     if (k0 + V <= n) {
       const int2 v = __ldg(reinterpret_cast<const int2*>(src.q + k0));
-      r.q[0] = v.x;
-      r.q[1] = v.y;
+      r.w[0] = (u32)v.x;
+      r.w[1] = (u32)v.y;
     } else {
 #pragma unroll
-      for (int j = 0; j < V; ++j) r.q[j] = k0 + j < n ? __ldg(src.q + k0 + j) : 0;
+      for (int j = 0; j < V; ++j) r.w[j] = k0 + j < n ? (u32)__ldg(src.q + k0 + j) : 0u;
     }
     r.o = k0 < n ? (__ldg(src.obits + (k0 >> 5)) >> (k0 & 31)) & 3u : 0u;  // V = 2, k0 even
   } else {
     if (k0 + V <= n) {
       const uint4 v = __ldg(reinterpret_cast<const uint4*>(src.P + k0));
-      const u32 w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-      for (int j = 0; j < V; ++j) {
-        if constexpr (sizeof(TV) == 4) r.x[j] = __uint_as_float(w[j]);
-        else r.x[j] = (TV)((w[j >> 1] >> (16 * (j & 1))) & 0xffffu);
-      }
+      r.w[0] = v.x;
+      r.w[1] = v.y;
+      r.w[2] = v.z;
+      r.w[3] = v.w;
     } else {
 #pragma unroll
-      for (int j = 0; j < V; ++j) r.x[j] = k0 + j < n ? __ldg(src.P + k0 + j) : TV(0);
+      for (int i = 0; i < 4; ++i) r.w[i] = 0u;
+#pragma unroll
+      for (int j = 0; j < V; ++j) {
+        if (k0 + j < n) {
+          if constexpr (sizeof(TV) == 4) r.w[j] = __float_as_uint(__ldg(src.P + k0 + j));
+          else r.w[j >> 1] |= (u32)__ldg(src.P + k0 + j) << (16 * (j & 1));
+        }
+      }
     }
   }
 }
@@ -230,12 +236,13 @@ __device__ __forceinline__ int sym_eval(const Src<TV, FROM_Q>& src,
                                         const SymVec<TV, FROM_Q>& r, int j, bool& out) {
   if constexpr (FROM_Q) {
     out = ((r.o >> j) & 1u) != 0u;
-    return out ? 0 : r.q[j];
+    return out ? 0 : (int)r.w[j];
   } else if constexpr (sizeof(TV) == 4) {
-    return quant_f32(r.x[j], src.e, out);
+    return quant_f32(__uint_as_float(r.w[j]), src.e, out);
   } else {
     out = false;
-    return quant_u16_fd(r.x[j], src.dark, src.e.eb_int, src.fd);
+    const TV x = (TV)((r.w[j >> 1] >> (16 * (j & 1))) & 0xffffu);
+    return quant_u16_fd(x, src.dark, src.e.eb_int, src.fd);
   }
 }
 
@@ -281,10 +288,13 @@ __device__ __forceinline__ void flush_hist(u32* h, unsigned long long* g, u32 S,
 // barrier anywhere in the loop) and goes to the item's global histogram when
 // the warp moves to another item. Symbol-0 positions (records) are only
 // counted here, per pack chunk (an atomic per lane and step that has one);
-// they are written by k_pack once the codebook kernel has turned the counts
-// into offsets, so that no segment waits for another.
+// they are written by k_pack_count once the codebook kernel has turned the
+// counts into offsets, so that no segment waits for another.
+// (first-order forms: registers for four blocks per SM for uint16 values,
+// three for float32)
 template <typename TV, bool FROM_Q, int ORDER>
-__global__ void __launch_bounds__(kThreads) k_symbols(const __grid_constant__ Batch B) {
+__global__ void __launch_bounds__(kThreads, ORDER != 1 || FROM_Q ? 1 : (sizeof(TV) == 2 ? 4 : 3))
+k_symbols(const __grid_constant__ Batch B) {
   if (halted(B.status)) return;  // a tile scan of this call gave up
   using Vec = SymVec<TV, FROM_Q>;
   constexpr int V = Vec::V;
@@ -836,9 +846,9 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__
     lens_ws[s] = len[s];
     if (kHeaderBytes + s < cap) out[kHeaderBytes + s] = len[s];
   }
-  // the item's records: per-chunk counts (from the symbol kernel) into
-  // offsets, and their total
-  {
+  // the records of an item with at most kInScanMax chunks: per-chunk counts
+  // (from the symbol kernel) into offsets (larger items: k_scan_pairs<1>)
+  if (I.pscan) {
     __shared__ u64 scratch64[40];
     const u64 n = umin(I.sizes[0], I.N);
     const u64 nch = (n + B.c.C - 1) / B.c.C;
@@ -852,58 +862,178 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__
 }
 
 // ------------------------------------------------------------------- pack
-// One pass over the symbols, chunks from global tickets in order (every
-// item's chunks in order). A block forms its chunk's codes and bit offsets,
-// publishes the chunk's payload word count to a decoupled look-back over the
-// item's chunks, assembles the words in shared memory meanwhile, then takes
-// the chunk's first word from the look-back and stores the words and the
-// chunk table entry; the chunk's records go to the offsets the codebook
-// kernel scanned. A ticket is held only by a running block, which publishes
-// its count before it waits, so every wait ends; it is bounded all the same
-// (ROIX_ETIMEOUT).
+// Passes none of whose blocks waits on another: k_pack_count sums the code
+// lengths of every chunk; the chunks' word and record counts become offsets
+// (for items with at most kInScanMax chunks in the codebook kernel and in
+// k_pack_count, which then also writes their records; for larger items in
+// k_scan_pairs<1>, followed by k_records), and k_pack writes every chunk's
+// words at its offset (chunks from global tickets in order).
 
-// The records of chunk t: its symbol-0 positions in order, from the record
-// bitmap the symbol kernel wrote (thread i with a contiguous share of the
-// chunk's bitmap words, a block scan of their popcounts), each written as
-// (k | kind << 63, payload) from offset rec0 on; the code or the raw value is
-// formed again from the pixel section (or the staged codes). Called by the
-// whole block.
+// Warps, one chunk at a time: lane l holds symbols [8 l, 8 l + 8) of each
+// round of 256 (coalesced 16-byte loads); the code lengths come from the
+// item's byte table (2R bytes, read through L1). For an item with at most
+// kInScanMax chunks the warp also writes the chunk's records, if it holds
+// any: the symbol-0 positions in order, from the
+// record bitmap the symbol kernel wrote (lane l with words l, l + 32, ...; a
+// warp scan of their popcounts), each as (k | kind << 63, payload) at the
+// chunk's record offset (scanned by the codebook kernel); the code or the raw
+// value is formed again from the pixel section (or the staged codes). For an
+// item with at most kInScanMax chunks, the warp that counts the item's last
+// chunk scans the chunks' word counts into their offsets.
 template <typename TV, bool FROM_Q>
-__device__ void pack_records(const Batch& B, const Item& I, const ItemEb& eb, u64 t, u64 n,
-                             u64 rec0, u32* scratch) {
+__global__ void __launch_bounds__(kThreads) k_pack_count(const __grid_constant__ Batch B) {
+  if (halted(B.status)) return;  // a tile scan of this call gave up
+  __shared__ u64 pre[kMaxBatch + 1];
+  __shared__ u64 nn[kMaxBatch];
   const u32 C = B.c.C;
-  const u64 w0 = t * (C / 32);
-  const u32 nw = (u32)((umin(n, (t + 1) * (u64)C) - t * (u64)C + 31) / 32);
-  const u32 per = (nw + blockDim.x - 1) / blockDim.x;
-  const u32 j0 = min(nw, threadIdx.x * per), j1 = min(nw, j0 + per);
-  const u32* __restrict__ rbits = I.rbits;
-  u32 cnt = 0;
-  for (u32 j = j0; j < j1; ++j) cnt += __popc(__ldg(rbits + w0 + j));
-  u32 tot;
-  u64 o = rec0 + block_excl_scan<u32>(cnt, scratch, &tot);
-  if (cnt == 0) return;
+  const int lane = threadIdx.x & 31;
+  tile_prefix(B, pre, C, 1, nn);
+  const u64 total = pre[B.n];
+  const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
+  constexpr u32 kIn = 4;  // vector loads of a lane in flight at once
+  u32 cur = 0xffffffffu;  // item whose records source is set
   Src<TV, FROM_Q> src{};
-  src.P = (const TV*)I.P;
-  src.q = I.q;
-  src.obits = I.obits;
-  src.dark = B.c.dark;
-  if constexpr (!FROM_Q) {
-    src.e = eb.e;
-    src.fd = eb.fd;
-  }
-  for (u32 j = j0; j < j1; ++j) {
-    u32 zm = __ldg(rbits + w0 + j);
-    while (zm) {
-      const int q = __ffs(zm) - 1;
-      zm &= zm - 1;
-      const u64 k = (w0 + j) * 32 + q;
-      bool out;
-      const int c = src.code(k, out);
-      if (o < I.rec_cap) {
-        I.rk[o] = k | (out ? (1ull << 63) : 0ull);
-        I.rv[o] = out ? src.raw_bits(k) : (u32)c;
+  for (u64 gt = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5; gt < total; gt += nwarps) {
+    const u32 item = find_item(pre, B.n, gt);
+    const Item& I = B.it[item];
+    const u64 n = nn[item];
+    const uint16_t* __restrict__ sym = I.sym;
+    const uint8_t* __restrict__ len = I.lens;  // 2R bytes: stays in L1
+    const u64 t = gt - pre[item];
+    const u64 c0 = t * C + (u64)lane * 8;
+    const u32 steps = C / 256;  // 8 symbols per lane and step
+    u32 bits = 0;
+    if (t * C + C <= n) {  // a full chunk: no bounds tests
+      for (u32 r0 = 0; r0 < steps; r0 += kIn) {
+        uint4 v[kIn];
+#pragma unroll
+        for (u32 q = 0; q < kIn; ++q)
+          if (r0 + q < steps)
+            v[q] = __ldg(reinterpret_cast<const uint4*>(sym + c0 + (u64)(r0 + q) * 256));
+#pragma unroll
+        for (u32 q = 0; q < kIn; ++q)
+          if (r0 + q < steps)
+            bits += __ldg(len + (v[q].x & 0xffffu)) + __ldg(len + (v[q].x >> 16)) +
+                    __ldg(len + (v[q].y & 0xffffu)) + __ldg(len + (v[q].y >> 16)) +
+                    __ldg(len + (v[q].z & 0xffffu)) + __ldg(len + (v[q].z >> 16)) +
+                    __ldg(len + (v[q].w & 0xffffu)) + __ldg(len + (v[q].w >> 16));
       }
-      ++o;
+    } else {
+      for (u32 r = 0; r < steps; ++r) {
+        const u64 k = c0 + (u64)r * 256;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (k + q < n) bits += __ldg(len + __ldg(sym + k + q));
+      }
+    }
+    bits = __reduce_add_sync(0xffffffffu, bits);
+    if (lane == 0) I.cw[t] = (bits + 31) >> 5;
+    if (I.pscan && I.crec[t] != 0u) {  // the chunk's records (a small item's)
+      if (item != cur) {
+        cur = item;
+        const Desc d = desc_of(B, I);
+        src.P = (const TV*)I.P;
+        src.q = I.q;
+        src.obits = I.obits;
+        src.dark = d.dark;
+        if constexpr (!FROM_Q) {
+          src.e = make_eb(d, I.rst->vmin_key, I.rst->vmax_key);
+          src.fd = FastDiv(2u * (u32)src.e.eb_int);
+        }
+      }
+      const u32* __restrict__ rbits = I.rbits;
+      u64 idx = I.crecoff[t];
+      const u64 w0 = t * (C / 32), nwords = (umin(n, (t + 1) * (u64)C) - t * C + 31) / 32;
+      for (u64 j0 = 0; j0 < nwords; j0 += 32) {
+        const u64 j = j0 + lane;
+        u32 zm = j < nwords ? __ldg(rbits + w0 + j) : 0u;
+        const u32 cnt = __popc(zm);
+        const u32 inc = warp_incl_scan(cnt);
+        u64 o = idx + inc - cnt;
+        while (zm) {
+          const int q = __ffs(zm) - 1;
+          zm &= zm - 1;
+          const u64 k = (w0 + j) * 32 + q;
+          bool out;
+          const int c = src.code(k, out);
+          if (o < I.rec_cap) {
+            I.rk[o] = k | (out ? (1ull << 63) : 0ull);
+            I.rv[o] = out ? src.raw_bits(k) : (u32)c;
+          }
+          ++o;
+        }
+        idx += __shfl_sync(0xffffffffu, inc, 31);
+      }
+    }
+    const u64 nch = pre[item + 1] - pre[item];
+    if (I.pscan && count_done(&I.st->done_pack, nch)) {  // the item's chunk offsets
+      u64 tw, tr;
+      warp_scan2(I.cw, nullptr, nch, I.cwoff, nullptr, tw, tr);
+      if (lane == 0) I.st->nwords = tw;
+    }
+  }
+}
+
+// Warps, one chunk at a time, only chunks that hold records of items with
+// more than kInScanMax chunks (k_pack_count writes those of the others): the
+// symbol-0 positions of the chunk in order, from the record bitmap the symbol
+// kernel wrote (lane l with words l, l + 32, ...; a warp scan of their
+// popcounts), each written as (k | kind << 63, payload) at the chunk's record
+// offset (from k_scan_pairs<1>); the code or the raw value is formed again from
+// the pixel section (or the staged codes).
+template <typename TV, bool FROM_Q>
+__global__ void __launch_bounds__(kThreads) k_records(const __grid_constant__ Batch B) {
+  if (halted(B.status)) return;  // a tile scan of this call gave up
+  __shared__ u64 pre[kMaxBatch + 1];
+  const u32 C = B.c.C;
+  const int lane = threadIdx.x & 31;
+  tile_prefix(B, pre, C, 1);
+  const u64 total = pre[B.n];
+  const u64 warp0 = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
+  u32 cur = 0xffffffffu;
+  Src<TV, FROM_Q> src{};
+  u64 n = 0;
+  for (u64 gt = warp0; gt < total; gt += nwarps) {
+    const u32 item = find_item(pre, B.n, gt);
+    const Item& I = B.it[item];
+    const u64 t = gt - pre[item];
+    if (I.pscan || I.crec[t] == 0u) continue;
+    if (item != cur) {  // the item's error-bound constants, formed only for chunks with records
+      cur = item;
+      const Desc d = desc_of(B, I);
+      src.P = (const TV*)I.P;
+      src.q = I.q;
+      src.obits = I.obits;
+      src.dark = d.dark;
+      if constexpr (!FROM_Q) {
+        src.e = make_eb(d, I.rst->vmin_key, I.rst->vmax_key);
+        src.fd = FastDiv(2u * (u32)src.e.eb_int);
+      }
+      n = umin(I.sizes[0], I.N);
+    }
+    const u32* __restrict__ rbits = I.rbits;
+    u64 idx = I.crecoff[t];
+    const u64 w0 = t * (C / 32), nwords = (umin(n, (t + 1) * (u64)C) - t * C + 31) / 32;
+    for (u64 j0 = 0; j0 < nwords; j0 += 32) {
+      const u64 j = j0 + lane;
+      u32 zm = j < nwords ? __ldg(rbits + w0 + j) : 0u;
+      const u32 cnt = __popc(zm);
+      const u32 inc = warp_incl_scan(cnt);
+      u64 o = idx + inc - cnt;
+      while (zm) {
+        const int q = __ffs(zm) - 1;
+        zm &= zm - 1;
+        const u64 k = (w0 + j) * 32 + q;
+        bool out;
+        const int c = src.code(k, out);
+        if (o < I.rec_cap) {
+          I.rk[o] = k | (out ? (1ull << 63) : 0ull);
+          I.rv[o] = out ? src.raw_bits(k) : (u32)c;
+        }
+        ++o;
+      }
+      idx += __shfl_sync(0xffffffffu, inc, 31);
     }
   }
 }
@@ -916,9 +1046,8 @@ __device__ void pack_records(const Batch& B, const Item& I, const ItemEb& eb, u6
 // chunk's words (MSB first) in a shared buffer: the word being filled stays
 // in a register, a code is placed by one shift (and the part that runs past
 // the word by one funnel shift), and a full word leaves by one shared OR (so
-// the words shared with the neighbouring threads need no other care); warp 0
-// waits for the chunk's word offset; the words are stored with coalesced
-// stores at that offset.
+// the words shared with the neighbouring threads need no other care); the
+// words are stored with coalesced stores at the chunk's offset.
 template <int EPT>
 __global__ void __launch_bounds__(kThreads, EPT <= 16 ? 5 : 1) k_pack(const __grid_constant__ Batch B) {
   if (halted(B.status)) return;  // a tile scan of this call gave up
@@ -928,9 +1057,6 @@ __global__ void __launch_bounds__(kThreads, EPT <= 16 ? 5 : 1) k_pack(const __gr
   __shared__ u64 s_tile;
   __shared__ u64 pre[kMaxBatch + 1];
   __shared__ u64 nval[kMaxBatch], pay0s[kMaxBatch], tab0s[kMaxBatch];
-  __shared__ u64 s_w0;     // the chunk's first payload word (from the look-back)
-  __shared__ ItemEb s_eb;  // error-bound constants of the item whose records are written
-  __shared__ u32 s_ebi;
   const u32 C = B.c.C, S = B.c.S;
   const int tid = threadIdx.x;
   tile_prefix(B, pre, C, 1, nval);
@@ -944,7 +1070,6 @@ __global__ void __launch_bounds__(kThreads, EPT <= 16 ? 5 : 1) k_pack(const __gr
   const u64 total = pre[B.n];
   const u32 wb_words = C * kLMax / 64 + 2;
   for (u32 i = tid; i < wb_words; i += blockDim.x) wb[i] = 0ull;
-  if (tid == 0) s_ebi = 0xffffffffu;
   u32 cur = 0xffffffffu;
   constexpr int NV = EPT % 8 == 0 ? EPT / 8 : 1;  // 16-byte loads per thread
   while (true) {
@@ -966,7 +1091,7 @@ __global__ void __launch_bounds__(kThreads, EPT <= 16 ? 5 : 1) k_pack(const __gr
 #pragma unroll
       for (int v = 0; v < NV; ++v) raw[v] = __ldg(reinterpret_cast<const uint4*>(sym + k0 + 8 * v));
     }
-    const u32 nrec = __ldg(I.crec + t);
+    const u64 cw0 = __ldg(I.cwoff + t);
     if (item != cur) {  // the item's code table into shared memory
       cur = item;
       for (u32 i = tid; i < S; i += blockDim.x) tab[i] = __ldg(I.codes + i);
@@ -993,11 +1118,6 @@ __global__ void __launch_bounds__(kThreads, EPT <= 16 ? 5 : 1) k_pack(const __gr
     u32 cbits;
     const u32 off = block_excl_scan<u32>(bits, scratch, &cbits);
     const u32 words = (cbits + 31) >> 5;
-    const bool hold = B.c.hold_scans && item == 0;  // test hook: chunk 0 never publishes
-    if (tid == 0) {
-      const u64 mine[1] = {words};
-      lookback_publish<1>(I.lbp, t, mine, hold);
-    }
     // the thread's codes are contiguous in the chunk's stream [off, off +
     // bits): `acc` holds word w's bits from position `fill` on (MSB first)
     if (bits) {
@@ -1018,17 +1138,7 @@ __global__ void __launch_bounds__(kThreads, EPT <= 16 ? 5 : 1) k_pack(const __gr
       }
       if (fill) atomicOr(&wb32[w], acc);
     }
-    if (tid < 32) {  // the chunk's first word: the words of the item's chunks before it
-      const u64 mine[1] = {words};
-      u64 excl[1];
-      lookback_wait<1>(I.lbp, t, mine, excl, B.status, B.c.spin_limit);
-      if (tid == 0) {
-        s_w0 = excl[0];
-        if (t == pre[item + 1] - pre[item] - 1) I.st->nwords = excl[0] + words;
-      }
-    }
     __syncthreads();
-    const u64 cw0 = s_w0;
     const u64 tab0 = tab0s[item], cap = I.cap;
     uint8_t* out = I.out;
     if (tid == 0 && tab0 + 8ull * t + 8 <= cap)  // the chunk table entry
@@ -1039,32 +1149,10 @@ __global__ void __launch_bounds__(kThreads, EPT <= 16 ? 5 : 1) k_pack(const __gr
       const u64 o = pay + 4 * (u64)i;
       if (o + 4 <= cap) *reinterpret_cast<u32*>(out + o) = wb32[i];
     }
-    if (nrec) {  // the chunk's records (uniform: one chunk per block)
-      const bool from_q = I.q != nullptr;
-      if (!from_q && s_ebi != item) {  // the item's error-bound constants, once per switch
-        __syncthreads();
-        if (tid == 0) {
-          s_eb.e = make_eb(desc_of(B, I), I.rst->vmin_key, I.rst->vmax_key);
-          s_eb.fd = FastDiv(2u * (u32)s_eb.e.eb_int);
-          s_ebi = item;
-        }
-        __syncthreads();
-      }
-      const u64 rec0 = __ldg(I.crecoff + t);
-      if (B.c.dtype == ROIX_F32) {
-        if (from_q) pack_records<float, true>(B, I, s_eb, t, n, rec0, scratch);
-        else pack_records<float, false>(B, I, s_eb, t, n, rec0, scratch);
-      } else {
-        if (from_q) pack_records<unsigned short, true>(B, I, s_eb, t, n, rec0, scratch);
-        else pack_records<unsigned short, false>(B, I, s_eb, t, n, rec0, scratch);
-      }
-    }
     __syncthreads();
     for (u32 i = tid; i < (words + 1) / 2; i += blockDim.x) wb[i] = 0ull;
   }
 }
-
-
 
 // --------------------------------------------------------------- finalize
 __device__ __forceinline__ void put_bytes(uint8_t* h, u32 off, const void* src, u32 bytes) {
@@ -1260,6 +1348,39 @@ void launch_codebook(const Launch& L, const Batch& B) {
 
 void launch_pack(const Launch& L, const Batch& B, u64 ranges_cap) {
   if (ranges_cap == 0) return;
+  const u64 wpb = kThreads / 32;
+  {  // chunk sizes and records
+    const bool from_q = B.it[0].q != nullptr;
+    auto count = [&](auto kernel) {
+      u64 grid = (u64)grid_for((const void*)kernel, kThreads, 0, L.sms);
+      grid = umin(grid, (ranges_cap + wpb - 1) / wpb);
+      kernel<<<(unsigned)grid, kThreads, 0, L.stream>>>(B);
+    };
+    if (B.c.dtype == ROIX_F32) {
+      if (from_q) count(k_pack_count<float, true>);
+      else count(k_pack_count<float, false>);
+    } else {
+      if (from_q) count(k_pack_count<unsigned short, true>);
+      else count(k_pack_count<unsigned short, false>);
+    }
+  }
+  // chunk and record offsets, then records, of the items too large for the
+  // in-kernel scans
+  u64 scan_tiles = 0;
+  for (u32 i = 0; i < B.n; ++i)
+    if (!B.it[i].pscan) scan_tiles += (B.it[i].N + B.c.C - 1) / B.c.C / kScanTile + 1;
+  launch_scan_pairs(L, B, 1, scan_tiles);
+  if (scan_tiles) {
+    const bool from_q = B.it[0].q != nullptr;
+    const u64 grid = umin((ranges_cap + wpb - 1) / wpb, (u64)L.sms * 8);
+    if (B.c.dtype == ROIX_F32) {
+      if (from_q) k_records<float, true><<<(unsigned)grid, kThreads, 0, L.stream>>>(B);
+      else k_records<float, false><<<(unsigned)grid, kThreads, 0, L.stream>>>(B);
+    } else {
+      if (from_q) k_records<unsigned short, true><<<(unsigned)grid, kThreads, 0, L.stream>>>(B);
+      else k_records<unsigned short, false><<<(unsigned)grid, kThreads, 0, L.stream>>>(B);
+    }
+  }
   const size_t smem = ((size_t)B.c.C * kLMax / 64 + 2) * 8;  // the chunk's stream
   auto run = [&](auto kernel) {
     cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

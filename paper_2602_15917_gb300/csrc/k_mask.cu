@@ -877,19 +877,23 @@ __global__ void __launch_bounds__(kThreads, 4) k_front_count(const __grid_consta
   }
 }
 
-// Exclusive scans of the compaction tiles' two counts (ftn, ftb -> ftno,
-// ftbo; totals n, nb) of the items the counting kernel does not scan, several
-// blocks per item: a block takes kScanTile entries (8 consecutive ones per
-// thread), scans them, and a decoupled look-back over the item's few scan
-// tiles gives its offset.
+// Exclusive scans of two counts per tile or chunk, several blocks per item:
+// a block takes kScanTile entries (8 consecutive ones per thread), scans them,
+// and a decoupled look-back over the item's few scan tiles gives its offset.
+// MODE 0: compaction tiles (ftn, ftb -> ftno, ftbo; totals n, nb); MODE 1:
+// pack chunks (cw, crec -> cwoff, crecoff; totals nwords, nout).
+template <int MODE>
 __global__ void __launch_bounds__(1024) k_scan_pairs(const __grid_constant__ Batch B) {
+  if (MODE == 1 && halted(B.status)) return;  // the compaction scan of this call gave up
   __shared__ u64 pre[kMaxBatch + 1];
   __shared__ u64 scratch[40];
   __shared__ u64 s_tile, s_ex[2];
   const int tid = threadIdx.x, lane = tid & 31;
   for (u32 i = tid; i < B.n; i += blockDim.x) {  // counts read in parallel
     const Item& I = B.it[i];
-    pre[i + 1] = I.fscan ? 0 : (I.ftiles + kScanTile - 1) / kScanTile;
+    const u64 cnt = MODE == 0 ? I.ftiles : (umin(I.sizes[0], I.N) + B.c.C - 1) / B.c.C;
+    const bool done = MODE == 0 ? I.fscan != 0 : I.pscan != 0;  // scanned by the counting kernel
+    pre[i + 1] = done ? 0 : (cnt + kScanTile - 1) / kScanTile;
   }
   __syncthreads();
   if (tid == 0) {
@@ -904,19 +908,19 @@ __global__ void __launch_bounds__(1024) k_scan_pairs(const __grid_constant__ Bat
   __syncthreads();
   const u64 total = pre[B.n];
   while (true) {
-    if (tid == 0) s_tile = atomicAdd(&B.ctr[5], 1u);
+    if (tid == 0) s_tile = atomicAdd(&B.ctr[5 + MODE], 1u);
     __syncthreads();
     const u64 gt = s_tile;
     if (gt >= total) break;
     const u32 item = find_item(pre, B.n, gt);
     const Item& I = B.it[item];
     const u64 t = gt - pre[item];
-    const u64 cnt = I.ftiles;
+    const u64 cnt = MODE == 0 ? I.ftiles : (umin(I.sizes[0], I.N) + B.c.C - 1) / B.c.C;
     const u64 ntiles = (cnt + kScanTile - 1) / kScanTile;
-    const u32* __restrict__ a = I.ftn;
-    const u32* __restrict__ b = I.ftb;
-    u64* __restrict__ ao = I.ftno;
-    u64* __restrict__ bo = I.ftbo;
+    const u32* __restrict__ a = MODE == 0 ? I.ftn : I.cw;
+    const u32* __restrict__ b = MODE == 0 ? I.ftb : I.crec;
+    u64* __restrict__ ao = MODE == 0 ? I.ftno : I.cwoff;
+    u64* __restrict__ bo = MODE == 0 ? I.ftbo : I.crecoff;
     const u64 i0 = t * kScanTile + (u64)tid * 8;
     u32 va[8], vb[8];
     u64 sa = 0, sb = 0;
@@ -932,14 +936,20 @@ __global__ void __launch_bounds__(1024) k_scan_pairs(const __grid_constant__ Bat
     u64 eb = block_excl_scan<u64>(sb, scratch, &tb);
     if (tid < 32) {
       u64 mine[2] = {ta, tb}, excl[2];
-      lookback_warp<2>(I.lbsf, t, mine, excl, B.status, B.c.spin_limit,
+      lookback_warp<2>(MODE == 0 ? I.lbsf : I.lbsp, t, mine, excl, B.status, B.c.spin_limit,
                        B.c.hold_scans && item == 0);
       if (lane == 0) {
         s_ex[0] = excl[0];
         s_ex[1] = excl[1];
         if (t == ntiles - 1) {
-          I.sizes[0] = excl[0] + ta;
-          I.sizes[1] = excl[1] + tb;
+          if (MODE == 0) {
+            I.sizes[0] = excl[0] + ta;
+            I.sizes[1] = excl[1] + tb;
+          } else {
+            I.st->nwords = excl[0] + ta;
+            I.st->nout = excl[1] + tb;
+            if (excl[1] + tb > I.rec_cap) I.st->cap_flag = 1u;
+          }
         }
       }
     }
@@ -1275,10 +1285,11 @@ int occupancy_grid(const void* fn, int threads, size_t smem, int sms) {
 
 }  // namespace
 
-void launch_scan_pairs(const Launch& L, const Batch& B, u64 tiles_cap) {
+void launch_scan_pairs(const Launch& L, const Batch& B, int mode, u64 tiles_cap) {
   if (tiles_cap == 0) return;
   const u64 grid = umin(tiles_cap, (u64)L.sms * 2);
-  k_scan_pairs<<<(unsigned)grid, 1024, 0, L.stream>>>(B);
+  if (mode == 0) k_scan_pairs<0><<<(unsigned)grid, 1024, 0, L.stream>>>(B);
+  else k_scan_pairs<1><<<(unsigned)grid, 1024, 0, L.stream>>>(B);
 }
 
 void launch_threshold(const Launch& L, const Batch& B) {
@@ -1357,7 +1368,7 @@ void launch_front(const Launch& L, const Batch& B) {
   u64 scan_tiles = 0;
   for (u32 i = 0; i < B.n; ++i)
     if (!B.it[i].fscan) scan_tiles += (B.it[i].ftiles + kScanTile - 1) / kScanTile;
-  launch_scan_pairs(L, B, scan_tiles);
+  launch_scan_pairs(L, B, 0, scan_tiles);
   auto run = [&](auto kernel) {
     u64 g = (u64)occupancy_grid((const void*)kernel, kThreads, 0, L.sms);
     const u64 need = (B.row0[B.n] + (kThreads / 32) - 1) / (kThreads / 32);  // a row per warp

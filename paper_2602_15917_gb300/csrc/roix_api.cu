@@ -203,8 +203,8 @@ u32 front_rows_per_tile(const Desc& d) {
 struct ItemPlan {
   size_t crec, hist, sff, sfp;  // zeroed
   size_t sfa, spa;
-  u64 stf;  // scan tiles of the compaction
-  size_t ftn, ftb, ftno, ftbo, rno, rbo, Dm, crecoff, rbits, T, P, sym, rk, rv, lens, codes;
+  u64 stf, stp;  // scan tiles of the compaction and of the pack
+  size_t ftn, ftb, ftno, ftbo, rno, rbo, Dm, cw, cwoff, crecoff, rbits, T, P, sym, rk, rv, lens, codes;
   // largest-component scratch (keep = 1): zeroed flags and counters, then data
   size_t cf, cvars, ca, crr, cro, cxs, cxe, cpar, csize, T2;
   u64 ctiles;
@@ -244,8 +244,9 @@ BatchPlan plan_batch(const Desc& c, const roix_dims* dims, const u64* n_caps, co
     p.crec = a.take(4 * (p.pchunks + 1));
     p.hist = a.take(8 * (size_t)c.S);
     p.stf = (p.ftiles + kScanTile - 1) / kScanTile;
+    p.stp = (p.pchunks + kScanTile - 1) / kScanTile;
     p.sff = a.take(4 * (p.stf + 1));
-    p.sfp = a.take(4 * (p.pchunks + 1));  // a look-back flag per pack chunk
+    p.sfp = a.take(4 * (p.stp + 1));
     if (c.keep) {
       const u64 rows = dims[i].ny * dims[i].nz;
       p.ctiles = (rows + 2047) / 2048;
@@ -260,7 +261,7 @@ BatchPlan plan_batch(const Desc& c, const roix_dims* dims, const u64* n_caps, co
     ItemPlan& p = bp.items[i];
     const u64 rows = dims[i].ny * dims[i].nz, W = (dims[i].nx + 31) / 32;
     p.sfa = a.take(8 * 2 * 2 * (p.stf + 1));
-    p.spa = a.take(8 * 2 * (p.pchunks + 1));
+    p.spa = a.take(8 * 2 * 2 * (p.stp + 1));
     p.ftn = a.take(4 * (p.ftiles + 1));
     p.ftb = a.take(4 * (p.ftiles + 1));
     p.ftno = a.take(8 * (p.ftiles + 1));
@@ -268,6 +269,8 @@ BatchPlan plan_batch(const Desc& c, const roix_dims* dims, const u64* n_caps, co
     p.Dm = c.dilate ? a.take(4 * rows * W + 16) : 0;
     p.rno = a.take(4 * rows + 16);
     p.rbo = a.take(4 * rows + 16);
+    p.cw = a.take(4 * (p.pchunks + 1));
+    p.cwoff = a.take(8 * (p.pchunks + 1));
     p.crecoff = a.take(8 * (p.pchunks + 1));
     p.rbits = a.take(4 * (p.n_cap / 32 + 2));
     p.T = need_T ? a.take(4 * rows * W + 16) : 0;
@@ -345,7 +348,7 @@ void fill_batch(Batch& B, const Desc& c, const BatchPlan& bp, const roix_dims* d
     I.codes = (u32*)(ws + p.codes);
     I.sizes = &I.st->n;
     I.lbsf = lb_at<2>(ws, p.sff, p.sfa, p.stf);
-    I.lbp = lb_at<1>(ws, p.sfp, p.spa, p.pchunks);
+    I.lbsp = lb_at<2>(ws, p.sfp, p.spa, p.stp);
     I.ftn = (u32*)(ws + p.ftn);
     I.ftb = (u32*)(ws + p.ftb);
     I.ftno = (u64*)(ws + p.ftno);
@@ -354,6 +357,8 @@ void fill_batch(Batch& B, const Desc& c, const BatchPlan& bp, const roix_dims* d
     I.rno = (u32*)(ws + p.rno);
     I.rbo = (u32*)(ws + p.rbo);
     I.crec = (u32*)(ws + p.crec);
+    I.cw = (u32*)(ws + p.cw);
+    I.cwoff = (u64*)(ws + p.cwoff);
     I.crecoff = (u64*)(ws + p.crecoff);
     I.rbits = (u32*)(ws + p.rbits);
     I.rpt = p.rpt;
@@ -361,6 +366,7 @@ void fill_batch(Batch& B, const Desc& c, const BatchPlan& bp, const roix_dims* d
     I.m_ny = recip64(I.ny);
     I.ftiles = p.ftiles;
     I.fscan = p.ftiles <= kInScanMax ? 1u : 0u;
+    I.pscan = p.pchunks <= kInScanMax ? 1u : 0u;
     B.seg0[i] = seg;
     B.ftile0[i] = ft;
     B.row0[i] = rw;

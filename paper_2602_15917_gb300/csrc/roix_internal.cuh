@@ -113,37 +113,29 @@ __device__ bool lookback(LookBack<NV> lb, u64 t, const u64 (&mine)[NV], u64 (&ex
   return timed_out;
 }
 
-// Warp-parallel form (Merrill & Garland's window variant), in two parts so
-// that a block can publish its aggregate first and wait later.
-// lookback_publish (one thread): the tile's aggregate, or for tile 0 its
-// inclusive prefix (hold: tile 0 publishes nothing, as in lookback()).
+// Warp-parallel form (Merrill & Garland's window variant): all 32 lanes of one
+// warp call it; lane j inspects predecessor t-1-j, so a window of 32 flags is
+// read per L2 round trip. Lanes up to the nearest inclusive prefix must have
+// published; their aggregates and that prefix are summed by a warp reduction.
+// Returns the exclusive prefix in every lane. Bounded like lookback().
 template <int NV>
-__device__ __forceinline__ void lookback_publish(LookBack<NV> lb, u64 t, const u64 (&mine)[NV],
-                                                 bool hold = false) {
-  if (t == 0) {
-    if (hold) return;
-    for (int i = 0; i < NV; ++i) st_relaxed(&lb.inc[i], mine[i]);
-    st_release(&lb.flags[0], 2u);
-    return;
-  }
-  for (int i = 0; i < NV; ++i) st_relaxed(&lb.agg[t * NV + i], mine[i]);
-  st_release(&lb.flags[t], 1u);
-}
-
-// lookback_wait (all 32 lanes of one warp, after lookback_publish): lane j
-// inspects predecessor t-1-j, so a window of 32 flags is read per L2 round
-// trip. Lanes up to the nearest inclusive prefix must have published; their
-// aggregates and that prefix are summed by a warp reduction, and the tile's
-// inclusive prefix is published. Returns the exclusive prefix in every lane;
-// true when the wait gave up (ROIX_ETIMEOUT set, bounded like lookback()).
-template <int NV>
-__device__ bool lookback_wait(LookBack<NV> lb, u64 t, const u64 (&mine)[NV], u64 (&excl)[NV],
-                              u32* status, u32 limit) {
+__device__ bool lookback_warp(LookBack<NV> lb, u64 t, const u64 (&mine)[NV], u64 (&excl)[NV],
+                              u32* status, u32 limit, bool hold = false) {
   const int lane = threadIdx.x & 31;
   for (int i = 0; i < NV; ++i) excl[i] = 0;
-  if (t == 0) return false;
+  if (t == 0) {
+    if (lane == 0 && !hold) {
+      for (int i = 0; i < NV; ++i) st_relaxed(&lb.inc[i], mine[i]);
+      st_release(&lb.flags[0], 2u);
+    }
+    return false;
+  }
   limit = spin_limit_of(limit);
   bool timed_out = false;
+  if (lane == 0) {
+    for (int i = 0; i < NV; ++i) st_relaxed(&lb.agg[t * NV + i], mine[i]);
+    st_release(&lb.flags[t], 1u);
+  }
   long long base = (long long)t - 1;
   u32 spins = 0;
   while (true) {
@@ -179,14 +171,6 @@ __device__ bool lookback_wait(LookBack<NV> lb, u64 t, const u64 (&mine)[NV], u64
     st_release(&lb.flags[t], 2u);
   }
   return timed_out;
-}
-
-// Both parts at once (all 32 lanes of one warp).
-template <int NV>
-__device__ bool lookback_warp(LookBack<NV> lb, u64 t, const u64 (&mine)[NV], u64 (&excl)[NV],
-                              u32* status, u32 limit, bool hold = false) {
-  if ((threadIdx.x & 31) == 0) lookback_publish(lb, t, mine, hold);
-  return lookback_wait(lb, t, mine, excl, status, limit);
 }
 
 // A kernel of the compression path that runs after a tile scan: true when a
@@ -394,11 +378,11 @@ struct State {
   u32 status;                          // context status word (state 0 only)
   u32 ctr_front, ctr_quant, ctr_pack;  // dynamic tile counters (state 0: batch tickets)
   u32 ctr_write, ctr_front2;           // pack-write and compaction-write tickets
-  u32 ctr_scan_f, pad1;                // tile scans of the compaction
+  u32 ctr_scan_f, ctr_scan_p;          // tile scans of the compaction and of the pack
   u64 n, nb, nout, nwords;             // sizes found on the device
   u32 vmin_key, vmax_key;              // range of retained finite values
   u32 cap_flag, pad0;
-  u32 done_front, pad2;                // compaction tiles counted (the last one scans)
+  u32 done_front, done_pack;           // tiles / chunks counted (the last one scans)
   u64 total;
   roix_eb_info eb;
 };
@@ -466,12 +450,13 @@ struct Item {
   u32* ftb;                            // [tiles] boundaries per compaction tile
   u64* ftno;                           // [tiles] first retained voxel of each tile
   u64* ftbo;                           // [tiles] first boundary of each tile
-  LookBack<2> lbsf;                    // look-back of the compaction tile scan (8192 a tile)
-  LookBack<1> lbp;                     // look-back of the pack: payload words per chunk
+  LookBack<2> lbsf, lbsp;              // look-backs of the tile scans (8192 entries a tile)
   u32* rno;                            // [rows] first retained voxel of the row in its tile
   u32* rbo;                            // [rows] first boundary of the row in its tile
   u32* crec;                           // [chunks] records per pack chunk (zeroed)
   u32* rbits;                          // [n / 32] record bitmap (bit k: symbol k is 0)
+  u32* cw;                             // [chunks] payload words per chunk
+  u64* cwoff;                          // [chunks] first payload word of each chunk
   u64* crecoff;                        // [chunks] first record of each chunk
   u32 rpt;                             // rows per front tile
   u32 vec;                             // rows are 16-byte aligned (vector loads)
@@ -480,7 +465,9 @@ struct Item {
                                        // bit 1 = T holds the plane after z = nz - 1
   u64 ftiles;                          // front tiles
   u32 fscan;                           // the counting kernel scans the tile totals
-                                       // (ftiles <= kInScanMax), not k_scan_pairs
+                                       // (ftiles <= kInScanMax), not k_scan_pairs<0>
+  u32 pscan;                           // k_pack_count scans the chunk word counts
+                                       // (chunks <= kInScanMax), not k_scan_pairs<1>
   u64 m_nx, m_spr, m_rpt, m_ny;        // recip64 of nx, of the 1024-voxel segments per
                                        // row, of rpt and of ny (divisions by multiply-high)
 };
@@ -700,10 +687,11 @@ __device__ __forceinline__ bool count_done(u32* done, u64 total) {
   if (last) __threadfence();  // the other tiles' totals after the count
   return last;
 }
-// Exclusive scans of the pairs (ftn, ftb) over compaction tiles into ftno,
-// ftbo and the item's n, nb, for items the counting kernel does not scan;
-// tiles_cap bounds the scan tiles of the batch.
-void launch_scan_pairs(const Launch& L, const Batch& B, u64 tiles_cap);
+// Exclusive scans of the pairs (ftn, ftb) over compaction tiles (mode 0: into
+// ftno, ftbo and the item's n, nb) or (cw, crec) over pack chunks (mode 1:
+// into cwoff, crecoff and the item's nwords, nout); tiles_cap bounds the scan
+// tiles of the batch.
+void launch_scan_pairs(const Launch& L, const Batch& B, int mode, u64 tiles_cap);
 void launch_threshold(const Launch& L, const Batch& B);
 void launch_dilate(const Launch& L, const Desc& d, const u32* T, u32* D, u64* popcount);
 void launch_front(const Launch& L, const Batch& B);
