@@ -987,9 +987,17 @@ struct RunList {
   u32 ppre[kRunCap + 1];  // prefix of the runs' head and tail elements
 };
 
-// Largest i < n with pre[i] <= x (pre[0] = 0, nondecreasing).
-__device__ __forceinline__ u32 run_of(const u32* pre, u32 n, u32 x) {
-  u32 lo = 0, hi = n;
+// Largest i < n with pre[i] <= x (pre nondecreasing), given pre[lo] <= x: a
+// lane's chunks rise, so the search gallops forward from the run of its
+// previous chunk and then bisects the last step.
+__device__ __forceinline__ u32 run_from(const u32* pre, u32 n, u32 x, u32 lo) {
+  u32 hi = lo + 1, step = 2;
+  while (hi < n && pre[hi] <= x) {
+    lo = hi;
+    hi = lo + step;
+    step <<= 1;
+  }
+  if (hi > n) hi = n;
   while (hi - lo > 1) {
     const u32 mid = (lo + hi) >> 1;
     if (pre[mid] <= x) lo = mid;
@@ -1032,6 +1040,7 @@ __device__ void flush_runs(RunList& rl, u32 nr, int lane, u32& kmin, u32& kmax) 
   __syncwarp();
   // whole 16-byte chunks, four per lane at a time (their loads issued together)
   constexpr int kU = 4;
+  u32 ri = 0;  // run of the lane's latest chunk
   for (u32 u0 = lane; u0 < cacc; u0 += 32 * kU) {
     u32 w[kU][5];
     u64 dq[kU];
@@ -1044,7 +1053,7 @@ __device__ void flush_runs(RunList& rl, u32 nr, int lane, u32& kmin, u32& kmax) 
 #pragma unroll
       for (int e = 0; e < 5; ++e) w[q][e] = 0u;
       if (u < cacc) {
-        const u32 i = run_of(rl.cpre, nr, u);
+        const u32 i = ri = run_from(rl.cpre, nr, u, ri);
         const u32 k = u - rl.cpre[i];
         const u32 len = rl.len[i];
         const u64 db = rl.dst[i];
@@ -1068,22 +1077,22 @@ __device__ void flush_runs(RunList& rl, u32 nr, int lane, u32& kmin, u32& kmax) 
             __funnelshift_r(w[q][0], w[q][1], sh), __funnelshift_r(w[q][1], w[q][2], sh),
             __funnelshift_r(w[q][2], w[q][3], sh), __funnelshift_r(w[q][3], w[q][4], sh));
         *reinterpret_cast<uint4*>(dq[q]) = v;
-        if constexpr (sizeof(TV) != 1) {  // (8-bit values carry no range)
-          const u32 qq[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            if constexpr (sizeof(TV) == 4) {
-              range_add<float>(__uint_as_float(qq[j]), kmin, kmax);
-            } else {
-              range_add<unsigned short>((unsigned short)(qq[j] & 0xffffu), kmin, kmax);
-              range_add<unsigned short>((unsigned short)(qq[j] >> 16), kmin, kmax);
-            }
-          }
-        }
+        if constexpr (sizeof(TV) == 4) {
+          range_add<float>(__uint_as_float(v.x), kmin, kmax);
+          range_add<float>(__uint_as_float(v.y), kmin, kmax);
+          range_add<float>(__uint_as_float(v.z), kmin, kmax);
+          range_add<float>(__uint_as_float(v.w), kmin, kmax);
+        } else if constexpr (sizeof(TV) == 2) {  // eight values: packed 16-bit minima, maxima
+          const u32 mn = __vminu2(__vminu2(v.x, v.y), __vminu2(v.z, v.w));
+          const u32 mx = __vmaxu2(__vmaxu2(v.x, v.y), __vmaxu2(v.z, v.w));
+          kmin = min(kmin, min(mn & 0xffffu, mn >> 16) + 1u);
+          kmax = max(kmax, max(mx & 0xffffu, mx >> 16) + 1u);
+        }  // (8-bit values carry no range)
       }
     }
   }
   // head and tail elements, four per lane at a time
+  ri = 0;
   for (u32 e0 = lane; e0 < pacc; e0 += 32 * kU) {
     TV vq[kU];
     TV* dp[kU];
@@ -1093,7 +1102,7 @@ __device__ void flush_runs(RunList& rl, u32 nr, int lane, u32& kmin, u32& kmax) 
       dp[q] = nullptr;
       vq[q] = TV(0);
       if (e < pacc) {
-        const u32 i = run_of(rl.ppre, nr, e);
+        const u32 i = ri = run_from(rl.ppre, nr, e, ri);
         const u32 k = e - rl.ppre[i];
         const u32 len = rl.len[i];
         const u64 db = rl.dst[i];
@@ -1167,20 +1176,21 @@ __global__ void __launch_bounds__(kThreads, 4) k_front_write(const __grid_consta
         flush_range(cur == 0xffffffffu ? nullptr : B.it[cur].rst, kmin, kmax, lane);
         cur = item;
       }
-      const Desc d = desc_of(B, I);
       const u64 r = g0 + j - B.row0[item];
-      const u32 W = (u32)d.W;
-      const bool end_extra = (d.nx & 31) == 0;
+      const u32 W = (u32)I.W, nx = (u32)I.nx;  // nx < 2^16 (boundaries are 16-bit)
+      const bool end_extra = (nx & 31) == 0;
+      const u32 tail = end_extra ? 0xffffffffu : (1u << (nx & 31)) - 1u;  // last word's bits
+      auto lmask = [&](u32 w) { return w == W - 1 ? tail : 0xffffffffu; };
       const u32* drow = (B.c.dilate ? I.D : I.T) + r * W;
-      const TV* irow = (const TV*)I.in + r * d.nx;
+      const TV* irow = (const TV*)I.in + (u64)r * nx;
       TV* __restrict__ P = (TV*)I.P;
       uint16_t* __restrict__ bounds = I.bounds;
       const u64 bounds_cap = I.bounds_cap;
       if (nbr == 0xffffffffu) {  // container too small for the counts: count again
         u32 rb = 0;
         for (u32 w = lane; w < W; w += 32) {
-          const u32 dv = __ldg(drow + w) & last_mask(d, w);
-          const u32 pv = w ? __ldg(drow + w - 1) & last_mask(d, w - 1) : 0u;
+          const u32 dv = __ldg(drow + w) & lmask(w);
+          const u32 pv = w ? __ldg(drow + w - 1) & lmask(w - 1) : 0u;
           rb += __popc(dv ^ ((dv << 1) | (pv >> 31))) + ((end_extra && w == W - 1) ? (dv >> 31) : 0u);
         }
         nbr = warp_sum(rb);
@@ -1192,8 +1202,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_front_write(const __grid_consta
         const u32 w = w0 + lane;
         u32 ev = 0u, ex = 0u;
         if (w < W) {
-          const u32 dv = __ldg(drow + w) & last_mask(d, w);
-          const u32 pv = w ? __ldg(drow + w - 1) & last_mask(d, w - 1) : 0u;
+          const u32 dv = __ldg(drow + w) & lmask(w);
+          const u32 pv = w ? __ldg(drow + w - 1) & lmask(w - 1) : 0u;
           ev = dv ^ ((dv << 1) | (pv >> 31));
           ex = (end_extra && w == W - 1) ? (dv >> 31) : 0u;
         }
@@ -1209,9 +1219,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_front_write(const __grid_consta
           ++o;
         }
         if (ex) {
-          if (ob + o < bounds_cap) bounds[ob + o] = (uint16_t)d.nx;
+          if (ob + o < bounds_cap) bounds[ob + o] = (uint16_t)nx;
           else set_status(B.status, ROIX_ECAPACITY);
-          if (fast && o < kListCap) lst[o] = (uint16_t)d.nx;
+          if (fast && o < kListCap) lst[o] = (uint16_t)nx;
         }
         bo += __shfl_sync(0xffffffffu, inc, 31);
       }
@@ -1241,7 +1251,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_front_write(const __grid_consta
       } else {
         // many short runs: lanes take the bits of one word at a time
         for (u32 w0 = 0; w0 < W; w0 += 32) {
-          const u32 dv_l = w0 + lane < W ? __ldg(drow + w0 + lane) & last_mask(d, w0 + lane) : 0u;
+          const u32 dv_l = w0 + lane < W ? __ldg(drow + w0 + lane) & lmask(w0 + lane) : 0u;
           const u32 pn = __popc(dv_l);
           const u32 sn = warp_incl_scan(pn) - pn;
           u32 nz = __ballot_sync(0xffffffffu, dv_l != 0u);
