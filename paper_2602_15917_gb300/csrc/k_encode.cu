@@ -862,6 +862,53 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__
 }
 
 // ------------------------------------------------------------------- pack
+// The records of chunk t of item I (a whole warp): the chunk's symbol-0
+// positions in order, from the record bitmap the symbol kernel wrote (all of
+// the lane's bitmap words, j = 32 g + lane, loaded before any is used; a warp
+// scan of their popcounts per group g), each written straight into the
+// container's record sections (keys at byte offset okey, values at oval) as
+// (k | kind << 63, payload) from record idx on; the code or the raw value is
+// formed again from the pixel section (or the staged codes).
+template <typename TV, bool FROM_Q>
+__device__ __forceinline__ void chunk_records(const Item& I, const Src<TV, FROM_Q>& src, u64 t,
+                                              u64 n, u32 C, u64 idx, u64 okey, u64 oval,
+                                              int lane) {
+  constexpr int kG = 16;  // 32-word groups of a chunk (C <= 16384)
+  const u32* __restrict__ rbits = I.rbits;
+  uint8_t* out = I.out;
+  const u64 cap = I.cap, rec_cap = I.rec_cap;
+  const u64 w0 = t * (C / 32);
+  const u32 nw = (u32)((umin(n, (t + 1) * (u64)C) - t * (u64)C + 31) / 32);
+  u32 zm[kG];
+#pragma unroll
+  for (int g = 0; g < kG; ++g) {
+    const u32 j = (u32)g * 32 + (u32)lane;
+    zm[g] = j < nw ? __ldg(rbits + w0 + j) : 0u;
+  }
+#pragma unroll
+  for (int g = 0; g < kG; ++g) {
+    if ((u32)g * 32 >= nw) break;
+    u32 z = zm[g];
+    const u32 cnt = __popc(z);
+    const u32 inc = warp_incl_scan(cnt);
+    u64 o = idx + inc - cnt;
+    while (z) {
+      const int q = __ffs(z) - 1;
+      z &= z - 1;
+      const u64 k = (w0 + (u64)g * 32 + lane) * 32 + q;
+      bool outl;
+      const int c = src.code(k, outl);
+      if (o < rec_cap) {
+        const u64 ok = okey + 8 * o, ov = oval + 4 * o;
+        if (ok + 8 <= cap) *reinterpret_cast<u64*>(out + ok) = k | (outl ? (1ull << 63) : 0ull);
+        if (ov + 4 <= cap) *reinterpret_cast<u32*>(out + ov) = outl ? src.raw_bits(k) : (u32)c;
+      }
+      ++o;
+    }
+    idx += __shfl_sync(0xffffffffu, inc, 31);
+  }
+}
+
 // Passes none of whose blocks waits on another: k_pack_count sums the code
 // lengths of every chunk; the chunks' word and record counts become offsets
 // (for items with at most kInScanMax chunks in the codebook kernel and in
@@ -941,29 +988,9 @@ __global__ void __launch_bounds__(kThreads) k_pack_count(const __grid_constant__
           src.fd = FastDiv(2u * (u32)src.e.eb_int);
         }
       }
-      const u32* __restrict__ rbits = I.rbits;
-      u64 idx = I.crecoff[t];
-      const u64 w0 = t * (C / 32), nwords = (umin(n, (t + 1) * (u64)C) - t * C + 31) / 32;
-      for (u64 j0 = 0; j0 < nwords; j0 += 32) {
-        const u64 j = j0 + lane;
-        u32 zm = j < nwords ? __ldg(rbits + w0 + j) : 0u;
-        const u32 cnt = __popc(zm);
-        const u32 inc = warp_incl_scan(cnt);
-        u64 o = idx + inc - cnt;
-        while (zm) {
-          const int q = __ffs(zm) - 1;
-          zm &= zm - 1;
-          const u64 k = (w0 + j) * 32 + q;
-          bool out;
-          const int c = src.code(k, out);
-          if (o < I.rec_cap) {
-            I.rk[o] = k | (out ? (1ull << 63) : 0ull);
-            I.rv[o] = out ? src.raw_bits(k) : (u32)c;
-          }
-          ++o;
-        }
-        idx += __shfl_sync(0xffffffffu, inc, 31);
-      }
+      // record sections of the container: offsets from the item's sizes
+      const Layout Lo = make_layout(B.c.S, I.rows, I.sizes[1], I.st->nout, (n + C - 1) / C, 0);
+      chunk_records<TV, FROM_Q>(I, src, t, n, C, I.crecoff[t], Lo.off_outk, Lo.off_outv, lane);
     }
     const u64 nch = pre[item + 1] - pre[item];
     if (I.pscan && count_done(&I.st->done_pack, nch)) {  // the item's chunk offsets
@@ -993,7 +1020,7 @@ __global__ void __launch_bounds__(kThreads) k_records(const __grid_constant__ Ba
   const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
   u32 cur = 0xffffffffu;
   Src<TV, FROM_Q> src{};
-  u64 n = 0;
+  u64 n = 0, okey = 0, oval = 0;
   for (u64 gt = warp0; gt < total; gt += nwarps) {
     const u32 item = find_item(pre, B.n, gt);
     const Item& I = B.it[item];
@@ -1011,54 +1038,90 @@ __global__ void __launch_bounds__(kThreads) k_records(const __grid_constant__ Ba
         src.fd = FastDiv(2u * (u32)src.e.eb_int);
       }
       n = umin(I.sizes[0], I.N);
+      const Layout Lo = make_layout(B.c.S, I.rows, I.sizes[1], I.st->nout, (n + C - 1) / C, 0);
+      okey = Lo.off_outk;
+      oval = Lo.off_outv;
     }
-    const u32* __restrict__ rbits = I.rbits;
-    u64 idx = I.crecoff[t];
-    const u64 w0 = t * (C / 32), nwords = (umin(n, (t + 1) * (u64)C) - t * C + 31) / 32;
-    for (u64 j0 = 0; j0 < nwords; j0 += 32) {
-      const u64 j = j0 + lane;
-      u32 zm = j < nwords ? __ldg(rbits + w0 + j) : 0u;
-      const u32 cnt = __popc(zm);
-      const u32 inc = warp_incl_scan(cnt);
-      u64 o = idx + inc - cnt;
-      while (zm) {
-        const int q = __ffs(zm) - 1;
-        zm &= zm - 1;
-        const u64 k = (w0 + j) * 32 + q;
-        bool out;
-        const int c = src.code(k, out);
-        if (o < I.rec_cap) {
-          I.rk[o] = k | (out ? (1ull << 63) : 0ull);
-          I.rv[o] = out ? src.raw_bits(k) : (u32)c;
-        }
-        ++o;
-      }
-      idx += __shfl_sync(0xffffffffu, inc, 31);
-    }
+    chunk_records<TV, FROM_Q>(I, src, t, n, C, I.crecoff[t], okey, oval, lane);
   }
 }
 
-// Persistent blocks, one chunk of C symbols at a time: thread i loads its
-// EPT = C / 256 consecutive symbols (16-byte loads) and keeps their table
-// entries (code left-justified, length in the low byte; the item's table in
-// shared memory) in registers; a block scan of the per-thread bit counts
-// gives each thread its bit offset; each thread ORs its codes into the
-// chunk's words (MSB first) in a shared buffer: the word being filled stays
-// in a register, a code is placed by one shift (and the part that runs past
-// the word by one funnel shift), and a full word leaves by one shared OR (so
-// the words shared with the neighbouring threads need no other care); the
-// words are stored with coalesced stores at the chunk's offset.
+// Bulk copies into shared memory (cp.async.bulk, completion on an mbarrier).
+__device__ __forceinline__ u32 smem_addr(const void* p) {
+  return (u32)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(u64* bar, u32 count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(u64* bar, u32 bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// global -> shared, 16-byte aligned addresses, bytes a multiple of 16
+__device__ __forceinline__ void bulk_to_smem(void* dst, const void* src, u32 bytes, u64* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+// true once the phase of the given parity has completed; false after `limit`
+// unsuccessful polls
+__device__ __forceinline__ bool mbar_wait(u64* bar, u32 parity, u32 limit) {
+  for (u32 i = 0; i < limit; ++i) {
+    u32 ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// Shared memory of k_pack: two buffers of C symbols, two code tables (each
+// rounded to 16 bytes), the chunk's stream.
+__host__ __device__ __forceinline__ u32 pack_tab_words(u32 S) { return (S + 3u) & ~3u; }
+__host__ __device__ __forceinline__ size_t pack_smem(u32 C, u32 S) {
+  return (size_t)4 * C + (size_t)8 * pack_tab_words(S) + ((size_t)C * kLMax / 64 + 2) * 8;
+}
+
+// Persistent blocks, one chunk of C symbols at a time, double-buffered: the
+// chunk's symbols (and the item's code table, when it differs from the one
+// already in that buffer) arrive in shared memory by bulk copies issued a
+// chunk ahead, and the ticket of the chunk after that is requested while the
+// current one is packed. Thread i takes its EPT = C / 256 consecutive symbols
+// and keeps their table entries (code left-justified, length in the low
+// byte) in registers; a block scan of the per-thread bit counts gives each
+// thread its bit offset; each thread ORs its codes into the chunk's words
+// (MSB first) in a shared buffer: the word being filled stays in a register,
+// a code is placed by one shift (and the part that runs past the word by one
+// funnel shift), and a full word leaves by one shared OR (so the words shared
+// with the neighbouring threads need no other care); the words are stored
+// with coalesced stores at the chunk's offset. Waits on the copies are
+// bounded (ROIX_ETIMEOUT).
 template <int EPT>
 __global__ void __launch_bounds__(kThreads, EPT <= 16 ? 5 : 1) k_pack(const __grid_constant__ Batch B) {
   if (halted(B.status)) return;  // a tile scan of this call gave up
-  extern __shared__ unsigned long long wb[];  // [C * kLMax / 64 + 2]
-  __shared__ u32 tab[kMaxSym];
+  extern __shared__ __align__(16) unsigned char pk_smem[];
   __shared__ u32 scratch[40];
-  __shared__ u64 s_tile;
+  __shared__ __align__(8) u64 mbar[2];
+  __shared__ u64 s_tick[2];
+  __shared__ u32 s_titem[2];  // item whose code table a buffer holds
+  __shared__ int s_bad;
   __shared__ u64 pre[kMaxBatch + 1];
   __shared__ u64 nval[kMaxBatch], pay0s[kMaxBatch], tab0s[kMaxBatch];
-  const u32 C = B.c.C, S = B.c.S;
+  const u32 C = B.c.C, S = B.c.S, tabw = pack_tab_words(S);
+  uint16_t* sbuf = reinterpret_cast<uint16_t*>(pk_smem);                          // [2][C]
+  u32* tabs = reinterpret_cast<u32*>(pk_smem + 4 * (size_t)C);                      // [2][tabw]
+  unsigned long long* wb =
+      reinterpret_cast<unsigned long long*>(pk_smem + 4 * (size_t)C + 8 * (size_t)tabw);
   const int tid = threadIdx.x;
+  const u32 limit = spin_limit_of(B.c.spin_limit);
   tile_prefix(B, pre, C, 1, nval);
   // per item: byte offsets of the payload and of the chunk table
   for (u32 i = tid; i < B.n; i += blockDim.x) {
@@ -1070,48 +1133,78 @@ __global__ void __launch_bounds__(kThreads, EPT <= 16 ? 5 : 1) k_pack(const __gr
   const u64 total = pre[B.n];
   const u32 wb_words = C * kLMax / 64 + 2;
   for (u32 i = tid; i < wb_words; i += blockDim.x) wb[i] = 0ull;
-  u32 cur = 0xffffffffu;
-  constexpr int NV = EPT % 8 == 0 ? EPT / 8 : 1;  // 16-byte loads per thread
-  while (true) {
-    if (tid == 0) s_tile = atomicAdd(&B.ctr[3], 1u);
-    __syncthreads();
-    const u64 gt = s_tile;
+  // (thread 0) the copies of ticket gt's chunk into buffer b
+  auto issue = [&](int b, u64 gt) {
+    const u32 item = find_item(pre, B.n, gt);
+    const Item& I = B.it[item];
+    const u64 t = gt - pre[item];
+    const u32 nsym = (u32)umin(C, nval[item] - t * C);
+    const u32 sb = (2u * nsym + 15u) & ~15u;  // (the symbol buffer has 16 bytes of slack)
+    const u32 tb = s_titem[b] != item ? 4u * tabw : 0u;
+    s_titem[b] = item;
+    mbar_expect_tx(&mbar[b], sb + tb);
+    bulk_to_smem(sbuf + (size_t)b * C, I.sym + t * C, sb, &mbar[b]);
+    if (tb) bulk_to_smem(tabs + (size_t)b * tabw, I.codes, tb, &mbar[b]);
+  };
+  if (tid == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_titem[0] = s_titem[1] = 0xffffffffu;
+    for (int b = 0; b < 2; ++b) {
+      const u64 gt = atomicAdd(&B.ctr[3], 1u);
+      s_tick[b] = gt;
+      if (gt < total) issue(b, gt);
+    }
+  }
+  __syncthreads();
+  u32 phase = 0u;  // bit b: parity of buffer b's next completion
+  for (int b = 0;; b ^= 1) {
+    const u64 gt = s_tick[b];
     if (gt >= total) break;
+    u64 nt = 0;  // the ticket buffer b takes next, requested now
+    if (tid == 0) nt = atomicAdd(&B.ctr[3], 1u);
     const u32 item = find_item(pre, B.n, gt);
     const Item& I = B.it[item];
     const u64 n = nval[item];
-    const uint16_t* __restrict__ sym = I.sym;
     const u32 t = (u32)(gt - pre[item]);  // chunk of the item (n < 2^32 C)
     const u64 k0 = (u64)t * C + (u64)tid * EPT;
-    // the chunk's symbols and word offset are requested before the item's
-    // code table is (re)loaded, so that the two latencies overlap
-    const bool whole = EPT % 8 == 0 && k0 + EPT <= n;
-    uint4 raw[NV];
-    if (whole) {
-#pragma unroll
-      for (int v = 0; v < NV; ++v) raw[v] = __ldg(reinterpret_cast<const uint4*>(sym + k0 + 8 * v));
-    }
     const u64 cw0 = __ldg(I.cwoff + t);
-    if (item != cur) {  // the item's code table into shared memory
-      cur = item;
-      for (u32 i = tid; i < S; i += blockDim.x) tab[i] = __ldg(I.codes + i);
+    const bool ok = mbar_wait(&mbar[b], (phase >> b) & 1u, limit);
+    if (__syncthreads_or(!ok)) {  // a copy never completed: give up, and wait for the other
+      if (tid == 0) {
+        s_bad = 1;
+        set_status(B.status, ROIX_ETIMEOUT);
+        if (s_tick[b ^ 1] < total) mbar_wait(&mbar[b ^ 1], (phase >> (b ^ 1)) & 1u, limit);
+      }
       __syncthreads();
+      return;
     }
+    phase ^= 1u << b;
+    const uint16_t* sy = sbuf + (size_t)b * C + (size_t)tid * EPT;
+    const u32* tab = tabs + (size_t)b * tabw;
+    const bool whole = k0 + EPT <= n;
     u32 e[EPT];
     u32 bits = 0;
-    if (whole) {
+    if constexpr (EPT % 8 == 0) {
+      if (whole) {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const u32 w4[4] = {raw[v].x, raw[v].y, raw[v].z, raw[v].w};
+        for (int v = 0; v < EPT / 8; ++v) {
+          const uint4 r = reinterpret_cast<const uint4*>(sy)[v];
+          const u32 w4[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          e[8 * v + 2 * q] = tab[w4[q] & 0xffffu];
-          e[8 * v + 2 * q + 1] = tab[w4[q] >> 16];
+          for (int q = 0; q < 4; ++q) {
+            e[8 * v + 2 * q] = tab[w4[q] & 0xffffu];
+            e[8 * v + 2 * q + 1] = tab[w4[q] >> 16];
+          }
         }
+      } else {
+#pragma unroll
+        for (int j = 0; j < EPT; ++j) e[j] = k0 + j < n ? tab[sy[j]] : 0u;
       }
     } else {
 #pragma unroll
-      for (int j = 0; j < EPT; ++j) e[j] = k0 + j < n ? tab[__ldg(sym + k0 + j)] : 0u;
+      for (int j = 0; j < EPT; ++j) e[j] = k0 + j < n ? tab[sy[j]] : 0u;
     }
 #pragma unroll
     for (int j = 0; j < EPT; ++j) bits += e[j] & 0xffu;
@@ -1149,7 +1242,11 @@ __global__ void __launch_bounds__(kThreads, EPT <= 16 ? 5 : 1) k_pack(const __gr
       const u64 o = pay + 4 * (u64)i;
       if (o + 4 <= cap) *reinterpret_cast<u32*>(out + o) = wb32[i];
     }
-    __syncthreads();
+    __syncthreads();  // buffer b and the stream are read: refill, clear
+    if (tid == 0) {
+      s_tick[b] = nt;
+      if (nt < total) issue(b, nt);
+    }
     for (u32 i = tid; i < (words + 1) / 2; i += blockDim.x) wb[i] = 0ull;
   }
 }
@@ -1167,9 +1264,6 @@ __global__ void __launch_bounds__(kThreads) k_finalize(const __grid_constant__ B
   State* st = I.st;
   uint8_t* out = I.out;
   const u64 cap = I.cap;
-  const u64 rec_cap = I.rec_cap;
-  const u64* __restrict__ rk = I.rk;
-  const u32* __restrict__ rv = I.rv;
   const uint16_t* counts_src = I.counts_src;
   const uint16_t* bounds_src = I.bounds_src;
   const u64 n = umin(I.sizes[0], I.N), nb = I.sizes[1], nout = st->nout, nwords = st->nwords;
@@ -1242,12 +1336,6 @@ __global__ void __launch_bounds__(kThreads) k_finalize(const __grid_constant__ B
     const u32 g = (u32)(gtid / 16), b = (u32)(gtid % 16);
     const u64 o = gaps[g][0] + b;
     if (o < gaps[g][1] && o < cap) out[o] = 0;
-  }
-  // outlier records
-  for (u64 i = gtid; i < umin(nout, rec_cap); i += gstride) {
-    const u64 ok = Lo.off_outk + 8 * i, ov = Lo.off_outv + 4 * i;
-    if (ok + 8 <= cap) *reinterpret_cast<u64*>(out + ok) = rk[i];
-    if (ov + 4 <= cap) *reinterpret_cast<u32*>(out + ov) = rv[i];
   }
   // geometry from the staged buffers
   if (counts_src)
@@ -1381,7 +1469,7 @@ void launch_pack(const Launch& L, const Batch& B, u64 ranges_cap) {
       else k_records<unsigned short, false><<<(unsigned)grid, kThreads, 0, L.stream>>>(B);
     }
   }
-  const size_t smem = ((size_t)B.c.C * kLMax / 64 + 2) * 8;  // the chunk's stream
+  const size_t smem = pack_smem(B.c.C, B.c.S);  // symbol buffers, code tables, stream
   auto run = [&](auto kernel) {
     cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);

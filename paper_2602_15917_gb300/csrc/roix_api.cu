@@ -204,7 +204,7 @@ struct ItemPlan {
   size_t crec, hist, sff, sfp;  // zeroed
   size_t sfa, spa;
   u64 stf, stp;  // scan tiles of the compaction and of the pack
-  size_t ftn, ftb, ftno, ftbo, rno, rbo, Dm, cw, cwoff, crecoff, rbits, T, P, sym, rk, rv, lens, codes;
+  size_t ftn, ftb, ftno, ftbo, rno, rbo, Dm, cw, cwoff, crecoff, rbits, T, P, sym, lens, codes;
   // largest-component scratch (keep = 1): zeroed flags and counters, then data
   size_t cf, cvars, ca, crr, cro, cxs, cxe, cpar, csize, T2;
   u64 ctiles;
@@ -276,10 +276,8 @@ BatchPlan plan_batch(const Desc& c, const roix_dims* dims, const u64* n_caps, co
     p.T = need_T ? a.take(4 * rows * W + 16) : 0;
     p.P = need_P ? a.take(esz * p.n_cap + 16) : 0;
     p.sym = a.take(2 * p.n_cap + 16);
-    p.rk = a.take(8 * (p.rec_cap + 1));
-    p.rv = a.take(4 * (p.rec_cap + 1));
     p.lens = a.take(c.S + 16);
-    p.codes = a.take(4 * (size_t)c.S);
+    p.codes = a.take(4 * (size_t)c.S + 16);  // (copied in 16-byte units)
     if (c.keep) {
       Desc di = c;
       di.nx = dims[i].nx;
@@ -340,8 +338,6 @@ void fill_batch(Batch& B, const Desc& c, const BatchPlan& bp, const roix_dims* d
     I.T = p.T ? (u32*)(ws + p.T) : nullptr;
     I.P = p.P ? (void*)(ws + p.P) : nullptr;
     I.sym = (uint16_t*)(ws + p.sym);
-    I.rk = (u64*)(ws + p.rk);
-    I.rv = (u32*)(ws + p.rv);
     I.rec_cap = p.rec_cap;
     I.hist = (unsigned long long*)(ws + p.hist);
     I.lens = (uint8_t*)(ws + p.lens);

@@ -429,9 +429,7 @@ struct Item {
   u32* T;                              // thresholded mask (fused path)
   void* P;                             // pixel section
   uint16_t* sym;
-  u64* rk;                             // records
-  u32* rv;
-  u64 rec_cap;
+  u64 rec_cap;                         // records the container can hold
   unsigned long long* hist;
   uint8_t* lens;
   u32* codes;

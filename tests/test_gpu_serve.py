@@ -78,7 +78,8 @@ def test_server_refuses_request_larger_than_a_lane():
         pytest.skip("no GPU")
     import paper_2602_15917_gb300 as roix
     srv = roix.RoixServer(0, hbm_budget=64 << 20, lanes=2, max_batch=8)
-    x = torch.zeros((64, 256, 256), dtype=torch.float32, device="cuda")  # 16 MiB input
+    # 32 MiB input: its pixel section alone fills a 32 MiB lane
+    x = torch.zeros((128, 256, 256), dtype=torch.float32, device="cuda")
     out = torch.empty(x.numel() * 4 + 65536, dtype=torch.uint8, device="cuda")
     assert srv.submit(1, x, out, eb=1e-3) == 2  # ROIX_ENOMEM: never fits 32 MiB
     srv.close()
