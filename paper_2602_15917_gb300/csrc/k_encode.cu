@@ -157,28 +157,32 @@ __device__ __forceinline__ u32 symbol_of(int c, int prev, bool out, u32 R) {
   return (dd + R - 1u < 2u * R - 1u) ? dd + R : 0u;
 }
 
-// Segments of kQuantTile values, every item's segments in order: prefix of
-// ceil(n_i / per) / group over the items (n_i found by the compaction),
-// computed by each block at start.
-__device__ __forceinline__ void tile_prefix(const Batch& B, u64* pre, u64 per, u64 group,
+// Segments of `per` values (a power of two), every item's segments in order:
+// prefix of ceil(n_i / per) over the items (n_i found by the compaction),
+// formed by warp 0 of each block at start (lane l holds items 2l and 2l + 1;
+// kMaxBatch = 64) with one warp scan.
+__device__ __forceinline__ void tile_prefix(const Batch& B, u64* pre, u64 per,
                                             u64* counts = nullptr) {
-  // every item's count read by a thread of its own (the loads overlap), the
-  // prefix summed by one thread from shared memory
-  for (u32 i = threadIdx.x; i < B.n; i += blockDim.x) {
-    const Item& I = B.it[i];
-    const u64 n = umin(I.sizes[0], I.N);
-    pre[i + 1] = ((n + per - 1) / per + group - 1) / group;
-    if (counts) counts[i] = n;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    u64 acc = 0;
-    for (u32 i = 0; i < B.n; ++i) {
-      const u64 c = pre[i + 1];
-      pre[i] = acc;
-      acc += c;
+  static_assert(kMaxBatch <= 64, "two items per lane");
+  if (threadIdx.x < 32) {
+    const u32 lane = threadIdx.x, sh = (u32)(__ffsll((long long)per) - 1);
+    u64 c[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const u32 i = 2 * lane + k;
+      c[k] = 0;
+      if (i < B.n) {
+        const Item& I = B.it[i];
+        const u64 n = umin(I.sizes[0], I.N);
+        c[k] = (n + per - 1) >> sh;
+        if (counts) counts[i] = n;
+      }
     }
-    pre[B.n] = acc;
+    const u64 inc = warp_incl_scan<u64>(c[0] + c[1]);
+    const u64 ex = inc - c[0] - c[1];
+    if (2 * lane < B.n) pre[2 * lane] = ex;
+    if (2 * lane + 1 < B.n) pre[2 * lane + 1] = ex + c[0];
+    if (lane == 31) pre[B.n] = inc;
   }
   __syncthreads();
 }
@@ -311,7 +315,7 @@ k_symbols(const __grid_constant__ Batch B) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   u32* h = hsm + (u32)warp * S;
   for (u32 i = lane; i < S; i += 32) h[i] = 0;
-  tile_prefix(B, pre, kQuantTile, 1);
+  tile_prefix(B, pre, kQuantTile);
   const u64 total = pre[B.n];
   u32 cur = 0xffffffffu;
   u32 since_flush = 0;
@@ -526,74 +530,60 @@ __device__ long long g_cb_probe[16];
 #define CB_MARK(i)
 #endif
 
-// Two-queue Huffman construction (van Leeuwen 1976) by one warp, in rounds.
-// The sequential form pops the two lightest fronts of the leaf queue (leaves
-// 0..m-1 sorted ascending) and of the internal queue (nodes m.. in creation
-// order), a leaf winning ties, and appends their sum to the internal queue.
-// Every node created from now on weighs at least 2 x_min (x_min = the lighter
-// front), so every known leaf or internal node of weight <= T = 2 x_min is
-// popped before any of them, in merged order (weight, leaves before internal
-// nodes on a tie, queue order within a queue); a round therefore takes those
-// K nodes at once (K rounded down to even; the odd one waits for the next
-// round), merges the two runs (merge path: each lane finds where its share of
-// the merged order starts by a binary search on the diagonal, then merges its
-// share; a leaf goes first when it is no heavier than the internal node) and
+// Two-queue Huffman construction (van Leeuwen 1976) by the whole block, in
+// rounds. The sequential form pops the two lightest fronts of the leaf queue
+// (leaves 0..m-1 sorted ascending) and of the internal queue (nodes m.. in
+// creation order), a leaf winning ties, and appends their sum to the internal
+// queue. Every node created from now on weighs at least 2 x_min (x_min = the
+// lighter front), so every known leaf or internal node of weight <= T =
+// 2 x_min is popped before any of them, in merged order (weight, leaves before
+// internal nodes on a tie, queue order within a queue); a round therefore
+// takes those K nodes at once (K rounded down to even; the odd one waits for
+// the next round), places each in the merged order by its rank (a leaf: its
+// index plus the internal nodes lighter than it; an internal node: its index
+// plus the leaves no heavier than it; binary searches in the other run), and
 // pairs merged positions 2p, 2p + 1 into new nodes m + created + p, which is
 // the sequential algorithm's order of pops and of creations. When K < 2 the two
 // lightest fronts are popped as one sequential step. Rounds: about
-// log2(total weight / lightest leaf) plus those steps. par[] receives every
-// node's parent; mid[] (2m entries) is scratch; rstart[] (rounds + 1 entries)
-// receives each round's first created node and *nrounds their number, for the
-// depths. All 32 lanes call it.
+// log2(total weight / lightest leaf) plus those steps, each a few block
+// barriers. par[] receives every node's parent; mid[] (2m entries) is scratch;
+// rstart[] (rounds + 1 entries) receives each round's first created node and
+// *nrounds their number, for the depths. Called by every thread of the block.
 constexpr u64 kNoWeight = ~0ull;
 
-// Number of a[lo..hi) (ascending) that are <= t (le) or < t (!le), by the warp:
-// two rounds of 32 probes (ranges up to 1024; longer ones continue by 32^2).
+// Number of i in [0, len) with pred(i), by the block (len uniform); with
+// `prefix`, pred holds on a prefix of the range, and counting stops at the
+// first block-sized part where it fails.
 template <typename F>
-__device__ __forceinline__ u32 warp_count_below(F a, u32 lo, u32 hi, u64 t, bool le, int lane) {
-  u32 base = lo;
-  u32 len = hi - lo;
-  while (len > 32) {
-    const u32 stride = (len + 31) / 32;
-    const u32 i = base + (u32)lane * stride;
-    bool in = false;
-    if (i < base + len) {
-      const u64 v = a(i);
-      in = le ? v <= t : v < t;
-    }
-    const u32 b = __ballot_sync(0xffffffffu, in);
-    const u32 k = (u32)__popc(b);  // probes in the prefix (the array ascends)
-    if (k == 0) return base - lo;
-    const u32 nb = base + (k - 1) * stride;  // the last probe inside the prefix
-    len = min(stride, base + len - nb);
-    base = nb;
+__device__ __forceinline__ u32 block_count(u32 len, bool prefix, F pred) {
+  u32 c = 0;
+  for (u32 b0 = 0; b0 < len; b0 += blockDim.x) {
+    const u32 i = b0 + threadIdx.x;
+    const u32 k = (u32)__syncthreads_count(i < len && pred(i));
+    c += k;
+    if (prefix && k < min(blockDim.x, len - b0)) break;
   }
-  bool in = false;
-  if ((u32)lane < len) {
-    const u64 v = a(base + lane);
-    in = le ? v <= t : v < t;
-  }
-  return base - lo + (u32)__popc(__ballot_sync(0xffffffffu, in));
+  return c;
 }
 
-__device__ void huffman_merge_warp(const u64* key, u64* wi, int32_t* par, int32_t* mid,
-                                   u32* rstart, u32* nrounds, u32 m) {
-  const int lane = threadIdx.x & 31;
+__device__ void huffman_merge_block(const u64* key, u64* wi, int32_t* par, int32_t* mid,
+                                    u32* rstart, u32* nrounds, u32 m) {
+  const u32 tid = threadIdx.x;
   auto lw = [&](u32 i) -> u64 { return key[i] >> 16; };
-  auto iw = [&](u32 i) -> u64 { return wi[i]; };
   u32 lf = 0, in = 0, created = 0, rounds = 0;
   while (created + 1 < m) {
-    if (lane == 0) rstart[rounds] = created;  // first node of this round
+    if (tid == 0) rstart[rounds] = created;  // first node of this round
     ++rounds;
     const u64 a0 = lf < m ? lw(lf) : kNoWeight;
     const u64 b0 = in < created ? wi[in] : kNoWeight;
     const u64 xmin = a0 < b0 ? a0 : b0;
     const u64 T = xmin > (kNoWeight >> 1) ? kNoWeight : 2 * xmin;
-    const u32 na = warp_count_below(lw, lf, m, T, true, lane);
-    const u32 nb = warp_count_below(iw, in, created, T, true, lane);
+    const u32 na = block_count(m - lf, true, [&](u32 i) { return lw(lf + i) <= T; });
+    const u32 nb = block_count(created - in, true, [&](u32 i) { return wi[in + i] <= T; });
     const u32 K = na + nb;
     if (K < 2) {
-      // one sequential step: the two lightest fronts, a leaf winning ties
+      // one sequential step: the two lightest fronts, a leaf winning ties (every
+      // thread follows it; thread 0 writes)
       u32 l = lf, q = in;
       int32_t id[2];
       u64 w[2];
@@ -609,83 +599,79 @@ __device__ void huffman_merge_warp(const u64* key, u64* wi, int32_t* par, int32_
           ++q;
         }
       }
-      if (lane == 0) {
+      __syncthreads();  // every thread has read the fronts
+      if (tid == 0) {
         wi[created] = w[0] + w[1];
         par[id[0]] = (int32_t)(m + created);
         par[id[1]] = (int32_t)(m + created);
       }
-      __syncwarp();
+      __syncthreads();
       lf = l;
       in = q;
       ++created;
       continue;
     }
     const u32 P = K >> 1, out = 2 * P;
-    // merge path: lane l writes merged positions [o0, o1); its start splits
-    // into ia leaves and o0 - ia internal nodes (a leaf goes first when it is
-    // no heavier than the internal node); then a sequential merge
-    const u32 per = (out + 31) >> 5;
-    const u32 o0 = min(out, (u32)lane * per), o1 = min(out, o0 + per);
-    u32 lo = o0 > nb ? o0 - nb : 0u, hi = min(o0, na);
-    while (lo < hi) {  // the largest ia with leaf ia - 1 before internal o0 - ia
-      const u32 c = (lo + hi + 1) >> 1;
-      const u32 jb = o0 - c;
-      if (jb >= nb || lw(lf + c - 1) <= wi[in + jb]) lo = c;
-      else hi = c - 1;
-    }
-    u32 ia = lo, ib = o0 - lo, taken = 0;
-    u64 wa = ia < na ? lw(lf + ia) : kNoWeight, wb = ib < nb ? wi[in + ib] : kNoWeight;
-    for (u32 o = o0; o < o1; ++o) {
-      if (ia < na && (ib >= nb || wa <= wb)) {
-        mid[o] = (int32_t)(lf + ia);
-        ++ia;
-        ++taken;
-        wa = ia < na ? lw(lf + ia) : kNoWeight;
-      } else {
-        mid[o] = (int32_t)(m + in + ib);
-        ++ib;
-        wb = ib < nb ? wi[in + ib] : kNoWeight;
+    // merged positions of the K nodes; those below `out` are paired
+    const u32 ca = block_count(K, false, [&](u32 e) {
+      if (e < na) {  // leaf lf + e: after the internal nodes strictly lighter
+        const u64 w = lw(lf + e);
+        u32 lo = 0, hi = nb;
+        while (lo < hi) {
+          const u32 c = (lo + hi) >> 1;
+          if (wi[in + c] < w) lo = c + 1;
+          else hi = c;
+        }
+        const u32 pos = e + lo;
+        if (pos < out) mid[pos] = (int32_t)(lf + e);
+        return pos < out;
       }
-    }
-    const u32 ca = warp_sum(taken);  // leaves among the paired nodes
-    __syncwarp();
-    for (u32 p = lane; p < P; p += 32) {
+      const u32 j = e - na;  // internal node in + j: after the leaves no heavier
+      const u64 w = wi[in + j];
+      u32 lo = 0, hi = na;
+      while (lo < hi) {
+        const u32 c = (lo + hi) >> 1;
+        if (lw(lf + c) <= w) lo = c + 1;
+        else hi = c;
+      }
+      const u32 pos = j + lo;
+      if (pos < out) mid[pos] = (int32_t)(m + in + j);
+      return false;
+    });  // (its barriers also order the mid[] writes before the pairing)
+    for (u32 p = tid; p < P; p += blockDim.x) {
       const u32 x = (u32)mid[2 * p], y = (u32)mid[2 * p + 1];
       const u64 wx = x < m ? lw(x) : wi[x - m], wy = y < m ? lw(y) : wi[y - m];
       wi[created + p] = wx + wy;
       par[x] = (int32_t)(m + created + p);
       par[y] = (int32_t)(m + created + p);
     }
-    __syncwarp();
+    __syncthreads();
     lf += ca;
     in += out - ca;
     created += P;
   }
-  if (lane == 0) {
+  if (tid == 0) {
     par[2 * m - 2] = -1;
     rstart[rounds] = created;
     *nrounds = rounds;
   }
-  __syncwarp();
+  __syncthreads();
 }
 
-// Depth of every node (its distance to the root) from the rounds of
-// huffman_merge_warp: a node's parent was created in a later round, so the
-// rounds are taken last to first, each round's nodes in parallel, then the
-// leaves. dep[] receives 2m - 1 depths. All 32 lanes call it.
-__device__ void huffman_depths_warp(const int32_t* par, int32_t* dep, const u32* rstart,
-                                    u32 nrounds, u32 m) {
-  const int lane = threadIdx.x & 31;
-  if (lane == 0) dep[2 * m - 2] = 0;
-  __syncwarp();
+// Depths by the rounds in reverse (a node's parent is created in a later
+// round), then the leaves; by the whole block.
+__device__ void huffman_depths_block(const int32_t* par, int32_t* dep, const u32* rstart,
+                                     u32 nrounds, u32 m) {
+  if (threadIdx.x == 0) dep[2 * m - 2] = 0;
+  __syncthreads();
   for (int r = (int)nrounds - 1; r >= 0; --r) {
-    for (u32 v = rstart[r] + (u32)lane; v < rstart[r + 1]; v += 32) {
+    for (u32 v = rstart[r] + threadIdx.x; v < rstart[r + 1]; v += blockDim.x) {
       if (v + 2 < m) dep[m + v] = dep[par[m + v]] + 1;  // the root (v = m - 2) keeps 0
     }
-    __syncwarp();
+    __syncthreads();
   }
-  for (u32 i = lane; i < m; i += 32) dep[i] = dep[par[i]] + 1;
-  __syncwarp();
+  for (u32 i = threadIdx.x; i < m; i += blockDim.x) dep[i] = dep[par[i]] + 1;
+  __syncthreads();
 }
 
 __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__ Batch B) {
@@ -748,15 +734,12 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__
       bl[1] = 1;
     }
   } else if (m >= 2) {
-    // two-queue construction by warp 0, in rounds (dep is scratch until the
+    // two-queue construction by the block, in rounds (dep is scratch until the
     // depths, bl holds the rounds' first nodes until the lengths are counted)
     __shared__ u32 s_rounds;
-    if (tid < 32) {
-      huffman_merge_warp(key, wint, par, dep, bl, &s_rounds, m);
-      CB_MARK(3)
-      huffman_depths_warp(par, dep, bl, s_rounds, m);
-    }
-    __syncthreads();
+    huffman_merge_block(key, wint, par, dep, bl, &s_rounds, m);
+    CB_MARK(3)
+    huffman_depths_block(par, dep, bl, s_rounds, m);
     CB_MARK(4)
     for (u32 i = tid; i < bl_entries(S); i += kCbThreads) bl[i] = 0;
     __syncthreads();
@@ -934,7 +917,7 @@ __global__ void __launch_bounds__(kThreads) k_pack_count(const __grid_constant__
   __shared__ u64 nn[kMaxBatch];
   const u32 C = B.c.C;
   const int lane = threadIdx.x & 31;
-  tile_prefix(B, pre, C, 1, nn);
+  tile_prefix(B, pre, C, nn);
   const u64 total = pre[B.n];
   const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
   constexpr u32 kIn = 4;  // vector loads of a lane in flight at once
@@ -1014,7 +997,7 @@ __global__ void __launch_bounds__(kThreads) k_records(const __grid_constant__ Ba
   __shared__ u64 pre[kMaxBatch + 1];
   const u32 C = B.c.C;
   const int lane = threadIdx.x & 31;
-  tile_prefix(B, pre, C, 1);
+  tile_prefix(B, pre, C);
   const u64 total = pre[B.n];
   const u64 warp0 = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
@@ -1112,6 +1095,7 @@ __global__ void __launch_bounds__(kThreads, EPT <= 16 ? 5 : 1) k_pack(const __gr
   __shared__ __align__(8) u64 mbar[2];
   __shared__ u64 s_tick[2];
   __shared__ u32 s_titem[2];  // item whose code table a buffer holds
+  __shared__ u32 s_item[2], s_t[2];  // a buffer's chunk: item, chunk of the item
   __shared__ int s_bad;
   __shared__ u64 pre[kMaxBatch + 1];
   __shared__ u64 nval[kMaxBatch], pay0s[kMaxBatch], tab0s[kMaxBatch];
@@ -1122,7 +1106,7 @@ __global__ void __launch_bounds__(kThreads, EPT <= 16 ? 5 : 1) k_pack(const __gr
       reinterpret_cast<unsigned long long*>(pk_smem + 4 * (size_t)C + 8 * (size_t)tabw);
   const int tid = threadIdx.x;
   const u32 limit = spin_limit_of(B.c.spin_limit);
-  tile_prefix(B, pre, C, 1, nval);
+  tile_prefix(B, pre, C, nval);
   // per item: byte offsets of the payload and of the chunk table
   for (u32 i = tid; i < B.n; i += blockDim.x) {
     const Item& I = B.it[i];
@@ -1138,6 +1122,8 @@ __global__ void __launch_bounds__(kThreads, EPT <= 16 ? 5 : 1) k_pack(const __gr
     const u32 item = find_item(pre, B.n, gt);
     const Item& I = B.it[item];
     const u64 t = gt - pre[item];
+    s_item[b] = item;
+    s_t[b] = (u32)t;  // (n < 2^32 C)
     const u32 nsym = (u32)umin(C, nval[item] - t * C);
     const u32 sb = (2u * nsym + 15u) & ~15u;  // (the symbol buffer has 16 bytes of slack)
     const u32 tb = s_titem[b] != item ? 4u * tabw : 0u;
@@ -1164,10 +1150,9 @@ __global__ void __launch_bounds__(kThreads, EPT <= 16 ? 5 : 1) k_pack(const __gr
     if (gt >= total) break;
     u64 nt = 0;  // the ticket buffer b takes next, requested now
     if (tid == 0) nt = atomicAdd(&B.ctr[3], 1u);
-    const u32 item = find_item(pre, B.n, gt);
+    const u32 item = s_item[b], t = s_t[b];
     const Item& I = B.it[item];
     const u64 n = nval[item];
-    const u32 t = (u32)(gt - pre[item]);  // chunk of the item (n < 2^32 C)
     const u64 k0 = (u64)t * C + (u64)tid * EPT;
     const u64 cw0 = __ldg(I.cwoff + t);
     const bool ok = mbar_wait(&mbar[b], (phase >> b) & 1u, limit);
