@@ -530,7 +530,7 @@ __device__ long long g_cb_probe[16];
 #define CB_MARK(i)
 #endif
 
-// Two-queue Huffman construction (van Leeuwen 1976) by the whole block, in
+// Two-queue Huffman construction (van Leeuwen 1976) by a team of threads, in
 // rounds. The sequential form pops the two lightest fronts of the leaf queue
 // (leaves 0..m-1 sorted ascending) and of the internal queue (nodes m.. in
 // creation order), a leaf winning ties, and appends their sum to the internal
@@ -545,28 +545,46 @@ __device__ long long g_cb_probe[16];
 // pairs merged positions 2p, 2p + 1 into new nodes m + created + p, which is
 // the sequential algorithm's order of pops and of creations. When K < 2 the two
 // lightest fronts are popped as one sequential step. Rounds: about
-// log2(total weight / lightest leaf) plus those steps, each a few block
+// log2(total weight / lightest leaf) plus those steps, each a few team
 // barriers. par[] receives every node's parent; mid[] (2m entries) is scratch;
 // rstart[] (rounds + 1 entries) receives each round's first created node and
-// *nrounds their number, for the depths. Called by every thread of the block.
+// *nrounds their number, for the depths. Called by every thread of the team.
 constexpr u64 kNoWeight = ~0ull;
 
-// Number of i in [0, len) with pred(i), by the block (len uniform); with
+// The construction runs on a team of the block's first kTeam threads, which
+// synchronise on named barrier 1 (a round's steps are short: a larger team
+// spends more issue slots than it saves).
+constexpr u32 kTeam = 128;
+__device__ __forceinline__ void team_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kTeam) : "memory");
+}
+// Number of team threads whose p is true (a barrier of the team).
+__device__ __forceinline__ u32 team_count(bool p) {
+  u32 r;
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.u32 q, %1, 0;\n bar.red.popc.u32 %0, 1, %2, q;\n}\n"
+      : "=r"(r)
+      : "r"((u32)p), "n"(kTeam)
+      : "memory");
+  return r;
+}
+
+// Number of i in [0, len) with pred(i), by the team (len uniform); with
 // `prefix`, pred holds on a prefix of the range, and counting stops at the
-// first block-sized part where it fails.
+// first team-sized part where it fails.
 template <typename F>
-__device__ __forceinline__ u32 block_count(u32 len, bool prefix, F pred) {
+__device__ __forceinline__ u32 team_count_range(u32 len, bool prefix, F pred) {
   u32 c = 0;
-  for (u32 b0 = 0; b0 < len; b0 += blockDim.x) {
+  for (u32 b0 = 0; b0 < len; b0 += kTeam) {
     const u32 i = b0 + threadIdx.x;
-    const u32 k = (u32)__syncthreads_count(i < len && pred(i));
+    const u32 k = team_count(i < len && pred(i));
     c += k;
-    if (prefix && k < min(blockDim.x, len - b0)) break;
+    if (prefix && k < min(kTeam, len - b0)) break;
   }
   return c;
 }
 
-__device__ void huffman_merge_block(const u64* key, u64* wi, int32_t* par, int32_t* mid,
+__device__ void huffman_merge_team(const u64* key, u64* wi, int32_t* par, int32_t* mid,
                                     u32* rstart, u32* nrounds, u32 m) {
   const u32 tid = threadIdx.x;
   auto lw = [&](u32 i) -> u64 { return key[i] >> 16; };
@@ -578,8 +596,8 @@ __device__ void huffman_merge_block(const u64* key, u64* wi, int32_t* par, int32
     const u64 b0 = in < created ? wi[in] : kNoWeight;
     const u64 xmin = a0 < b0 ? a0 : b0;
     const u64 T = xmin > (kNoWeight >> 1) ? kNoWeight : 2 * xmin;
-    const u32 na = block_count(m - lf, true, [&](u32 i) { return lw(lf + i) <= T; });
-    const u32 nb = block_count(created - in, true, [&](u32 i) { return wi[in + i] <= T; });
+    const u32 na = team_count_range(m - lf, true, [&](u32 i) { return lw(lf + i) <= T; });
+    const u32 nb = team_count_range(created - in, true, [&](u32 i) { return wi[in + i] <= T; });
     const u32 K = na + nb;
     if (K < 2) {
       // one sequential step: the two lightest fronts, a leaf winning ties (every
@@ -599,13 +617,13 @@ __device__ void huffman_merge_block(const u64* key, u64* wi, int32_t* par, int32
           ++q;
         }
       }
-      __syncthreads();  // every thread has read the fronts
+      team_sync();  // every thread has read the fronts
       if (tid == 0) {
         wi[created] = w[0] + w[1];
         par[id[0]] = (int32_t)(m + created);
         par[id[1]] = (int32_t)(m + created);
       }
-      __syncthreads();
+      team_sync();
       lf = l;
       in = q;
       ++created;
@@ -613,7 +631,7 @@ __device__ void huffman_merge_block(const u64* key, u64* wi, int32_t* par, int32
     }
     const u32 P = K >> 1, out = 2 * P;
     // merged positions of the K nodes; those below `out` are paired
-    const u32 ca = block_count(K, false, [&](u32 e) {
+    const u32 ca = team_count_range(K, false, [&](u32 e) {
       if (e < na) {  // leaf lf + e: after the internal nodes strictly lighter
         const u64 w = lw(lf + e);
         u32 lo = 0, hi = nb;
@@ -638,14 +656,14 @@ __device__ void huffman_merge_block(const u64* key, u64* wi, int32_t* par, int32
       if (pos < out) mid[pos] = (int32_t)(m + in + j);
       return false;
     });  // (its barriers also order the mid[] writes before the pairing)
-    for (u32 p = tid; p < P; p += blockDim.x) {
+    for (u32 p = tid; p < P; p += kTeam) {
       const u32 x = (u32)mid[2 * p], y = (u32)mid[2 * p + 1];
       const u64 wx = x < m ? lw(x) : wi[x - m], wy = y < m ? lw(y) : wi[y - m];
       wi[created + p] = wx + wy;
       par[x] = (int32_t)(m + created + p);
       par[y] = (int32_t)(m + created + p);
     }
-    __syncthreads();
+    team_sync();
     lf += ca;
     in += out - ca;
     created += P;
@@ -655,23 +673,23 @@ __device__ void huffman_merge_block(const u64* key, u64* wi, int32_t* par, int32
     rstart[rounds] = created;
     *nrounds = rounds;
   }
-  __syncthreads();
+  team_sync();
 }
 
 // Depths by the rounds in reverse (a node's parent is created in a later
-// round), then the leaves; by the whole block.
-__device__ void huffman_depths_block(const int32_t* par, int32_t* dep, const u32* rstart,
-                                     u32 nrounds, u32 m) {
+// round), then the leaves; by the team.
+__device__ void huffman_depths_team(const int32_t* par, int32_t* dep, const u32* rstart,
+                                    u32 nrounds, u32 m) {
   if (threadIdx.x == 0) dep[2 * m - 2] = 0;
-  __syncthreads();
+  team_sync();
   for (int r = (int)nrounds - 1; r >= 0; --r) {
-    for (u32 v = rstart[r] + threadIdx.x; v < rstart[r + 1]; v += blockDim.x) {
+    for (u32 v = rstart[r] + threadIdx.x; v < rstart[r + 1]; v += kTeam) {
       if (v + 2 < m) dep[m + v] = dep[par[m + v]] + 1;  // the root (v = m - 2) keeps 0
     }
-    __syncthreads();
+    team_sync();
   }
-  for (u32 i = threadIdx.x; i < m; i += blockDim.x) dep[i] = dep[par[i]] + 1;
-  __syncthreads();
+  for (u32 i = threadIdx.x; i < m; i += kTeam) dep[i] = dep[par[i]] + 1;
+  team_sync();
 }
 
 __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__ Batch B) {
@@ -734,12 +752,15 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const __grid_constant__
       bl[1] = 1;
     }
   } else if (m >= 2) {
-    // two-queue construction by the block, in rounds (dep is scratch until the
+    // two-queue construction by the team, in rounds (dep is scratch until the
     // depths, bl holds the rounds' first nodes until the lengths are counted)
     __shared__ u32 s_rounds;
-    huffman_merge_block(key, wint, par, dep, bl, &s_rounds, m);
-    CB_MARK(3)
-    huffman_depths_block(par, dep, bl, s_rounds, m);
+    if (tid < (int)kTeam) {
+      huffman_merge_team(key, wint, par, dep, bl, &s_rounds, m);
+      CB_MARK(3)
+      huffman_depths_team(par, dep, bl, s_rounds, m);
+    }
+    __syncthreads();
     CB_MARK(4)
     for (u32 i = tid; i < bl_entries(S); i += kCbThreads) bl[i] = 0;
     __syncthreads();
