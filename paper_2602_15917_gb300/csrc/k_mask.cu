@@ -84,6 +84,55 @@ __device__ __forceinline__ void thr_segment(const Desc& d, const TV* __restrict_
   if ((u32)lane < nw) T[r * d.W + (x0 >> 5) + lane] = mine;
 }
 
+// Non-pass flags of two uint16 values in one word: bits 15 and 31 set where
+// the value lies outside [lo, hi] (lo2, hi2: the bounds in both halves). The
+// value is clamped with packed 16-bit max and min, and a half differs from its
+// clamp exactly when it fails; a half is nonzero when its low 15 bits plus
+// 0x7fff carry into its top bit, or the top bit is set already.
+__device__ __forceinline__ u32 fail2_u16(u32 v, u32 lo2, u32 hi2) {
+  u32 c;
+  asm("max.u16x2 %0, %1, %2;" : "=r"(c) : "r"(v), "r"(lo2));
+  asm("min.u16x2 %0, %0, %1;" : "+r"(c) : "r"(hi2));
+  const u32 e = c ^ v;
+  return ((e & 0x7fff7fffu) + 0x7fff7fffu) | e;
+}
+
+// Four non-pass flags (bits 15, 31 of f0, then of f1) as bits 0..3: the
+// bytes holding them gathered by one byte permute, then their top bits
+// collected by one multiply (the products land on distinct bit positions, so
+// nothing carries into bits 28..31).
+__device__ __forceinline__ u32 flags4(u32 f0, u32 f1) {
+  const u32 p = __byte_perm(f0, f1, 0x7531) & 0x80808080u;
+  return (p * 0x00204081u) >> 28;
+}
+
+// The kPer pass bits of one 16-byte vector of values (bit k = element k).
+template <typename TV>
+__device__ __forceinline__ u32 vec_pass_bits(const PassTest& pt, const uint4& v) {
+  u32 bits = 0;
+  if constexpr (sizeof(TV) == 2) {
+    if (pt.lo > 65535u) return 0u;  // nothing passes
+    const u32 lo = pt.lo, hi = pt.lo + pt.span;  // hi <= 65535
+    const u32 lo2 = lo | (lo << 16), hi2 = hi | (hi << 16);
+    const u32 f = flags4(fail2_u16(v.x, lo2, hi2), fail2_u16(v.y, lo2, hi2)) |
+                  (flags4(fail2_u16(v.z, lo2, hi2), fail2_u16(v.w, lo2, hi2)) << 4);
+    return ~f & 0xffu;
+  } else if constexpr (sizeof(TV) == 4) {
+    bits = (passes(pt, __uint_as_float(v.x)) ? 1u : 0u) |
+           (passes(pt, __uint_as_float(v.y)) ? 2u : 0u) |
+           (passes(pt, __uint_as_float(v.z)) ? 4u : 0u) |
+           (passes(pt, __uint_as_float(v.w)) ? 8u : 0u);
+  } else {
+    const u32 q[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+        bits |= (passes(pt, (q[k] >> (8 * b)) & 0xffu) ? 1u : 0u) << (4 * k + b);
+  }
+  return bits;
+}
+
 // Vector form for 16-byte aligned rows (float32: nx % 4 == 0, uint16: nx % 8
 // == 0, uint8: nx % 16 == 0). A warp reads a 1024-voxel segment with 8
 // (float4), 4 or 2 (uint4) coalesced 512-byte loads, all in flight before use.
@@ -110,29 +159,7 @@ __device__ __forceinline__ void thr_segment_vec(const Desc& d, const TV* __restr
 #pragma unroll
   for (int i = 0; i < kLoads; ++i) {
     const u32 x = x0 + (u32)i * (32 * kPer) + (u32)lane * kPer;
-    u32 bits = 0;
-    if (x < nx) {
-      if constexpr (sizeof(TV) == 4) {
-        bits = (passes(pt, __uint_as_float(v[i].x)) ? 1u : 0u) |
-               (passes(pt, __uint_as_float(v[i].y)) ? 2u : 0u) |
-               (passes(pt, __uint_as_float(v[i].z)) ? 4u : 0u) |
-               (passes(pt, __uint_as_float(v[i].w)) ? 8u : 0u);
-      } else if constexpr (sizeof(TV) == 2) {
-        const u32 q[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          bits |= (passes(pt, q[k] & 0xffffu) ? 1u : 0u) << (2 * k);
-          bits |= (passes(pt, q[k] >> 16) ? 1u : 0u) << (2 * k + 1);
-        }
-      } else {
-        const u32 q[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-#pragma unroll
-          for (int b = 0; b < 4; ++b)
-            bits |= (passes(pt, (q[k] >> (8 * b)) & 0xffu) ? 1u : 0u) << (4 * k + b);
-      }
-    }
+    const u32 bits = x < nx ? vec_pass_bits<TV>(pt, v[i]) : 0u;
     u32 t = bits << (kPer * (lane & (kLanesPerWord - 1)));
 #pragma unroll
     for (int o = 1; o < kLanesPerWord; o <<= 1) t |= __shfl_xor_sync(0xffffffffu, t, o);
@@ -154,33 +181,6 @@ __device__ __forceinline__ void thr_segment_vec(const Desc& d, const TV* __restr
 // current step's mask words are written, and give the first flat word after
 // the step (at the end of a warp's range, a ballot over its 32 voxels does).
 constexpr u32 kFlatSpan = 1024;
-
-// The kPer pass bits of one 16-byte vector of values (bit k = element k).
-template <typename TV>
-__device__ __forceinline__ u32 vec_pass_bits(const PassTest& pt, const uint4& v) {
-  u32 bits = 0;
-  if constexpr (sizeof(TV) == 4) {
-    bits = (passes(pt, __uint_as_float(v.x)) ? 1u : 0u) |
-           (passes(pt, __uint_as_float(v.y)) ? 2u : 0u) |
-           (passes(pt, __uint_as_float(v.z)) ? 4u : 0u) |
-           (passes(pt, __uint_as_float(v.w)) ? 8u : 0u);
-  } else if constexpr (sizeof(TV) == 2) {
-    const u32 q[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      bits |= (passes(pt, q[k] & 0xffffu) ? 1u : 0u) << (2 * k);
-      bits |= (passes(pt, q[k] >> 16) ? 1u : 0u) << (2 * k + 1);
-    }
-  } else {
-    const u32 q[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-#pragma unroll
-      for (int b = 0; b < 4; ++b)
-        bits |= (passes(pt, (q[k] >> (8 * b)) & 0xffu) ? 1u : 0u) << (4 * k + b);
-  }
-  return bits;
-}
 
 // The flat word of voxels [x0, x0 + 32) (x0 a multiple of 32, the volume
 // 16-byte aligned): 16-byte loads when all 32 lie inside, else one value at a
@@ -214,18 +214,22 @@ __device__ __forceinline__ u32 flat_word(const PassTest& pt, const TV* __restric
 // Mask words of the rows whose voxels x = 32 w .. start in flat step [a, a +
 // 1024): F = that step's flat words (lane j: word j), f32 = the next step's
 // word 0; r / rel0: the row holding voxel a and its first voxel's position
-// relative to a (<= 0). Positions within the step are 32-bit (nx >= 256, so at
-// most five rows start words in a step).
+// relative to a (<= 0). Positions within the step are 32-bit. NR bounds the
+// rows that start words in a step: 2 when nx >= 1024, 3 when nx >= 512, 5
+// when nx >= 256.
+template <int NR>
 __device__ __forceinline__ void flat_emit(const Desc& d, u32* __restrict__ T, u64 a, u32 F,
                                           u32 f32, u64 r, int rel0, int lim, int lane) {
   const int nx = (int)d.nx, W = (int)d.W;
-  int cnt[5], wlo[5];
+  const u32 tail = (nx & 31) ? (1u << (nx & 31)) - 1u : 0xffffffffu;  // last word's bits
+  const u64 rows_left = d.rows - r;
+  int cnt[NR], wlo[NR];
   int total = 0;
 #pragma unroll
-  for (int k = 0; k < 5; ++k) {
+  for (int k = 0; k < NR; ++k) {
     const int rel = rel0 + k * nx;  // row r + k starts at a + rel
     int lo = 0, hi = 0;
-    if (r + k < d.rows && rel < lim) {
+    if ((u64)k < rows_left && rel < lim) {
       lo = rel >= 0 ? 0 : (-rel + 31) >> 5;
       hi = min(W, (lim - rel + 31) >> 5);  // words with start < lim
       if (hi < lo) hi = lo;
@@ -234,15 +238,15 @@ __device__ __forceinline__ void flat_emit(const Desc& d, u32* __restrict__ T, u6
     wlo[k] = lo;
     total += cnt[k];
   }
-  int pre[5];  // words of the rows before row r + k (constant indices: registers)
+  int pre[NR];  // words of the rows before row r + k (constant indices: registers)
   pre[0] = 0;
 #pragma unroll
-  for (int k = 1; k < 5; ++k) pre[k] = pre[k - 1] + cnt[k - 1];
+  for (int k = 1; k < NR; ++k) pre[k] = pre[k - 1] + cnt[k - 1];
   for (int o0 = 0; o0 < total; o0 += 32) {
     const int o = o0 + lane;
     int k = 0, acc = 0, wl = wlo[0];
 #pragma unroll
-    for (int q = 1; q < 5; ++q)
+    for (int q = 1; q < NR; ++q)
       if (o >= pre[q]) {
         k = q;
         acc = pre[q];
@@ -257,7 +261,7 @@ __device__ __forceinline__ void flat_emit(const Desc& d, u32* __restrict__ T, u6
     if (j == 31) hi = f32;
     if (have) {
       u32 v = sh ? __funnelshift_r(lo, hi, sh) : lo;
-      v &= last_mask(d, (u64)w);
+      if (w == W - 1) v &= tail;
       T[(r + k) * d.W + w] = v;
     }
   }
@@ -298,7 +302,9 @@ __device__ __forceinline__ void thr_flat_range(const Batch& B, u64 s0, u64 s1, i
         f32 = __ballot_sync(0xffffffffu, p);
       }
       const int lim = (int)umin(kFlatSpan, N - a);
-      flat_emit(d, T, a, F, f32, r, rel0, lim, lane);
+      if (nx >= 1024) flat_emit<2>(d, T, a, F, f32, r, rel0, lim, lane);
+      else if (nx >= 512) flat_emit<3>(d, T, a, F, f32, r, rel0, lim, lane);
+      else flat_emit<5>(d, T, a, F, f32, r, rel0, lim, lane);
       F = Fn;
       a = an;
       rel0 -= (int)kFlatSpan;
