@@ -1145,10 +1145,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_front_write(const __grid_consta
   u32 kmin = 0xffffffffu, kmax = 0u;
   u32 cur = 0xffffffffu;  // item whose range the warp accumulates
   // rows per ticket: kRowsPerTicket, fewer when the batch has too few rows to
-  // give every warp about two tickets (a warp walks a ticket's rows one after
-  // another, so short batches finish sooner spread over more warps)
+  // give every warp about four tickets (a warp walks a ticket's rows one after
+  // another; with rows of unequal lengths, as in a batch of images of several
+  // sizes, the last tickets decide when the kernel ends)
   const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
-  const u32 per = (u32)umax(1, umin(kRowsPerTicket, total_rows / (2 * nwarps)));
+  const u32 per = (u32)umax(1, umin(kRowsPerTicket, total_rows / (4 * nwarps)));
   while (true) {
     u64 g0 = 0;
     if (lane == 0) g0 = atomicAdd(&B.ctr[4], per);
