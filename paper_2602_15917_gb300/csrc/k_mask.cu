@@ -454,7 +454,7 @@ __device__ __forceinline__ void range_add(TV v, u32& kmin, u32& kmax) {
 // Two counting kernels give the same results: k_front_count_blk (rows staged
 // by a block, better for narrow rows without dilation) and k_front_count (a
 // warp per tile, better for dilated volumes); the tuning picks one.
-constexpr int kStage = 8;  // mask words a thread has in flight while staging a band
+constexpr int kStage = 16;  // mask words a thread has in flight while staging a band
 
 struct FrontSmem {
   u32 wn[kThreads / 32], wb[kThreads / 32];  // per-warp totals, then offsets
