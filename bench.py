@@ -79,7 +79,7 @@ def group_launches(xs, cfg=None, tuning=None) -> int:
 # kernel of its stage changes.
 TRAFFIC_MB = {
     ("projections64", 2048, 0): {
-        "front": 124.67,
+        "front": 124.89,
         "source": "ncu --set full of the step's kernels (k_front_count_blk + k_front_write), "
                   "bench.py --steps 1 --warmup 3 --no-cpu --extras 0 --tune 0 --graph 0",
     },
