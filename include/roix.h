@@ -392,18 +392,22 @@ size_t roix_slabs_workspace_size(roix_dtype dtype, roix_dims dims, uint64_t slab
 /* --------------------------------------------------------------- serving
  * A serving loop for compression requests that arrive over time (no paper
  * counterpart; a deployment form of roix_compress_batch). The server holds
- * `lanes` contexts, each with its own stream and a workspace of
- * hbm_budget / lanes bytes reserved at creation: the device state (masks,
- * pixel sections, symbols, records, code tables) of the requests it admits.
- * A scheduler thread batches continuously: when a lane is free, the oldest
- * pending request opens a batch and later pending requests with the same
- * dtype and settings join it, in arrival order, while the batch has fewer
- * than max_batch items and its workspace fits the lane. Batches on different
- * lanes run concurrently. Each request's container is the one roix_compress
- * writes for it alone. Requests reference caller-owned device buffers that
- * must stay valid until their completion is polled. */
+ * one device arena of hbm_budget bytes (allocated at creation) and `lanes`
+ * contexts, each with its own stream. A batch's workspace, the device state
+ * (masks, pixel sections, symbols, records, code tables) of the requests it
+ * holds, is taken from the arena when the batch is admitted and returned
+ * when it completes. A scheduler thread batches continuously: when a lane is
+ * free and the oldest pending request's workspace fits the largest free
+ * region of the arena, that request opens a batch and later pending requests
+ * with the same dtype and settings join it, in arrival order, while the batch
+ * has fewer than max_batch items and its workspace still fits the region;
+ * otherwise the oldest request (and the queue behind it) waits until memory
+ * is returned. Batches on different lanes run concurrently. Each request's
+ * container is the one roix_compress writes for it alone. Requests reference
+ * caller-owned device buffers that must stay valid until their completion is
+ * polled. */
 typedef struct {
-  uint64_t hbm_budget;  /* bytes of workspace over all lanes */
+  uint64_t hbm_budget;  /* bytes of the workspace arena the batches share */
   uint32_t lanes;       /* batches in flight at once (>= 1) */
   uint32_t max_batch;   /* requests per batch, 1..64 */
 } roix_server_config;
@@ -428,11 +432,13 @@ typedef struct {
 } roix_completion;
 
 typedef struct {
-  uint64_t submitted, completed, batches, bytes_in, max_queue, pending, lane_bytes;
+  uint64_t submitted, completed, batches, bytes_in, max_queue, pending;
+  uint64_t budget_bytes;  /* the arena */
+  uint64_t in_use_bytes;  /* workspace of the batches in flight */
 } roix_server_stats;
 
 roix_status roix_server_create(int device, const roix_server_config* cfg, roix_server** out);
-/* Thread-safe. ROIX_ENOMEM: the request alone does not fit one lane. */
+/* Thread-safe. ROIX_ENOMEM: the request's workspace alone exceeds the budget. */
 roix_status roix_server_submit(roix_server* s, const roix_request* req);
 /* Non-blocking: moves up to `max` completions to `out`, returns how many. */
 uint32_t roix_server_poll(roix_server* s, roix_completion* out, uint32_t max);

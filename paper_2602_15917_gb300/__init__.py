@@ -88,7 +88,7 @@ class Completion(C.Structure):
 class ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("batches", C.c_uint64),
                 ("bytes_in", C.c_uint64), ("max_queue", C.c_uint64), ("pending", C.c_uint64),
-                ("lane_bytes", C.c_uint64)]
+                ("budget_bytes", C.c_uint64), ("in_use_bytes", C.c_uint64)]
 
 
 class Tuning(C.Structure):

@@ -53,8 +53,22 @@ static_assert(sizeof(State) <= kStateBytes, "state fits its slot");
 
 }  // namespace
 
+void roix::borrow_ws(roix_ctx* ctx, char* ws, size_t bytes) {
+  if (ctx->ws && !ctx->ws_borrowed) {
+    cudaDeviceSynchronize();
+    cudaFree(ctx->ws);
+  }
+  ctx->ws = ws;
+  ctx->ws_bytes = bytes;
+  ctx->ws_borrowed = true;
+}
+
 roix_status roix::ensure_ws(roix_ctx* ctx, size_t bytes, bool exact) {
   if (bytes <= ctx->ws_bytes) return ROIX_OK;
+  if (ctx->ws_borrowed)
+    return fail(ctx, ROIX_ENOMEM, "the borrowed workspace holds " +
+                                      std::to_string(ctx->ws_bytes) + " bytes, " +
+                                      std::to_string(bytes) + " needed");
   if (ctx->ws) {
     // keep an unread device status across the reallocation
     cudaDeviceSynchronize();
@@ -510,7 +524,7 @@ roix_status roix_ctx_create(int device, roix_ctx** out) {
 roix_status roix_ctx_destroy(roix_ctx* ctx) {
   if (!ctx) return ROIX_EINVAL;
   DeviceGuard g(ctx->device);
-  if (ctx->ws) {
+  if (ctx->ws && !ctx->ws_borrowed) {
     cudaDeviceSynchronize();
     cudaFree(ctx->ws);
   }

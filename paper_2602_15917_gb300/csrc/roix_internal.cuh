@@ -597,6 +597,7 @@ struct roix_ctx {
   int sms = 0;
   char* ws = nullptr;
   size_t ws_bytes = 0;
+  bool ws_borrowed = false;  // ws belongs to a server's arena (never grown or freed here)
   roix::u32 pending = 0;  // status carried over a workspace reallocation
   std::string err;
   int profile = 0;        // per-stage events in the fused path
@@ -611,6 +612,9 @@ namespace roix {
 
 // Host: grows the context workspace (synchronises the device); exact = no headroom.
 roix_status ensure_ws(roix_ctx* ctx, size_t bytes, bool exact = false);
+// Host: the context works in a caller's region [ws, ws + bytes) from now on
+// (the serving loop's arena); the region is not grown or freed by the context.
+void borrow_ws(roix_ctx* ctx, char* ws, size_t bytes);
 // Host: workspace bytes of one fused group of items sharing the settings `c`.
 size_t batch_workspace(const Desc& c, const roix_item* items, u32 n);
 

@@ -1,20 +1,26 @@
 // Serving loop: continuous batching of compression requests under an HBM
 // budget (roix_server_*). Host code only; the work is roix_compress_batch.
 //
-// The server owns `lanes` contexts, each with a CUDA stream and a workspace
-// of hbm_budget / lanes bytes reserved at creation (the device state of the
-// requests it admits: masks, pixel sections, symbols, records, code tables).
-// A scheduler thread loops:
+// The server owns one device arena of hbm_budget bytes, allocated at
+// creation, and `lanes` contexts, each with a CUDA stream. A batch's
+// workspace (the device state of its requests: masks, pixel sections,
+// symbols, records, code tables) is carved out of the arena when the batch is
+// admitted (first fit, 256-byte aligned) and given back when it completes, so
+// one large volume may use most of the budget while many small projections
+// share it. A scheduler thread loops:
 //   1. reap: lanes whose completion event has fired hand their requests' sizes
 //      and status (copied to pinned host memory behind the batch) to the
-//      completion queue and become free;
-//   2. admit: while a lane is free and requests are pending, the oldest
-//      pending request opens a batch, and every later pending request with the
-//      same settings joins it in arrival order while the batch has fewer than
-//      max_batch items and its workspace still fits the lane;
+//      completion queue, free their region of the arena and become free;
+//   2. admit: while a lane is free, the oldest pending request opens a batch
+//      if its workspace fits the largest free region of the arena (otherwise
+//      it waits, and so do the requests behind it), and every later pending
+//      request with the same settings joins it in arrival order while the
+//      batch has fewer than max_batch items and its workspace still fits that
+//      region;
 //   3. otherwise wait for a submission or a short poll interval.
 // Requests that arrive while other batches run are admitted as soon as a lane
-// frees up, and batches on different lanes overlap on the device.
+// and the memory they need free up, and batches on different lanes overlap on
+// the device.
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -59,14 +65,19 @@ struct Lane {
   bool busy = false;
   std::vector<Pending> batch;
   double t_admit = 0.0;
+  u64 ws_off = 0, ws_size = 0;  // the batch's region of the arena
 };
+
+constexpr u64 kArenaAlign = 256;
 
 }  // namespace
 
 struct roix_server {
   int device = 0;
   roix_server_config cfg{};
-  size_t lane_bytes = 0;
+  char* arena = nullptr;                     // hbm_budget bytes of device memory
+  std::vector<std::pair<u64, u64>> used;     // regions in use (offset, size), by offset
+  u64 in_use = 0;
   std::vector<Lane> lanes;
   std::mutex mu;
   std::condition_variable cv;
@@ -99,7 +110,44 @@ size_t request_workspace(const roix_request& r, u32 n, const roix_request* more)
   return batch_workspace(c, items.data(), n);
 }
 
-// Lane finished: completions out, lane free (scheduler thread).
+// Arena regions (scheduler thread only). The largest free gap:
+u64 largest_gap(const roix_server* s) {
+  u64 best = 0, at = 0;
+  for (const auto& r : s->used) {
+    if (r.first > at) best = best > r.first - at ? best : r.first - at;
+    at = r.first + r.second;
+  }
+  const u64 end = s->cfg.hbm_budget;
+  if (end > at) best = best > end - at ? best : end - at;
+  return best;
+}
+
+// First fit of `bytes` (a multiple of kArenaAlign); ~0 when nothing fits.
+u64 arena_take(roix_server* s, u64 bytes) {
+  u64 at = 0;
+  size_t k = 0;
+  for (; k <= s->used.size(); ++k) {
+    const u64 next = k < s->used.size() ? s->used[k].first : s->cfg.hbm_budget;
+    if (next >= at && next - at >= bytes) break;
+    if (k < s->used.size()) at = s->used[k].first + s->used[k].second;
+  }
+  if (k > s->used.size()) return ~0ull;
+  s->used.insert(s->used.begin() + k, {at, bytes});
+  return at;
+}
+
+void arena_give(roix_server* s, u64 off) {
+  for (size_t k = 0; k < s->used.size(); ++k)
+    if (s->used[k].first == off) {
+      s->used.erase(s->used.begin() + k);
+      return;
+    }
+}
+
+u64 round_up(u64 v, u64 a) { return (v + a - 1) / a * a; }
+
+// Lane finished: completions out, region back to the arena, lane free
+// (scheduler thread).
 void reap(roix_server* s, Lane& L) {
   const double t = s->now();
   const u32 st = *L.status_host;
@@ -116,6 +164,11 @@ void reap(roix_server* s, Lane& L) {
     s->done.push_back(c);
     ++s->completed;
   }
+  if (L.ws_size) {
+    arena_give(s, L.ws_off);
+    s->in_use -= L.ws_size;
+    L.ws_size = 0;
+  }
   L.batch.clear();
   L.busy = false;
 }
@@ -123,9 +176,13 @@ void reap(roix_server* s, Lane& L) {
 // Forms a batch from the pending queue for a free lane (scheduler thread).
 bool admit(roix_server* s, Lane& L) {
   std::vector<Pending> batch;
+  u64 need = 0;
   {
     std::lock_guard<std::mutex> lock(s->mu);
     if (s->pending.empty()) return false;
+    const u64 room = largest_gap(s);
+    need = request_workspace(s->pending.front().req, 1, nullptr);
+    if (need > room) return false;  // the oldest request waits for memory
     batch.push_back(s->pending.front());
     s->pending.pop_front();
     std::vector<roix_request> reqs{batch[0].req};
@@ -135,13 +192,18 @@ bool admit(roix_server* s, Lane& L) {
         continue;
       }
       reqs.push_back(it->req);
-      if (request_workspace(reqs[0], (u32)reqs.size(), reqs.data() + 1) > s->lane_bytes) {
+      const u64 grown = request_workspace(reqs[0], (u32)reqs.size(), reqs.data() + 1);
+      if (grown > room) {
         reqs.pop_back();
-        break;  // arrival order is kept: later requests wait for the next lane
+        break;  // arrival order is kept: later requests wait for the next batch
       }
+      need = grown;
       batch.push_back(*it);
       it = s->pending.erase(it);
     }
+    L.ws_size = round_up(need, kArenaAlign);
+    L.ws_off = arena_take(s, L.ws_size);  // fits: need <= the largest gap
+    s->in_use += L.ws_size;
   }
   const u32 n = (u32)batch.size();
   std::vector<roix_item> items(n);
@@ -151,6 +213,9 @@ bool admit(roix_server* s, Lane& L) {
   }
   const roix_request& r0 = batch[0].req;
   L.t_admit = s->now();
+  // the batch works in its region; the context status word starts clear
+  borrow_ws(L.ctx, s->arena + L.ws_off, L.ws_size);
+  cudaMemsetAsync(s->arena + L.ws_off, 0, 4, L.stream);
   roix_status st = roix_compress_batch(L.ctx, n, items.data(), r0.dtype, &r0.roi, &r0.eb,
                                        &r0.params, L.stream);
   if (st == ROIX_OK) {
@@ -209,16 +274,20 @@ roix_status roix_server_create(int device, const roix_server_config* cfg, roix_s
   roix_server* s = new roix_server();
   s->device = device;
   s->cfg = *cfg;
-  s->lane_bytes = cfg->hbm_budget / cfg->lanes;
   s->t0 = Clock::now();
   s->lanes.resize(cfg->lanes);
   int prev = -1;
   cudaGetDevice(&prev);
   cudaSetDevice(device);
   roix_status st = ROIX_OK;
+  if (cudaMalloc(&s->arena, cfg->hbm_budget) != cudaSuccess) {
+    cudaGetLastError();
+    s->arena = nullptr;
+    st = ROIX_ENOMEM;
+  }
   for (Lane& L : s->lanes) {
+    if (st != ROIX_OK) break;
     if ((st = roix_ctx_create(device, &L.ctx)) != ROIX_OK) break;
-    if ((st = roix_reserve(L.ctx, s->lane_bytes)) != ROIX_OK) break;
     if (cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess ||
         cudaMalloc(&L.sizes_dev, 8 * cfg->max_batch) != cudaSuccess ||
@@ -241,13 +310,13 @@ roix_status roix_server_create(int device, const roix_server_config* cfg, roix_s
 
 roix_status roix_server_submit(roix_server* s, const roix_request* r) {
   if (!s || !r) return ROIX_EINVAL;
-  // a request must fit one lane on its own, and be a valid call
+  // a request must fit the budget on its own, and be a valid call
   Desc c;
   if (make_desc(nullptr, r->dtype, r->dims, &r->roi, &r->eb, &r->params, &c) != ROIX_OK)
     return ROIX_EINVAL;
   const u64 N = r->dims.nx * r->dims.ny * r->dims.nz;
   if ((N && !r->in) || !r->out || ((uintptr_t)r->out & 15)) return ROIX_EINVAL;
-  if (request_workspace(*r, 1, nullptr) > s->lane_bytes) return ROIX_ENOMEM;
+  if (request_workspace(*r, 1, nullptr) > s->cfg.hbm_budget) return ROIX_ENOMEM;
   {
     std::lock_guard<std::mutex> lock(s->mu);
     if (s->stop) return ROIX_EBUSY;
@@ -293,7 +362,8 @@ roix_status roix_server_get_stats(roix_server* s, roix_server_stats* out) {
   out->bytes_in = s->bytes_in;
   out->max_queue = s->max_queue;
   out->pending = s->pending.size();
-  out->lane_bytes = s->lane_bytes;
+  out->budget_bytes = s->cfg.hbm_budget;
+  out->in_use_bytes = s->in_use;
   return ROIX_OK;
 }
 
@@ -317,6 +387,7 @@ roix_status roix_server_destroy(roix_server* s) {
     if (L.status_host) cudaFreeHost(L.status_host);
     if (L.ctx) roix_ctx_destroy(L.ctx);
   }
+  if (s->arena) cudaFree(s->arena);
   if (prev >= 0) cudaSetDevice(prev);
   delete s;
   return ROIX_OK;

@@ -73,13 +73,59 @@ def test_server_mix_equals_alone():
     alone.close()
 
 
-def test_server_refuses_request_larger_than_a_lane():
+def test_server_refuses_request_larger_than_the_budget():
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
     import paper_2602_15917_gb300 as roix
     srv = roix.RoixServer(0, hbm_budget=64 << 20, lanes=2, max_batch=8)
-    # 32 MiB input: its pixel section alone fills a 32 MiB lane
-    x = torch.zeros((128, 256, 256), dtype=torch.float32, device="cuda")
+    # 64 MiB input: its pixel section alone fills the 64 MiB arena
+    x = torch.zeros((256, 256, 256), dtype=torch.float32, device="cuda")
     out = torch.empty(x.numel() * 4 + 65536, dtype=torch.uint8, device="cuda")
-    assert srv.submit(1, x, out, eb=1e-3) == 2  # ROIX_ENOMEM: never fits 32 MiB
+    assert srv.submit(1, x, out, eb=1e-3) == 2  # ROIX_ENOMEM: never fits
+    srv.close()
+
+
+def test_server_large_request_waits_for_memory_then_runs():
+    """Two requests that each need most of the arena: the second waits until
+    the first has returned its workspace (and the requests behind it wait
+    too, in arrival order), then runs; every container equals the one
+    compressed alone, and the arena is empty at the end."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2602_15917_gb300 as roix
+    cfg = dict(eb=1e-3, eb_mode="rel", threshold=0.1, dilate=1)
+    small = [phantom.ellipsoids(shape=(24, 40, 40), seed=50 + i) for i in range(8)]
+    bigs = [phantom.ellipsoids(shape=(160, 160, 160), seed=77 + i) for i in range(2)]
+    xs = small[:4] + bigs + small[4:]
+    alone = roix.Roix(0)
+    refs = [alone.compress_bytes(x.cuda(), **cfg).cpu().numpy() for x in xs]
+    need_big = alone.workspace_size(bigs[0].shape, torch.float32, bigs[0].numel() * 4 + 65536,
+                                    **cfg)
+    alone.close()
+    budget = int(need_big * 1.3)  # one big request at a time
+    srv = roix.RoixServer(0, hbm_budget=budget, lanes=3, max_batch=4)
+    outs = []
+    for tag, x in enumerate(xs):
+        xd = x.cuda()
+        out = torch.empty(x.numel() * 4 + 65536, dtype=torch.uint8, device="cuda")
+        outs.append((xd, out))
+        assert srv.submit(tag, xd, out, **cfg) == 0
+    assert srv.drain(60.0) == 0
+    got = {}
+    while True:
+        cs = srv.poll()
+        if not cs:
+            break
+        for c in cs:
+            got[c["tag"]] = c
+    assert sorted(got) == list(range(len(xs)))
+    for tag, ref in enumerate(refs):
+        c = got[tag]
+        assert c["status"] == 0
+        buf = outs[tag][1][:c["size"]].cpu().numpy()
+        assert np.array_equal(buf, ref), tag
+    # the second big request was admitted only after the first had completed
+    assert got[5]["t_admit"] >= got[4]["t_done"]
+    stats = srv.stats()
+    assert stats["in_use_bytes"] == 0 and stats["budget_bytes"] == budget
     srv.close()
