@@ -932,7 +932,7 @@ __device__ __forceinline__ void chunk_records(const Item& I, const Src<TV, FROM_
 // item with at most kInScanMax chunks, the warp that counts the item's last
 // chunk scans the chunks' word counts into their offsets.
 template <typename TV, bool FROM_Q>
-__global__ void __launch_bounds__(kThreads) k_pack_count(const __grid_constant__ Batch B) {
+__global__ void __launch_bounds__(kThreads, 4) k_pack_count(const __grid_constant__ Batch B) {
   if (halted(B.status)) return;  // a tile scan of this call gave up
   __shared__ u64 pre[kMaxBatch + 1];
   __shared__ u64 nn[kMaxBatch];

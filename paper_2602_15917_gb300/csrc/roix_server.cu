@@ -31,6 +31,7 @@
 #include <vector>
 
 #include "roix_internal.cuh"
+#include "roix_regions.h"
 
 using namespace roix;
 
@@ -75,9 +76,8 @@ constexpr u64 kArenaAlign = 256;
 struct roix_server {
   int device = 0;
   roix_server_config cfg{};
-  char* arena = nullptr;                     // hbm_budget bytes of device memory
-  std::vector<std::pair<u64, u64>> used;     // regions in use (offset, size), by offset
-  u64 in_use = 0;
+  char* arena = nullptr;  // hbm_budget bytes of device memory
+  Regions regions;        // its regions in use (scheduler thread, under mu)
   std::vector<Lane> lanes;
   std::mutex mu;
   std::condition_variable cv;
@@ -110,40 +110,6 @@ size_t request_workspace(const roix_request& r, u32 n, const roix_request* more)
   return batch_workspace(c, items.data(), n);
 }
 
-// Arena regions (scheduler thread only). The largest free gap:
-u64 largest_gap(const roix_server* s) {
-  u64 best = 0, at = 0;
-  for (const auto& r : s->used) {
-    if (r.first > at) best = best > r.first - at ? best : r.first - at;
-    at = r.first + r.second;
-  }
-  const u64 end = s->cfg.hbm_budget;
-  if (end > at) best = best > end - at ? best : end - at;
-  return best;
-}
-
-// First fit of `bytes` (a multiple of kArenaAlign); ~0 when nothing fits.
-u64 arena_take(roix_server* s, u64 bytes) {
-  u64 at = 0;
-  size_t k = 0;
-  for (; k <= s->used.size(); ++k) {
-    const u64 next = k < s->used.size() ? s->used[k].first : s->cfg.hbm_budget;
-    if (next >= at && next - at >= bytes) break;
-    if (k < s->used.size()) at = s->used[k].first + s->used[k].second;
-  }
-  if (k > s->used.size()) return ~0ull;
-  s->used.insert(s->used.begin() + k, {at, bytes});
-  return at;
-}
-
-void arena_give(roix_server* s, u64 off) {
-  for (size_t k = 0; k < s->used.size(); ++k)
-    if (s->used[k].first == off) {
-      s->used.erase(s->used.begin() + k);
-      return;
-    }
-}
-
 u64 round_up(u64 v, u64 a) { return (v + a - 1) / a * a; }
 
 // Lane finished: completions out, region back to the arena, lane free
@@ -165,8 +131,7 @@ void reap(roix_server* s, Lane& L) {
     ++s->completed;
   }
   if (L.ws_size) {
-    arena_give(s, L.ws_off);
-    s->in_use -= L.ws_size;
+    s->regions.give(L.ws_off);
     L.ws_size = 0;
   }
   L.batch.clear();
@@ -180,7 +145,7 @@ bool admit(roix_server* s, Lane& L) {
   {
     std::lock_guard<std::mutex> lock(s->mu);
     if (s->pending.empty()) return false;
-    const u64 room = largest_gap(s);
+    const u64 room = s->regions.largest_gap();
     need = request_workspace(s->pending.front().req, 1, nullptr);
     if (need > room) return false;  // the oldest request waits for memory
     batch.push_back(s->pending.front());
@@ -201,9 +166,8 @@ bool admit(roix_server* s, Lane& L) {
       batch.push_back(*it);
       it = s->pending.erase(it);
     }
-    L.ws_size = round_up(need, kArenaAlign);
-    L.ws_off = arena_take(s, L.ws_size);  // fits: need <= the largest gap
-    s->in_use += L.ws_size;
+    L.ws_size = round_up(need, kArenaAlign);  // (room is a multiple of kArenaAlign)
+    L.ws_off = s->regions.take(L.ws_size);   // fits: need <= the largest gap
   }
   const u32 n = (u32)batch.size();
   std::vector<roix_item> items(n);
@@ -274,6 +238,7 @@ roix_status roix_server_create(int device, const roix_server_config* cfg, roix_s
   roix_server* s = new roix_server();
   s->device = device;
   s->cfg = *cfg;
+  s->regions.size = cfg->hbm_budget / kArenaAlign * kArenaAlign;
   s->t0 = Clock::now();
   s->lanes.resize(cfg->lanes);
   int prev = -1;
@@ -363,7 +328,7 @@ roix_status roix_server_get_stats(roix_server* s, roix_server_stats* out) {
   out->max_queue = s->max_queue;
   out->pending = s->pending.size();
   out->budget_bytes = s->cfg.hbm_budget;
-  out->in_use_bytes = s->in_use;
+  out->in_use_bytes = s->regions.in_use;
   return ROIX_OK;
 }
 
