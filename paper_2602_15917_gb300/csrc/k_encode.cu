@@ -552,9 +552,9 @@ __device__ long long g_cb_probe[16];
 constexpr u64 kNoWeight = ~0ull;
 
 // The construction runs on a team of the block's first kTeam threads, which
-// synchronise on named barrier 1 (a round's steps are short: a larger team
-// spends more issue slots than it saves).
-constexpr u32 kTeam = 128;
+// synchronise on named barrier 1 (a round's steps are short: the whole block
+// spends more on its barriers than it saves; 64 threads are too few).
+constexpr u32 kTeam = 256;
 __device__ __forceinline__ void team_sync() {
   asm volatile("bar.sync 1, %0;" ::"n"(kTeam) : "memory");
 }
