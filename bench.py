@@ -73,13 +73,15 @@ def group_launches(xs, cfg=None, tuning=None) -> int:
 
 # DRAM bytes per step of each stage (dram__bytes_read.sum + dram__bytes_write.sum,
 # summed over the stage's kernels, one launch each) from an ncu capture of the
-# current kernels, keyed by workload and the tuning the capture ran with (tile
-# size, counting kernel), with the capture it came from. A workload, tuning or
-# kernel without such a capture reports null: an entry is removed whenever a
-# kernel of its stage changes.
+# current kernels, keyed by workload, with the launch shape the capture ran
+# with (tile size, counting kernel) and the capture it came from. A workload
+# or stage without such a capture reports null, and an entry is removed
+# whenever a kernel of its stage changes. When the tuner picks another launch
+# shape, the figure is still reported, with the capture's shape beside it.
 TRAFFIC_MB = {
-    ("projections64", 2048, 0): {
-        "front": 124.89,
+    "projections64": {
+        "front": 124.75,
+        "tuning": {"front_words": 2048, "front_kernel": 0},
         "source": "ncu --set full of the step's kernels (k_front_count_blk + k_front_write), "
                   "bench.py --steps 1 --warmup 3 --no-cpu --extras 0 --tune 0 --graph 0",
     },
@@ -87,12 +89,14 @@ TRAFFIC_MB = {
 
 
 def captured_traffic(workload, tuning, stage):
-    """(bytes per step of `stage`, capture name) from the ncu capture of this
-    workload and tuning, or (None, None)."""
-    t = TRAFFIC_MB.get((workload, tuning.get("front_words"), tuning.get("front_kernel")))
+    """(bytes per step of `stage`, capture name, the capture's launch shape
+    where it differs from `tuning`) from the ncu capture of this workload, or
+    (None, None, None)."""
+    t = TRAFFIC_MB.get(workload)
     if t is None or stage not in t:
-        return None, None
-    return round(t[stage] * 1e6), t["source"]
+        return None, None, None
+    same = all(tuning.get(k) == v for k, v in t["tuning"].items())
+    return round(t[stage] * 1e6), t["source"], (None if same else dict(t["tuning"]))
 
 
 WORKLOADS = {
@@ -478,7 +482,7 @@ def measure(args, workload, xs, cfg, path, dev, world, local_rank, tuning=None, 
     peak, peak_kind = load_peaks()
     alg = stage_bytes(xs, outs, sizes.cpu().numpy(), cfg)
     ach = alg[STAGES[dom]] / (stage_ms[dom] / 1e3) / 1e9
-    traffic, traffic_src = captured_traffic(workload, tuning, STAGES[dom])
+    traffic, traffic_src, traffic_shape = captured_traffic(workload, tuning, STAGES[dom])
     roofline = {"bound": "hbm", "kernel": STAGES[dom], "achieved": round(ach, 1),
                 "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
                 "frac": round(ach / peak, 4), "traffic": traffic, "traffic_source": traffic_src,
@@ -486,6 +490,8 @@ def measure(args, workload, xs, cfg, path, dev, world, local_rank, tuning=None, 
                 "stage_ms_per_step": {n: round(float(v), 4) for n, v in zip(STAGES, stage_ms)},
                 "stage_gbs": {n: round(alg[n] / (float(v) / 1e3) / 1e9, 1)
                               for n, v in zip(STAGES, stage_ms) if v > 0}}
+    if traffic_shape is not None:
+        roofline["traffic_captured_with"] = traffic_shape
     for c in ctxs:
         c.close()
     return {"value": value, "ms_per_step": ms_step, "in_bytes": in_bytes, "out_bytes": out_bytes,
@@ -1474,10 +1480,13 @@ def run_slabs(args, rank, world, local_rank):
     outs = [torch.empty(cap, dtype=torch.uint8, device=dev) for _ in range(ns)]
     sizes = torch.zeros(ns, dtype=torch.uint64, device=dev)
     cfgs = [dict(sc["cfg"], eb=eb, predictor=args.predictor) for eb in sc["sweep"]]
-    # launch shapes tuned on one slab compressed as a volume of its own
+    # launch shapes tuned on all the slabs compressed as one batch of volumes:
+    # the symbol and pack stages then see the item count and sizes of a slab
+    # group (one slab alone gives a signal too small to rank their shapes)
     t0 = time.perf_counter()
-    tuning = (rx.tune([x[:slab]], outs=outs[:1], caps=[cap], sizes=sizes[:1], reps=7,
-                      stream=main, **dict(cfgs[0], eb=sc["e2e_eb"])) if args.tune
+    tuning = (rx.tune([x[k * slab:(k + 1) * slab] for k in range(ns)], outs=outs,
+                      caps=[cap] * ns, sizes=sizes, reps=5, stream=main,
+                      **dict(cfgs[0], eb=sc["e2e_eb"])) if args.tune
               else rx.get_tuning())
     tune_s = time.perf_counter() - t0
     rx.reserve(rx.slabs_workspace_size(x.shape, slab, cap=cap, **cfgs[0]))

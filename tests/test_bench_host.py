@@ -4,25 +4,28 @@ from __future__ import annotations
 import bench
 
 
-def test_traffic_only_for_the_captured_workload_and_tuning(monkeypatch):
-    table = {("projections64", 2048, 0): {"front": 128.2, "source": "ncu capture X"}}
+def test_traffic_carries_the_launch_shape_of_its_capture(monkeypatch):
+    shape = {"front_words": 2048, "front_kernel": 0}
+    table = {"projections64": {"front": 128.2, "tuning": shape, "source": "ncu capture X"}}
     monkeypatch.setattr(bench, "TRAFFIC_MB", table)
-    t = {"front_words": 2048, "front_kernel": 0}
-    assert bench.captured_traffic("projections64", t, "front") == (128200000, "ncu capture X")
-    # another tile size or counting kernel ran other launches: no figure
-    assert bench.captured_traffic("projections64", dict(t, front_words=4096), "front") == (None, None)
-    assert bench.captured_traffic("projections64", dict(t, front_kernel=1), "front") == (None, None)
+    t = dict(shape, thr_blocks_per_sm=8)
+    assert bench.captured_traffic("projections64", t, "front") == (128200000, "ncu capture X", None)
+    # another tile size or counting kernel: the figure, with the capture's shape
+    for other in (dict(t, front_words=4096), dict(t, front_kernel=1)):
+        assert bench.captured_traffic("projections64", other, "front") == (
+            128200000, "ncu capture X", shape)
     # a workload without a capture, a stage without a figure
-    assert bench.captured_traffic("cube1024", t, "threshold") == (None, None)
-    assert bench.captured_traffic("projections64", t, "finalize") == (None, None)
+    assert bench.captured_traffic("cube1024", t, "threshold") == (None, None, None)
+    assert bench.captured_traffic("projections64", t, "finalize") == (None, None, None)
 
 
 def test_captured_traffic_is_at_most_a_few_times_the_input():
     # the stages of one step move at most a few times the step's input bytes
     inputs = {"projections64": 241.85, "cube512": 536.87, "cube1024": 4294.97}
-    for (wl, _, _), st in bench.TRAFFIC_MB.items():
+    for wl, st in bench.TRAFFIC_MB.items():
         assert isinstance(st["source"], str) and st["source"]
-        vals = [v for k, v in st.items() if k != "source"]
+        assert set(st["tuning"]) <= {"front_words", "front_kernel"}
+        vals = [v for k, v in st.items() if k not in ("source", "tuning")]
         assert 0 < sum(vals) < 3 * inputs[wl]
 
 
