@@ -425,7 +425,9 @@ k_symbols(const __grid_constant__ Batch B) {
       }
     };
     if (base + kQuantTile <= n) {  // a whole segment: no bounds checks
-#pragma unroll
+      // (the batches are not unrolled: one copy of kBatch step bodies keeps
+      // the loop inside the instruction cache; all kSteps copies missed it)
+#pragma unroll 1
       for (int b0 = 0; b0 < kSteps; b0 += kBatch) {
         Vec r[kBatch];
 #pragma unroll
