@@ -80,10 +80,11 @@ def group_launches(xs, cfg=None, tuning=None) -> int:
 # shape, the figure is still reported, with the capture's shape beside it.
 TRAFFIC_MB = {
     "projections64": {
-        "front": 124.82,
+        "front": 124.81,
         "tuning": {"front_words": 2048, "front_kernel": 0},
-        "source": "ncu --set full of the step's kernels (k_front_count_blk + k_front_write), "
-                  "bench.py --steps 1 --warmup 3 --no-cpu --extras 0 --tune 0 --graph 0",
+        "source": "ncu --set full, one capture per kernel (k_front_count_blk, k_front_write), "
+                  "one launch each: bench.py --steps 1 --warmup 3 --no-cpu --extras 0 --tune 0 "
+                  "--graph 0",
     },
 }
 
