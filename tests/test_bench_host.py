@@ -40,3 +40,26 @@ def test_sub_line_keeps_the_measurement_fields():
     for k in ("latency", "clocks", "roofline", "tuning"):
         assert line[k] == m[k]
 
+
+
+def _shaped(shape, dtype):
+    import torch
+    # a view of one element: shape, element size and an aligned pointer, no storage
+    return torch.empty(1, dtype=dtype).expand(*shape)
+
+
+def test_launch_count_rules_match_the_profiled_launch_lists():
+    import torch
+    import phantom
+    # 64 uint16 projections 512..2048 wide: the flat binarisation, no scans —
+    # the nine kernels of one step in the ncu launch list of that workload
+    xs = [_shaped((s, s), torch.uint16) for s in phantom.projection_sides(64, 512, 2048, 0)]
+    assert bench.group_launches(xs) == 9
+    # the 1024^3 float32 volume: the row form, the compaction's tile scan, the
+    # pack's chunk scan and records — twelve kernels in its launch list
+    assert bench.group_launches([_shaped((1024, 1024, 1024), torch.float32)]) == 12
+    # a small volume: no scan launches; 1024-voxel rows take the row form
+    assert bench.group_launches([_shaped((16, 64, 1024), torch.float32)]) == 9
+    # a larger tile (front_words) halves the tiles, not the chunks
+    assert bench.group_launches([_shaped((1024, 1024, 1024), torch.float32)],
+                                tuning={"front_words": 16384}) == 12
